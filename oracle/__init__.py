@@ -1,0 +1,162 @@
+"""ctypes wrapper of the multislice-Leiden ORACLE (test infrastructure only).
+
+Only the tests, the smoke check and the benchmark's CPU baseline import this
+package.  The shared object ``liboracle.so`` is compiled from ``oracle.cpp``
+by :func:`build` (plain g++, single-threaded code, ``-ffp-contract=off`` so
+that the fixed FP64 evaluation order of Q is kept on every host).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liboracle.so")
+
+OK, EINVAL, EOVERFLOW = 0, -1, -3
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: oracle status {code}")
+        self.code = code
+
+
+class _Csr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("indptr", C.c_void_p), ("indices", C.c_void_p), ("weights", C.c_void_p)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("n_iterations", C.c_int32), ("K", C.c_int32), ("max_rounds", C.c_int32),
+                ("max_levels", C.c_int32), ("seed", C.c_uint64), ("stop_level", C.c_int32),
+                ("stop_stage", C.c_int32), ("stop_rounds", C.c_int32)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("levels", C.c_int32), ("lm_rounds", C.c_int64),
+                ("lm_edges", C.c_int64), ("lm_moves", C.c_int64), ("last_level0_moves", C.c_int64),
+                ("out_n", C.c_int64), ("next_n", C.c_int64), ("next_nnz", C.c_int64),
+                ("next_checksum", C.c_uint64), ("stop_reason", C.c_int32), ("pad_", C.c_int32)]
+
+
+def build(force: bool = False) -> str:
+    src = os.path.join(HERE, "oracle.cpp")
+    if force or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < max(
+            os.path.getmtime(src), os.path.getmtime(os.path.join(HERE, "oracle.h"))):
+        tmp = LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC",
+                               src, "-o", tmp])
+        os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        L.orc_leiden.argtypes = [P, C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_int64, P, P, P, C.c_int64,
+                                 P, P]
+        L.orc_modularity.argtypes = [P, C.c_int32, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, P]
+        L.orc_move_key.argtypes = [P, C.c_int32, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int64,
+                                   C.c_int64, P]
+        L.orc_lambda.argtypes = [P, C.c_int32, C.c_int64, C.c_int64, P, P]
+        L.orc_count_improving.argtypes = [P, C.c_int32, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, P]
+        L.orc_mix64.argtypes = [C.c_uint64]
+        L.orc_mix64.restype = C.c_uint64
+        L.orc_default_opts.argtypes = [P]
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+class _Slices:
+    """Keeps the numpy arrays alive while the struct array is in use."""
+
+    def __init__(self, snaps):
+        self.arrays = []
+        self.arr = (_Csr * max(len(snaps), 1))()
+        for s, sn in enumerate(snaps):
+            ip = np.ascontiguousarray(sn.indptr, dtype=np.int64)
+            ix = np.ascontiguousarray(sn.indices, dtype=np.int32)
+            w = np.ascontiguousarray(sn.weights, dtype=np.int32)
+            self.arrays += [ip, ix, w]
+            self.arr[s] = _Csr(len(ip) - 1, _ptr(ip), _ptr(ix), _ptr(w))
+        self.T = len(snaps)
+        self.N = (len(snaps[0].indptr) - 1) * len(snaps) if snaps else 0
+
+    @property
+    def ptr(self):
+        return C.cast(self.arr, C.c_void_p)
+
+
+def _check(rc, what):
+    if rc != OK:
+        raise OracleError(rc, what)
+
+
+def leiden(snaps, gamma=(1, 1), omega=(1, 1), n_iterations=2, K=4, max_rounds=100, max_levels=32, seed=0,
+           init=None, stop_level=-1, stop_stage=0, stop_rounds=0):
+    """Returns (labels int32[...], Q, stats dict)."""
+    S = _Slices(snaps)
+    o = _Opts(n_iterations, K, max_rounds, max_levels, seed, stop_level, stop_stage, stop_rounds)
+    cap = max(S.N, 1)
+    out = np.zeros(cap, dtype=np.int32)
+    Q = C.c_double(0.0)
+    st = _Stats()
+    init_a = None if init is None else np.ascontiguousarray(init, dtype=np.int32)
+    rc = lib().orc_leiden(S.ptr, S.T, gamma[0], gamma[1], omega[0], omega[1], C.byref(o), _ptr(init_a),
+                          _ptr(out), cap, C.byref(Q), C.byref(st))
+    _check(rc, "orc_leiden")
+    stats = {f: getattr(st, f) for f, _ in _Stats._fields_}
+    return out[: st.out_n].copy(), Q.value, stats
+
+
+def modularity(snaps, labels, gamma=(1, 1), omega=(1, 1)):
+    S = _Slices(snaps)
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    Q = C.c_double(0.0)
+    _check(lib().orc_modularity(S.ptr, S.T, _ptr(lab), gamma[0], gamma[1], omega[0], omega[1], C.byref(Q)),
+           "orc_modularity")
+    return Q.value
+
+
+def move_key(snaps, labels, v, c, gamma=(1, 1), omega=(1, 1)) -> int:
+    S = _Slices(snaps)
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    out = (C.c_uint64 * 2)()
+    _check(lib().orc_move_key(S.ptr, S.T, _ptr(lab), gamma[0], gamma[1], omega[0], omega[1], v, c, out),
+           "orc_move_key")
+    x = out[0] | (out[1] << 64)
+    return x - (1 << 128) if x >> 127 else x
+
+
+def lambdas(snaps, gamma=(1, 1)):
+    S = _Slices(snaps)
+    lam = np.zeros(2 * S.T, dtype=np.uint64)
+    tm = np.zeros(S.T, dtype=np.int64)
+    _check(lib().orc_lambda(S.ptr, S.T, gamma[0], gamma[1], _ptr(lam), _ptr(tm)), "orc_lambda")
+    return [int(lam[2 * s]) | (int(lam[2 * s + 1]) << 64) for s in range(S.T)], [int(x) for x in tm]
+
+
+def count_improving(snaps, labels, gamma=(1, 1), omega=(1, 1)) -> int:
+    S = _Slices(snaps)
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    cnt = C.c_int64(0)
+    _check(lib().orc_count_improving(S.ptr, S.T, _ptr(lab), gamma[0], gamma[1], omega[0], omega[1],
+                                     C.byref(cnt)), "orc_count_improving")
+    return cnt.value
+
+
+def mix64(x: int) -> int:
+    return int(lib().orc_mix64(x & ((1 << 64) - 1)))

@@ -1,0 +1,723 @@
+// Multislice-Leiden ORACLE -- test infrastructure only (see oracle.h).
+//
+// Plain single-threaded C++: std::map / std::vector containers, no blocking,
+// no fusion, no parallelism.  Each function names the passage of the paper
+// ("Accelerating Dynamic Graph Clustering on GPU Architectures with cuGraph")
+// that it follows; where the paper is silent, the comment states the reading
+// this implementation takes.
+//
+// Units.  Integer edge weights w >= 1 and rationals gamma = gn/gd,
+// omega = on/od.  An adjacency weight W is kept in units of 1/od: an
+// intra-slice edge of weight w counts od*w, a coupling edge counts on.
+// Node strengths k, community sums Sigma and 2m_s are raw (unscaled) sums of
+// intra-slice weights, as in the null term of Eq. multislice-modularity.
+#include "oracle.h"
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <vector>
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+namespace {
+
+const int P_BITS = 64;  // quantisation exponent P of the null coefficient
+
+// ---------------------------------------------------------------------------
+// Counter-based hash: the SplitMix64 output finaliser (Steele, Lea & Flood,
+// "Fast splittable pseudorandom number generators", OOPSLA 2014), written
+// from its published definition.
+uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+// Vertex class of node v for (seed, tag, iteration, level, round) (reading:
+// the synchronous schedule draws one class in [0, K) per node and round from
+// a counter-based hash; tag 0 = local moving, 1 = refinement).
+int vertex_class(uint64_t seed, uint64_t tag, uint64_t it, uint64_t lvl, uint64_t r, uint64_t v, int K) {
+  uint64_t h = mix64(seed ^ mix64(tag ^ mix64(it ^ mix64(lvl ^ mix64(r ^ mix64(v))))));
+  return (int)(h % (uint64_t)K);
+}
+
+// ---------------------------------------------------------------------------
+// A level of the optimisation: nodes, symmetric weighted adjacency (no
+// self-loops) and per-node slice-strength vectors k_{v,s} (only k > 0 kept).
+struct Level {
+  int64_t N = 0;
+  std::vector<std::vector<std::pair<int32_t, int64_t>>> adj;   // (u, W) sorted by u
+  std::vector<std::vector<std::pair<int32_t, int64_t>>> kvec;  // (s, k) sorted by s
+  int64_t nnz() const {
+    int64_t t = 0;
+    for (const auto& a : adj) t += (int64_t)a.size();
+    return t;
+  }
+};
+
+struct Problem {
+  int32_t T = 0;
+  int64_t n = 0;
+  int64_t gn = 1, gd = 1, on = 1, od = 1;
+  std::vector<int64_t> two_m;  // 2m_s
+  std::vector<u128> lambda;    // Lambda_s
+};
+
+bool valid_rational(int64_t num, int64_t den, bool allow_zero) {
+  const int64_t lim = (int64_t)1 << 31;
+  if (den < 1 || den > lim) return false;
+  if (num < (allow_zero ? 0 : 1) || num > lim) return false;
+  return true;
+}
+
+// Input validation (reading: the paper takes simple undirected snapshots; this
+// implementation rejects self-loops, duplicates, asymmetric entries and
+// weights < 1, and requires every snapshot to have the same n).
+int validate(const orc_csr* slices, int32_t T) {
+  if (T < 1 || slices == nullptr) return ORC_EINVAL;
+  int64_t n = slices[0].n;
+  if (n < 0 || n > ((int64_t)1 << 31) - 1) return ORC_EINVAL;
+  if (n * (int64_t)T > ((int64_t)1 << 31) - 1) return ORC_EINVAL;
+  for (int32_t s = 0; s < T; ++s) {
+    const orc_csr& A = slices[s];
+    if (A.n != n) return ORC_EINVAL;
+    if (n > 0 && A.indptr == nullptr) return ORC_EINVAL;
+    if (n == 0) continue;
+    if (A.indptr[0] != 0) return ORC_EINVAL;
+    for (int64_t i = 0; i < n; ++i)
+      if (A.indptr[i + 1] < A.indptr[i]) return ORC_EINVAL;
+    for (int64_t i = 0; i < n; ++i) {
+      for (int64_t e = A.indptr[i]; e < A.indptr[i + 1]; ++e) {
+        int32_t j = A.indices[e];
+        if (j < 0 || j >= n || j == i) return ORC_EINVAL;
+        if (e > A.indptr[i] && A.indices[e - 1] >= j) return ORC_EINVAL;
+        if (A.weights[e] < 1) return ORC_EINVAL;
+        // symmetric: entry (j, i) with the same weight
+        const int32_t* b = A.indices + A.indptr[j];
+        const int32_t* en = A.indices + A.indptr[j + 1];
+        const int32_t* f = std::lower_bound(b, en, (int32_t)i);
+        if (f == en || *f != i) return ORC_EINVAL;
+        if (A.weights[A.indptr[j] + (f - b)] != A.weights[e]) return ORC_EINVAL;
+      }
+    }
+  }
+  return ORC_OK;
+}
+
+// 2m_s and the quantised null coefficients
+//   Lambda_s = floor(gn * 2^P / (gd * 2m_s))   (0 for an edgeless slice).
+// Reading: with per-slice denominators 2m_s, an exact comparison of gains of
+// multi-slice nodes would need lcm(2m_s); both implementations instead
+// compare keys built from Lambda_s, i.e. they optimise Q_MS with
+// gamma'_s = Lambda_s*2m_s/2^P, within 2m_s/2^64 of gamma (relative).
+void slice_masses(const orc_csr* slices, Problem& p) {
+  p.two_m.assign(p.T, 0);
+  p.lambda.assign(p.T, 0);
+  for (int32_t s = 0; s < p.T; ++s) {
+    int64_t t = 0;
+    for (int64_t e = 0; e < (p.n > 0 ? slices[s].indptr[p.n] : 0); ++e) t += slices[s].weights[e];
+    p.two_m[s] = t;
+    if (t > 0) p.lambda[s] = (((u128)(uint64_t)p.gn) << P_BITS) / ((u128)(uint64_t)p.gd * (u128)(uint64_t)t);
+  }
+}
+
+// Overflow guard: every key below stays inside a signed 128-bit integer when
+//   od*sum(2m_s) + 2*on*n_cpl < 2^61   and   gamma*od*sum(2m_s) < 2^61.
+int check_bounds(const Problem& p) {
+  u128 sum2m = 0;
+  for (int64_t t : p.two_m) sum2m += (u128)(uint64_t)t;
+  u128 ncpl = (u128)(uint64_t)p.n * (u128)(uint64_t)(p.T - 1);
+  u128 lim = (u128)1 << 61;
+  if ((u128)(uint64_t)p.od * sum2m + 2 * (u128)(uint64_t)p.on * ncpl >= lim) return ORC_EOVERFLOW;
+  if ((u128)(uint64_t)p.gn * (u128)(uint64_t)p.od * sum2m >= lim * (u128)(uint64_t)p.gd) return ORC_EOVERFLOW;
+  return ORC_OK;
+}
+
+// Level 0: the supra-graph of Eq. supra-adjacency.  Supra-node v = s*n + i.
+// Intra-slice edge (i,j) of snapshot s -> (s*n+i, s*n+j) with W = od*w.
+// Ordinal coupling (i,s)-(i,s+1) for s < T-1 with W = on (omitted when on=0).
+Level build_level0(const orc_csr* slices, const Problem& p) {
+  Level L;
+  L.N = p.n * p.T;
+  L.adj.assign(L.N, {});
+  L.kvec.assign(L.N, {});
+  for (int32_t s = 0; s < p.T; ++s) {
+    for (int64_t i = 0; i < p.n; ++i) {
+      int64_t v = (int64_t)s * p.n + i;
+      auto& a = L.adj[v];
+      if (s > 0 && p.on > 0) a.push_back({(int32_t)(v - p.n), p.on});
+      int64_t k = 0;
+      for (int64_t e = slices[s].indptr[i]; e < slices[s].indptr[i + 1]; ++e) {
+        a.push_back({(int32_t)((int64_t)s * p.n + slices[s].indices[e]), p.od * (int64_t)slices[s].weights[e]});
+        k += slices[s].weights[e];
+      }
+      if (s < p.T - 1 && p.on > 0) a.push_back({(int32_t)(v + p.n), p.on});
+      if (k > 0) L.kvec[v].push_back({s, k});
+    }
+  }
+  return L;
+}
+
+// Sum_s Lambda_s * k_{v,s} * X_s over the slices of v, where X_s is supplied by
+// `get` (a community or sub-community slice sum).
+template <class F>
+u128 null_sum(const Problem& p, const std::vector<std::pair<int32_t, int64_t>>& kv, F get) {
+  u128 t = 0;
+  for (const auto& sk : kv) {
+    int64_t x = get(sk.first);
+    t += p.lambda[sk.first] * (u128)(uint64_t)sk.second * (u128)(uint64_t)x;
+  }
+  return t;
+}
+
+// Exact move key (Eq. multislice-modularity; the change of Q_MS when v joins
+// community c is 2/(2mu) * [g(v,c) - g(v,a)] with
+//   g(v,c) = W(v,c\v)/od - sum_s gamma k_{v,s} Sigma_{c\v,s} / 2m_s).
+// Scaled by od*2^P and with gamma/2m_s quantised to Lambda_s/2^P:
+//   G(v,c) = 2^P W(v,c\v) - od * sum_s Lambda_s k_{v,s} Sigma_{c\v,s}.
+i128 key(const Problem& p, int64_t W, u128 nullsum) {
+  return (((i128)W) << P_BITS) - (i128)((u128)(uint64_t)p.od * nullsum);
+}
+
+typedef std::map<int32_t, int64_t> SliceMap;  // slice -> sum
+
+// ---------------------------------------------------------------------------
+// Local moving (Louvain/Leiden move phase, Sec. 3.2) under the synchronous
+// schedule.  Reading (the paper gives none): in round r, sub-round q, every
+// node whose class is q decides against the state at the start of the
+// sub-round; then all decisions are applied at once.
+struct MoveResult {
+  int64_t rounds = 0, moves = 0, first_round_moves = 0;
+};
+
+const int32_t NO_MOVE = -1;
+const int32_t TO_EMPTY = -2;
+
+MoveResult local_move(const Level& G, const Problem& p, const orc_opts& o, std::vector<int32_t>& c, int it, int lvl,
+                      int max_rounds, orc_stats* st) {
+  MoveResult res;
+  const int64_t N = G.N;
+  std::vector<int64_t> size(N, 0);
+  for (int64_t v = 0; v < N; ++v) size[c[v]]++;
+  std::vector<SliceMap> Sigma(N);  // Sigma[c][s]
+  for (int64_t v = 0; v < N; ++v)
+    for (const auto& sk : G.kvec[v]) Sigma[c[v]][sk.first] += sk.second;
+  auto sig = [&](int32_t comm, int32_t s) -> int64_t {
+    auto it2 = Sigma[comm].find(s);
+    return it2 == Sigma[comm].end() ? 0 : it2->second;
+  };
+  const int64_t nnz = G.nnz();
+  for (int r = 0; r < max_rounds; ++r) {
+    int64_t moved = 0;
+    res.rounds++;
+    if (st) {
+      st->lm_rounds++;
+      st->lm_edges += nnz;
+    }
+    for (int q = 0; q < o.K; ++q) {
+      std::vector<int32_t> target(N, NO_MOVE);
+      // ---- decide (reads the sub-round snapshot only) ----
+      for (int64_t v = 0; v < N; ++v) {
+        if (vertex_class(o.seed, 0, it, lvl, r, v, o.K) != q) continue;
+        const int32_t a = c[v];
+        std::map<int32_t, int64_t> Wmap;  // neighbour community -> W(v, c)
+        for (const auto& uw : G.adj[v]) Wmap[c[uw.first]] += uw.second;
+        const int64_t Wa = Wmap.count(a) ? Wmap[a] : 0;
+        const i128 Ga = key(p, Wa, null_sum(p, G.kvec[v], [&](int32_t s) {
+                              int64_t kvs = 0;
+                              for (const auto& sk : G.kvec[v])
+                                if (sk.first == s) kvs = sk.second;
+                              return sig(a, s) - kvs;  // Sigma_{a\v,s}
+                            }));
+        int32_t best = a;
+        i128 Gbest = Ga;
+        for (const auto& cw : Wmap) {  // ascending community label
+          if (cw.first == a) continue;
+          const i128 Gc = key(p, cw.second, null_sum(p, G.kvec[v], [&](int32_t s) { return sig(cw.first, s); }));
+          if (Gc > Gbest || (Gc == Gbest && cw.first < best)) {
+            best = cw.first;
+            Gbest = Gc;
+          }
+        }
+        // An empty community (key 0) is a candidate when v is not alone; it
+        // ranks after every label on ties.
+        if (size[a] > 1 && Gbest < 0) {
+          best = TO_EMPTY;
+          Gbest = 0;
+        }
+        if (!(Gbest > Ga)) continue;  // strict improvement only
+        // Singleton-swap guard: a node alone in its community moves into
+        // another singleton community only if that label is smaller.
+        if (size[a] == 1 && best != TO_EMPTY && size[best] == 1 && best > a) continue;
+        target[v] = best;
+      }
+      // ---- apply ----
+      int64_t n_moves = 0;
+      for (int64_t v = 0; v < N; ++v) {
+        if (target[v] < 0) continue;
+        const int32_t a = c[v], b = target[v];
+        size[a]--;
+        size[b]++;
+        for (const auto& sk : G.kvec[v]) {
+          Sigma[a][sk.first] -= sk.second;
+          Sigma[b][sk.first] += sk.second;
+        }
+        c[v] = b;
+        n_moves++;
+      }
+      // Moves to an empty community: in ascending node order, the ascending
+      // labels that are unused once every other move is applied and the
+      // movers themselves have left (reading; the paper is silent).
+      std::vector<int64_t> empties;
+      for (int64_t v = 0; v < N; ++v) {
+        if (target[v] != TO_EMPTY) continue;
+        const int32_t a = c[v];
+        size[a]--;
+        for (const auto& sk : G.kvec[v]) Sigma[a][sk.first] -= sk.second;
+        empties.push_back(v);
+      }
+      if (!empties.empty()) {
+        int32_t L = 0;
+        for (int64_t v : empties) {
+          while (size[L] != 0) ++L;
+          c[v] = L;
+          size[L] = 1;
+          for (const auto& sk : G.kvec[v]) Sigma[L][sk.first] += sk.second;
+          ++L;
+          n_moves++;
+        }
+      }
+      moved += n_moves;
+    }
+    res.moves += moved;
+    if (r == 0) res.first_round_moves = moved;
+    if (st) st->lm_moves += moved;
+    if (moved == 0) break;
+  }
+  return res;
+}
+
+// ---------------------------------------------------------------------------
+// Refinement (Leiden, Sec. 3.2; Traag et al. 2019, refinement phase) in the
+// greedy limit.  Inside each local-moving community C every node starts as
+// its own sub-community; one pass of K sub-rounds (class tag 1, round 0).
+// A node still alone in its sub-community and well connected to C joins the
+// well-connected sub-community R of C with the largest positive key
+//   2^P W(v,R) - od * sum_s Lambda_s k_{v,s} K_{R,s}
+// (ties -> smallest label).  A singleton sub-community whose node is active
+// in the same sub-round is not a target.  Well-connectedness of a set X in C:
+//   2^P W(X, C\X) >= od * sum_s Lambda_s K_{X,s} (K_{C,s} - K_{X,s}).
+std::vector<int32_t> refine(const Level& G, const Problem& p, const orc_opts& o, const std::vector<int32_t>& P, int it,
+                            int lvl) {
+  const int64_t N = G.N;
+  std::vector<int32_t> R(N);
+  for (int64_t v = 0; v < N; ++v) R[v] = (int32_t)v;
+  std::vector<SliceMap> KC(N);  // K_{C,s} of local-moving communities
+  for (int64_t v = 0; v < N; ++v)
+    for (const auto& sk : G.kvec[v]) KC[P[v]][sk.first] += sk.second;
+  auto kc = [&](int32_t C, int32_t s) -> int64_t {
+    auto f = KC[C].find(s);
+    return f == KC[C].end() ? 0 : f->second;
+  };
+  std::vector<int64_t> Wc(N, 0);  // W(v, C\v)
+  for (int64_t v = 0; v < N; ++v)
+    for (const auto& uw : G.adj[v])
+      if (P[uw.first] == P[v]) Wc[v] += uw.second;
+
+  for (int q = 0; q < o.K; ++q) {
+    // snapshot statistics, recomputed from scratch
+    std::vector<int64_t> sizeR(N, 0), Wout(N, 0), member(N, -1);
+    std::vector<SliceMap> KR(N);
+    std::vector<int32_t> PofR(N, -1);
+    for (int64_t v = 0; v < N; ++v) {
+      sizeR[R[v]]++;
+      member[R[v]] = v;
+      PofR[R[v]] = P[v];
+      for (const auto& sk : G.kvec[v]) KR[R[v]][sk.first] += sk.second;
+      for (const auto& uw : G.adj[v])
+        if (P[uw.first] == P[v] && R[uw.first] != R[v]) Wout[R[v]] += uw.second;
+    }
+    auto kr = [&](int32_t X, int32_t s) -> int64_t {
+      auto f = KR[X].find(s);
+      return f == KR[X].end() ? 0 : f->second;
+    };
+    std::vector<char> wc(N, 0);
+    for (int64_t X = 0; X < N; ++X) {
+      if (sizeR[X] == 0) continue;
+      u128 rhs = 0;
+      for (const auto& sk : KR[X])
+        rhs += p.lambda[sk.first] * (u128)(uint64_t)sk.second * (u128)(uint64_t)(kc(PofR[X], sk.first) - sk.second);
+      wc[X] = key(p, Wout[X], rhs) >= 0;
+    }
+    std::vector<int32_t> target(N, NO_MOVE);
+    for (int64_t v = 0; v < N; ++v) {
+      if (vertex_class(o.seed, 1, it, lvl, 0, v, o.K) != q) continue;
+      if (sizeR[R[v]] != 1) continue;
+      const int32_t C = P[v];
+      // v alone: well connected iff 2^P W(v,C\v) >= od sum Lambda k (K_C - k)
+      u128 rhs = 0;
+      for (const auto& sk : G.kvec[v])
+        rhs += p.lambda[sk.first] * (u128)(uint64_t)sk.second * (u128)(uint64_t)(kc(C, sk.first) - sk.second);
+      if (key(p, Wc[v], rhs) < 0) continue;
+      std::map<int32_t, int64_t> Wmap;
+      for (const auto& uw : G.adj[v])
+        if (P[uw.first] == C) Wmap[R[uw.first]] += uw.second;
+      int32_t best = NO_MOVE;
+      i128 Gbest = 0;  // key of staying alone
+      for (const auto& xw : Wmap) {
+        const int32_t X = xw.first;
+        if (X == R[v]) continue;
+        if (sizeR[X] == 1 && vertex_class(o.seed, 1, it, lvl, 0, member[X], o.K) == q) continue;
+        if (!wc[X]) continue;
+        const i128 Gx = key(p, xw.second, null_sum(p, G.kvec[v], [&](int32_t s) { return kr(X, s); }));
+        if (Gx > Gbest) {  // ascending X: the first maximum is the smallest label
+          best = X;
+          Gbest = Gx;
+        }
+      }
+      target[v] = best;
+    }
+    for (int64_t v = 0; v < N; ++v)
+      if (target[v] >= 0) R[v] = target[v];
+  }
+  return R;
+}
+
+int64_t count_distinct(const std::vector<int32_t>& x, int64_t N) {
+  std::vector<char> seen(N, 0);
+  int64_t d = 0;
+  for (int32_t v : x)
+    if (!seen[v]) {
+      seen[v] = 1;
+      ++d;
+    }
+  return d;
+}
+
+uint64_t level_checksum(const Level& L) {
+  uint64_t h = 0;
+  for (int64_t x = 0; x < L.N; ++x) {
+    for (const auto& yw : L.adj[x]) h += mix64(mix64(mix64((uint64_t)yw.second) ^ (uint64_t)yw.first) ^ (uint64_t)x);
+    for (const auto& sk : L.kvec[x])
+      h += mix64(mix64(mix64((uint64_t)sk.second) ^ (uint64_t)sk.first) ^ ((uint64_t)x + 0x9E3779B97F4A7C15ULL));
+  }
+  return h;
+}
+
+// Aggregation (Louvain/Leiden, Sec. 3.2): one node per refined community,
+// numbered by ascending refined label; edge weights summed between distinct
+// new nodes (self-loops dropped: no key or check below reads them and Q is
+// always evaluated on level 0); slice vectors summed; the initial label of a
+// new node is the smallest new id inside its local-moving community.
+Level aggregate(const Level& G, const std::vector<int32_t>& P, const std::vector<int32_t>& R,
+                std::vector<int32_t>& next_labels, std::vector<int32_t>& map) {
+  const int64_t N = G.N;
+  std::vector<int32_t> newid(N, -1);
+  std::vector<char> used(N, 0);
+  for (int64_t v = 0; v < N; ++v) used[R[v]] = 1;
+  int32_t Np = 0;
+  for (int64_t L = 0; L < N; ++L)
+    if (used[L]) newid[L] = Np++;
+  std::vector<std::map<int32_t, int64_t>> adjm(Np), km(Np);
+  map.assign(N, 0);
+  for (int64_t v = 0; v < N; ++v) {
+    const int32_t x = newid[R[v]];
+    map[v] = x;
+    for (const auto& uw : G.adj[v]) {
+      const int32_t y = newid[R[uw.first]];
+      if (y != x) adjm[x][y] += uw.second;
+    }
+    for (const auto& sk : G.kvec[v]) km[x][sk.first] += sk.second;
+  }
+  Level H;
+  H.N = Np;
+  H.adj.resize(Np);
+  H.kvec.resize(Np);
+  for (int32_t x = 0; x < Np; ++x) {
+    for (const auto& e : adjm[x]) H.adj[x].push_back(e);
+    for (const auto& e : km[x])
+      if (e.second > 0) H.kvec[x].push_back(e);
+  }
+  std::vector<int32_t> minid(N, INT32_MAX);
+  for (int64_t v = 0; v < N; ++v) minid[P[v]] = std::min(minid[P[v]], map[v]);
+  next_labels.assign(Np, 0);
+  for (int64_t v = 0; v < N; ++v) next_labels[map[v]] = minid[P[v]];
+  return H;
+}
+
+// Canonical labels: renumbered by first occurrence over supra-node order.
+void canonicalise(std::vector<int32_t>& x) {
+  std::map<int32_t, int32_t> ren;
+  for (auto& l : x) {
+    auto f = ren.find(l);
+    if (f == ren.end()) f = ren.emplace(l, (int32_t)ren.size()).first;
+    l = f->second;
+  }
+}
+
+// u128 -> double, round to nearest (the compiler's conversion).
+double u128_to_double(u128 x) { return (double)x; }
+
+// Q_MS in FP64 (Eq. multislice-modularity with ordinal coupling):
+//   2mu Q = I + omega*J - gamma * sum_s (sum_c Sigma_{c,s}^2) / 2m_s,
+//   I = sum of intra-slice weights over ordered pairs in one community,
+//   J = number of ordered coupling pairs in one community,
+//   2mu = sum_s 2m_s + 2*omega*n*(T-1).
+// Fixed evaluation order (reading, shared by both implementations): slice
+// terms as (double)S_s/(double)2m_s summed in ascending s, then omega*J as
+// ((double)on*(double)J)/(double)od, then the numerator, then the division.
+double modularity_of(const orc_csr* slices, const Problem& p, const std::vector<int32_t>& labels) {
+  const int64_t n = p.n;
+  int64_t I = 0, J = 0;
+  std::map<int32_t, SliceMap> sig;
+  for (int32_t s = 0; s < p.T; ++s) {
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t v = (int64_t)s * n + i;
+      int64_t k = 0;
+      for (int64_t e = slices[s].indptr[i]; e < slices[s].indptr[i + 1]; ++e) {
+        const int64_t u = (int64_t)s * n + slices[s].indices[e];
+        if (labels[u] == labels[v]) I += slices[s].weights[e];
+        k += slices[s].weights[e];
+      }
+      if (s > 0 && labels[v - n] == labels[v]) J++;
+      if (s < p.T - 1 && labels[v + n] == labels[v]) J++;
+      sig[labels[v]][s] += k;
+    }
+  }
+  std::vector<u128> S(p.T, 0);
+  for (const auto& cs : sig)
+    for (const auto& sk : cs.second) S[sk.first] += (u128)(uint64_t)sk.second * (u128)(uint64_t)sk.second;
+  double nullsum = 0.0;
+  for (int32_t s = 0; s < p.T; ++s)
+    if (p.two_m[s] > 0) nullsum += u128_to_double(S[s]) / (double)p.two_m[s];
+  const double wJ = ((double)p.on * (double)J) / (double)p.od;
+  const double gam = (double)p.gn / (double)p.gd;
+  int64_t sum2m = 0;
+  for (int64_t t : p.two_m) sum2m += t;
+  const int64_t twomu_num = p.od * sum2m + 2 * p.on * n * (int64_t)(p.T - 1);
+  if (twomu_num == 0) return 0.0;  // reading: no edges and no coupling -> Q = 0
+  const double twomu = (double)twomu_num / (double)p.od;
+  const double num = ((double)I + wJ) - gam * nullsum;
+  return num / twomu;
+}
+
+int setup(const orc_csr* slices, int32_t T, int64_t gn, int64_t gd, int64_t on, int64_t od, Problem& p) {
+  int rc = validate(slices, T);
+  if (rc) return rc;
+  if (!valid_rational(gn, gd, false) || !valid_rational(on, od, true)) return ORC_EINVAL;
+  p.T = T;
+  p.n = slices[0].n;
+  p.gn = gn;
+  p.gd = gd;
+  p.on = on;
+  p.od = od;
+  slice_masses(slices, p);
+  return check_bounds(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t orc_mix64(uint64_t x) { return mix64(x); }
+
+void orc_default_opts(orc_opts* o) {
+  o->n_iterations = 2;  // two optimisation passes (paper Sec. 4)
+  o->K = 4;
+  o->max_rounds = 100;
+  o->max_levels = 32;
+  o->seed = 0;
+  o->stop_level = -1;
+  o->stop_stage = 0;
+  o->stop_rounds = 0;
+}
+
+int orc_lambda(const orc_csr* slices, int32_t T, int64_t gn, int64_t gd, uint64_t* lam, int64_t* two_m) {
+  Problem p;
+  int rc = setup(slices, T, gn, gd, 1, 1, p);
+  if (rc) return rc;
+  for (int32_t s = 0; s < T; ++s) {
+    lam[2 * s] = (uint64_t)p.lambda[s];
+    lam[2 * s + 1] = (uint64_t)(p.lambda[s] >> 64);
+    two_m[s] = p.two_m[s];
+  }
+  return ORC_OK;
+}
+
+int orc_modularity(const orc_csr* slices, int32_t T, const int32_t* labels, int64_t gn, int64_t gd, int64_t on,
+                   int64_t od, double* Q_out) {
+  Problem p;
+  int rc = setup(slices, T, gn, gd, on, od, p);
+  if (rc) return rc;
+  const int64_t N = p.n * T;
+  std::vector<int32_t> lab(labels, labels + N);
+  for (int32_t l : lab)
+    if (l < 0 || l >= N) return ORC_EINVAL;
+  *Q_out = modularity_of(slices, p, lab);
+  return ORC_OK;
+}
+
+int orc_move_key(const orc_csr* slices, int32_t T, const int32_t* labels, int64_t gn, int64_t gd, int64_t on,
+                 int64_t od, int64_t v, int64_t c, uint64_t out[2]) {
+  Problem p;
+  int rc = setup(slices, T, gn, gd, on, od, p);
+  if (rc) return rc;
+  Level G = build_level0(slices, p);
+  if (v < 0 || v >= G.N) return ORC_EINVAL;
+  i128 Gk = 0;
+  if (c >= 0) {
+    int64_t W = 0;
+    for (const auto& uw : G.adj[v])
+      if (labels[uw.first] == c) W += uw.second;
+    SliceMap sig;
+    for (int64_t u = 0; u < G.N; ++u)
+      if (labels[u] == c && u != v)
+        for (const auto& sk : G.kvec[u]) sig[sk.first] += sk.second;
+    Gk = key(p, W, null_sum(p, G.kvec[v], [&](int32_t s) { return sig.count(s) ? sig[s] : 0; }));
+  }
+  out[0] = (uint64_t)(u128)Gk;
+  out[1] = (uint64_t)((u128)Gk >> 64);
+  return ORC_OK;
+}
+
+int orc_count_improving(const orc_csr* slices, int32_t T, const int32_t* labels, int64_t gn, int64_t gd, int64_t on,
+                        int64_t od, int64_t* count) {
+  Problem p;
+  int rc = setup(slices, T, gn, gd, on, od, p);
+  if (rc) return rc;
+  Level G = build_level0(slices, p);
+  std::vector<int64_t> size(G.N, 0);
+  std::vector<SliceMap> Sigma(G.N);
+  for (int64_t v = 0; v < G.N; ++v) {
+    if (labels[v] < 0 || labels[v] >= G.N) return ORC_EINVAL;
+    size[labels[v]]++;
+    for (const auto& sk : G.kvec[v]) Sigma[labels[v]][sk.first] += sk.second;
+  }
+  int64_t cnt = 0;
+  for (int64_t v = 0; v < G.N; ++v) {
+    const int32_t a = labels[v];
+    std::map<int32_t, int64_t> Wmap;
+    for (const auto& uw : G.adj[v]) Wmap[labels[uw.first]] += uw.second;
+    auto ga = key(p, Wmap.count(a) ? Wmap[a] : 0, null_sum(p, G.kvec[v], [&](int32_t s) {
+                    int64_t kvs = 0;
+                    for (const auto& sk : G.kvec[v])
+                      if (sk.first == s) kvs = sk.second;
+                    return (Sigma[a].count(s) ? Sigma[a][s] : 0) - kvs;  // Sigma_{a\v,s}
+                  }));
+    bool imp = (size[a] > 1 && ga < 0);
+    for (const auto& cw : Wmap) {
+      if (cw.first == a) continue;
+      auto gc = key(p, cw.second, null_sum(p, G.kvec[v], [&](int32_t s) {
+                      return Sigma[cw.first].count(s) ? Sigma[cw.first][s] : 0;
+                    }));
+      if (gc > ga) imp = true;
+    }
+    cnt += imp;
+  }
+  *count = cnt;
+  return ORC_OK;
+}
+
+int orc_leiden(const orc_csr* slices, int32_t T, int64_t gn, int64_t gd, int64_t on, int64_t od, const orc_opts* o,
+               const int32_t* init_labels, int32_t* labels_out, int64_t labels_cap, double* Q_out, orc_stats* st) {
+  Problem p;
+  int rc = setup(slices, T, gn, gd, on, od, p);
+  if (rc) return rc;
+  orc_opts opt;
+  orc_default_opts(&opt);
+  if (o) opt = *o;
+  if (opt.n_iterations < 1 || opt.K < 1 || opt.max_rounds < 1 || opt.max_levels < 1) return ORC_EINVAL;
+  orc_stats local{};
+  if (!st) st = &local;
+  std::memset(st, 0, sizeof(*st));
+
+  const Level L0 = build_level0(slices, p);
+  const int64_t N0 = L0.N;
+  std::vector<int32_t> labels(N0);
+  for (int64_t v = 0; v < N0; ++v) {
+    labels[v] = init_labels ? init_labels[v] : (int32_t)v;
+    if (labels[v] < 0 || labels[v] >= N0) return ORC_EINVAL;
+  }
+  std::vector<int32_t> prev;
+  for (int it = 0; it < opt.n_iterations; ++it) {
+    st->iterations = it + 1;
+    Level cur_store;
+    const Level* cur = &L0;
+    std::vector<int32_t> c = labels;
+    std::vector<std::vector<int32_t>> maps;
+    int lvl = 0;
+    for (;; ++lvl) {
+      const bool stop_here = (it == 0 && opt.stop_level == lvl);
+      int rounds = opt.max_rounds;
+      if (stop_here && opt.stop_rounds > 0) rounds = opt.stop_rounds;
+      if (stop_here && opt.stop_rounds < 0) rounds = 0;  // keep the level's initial labels
+      MoveResult mr = local_move(*cur, p, opt, c, it, lvl, rounds, st);
+      if (lvl == 0) st->last_level0_moves = mr.moves;
+      if (stop_here && opt.stop_stage == 1) {
+        if ((int64_t)c.size() > labels_cap) return ORC_EINVAL;
+        std::copy(c.begin(), c.end(), labels_out);
+        st->out_n = (int64_t)c.size();
+        st->levels = lvl + 1;
+        return ORC_OK;
+      }
+      if (count_distinct(c, cur->N) == cur->N) {  // every community is a single node
+        st->stop_reason = 1;
+        break;
+      }
+      if (lvl + 1 >= opt.max_levels) {
+        st->stop_reason = 2;
+        break;
+      }
+      std::vector<int32_t> R = refine(*cur, p, opt, c, it, lvl);
+      if (stop_here && opt.stop_stage == 2) {
+        if ((int64_t)R.size() > labels_cap) return ORC_EINVAL;
+        std::copy(R.begin(), R.end(), labels_out);
+        st->out_n = (int64_t)R.size();
+        st->levels = lvl + 1;
+        return ORC_OK;
+      }
+      if (count_distinct(R, cur->N) == cur->N) {  // aggregation would not shrink the graph
+        st->stop_reason = 3;
+        break;
+      }
+      std::vector<int32_t> nl, mp;
+      Level nxt = aggregate(*cur, c, R, nl, mp);
+      if (stop_here && opt.stop_stage == 3) {
+        if ((int64_t)nl.size() > labels_cap) return ORC_EINVAL;
+        std::copy(nl.begin(), nl.end(), labels_out);
+        st->out_n = (int64_t)nl.size();
+        st->next_n = nxt.N;
+        st->next_nnz = nxt.nnz();
+        st->next_checksum = level_checksum(nxt);
+        st->levels = lvl + 1;
+        return ORC_OK;
+      }
+      maps.push_back(std::move(mp));
+      cur_store = std::move(nxt);
+      cur = &cur_store;
+      c = std::move(nl);
+    }
+    st->levels = lvl + 1;
+    // flatten the level maps down to supra-nodes
+    std::vector<int32_t> out(N0);
+    for (int64_t v = 0; v < N0; ++v) {
+      int64_t x = v;
+      for (const auto& m : maps) x = m[x];
+      out[v] = c[x];
+    }
+    canonicalise(out);
+    const bool same = (it > 0 && out == prev);
+    prev = out;
+    labels = out;
+    if (same) break;
+  }
+  if (labels_cap < N0) return ORC_EINVAL;
+  std::copy(prev.begin(), prev.end(), labels_out);
+  st->out_n = N0;
+  if (Q_out) *Q_out = modularity_of(slices, p, prev);
+  return ORC_OK;
+}
+
+}  // extern "C"

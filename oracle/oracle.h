@@ -1,0 +1,121 @@
+/*
+ * Multislice-Leiden ORACLE -- test infrastructure only.
+ *
+ * A plain, slow, single-threaded CPU statement of what the GPU library
+ * computes.  Only the test-suite, the smoke check and the benchmark's CPU
+ * baseline may load it; the product library never links or calls it, and the
+ * two share no code.
+ *
+ * Method (paper: "Accelerating Dynamic Graph Clustering on GPU Architectures
+ * with cuGraph", Sec. 3.2):
+ *   - objective: multislice modularity Q_MS (Eq. multislice-modularity) with
+ *     ordinal coupling omega between copies of a node in adjacent snapshots
+ *     and the per-slice null model gamma*k_is*k_js/2m_s;
+ *   - supra-graph: Eq. supra-adjacency (A^(t) blocks on the diagonal, omega*I
+ *     on the first off-diagonals);
+ *   - optimiser: Leiden (local moving, refinement, aggregation), as named in
+ *     Sec. 3.2, run under a deterministic synchronous schedule with exact
+ *     integer move keys (the paper fixes no schedule or arithmetic; the
+ *     readings are listed in the design notes of the repository).
+ *
+ * Parity status: Q (orc_modularity) is pinned by the tests to the spectral
+ * form Tr(C^T M C)/2mu (Sec. 3.2), to Newman-Girvan modularity at T=1
+ * (Eq. modularity) and to the omega=0 per-slice decomposition.  The move key
+ * (orc_move_key) is pinned to exact rational differences of Q_MS.  The
+ * partition returned by orc_leiden is "parity unpinned" by the paper (it
+ * prints no partitions); it is checked against invariants only: brute-force
+ * optimum bound, local optimality at convergence, connected communities,
+ * clique recovery, large-omega persistence and omega=0 decoupling.
+ */
+#ifndef MSLICE_ORACLE_H
+#define MSLICE_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes (same meaning as the library's, numbered independently). */
+#define ORC_OK 0
+#define ORC_EINVAL (-1)
+#define ORC_EOVERFLOW (-3)
+
+/* One snapshot: symmetric CSR, sorted columns, no self-loops, weights >= 1. */
+typedef struct {
+  int64_t n;
+  const int64_t* indptr;   /* n+1 */
+  const int32_t* indices;  /* indptr[n] */
+  const int32_t* weights;  /* indptr[n] */
+} orc_csr;
+
+typedef struct {
+  int32_t n_iterations; /* outer Leiden passes (paper Sec. 4: two passes) */
+  int32_t K;            /* sub-rounds per round */
+  int32_t max_rounds;   /* local-moving rounds per level */
+  int32_t max_levels;   /* aggregation levels */
+  uint64_t seed;
+  /* step-level debugging: when stop_level >= 0, iteration 0 stops at that
+   * level after stop_stage (1 = local moving, 2 = refinement, 3 = aggregation)
+   * and writes the raw level labels (not canonical) to labels_out:
+   * stage 1 -> local-moving labels, stage 2 -> refined labels,
+   * stage 3 -> initial labels of the next level.  stop_rounds > 0 caps the
+   * local-moving rounds of that level; stop_rounds < 0 runs none there (the
+   * level keeps its initial labels, so refinement can be driven directly). */
+  int32_t stop_level;
+  int32_t stop_stage;
+  int32_t stop_rounds;
+} orc_opts;
+
+typedef struct {
+  int32_t iterations;      /* outer iterations run */
+  int32_t levels;          /* levels in the last iteration */
+  int64_t lm_rounds;       /* local-moving rounds, all levels and iterations */
+  int64_t lm_edges;        /* sum over those rounds of the level's directed entries */
+  int64_t lm_moves;        /* node moves applied during local moving */
+  int64_t last_level0_moves; /* moves in the level-0 local moving of the last iteration */
+  int64_t out_n;           /* length of labels_out written */
+  int64_t next_n;          /* debug stage 3: nodes of the aggregated level */
+  int64_t next_nnz;        /* debug stage 3: directed entries of the aggregated level */
+  uint64_t next_checksum;  /* debug stage 3: order-free checksum of the aggregated level */
+  int32_t stop_reason;     /* last iteration's level loop ended because: 1 every community
+                              was a single node, 2 max_levels, 3 refinement merged nothing */
+  int32_t pad_;
+} orc_stats;
+
+void orc_default_opts(orc_opts* o);
+
+/* Full multislice Leiden; labels_out holds N = n*T canonical labels
+ * (renumbered by first occurrence), Q_out the FP64 Q_MS with the true gamma.
+ * init_labels (nullable) must lie in [0, N). */
+int orc_leiden(const orc_csr* slices, int32_t T, int64_t gamma_num, int64_t gamma_den,
+               int64_t omega_num, int64_t omega_den, const orc_opts* o, const int32_t* init_labels,
+               int32_t* labels_out, int64_t labels_cap, double* Q_out, orc_stats* st);
+
+/* Q_MS of a level-0 labelling (labels in [0, N)). */
+int orc_modularity(const orc_csr* slices, int32_t T, const int32_t* labels, int64_t gamma_num,
+                   int64_t gamma_den, int64_t omega_num, int64_t omega_den, double* Q_out);
+
+/* Exact integer key G(v, c) of the level-0 supra-node v for community c under
+ * `labels` (c = -1 means an empty community).  Written as a signed 128-bit
+ * integer in out[0] (low) / out[1] (high). */
+int orc_move_key(const orc_csr* slices, int32_t T, const int32_t* labels, int64_t gamma_num,
+                 int64_t gamma_den, int64_t omega_num, int64_t omega_den, int64_t v, int64_t c,
+                 uint64_t out[2]);
+
+/* Quantised null coefficients Lambda_s, as 128-bit (lo, hi) pairs, and 2m_s. */
+int orc_lambda(const orc_csr* slices, int32_t T, int64_t gamma_num, int64_t gamma_den,
+               uint64_t* lambda_lohi, int64_t* two_m);
+
+/* Number of level-0 supra-nodes that have a single move (to a neighbouring
+ * community, or to an empty one when not alone) with a strictly larger key
+ * than staying. */
+int orc_count_improving(const orc_csr* slices, int32_t T, const int32_t* labels, int64_t gamma_num,
+                        int64_t gamma_den, int64_t omega_num, int64_t omega_den, int64_t* count);
+
+/* The counter-based hash used to draw vertex classes (SplitMix64 finaliser). */
+uint64_t orc_mix64(uint64_t x);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,456 @@
+"""Pins of the CPU oracle to facts fixed by the paper and by mathematics.
+
+None of these re-types the oracle's own formula.  Each pin reaches the same
+quantity another way:
+  * Q_MS against the spectral form Tr(C^T M C)/2mu built from the dense
+    supra-modularity matrix (Sec. 3.2: equal for a one-hot assignment C);
+  * Q_MS at T=1 against networkx's Newman-Girvan modularity (Eq. modularity);
+  * Q_MS at omega=0 against the 2m_s-weighted sum of per-slice networkx values;
+  * the integer move key against exact rational differences of Q_MS;
+  * the schedule hash against published SplitMix64 outputs;
+  * the optimiser against brute force over all set partitions, local
+    optimality and connectivity at convergence, clique recovery, large-omega
+    persistence and omega=0 decoupling.
+"""
+import itertools
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_03695_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- helpers
+def dense_slices(snaps):
+    out = []
+    for sn in snaps:
+        n = sn.n
+        A = np.zeros((n, n), dtype=np.int64)
+        for i in range(n):
+            for e in range(sn.indptr[i], sn.indptr[i + 1]):
+                A[i, sn.indices[e]] = sn.weights[e]
+        out.append(A)
+    return out
+
+
+def spectral_Q(snaps, labels, gamma, omega, gamma_slices=None):
+    """Tr(C^T M C) / 2mu with the supra-modularity matrix M (Sec. 3.2):
+    diagonal blocks A^(s) - gamma_s k^(s) k^(s)T / 2m_s, first off-diagonal
+    blocks omega*I (Eq. supra-adjacency), exact rationals."""
+    A = dense_slices(snaps)
+    T, n = len(A), A[0].shape[0]
+    N = n * T
+    g = Fraction(gamma[0], gamma[1])
+    w = Fraction(omega[0], omega[1])
+    M = [[Fraction(0)] * N for _ in range(N)]
+    two_mu = Fraction(0)
+    for s in range(T):
+        k = A[s].sum(axis=1)
+        m2 = int(k.sum())
+        gs = gamma_slices[s] if gamma_slices is not None else g
+        for i in range(n):
+            for j in range(n):
+                x = Fraction(int(A[s][i, j]))
+                two_mu += x
+                if m2 > 0:
+                    x -= gs * int(k[i]) * int(k[j]) / m2
+                M[s * n + i][s * n + j] = x
+        if s + 1 < T:
+            for i in range(n):
+                M[s * n + i][(s + 1) * n + i] = w
+                M[(s + 1) * n + i][s * n + i] = w
+                two_mu += 2 * w
+    labs = sorted(set(int(x) for x in labels))
+    col = {c: j for j, c in enumerate(labs)}
+    tr = Fraction(0)
+    # Tr(C^T M C) = sum over communities of the sum of M over member pairs
+    for a in range(N):
+        for b in range(N):
+            if col[int(labels[a])] == col[int(labels[b])]:
+                tr += M[a][b]
+    if two_mu == 0:
+        return Fraction(0)
+    return tr / two_mu
+
+
+def nx_graph(sn):
+    nx = pytest.importorskip("networkx")
+    G = nx.Graph()
+    G.add_nodes_from(range(sn.n))
+    for i in range(sn.n):
+        for e in range(sn.indptr[i], sn.indptr[i + 1]):
+            j = int(sn.indices[e])
+            if i < j:
+                G.add_edge(i, j, weight=int(sn.weights[e]))
+    return G
+
+
+def communities_of(labels):
+    d = {}
+    for i, c in enumerate(labels):
+        d.setdefault(int(c), set()).add(i)
+    return list(d.values())
+
+
+def set_partitions(n):
+    """All set partitions of range(n) as label arrays (restricted growth)."""
+    a = [0] * n
+
+    def rec(i, m):
+        if i == n:
+            yield list(a)
+            return
+        for c in range(m + 1):
+            a[i] = c
+            yield from rec(i + 1, max(m, c + 1))
+
+    if n == 0:
+        yield []
+        return
+    yield from rec(0, 0)
+
+
+def components_ok(snaps, labels, omega):
+    """Every community induces a connected subgraph of the supra-graph."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    T, n = len(snaps), snaps[0].n
+    N = n * T
+    rows, cols = [], []
+    for s, sn in enumerate(snaps):
+        r = np.repeat(np.arange(n), np.diff(sn.indptr)) + s * n
+        rows.append(r)
+        cols.append(sn.indices.astype(np.int64) + s * n)
+    if omega[0] > 0:
+        for s in range(T - 1):
+            rows.append(np.arange(n) + s * n)
+            cols.append(np.arange(n) + (s + 1) * n)
+    rows = np.concatenate(rows) if rows else np.zeros(0, np.int64)
+    cols = np.concatenate(cols) if cols else np.zeros(0, np.int64)
+    lab = np.asarray(labels)
+    keep = lab[rows] == lab[cols]
+    A = coo_matrix((np.ones(keep.sum()), (rows[keep], cols[keep])), shape=(N, N))
+    ncomp, comp = connected_components(A, directed=False)
+    return ncomp == len(set(lab.tolist()))
+
+
+def rand_rational(rng, lo_num=1):
+    return (int(rng.integers(lo_num, 5)), int(rng.integers(1, 4)))
+
+
+# ----------------------------------------------------------------- hash
+def test_mix64_published_vectors():
+    gamma = 0x9E3779B97F4A7C15
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "splitmix64_seed0.txt")) if not ln.startswith("#")]
+    assert len(rows) == 3
+    for i, out in rows:
+        assert oracle.mix64((int(i) * gamma) % (1 << 64)) == int(out, 16)
+
+
+# ----------------------------------------------------------------- Q_MS
+@pytest.mark.parametrize("seed", range(12))
+def test_modularity_equals_spectral_form(seed):
+    rng = np.random.default_rng(100 + seed)
+    T = int(rng.integers(1, 4))
+    n = int(rng.integers(2, 6))
+    snaps = synth.random_temporal(n, T, p=0.5, w_max=4, seed=seed, p_empty=0.2)
+    gamma = rand_rational(rng)
+    omega = rand_rational(rng, lo_num=0)
+    labels = rng.integers(0, n * T, size=n * T).astype(np.int32)
+    Q = oracle.modularity(snaps, labels, gamma, omega)
+    ref = spectral_Q(snaps, labels, gamma, omega)
+    assert Q == pytest.approx(float(ref), rel=1e-12, abs=1e-15)
+
+
+def test_modularity_T1_newman_girvan():
+    nx = pytest.importorskip("networkx")
+    for seed in range(8):
+        rng = np.random.default_rng(seed)
+        snaps = synth.random_temporal(30, 1, p=0.2, w_max=5, seed=seed)
+        labels = rng.integers(0, 4, size=30).astype(np.int32)
+        for gamma in [(1, 1), (1, 2), (3, 2)]:
+            Q = oracle.modularity(snaps, labels, gamma, (1, 1))
+            ref = nx.community.modularity(nx_graph(snaps[0]), communities_of(labels), weight="weight",
+                                          resolution=gamma[0] / gamma[1])
+            assert Q == pytest.approx(ref, rel=1e-12, abs=1e-14)
+
+
+def test_modularity_omega0_decouples():
+    nx = pytest.importorskip("networkx")
+    for seed in range(6):
+        rng = np.random.default_rng(seed)
+        n, T = 25, 3
+        snaps = synth.random_temporal(n, T, p=0.25, w_max=3, seed=10 + seed)
+        labels = rng.integers(0, n * T, size=n * T).astype(np.int32)
+        Q = oracle.modularity(snaps, labels, (1, 1), (0, 1))
+        m2 = [int(sn.weights.sum()) for sn in snaps]
+        tot = 0.0
+        for s, sn in enumerate(snaps):
+            if m2[s] == 0:
+                continue
+            qs = nx.community.modularity(nx_graph(sn), communities_of(labels[s * n:(s + 1) * n]), weight="weight")
+            tot += m2[s] / sum(m2) * qs
+        assert Q == pytest.approx(tot, rel=1e-12)
+
+
+def test_modularity_edge_cases():
+    # no edges at all and one slice: 2mu = 0, Q reads as 0
+    snaps = synth.random_temporal(4, 1, p=0.0, seed=0)
+    assert oracle.modularity(snaps, np.arange(4), (1, 1), (1, 1)) == 0.0
+    # edgeless slices but coupling: Q = omega*J / 2mu = 1 for one community
+    snaps = synth.random_temporal(3, 2, p=0.0, seed=0)
+    assert oracle.modularity(snaps, np.zeros(6), (1, 1), (1, 1)) == pytest.approx(1.0)
+    # every node alone: Q = -gamma * sum_s sum_i k_i^2 / (2m_s * 2mu)
+    snaps = synth.cliques_temporal([3], 1)
+    assert oracle.modularity(snaps, np.arange(3), (1, 1), (1, 1)) == pytest.approx(-1.0 / 3.0)
+
+
+# ----------------------------------------------------------------- keys
+def test_lambda_definition():
+    snaps = synth.random_temporal(12, 4, p=0.3, w_max=9, seed=3, p_empty=0.3)
+    for gamma in [(1, 1), (3, 7), (2, 1), (1, 3)]:
+        lam, m2 = oracle.lambdas(snaps, gamma)
+        for s, sn in enumerate(snaps):
+            assert m2[s] == int(sn.weights.sum())
+            want = (gamma[0] << 64) // (gamma[1] * m2[s]) if m2[s] else 0
+            assert lam[s] == want
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_move_key_is_scaled_delta_Q(seed):
+    """(G(v,c) - G(v,a)) * 2 / (2mu * od * 2^64) equals the exact change of
+    Q_MS under the quantised resolution gamma'_s = Lambda_s 2m_s / 2^64."""
+    rng = np.random.default_rng(500 + seed)
+    T = int(rng.integers(1, 4))
+    n = int(rng.integers(2, 5))
+    snaps = synth.random_temporal(n, T, p=0.6, w_max=5, seed=seed, p_empty=0.15)
+    gamma = rand_rational(rng)
+    omega = rand_rational(rng, lo_num=0)
+    N = n * T
+    labels = rng.integers(0, max(2, N // 2), size=N).astype(np.int32)
+    lam, m2 = oracle.lambdas(snaps, gamma)
+    gq = [Fraction(lam[s] * m2[s], 1 << 64) if m2[s] else Fraction(0) for s in range(T)]
+    two_mu = Fraction(sum(m2)) + 2 * Fraction(omega[0], omega[1]) * n * (T - 1)
+    if two_mu == 0:
+        return
+    base = spectral_Q(snaps, labels, gamma, omega, gamma_slices=gq)
+    for _ in range(6):
+        v = int(rng.integers(0, N))
+        a = int(labels[v])
+        choices = [int(x) for x in set(labels.tolist())] + [-1]
+        c = choices[int(rng.integers(0, len(choices)))]
+        new = labels.copy()
+        new[v] = c if c >= 0 else N + 7  # a fresh, empty community
+        after = spectral_Q(snaps, new, gamma, omega, gamma_slices=gq)
+        Gc = oracle.move_key(snaps, labels, v, c, gamma, omega)
+        Ga = oracle.move_key(snaps, labels, v, a, gamma, omega)
+        assert Fraction(2 * (Gc - Ga), 1) / (two_mu * omega[1] * (1 << 64)) == after - base
+
+
+def test_quantised_gamma_is_close():
+    snaps = synth.config_graph(1)
+    lam, m2 = oracle.lambdas(snaps, (1, 1))
+    for s in range(len(snaps)):
+        g = Fraction(lam[s] * m2[s], 1 << 64)
+        assert 0 <= 1 - g < Fraction(m2[s], 1 << 64)
+
+
+# ----------------------------------------------------------------- optimiser
+@pytest.mark.parametrize("seed", range(6))
+def test_bruteforce_bound_and_local_optimum(seed):
+    rng = np.random.default_rng(900 + seed)
+    T = int(rng.integers(1, 3))
+    n = int(rng.integers(3, 5 if T == 2 else 9))
+    snaps = synth.random_temporal(n, T, p=0.5, w_max=3, seed=seed)
+    gamma, omega = (1, 1), (1, 2)
+    N = n * T
+    best = -1.0
+    for part in set_partitions(N):
+        lab = np.array(part, dtype=np.int32)
+        q = oracle.modularity(snaps, lab, gamma, omega)
+        if part == list(range(N)) or seed % 3 == 0 and len(set(part)) <= 2:
+            assert q == pytest.approx(float(spectral_Q(snaps, lab, gamma, omega)), rel=1e-12, abs=1e-15)
+        best = max(best, q)
+    labels, Q, st = oracle.leiden(snaps, gamma, omega, n_iterations=20)
+    assert Q <= best + 1e-12
+    assert Q == pytest.approx(oracle.modularity(snaps, labels, gamma, omega), rel=1e-15)
+    if st["last_level0_moves"] == 0:
+        assert oracle.count_improving(snaps, labels, gamma, omega) == 0
+
+
+def test_disjoint_cliques():
+    snaps = synth.cliques_temporal([5, 6, 7, 4], T=3, w=2)
+    labels, Q, _ = oracle.leiden(snaps, (1, 1), (1, 1))
+    n = 22
+    want = np.repeat(np.arange(4), [5, 6, 7, 4])
+    for s in range(3):
+        got = labels[s * n:(s + 1) * n]
+        # same grouping inside the slice, and the same labels in every slice
+        assert len(set(zip(got.tolist(), want.tolist()))) == 4
+        assert (got == labels[:n]).all()
+    assert len(set(labels.tolist())) == 4
+
+
+def test_large_omega_persistence():
+    snaps, _ = synth.planted_partition_temporal(60, 4, n_blocks=3, p_in=0.3, p_out=0.05, switch_frac=0.2, seed=5)
+    labels, Q, st = oracle.leiden(snaps, (1, 1), (10 ** 6, 1), n_iterations=10)
+    n = 60
+    for s in range(1, 4):
+        assert (labels[s * n:(s + 1) * n] == labels[:n]).all()
+
+
+def test_omega_zero_decoupling():
+    snaps, _ = synth.planted_partition_temporal(80, 3, n_blocks=4, p_in=0.3, p_out=0.03, switch_frac=0.1, seed=7)
+    n = 80
+    labels, Q, st = oracle.leiden(snaps, (1, 1), (0, 1), n_iterations=10)
+    sets = [set(labels[s * n:(s + 1) * n].tolist()) for s in range(3)]
+    for a, b in itertools.combinations(sets, 2):
+        assert not (a & b)  # no community spans two slices
+    if st["last_level0_moves"] == 0:
+        for s in range(3):
+            assert oracle.count_improving([snaps[s]], labels[s * n:(s + 1) * n], (1, 1), (0, 1)) == 0
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_converged_invariants(seed):
+    rng = np.random.default_rng(seed)
+    T = int(rng.integers(1, 5))
+    snaps, _ = synth.planted_partition_temporal(int(rng.integers(20, 80)), T, n_blocks=3, p_in=0.25, p_out=0.04,
+                                                switch_frac=0.1, w_max=4, seed=seed)
+    omega = [(1, 1), (1, 10), (10, 1), (0, 1)][seed % 4]
+    labels, Q, st = oracle.leiden(snaps, (1, 1), omega, n_iterations=30)
+    if st["last_level0_moves"] == 0:
+        assert oracle.count_improving(snaps, labels, (1, 1), omega) == 0
+    if st["stop_reason"] == 1:
+        assert components_ok(snaps, labels, omega)
+
+
+def test_converged_invariants_not_vacuous():
+    hits_opt = hits_conn = 0
+    for seed in range(8):
+        rng = np.random.default_rng(seed)
+        T = int(rng.integers(1, 5))
+        snaps, _ = synth.planted_partition_temporal(int(rng.integers(20, 80)), T, n_blocks=3, p_in=0.25,
+                                                    p_out=0.04, switch_frac=0.1, w_max=4, seed=seed)
+        omega = [(1, 1), (1, 10), (10, 1), (0, 1)][seed % 4]
+        _, _, st = oracle.leiden(snaps, (1, 1), omega, n_iterations=30)
+        hits_opt += st["last_level0_moves"] == 0
+        hits_conn += st["stop_reason"] == 1
+    assert hits_opt >= 6 and hits_conn >= 6
+
+
+def test_canonical_labels_and_stats():
+    snaps = synth.config_graph(1)
+    labels, Q, st = oracle.leiden(snaps)
+    first = {}
+    for v, c in enumerate(labels.tolist()):
+        first.setdefault(c, v)
+    assert sorted(first) == list(range(len(first)))
+    assert all(first[c] < first[c + 1] for c in range(len(first) - 1))
+    assert st["iterations"] <= 2 and st["lm_rounds"] >= 2
+    nnz0 = sum(sn.nnz for sn in snaps) + 2 * 1000 * 3
+    assert st["lm_edges"] >= nnz0
+
+
+def test_debug_stages_consistent():
+    snaps = synth.config_graph(1)
+    N = 4000
+    p1, _, s1 = oracle.leiden(snaps, stop_level=0, stop_stage=1)
+    r2, _, s2 = oracle.leiden(snaps, stop_level=0, stop_stage=2)
+    i3, _, s3 = oracle.leiden(snaps, stop_level=0, stop_stage=3)
+    assert len(p1) == len(r2) == N
+    # refined communities nest inside the local-moving communities
+    for R in set(r2.tolist()):
+        assert len(set(p1[r2 == R].tolist())) == 1
+    assert s3["next_n"] == len(set(r2.tolist())) == len(i3)
+    r1, _, _ = oracle.leiden(snaps, stop_level=0, stop_stage=1, stop_rounds=1)
+    assert (r1 != np.arange(N)).any()
+
+
+def test_warm_start_identity():
+    snaps = synth.config_graph(1)
+    labels, Q, _ = oracle.leiden(snaps)
+    l2, Q2, st = oracle.leiden(snaps, init=labels, n_iterations=1)
+    assert Q2 >= Q - 1e-12
+
+
+def test_input_validation():
+    good = synth.random_temporal(6, 2, p=0.5, seed=1)
+    N = 12
+    bad_n = [good[0], synth.random_temporal(5, 1, p=0.5, seed=1)[0]]
+    with pytest.raises(oracle.OracleError):
+        oracle.leiden(bad_n)
+    sn = good[0]
+    # asymmetric weight
+    w = sn.weights.copy()
+    w[0] += 1
+    with pytest.raises(oracle.OracleError):
+        oracle.leiden([synth.Snapshot(sn.indptr, sn.indices, w), good[1]])
+    # zero weight
+    w = sn.weights.copy()
+    w[:] = 0
+    with pytest.raises(oracle.OracleError):
+        oracle.modularity([synth.Snapshot(sn.indptr, sn.indices, w), good[1]], np.zeros(N))
+    # self loop
+    sl = synth.Snapshot(np.array([0, 1, 1], np.int64), np.array([0], np.int32), np.array([1], np.int32))
+    with pytest.raises(oracle.OracleError):
+        oracle.leiden([sl])
+    # unsorted row
+    ip = np.array([0, 2, 3, 4], np.int64)
+    ix = np.array([2, 1, 0, 0], np.int32)
+    with pytest.raises(oracle.OracleError):
+        oracle.leiden([synth.Snapshot(ip, ix, np.ones(4, np.int32))])
+    for g, o in [((0, 1), (1, 1)), ((1, 0), (1, 1)), ((1, 1), (-1, 1)), ((1, 1), (1, 0))]:
+        with pytest.raises(oracle.OracleError):
+            oracle.leiden(good, g, o)
+    with pytest.raises(oracle.OracleError):
+        oracle.leiden(good, init=np.full(N, N))
+    # overflow guard
+    big = synth.Snapshot(sn.indptr, sn.indices, np.full(sn.nnz, 2 ** 30, np.int32))
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.leiden([big] * 2, (1, 1), (1, 2 ** 31))
+    assert e.value.code == oracle.EOVERFLOW
+
+
+def test_empty_graph():
+    snaps = [synth.Snapshot(np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int32))]
+    labels, Q, st = oracle.leiden(snaps)
+    assert len(labels) == 0 and Q == 0.0
+
+
+# ----------------------------------------------------------------- hand-worked examples
+def load_golden_case(name):
+    d = {"edges": []}
+    for ln in open(os.path.join(GOLDEN, name)):
+        ln = ln.split("#")[0].split()
+        if not ln:
+            continue
+        if ln[0] == "e":
+            d["edges"].append(tuple(int(x) for x in ln[1:]))
+        else:
+            d[ln[0]] = [int(x) for x in ln[1:]]
+    n, T = d["n"][0], d["T"][0]
+    snaps = []
+    for s in range(T):
+        es = [e for e in d["edges"] if (len(e) == 3 and s == 0) or (len(e) == 4 and e[3] == s)]
+        u = np.array([e[0] for e in es], np.int64)
+        v = np.array([e[1] for e in es], np.int64)
+        w = np.array([e[2] for e in es], np.int32)
+        snaps.append(synth.csr_from_edges(n, u, v, w))
+    return d, snaps
+
+
+@pytest.mark.parametrize("name", ["local_move_path_ties.txt", "local_move_empty_target.txt",
+                                  "refine_wellconnected.txt"])
+def test_hand_worked_steps(name):
+    d, snaps = load_golden_case(name)
+    lvl, stage, rounds = d["stop"]
+    labels, _, _ = oracle.leiden(snaps, tuple(d["gamma"]), tuple(d["omega"]), K=d["K"][0], seed=d["seed"][0],
+                                 init=np.array(d["init"], np.int32) if "init" in d else None,
+                                 stop_level=lvl, stop_stage=stage, stop_rounds=rounds)
+    assert labels.tolist() == d["expect"]
