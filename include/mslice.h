@@ -1,0 +1,164 @@
+/*
+ * mslice -- multislice-modularity Leiden on one GPU (sm_103a), C ABI.
+ *
+ * The library optimises multislice modularity Q_MS (Mucha et al.), the
+ * objective of Eq. multislice-modularity in "Accelerating Dynamic Graph
+ * Clustering on GPU Architectures with cuGraph" (Sec. 3.2), on the
+ * supra-graph of T snapshots (Eq. supra-adjacency): intra-snapshot edges with
+ * the per-snapshot null model gamma*k_is*k_js/2m_s, plus ordinal coupling
+ * edges of weight omega between the copies of a node in adjacent snapshots.
+ * The optimiser is Leiden (local moving, refinement, aggregation; Sec. 3.2)
+ * under a deterministic synchronous schedule with exact integer move keys,
+ * so that repeated runs, and any other implementation of the same schedule,
+ * give bit-identical partitions.
+ *
+ * Conventions shared by every entry point:
+ *   - Status: 0 = MSLICE_OK, negative = error (below).  On error nothing is
+ *     written to the outputs; mslice_last_error() describes the failure.
+ *   - Snapshots: symmetric CSR over the same n nodes, int64 row pointers
+ *     starting at 0, int32 column indices sorted strictly ascending in every
+ *     row, no self-loops, int32 weights >= 1, entry (j,i) present with the
+ *     same weight as (i,j).  Violations give MSLICE_EINVAL.
+ *   - Supra-node of node i in snapshot s (0-based): v = s*n + i; N = n*T.
+ *   - Rationals gamma = gamma_num/gamma_den > 0 and omega = omega_num/omega_den
+ *     >= 0, each numerator and denominator in [0, 2^31] (denominators >= 1).
+ *   - Overflow guard (MSLICE_EOVERFLOW): omega_den*sum_s 2m_s
+ *     + 2*omega_num*n*(T-1) < 2^61 and gamma*omega_den*sum_s 2m_s < 2^61,
+ *     where 2m_s is the sum of snapshot s's weights over both directions.
+ *   - Ownership: inputs belong to the caller and are read only during the
+ *     call.  A handle owns all device memory it allocates.  Outputs are
+ *     written to caller buffers (host memory unless MSLICE_DEVICE_PTRS).
+ *   - Streams: work runs on the stream given at build time (NULL = the
+ *     legacy default stream); calls return after that stream is synchronised.
+ *     Calls on one handle must not overlap; different handles are
+ *     independent.
+ */
+#ifndef MSLICE_H
+#define MSLICE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MSLICE_OK 0
+#define MSLICE_EINVAL (-1)    /* malformed input, bad rational, bad label */
+#define MSLICE_ENOMEM (-2)    /* device allocation failed */
+#define MSLICE_EOVERFLOW (-3) /* the 128-bit key bound above does not hold */
+#define MSLICE_ECUDA (-4)     /* a CUDA runtime call failed */
+#define MSLICE_ETIMEOUT (-5)  /* a bounded device wait gave up */
+
+/* Input/output pointers are device pointers (build: the snapshot arrays;
+ * leiden/modularity: labels). */
+#define MSLICE_DEVICE_PTRS 1
+
+typedef struct {
+  int64_t n;              /* nodes of the snapshot (equal for all snapshots) */
+  const int64_t* indptr;  /* n+1 row pointers */
+  const int32_t* indices; /* indptr[n] column indices */
+  const int32_t* weights; /* indptr[n] weights >= 1 */
+} mslice_csr;
+
+/* Coupling between snapshots (Eq. multislice-modularity, omega^(sr)):
+ * ORDINAL links (i,s) and (i,s+1) with weight omega. */
+typedef enum { MSLICE_ORDINAL = 0 } mslice_coupling;
+
+typedef struct mslice_graph* mslice_handle;
+
+typedef struct {
+  int32_t n_iterations; /* outer Leiden passes; default 2 (the paper caps runs
+                           at two optimisation passes, Sec. 4) */
+  int32_t K;            /* synchronous sub-rounds per local-moving round; default 4 */
+  int32_t max_rounds;   /* local-moving rounds per level; default 100 */
+  int32_t max_levels;   /* aggregation levels; default 32 */
+  uint64_t seed;        /* seed of the counter-based class hash; default 0 */
+  int64_t gamma_num, gamma_den; /* resolution; default 1/1 */
+  int64_t omega_num, omega_den; /* coupling; default 1/1 (overrides the build value) */
+  int32_t flags;        /* MSLICE_DEVICE_PTRS: init/labels_out are device pointers */
+  /* Step-level debugging (the library's own tests compare it stage by stage):
+   * when stop_level >= 0 the first iteration stops at that level after
+   * stop_stage (1 local moving, 2 refinement, 3 aggregation) and labels_out
+   * receives the raw labels of that level (stage 3: the initial labels of the
+   * next level); stop_rounds > 0 caps the local-moving rounds of that level,
+   * stop_rounds < 0 runs none.  Set stop_level = -1 for normal use. */
+  int32_t stop_level;
+  int32_t stop_stage;
+  int32_t stop_rounds;
+} mslice_opts;
+
+typedef struct {
+  int32_t iterations;        /* outer iterations run */
+  int32_t levels;            /* levels of the last iteration */
+  int64_t lm_rounds;         /* local-moving rounds over all levels/iterations */
+  int64_t lm_edges;          /* sum over those rounds of the level's directed entries */
+  int64_t lm_moves;          /* node moves applied by local moving */
+  int64_t last_level0_moves; /* moves of the last iteration's level-0 local moving */
+  int64_t out_n;             /* labels written */
+  int64_t next_n, next_nnz;  /* debug stage 3: size of the aggregated level */
+  uint64_t next_checksum;    /* debug stage 3: order-free checksum of that level */
+  int32_t stop_reason;       /* 1 all singletons, 2 max_levels, 3 no shrink */
+  int32_t pad_;
+  int64_t kernel_launches;   /* kernels this call launched */
+  double ms_total;           /* device time of the call (CUDA events) */
+  double ms_local_move;      /* ... of which local moving */
+  double ms_refine;          /* ... refinement */
+  double ms_aggregate;       /* ... aggregation */
+  double ms_modularity;      /* ... Q evaluation */
+} mslice_stats;
+
+/* Defaults above; stop_level = -1. */
+void mslice_default_opts(mslice_opts* o);
+
+/* Builds the level-0 supra-graph (Eq. supra-adjacency) on the device from T
+ * snapshots: concatenates the snapshot rows at offset s*n, inserts the
+ * ordinal coupling entries, computes k_v and 2m_s, and validates the input.
+ * The coupling entries are stored as flags, so omega given here is only the
+ * default for later calls.  slices[] are host arrays (copied to the device);
+ * *out receives the handle.  Errors: EINVAL (T < 1, n mismatch, malformed
+ * CSR, bad omega), ENOMEM, ECUDA. */
+int mslice_build(const mslice_csr* slices, int32_t T, mslice_coupling cpl, int64_t omega_num,
+                 int64_t omega_den, mslice_handle* out);
+
+/* As mslice_build; flags = MSLICE_DEVICE_PTRS when the snapshot arrays are
+ * device pointers; stream = cudaStream_t the handle runs on (NULL: default). */
+int mslice_build_ex(const mslice_csr* slices, int32_t T, mslice_coupling cpl, int64_t omega_num,
+                    int64_t omega_den, int32_t flags, void* stream, mslice_handle* out);
+
+/* Multislice Leiden with default options and the given gamma, omega,
+ * max_levels and seed.  labels_out: host int32[N], canonical labels (first
+ * occurrence order over supra-nodes).  Q_out: FP64 Q_MS of those labels with
+ * the exact gamma (Eq. multislice-modularity).  Errors: EINVAL, EOVERFLOW,
+ * ENOMEM, ECUDA. */
+int mslice_leiden(mslice_handle h, int64_t gamma_num, int64_t gamma_den, int64_t omega_num,
+                  int64_t omega_den, int32_t max_levels, uint64_t seed, int32_t* labels_out,
+                  double* Q_out);
+
+/* Full-option Leiden.  init_labels (nullable) = warm start, int32[N] in
+ * [0, N) (checkpoint/resume: a previous result).  labels_out has room for N
+ * labels.  st (nullable) receives counters and phase times. */
+int mslice_leiden_ex(mslice_handle h, const mslice_opts* o, const int32_t* init_labels,
+                     int32_t* labels_out, double* Q_out, mslice_stats* st);
+
+/* Q_MS (Eq. multislice-modularity, ordinal coupling) of int32[N] labels in
+ * [0, N) (host pointer).  Errors: EINVAL, EOVERFLOW, ENOMEM, ECUDA. */
+int mslice_modularity(mslice_handle h, const int32_t* labels, int64_t gamma_num, int64_t gamma_den,
+                      int64_t omega_num, int64_t omega_den, double* Q_out);
+
+/* As mslice_modularity; flags = MSLICE_DEVICE_PTRS for a device pointer. */
+int mslice_modularity_ex(mslice_handle h, const int32_t* labels, int64_t gamma_num, int64_t gamma_den,
+                         int64_t omega_num, int64_t omega_den, int32_t flags, double* Q_out);
+
+/* Sizes of a built handle: N supra-nodes, T, n, stored level-0 entries
+ * (intra + coupling, both directions). Any pointer may be NULL. */
+int mslice_info(mslice_handle h, int64_t* N, int32_t* T, int64_t* n, int64_t* nnz);
+
+/* Releases the handle and its device memory (NULL is ignored). */
+void mslice_free(mslice_handle h);
+
+/* Message of the calling thread's last error ("" if none). */
+const char* mslice_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

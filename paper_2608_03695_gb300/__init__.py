@@ -1,0 +1,209 @@
+"""Python binding of the mslice CUDA library (multislice-modularity Leiden).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``libmslice.so`` (built from ``csrc/`` for sm_103a).  Importing the
+package does not need a GPU; calling into the library does, and there is no
+CPU fallback: a missing library raises :class:`LibraryMissing`.
+
+The entry points mirror ``include/mslice.h``:
+
+* :func:`mslice_build` -- supra-graph of T snapshots (Eq. supra-adjacency)
+* :meth:`Handle.mslice_leiden` -- Leiden on multislice modularity (Sec. 3.2)
+* :meth:`Handle.mslice_modularity` -- Q_MS of a labelling
+  (Eq. multislice-modularity)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmslice.so")
+
+MSLICE_OK, MSLICE_EINVAL, MSLICE_ENOMEM, MSLICE_EOVERFLOW, MSLICE_ECUDA, MSLICE_ETIMEOUT = 0, -1, -2, -3, -4, -5
+MSLICE_DEVICE_PTRS = 1
+MSLICE_ORDINAL = 0
+
+# every symbol include/mslice.h declares
+EXPORTS = ["mslice_default_opts", "mslice_build", "mslice_build_ex", "mslice_leiden", "mslice_leiden_ex",
+           "mslice_modularity", "mslice_modularity_ex", "mslice_info", "mslice_free", "mslice_last_error"]
+
+
+class LibraryMissing(RuntimeError):
+    pass
+
+
+class MsliceError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mslice error {code}: {msg}")
+        self.code = code
+
+
+class Csr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("indptr", C.c_void_p), ("indices", C.c_void_p), ("weights", C.c_void_p)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("n_iterations", C.c_int32), ("K", C.c_int32), ("max_rounds", C.c_int32),
+                ("max_levels", C.c_int32), ("seed", C.c_uint64), ("gamma_num", C.c_int64),
+                ("gamma_den", C.c_int64), ("omega_num", C.c_int64), ("omega_den", C.c_int64),
+                ("flags", C.c_int32), ("stop_level", C.c_int32), ("stop_stage", C.c_int32),
+                ("stop_rounds", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("levels", C.c_int32), ("lm_rounds", C.c_int64),
+                ("lm_edges", C.c_int64), ("lm_moves", C.c_int64), ("last_level0_moves", C.c_int64),
+                ("out_n", C.c_int64), ("next_n", C.c_int64), ("next_nnz", C.c_int64),
+                ("next_checksum", C.c_uint64), ("stop_reason", C.c_int32), ("pad_", C.c_int32),
+                ("kernel_launches", C.c_int64), ("ms_total", C.c_double), ("ms_local_move", C.c_double),
+                ("ms_refine", C.c_double), ("ms_aggregate", C.c_double), ("ms_modularity", C.c_double)]
+
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compiles libmslice.so in-tree (nvcc, sm_103a)."""
+    from . import build_lib
+    return build_lib.build(force=force)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise LibraryMissing(f"{LIB_PATH} is not built; run paper_2608_03695_gb300.build()")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        L.mslice_default_opts.argtypes = [P]
+        L.mslice_build.argtypes = [P, C.c_int32, C.c_int, C.c_int64, C.c_int64, P]
+        L.mslice_build_ex.argtypes = [P, C.c_int32, C.c_int, C.c_int64, C.c_int64, C.c_int32, P, P]
+        L.mslice_leiden.argtypes = [P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_uint64, P, P]
+        L.mslice_leiden_ex.argtypes = [P, P, P, P, P, P]
+        L.mslice_modularity.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, P]
+        L.mslice_modularity_ex.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int32, P]
+        L.mslice_info.argtypes = [P, P, P, P, P]
+        L.mslice_free.argtypes = [P]
+        L.mslice_free.restype = None
+        L.mslice_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc, what):
+    if rc != MSLICE_OK:
+        raise MsliceError(rc, f"{what}: {lib().mslice_last_error().decode()}")
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):  # torch tensor (device or host)
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def default_opts() -> Opts:
+    o = Opts()
+    lib().mslice_default_opts(C.byref(o))
+    return o
+
+
+class Handle:
+    """An mslice handle: the level-0 supra-graph resident on the device."""
+
+    def __init__(self, h, keep):
+        self._h = h
+        self._keep = keep
+        N, T, n, nnz = C.c_int64(), C.c_int32(), C.c_int64(), C.c_int64()
+        _check(lib().mslice_info(h, C.byref(N), C.byref(T), C.byref(n), C.byref(nnz)), "mslice_info")
+        self.N, self.T, self.n, self.nnz = N.value, T.value, n.value, nnz.value
+
+    def close(self):
+        if self._h:
+            lib().mslice_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def mslice_leiden(self, gamma=(1, 1), omega=(1, 1), max_levels=32, seed=0, n_iterations=2, K=4,
+                      max_rounds=100, init=None, stop_level=-1, stop_stage=0, stop_rounds=0, out=None):
+        """Returns (labels, Q, stats).  With ``out`` a device tensor (int32[N])
+        the labels stay on the device (MSLICE_DEVICE_PTRS); ``init`` may then
+        be a device tensor as well."""
+        o = default_opts()
+        o.gamma_num, o.gamma_den = gamma
+        o.omega_num, o.omega_den = omega
+        o.max_levels, o.seed, o.n_iterations, o.K, o.max_rounds = max_levels, seed, n_iterations, K, max_rounds
+        o.stop_level, o.stop_stage, o.stop_rounds = stop_level, stop_stage, stop_rounds
+        dev = out is not None and hasattr(out, "is_cuda") and out.is_cuda
+        if dev:
+            o.flags = MSLICE_DEVICE_PTRS
+            labels = out
+        else:
+            labels = np.zeros(max(self.N, 1), dtype=np.int32)
+        init_a = init
+        if init is not None and not hasattr(init, "data_ptr"):
+            init_a = np.ascontiguousarray(init, dtype=np.int32)
+        Q = C.c_double(0.0)
+        st = Stats()
+        _check(lib().mslice_leiden_ex(self._h, C.byref(o), _ptr(init_a), _ptr(labels), C.byref(Q), C.byref(st)),
+               "mslice_leiden_ex")
+        stats = {f: getattr(st, f) for f, _ in Stats._fields_}
+        if dev:
+            return labels, Q.value, stats
+        return labels[: st.out_n].copy(), Q.value, stats
+
+    def mslice_modularity(self, labels, gamma=(1, 1), omega=(1, 1)):
+        dev = hasattr(labels, "is_cuda") and labels.is_cuda
+        lab = labels if dev else np.ascontiguousarray(labels, dtype=np.int32)
+        Q = C.c_double(0.0)
+        _check(lib().mslice_modularity_ex(self._h, _ptr(lab), gamma[0], gamma[1], omega[0], omega[1],
+                                          MSLICE_DEVICE_PTRS if dev else 0, C.byref(Q)), "mslice_modularity_ex")
+        return Q.value
+
+    # short aliases
+    leiden = mslice_leiden
+    modularity = mslice_modularity
+
+
+def mslice_build(snaps, omega=(1, 1), stream=None, device_ptrs=False) -> Handle:
+    """Builds a handle from T snapshots.  ``snaps`` holds objects with
+    ``indptr``/``indices``/``weights`` arrays (numpy host arrays, or torch
+    device tensors with ``device_ptrs=True``)."""
+    T = len(snaps)
+    arr = (Csr * max(T, 1))()
+    keep = []
+    for s, sn in enumerate(snaps):
+        if device_ptrs:
+            ip, ix, w = sn.indptr, sn.indices, sn.weights
+            n = ip.numel() - 1
+        else:
+            ip = np.ascontiguousarray(sn.indptr, dtype=np.int64)
+            ix = np.ascontiguousarray(sn.indices, dtype=np.int32)
+            w = np.ascontiguousarray(sn.weights, dtype=np.int32)
+            n = len(ip) - 1
+        keep += [ip, ix, w]
+        arr[s] = Csr(n, _ptr(ip).value, _ptr(ix).value if _ptr(ix) is not None else None,
+                     _ptr(w).value if _ptr(w) is not None else None)
+    h = C.c_void_p()
+    st = C.c_void_p(stream) if stream is not None else None
+    _check(lib().mslice_build_ex(C.cast(arr, C.c_void_p), T, MSLICE_ORDINAL, omega[0], omega[1],
+                                 MSLICE_DEVICE_PTRS if device_ptrs else 0, st, C.byref(h)), "mslice_build_ex")
+    return Handle(h, keep)
+
+
+build_graph = mslice_build

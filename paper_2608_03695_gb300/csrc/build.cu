@@ -1,0 +1,194 @@
+// Supra-graph builder (Eq. supra-adjacency): the level-0 CSR over N = n*T
+// supra-nodes.  Row v = s*n + i holds, in ascending column order, the
+// coupling entry to v-n (s > 0), the snapshot-s row of i shifted by s*n, and
+// the coupling entry to v+n (s < T-1).  Entries are 8-byte {col, w} pairs;
+// w = 0 flags a coupling entry, so the coupling weight omega is applied at
+// solve time and an omega sweep needs no rebuild.
+#include "build.h"
+
+#include <algorithm>
+
+namespace mslice {
+
+namespace {
+
+struct SliceTable {
+  const int64_t* const* indptr;
+  const int32_t* const* indices;
+  const int32_t* const* weights;
+};
+
+// indptr of every snapshot: starts at 0, non-decreasing, ends at nnz_s.
+__global__ void k_check_indptr(SliceTable st, const int64_t* nnz, int32_t T, int64_t n, unsigned* status) {
+  const int64_t total = n * (int64_t)T;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < total; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t s = (int32_t)(v / n);
+    const int64_t i = v - (int64_t)s * n;
+    const int64_t a = st.indptr[s][i], b = st.indptr[s][i + 1];
+    bool bad = (b < a) || (a < 0) || (b > nnz[s]);
+    if (i == 0 && a != 0) bad = true;
+    if (i == n - 1 && b != nnz[s]) bad = true;
+    if (bad) atomicOr(status, ERR_BAD_INPUT);
+  }
+}
+
+// Row contents: sorted strictly ascending, in range, no self-loop, w >= 1,
+// and the mirrored entry (j, i) present with the same weight.  One warp per
+// supra-row.
+__global__ void k_check_rows(SliceTable st, int32_t T, int64_t n, unsigned* status) {
+  const int64_t total = n * (int64_t)T;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = (((int64_t)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); v < total; v += warps) {
+    const int32_t s = (int32_t)(v / n);
+    const int64_t i = v - (int64_t)s * n;
+    const int64_t* ip = st.indptr[s];
+    const int32_t* ix = st.indices[s];
+    const int32_t* wt = st.weights[s];
+    const int64_t a = ip[i], b = ip[i + 1];
+    bool bad = false;
+    for (int64_t e = a + lane; e < b; e += 32) {
+      const int32_t j = ix[e];
+      const int32_t w = wt[e];
+      if (j < 0 || j >= n || j == i || w < 1) {
+        bad = true;
+        continue;
+      }
+      if (e > a && ix[e - 1] >= j) bad = true;
+      // binary search for i in row j
+      int64_t lo = ip[j], hi = ip[j + 1];
+      while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (ix[mid] < i)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      if (lo >= ip[j + 1] || ix[lo] != i || wt[lo] != w) bad = true;
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ERR_BAD_INPUT);
+  }
+}
+
+__global__ void k_row_len(SliceTable st, int32_t T, int64_t n, int64_t* len) {
+  const int64_t total = n * (int64_t)T;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < total; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t s = (int32_t)(v / n);
+    const int64_t i = v - (int64_t)s * n;
+    len[v] = (st.indptr[s][i + 1] - st.indptr[s][i]) + (s > 0 ? 1 : 0) + (s < T - 1 ? 1 : 0);
+  }
+}
+
+// One warp per supra-row: copies the shifted snapshot row, adds the coupling
+// flags, and writes k_v = sum of the row's intra weights.
+__global__ void k_fill_rows(SliceTable st, int32_t T, int64_t n, const int64_t* rowptr, int2* adj, int64_t* k) {
+  const int64_t total = n * (int64_t)T;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = (((int64_t)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); v < total; v += warps) {
+    const int32_t s = (int32_t)(v / n);
+    const int64_t i = v - (int64_t)s * n;
+    const int64_t a = st.indptr[s][i], b = st.indptr[s][i + 1];
+    int64_t out = rowptr[v];
+    if (s > 0) {
+      if (lane == 0) adj[out] = make_int2((int32_t)(v - n), 0);
+      out += 1;
+    }
+    const int32_t off = (int32_t)((int64_t)s * n);
+    long long ksum = 0;
+    for (int64_t e = a + lane; e < b; e += 32) {
+      const int32_t w = st.weights[s][e];
+      adj[out + (e - a)] = make_int2(st.indices[s][e] + off, w);
+      ksum += w;
+    }
+    ksum = warp_sum(ksum);
+    if (s < T - 1 && lane == 0) adj[out + (b - a)] = make_int2((int32_t)(v + n), 0);
+    if (lane == 0) k[v] = ksum;
+  }
+}
+
+// 2m_s = sum of k_v over the rows of snapshot s: blockIdx.y is the snapshot,
+// blocks stride over its rows, one atomic per block.
+__global__ void k_slice_mass(const int64_t* k, int64_t n, ull* two_m) {
+  __shared__ ull sm[32];
+  const int32_t s = blockIdx.y;
+  ull t = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    t += (ull)k[(int64_t)s * n + i];
+  t = warp_sum(t);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    ull x = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0ull;
+    x = warp_sum(x);
+    if (threadIdx.x == 0 && x) atomicAdd(&two_m[s], x);
+  }
+}
+
+__global__ void k_lambda(const int64_t* two_m, int32_t T, long long gn, long long gd, u128* lam) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= T) return;
+  const long long t = two_m[s];
+  lam[s] = t > 0 ? (((u128)(ull)gn) << P_BITS) / ((u128)(ull)gd * (u128)(ull)t) : (u128)0;
+}
+
+unsigned gs(int64_t n, int per) {
+  int64_t g = (n + per - 1) / per;
+  if (g > 152 * 16) g = 152 * 16;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+void build_supra(Ctx& c, const std::vector<const int64_t*>& indptr, const std::vector<const int32_t*>& indices,
+                 const std::vector<const int32_t*>& weights, const std::vector<int64_t>& nnz, int64_t n,
+                 SupraGraph& g) {
+  const int32_t T = (int32_t)indptr.size();
+  g.T = T;
+  g.n = n;
+  g.N = n * T;
+  // device table of snapshot pointers
+  const int64_t** d_ip = c.ws->get<const int64_t*>("b_ip", T);
+  const int32_t** d_ix = c.ws->get<const int32_t*>("b_ix", T);
+  const int32_t** d_wt = c.ws->get<const int32_t*>("b_wt", T);
+  int64_t* d_nnz = c.ws->get<int64_t>("b_nnz", T);
+  check_cuda(cudaMemcpyAsync(d_ip, indptr.data(), T * sizeof(void*), cudaMemcpyHostToDevice, c.stream), "copy");
+  check_cuda(cudaMemcpyAsync(d_ix, indices.data(), T * sizeof(void*), cudaMemcpyHostToDevice, c.stream), "copy");
+  check_cuda(cudaMemcpyAsync(d_wt, weights.data(), T * sizeof(void*), cudaMemcpyHostToDevice, c.stream), "copy");
+  check_cuda(cudaMemcpyAsync(d_nnz, nnz.data(), T * sizeof(int64_t), cudaMemcpyHostToDevice, c.stream), "copy");
+  SliceTable st{d_ip, d_ix, d_wt};
+  check_cuda(cudaMemsetAsync(c.d_status, 0, sizeof(unsigned), c.stream), "memset");
+  if (g.N > 0) {
+    launch(c, k_check_indptr, dim3(gs(g.N, 256)), dim3(256), 0, st, (const int64_t*)d_nnz, T, n, c.d_status);
+    check_status(c, "snapshot row pointers");
+    launch(c, k_check_rows, dim3(gs(g.N * 32, 256)), dim3(256), 0, st, T, n, c.d_status);
+    check_status(c, "snapshot rows");
+  }
+  int64_t* len = c.ws->get<int64_t>("b_len", g.N + 1);
+  g.rowptr = static_cast<int64_t*>(g.mem.get_bytes("rowptr0", (g.N + 1) * sizeof(int64_t)));
+  if (g.N > 0) launch(c, k_row_len, dim3(gs(g.N, 256)), dim3(256), 0, st, T, n, len);
+  int64_t* d_total = c.ws->get<int64_t>("b_total", 1);
+  scan_excl(c, len, g.rowptr, g.N, d_total);
+  check_cuda(cudaMemcpyAsync(g.rowptr + g.N, d_total, sizeof(int64_t), cudaMemcpyDeviceToDevice, c.stream), "copy");
+  g.nnz = *static_cast<int64_t*>(readback(c, d_total, sizeof(int64_t)));
+  g.adj = static_cast<int2*>(g.mem.get_bytes("adj0", (g.nnz ? g.nnz : 1) * sizeof(int2)));
+  g.k = static_cast<int64_t*>(g.mem.get_bytes("k0", (g.N ? g.N : 1) * sizeof(int64_t)));
+  g.two_m = static_cast<int64_t*>(g.mem.get_bytes("two_m", T * sizeof(int64_t)));
+  check_cuda(cudaMemsetAsync(g.two_m, 0, T * sizeof(int64_t), c.stream), "memset");
+  if (g.N > 0) {
+    launch(c, k_fill_rows, dim3(gs(g.N * 32, 256)), dim3(256), 0, st, T, n, (const int64_t*)g.rowptr, g.adj, g.k);
+    unsigned gx = (unsigned)std::min<int64_t>((n + 255) / 256, 64);
+    launch(c, k_slice_mass, dim3(gx, T), dim3(256), 0, (const int64_t*)g.k, n, (ull*)g.two_m);
+  }
+  g.two_m_host.resize(T);
+  check_cuda(cudaMemcpyAsync(g.two_m_host.data(), g.two_m, T * sizeof(int64_t), cudaMemcpyDeviceToHost, c.stream),
+             "copy");
+  sync(c);
+  g.nnz_intra = g.nnz - 2 * n * (int64_t)(T - 1);
+}
+
+void compute_lambda(Ctx& c, const SupraGraph& g, long long gn, long long gd, u128* lam) {
+  launch(c, k_lambda, dim3(grid_for(g.T, 128)), dim3(128), 0, (const int64_t*)g.two_m, g.T, gn, gd, lam);
+}
+
+}  // namespace mslice

@@ -1,0 +1,188 @@
+// Device-side building blocks shared by the mslice kernels (sm_103a).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mslice {
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+typedef unsigned long long ull;
+
+constexpr int P_BITS = 64;           // quantisation exponent of the null coefficient
+constexpr int32_t NO_MOVE = -1;      // decision: stay
+constexpr int32_t TO_EMPTY = -2;     // decision: move to an empty community
+constexpr ull EMPTY_KEY = ~0ull;     // free hash slot
+
+// Error bits of the device status word.
+constexpr unsigned ERR_HASH_FULL = 1u;   // a probe sequence exceeded the table
+constexpr unsigned ERR_BAD_INPUT = 2u;   // validation of a snapshot failed
+constexpr unsigned ERR_INTERNAL = 4u;    // an internal consistency check failed
+
+// SplitMix64 output finaliser (Steele, Lea & Flood, OOPSLA 2014), written from
+// its published definition.  Drives the vertex classes of the schedule.
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+// Class of node v in round r of level lvl, iteration it; tag 0 = local
+// moving, 1 = refinement.  The chain folds one counter per step.
+__host__ __device__ __forceinline__ int vertex_class(uint64_t seed, uint64_t tag, uint64_t it, uint64_t lvl,
+                                                     uint64_t r, uint64_t v, int K) {
+  uint64_t h = mix64(seed ^ mix64(tag ^ mix64(it ^ mix64(lvl ^ mix64(r ^ mix64(v))))));
+  return (int)(h % (uint64_t)K);
+}
+
+// -------------------------------------------------------------------------
+// Open-addressing hash keyed by a 64-bit key with an int64 payload, one
+// 16-byte slot per entry so a probe touches one sector.  Linear probing over
+// an arbitrary capacity (Lemire's multiply-high range reduction), bounded
+// probe length; payload updates are integer atomics, so the stored values do
+// not depend on the order of the updates.
+struct alignas(16) Slot {
+  ull key;
+  long long val;
+};
+
+struct HashView {
+  Slot* slots;
+  uint64_t cap;
+  unsigned* status;
+};
+
+__device__ __forceinline__ uint64_t hash_home(ull key, uint64_t cap) {
+  return __umul64hi(mix64(key ^ 0x9E3779B97F4A7C15ULL), cap);
+}
+
+__device__ __forceinline__ ull pack_cs(int32_t c, int32_t s) {
+  return ((ull)(uint32_t)c << 32) | (uint32_t)s;
+}
+
+__device__ __forceinline__ void hash_add(const HashView& h, ull key, long long delta) {
+  uint64_t i = hash_home(key, h.cap);
+  for (uint64_t probe = 0; probe < h.cap; ++probe) {
+    ull k = h.slots[i].key;
+    if (k == key) {
+      atomicAdd((ull*)&h.slots[i].val, (ull)delta);
+      return;
+    }
+    if (k == EMPTY_KEY) {
+      ull prev = atomicCAS(&h.slots[i].key, EMPTY_KEY, key);
+      if (prev == EMPTY_KEY || prev == key) {
+        atomicAdd((ull*)&h.slots[i].val, (ull)delta);
+        return;
+      }
+    }
+    i = (i + 1 == h.cap) ? 0 : i + 1;
+  }
+  atomicOr(h.status, ERR_HASH_FULL);
+}
+
+// Read-only lookup (0 when absent).  Only valid while no thread inserts.
+__device__ __forceinline__ long long hash_get(const HashView& h, ull key) {
+  uint64_t i = hash_home(key, h.cap);
+  for (uint64_t probe = 0; probe < h.cap; ++probe) {
+    const Slot s = h.slots[i];
+    if (s.key == key) return s.val;
+    if (s.key == EMPTY_KEY) return 0;
+    i = (i + 1 == h.cap) ? 0 : i + 1;
+  }
+  return 0;
+}
+
+// -------------------------------------------------------------------------
+// Unsigned 128-bit accumulation into two 64-bit words with carry propagation.
+// Exact as long as the true sum stays below 2^128.
+__device__ __forceinline__ void atomic_add_u128(ull* lohi, u128 x) {
+  ull lo = (ull)x, hi = (ull)(x >> 64);
+  ull old = atomicAdd(&lohi[0], lo);
+  if (old + lo < old) hi += 1;
+  if (hi) atomicAdd(&lohi[1], hi);
+}
+
+// u128 -> double, round to nearest even.  The top 64 significant bits are
+// converted by the hardware's correctly rounded u64 conversion with every
+// lower bit folded into the least significant one (a sticky bit); since the
+// u64 holds 11 bits below the double's rounding position, the sticky bit
+// decides ties exactly as an infinitely precise conversion would.
+__device__ __forceinline__ double u128_to_double(u128 x) {
+  ull hi = (ull)(x >> 64), lo = (ull)x;
+  if (hi == 0) return __ull2double_rn(lo);
+  int lz = __clzll((long long)hi);
+  u128 y = x << lz;
+  ull top = (ull)(y >> 64);
+  ull rest = (ull)y;
+  top |= (rest != 0) ? 1ull : 0ull;
+  return ldexp(__ull2double_rn(top), 64 - lz);
+}
+
+// -------------------------------------------------------------------------
+// Candidate of a move decision: larger key wins, ties go to the smaller label.
+struct Cand {
+  i128 G;
+  int32_t label;  // INT32_MAX = none
+};
+
+__device__ __forceinline__ bool better(const Cand& a, const Cand& b) {
+  if (a.label == INT32_MAX) return false;
+  if (b.label == INT32_MAX) return true;
+  if (a.G != b.G) return a.G > b.G;
+  return a.label < b.label;
+}
+
+__device__ __forceinline__ Cand shfl_cand(const Cand& c, int src) {
+  Cand o;
+  ull lo = (ull)(u128)c.G, hi = (ull)((u128)c.G >> 64);
+  lo = __shfl_sync(0xffffffffu, lo, src);
+  hi = __shfl_sync(0xffffffffu, hi, src);
+  o.G = (i128)(((u128)hi << 64) | lo);
+  o.label = __shfl_sync(0xffffffffu, c.label, src);
+  return o;
+}
+
+__device__ __forceinline__ Cand shfl_xor_cand(const Cand& c, int m) {
+  Cand o;
+  ull lo = (ull)(u128)c.G, hi = (ull)((u128)c.G >> 64);
+  lo = __shfl_xor_sync(0xffffffffu, lo, m);
+  hi = __shfl_xor_sync(0xffffffffu, hi, m);
+  o.G = (i128)(((u128)hi << 64) | lo);
+  o.label = __shfl_xor_sync(0xffffffffu, c.label, m);
+  return o;
+}
+
+__device__ __forceinline__ Cand warp_best(Cand c) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    Cand o = shfl_xor_cand(c, m);
+    if (better(o, c)) c = o;
+  }
+  return c;
+}
+
+template <int WARPS>
+__device__ __forceinline__ Cand block_best(Cand c, Cand* sm) {
+  c = warp_best(c);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sm[w] = c;
+  __syncthreads();
+  if (w == 0) {
+    Cand x = lane < WARPS ? sm[lane] : Cand{0, INT32_MAX};
+    x = warp_best(x);
+    if (lane == 0) sm[0] = x;
+  }
+  __syncthreads();
+  Cand r = sm[0];
+  __syncthreads();
+  return r;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T x) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) x += __shfl_xor_sync(0xffffffffu, x, m);
+  return x;
+}
+
+}  // namespace mslice

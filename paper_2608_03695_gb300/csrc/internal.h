@@ -1,0 +1,95 @@
+// Host-side internals of the mslice library: error handling, device
+// workspace, launch bookkeeping and the kernel entry wrappers shared between
+// translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <utility>
+
+#include "common.cuh"
+
+namespace mslice {
+
+struct Error {
+  int code;
+  std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what);
+
+// Growable named device buffers owned by a handle.  Contents are undefined
+// after a grow; callers clear what they need.
+class Workspace {
+ public:
+  ~Workspace();
+  void* get_bytes(const std::string& name, size_t bytes);
+  template <class T>
+  T* get(const std::string& name, size_t count) {
+    return static_cast<T*>(get_bytes(name, (count ? count : 1) * sizeof(T)));
+  }
+  void release(const std::string& name);
+  void release_all();
+  size_t bytes_held() const;
+
+ private:
+  std::map<std::string, std::pair<void*, size_t>> bufs_;
+};
+
+struct Ctx {
+  cudaStream_t stream = nullptr;
+  Workspace* ws = nullptr;
+  unsigned* d_status = nullptr;  // device error bits
+  int64_t launches = 0;
+  void* pinned = nullptr;        // small pinned host buffer for readbacks (>= 4 KB)
+};
+
+template <class... KArgs, class... Args>
+inline void launch(Ctx& c, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, Args&&... args) {
+  if (grid.x == 0 || grid.y == 0 || grid.z == 0) return;
+  k<<<grid, block, smem, c.stream>>>(std::forward<Args>(args)...);
+  c.launches++;
+  check_cuda(cudaGetLastError(), "kernel launch");
+}
+
+inline unsigned grid_for(int64_t n, int per_block) {
+  int64_t g = (n + per_block - 1) / per_block;
+  return (unsigned)(g < 1 ? 0 : g);
+}
+
+// Reads `bytes` from device memory into the pinned buffer and synchronises.
+void* readback(Ctx& c, const void* dptr, size_t bytes);
+void sync(Ctx& c);
+// Synchronises and throws if the device status word holds an error bit.
+void check_status(Ctx& c, const char* where);
+
+// ---- primitives (primitives.cu) ----
+// out[i] = sum_{j<i} in[j] (int64 accumulation); *d_total (device, nullable)
+// receives the full sum.  in and out may alias.  With `cond` (device,
+// nullable) the kernels do nothing when *cond == 0, so a scan can sit in a
+// stream behind work whose outcome decides whether it is needed.
+void scan_excl(Ctx& c, const int32_t* in, int64_t* out, int64_t n, int64_t* d_total,
+               const int32_t* cond = nullptr);
+void scan_excl(Ctx& c, const int64_t* in, int64_t* out, int64_t n, int64_t* d_total,
+               const int32_t* cond = nullptr);
+void scan_excl(Ctx& c, const int32_t* in, int32_t* out, int64_t n, int32_t* d_total,
+               const int32_t* cond = nullptr);
+
+// Stable LSD radix sort of (key, value) pairs on the low `key_bits` bits.
+// Returns the buffer pair that holds the result (either the inputs or the
+// alternates).
+struct SortBufs {
+  uint64_t* keys;
+  long long* vals;
+};
+SortBufs radix_sort_pairs(Ctx& c, uint64_t* keys, long long* vals, uint64_t* keys_alt, long long* vals_alt,
+                          int64_t n, int key_bits);
+
+void fill_i32(Ctx& c, int32_t* p, int32_t v, int64_t n);
+void fill_i64(Ctx& c, int64_t* p, int64_t v, int64_t n);
+void iota_i32(Ctx& c, int32_t* p, int64_t n);
+
+}  // namespace mslice

@@ -1,0 +1,73 @@
+// A level of the optimisation as the kernels see it.  Level 0 is the
+// supra-graph itself ({col, w} entries, coupling flagged by w = 0, one
+// snapshot per node); aggregated levels hold int64 weights already scaled to
+// units of 1/omega_den and per-node lists of (snapshot, strength).
+#pragma once
+#include "internal.h"
+
+namespace mslice {
+
+struct LevelDev {
+  int32_t N = 0;
+  int32_t n = 1;  // level 0: nodes per snapshot
+  int32_t is0 = 1;
+  const int64_t* rowptr = nullptr;
+  const int2* adj0 = nullptr;   // level 0
+  const int64_t* k0 = nullptr;  // level 0
+  const int32_t* col = nullptr; // aggregated levels
+  const long long* W = nullptr;
+  const int64_t* sptr = nullptr;
+  const int32_t* sidx = nullptr;
+  const long long* sval = nullptr;
+  long long on = 1, od = 1;
+};
+
+// Entry e of the adjacency: neighbour u and weight W in units of 1/od.
+// A coupling entry has weight on and is absent when on = 0.
+__device__ __forceinline__ bool edge_at(const LevelDev& g, int64_t e, int32_t& u, long long& W) {
+  if (g.is0) {
+    const int2 x = g.adj0[e];
+    u = x.x;
+    if (x.y == 0) {
+      W = g.on;
+      return g.on > 0;
+    }
+    W = (long long)x.y * g.od;
+    return true;
+  }
+  u = g.col[e];
+  W = g.W[e];
+  return true;
+}
+
+// Snapshot-strength list of node v: entries [b, e).
+__device__ __forceinline__ void slice_range(const LevelDev& g, int32_t v, int64_t& b, int64_t& e) {
+  if (g.is0) {
+    b = 0;
+    e = g.k0[v] > 0 ? 1 : 0;
+  } else {
+    b = g.sptr[v];
+    e = g.sptr[v + 1];
+  }
+}
+
+__device__ __forceinline__ void slice_entry(const LevelDev& g, int32_t v, int64_t j, int32_t& s, long long& k) {
+  if (g.is0) {
+    s = v / g.n;
+    k = g.k0[v];
+  } else {
+    s = g.sidx[j];
+    k = g.sval[j];
+  }
+}
+
+// Host-side level: device arrays live in the solver's workspace.
+struct Level {
+  LevelDev d;
+  int64_t nnz = 0;       // stored entries
+  int64_t nnz_eff = 0;   // entries that are edges for this omega
+  int64_t ns = 0;        // snapshot-strength entries
+  int32_t max_deg = 0;
+};
+
+}  // namespace mslice

@@ -1,0 +1,184 @@
+// Multislice modularity (Eq. multislice-modularity, ordinal coupling) of a
+// level-0 labelling, from exact integer sums:
+//   2mu Q = I + omega*J - gamma * sum_s S_s / 2m_s
+//   I   = intra-snapshot weight over ordered pairs inside one community,
+//   J   = ordered coupling pairs inside one community,
+//   S_s = sum_c Sigma_{c,s}^2 (128-bit),
+//   2mu = sum_s 2m_s + 2*omega*n*(T-1).
+// The FP64 combination follows one fixed order (slice terms in ascending s,
+// then omega*J, the numerator, the division), with explicitly rounded
+// operations so no contraction changes the result.
+//
+// Also: canonical relabelling (first occurrence order), distinct counting
+// and the order-free level checksum used by the step-level tests.
+#include "solver.h"
+
+namespace mslice {
+
+namespace {
+
+__global__ void k_IJ(LevelDev g, const int32_t* labels, ull* IJ) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  ull I = 0, J = 0;
+  for (int64_t v = (((int64_t)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); v < g.N; v += warps) {
+    const int32_t c = labels[v];
+    for (int64_t e = g.rowptr[v] + lane; e < g.rowptr[v + 1]; e += 32) {
+      const int2 x = g.adj0[e];
+      if (labels[x.x] == c) {
+        if (x.y > 0)
+          I += (ull)x.y;
+        else
+          J += 1;
+      }
+    }
+  }
+  I = warp_sum(I);
+  J = warp_sum(J);
+  if (lane == 0) {
+    if (I) atomicAdd(&IJ[0], I);
+    if (J) atomicAdd(&IJ[1], J);
+  }
+}
+
+// S_s += Sigma_{c,s}^2 over the table; per-block partial sums in shared
+// memory when T is small enough, global 128-bit atomics otherwise.
+__global__ void k_S(HashView h, int32_t T, ull* S) {
+  extern __shared__ ull sm[];  // 2*T words when used
+  const bool use_sm = T <= 1024;
+  if (use_sm) {
+    for (int i = threadIdx.x; i < 2 * T; i += blockDim.x) sm[i] = 0;
+    __syncthreads();
+  }
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < h.cap; i += (uint64_t)gridDim.x * blockDim.x) {
+    const Slot sl = h.slots[i];
+    if (sl.key == EMPTY_KEY || sl.val == 0) continue;
+    const int32_t s = (int32_t)(sl.key & 0xffffffffu);
+    const u128 sq = (u128)(ull)sl.val * (u128)(ull)sl.val;
+    if (use_sm)
+      atomic_add_u128(&sm[2 * s], sq);
+    else
+      atomic_add_u128(&S[2 * s], sq);
+  }
+  if (use_sm) {
+    __syncthreads();
+    for (int s = threadIdx.x; s < T; s += blockDim.x) {
+      const u128 x = ((u128)sm[2 * s + 1] << 64) | sm[2 * s];
+      if (x) atomic_add_u128(&S[2 * s], x);
+    }
+  }
+}
+
+__global__ void k_Q(const ull* IJ, const ull* S, const int64_t* two_m, int32_t T, int64_t n, long long gn,
+                    long long gd, long long on, long long od, double* Q) {
+  double nullsum = 0.0;
+  long long sum2m = 0;
+  for (int s = 0; s < T; ++s) {
+    const long long t = two_m[s];
+    sum2m += t;
+    if (t > 0) {
+      const u128 x = ((u128)S[2 * s + 1] << 64) | S[2 * s];
+      nullsum = __dadd_rn(nullsum, __ddiv_rn(u128_to_double(x), __ll2double_rn(t)));
+    }
+  }
+  const double wJ = __ddiv_rn(__dmul_rn(__ll2double_rn(on), __ull2double_rn(IJ[1])), __ll2double_rn(od));
+  const double gam = __ddiv_rn(__ll2double_rn(gn), __ll2double_rn(gd));
+  const long long twomu_num = od * sum2m + 2 * on * n * (long long)(T - 1);
+  if (twomu_num == 0) {
+    *Q = 0.0;
+    return;
+  }
+  const double twomu = __ddiv_rn(__ll2double_rn(twomu_num), __ll2double_rn(od));
+  const double num = __dsub_rn(__dadd_rn(__ull2double_rn(IJ[0]), wJ), __dmul_rn(gam, nullsum));
+  *Q = __ddiv_rn(num, twomu);
+}
+
+__global__ void k_first(const int32_t* x, int64_t N, int32_t* first) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x)
+    atomicMin(&first[x[v]], (int32_t)v);
+}
+
+__global__ void k_first_flag(const int32_t* x, const int32_t* first, int64_t N, int32_t* flag) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x)
+    flag[v] = first[x[v]] == (int32_t)v ? 1 : 0;
+}
+
+__global__ void k_canon(const int32_t* x, const int32_t* first, const int32_t* rank, int64_t N, int32_t* out) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x)
+    out[v] = rank[first[x[v]]];
+}
+
+__global__ void k_mark(const int32_t* x, int64_t N, int32_t* flag) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x)
+    flag[x[v]] = 1;
+}
+
+__global__ void k_checksum(LevelDev g, ull* out) {
+  ull h = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t e = g.rowptr[v]; e < g.rowptr[v + 1]; ++e)
+      h += mix64(mix64(mix64((ull)g.W[e]) ^ (ull)g.col[e]) ^ (ull)v);
+    for (int64_t j = g.sptr[v]; j < g.sptr[v + 1]; ++j)
+      h += mix64(mix64(mix64((ull)g.sval[j]) ^ (ull)g.sidx[j]) ^ ((ull)v + 0x9E3779B97F4A7C15ULL));
+  }
+  h = warp_sum(h);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, h);
+}
+
+unsigned gsz(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+void modularity(Solver& S, const int32_t* labels0, double* Q) {
+  Ctx& c = *S.c;
+  const SupraGraph& G = *S.G0;
+  const LevelDev g = level0_view(G, S.p.on, S.p.od);
+  sigma_rebuild(S, Level{g}, labels0);
+  ull* acc = c.ws->get<ull>("q_acc", 2 + 2 * (size_t)G.T);
+  double* dQ = c.ws->get<double>("q_out", 1);
+  check_cuda(cudaMemsetAsync(acc, 0, (2 + 2 * (size_t)G.T) * sizeof(ull), c.stream), "memset");
+  if (G.N > 0) launch(c, k_IJ, dim3(gsz(G.N * 32)), dim3(256), 0, g, labels0, acc);
+  const size_t smem = G.T <= 1024 ? 2 * (size_t)G.T * sizeof(ull) : 0;
+  launch(c, k_S, dim3(gsz((int64_t)S.sig.cap)), dim3(256), smem, S.sig, G.T, acc + 2);
+  launch(c, k_Q, dim3(1), dim3(1), 0, (const ull*)acc, (const ull*)(acc + 2), (const int64_t*)G.two_m, G.T, G.n,
+         S.p.gn, S.p.gd, S.p.on, S.p.od, dQ);
+  *Q = *static_cast<const double*>(readback(c, dQ, sizeof(double)));
+}
+
+void canonicalise(Solver& S, const int32_t* x, int32_t* out, int64_t N) {
+  Ctx& c = *S.c;
+  if (N == 0) return;
+  int32_t* first = S.tmp32a;
+  int32_t* rank = S.tmp32b;
+  fill_i32(c, first, INT32_MAX, N);
+  launch(c, k_first, dim3(gsz(N)), dim3(256), 0, x, N, first);
+  int32_t* flag = S.freelist;
+  launch(c, k_first_flag, dim3(gsz(N)), dim3(256), 0, x, (const int32_t*)first, N, flag);
+  scan_excl(c, flag, rank, N, (int32_t*)nullptr);
+  launch(c, k_canon, dim3(gsz(N)), dim3(256), 0, x, (const int32_t*)first, (const int32_t*)rank, N, out);
+}
+
+int64_t count_distinct(Solver& S, const int32_t* x, int64_t N) {
+  Ctx& c = *S.c;
+  if (N == 0) return 0;
+  int32_t* flag = S.freelist;
+  check_cuda(cudaMemsetAsync(flag, 0, N * sizeof(int32_t), c.stream), "memset");
+  launch(c, k_mark, dim3(gsz(N)), dim3(256), 0, x, N, flag);
+  int32_t* d_tot = c.ws->get<int32_t>("cd_tot", 1);
+  scan_excl(c, flag, S.tmp32a, N, d_tot);
+  return *static_cast<const int32_t*>(readback(c, d_tot, sizeof(int32_t)));
+}
+
+uint64_t level_checksum(Solver& S, const Level& L) {
+  Ctx& c = *S.c;
+  ull* d = c.ws->get<ull>("ck_out", 1);
+  check_cuda(cudaMemsetAsync(d, 0, sizeof(ull), c.stream), "memset");
+  if (L.d.N > 0) launch(c, k_checksum, dim3(gsz(L.d.N)), dim3(256), 0, L.d, d);
+  return *static_cast<const ull*>(readback(c, d, sizeof(ull)));
+}
+
+}  // namespace mslice

@@ -1,0 +1,281 @@
+// Refinement (the Leiden refinement phase named in Sec. 3.2; Traag et al.
+// 2019) in its greedy form.  Inside every local-moving community C each node
+// starts as its own sub-community; one pass of K sub-rounds (class tag 1,
+// round 0).  A node still alone in its sub-community and well connected to C,
+//   2^64 W(v,C\v) >= od sum_s Lambda_s k_{v,s} (K_{C,s} - k_{v,s}),
+// joins the well-connected sub-community R of C (reached by one of its edges
+// inside C) with the largest positive key
+//   2^64 W(v,R) - od sum_s Lambda_s k_{v,s} K_{R,s}
+// (ties to the smallest label).  Well connected:
+//   2^64 W(R,C\R) >= od sum_s Lambda_s K_{R,s} (K_{C,s} - K_{R,s}).
+// A singleton sub-community whose node is active in the same sub-round is
+// not a target, so a joined node never leaves and every sub-community stays
+// connected.  A non-empty sub-community label L always contains node L, so a
+// singleton's label is its node.
+//
+// W(R,C\R) is maintained incrementally: when the set M of nodes joins R,
+//   W(R u M, C\(R u M)) = W(R,C\R) + sum_{v in M} [W(v,C\v) - 2 W(v,R)]
+//                         - sum_{v in M} W(v, M\v).
+#include "decide.cuh"
+#include "solver.h"
+
+namespace mslice {
+
+namespace {
+
+__device__ __forceinline__ u128 lam_k_x(const u128* lam, int32_t s, long long k, long long x) {
+  return lam[s] * (u128)(ull)k * (u128)(ull)x;
+}
+
+// Per node: W(v,C\v), eligibility, initial sub-community state.
+__global__ void k_ref_init(LevelDev g, const int32_t* P, HashView sig, const u128* lam, long long od, int32_t* R,
+                           int32_t* sizeR, long long* Wc, long long* Wout, uint8_t* elig, HashView kr) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = (((int64_t)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); v < g.N; v += warps) {
+    const int32_t C = P[v];
+    long long w = 0;
+    for (int64_t e = g.rowptr[v] + lane; e < g.rowptr[v + 1]; e += 32) {
+      int32_t u;
+      long long W;
+      if (edge_at(g, e, u, W) && P[u] == C) w += W;
+    }
+    w = warp_sum(w);
+    if (lane == 0) {
+      R[v] = (int32_t)v;
+      sizeR[v] = 1;
+      Wc[v] = w;
+      Wout[v] = w;
+      int64_t b, e;
+      slice_range(g, (int32_t)v, b, e);
+      u128 rhs = 0;
+      for (int64_t j = b; j < e; ++j) {
+        int32_t s;
+        long long k;
+        slice_entry(g, (int32_t)v, j, s, k);
+        rhs += lam_k_x(lam, s, k, hash_get(sig, pack_cs(C, s)) - k);
+        hash_add(kr, pack_cs((int32_t)v, s), k);
+      }
+      elig[v] = ((((i128)w) << P_BITS) - (i128)((u128)(ull)od * rhs)) >= 0 ? 1 : 0;
+    }
+  }
+}
+
+__global__ void k_hash_clear2(Slot* slots, uint64_t cap) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += (uint64_t)gridDim.x * blockDim.x)
+    slots[i] = Slot{EMPTY_KEY, 0};
+}
+
+__global__ void k_zero_rhs(ull* rhs, int64_t n2) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x)
+    rhs[i] = 0;
+}
+
+// sum_s Lambda_s K_{R,s} (K_{C,s} - K_{R,s}) for every sub-community with
+// more than one node (singletons reuse their eligibility).
+__global__ void k_rhs_accum(HashView kr, const int32_t* sizeR, const int32_t* P, HashView sig, const u128* lam,
+                            ull* rhs) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < kr.cap; i += (uint64_t)gridDim.x * blockDim.x) {
+    const Slot sl = kr.slots[i];
+    if (sl.key == EMPTY_KEY || sl.val == 0) continue;
+    const int32_t Rl = (int32_t)(sl.key >> 32);
+    const int32_t s = (int32_t)(sl.key & 0xffffffffu);
+    if (sizeR[Rl] <= 1) continue;
+    const long long KC = hash_get(sig, pack_cs(P[Rl], s));
+    atomic_add_u128(&rhs[2 * (int64_t)Rl], lam_k_x(lam, s, sl.val, KC - sl.val));
+  }
+}
+
+__global__ void k_wc(int32_t N, const int32_t* sizeR, const long long* Wout, const ull* rhs, const uint8_t* elig,
+                     long long od, uint8_t* wc) {
+  for (int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; L < N; L += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t sz = sizeR[L];
+    uint8_t f = 0;
+    if (sz == 1) {
+      f = elig[L];
+    } else if (sz > 1) {
+      const u128 x = ((u128)rhs[2 * L + 1] << 64) | rhs[2 * L];
+      f = ((((i128)Wout[L]) << P_BITS) - (i128)((u128)(ull)od * x)) >= 0 ? 1 : 0;
+    }
+    wc[L] = f;
+  }
+}
+
+struct RefPolicy {
+  LevelDev g;
+  const int32_t* P;
+  const int32_t* R;
+  const int32_t* sizeR;
+  const uint8_t* elig;
+  const uint8_t* wc;
+  HashView kr;
+  const u128* lam;
+  int32_t* target;
+  long long* Wsel;
+  long long od;
+  uint64_t seed, it, lvl;
+  int K, q;
+
+  __device__ bool begin(int32_t v) const { return sizeR[R[v]] == 1 && elig[v]; }
+  __device__ void skip(int32_t v) const { target[v] = NO_MOVE; }
+  __device__ bool edge(int32_t v, int64_t e, int32_t& key, long long& w) const {
+    int32_t u;
+    if (!edge_at(g, e, u, w)) return false;
+    if (P[u] != P[v]) return false;
+    key = R[u];
+    return true;
+  }
+  __device__ int32_t own_key(int32_t) const { return -1; }
+  __device__ Cand cand(int32_t v, int32_t X, long long W) const {
+    if (X == R[v]) return Cand{0, INT32_MAX};
+    if (sizeR[X] == 1 && vertex_class(seed, 1, it, lvl, 0, (uint64_t)X, K) == q) return Cand{0, INT32_MAX};
+    if (!wc[X]) return Cand{0, INT32_MAX};
+    int64_t b, e;
+    slice_range(g, v, b, e);
+    u128 ns = 0;
+    for (int64_t j = b; j < e; ++j) {
+      int32_t s;
+      long long k;
+      slice_entry(g, v, j, s, k);
+      ns += lam_k_x(lam, s, k, hash_get(kr, pack_cs(X, s)));
+    }
+    const i128 G = (((i128)W) << P_BITS) - (i128)((u128)(ull)od * ns);
+    if (G <= 0) return Cand{0, INT32_MAX};
+    return Cand{G, X};
+  }
+  __device__ void finish(int32_t v, const Cand& best, long long Wb, long long) const {
+    if (best.label != INT32_MAX) {
+      target[v] = best.label;
+      Wsel[v] = Wb;
+    } else {
+      target[v] = NO_MOVE;
+    }
+  }
+};
+
+struct Segs3 {
+  const int32_t* list[3];
+  const int32_t* count[3];
+};
+
+__device__ __forceinline__ int seg3_total(const Segs3& sg) { return *sg.count[0] + *sg.count[1] + *sg.count[2]; }
+__device__ __forceinline__ bool seg3_item(const Segs3& sg, int64_t idx, int32_t& v) {
+  for (int t = 0; t < 3; ++t) {
+    const int cnt = *sg.count[t];
+    if (idx < cnt) {
+      v = sg.list[t][idx];
+      return true;
+    }
+    idx -= cnt;
+  }
+  return false;
+}
+
+// One warp per active node: movers compute W(v, M_t \ v) over their edges to
+// other movers with the same target, then update sizes, K_{R,s} and W(R,C\R).
+__global__ void k_ref_apply(LevelDev g, Segs3 sg, const int32_t* P, const int32_t* target, const long long* Wc,
+                            const long long* Wsel, int32_t* R, int32_t* sizeR, long long* Wout, HashView kr) {
+  const int lane = threadIdx.x & 31;
+  const int total = seg3_total(sg);
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t idx = (((int64_t)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); idx < total; idx += warps) {
+    int32_t v;
+    if (!seg3_item(sg, idx, v)) break;
+    const int32_t t = target[v];
+    if (t < 0) continue;
+    long long wp = 0;
+    for (int64_t e = g.rowptr[v] + lane; e < g.rowptr[v + 1]; e += 32) {
+      int32_t u;
+      long long W;
+      if (edge_at(g, e, u, W) && target[u] == t && P[u] == P[v]) wp += W;
+    }
+    wp = warp_sum(wp);
+    if (lane == 0) {
+      R[v] = t;
+      atomicSub(&sizeR[v], 1);
+      atomicAdd(&sizeR[t], 1);
+      atomicAdd((ull*)&Wout[t], (ull)(Wc[v] - 2 * Wsel[v] - wp));
+      Wout[v] = 0;
+      int64_t b, e;
+      slice_range(g, v, b, e);
+      for (int64_t j = b; j < e; ++j) {
+        int32_t s;
+        long long k;
+        slice_entry(g, v, j, s, k);
+        hash_add(kr, pack_cs(v, s), -k);
+        hash_add(kr, pack_cs(t, s), k);
+      }
+    }
+  }
+}
+
+__global__ void k_ref_reset(Segs3 sg, int32_t* target) {
+  const int total = seg3_total(sg);
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v;
+    if (seg3_item(sg, idx, v)) target[v] = NO_MOVE;
+  }
+}
+
+unsigned fixed_grid(int per_sm) { return 152u * (unsigned)per_sm; }
+
+}  // namespace
+
+void bucket(Solver& S, const Level& L, uint64_t tag, int it, int lvl, int r);
+
+void refine(Solver& S, const Level& L, const int32_t* P, int it, int lvl) {
+  Ctx& c = *S.c;
+  const int32_t N = L.d.N;
+  if (N == 0) return;
+  launch(c, k_hash_clear2, dim3(fixed_grid(8)), dim3(256), 0, S.kr.slots, S.kr.cap);
+  launch(c, k_ref_init, dim3(fixed_grid(8)), dim3(256), 0, L.d, P, S.sig, (const u128*)S.lam, S.p.od, S.R, S.sizeR,
+         S.Wc, S.Wout, S.elig, S.kr);
+  bucket(S, L, 1, it, lvl, 0);
+  RefPolicy pol;
+  pol.g = L.d;
+  pol.P = P;
+  pol.R = S.R;
+  pol.sizeR = S.sizeR;
+  pol.elig = S.elig;
+  pol.wc = S.wc;
+  pol.kr = S.kr;
+  pol.lam = S.lam;
+  pol.target = S.target;
+  pol.Wsel = S.Wsel;
+  pol.od = S.p.od;
+  pol.seed = S.p.seed;
+  pol.it = (uint64_t)it;
+  pol.lvl = (uint64_t)lvl;
+  pol.K = S.p.K;
+  for (int q = 0; q < S.p.K; ++q) {
+    // well-connectedness of every sub-community at the sub-round start
+    if (q > 0) {
+      launch(c, k_zero_rhs, dim3(fixed_grid(8)), dim3(256), 0, S.rhs, 2 * (int64_t)N);
+      launch(c, k_rhs_accum, dim3(fixed_grid(8)), dim3(256), 0, S.kr, (const int32_t*)S.sizeR, P, S.sig,
+             (const u128*)S.lam, S.rhs);
+    }
+    launch(c, k_wc, dim3(fixed_grid(8)), dim3(256), 0, N, (const int32_t*)S.sizeR, (const long long*)S.Wout,
+           (const ull*)S.rhs, (const uint8_t*)S.elig, S.p.od, S.wc);
+    pol.q = q;
+    Segs3 sg;
+    for (int t = 0; t < 3; ++t) {
+      sg.list[t] = S.lists + (int64_t)q * S.N0 + S.tier_off[t];
+      sg.count[t] = S.cursors + 3 * q + t;
+    }
+    if (S.tier_cnt[0] > 0)
+      launch(c, k_decide_warp<RefPolicy>, dim3(fixed_grid(8)), dim3(DECIDE_WARP_THREADS), 0, pol, sg.list[0],
+             sg.count[0]);
+    if (S.tier_cnt[1] > 0)
+      launch(c, k_decide_block<RefPolicy>, dim3(fixed_grid(8)), dim3(BLOCK_TIER_THREADS), 0, pol, sg.list[1],
+             sg.count[1]);
+    if (S.tier_cnt[2] > 0)
+      launch(c, k_decide_global<RefPolicy>, dim3(fixed_grid(4)), dim3(GLOBAL_TIER_THREADS), 0, pol, sg.list[2],
+             sg.count[2], S.gkeys, S.gvals, (const int64_t*)S.goff, c.d_status);
+    launch(c, k_ref_apply, dim3(fixed_grid(8)), dim3(256), 0, L.d, sg, P, (const int32_t*)S.target,
+           (const long long*)S.Wc, (const long long*)S.Wsel, S.R, S.sizeR, S.Wout, S.kr);
+    launch(c, k_ref_reset, dim3(fixed_grid(4)), dim3(256), 0, sg, S.target);
+  }
+}
+
+}  // namespace mslice

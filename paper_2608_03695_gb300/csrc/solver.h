@@ -1,0 +1,93 @@
+// Per-call solver state and the phases of one Leiden solve.
+#pragma once
+#include "build.h"
+#include "level.h"
+
+namespace mslice {
+
+struct SolveParams {
+  long long gn = 1, gd = 1, on = 1, od = 1;
+  int32_t K = 4, max_rounds = 100, max_levels = 32, n_iterations = 2;
+  uint64_t seed = 0;
+};
+
+struct PhaseTimer;
+
+struct Solver {
+  Ctx* c = nullptr;
+  const SupraGraph* G0 = nullptr;
+  SolveParams p;
+  u128* lam = nullptr;  // Lambda_s, T entries
+  int64_t N0 = 0;
+
+  // node-indexed scratch, sized for level 0 (every level is smaller)
+  int32_t* target = nullptr;
+  int32_t* size = nullptr;
+  int32_t* tmp32a = nullptr;
+  int32_t* tmp32b = nullptr;
+  int32_t* freelist = nullptr;
+  uint8_t* tier = nullptr;
+  int32_t* lists = nullptr;     // K rows of N0 entries: nodes bucketed by class and tier
+  int32_t* cursors = nullptr;   // 3K bucket fill counts (device)
+  int32_t* counters = nullptr;  // [0] moves in round (low), [1] moves (high), [2] moves to empty in sub-round
+  int64_t* goff = nullptr;      // global-tier table offsets
+  int32_t* gkeys = nullptr;
+  long long* gvals = nullptr;
+  int64_t gcap = 0;
+
+  // community slice sums Sigma_{c,s}
+  HashView sig{};
+  // refinement state
+  int32_t* R = nullptr;
+  int32_t* sizeR = nullptr;
+  long long* Wc = nullptr;
+  long long* Wout = nullptr;
+  long long* Wsel = nullptr;
+  ull* rhs = nullptr;  // 2 words per node
+  uint8_t* elig = nullptr;
+  uint8_t* wc = nullptr;
+  HashView kr{};
+
+  int32_t tier_off[3] = {0, 0, 0};
+  int32_t tier_cnt[3] = {0, 0, 0};
+
+  // statistics
+  int64_t lm_rounds = 0, lm_edges = 0, lm_moves = 0;
+};
+
+void solver_alloc(Solver& S);
+
+// Degree tiers, global-tier scratch; once per level.
+void prepare_level(Solver& S, const Level& L);
+
+struct MoveOut {
+  int64_t rounds = 0, moves = 0;
+};
+// Local moving of `labels` (N entries, values in [0, N)) at level lvl.
+MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, int max_rounds);
+
+// Refinement of the local-moving partition P; result in S.R.
+void refine(Solver& S, const Level& L, const int32_t* P, int it, int lvl);
+
+// Number of distinct values in x[0, N) (values in [0, N)).
+int64_t count_distinct(Solver& S, const int32_t* x, int64_t N);
+
+// Aggregation; returns false when the refined partition has N communities.
+bool aggregate(Solver& S, const Level& L, const int32_t* P, Level& next, const std::string& slot,
+               int32_t* next_labels, int32_t* node_of0, int64_t* checksum);
+
+// Rebuilds Sigma_{c,s} of `labels` at level L.
+void sigma_rebuild(Solver& S, const Level& L, const int32_t* labels);
+
+// Canonical labels (first occurrence order) of x[0, N) into out.
+void canonicalise(Solver& S, const int32_t* x, int32_t* out, int64_t N);
+
+// Q_MS of level-0 labels with the true gamma; result in *Q (host).
+void modularity(Solver& S, const int32_t* labels0, double* Q);
+
+// Order-free checksum of a level (debug stage 3).
+uint64_t level_checksum(Solver& S, const Level& L);
+
+LevelDev level0_view(const SupraGraph& G, long long on, long long od);
+
+}  // namespace mslice

@@ -1,0 +1,61 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry
+point the header declares; host-side marshalling checks."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import paper_2608_03695_gb300 as pkg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(mslice_[a-z_]+)\s*\(", text, re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pkg.build()
+    return C.CDLL(pkg.LIB_PATH)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(pkg.EXPORTS) == names
+
+
+def test_default_opts_and_error_string(lib):
+    o = pkg.default_opts()
+    assert (o.n_iterations, o.K, o.max_rounds, o.max_levels, o.stop_level) == (2, 4, 100, 32, -1)
+    assert (o.gamma_num, o.gamma_den, o.omega_num, o.omega_den) == (1, 1, 1, 1)
+    L = pkg.lib()
+    assert L.mslice_last_error() == b""
+
+
+def test_host_side_rejections_need_no_gpu():
+    L = pkg.lib()
+    h = C.c_void_p()
+    # T < 1 and a null handle are rejected before any CUDA call
+    assert L.mslice_build(None, 0, 0, 1, 1, C.byref(h)) == pkg.MSLICE_EINVAL
+    assert L.mslice_info(None, None, None, None, None) == pkg.MSLICE_EINVAL
+    assert L.mslice_leiden_ex(None, None, None, None, None, None) == pkg.MSLICE_EINVAL
+    assert b"handle" in L.mslice_last_error()
+    L.mslice_free(None)
+
+
+def test_struct_layouts_match_header():
+    # field order and sizes of the ctypes mirrors follow include/mslice.h
+    assert C.sizeof(pkg.Csr) == 32
+    assert C.sizeof(pkg.Opts) == 4 * 4 + 8 + 4 * 8 + 4 * 4
+    assert C.sizeof(pkg.Stats) == 4 + 4 + 8 * 7 + 8 + 4 + 4 + 8 + 8 * 5
