@@ -51,6 +51,10 @@ extern "C" {
 /* Input/output pointers are device pointers (build: the snapshot arrays;
  * leiden/modularity: labels). */
 #define MSLICE_DEVICE_PTRS 1
+/* leiden: time every local-moving decision kernel with CUDA events on the
+ * handle's stream (fills ms_decide / decide_launches / decide_bytes; adds a
+ * little host overhead per launch). */
+#define MSLICE_PROFILE 2
 
 typedef struct {
   int64_t n;              /* nodes of the snapshot (equal for all snapshots) */
@@ -104,6 +108,13 @@ typedef struct {
   double ms_refine;          /* ... refinement */
   double ms_aggregate;       /* ... aggregation */
   double ms_modularity;      /* ... Q evaluation */
+  double ms_decide;          /* MSLICE_PROFILE: summed durations of the local-moving decision kernels */
+  int64_t decide_launches;   /* MSLICE_PROFILE: number of those launches */
+  int64_t decide_bytes;      /* MSLICE_PROFILE: algorithmic bytes those launches move, per round
+                                12 B per directed entry (column, weight, neighbour label) and 40 B
+                                per node (row pointer, own label, strength, decision, the own
+                                community's 16-byte table slot); probes of other candidate
+                                communities are not counted, so this is a lower bound */
 } mslice_stats;
 
 /* Defaults above; stop_level = -1. */
@@ -151,6 +162,10 @@ int mslice_modularity_ex(mslice_handle h, const int32_t* labels, int64_t gamma_n
 /* Sizes of a built handle: N supra-nodes, T, n, stored level-0 entries
  * (intra + coupling, both directions). Any pointer may be NULL. */
 int mslice_info(mslice_handle h, int64_t* N, int32_t* T, int64_t* n, int64_t* nnz);
+
+/* Kernels launched on this handle since it was built (build included);
+ * -1 for a NULL handle. */
+int64_t mslice_kernel_launches(mslice_handle h);
 
 /* Releases the handle and its device memory (NULL is ignored). */
 void mslice_free(mslice_handle h);

@@ -24,11 +24,13 @@ LIB_PATH = os.path.join(HERE, "libmslice.so")
 
 MSLICE_OK, MSLICE_EINVAL, MSLICE_ENOMEM, MSLICE_EOVERFLOW, MSLICE_ECUDA, MSLICE_ETIMEOUT = 0, -1, -2, -3, -4, -5
 MSLICE_DEVICE_PTRS = 1
+MSLICE_PROFILE = 2
 MSLICE_ORDINAL = 0
 
 # every symbol include/mslice.h declares
 EXPORTS = ["mslice_default_opts", "mslice_build", "mslice_build_ex", "mslice_leiden", "mslice_leiden_ex",
-           "mslice_modularity", "mslice_modularity_ex", "mslice_info", "mslice_free", "mslice_last_error"]
+           "mslice_modularity", "mslice_modularity_ex", "mslice_info", "mslice_kernel_launches", "mslice_free",
+           "mslice_last_error"]
 
 
 class LibraryMissing(RuntimeError):
@@ -59,7 +61,8 @@ class Stats(C.Structure):
                 ("out_n", C.c_int64), ("next_n", C.c_int64), ("next_nnz", C.c_int64),
                 ("next_checksum", C.c_uint64), ("stop_reason", C.c_int32), ("pad_", C.c_int32),
                 ("kernel_launches", C.c_int64), ("ms_total", C.c_double), ("ms_local_move", C.c_double),
-                ("ms_refine", C.c_double), ("ms_aggregate", C.c_double), ("ms_modularity", C.c_double)]
+                ("ms_refine", C.c_double), ("ms_aggregate", C.c_double), ("ms_modularity", C.c_double),
+                ("ms_decide", C.c_double), ("decide_launches", C.c_int64), ("decide_bytes", C.c_int64)]
 
 
 _lib = None
@@ -86,6 +89,8 @@ def lib():
         L.mslice_modularity.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, P]
         L.mslice_modularity_ex.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int32, P]
         L.mslice_info.argtypes = [P, P, P, P, P]
+        L.mslice_kernel_launches.argtypes = [P]
+        L.mslice_kernel_launches.restype = C.c_int64
         L.mslice_free.argtypes = [P]
         L.mslice_free.restype = None
         L.mslice_last_error.restype = C.c_char_p
@@ -139,8 +144,13 @@ class Handle:
     def __exit__(self, *a):
         self.close()
 
+    @property
+    def kernel_launches(self) -> int:
+        return int(lib().mslice_kernel_launches(self._h))
+
     def mslice_leiden(self, gamma=(1, 1), omega=(1, 1), max_levels=32, seed=0, n_iterations=2, K=4,
-                      max_rounds=100, init=None, stop_level=-1, stop_stage=0, stop_rounds=0, out=None):
+                      max_rounds=100, init=None, stop_level=-1, stop_stage=0, stop_rounds=0, out=None,
+                      profile=False):
         """Returns (labels, Q, stats).  With ``out`` a device tensor (int32[N])
         the labels stay on the device (MSLICE_DEVICE_PTRS); ``init`` may then
         be a device tensor as well."""
@@ -150,11 +160,11 @@ class Handle:
         o.max_levels, o.seed, o.n_iterations, o.K, o.max_rounds = max_levels, seed, n_iterations, K, max_rounds
         o.stop_level, o.stop_stage, o.stop_rounds = stop_level, stop_stage, stop_rounds
         dev = out is not None and hasattr(out, "is_cuda") and out.is_cuda
+        if profile:
+            o.flags |= MSLICE_PROFILE
         if dev:
-            o.flags = MSLICE_DEVICE_PTRS
-            labels = out
-        else:
-            labels = np.zeros(max(self.N, 1), dtype=np.int32)
+            o.flags |= MSLICE_DEVICE_PTRS
+        labels = out if out is not None else np.zeros(max(self.N, 1), dtype=np.int32)
         init_a = init
         if init is not None and not hasattr(init, "data_ptr"):
             init_a = np.ascontiguousarray(init, dtype=np.int32)
@@ -163,7 +173,7 @@ class Handle:
         _check(lib().mslice_leiden_ex(self._h, C.byref(o), _ptr(init_a), _ptr(labels), C.byref(Q), C.byref(st)),
                "mslice_leiden_ex")
         stats = {f: getattr(st, f) for f, _ in Stats._fields_}
-        if dev:
+        if out is not None:
             return labels, Q.value, stats
         return labels[: st.out_n].copy(), Q.value, stats
 
@@ -180,15 +190,16 @@ class Handle:
     modularity = mslice_modularity
 
 
-def mslice_build(snaps, omega=(1, 1), stream=None, device_ptrs=False) -> Handle:
+def mslice_build(snaps, omega=(1, 1), stream=None, device_ptrs=False, host_tensors=False) -> Handle:
     """Builds a handle from T snapshots.  ``snaps`` holds objects with
-    ``indptr``/``indices``/``weights`` arrays (numpy host arrays, or torch
-    device tensors with ``device_ptrs=True``)."""
+    ``indptr``/``indices``/``weights`` arrays: numpy host arrays, torch host
+    tensors (``host_tensors=True``, e.g. pinned memory) or torch device
+    tensors (``device_ptrs=True``)."""
     T = len(snaps)
     arr = (Csr * max(T, 1))()
     keep = []
     for s, sn in enumerate(snaps):
-        if device_ptrs:
+        if device_ptrs or host_tensors:
             ip, ix, w = sn.indptr, sn.indices, sn.weights
             n = ip.numel() - 1
         else:

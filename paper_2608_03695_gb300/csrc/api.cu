@@ -39,11 +39,11 @@ void* Workspace::get_bytes(const std::string& name, size_t bytes) {
   auto it = bufs_.find(name);
   if (it != bufs_.end()) {
     if (it->second.second >= bytes) return it->second.first;
-    cudaFree(it->second.first);
+    cudaFreeAsync(it->second.first, stream);
     bufs_.erase(it);
   }
   void* p = nullptr;
-  cudaError_t e = cudaMalloc(&p, bytes);
+  cudaError_t e = cudaMallocAsync(&p, bytes, stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     fail(MSLICE_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes for " + name + " failed");
@@ -55,12 +55,13 @@ void* Workspace::get_bytes(const std::string& name, size_t bytes) {
 void Workspace::release(const std::string& name) {
   auto it = bufs_.find(name);
   if (it == bufs_.end()) return;
-  cudaFree(it->second.first);
+  cudaFreeAsync(it->second.first, stream);
   bufs_.erase(it);
 }
 
 void Workspace::release_all() {
-  for (auto& kv : bufs_) cudaFree(kv.second.first);
+  for (auto& kv : bufs_) cudaFreeAsync(kv.second.first, stream);
+  if (!bufs_.empty()) cudaStreamSynchronize(stream);
   bufs_.clear();
 }
 
@@ -156,6 +157,7 @@ struct mslice_graph {
   unsigned* d_status = nullptr;
   void* pinned = nullptr;
   long long on = 1, od = 1;
+  int64_t launches = 0;
   Ctx ctx() {
     Ctx c;
     c.stream = stream;
@@ -165,6 +167,8 @@ struct mslice_graph {
     return c;
   }
   ~mslice_graph() {
+    ws.release_all();
+    G.mem.release_all();
     if (pinned) cudaFreeHost(pinned);
   }
 };
@@ -183,6 +187,21 @@ int guard(const std::function<void()>& f) {
     g_last_error = "host allocation failed";
     return MSLICE_ENOMEM;
   }
+}
+
+// Freed stream-ordered allocations stay in the device's default pool, so
+// handles created and released in a loop do not pay for fresh allocations.
+void keep_pool_memory() {
+  static bool done = false;
+  if (done) return;
+  int dev = 0;
+  cudaMemPool_t pool;
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  done = true;
 }
 
 bool rational_ok(int64_t num, int64_t den, bool allow_zero) {
@@ -247,6 +266,9 @@ int mslice_build_ex(const mslice_csr* slices, int32_t T, mslice_coupling cpl, in
       if (slices[s].n != n) fail(MSLICE_EINVAL, "snapshots must have the same n");
     h = new mslice_graph();
     h->stream = static_cast<cudaStream_t>(stream);
+    h->ws.stream = h->stream;
+    h->G.mem.stream = h->stream;
+    keep_pool_memory();
     h->on = omega_num;
     h->od = omega_den;
     check_cuda(cudaMallocHost(&h->pinned, 4096), "pinned buffer");
@@ -296,6 +318,7 @@ int mslice_build_ex(const mslice_csr* slices, int32_t T, mslice_coupling cpl, in
       }
     }
     build_supra(c, ip, ix, wt, nnz, n, h->G);
+    h->launches += c.launches;
     // staged host copies are not needed after the build
     if (!dev)
       for (int32_t s = 0; s < T; ++s) {
@@ -329,6 +352,8 @@ int mslice_info(mslice_handle h, int64_t* N, int32_t* T, int64_t* n, int64_t* nn
 
 void mslice_free(mslice_handle h) { delete h; }
 
+int64_t mslice_kernel_launches(mslice_handle h) { return h ? h->launches : -1; }
+
 int mslice_leiden_ex(mslice_handle h, const mslice_opts* o, const int32_t* init_labels, int32_t* labels_out,
                      double* Q_out, mslice_stats* st) {
   return guard([&] {
@@ -345,6 +370,9 @@ int mslice_leiden_ex(mslice_handle h, const mslice_opts* o, const int32_t* init_
     const SupraGraph& G = h->G;
     check_bounds(G, opt.gamma_num, opt.gamma_den, opt.omega_num, opt.omega_den);
     Ctx c = h->ctx();
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_spans;
+    c.profile = (opt.flags & MSLICE_PROFILE) != 0;
+    c.prof_spans = &prof_spans;
     PhaseClock clock(c);
     cudaEvent_t t_all = clock.begin();
 
@@ -506,6 +534,20 @@ int mslice_leiden_ex(mslice_handle h, const mslice_opts* o, const int32_t* init_
     stats.lm_edges = S.lm_edges;
     stats.lm_moves = S.lm_moves;
     stats.kernel_launches = c.launches;
+    h->launches += c.launches;
+    if (c.profile) {
+      double dms = 0;
+      for (auto& sp : prof_spans) {
+        float ms = 0;
+        check_cuda(cudaEventElapsedTime(&ms, sp.first, sp.second), "event time");
+        dms += ms;
+        cudaEventDestroy(sp.first);
+        cudaEventDestroy(sp.second);
+      }
+      stats.ms_decide = dms;
+      stats.decide_launches = (int64_t)prof_spans.size();
+      stats.decide_bytes = c.prof_bytes;
+    }
     if (st) *st = stats;
   });
 }
@@ -554,6 +596,7 @@ int mslice_modularity_ex(mslice_handle h, const int32_t* labels, int64_t gamma_n
     double Q = 0.0;
     modularity(S, lab, &Q);
     check_status(c, "modularity");
+    h->launches += c.launches;
     if (Q_out) *Q_out = Q;
   });
 }

@@ -8,6 +8,7 @@
 #include <map>
 #include <string>
 #include <utility>
+#include <vector>
 
 #include "common.cuh"
 
@@ -25,6 +26,7 @@ void check_cuda(cudaError_t e, const char* what);
 // after a grow; callers clear what they need.
 class Workspace {
  public:
+  cudaStream_t stream = nullptr;  // allocations are ordered on this stream
   ~Workspace();
   void* get_bytes(const std::string& name, size_t bytes);
   template <class T>
@@ -44,6 +46,9 @@ struct Ctx {
   Workspace* ws = nullptr;
   unsigned* d_status = nullptr;  // device error bits
   int64_t launches = 0;
+  bool profile = false;          // event-time the decision kernels
+  int64_t prof_bytes = 0;        // algorithmic bytes of the timed kernels
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* prof_spans = nullptr;
   void* pinned = nullptr;        // small pinned host buffer for readbacks (>= 4 KB)
 };
 

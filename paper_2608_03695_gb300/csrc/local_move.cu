@@ -375,7 +375,21 @@ MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, 
   Ctx& c = *S.c;
   MoveOut out;
   const int32_t N = L.d.N;
-  if (N == 0 || max_rounds <= 0) return out;
+  if (N == 0) {
+    // an empty level runs one round that moves nothing
+    if (max_rounds > 0) {
+      out.rounds = 1;
+      S.lm_rounds++;
+    }
+    return out;
+  }
+  if (max_rounds <= 0) {
+    // no round: refinement still reads Sigma of the given labels
+    check_cuda(cudaMemsetAsync(S.size, 0, N * sizeof(int32_t), c.stream), "memset");
+    launch(c, k_hash_clear, dim3(fixed_grid(8)), dim3(256), 0, S.sig.slots, S.sig.cap);
+    launch(c, k_sigma_insert, dim3(grid_for(N, 256)), dim3(256), 0, L.d, (const int32_t*)labels, S.sig, S.size);
+    return out;
+  }
   LMPolicy pol;
   pol.g = L.d;
   pol.labels = labels;
@@ -393,9 +407,20 @@ MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, 
     bucket(S, L, 0, it, lvl, r);
     S.lm_rounds++;
     S.lm_edges += L.nnz_eff;
+    if (c.profile) c.prof_bytes += 12 * L.nnz_eff + 40 * (int64_t)N;
     for (int q = 0; q < S.p.K; ++q) {
       const Segs sg = bucket_segments(S, q);
-      decide_all(S, pol, sg);
+      if (c.profile) {
+        cudaEvent_t e0, e1;
+        check_cuda(cudaEventCreate(&e0), "event");
+        check_cuda(cudaEventCreate(&e1), "event");
+        check_cuda(cudaEventRecord(e0, c.stream), "event");
+        decide_all(S, pol, sg);
+        check_cuda(cudaEventRecord(e1, c.stream), "event");
+        c.prof_spans->push_back({e0, e1});
+      } else {
+        decide_all(S, pol, sg);
+      }
       launch(c, k_lm_apply, dim3(fixed_grid(4)), dim3(APPLY_THREADS), 0, L.d, sg, labels, S.size, S.sig, S.target,
              S.counters);
       // moves to empty communities (kernels return at once when there are none)

@@ -58,4 +58,4 @@ def test_struct_layouts_match_header():
     # field order and sizes of the ctypes mirrors follow include/mslice.h
     assert C.sizeof(pkg.Csr) == 32
     assert C.sizeof(pkg.Opts) == 4 * 4 + 8 + 4 * 8 + 4 * 4
-    assert C.sizeof(pkg.Stats) == 4 + 4 + 8 * 7 + 8 + 4 + 4 + 8 + 8 * 5
+    assert C.sizeof(pkg.Stats) == 4 + 4 + 8 * 7 + 8 + 4 + 4 + 8 + 8 * 5 + 8 * 3
