@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", default="mslice", choices=["mslice", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="one solve of the workload and exit (a short target for ncu captures)")
     return ap.parse_args()
 
 
@@ -200,6 +202,12 @@ def main():
 
     snaps = synth.config_graph(2)
     stream = torch.cuda.Stream()
+    if args.profile_run:
+        with pkg.mslice_build(snaps) as h:
+            _, Q, st = h.mslice_leiden()
+        print(json.dumps({"profile_run": True, "Q": Q, "kernel_launches": st["kernel_launches"],
+                          "ms_total": st["ms_total"]}), flush=True)
+        return
 
     class DevSnap:
         def __init__(self, s, pin=False, device=None):

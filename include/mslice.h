@@ -72,7 +72,7 @@ typedef struct mslice_graph* mslice_handle;
 typedef struct {
   int32_t n_iterations; /* outer Leiden passes; default 2 (the paper caps runs
                            at two optimisation passes, Sec. 4) */
-  int32_t K;            /* synchronous sub-rounds per local-moving round; default 4 */
+  int32_t K;            /* synchronous sub-rounds per local-moving round, 1..64; default 4 */
   int32_t max_rounds;   /* local-moving rounds per level; default 100 */
   int32_t max_levels;   /* aggregation levels; default 32 */
   uint64_t seed;        /* seed of the counter-based class hash; default 0 */

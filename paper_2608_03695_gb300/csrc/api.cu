@@ -11,7 +11,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <functional>
 #include <new>
 #include <string>
@@ -72,6 +75,48 @@ size_t Workspace::bytes_held() const {
 }
 
 void sync(Ctx& c) { check_cuda(cudaStreamSynchronize(c.stream), "stream synchronize"); }
+
+void trace_begin(Ctx& c, const void*, cudaEvent_t* e0) {
+  check_cuda(cudaEventCreate(e0), "event");
+  check_cuda(cudaEventRecord(*e0, c.stream), "event");
+}
+
+void trace_end(Ctx& c, const void* k, cudaEvent_t e0) {
+  cudaEvent_t e1;
+  check_cuda(cudaEventCreate(&e1), "event");
+  check_cuda(cudaEventRecord(e1, c.stream), "event");
+  c.trace->push_back({k, {e0, e1}});
+}
+
+// Per-kernel totals of a traced call, printed to stderr.
+static void trace_report(Ctx& c) {
+  sync(c);
+  std::map<std::string, std::pair<int64_t, double>> agg;
+  double tot = 0;
+  for (auto& t : *c.trace) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, t.second.first, t.second.second);
+    cudaEventDestroy(t.second.first);
+    cudaEventDestroy(t.second.second);
+    const char* name = nullptr;
+    if (cudaFuncGetName(&name, t.first) != cudaSuccess || !name) name = "?";
+    auto& a = agg[name];
+    a.first++;
+    a.second += ms;
+    tot += ms;
+  }
+  cudaGetLastError();
+  c.trace->clear();
+  std::vector<std::pair<double, std::string>> order;
+  for (auto& kv : agg) order.push_back({kv.second.second, kv.first});
+  std::sort(order.rbegin(), order.rend());
+  fprintf(stderr, "[mslice trace] %.3f ms in %zu kernel kinds\n", tot, order.size());
+  for (auto& o : order) {
+    const auto& a = agg[o.second];
+    fprintf(stderr, "[mslice trace] %9.3f ms %5.1f%% %7lld launches %8.1f us/launch  %.110s\n", a.second,
+            100.0 * a.second / (tot > 0 ? tot : 1), (long long)a.first, 1e3 * a.second / a.first, o.second.c_str());
+  }
+}
 
 void* readback(Ctx& c, const void* dptr, size_t bytes) {
   check_cuda(cudaMemcpyAsync(c.pinned, dptr, bytes, cudaMemcpyDeviceToHost, c.stream), "readback");
@@ -363,6 +408,7 @@ int mslice_leiden_ex(mslice_handle h, const mslice_opts* o, const int32_t* init_
     if (o) opt = *o;
     if (opt.n_iterations < 1 || opt.K < 1 || opt.max_rounds < 1 || opt.max_levels < 1)
       fail(MSLICE_EINVAL, "n_iterations, K, max_rounds and max_levels must be >= 1");
+    if (opt.K > 64) fail(MSLICE_EINVAL, "K must be at most 64");
     if (!rational_ok(opt.gamma_num, opt.gamma_den, false)) fail(MSLICE_EINVAL, "gamma must be a rational > 0");
     if (!rational_ok(opt.omega_num, opt.omega_den, true)) fail(MSLICE_EINVAL, "omega must be a rational >= 0");
     if (!labels_out && h->G.N > 0) fail(MSLICE_EINVAL, "null labels_out");
@@ -373,6 +419,8 @@ int mslice_leiden_ex(mslice_handle h, const mslice_opts* o, const int32_t* init_
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_spans;
     c.profile = (opt.flags & MSLICE_PROFILE) != 0;
     c.prof_spans = &prof_spans;
+    std::vector<std::pair<const void*, std::pair<cudaEvent_t, cudaEvent_t>>> trace;
+    if (std::getenv("MSLICE_TRACE")) c.trace = &trace;
     PhaseClock clock(c);
     cudaEvent_t t_all = clock.begin();
 
@@ -535,6 +583,7 @@ int mslice_leiden_ex(mslice_handle h, const mslice_opts* o, const int32_t* init_
     stats.lm_moves = S.lm_moves;
     stats.kernel_launches = c.launches;
     h->launches += c.launches;
+    if (c.trace) trace_report(c);
     if (c.profile) {
       double dms = 0;
       for (auto& sp : prof_spans) {

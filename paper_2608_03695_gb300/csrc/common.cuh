@@ -50,10 +50,13 @@ struct HashView {
   Slot* slots;
   uint64_t cap;
   unsigned* status;
+  ull* used = nullptr;  // optional: counts slots taken since the last clear
 };
 
+// Home slot: one multiplicative mixing step (Fibonacci hashing) and a
+// multiply-high range reduction; slot positions never affect results.
 __device__ __forceinline__ uint64_t hash_home(ull key, uint64_t cap) {
-  return __umul64hi(mix64(key ^ 0x9E3779B97F4A7C15ULL), cap);
+  return __umul64hi((key ^ (key >> 29)) * 0x9E3779B97F4A7C15ULL, cap);
 }
 
 __device__ __forceinline__ ull pack_cs(int32_t c, int32_t s) {
@@ -72,6 +75,7 @@ __device__ __forceinline__ void hash_add(const HashView& h, ull key, long long d
       ull prev = atomicCAS(&h.slots[i].key, EMPTY_KEY, key);
       if (prev == EMPTY_KEY || prev == key) {
         atomicAdd((ull*)&h.slots[i].val, (ull)delta);
+        if (prev == EMPTY_KEY && h.used) atomicAdd(h.used, 1ull);
         return;
       }
     }
@@ -91,6 +95,22 @@ __device__ __forceinline__ long long hash_get(const HashView& h, ull key) {
   }
   return 0;
 }
+
+// Lookup continuing from an already loaded home slot `first`.
+__device__ __forceinline__ long long hash_get_from(const HashView& h, ull key, const Slot& first) {
+  if (first.key == key) return first.val;
+  if (first.key == EMPTY_KEY) return 0;
+  uint64_t i = hash_home(key, h.cap);
+  for (uint64_t probe = 1; probe < h.cap; ++probe) {
+    i = (i + 1 == h.cap) ? 0 : i + 1;
+    const Slot s = h.slots[i];
+    if (s.key == key) return s.val;
+    if (s.key == EMPTY_KEY) return 0;
+  }
+  return 0;
+}
+
+__device__ __forceinline__ Slot hash_first(const HashView& h, ull key) { return h.slots[hash_home(key, h.cap)]; }
 
 // -------------------------------------------------------------------------
 // Unsigned 128-bit accumulation into two 64-bit words with carry propagation.

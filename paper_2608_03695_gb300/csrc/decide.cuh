@@ -1,81 +1,69 @@
 // Generic move-decision kernels.  For each node v of a work list the
 // neighbour weights are aggregated per key (community or sub-community
-// label), every distinct key is scored by the policy, and the best candidate
-// (largest key, ties to the smallest label) is handed to the policy.
+// label) in a small open-addressing table, every distinct key is scored by
+// the policy, and the best candidate (largest key, ties to the smallest
+// label) is handed to the policy together with the key of staying.
 //
-// Three tiers by degree, all grid-stride over a device-resident list whose
-// length is read on the device:
-//   warp   deg <= 32   one warp per node; lanes holding equal keys are grouped
-//                      with __match_any_sync and summed in shared memory;
-//   block  deg <= 1024 one block per node, shared-memory open-addressing table;
-//   global otherwise   one block per node, table in global scratch (2*deg
-//                      slots rounded up to a power of two, offset per node).
+// The work is latency-bound (row pointer -> entries -> neighbour labels ->
+// per-community table), so the kernels aim at many independent loads in
+// flight: small groups of lanes per low-degree node, all entry loads of a
+// lane issued before any insert, scoring restricted to the node's distinct
+// candidates, and the next node's row bounds fetched while the current node
+// is scored.  Adjacency entries are read with
+// evict-first loads so the label and community tables stay in L2.
+//
+// Five tiers by degree, all grid-stride over a device-resident list whose
+// length is read on the device (no host round trip):
+//   tier 0  deg <= 16    4-lane groups, eight nodes per warp, 32-slot tables
+//   tier 1  deg <= 32    8-lane groups, four nodes per warp, 64-slot tables
+//   tier 2  deg <= 128   one warp per node, 256-slot table
+//   tier 3  deg <= 1024  one 256-thread block per node, shared table of
+//                        2*deg slots rounded up to a power of two
+//   tier 4  larger       one block per node, table in global scratch
 //
 // Policy interface (all __device__):
 //   bool begin(v)                      node takes part (uniform per node)
+//   VCtx vctx(v)                       per-node values computed once (and
+//                                      loads issued early for finish())
 //   void skip(v)                       record "no move" for a non-participant
 //   bool edge(v, e, key&, w&)          entry e contributes w to key
-//   Cand cand(v, key, W)               score of moving v to key (INT32_MAX = not allowed)
-//   int32_t own_key(v)                 the key whose weight finish() needs (-1 none)
-//   void finish(v, best, W_best, W_own)
+//   Probe probe(v, vc, key)            first table load(s) for scoring key
+//   Cand cand(v, vc, key, W, probe)    score of moving to key (INT32_MAX = not allowed)
+//   int32_t own_key(v)                 the node's current key (-1 none)
+//   i128 own(v, vc, W_own)             score of staying
+//   void finish(v, best, W_best, G_own, vc)
 #pragma once
+#include "internal.h"
 #include "level.h"
 
 namespace mslice {
 
-constexpr int WARP_TIER_MAX = 32;
-constexpr int BLOCK_TIER_MAX = 1024;
-constexpr int BLOCK_TIER_SLOTS = 2048;
-constexpr int BLOCK_TIER_THREADS = 128;
-constexpr int GLOBAL_TIER_THREADS = 256;
-constexpr int DECIDE_WARP_THREADS = 256;
+// Tuning parameter (compile-time): minimum resident blocks per SM for the
+// group kernels, which caps their registers (occupancy matters more than
+// per-warp parallelism for these latency-bound loops).
+#ifndef MSLICE_GROUP_MIN_BLOCKS
+#define MSLICE_GROUP_MIN_BLOCKS 4
+#endif
+
+constexpr int NTIERS = 5;
+constexpr int TIER_MAX[NTIERS - 1] = {16, 32, 128, 1024};
+constexpr int TIER3_BITS = 11;  // 2 * 1024 slots
+constexpr int BLOCK_THREADS = 256;
+constexpr int GROUP_THREADS = 256;
+
+__host__ __device__ __forceinline__ int degree_tier(int64_t d) {
+  return d <= 16 ? 0 : (d <= 32 ? 1 : (d <= 128 ? 2 : (d <= 1024 ? 3 : 4)));
+}
 
 __device__ __forceinline__ uint32_t small_hash(int32_t key, int bits) {
   return ((uint32_t)key * 2654435769u) >> (32 - bits);
 }
 
-template <class Pol>
-__global__ void __launch_bounds__(DECIDE_WARP_THREADS) k_decide_warp(Pol pol, const int32_t* list, const int32_t* count_ptr) {
-  constexpr int WARPS = DECIDE_WARP_THREADS / 32;
-  __shared__ long long sw[WARPS][32];
-  const int count = *count_ptr;
-  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-  for (int idx = blockIdx.x * WARPS + wi; idx < count; idx += gridDim.x * WARPS) {
-    const int32_t v = list[idx];
-    if (!pol.begin(v)) {
-      if (lane == 0) pol.skip(v);
-      continue;
-    }
-    const int64_t beg = pol.g.rowptr[v];
-    const int deg = (int)(pol.g.rowptr[v + 1] - beg);
-    int32_t key = -1;
-    long long w = 0;
-    const bool valid = lane < deg && pol.edge(v, beg + lane, key, w);
-    sw[wi][lane] = 0;
-    __syncwarp();
-    const unsigned peers = __match_any_sync(0xffffffffu, valid ? key : -1);
-    const int leader = __ffs(peers) - 1;
-    if (valid) atomicAdd((ull*)&sw[wi][leader], (ull)w);
-    __syncwarp();
-    const bool lead = valid && leader == lane;
-    const long long Wk = lead ? sw[wi][lane] : 0;
-    Cand c{0, INT32_MAX};
-    if (lead) c = pol.cand(v, key, Wk);
-    const Cand best = warp_best(c);
-    const int32_t own = pol.own_key(v);
-    const unsigned mo = __ballot_sync(0xffffffffu, lead && key == own);
-    const unsigned mb = __ballot_sync(0xffffffffu, lead && key == best.label);
-    const long long Wown = mo ? sw[wi][__ffs(mo) - 1] : 0;
-    const long long Wb = mb ? sw[wi][__ffs(mb) - 1] : 0;
-    if (lane == 0) pol.finish(v, best, Wb, Wown);
-    __syncwarp();
-  }
-}
-
-template <int SLOTS_BITS>
-__device__ __forceinline__ void table_add(int32_t* hk, long long* hv, int32_t key, long long w) {
-  constexpr uint32_t mask = (1u << SLOTS_BITS) - 1u;
-  uint32_t i = small_hash(key, SLOTS_BITS);
+// Insert-or-add into a table of 2^bits slots (keys -1 = free).  Callers size
+// the table to at least twice the number of keys, so a free slot exists.
+__device__ __forceinline__ void table_add(int32_t* hk, long long* hv, int bits, int32_t key, long long w) {
+  const uint32_t mask = (1u << bits) - 1u;
+  uint32_t i = small_hash(key, bits);
   for (uint32_t p = 0; p <= mask; ++p) {
     const int32_t prev = atomicCAS(&hk[i], -1, key);
     if (prev == -1 || prev == key) {
@@ -83,6 +71,220 @@ __device__ __forceinline__ void table_add(int32_t* hk, long long* hv, int32_t ke
       return;
     }
     i = (i + 1) & mask;
+  }
+}
+
+__device__ __forceinline__ long long table_get(const int32_t* hk, const long long* hv, int bits, int32_t key) {
+  if (key < 0) return 0;
+  const uint32_t mask = (1u << bits) - 1u;
+  uint32_t i = small_hash(key, bits);
+  for (uint32_t p = 0; p <= mask; ++p) {
+    const int32_t k = hk[i];
+    if (k == key) return hv[i];
+    if (k == -1) return 0;
+    i = (i + 1) & mask;
+  }
+  return 0;
+}
+
+__device__ __forceinline__ Cand shfl_xor_cand_m(const Cand& c, int m, unsigned mask) {
+  Cand o;
+  ull lo = (ull)(u128)c.G, hi = (ull)((u128)c.G >> 64);
+  lo = __shfl_xor_sync(mask, lo, m);
+  hi = __shfl_xor_sync(mask, hi, m);
+  o.G = (i128)(((u128)hi << 64) | lo);
+  o.label = __shfl_xor_sync(mask, c.label, m);
+  return o;
+}
+
+template <int G>
+__device__ __forceinline__ Cand group_best(Cand c, unsigned mask) {
+#pragma unroll
+  for (int m = G / 2; m >= 1; m >>= 1) {
+    const Cand o = shfl_xor_cand_m(c, m, mask);
+    if (better(o, c)) c = o;
+  }
+  return c;
+}
+
+// Insert-or-add that reports the slot and whether this call claimed it.
+__device__ __forceinline__ int table_add_slot(int32_t* hk, long long* hv, int bits, int32_t key, long long w,
+                                              bool& fresh) {
+  const uint32_t mask = (1u << bits) - 1u;
+  uint32_t i = small_hash(key, bits);
+  for (uint32_t p = 0; p <= mask; ++p) {
+    const int32_t prev = atomicCAS(&hk[i], -1, key);
+    if (prev == -1 || prev == key) {
+      atomicAdd((ull*)&hv[i], (ull)w);
+      fresh = prev == -1;
+      return (int)i;
+    }
+    i = (i + 1) & mask;
+  }
+  fresh = false;
+  return -1;
+}
+
+// Tiers 0-2: G lanes per node, EPL entries per lane (deg <= G*EPL), 2^BITS
+// table slots per group in shared memory.  The distinct keys of a node are
+// listed as their slots are claimed, so scoring touches only real
+// candidates and only those slots are reset afterwards (the table is cleared
+// once per block, not once per node).
+template <class Pol, int G, int BITS, int EPL>
+__global__ void __launch_bounds__(GROUP_THREADS, MSLICE_GROUP_MIN_BLOCKS)
+    k_decide_groups(Pol pol, const int32_t* list, const int32_t* count_ptr) {
+  constexpr int WARPS = GROUP_THREADS / 32, GPW = 32 / G, SLOTS = 1 << BITS, MAXC = G * EPL;
+  constexpr int NG = WARPS * GPW;
+  __shared__ int32_t hk[NG][SLOTS];
+  __shared__ long long hv[NG][SLOTS];
+  __shared__ uint16_t cl[NG][MAXC];
+  __shared__ int32_t ncand[NG];
+  const int count = *count_ptr;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int gl = lane % G, gi = lane / G, gx = w * GPW + gi;
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (gi * G));
+  int32_t* K = hk[gx];
+  long long* V = hv[gx];
+  uint16_t* CL = cl[gx];
+#pragma unroll
+  for (int i = gl; i < SLOTS; i += G) {
+    K[i] = -1;
+    V[i] = 0;
+  }
+  if (gl == 0) ncand[gx] = 0;
+  __syncwarp(gmask);
+  const int ngroups = gridDim.x * NG;
+  int idx = blockIdx.x * NG + gx;
+  if (idx >= count) return;  // uniform per group
+  int32_t v = list[idx];
+  int64_t beg = pol.g.rowptr[v], end = pol.g.rowptr[v + 1];
+  for (;;) {
+    const int nidx = idx + ngroups;
+    const bool more = nidx < count;
+    const int32_t nv = more ? list[nidx] : 0;
+    int64_t nbeg = 0, nend = 0;
+    if (pol.begin(v)) {
+      const typename Pol::VCtx vc = pol.vctx(v);
+      int32_t keys[EPL];
+      long long ws[EPL];
+      bool ok[EPL];
+#pragma unroll
+      for (int j = 0; j < EPL; ++j) {
+        const int64_t e = beg + j * G + gl;
+        ok[j] = e < end && pol.edge(v, e, keys[j], ws[j]);
+      }
+      if (more) {
+        nbeg = pol.g.rowptr[nv];
+        nend = pol.g.rowptr[nv + 1];
+      }
+#pragma unroll
+      for (int j = 0; j < EPL; ++j) {
+        if (ok[j]) {
+          bool fresh;
+          const int slot = table_add_slot(K, V, BITS, keys[j], ws[j], fresh);
+          if (fresh) CL[atomicAdd(&ncand[gx], 1)] = (uint16_t)slot;
+        }
+      }
+      __syncwarp(gmask);
+      const int n = ncand[gx];
+      const int32_t own = pol.own_key(v);
+      Cand c{0, INT32_MAX};
+      for (int j = gl; j < n; j += G) {
+        const int slot = CL[j];
+        const int32_t key = K[slot];
+        if (key != own) {
+          const Cand x = pol.cand(v, vc, key, V[slot], pol.probe(v, vc, key));
+          if (better(x, c)) c = x;
+        }
+      }
+      i128 Gown = 0;
+      if (gl == 0) Gown = pol.own(v, vc, table_get(K, V, BITS, own));
+      c = group_best<G>(c, gmask);
+      if (gl == 0) {
+        const long long Wb = c.label != INT32_MAX ? table_get(K, V, BITS, c.label) : 0;
+        pol.finish(v, c, Wb, Gown, vc);
+      }
+      __syncwarp(gmask);
+      for (int j = gl; j < n; j += G) {
+        const int slot = CL[j];
+        K[slot] = -1;
+        V[slot] = 0;
+      }
+      if (gl == 0) ncand[gx] = 0;
+      __syncwarp(gmask);
+    } else {
+      if (gl == 0) pol.skip(v);
+      if (more) {
+        nbeg = pol.g.rowptr[nv];
+        nend = pol.g.rowptr[nv + 1];
+      }
+    }
+    if (!more) break;
+    idx = nidx;
+    v = nv;
+    beg = nbeg;
+    end = nend;
+  }
+}
+
+__device__ __forceinline__ int table_bits_for_degree(int64_t deg) {
+  int bits = 1;
+  while ((1ll << bits) < 2 * deg) ++bits;
+  return bits;
+}
+
+template <class Pol>
+__device__ __forceinline__ Cand score_range(const Pol& pol, int32_t v, const typename Pol::VCtx& vc, int32_t own,
+                                            const int32_t* hk, const long long* hv, int64_t S) {
+  Cand c{0, INT32_MAX};
+  for (int64_t i = threadIdx.x; i < S; i += blockDim.x) {
+    const int32_t k = hk[i];
+    if (k >= 0 && k != own) {
+      const Cand x = pol.cand(v, vc, k, hv[i], pol.probe(v, vc, k));
+      if (better(x, c)) c = x;
+    }
+  }
+  return c;
+}
+
+// Tier 3: one block per node, shared table of 2*deg (rounded up) slots.
+template <class Pol>
+__global__ void __launch_bounds__(BLOCK_THREADS) k_decide_block(Pol pol, const int32_t* list, const int32_t* count_ptr) {
+  constexpr int SLOTS = 1 << TIER3_BITS;
+  __shared__ int32_t hk[SLOTS];
+  __shared__ long long hv[SLOTS];
+  __shared__ Cand red[BLOCK_THREADS / 32];
+  __shared__ i128 own_sm;
+  const int count = *count_ptr;
+  for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
+    const int32_t v = list[idx];
+    if (!pol.begin(v)) {
+      if (threadIdx.x == 0) pol.skip(v);
+      continue;
+    }
+    const typename Pol::VCtx vc = pol.vctx(v);
+    const int64_t beg = pol.g.rowptr[v], end = pol.g.rowptr[v + 1];
+    const int bits = table_bits_for_degree(end - beg);
+    const int S = 1 << bits;
+    for (int i = threadIdx.x; i < S; i += BLOCK_THREADS) {
+      hk[i] = -1;
+      hv[i] = 0;
+    }
+    __syncthreads();
+    for (int64_t e = beg + threadIdx.x; e < end; e += BLOCK_THREADS) {
+      int32_t key;
+      long long w;
+      if (pol.edge(v, e, key, w)) table_add(hk, hv, bits, key, w);
+    }
+    __syncthreads();
+    const int32_t own = pol.own_key(v);
+    if (threadIdx.x == 0) own_sm = pol.own(v, vc, table_get(hk, hv, bits, own));
+    const Cand best = block_best<BLOCK_THREADS / 32>(score_range(pol, v, vc, own, hk, hv, S), red);
+    if (threadIdx.x == 0) {
+      const long long Wb = best.label != INT32_MAX ? table_get(hk, hv, bits, best.label) : 0;
+      pol.finish(v, best, Wb, own_sm, vc);
+    }
+    __syncthreads();
   }
 }
 
@@ -101,26 +303,13 @@ __device__ __forceinline__ void gtable_add(int32_t* hk, long long* hv, int bits,
   atomicOr(status, ERR_HASH_FULL);
 }
 
-__device__ __forceinline__ long long table_get(const int32_t* hk, const long long* hv, int bits, int32_t key) {
-  if (key < 0) return 0;
-  const uint32_t mask = (1u << bits) - 1u;
-  uint32_t i = small_hash(key, bits);
-  for (uint32_t p = 0; p <= mask; ++p) {
-    const int32_t k = hk[i];
-    if (k == key) return hv[i];
-    if (k == -1) return 0;
-    i = (i + 1) & mask;
-  }
-  return 0;
-}
-
+// Tier 4: one block per node, table in global scratch at goff[v].
 template <class Pol>
-__global__ void __launch_bounds__(BLOCK_TIER_THREADS) k_decide_block(Pol pol, const int32_t* list, const int32_t* count_ptr) {
-  constexpr int BITS = 11;
-  static_assert((1 << BITS) == BLOCK_TIER_SLOTS, "slots");
-  __shared__ int32_t hk[BLOCK_TIER_SLOTS];
-  __shared__ long long hv[BLOCK_TIER_SLOTS];
-  __shared__ Cand red[BLOCK_TIER_THREADS / 32];
+__global__ void __launch_bounds__(BLOCK_THREADS) k_decide_global(Pol pol, const int32_t* list, const int32_t* count_ptr,
+                                                                 int32_t* gkeys, long long* gvals, const int64_t* goff,
+                                                                 unsigned* status) {
+  __shared__ Cand red[BLOCK_THREADS / 32];
+  __shared__ i128 own_sm;
   const int count = *count_ptr;
   for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
     const int32_t v = list[idx];
@@ -128,85 +317,56 @@ __global__ void __launch_bounds__(BLOCK_TIER_THREADS) k_decide_block(Pol pol, co
       if (threadIdx.x == 0) pol.skip(v);
       continue;
     }
-    for (int i = threadIdx.x; i < BLOCK_TIER_SLOTS; i += BLOCK_TIER_THREADS) {
-      hk[i] = -1;
-      hv[i] = 0;
-    }
-    __syncthreads();
-    const int64_t beg = pol.g.rowptr[v], end = pol.g.rowptr[v + 1];
-    for (int64_t e = beg + threadIdx.x; e < end; e += BLOCK_TIER_THREADS) {
-      int32_t key;
-      long long w;
-      if (pol.edge(v, e, key, w)) table_add<BITS>(hk, hv, key, w);
-    }
-    __syncthreads();
-    Cand c{0, INT32_MAX};
-    for (int i = threadIdx.x; i < BLOCK_TIER_SLOTS; i += BLOCK_TIER_THREADS) {
-      const int32_t k = hk[i];
-      if (k >= 0) {
-        const Cand x = pol.cand(v, k, hv[i]);
-        if (better(x, c)) c = x;
-      }
-    }
-    const Cand best = block_best<BLOCK_TIER_THREADS / 32>(c, red);
-    if (threadIdx.x == 0) {
-      const long long Wb = best.label != INT32_MAX ? table_get(hk, hv, BITS, best.label) : 0;
-      const long long Wown = table_get(hk, hv, BITS, pol.own_key(v));
-      pol.finish(v, best, Wb, Wown);
-    }
-    __syncthreads();
-  }
-}
-
-__device__ __forceinline__ int table_bits_for_degree(int64_t deg) {
-  int bits = 1;
-  while ((1ll << bits) < 2 * deg) ++bits;
-  return bits;
-}
-
-template <class Pol>
-__global__ void __launch_bounds__(GLOBAL_TIER_THREADS) k_decide_global(Pol pol, const int32_t* list, const int32_t* count_ptr,
-                                int32_t* gkeys, long long* gvals, const int64_t* goff, unsigned* status) {
-  __shared__ Cand red[GLOBAL_TIER_THREADS / 32];
-  const int count = *count_ptr;
-  for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
-    const int32_t v = list[idx];
-    if (!pol.begin(v)) {
-      if (threadIdx.x == 0) pol.skip(v);
-      continue;
-    }
+    const typename Pol::VCtx vc = pol.vctx(v);
     const int64_t beg = pol.g.rowptr[v], end = pol.g.rowptr[v + 1];
     const int bits = table_bits_for_degree(end - beg);
     const int64_t S = 1ll << bits;
     int32_t* hk = gkeys + goff[v];
     long long* hv = gvals + goff[v];
-    for (int64_t i = threadIdx.x; i < S; i += GLOBAL_TIER_THREADS) {
+    for (int64_t i = threadIdx.x; i < S; i += BLOCK_THREADS) {
       hk[i] = -1;
       hv[i] = 0;
     }
     __syncthreads();
-    for (int64_t e = beg + threadIdx.x; e < end; e += GLOBAL_TIER_THREADS) {
+    for (int64_t e = beg + threadIdx.x; e < end; e += BLOCK_THREADS) {
       int32_t key;
       long long w;
       if (pol.edge(v, e, key, w)) gtable_add(hk, hv, bits, key, w, status);
     }
     __syncthreads();
-    Cand c{0, INT32_MAX};
-    for (int64_t i = threadIdx.x; i < S; i += GLOBAL_TIER_THREADS) {
-      const int32_t k = hk[i];
-      if (k >= 0) {
-        const Cand x = pol.cand(v, k, hv[i]);
-        if (better(x, c)) c = x;
-      }
-    }
-    const Cand best = block_best<GLOBAL_TIER_THREADS / 32>(c, red);
+    const int32_t own = pol.own_key(v);
+    if (threadIdx.x == 0) own_sm = pol.own(v, vc, table_get(hk, hv, bits, own));
+    const Cand best = block_best<BLOCK_THREADS / 32>(score_range(pol, v, vc, own, hk, hv, S), red);
     if (threadIdx.x == 0) {
       const long long Wb = best.label != INT32_MAX ? table_get(hk, hv, bits, best.label) : 0;
-      const long long Wown = table_get(hk, hv, bits, pol.own_key(v));
-      pol.finish(v, best, Wb, Wown);
+      pol.finish(v, best, Wb, own_sm, vc);
     }
     __syncthreads();
   }
+}
+
+// The tier lists of one sub-round (device pointers; counts on device).
+struct TierSegs {
+  const int32_t* list[NTIERS];
+  const int32_t* count[NTIERS];
+};
+
+// Launches the tiers of one sub-round; tier_cnt (host) skips tiers that are
+// empty at this level.  Grids are fixed multiples of the 152 SMs.
+template <class Pol>
+void decide_all(Ctx& c, const Pol& pol, const TierSegs& sg, const int32_t* tier_cnt, int32_t* gkeys,
+                long long* gvals, const int64_t* goff) {
+  if (tier_cnt[0] > 0)
+    launch(c, k_decide_groups<Pol, 4, 5, 4>, dim3(152 * 4), dim3(GROUP_THREADS), 0, pol, sg.list[0], sg.count[0]);
+  if (tier_cnt[1] > 0)
+    launch(c, k_decide_groups<Pol, 8, 6, 4>, dim3(152 * 4), dim3(GROUP_THREADS), 0, pol, sg.list[1], sg.count[1]);
+  if (tier_cnt[2] > 0)
+    launch(c, k_decide_groups<Pol, 32, 8, 4>, dim3(152 * 4), dim3(GROUP_THREADS), 0, pol, sg.list[2], sg.count[2]);
+  if (tier_cnt[3] > 0)
+    launch(c, k_decide_block<Pol>, dim3(152 * 4), dim3(BLOCK_THREADS), 0, pol, sg.list[3], sg.count[3]);
+  if (tier_cnt[4] > 0)
+    launch(c, k_decide_global<Pol>, dim3(152 * 2), dim3(BLOCK_THREADS), 0, pol, sg.list[4], sg.count[4], gkeys, gvals,
+           goff, c.d_status);
 }
 
 }  // namespace mslice

@@ -47,17 +47,37 @@ struct Ctx {
   unsigned* d_status = nullptr;  // device error bits
   int64_t launches = 0;
   bool profile = false;          // event-time the decision kernels
+  // MSLICE_TRACE: every launch is bracketed by CUDA events (per-kernel table
+  // printed at the end of a solve)
+  std::vector<std::pair<const void*, std::pair<cudaEvent_t, cudaEvent_t>>>* trace = nullptr;
   int64_t prof_bytes = 0;        // algorithmic bytes of the timed kernels
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* prof_spans = nullptr;
   void* pinned = nullptr;        // small pinned host buffer for readbacks (>= 4 KB)
 };
 
+void trace_begin(Ctx& c, const void* k, cudaEvent_t* e0);
+void trace_end(Ctx& c, const void* k, cudaEvent_t e0);
+
 template <class... KArgs, class... Args>
 inline void launch(Ctx& c, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, Args&&... args) {
   if (grid.x == 0 || grid.y == 0 || grid.z == 0) return;
+  cudaEvent_t e0 = nullptr;
+  if (c.trace) trace_begin(c, (const void*)k, &e0);
   k<<<grid, block, smem, c.stream>>>(std::forward<Args>(args)...);
   c.launches++;
   check_cuda(cudaGetLastError(), "kernel launch");
+  if (c.trace) trace_end(c, (const void*)k, e0);
+}
+
+// Cooperative launch (grid-wide barriers); the grid must be co-resident.
+template <class... KArgs, class... Args>
+inline void launch_coop(Ctx& c, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, Args... args) {
+  void* argv[] = {(void*)&args...};
+  cudaEvent_t e0 = nullptr;
+  if (c.trace) trace_begin(c, (const void*)k, &e0);
+  check_cuda(cudaLaunchCooperativeKernel((const void*)k, grid, block, argv, smem, c.stream), "cooperative launch");
+  c.launches++;
+  if (c.trace) trace_end(c, (const void*)k, e0);
 }
 
 inline unsigned grid_for(int64_t n, int per_block) {

@@ -26,7 +26,7 @@ struct LevelDev {
 // A coupling entry has weight on and is absent when on = 0.
 __device__ __forceinline__ bool edge_at(const LevelDev& g, int64_t e, int32_t& u, long long& W) {
   if (g.is0) {
-    const int2 x = g.adj0[e];
+    const int2 x = __ldcs(&g.adj0[e]);
     u = x.x;
     if (x.y == 0) {
       W = g.on;
@@ -35,8 +35,8 @@ __device__ __forceinline__ bool edge_at(const LevelDev& g, int64_t e, int32_t& u
     W = (long long)x.y * g.od;
     return true;
   }
-  u = g.col[e];
-  W = g.W[e];
+  u = __ldcs(&g.col[e]);
+  W = __ldcs(&g.W[e]);
   return true;
 }
 

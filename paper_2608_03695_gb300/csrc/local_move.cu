@@ -14,52 +14,73 @@
 // (key 0, losing ties); it moves only on a strict improvement; a node alone
 // in its community joins another singleton community only if that label is
 // smaller (otherwise two neighbouring singletons could swap forever).
+//
+// Sigma_{c,s} lives in a hash keyed (c, s) and is kept exact by the integer
+// atomics of every move; it is rebuilt from the labels only at the start of
+// a level and when tombstone keys fill half of the table.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cstring>
+
 #include "decide.cuh"
 #include "solver.h"
+
+namespace cg = cooperative_groups;
 
 namespace mslice {
 
 namespace {
 
 constexpr int APPLY_THREADS = 256;
+constexpr int EMPTY_THREADS = 512;
 
 unsigned fixed_grid(int per_sm) { return 152u * (unsigned)per_sm; }
 
 __global__ void k_tier(const int64_t* rowptr, int32_t N, uint8_t* tier, int32_t* cnt, int64_t* gsize) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t d = rowptr[v + 1] - rowptr[v];
-    const int t = d <= WARP_TIER_MAX ? 0 : (d <= BLOCK_TIER_MAX ? 1 : 2);
-    tier[v] = (uint8_t)t;
-    int64_t S = 0;
-    if (t == 2) {
-      S = 2;
-      while (S < 2 * d) S <<= 1;
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < N; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = base + threadIdx.x;
+    int t = -1;
+    if (v < N) {
+      const int64_t d = rowptr[v + 1] - rowptr[v];
+      t = degree_tier(d);
+      tier[v] = (uint8_t)t;
+      int64_t S = 0;
+      if (t == NTIERS - 1) {
+        S = 2;
+        while (S < 2 * d) S <<= 1;
+      }
+      gsize[v] = S;
     }
-    gsize[v] = S;
-    atomicAdd(&cnt[t], 1);
+    const unsigned peers = __match_any_sync(0xffffffffu, t);
+    if (t >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[t], __popc(peers));
   }
 }
 
 // Buckets the nodes of this round by (class, tier): row q of `lists` holds
 // class q, tier t at [tier_off[t], tier_off[t] + count).  Order inside a
 // bucket does not matter: decisions read only the sub-round snapshot.
+struct TierOff {
+  int32_t off[NTIERS];
+};
+
 __global__ void k_bucket(int32_t N, const uint8_t* tier, uint64_t seed, uint64_t tag, uint64_t it, uint64_t lvl,
-                         uint64_t r, int K, int32_t* lists, int64_t row_stride, int3 tier_off, int32_t* cursors) {
+                         uint64_t r, int K, int32_t* lists, int64_t row_stride, TierOff tier_off, int32_t* cursors) {
   const int lane = threadIdx.x & 31;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < N; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t v = base + threadIdx.x;
     const bool ok = v < N;
     int seg = -1;
-    if (ok) seg = vertex_class(seed, tag, it, lvl, r, (uint64_t)v, K) * 3 + tier[v];
+    if (ok) seg = vertex_class(seed, tag, it, lvl, r, (uint64_t)v, K) * NTIERS + tier[v];
     const unsigned peers = __match_any_sync(0xffffffffu, seg);
     const int leader = __ffs(peers) - 1;
     int pos = 0;
     if (ok && lane == leader) pos = atomicAdd(&cursors[seg], __popc(peers));
     pos = __shfl_sync(peers, pos, leader);
     if (ok) {
-      const int q = seg / 3, t = seg % 3;
-      const int off = t == 0 ? tier_off.x : (t == 1 ? tier_off.y : tier_off.z);
-      lists[(int64_t)q * row_stride + off + pos + __popc(peers & ((1u << lane) - 1u))] = (int32_t)v;
+      const int q = seg / NTIERS, t = seg % NTIERS;
+      lists[(int64_t)q * row_stride + tier_off.off[t] + pos + __popc(peers & ((1u << lane) - 1u))] = (int32_t)v;
     }
   }
 }
@@ -110,7 +131,33 @@ struct LMPolicy {
   int32_t* target;
   long long od;
 
+  typedef Slot Probe;
+  // Per node: own community and its size; at level 0 the node's snapshot s,
+  // strength k and A = od * Lambda_s * k, so a candidate costs one probe and
+  // one 128x64-bit product.
+  struct VCtx {
+    int32_t a, size_a, s;
+    bool single;
+    long long k;
+    u128 A;
+  };
+
   __device__ bool begin(int32_t) const { return true; }
+  __device__ VCtx vctx(int32_t v) const {
+    VCtx c;
+    c.a = labels[v];
+    c.size_a = size[c.a];
+    c.single = g.is0 != 0;
+    c.s = 0;
+    c.k = 0;
+    c.A = 0;
+    if (c.single) {
+      c.k = g.k0[v];
+      c.s = v / g.n;
+      if (c.k > 0) c.A = (u128)(ull)od * lam[c.s] * (u128)(ull)c.k;
+    }
+    return c;
+  }
   __device__ void skip(int32_t v) const { target[v] = NO_MOVE; }
   __device__ bool edge(int32_t, int64_t e, int32_t& key, long long& w) const {
     int32_t u;
@@ -123,32 +170,43 @@ struct LMPolicy {
     const u128 ns = null_sum(g, lam, sig, v, c, self);
     return (((i128)W) << P_BITS) - (i128)((u128)(ull)od * ns);
   }
-  __device__ Cand cand(int32_t v, int32_t c, long long W) const {
-    if (c == labels[v]) return Cand{0, INT32_MAX};
+  __device__ Probe probe(int32_t, const VCtx& vc, int32_t c) const {
+    if (vc.single && vc.k > 0) return hash_first(sig, pack_cs(c, vc.s));
+    return Slot{EMPTY_KEY, 0};
+  }
+  __device__ Cand cand(int32_t v, const VCtx& vc, int32_t c, long long W, const Probe& pr) const {
+    if (vc.single) {
+      const long long x = vc.k > 0 ? hash_get_from(sig, pack_cs(c, vc.s), pr) : 0;
+      return Cand{(((i128)W) << P_BITS) - (i128)(vc.A * (u128)(ull)x), c};
+    }
     return Cand{key_of(v, c, W, false), c};
   }
-  __device__ void finish(int32_t v, const Cand& best, long long, long long Wown) const {
-    const int32_t a = labels[v];
-    const i128 Ga = key_of(v, a, Wown, true);
+  __device__ i128 own(int32_t v, const VCtx& vc, long long Wown) const {
+    if (vc.single) {
+      const long long x = vc.k > 0 ? hash_get(sig, pack_cs(vc.a, vc.s)) - vc.k : 0;
+      return (((i128)Wown) << P_BITS) - (i128)(vc.A * (u128)(ull)x);
+    }
+    return key_of(v, vc.a, Wown, true);
+  }
+  __device__ void finish(int32_t v, const Cand& best, long long, const i128& Ga, const VCtx& vc) const {
+    const int32_t a = vc.a;
     const bool has = best.label != INT32_MAX;
     const i128 Gmax = (has && best.G > Ga) ? best.G : Ga;
     int32_t t = NO_MOVE;
-    if (size[a] > 1 && Gmax < 0) {
+    if (vc.size_a > 1 && Gmax < 0) {
       t = TO_EMPTY;
     } else if (has && best.G > Ga) {
-      if (!(size[a] == 1 && size[best.label] == 1 && best.label > a)) t = best.label;
+      if (!(vc.size_a == 1 && best.label > a && size[best.label] == 1)) t = best.label;
     }
     target[v] = t;
   }
 };
 
-struct Segs {
-  const int32_t* list[3];
-  const int32_t* count[3];
-};
+typedef TierSegs Segs;
 
 __device__ __forceinline__ bool seg_item(const Segs& sg, int64_t idx, int32_t& v) {
-  for (int t = 0; t < 3; ++t) {
+#pragma unroll
+  for (int t = 0; t < NTIERS; ++t) {
     const int cnt = *sg.count[t];
     if (idx < cnt) {
       v = sg.list[t][idx];
@@ -159,10 +217,16 @@ __device__ __forceinline__ bool seg_item(const Segs& sg, int64_t idx, int32_t& v
   return false;
 }
 
-__device__ __forceinline__ int seg_total(const Segs& sg) { return *sg.count[0] + *sg.count[1] + *sg.count[2]; }
+__device__ __forceinline__ int seg_total(const Segs& sg) {
+  int t = 0;
+#pragma unroll
+  for (int i = 0; i < NTIERS; ++i) t += *sg.count[i];
+  return t;
+}
 
-// Applies the sub-round's decisions: labels, community sizes and Sigma.
-// Moves to an empty community only leave here (the label is assigned below).
+// Applies the sub-round's decisions: labels, community sizes and Sigma, and
+// resets each applied decision.  Moves to an empty community only leave here
+// (their label is assigned by k_empty_pass).
 __global__ void k_lm_apply(LevelDev g, Segs sg, int32_t* labels, int32_t* size, HashView sig, int32_t* target,
                            int32_t* counters) {
   const int total = seg_total(sg);
@@ -187,6 +251,7 @@ __global__ void k_lm_apply(LevelDev g, Segs sg, int32_t* labels, int32_t* size, 
     if (t >= 0) {
       atomicAdd(&size[t], 1);
       labels[v] = t;
+      target[v] = NO_MOVE;
       local++;
     } else {
       local_empty++;
@@ -200,60 +265,110 @@ __global__ void k_lm_apply(LevelDev g, Segs sg, int32_t* labels, int32_t* size, 
   }
 }
 
-__global__ void k_free_flags(const int32_t* size, int32_t N, int32_t* flag, const int32_t* n_empty) {
-  if (*n_empty == 0) return;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    flag[i] = size[i] == 0 ? 1 : 0;
-}
-
-__global__ void k_free_scatter(const int32_t* size, const int32_t* rank, int32_t N, int32_t* freelist,
-                               const int32_t* n_empty) {
-  if (*n_empty == 0) return;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    if (size[i] == 0) freelist[rank[i]] = (int32_t)i;
-}
-
-__global__ void k_empty_flags(const int32_t* target, int32_t N, int32_t* flag, const int32_t* n_empty) {
-  if (*n_empty == 0) return;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    flag[i] = target[i] == TO_EMPTY ? 1 : 0;
-}
-
-// Moves to an empty community: in ascending node order, the ascending labels
-// that are free once every other move is applied and the movers have left.
-__global__ void k_empty_assign(LevelDev g, const int32_t* target, const int32_t* rank, const int32_t* freelist,
-                               int32_t* labels, int32_t* size, HashView sig, int32_t* counters) {
-  if (counters[2] == 0) return;
-  int local = 0;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += (int64_t)gridDim.x * blockDim.x) {
-    if (target[v] != TO_EMPTY) continue;
-    const int32_t L = freelist[rank[v]];
-    labels[v] = L;
-    size[L] = 1;
-    int64_t b, e;
-    slice_range(g, (int32_t)v, b, e);
-    for (int64_t j = b; j < e; ++j) {
-      int32_t s;
-      long long k;
-      slice_entry(g, (int32_t)v, j, s, k);
-      hash_add(sig, pack_cs(L, s), k);
+template <class T>
+__device__ __forceinline__ T block_scan_excl(T x, T* sm, T& total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  T incl = x;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const T y = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += y;
+  }
+  if (lane == 31) sm[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    const T a = lane < nw ? sm[lane] : T(0);
+    T ai = a;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const T y = __shfl_up_sync(0xffffffffu, ai, d);
+      if (lane >= d) ai += y;
     }
-    local++;
+    if (lane < nw) sm[lane] = ai - a;
+    if (lane == nw - 1) sm[32] = ai;
   }
-  local = warp_sum(local);
-  if ((threadIdx.x & 31) == 0 && local) atomicAdd((ull*)counters, (ull)local);
+  __syncthreads();
+  const T r = incl - x + sm[w];
+  total = sm[32];
+  __syncthreads();
+  return r;
 }
 
-__global__ void k_reset_targets(Segs sg, int32_t* target, int32_t* counters) {
-  const int total = seg_total(sg);
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    int32_t v;
-    if (seg_item(sg, idx, v)) target[v] = NO_MOVE;
+// Moves to an empty community (one cooperative launch; returns at once when
+// the sub-round has none).  In ascending node order, the movers take the
+// ascending labels that are free once every other move is applied and the
+// movers have left.  blk: 2*gridDim.x ints.
+__global__ void __launch_bounds__(EMPTY_THREADS) k_empty_pass(LevelDev g, int32_t* target, int32_t* labels,
+                                                              int32_t* size, HashView sig, int32_t* counters,
+                                                              int32_t* blk, int32_t* freelist) {
+  const int n_empty = counters[2];
+  if (n_empty == 0) return;
+  __shared__ int32_t sm[33];
+  cg::grid_group grid = cg::this_grid();
+  const int64_t N = g.N, nb = gridDim.x;
+  const int64_t chunk = (N + nb - 1) / nb;
+  const int64_t lo = min(N, (int64_t)blockIdx.x * chunk), hi = min(N, lo + chunk);
+  int cf = 0, ce = 0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    cf += size[i] == 0;
+    ce += target[i] == TO_EMPTY;
+  }
+  int tf, te;
+  block_scan_excl(cf, sm, tf);
+  block_scan_excl(ce, sm, te);
+  if (threadIdx.x == 0) {
+    blk[blockIdx.x] = tf;
+    blk[nb + blockIdx.x] = te;
+  }
+  grid.sync();
+  int pf = 0, pe = 0;
+  for (int b = threadIdx.x; b < blockIdx.x; b += blockDim.x) {
+    pf += blk[b];
+    pe += blk[nb + b];
+  }
+  int tot_pf, tot_pe;
+  block_scan_excl(pf, sm, tot_pf);
+  block_scan_excl(pe, sm, tot_pe);
+  pf = tot_pf;
+  pe = tot_pe;
+  // the first n_empty free labels, in order
+  for (int64_t base = lo; base < hi && pf < n_empty; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const int f = (i < hi && size[i] == 0) ? 1 : 0;
+    int tot;
+    const int r = block_scan_excl(f, sm, tot);
+    if (f && pf + r < n_empty) freelist[pf + r] = (int32_t)i;
+    pf += tot;
+  }
+  grid.sync();
+  for (int64_t base = lo; base < hi; base += blockDim.x) {
+    const int64_t v = base + threadIdx.x;
+    const int e = (v < hi && target[v] == TO_EMPTY) ? 1 : 0;
+    int tot;
+    const int r = block_scan_excl(e, sm, tot);
+    if (e) {
+      const int32_t L = freelist[pe + r];
+      labels[v] = L;
+      size[L] = 1;
+      int64_t b, en;
+      slice_range(g, (int32_t)v, b, en);
+      for (int64_t j = b; j < en; ++j) {
+        int32_t s;
+        long long k;
+        slice_entry(g, (int32_t)v, j, s, k);
+        hash_add(sig, pack_cs(L, s), k);
+      }
+      target[v] = NO_MOVE;
+    }
+    pe += tot;
+  }
+  grid.sync();
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    atomicAdd((ull*)counters, (ull)n_empty);
+    counters[2] = 0;
   }
 }
-
-__global__ void k_zero_empty(int32_t* counters) { counters[2] = 0; }
 
 }  // namespace
 
@@ -279,9 +394,11 @@ void solver_alloc(Solver& S) {
   S.tmp32b = c.ws->get<int32_t>("s_tmpb", N + 1);
   S.freelist = c.ws->get<int32_t>("s_free", N);
   S.tier = c.ws->get<uint8_t>("s_tier", N);
+  S.cls = c.ws->get<uint8_t>("s_cls", N);
   S.lists = c.ws->get<int32_t>("s_lists", (size_t)N * S.p.K);
-  S.cursors = c.ws->get<int32_t>("s_cursors", 3 * S.p.K + 3);
+  S.cursors = c.ws->get<int32_t>("s_cursors", NTIERS * S.p.K + NTIERS);
   S.counters = c.ws->get<int32_t>("s_counters", 8);
+  S.sig_used = c.ws->get<ull>("s_sig_used", 1);
   S.goff = c.ws->get<int64_t>("s_goff", N + 1);
   S.R = c.ws->get<int32_t>("s_R", N);
   S.sizeR = c.ws->get<int32_t>("s_sizeR", N);
@@ -292,10 +409,17 @@ void solver_alloc(Solver& S) {
   S.elig = c.ws->get<uint8_t>("s_elig", N);
   S.wc = c.ws->get<uint8_t>("s_wc", N);
   // hash tables keyed by (label, snapshot): at most one live key per
-  // (node, snapshot) entry plus the keys created by moves of one round
+  // (node, snapshot) entry; a rebuild is triggered when taken slots pass half
   const uint64_t cap = (uint64_t)(2 * N + 2 * ((N + S.p.K - 1) / S.p.K) + 64);
-  S.sig = HashView{c.ws->get<Slot>("s_sig", cap), cap, c.d_status};
-  S.kr = HashView{c.ws->get<Slot>("s_kr", cap), cap, c.d_status};
+  S.sig = HashView{c.ws->get<Slot>("s_sig", cap), cap, c.d_status, S.sig_used};
+  S.kr = HashView{c.ws->get<Slot>("s_kr", cap), cap, c.d_status, nullptr};
+  int max_blocks = 0;
+  check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_blocks, k_empty_pass, EMPTY_THREADS, 0), "occupancy");
+  int dev = 0, sms = 0;
+  check_cuda(cudaGetDevice(&dev), "device");
+  check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attribute");
+  S.empty_grid = std::max(1, std::min(max_blocks, 2) * sms);
+  S.empty_blk = c.ws->get<int32_t>("s_empty_blk", 2 * S.empty_grid);
   fill_i32(c, S.target, NO_MOVE, N);
   check_cuda(cudaMemsetAsync(S.counters, 0, 8 * sizeof(int32_t), c.stream), "memset");
 }
@@ -303,8 +427,8 @@ void solver_alloc(Solver& S) {
 void prepare_level(Solver& S, const Level& L) {
   Ctx& c = *S.c;
   const int32_t N = L.d.N;
-  int32_t* cnt = S.cursors;  // reused: 3 tier counts
-  check_cuda(cudaMemsetAsync(cnt, 0, 3 * sizeof(int32_t), c.stream), "memset");
+  int32_t* cnt = S.cursors;  // reused: tier counts
+  check_cuda(cudaMemsetAsync(cnt, 0, NTIERS * sizeof(int32_t), c.stream), "memset");
   int64_t* gsize = reinterpret_cast<int64_t*>(c.ws->get<int64_t>("s_gsize", (size_t)(N > 0 ? N : 1)));
   if (N > 0)
     launch(c, k_tier, dim3(grid_for(N, 256) < 4096 ? grid_for(N, 256) : 4096), dim3(256), 0, L.d.rowptr, N, S.tier,
@@ -313,19 +437,19 @@ void prepare_level(Solver& S, const Level& L) {
   scan_excl(c, gsize, S.goff, N, gtotal);
   check_cuda(cudaMemcpyAsync(S.goff + N, gtotal, sizeof(int64_t), cudaMemcpyDeviceToDevice, c.stream), "copy");
   struct {
-    int32_t cnt[3];
+    int32_t cnt[NTIERS];
     int32_t pad;
     int64_t gt;
   } hb;
-  check_cuda(cudaMemcpyAsync(&hb.cnt, cnt, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream), "copy");
+  check_cuda(cudaMemcpyAsync(&hb.cnt, cnt, NTIERS * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream), "copy");
   check_cuda(cudaMemcpyAsync(&hb.gt, gtotal, sizeof(int64_t), cudaMemcpyDeviceToHost, c.stream), "copy");
   sync(c);
-  S.tier_cnt[0] = hb.cnt[0];
-  S.tier_cnt[1] = hb.cnt[1];
-  S.tier_cnt[2] = hb.cnt[2];
-  S.tier_off[0] = 0;
-  S.tier_off[1] = hb.cnt[0];
-  S.tier_off[2] = hb.cnt[0] + hb.cnt[1];
+  int32_t off = 0;
+  for (int t = 0; t < NTIERS; ++t) {
+    S.tier_cnt[t] = hb.cnt[t];
+    S.tier_off[t] = off;
+    off += hb.cnt[t];
+  }
   if (hb.gt > S.gcap) {
     S.gcap = hb.gt;
     S.gkeys = c.ws->get<int32_t>("s_gkeys", S.gcap);
@@ -333,42 +457,36 @@ void prepare_level(Solver& S, const Level& L) {
   }
 }
 
-void sigma_rebuild(Solver& S, const Level& L, const int32_t* labels) {
+// Sigma (and, optionally, the community sizes) from the labels.
+static void rebuild_sigma(Solver& S, const Level& L, const int32_t* labels, bool sizes) {
   Ctx& c = *S.c;
+  const int32_t N = L.d.N;
+  if (sizes) check_cuda(cudaMemsetAsync(S.size, 0, (N > 0 ? N : 1) * sizeof(int32_t), c.stream), "memset");
+  if (S.sig_used) check_cuda(cudaMemsetAsync(S.sig_used, 0, sizeof(ull), c.stream), "memset");
   launch(c, k_hash_clear, dim3(fixed_grid(8)), dim3(256), 0, S.sig.slots, S.sig.cap);
-  if (L.d.N > 0)
-    launch(c, k_sigma_insert, dim3(grid_for(L.d.N, 256)), dim3(256), 0, L.d, labels, S.sig, (int32_t*)nullptr);
+  if (N > 0)
+    launch(c, k_sigma_insert, dim3(grid_for(N, 256)), dim3(256), 0, L.d, labels, S.sig, sizes ? S.size : nullptr);
 }
 
-// Buckets and returns the device segments of class q for every tier.
-static Segs bucket_segments(Solver& S, int q) {
-  Segs sg;
-  for (int t = 0; t < 3; ++t) {
+void sigma_rebuild(Solver& S, const Level& L, const int32_t* labels) { rebuild_sigma(S, L, labels, false); }
+
+TierSegs bucket_segments(Solver& S, int q) {
+  TierSegs sg;
+  for (int t = 0; t < NTIERS; ++t) {
     sg.list[t] = S.lists + (int64_t)q * S.N0 + S.tier_off[t];
-    sg.count[t] = S.cursors + 3 * q + t;
+    sg.count[t] = S.cursors + NTIERS * q + t;
   }
   return sg;
 }
 
 void bucket(Solver& S, const Level& L, uint64_t tag, int it, int lvl, int r) {
   Ctx& c = *S.c;
-  check_cuda(cudaMemsetAsync(S.cursors, 0, 3 * S.p.K * sizeof(int32_t), c.stream), "memset");
+  check_cuda(cudaMemsetAsync(S.cursors, 0, NTIERS * S.p.K * sizeof(int32_t), c.stream), "memset");
+  TierOff to;
+  for (int t = 0; t < NTIERS; ++t) to.off[t] = S.tier_off[t];
   if (L.d.N > 0)
     launch(c, k_bucket, dim3(grid_for(L.d.N, 256)), dim3(256), 0, L.d.N, (const uint8_t*)S.tier, S.p.seed, tag,
-           (uint64_t)it, (uint64_t)lvl, (uint64_t)r, S.p.K, S.lists, (int64_t)S.N0,
-           make_int3(S.tier_off[0], S.tier_off[1], S.tier_off[2]), S.cursors);
-}
-
-template <class Pol>
-void decide_all(Solver& S, const Pol& pol, const Segs& sg) {
-  Ctx& c = *S.c;
-  if (S.tier_cnt[0] > 0)
-    launch(c, k_decide_warp<Pol>, dim3(fixed_grid(8)), dim3(DECIDE_WARP_THREADS), 0, pol, sg.list[0], sg.count[0]);
-  if (S.tier_cnt[1] > 0)
-    launch(c, k_decide_block<Pol>, dim3(fixed_grid(8)), dim3(BLOCK_TIER_THREADS), 0, pol, sg.list[1], sg.count[1]);
-  if (S.tier_cnt[2] > 0)
-    launch(c, k_decide_global<Pol>, dim3(fixed_grid(4)), dim3(GLOBAL_TIER_THREADS), 0, pol, sg.list[2], sg.count[2],
-           S.gkeys, S.gvals, (const int64_t*)S.goff, c.d_status);
+           (uint64_t)it, (uint64_t)lvl, (uint64_t)r, S.p.K, S.lists, (int64_t)S.N0, to, S.cursors);
 }
 
 MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, int max_rounds) {
@@ -383,13 +501,10 @@ MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, 
     }
     return out;
   }
-  if (max_rounds <= 0) {
-    // no round: refinement still reads Sigma of the given labels
-    check_cuda(cudaMemsetAsync(S.size, 0, N * sizeof(int32_t), c.stream), "memset");
-    launch(c, k_hash_clear, dim3(fixed_grid(8)), dim3(256), 0, S.sig.slots, S.sig.cap);
-    launch(c, k_sigma_insert, dim3(grid_for(N, 256)), dim3(256), 0, L.d, (const int32_t*)labels, S.sig, S.size);
-    return out;
-  }
+  // community sizes and Sigma of the level's initial labels (refinement
+  // reads Sigma even when no round runs)
+  rebuild_sigma(S, L, labels, true);
+  if (max_rounds <= 0) return out;
   LMPolicy pol;
   pol.g = L.d;
   pol.labels = labels;
@@ -398,11 +513,9 @@ MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, 
   pol.lam = S.lam;
   pol.target = S.target;
   pol.od = S.p.od;
+  bool rebuild = false;
   for (int r = 0; r < max_rounds; ++r) {
-    // community sizes and Sigma from the labels
-    check_cuda(cudaMemsetAsync(S.size, 0, N * sizeof(int32_t), c.stream), "memset");
-    launch(c, k_hash_clear, dim3(fixed_grid(8)), dim3(256), 0, S.sig.slots, S.sig.cap);
-    launch(c, k_sigma_insert, dim3(grid_for(N, 256)), dim3(256), 0, L.d, (const int32_t*)labels, S.sig, S.size);
+    if (rebuild) rebuild_sigma(S, L, labels, false);
     check_cuda(cudaMemsetAsync(S.counters, 0, 3 * sizeof(int32_t), c.stream), "memset");
     bucket(S, L, 0, it, lvl, r);
     S.lm_rounds++;
@@ -415,32 +528,31 @@ MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, 
         check_cuda(cudaEventCreate(&e0), "event");
         check_cuda(cudaEventCreate(&e1), "event");
         check_cuda(cudaEventRecord(e0, c.stream), "event");
-        decide_all(S, pol, sg);
+        decide_all(c, pol, sg, S.tier_cnt, S.gkeys, S.gvals, S.goff);
         check_cuda(cudaEventRecord(e1, c.stream), "event");
         c.prof_spans->push_back({e0, e1});
       } else {
-        decide_all(S, pol, sg);
+        decide_all(c, pol, sg, S.tier_cnt, S.gkeys, S.gvals, S.goff);
       }
       launch(c, k_lm_apply, dim3(fixed_grid(4)), dim3(APPLY_THREADS), 0, L.d, sg, labels, S.size, S.sig, S.target,
              S.counters);
-      // moves to empty communities (kernels return at once when there are none)
-      const int32_t* n_empty = S.counters + 2;
-      launch(c, k_free_flags, dim3(fixed_grid(4)), dim3(256), 0, (const int32_t*)S.size, N, S.tmp32a, n_empty);
-      scan_excl(c, S.tmp32a, S.tmp32a, N, (int32_t*)nullptr, n_empty);
-      launch(c, k_free_scatter, dim3(fixed_grid(4)), dim3(256), 0, (const int32_t*)S.size, (const int32_t*)S.tmp32a, N,
-             S.freelist, n_empty);
-      launch(c, k_empty_flags, dim3(fixed_grid(4)), dim3(256), 0, (const int32_t*)S.target, N, S.tmp32b, n_empty);
-      scan_excl(c, S.tmp32b, S.tmp32b, N, (int32_t*)nullptr, n_empty);
-      launch(c, k_empty_assign, dim3(fixed_grid(4)), dim3(256), 0, L.d, (const int32_t*)S.target,
-             (const int32_t*)S.tmp32b, (const int32_t*)S.freelist, labels, S.size, S.sig, S.counters);
-      launch(c, k_reset_targets, dim3(fixed_grid(4)), dim3(256), 0, sg, S.target, S.counters);
-      launch(c, k_zero_empty, dim3(1), dim3(1), 0, S.counters);
+      launch_coop(c, k_empty_pass, dim3(S.empty_grid), dim3(EMPTY_THREADS), 0, L.d, S.target, labels, S.size, S.sig,
+                  S.counters, S.empty_blk, S.freelist);
     }
-    const int64_t moved = *static_cast<const int64_t*>(readback(c, S.counters, sizeof(int64_t)));
+    struct {
+      int64_t moved;
+      ull used;
+    } rb;
+    check_cuda(cudaMemcpyAsync(c.pinned, S.counters, sizeof(int64_t), cudaMemcpyDeviceToHost, c.stream), "copy");
+    check_cuda(cudaMemcpyAsync(static_cast<char*>(c.pinned) + 8, S.sig_used, sizeof(ull), cudaMemcpyDeviceToHost,
+                               c.stream), "copy");
+    sync(c);
+    std::memcpy(&rb, c.pinned, sizeof(rb));
     check_status(c, "local moving");
+    rebuild = rb.used * 2 > S.sig.cap;
     out.rounds++;
-    out.moves += moved;
-    if (moved == 0) break;
+    out.moves += rb.moved;
+    if (rb.moved == 0) break;
   }
   S.lm_moves += out.moves;
   return out;

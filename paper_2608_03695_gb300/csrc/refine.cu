@@ -61,6 +61,11 @@ __global__ void k_ref_init(LevelDev g, const int32_t* P, HashView sig, const u12
   }
 }
 
+__global__ void k_classes(int32_t N, uint64_t seed, uint64_t it, uint64_t lvl, int K, uint8_t* cls) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x)
+    cls[v] = (uint8_t)vertex_class(seed, 1, it, lvl, 0, (uint64_t)v, K);
+}
+
 __global__ void k_hash_clear2(Slot* slots, uint64_t cap) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += (uint64_t)gridDim.x * blockDim.x)
     slots[i] = Slot{EMPTY_KEY, 0};
@@ -108,15 +113,41 @@ struct RefPolicy {
   const int32_t* sizeR;
   const uint8_t* elig;
   const uint8_t* wc;
+  const uint8_t* cls;
   HashView kr;
   const u128* lam;
   int32_t* target;
   long long* Wsel;
   long long od;
-  uint64_t seed, it, lvl;
-  int K, q;
+  int q;
+
+  struct Probe {
+    Slot first;
+    int32_t size;
+    uint8_t cls, wc;
+  };
+  // Per node: at level 0 the snapshot s and A = od * Lambda_s * k.
+  struct VCtx {
+    int32_t s;
+    bool single;
+    long long k;
+    u128 A;
+  };
 
   __device__ bool begin(int32_t v) const { return sizeR[R[v]] == 1 && elig[v]; }
+  __device__ VCtx vctx(int32_t v) const {
+    VCtx c;
+    c.single = g.is0 != 0;
+    c.s = 0;
+    c.k = 0;
+    c.A = 0;
+    if (c.single) {
+      c.k = g.k0[v];
+      c.s = v / g.n;
+      if (c.k > 0) c.A = (u128)(ull)od * lam[c.s] * (u128)(ull)c.k;
+    }
+    return c;
+  }
   __device__ void skip(int32_t v) const { target[v] = NO_MOVE; }
   __device__ bool edge(int32_t v, int64_t e, int32_t& key, long long& w) const {
     int32_t u;
@@ -126,24 +157,40 @@ struct RefPolicy {
     return true;
   }
   __device__ int32_t own_key(int32_t) const { return -1; }
-  __device__ Cand cand(int32_t v, int32_t X, long long W) const {
-    if (X == R[v]) return Cand{0, INT32_MAX};
-    if (sizeR[X] == 1 && vertex_class(seed, 1, it, lvl, 0, (uint64_t)X, K) == q) return Cand{0, INT32_MAX};
-    if (!wc[X]) return Cand{0, INT32_MAX};
-    int64_t b, e;
-    slice_range(g, v, b, e);
-    u128 ns = 0;
-    for (int64_t j = b; j < e; ++j) {
-      int32_t s;
-      long long k;
-      slice_entry(g, v, j, s, k);
-      ns += lam_k_x(lam, s, k, hash_get(kr, pack_cs(X, s)));
+  __device__ i128 own(int32_t, const VCtx&, long long) const { return 0; }
+  __device__ Probe probe(int32_t, const VCtx& vc, int32_t X) const {
+    Probe p;
+    p.size = sizeR[X];
+    p.cls = cls[X];
+    p.wc = wc[X];
+    p.first = (vc.single && vc.k > 0) ? hash_first(kr, pack_cs(X, vc.s)) : Slot{EMPTY_KEY, 0};
+    return p;
+  }
+  // A singleton sub-community's label is its node, so cls[X] is the class of
+  // that node.
+  __device__ Cand cand(int32_t v, const VCtx& vc, int32_t X, long long W, const Probe& p) const {
+    if (p.size == 1 && p.cls == q) return Cand{0, INT32_MAX};
+    if (!p.wc) return Cand{0, INT32_MAX};
+    i128 G;
+    if (vc.single) {
+      const long long x = vc.k > 0 ? hash_get_from(kr, pack_cs(X, vc.s), p.first) : 0;
+      G = (((i128)W) << P_BITS) - (i128)(vc.A * (u128)(ull)x);
+    } else {
+      int64_t b, e;
+      slice_range(g, v, b, e);
+      u128 ns = 0;
+      for (int64_t j = b; j < e; ++j) {
+        int32_t s;
+        long long k;
+        slice_entry(g, v, j, s, k);
+        ns += lam_k_x(lam, s, k, hash_get(kr, pack_cs(X, s)));
+      }
+      G = (((i128)W) << P_BITS) - (i128)((u128)(ull)od * ns);
     }
-    const i128 G = (((i128)W) << P_BITS) - (i128)((u128)(ull)od * ns);
     if (G <= 0) return Cand{0, INT32_MAX};
     return Cand{G, X};
   }
-  __device__ void finish(int32_t v, const Cand& best, long long Wb, long long) const {
+  __device__ void finish(int32_t v, const Cand& best, long long Wb, const i128&, const VCtx&) const {
     if (best.label != INT32_MAX) {
       target[v] = best.label;
       Wsel[v] = Wb;
@@ -153,14 +200,17 @@ struct RefPolicy {
   }
 };
 
-struct Segs3 {
-  const int32_t* list[3];
-  const int32_t* count[3];
-};
+typedef TierSegs Segs3;
 
-__device__ __forceinline__ int seg3_total(const Segs3& sg) { return *sg.count[0] + *sg.count[1] + *sg.count[2]; }
+__device__ __forceinline__ int seg3_total(const Segs3& sg) {
+  int t = 0;
+#pragma unroll
+  for (int i = 0; i < NTIERS; ++i) t += *sg.count[i];
+  return t;
+}
 __device__ __forceinline__ bool seg3_item(const Segs3& sg, int64_t idx, int32_t& v) {
-  for (int t = 0; t < 3; ++t) {
+#pragma unroll
+  for (int t = 0; t < NTIERS; ++t) {
     const int cnt = *sg.count[t];
     if (idx < cnt) {
       v = sg.list[t][idx];
@@ -223,6 +273,7 @@ unsigned fixed_grid(int per_sm) { return 152u * (unsigned)per_sm; }
 }  // namespace
 
 void bucket(Solver& S, const Level& L, uint64_t tag, int it, int lvl, int r);
+TierSegs bucket_segments(Solver& S, int q);
 
 void refine(Solver& S, const Level& L, const int32_t* P, int it, int lvl) {
   Ctx& c = *S.c;
@@ -244,10 +295,8 @@ void refine(Solver& S, const Level& L, const int32_t* P, int it, int lvl) {
   pol.target = S.target;
   pol.Wsel = S.Wsel;
   pol.od = S.p.od;
-  pol.seed = S.p.seed;
-  pol.it = (uint64_t)it;
-  pol.lvl = (uint64_t)lvl;
-  pol.K = S.p.K;
+  pol.cls = S.cls;
+  launch(c, k_classes, dim3(fixed_grid(8)), dim3(256), 0, N, S.p.seed, (uint64_t)it, (uint64_t)lvl, S.p.K, S.cls);
   for (int q = 0; q < S.p.K; ++q) {
     // well-connectedness of every sub-community at the sub-round start
     if (q > 0) {
@@ -258,20 +307,8 @@ void refine(Solver& S, const Level& L, const int32_t* P, int it, int lvl) {
     launch(c, k_wc, dim3(fixed_grid(8)), dim3(256), 0, N, (const int32_t*)S.sizeR, (const long long*)S.Wout,
            (const ull*)S.rhs, (const uint8_t*)S.elig, S.p.od, S.wc);
     pol.q = q;
-    Segs3 sg;
-    for (int t = 0; t < 3; ++t) {
-      sg.list[t] = S.lists + (int64_t)q * S.N0 + S.tier_off[t];
-      sg.count[t] = S.cursors + 3 * q + t;
-    }
-    if (S.tier_cnt[0] > 0)
-      launch(c, k_decide_warp<RefPolicy>, dim3(fixed_grid(8)), dim3(DECIDE_WARP_THREADS), 0, pol, sg.list[0],
-             sg.count[0]);
-    if (S.tier_cnt[1] > 0)
-      launch(c, k_decide_block<RefPolicy>, dim3(fixed_grid(8)), dim3(BLOCK_TIER_THREADS), 0, pol, sg.list[1],
-             sg.count[1]);
-    if (S.tier_cnt[2] > 0)
-      launch(c, k_decide_global<RefPolicy>, dim3(fixed_grid(4)), dim3(GLOBAL_TIER_THREADS), 0, pol, sg.list[2],
-             sg.count[2], S.gkeys, S.gvals, (const int64_t*)S.goff, c.d_status);
+    const Segs3 sg = bucket_segments(S, q);
+    decide_all(c, pol, sg, S.tier_cnt, S.gkeys, S.gvals, S.goff);
     launch(c, k_ref_apply, dim3(fixed_grid(8)), dim3(256), 0, L.d, sg, P, (const int32_t*)S.target,
            (const long long*)S.Wc, (const long long*)S.Wsel, S.R, S.sizeR, S.Wout, S.kr);
     launch(c, k_ref_reset, dim3(fixed_grid(4)), dim3(256), 0, sg, S.target);

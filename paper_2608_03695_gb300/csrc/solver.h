@@ -27,9 +27,13 @@ struct Solver {
   int32_t* tmp32b = nullptr;
   int32_t* freelist = nullptr;
   uint8_t* tier = nullptr;
+  uint8_t* cls = nullptr;       // refinement class of every node of the level
   int32_t* lists = nullptr;     // K rows of N0 entries: nodes bucketed by class and tier
   int32_t* cursors = nullptr;   // 3K bucket fill counts (device)
   int32_t* counters = nullptr;  // [0] moves in round (low), [1] moves (high), [2] moves to empty in sub-round
+  ull* sig_used = nullptr;      // Sigma slots taken since its last rebuild
+  int32_t empty_grid = 0;       // co-resident grid of the empty-community pass
+  int32_t* empty_blk = nullptr;
   int64_t* goff = nullptr;      // global-tier table offsets
   int32_t* gkeys = nullptr;
   long long* gvals = nullptr;
@@ -48,8 +52,8 @@ struct Solver {
   uint8_t* wc = nullptr;
   HashView kr{};
 
-  int32_t tier_off[3] = {0, 0, 0};
-  int32_t tier_cnt[3] = {0, 0, 0};
+  int32_t tier_off[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int32_t tier_cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 
   // statistics
   int64_t lm_rounds = 0, lm_edges = 0, lm_moves = 0;
