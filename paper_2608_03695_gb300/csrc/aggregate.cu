@@ -54,22 +54,21 @@ __global__ void k_emit_edges(LevelDev g, const int32_t* R, const int32_t* newid,
   }
 }
 
-__global__ void k_emit_slices(HashView kr, const int32_t* newid, uint64_t T, uint64_t* keys, long long* vals,
+// Hashed K_{R,s}: entries in table order, sorted afterwards.
+__global__ void k_emit_slices(SigStore kr, const int32_t* newid, uint64_t T, uint64_t* keys, long long* vals,
                               ull* cursor) {
   const int lane = threadIdx.x & 31;
-  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < kr.cap; base += (uint64_t)gridDim.x * blockDim.x) {
+  const uint64_t span = ss_span(kr);
+  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < span; base += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t i = base + threadIdx.x;
     bool keep = false;
     uint64_t key = 0;
     long long val = 0;
-    if (i < kr.cap) {
-      const Slot sl = kr.slots[i];
-      if (sl.key != EMPTY_KEY && sl.val != 0) {
-        const int32_t Rl = (int32_t)(sl.key >> 32);
-        const uint64_t s = sl.key & 0xffffffffu;
+    if (i < span) {
+      int32_t Rl, s;
+      if (ss_entry(kr, i, Rl, s, val)) {
         keep = true;
-        key = (uint64_t)newid[Rl] * T + s;
-        val = sl.val;
+        key = (uint64_t)newid[Rl] * T + (uint64_t)s;
       }
     }
     const unsigned m = __ballot_sync(0xffffffffu, keep);
@@ -81,6 +80,34 @@ __global__ void k_emit_slices(HashView kr, const int32_t* newid, uint64_t T, uin
       const ull o = pos + __popc(m & ((1u << lane) - 1u));
       keys[o] = key;
       vals[o] = val;
+    }
+  }
+}
+
+// Dense K_{R,s}: rows are already in (new id, snapshot) order, since new ids
+// rank the present labels; count and copy the non-zero entries row by row.
+__global__ void k_dense_slice_counts(const long long* d, int32_t T, const int32_t* sizeR, const int32_t* newid,
+                                     int32_t N, int32_t* cnt) {
+  for (int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; L < N; L += (int64_t)gridDim.x * blockDim.x) {
+    if (sizeR[L] <= 0) continue;
+    int32_t c = 0;
+    for (int32_t s = 0; s < T; ++s) c += d[L * T + s] != 0;
+    cnt[newid[L]] = c;
+  }
+}
+
+__global__ void k_dense_slice_fill(const long long* d, int32_t T, const int32_t* sizeR, const int32_t* newid,
+                                   int32_t N, const int64_t* sptr, int32_t* sidx, long long* sval) {
+  for (int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; L < N; L += (int64_t)gridDim.x * blockDim.x) {
+    if (sizeR[L] <= 0) continue;
+    int64_t o = sptr[newid[L]];
+    for (int32_t s = 0; s < T; ++s) {
+      const long long x = d[L * T + s];
+      if (x != 0) {
+        sidx[o] = s;
+        sval[o] = x;
+        ++o;
+      }
     }
   }
 }
@@ -219,21 +246,36 @@ bool aggregate(Solver& S, const Level& L, const int32_t* P, Level& next, const s
 
   // ---- snapshot strengths ----
   const uint64_t T = (uint64_t)S.G0->T;
-  const int64_t scap = (int64_t)S.kr.cap;
-  uint64_t* sk0 = c.ws->get<uint64_t>("ag_sk0", scap);
-  long long* sv0 = c.ws->get<long long>("ag_sv0", scap);
-  uint64_t* sk1 = c.ws->get<uint64_t>("ag_sk1", scap);
-  long long* sv1 = c.ws->get<long long>("ag_sv1", scap);
-  launch(c, k_emit_slices, dim3(gsz(scap)), dim3(256), 0, S.kr, (const int32_t*)newid, T, sk0, sv0, cursor + 1);
-  const int64_t ms = (int64_t) * static_cast<const ull*>(readback(c, cursor + 1, sizeof(ull)));
-  const SortBufs ss = radix_sort_pairs(c, sk0, sv0, sk1, sv1, ms, bits_for((uint64_t)Np * T - 1));
   int64_t* sptr = c.ws->get<int64_t>(slot + "_sptr", (size_t)Np + 1);
-  int32_t* sidx = c.ws->get<int32_t>(slot + "_sidx", ms);
-  long long* sval = c.ws->get<long long>(slot + "_sval", ms);
+  int64_t ms = 0;
+  int32_t* sidx = nullptr;
+  long long* sval = nullptr;
   check_cuda(cudaMemsetAsync(cnt, 0, ((size_t)Np + 1) * sizeof(int32_t), c.stream), "memset");
-  launch(c, k_slices_of, dim3(gsz(ms)), dim3(256), 0, (const uint64_t*)ss.keys, (const long long*)ss.vals, ms, T, cnt,
-         sidx, sval);
-  scan_excl(c, cnt, sptr, (int64_t)Np + 1, (int64_t*)nullptr);
+  if (S.kr.d) {
+    launch(c, k_dense_slice_counts, dim3(gsz(N)), dim3(256), 0, (const long long*)S.kr.d, (int32_t)T,
+           (const int32_t*)S.sizeR, (const int32_t*)newid, N, cnt);
+    int64_t* d_ms = c.ws->get<int64_t>("ag_ms", 1);
+    scan_excl(c, cnt, sptr, (int64_t)Np + 1, d_ms);
+    ms = *static_cast<const int64_t*>(readback(c, d_ms, sizeof(int64_t)));
+    sidx = c.ws->get<int32_t>(slot + "_sidx", ms);
+    sval = c.ws->get<long long>(slot + "_sval", ms);
+    launch(c, k_dense_slice_fill, dim3(gsz(N)), dim3(256), 0, (const long long*)S.kr.d, (int32_t)T,
+           (const int32_t*)S.sizeR, (const int32_t*)newid, N, (const int64_t*)sptr, sidx, sval);
+  } else {
+    const int64_t scap = (int64_t)S.kr.h.cap;
+    uint64_t* sk0 = c.ws->get<uint64_t>("ag_sk0", scap);
+    long long* sv0 = c.ws->get<long long>("ag_sv0", scap);
+    uint64_t* sk1 = c.ws->get<uint64_t>("ag_sk1", scap);
+    long long* sv1 = c.ws->get<long long>("ag_sv1", scap);
+    launch(c, k_emit_slices, dim3(gsz(scap)), dim3(256), 0, S.kr, (const int32_t*)newid, T, sk0, sv0, cursor + 1);
+    ms = (int64_t) * static_cast<const ull*>(readback(c, cursor + 1, sizeof(ull)));
+    const SortBufs ss = radix_sort_pairs(c, sk0, sv0, sk1, sv1, ms, bits_for((uint64_t)Np * T - 1));
+    sidx = c.ws->get<int32_t>(slot + "_sidx", ms);
+    sval = c.ws->get<long long>(slot + "_sval", ms);
+    launch(c, k_slices_of, dim3(gsz(ms)), dim3(256), 0, (const uint64_t*)ss.keys, (const long long*)ss.vals, ms, T,
+           cnt, sidx, sval);
+    scan_excl(c, cnt, sptr, (int64_t)Np + 1, (int64_t*)nullptr);
+  }
   next.d.sptr = sptr;
   next.d.sidx = sidx;
   next.d.sval = sval;

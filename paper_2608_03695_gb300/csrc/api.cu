@@ -487,6 +487,14 @@ int mslice_leiden_ex(mslice_handle h, const mslice_opts* o, const int32_t* init_
         cudaEvent_t t0 = clock.begin();
         const MoveOut mo = local_move(S, cur, lab, it, lvl, rounds);
         clock.end(1, t0);
+        if (c.trace) {
+          sync(c);
+          float ms = 0;
+          cudaEventElapsedTime(&ms, t0, clock.spans.back().second.second);
+          fprintf(stderr, "[mslice level] it=%d lvl=%d N=%d nnz=%lld rounds=%lld moves=%lld lm_ms=%.3f tiers=%d/%d/%d/%d/%d\n",
+                  it, lvl, cur.d.N, (long long)cur.nnz, (long long)mo.rounds, (long long)mo.moves, ms, S.tier_cnt[0],
+                  S.tier_cnt[1], S.tier_cnt[2], S.tier_cnt[3], S.tier_cnt[4]);
+        }
         if (lvl == 0) stats.last_level0_moves = mo.moves;
         if (stop_here && opt.stop_stage == 1) {
           check_cuda(cudaMemcpyAsync(labels_out, lab, cur.d.N * sizeof(int32_t),
@@ -633,8 +641,7 @@ int mslice_modularity_ex(mslice_handle h, const int32_t* labels, int64_t gamma_n
     S.p.od = omega_den;
     S.N0 = G.N;
     const int64_t N = G.N > 0 ? G.N : 1;
-    const uint64_t cap = (uint64_t)(2 * N + 64);
-    S.sig = HashView{h->ws.get<Slot>("m_sig", cap), cap, c.d_status};
+    S.sig_used = h->ws.get<ull>("m_used", 1);
     int32_t* lab = h->ws.get<int32_t>("m_lab", N);
     if (G.N > 0) {
       const bool dev = (flags & MSLICE_DEVICE_PTRS) != 0;

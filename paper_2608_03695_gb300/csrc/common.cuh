@@ -113,6 +113,87 @@ __device__ __forceinline__ long long hash_get_from(const HashView& h, ull key, c
 __device__ __forceinline__ Slot hash_first(const HashView& h, ull key) { return h.slots[hash_home(key, h.cap)]; }
 
 // -------------------------------------------------------------------------
+// Table of per-(label, snapshot) sums (Sigma_{c,s}, K_{R,s}).  Dense rows of
+// T entries when labels x T fits the memory budget (one indexed load per
+// lookup, no hashing), the hash above otherwise.
+struct SigStore {
+  long long* d = nullptr;  // dense: rows x T, zero = absent
+  int64_t rows = 0;
+  int32_t T = 1;
+  HashView h{};
+};
+
+__device__ __forceinline__ long long ss_get(const SigStore& st, int32_t c, int32_t s) {
+  if (st.d) return st.d[(int64_t)c * st.T + s];
+  return hash_get(st.h, pack_cs(c, s));
+}
+
+__device__ __forceinline__ void ss_add(const SigStore& st, int32_t c, int32_t s, long long x) {
+  if (st.d)
+    atomicAdd((ull*)&st.d[(int64_t)c * st.T + s], (ull)x);
+  else
+    hash_add(st.h, pack_cs(c, s), x);
+}
+
+// First load of a lookup (issued early), and its resolution.
+__device__ __forceinline__ Slot ss_first(const SigStore& st, int32_t c, int32_t s) {
+  if (st.d) return Slot{pack_cs(c, s), st.d[(int64_t)c * st.T + s]};
+  return hash_first(st.h, pack_cs(c, s));
+}
+
+__device__ __forceinline__ long long ss_resolve(const SigStore& st, int32_t c, int32_t s, const Slot& first) {
+  if (st.d) return first.val;
+  return hash_get_from(st.h, pack_cs(c, s), first);
+}
+
+// The same lookups with the table kind fixed at compile time (the decision
+// kernels are instantiated for both kinds, keeping register use low).
+template <bool DENSE>
+__device__ __forceinline__ long long sst_get(const SigStore& st, int32_t c, int32_t s) {
+  if constexpr (DENSE)
+    return st.d[(int64_t)c * st.T + s];
+  else
+    return hash_get(st.h, pack_cs(c, s));
+}
+
+template <bool DENSE>
+__device__ __forceinline__ Slot sst_first(const SigStore& st, int32_t c, int32_t s) {
+  if constexpr (DENSE)
+    return Slot{0, st.d[(int64_t)c * st.T + s]};
+  else
+    return hash_first(st.h, pack_cs(c, s));
+}
+
+template <bool DENSE>
+__device__ __forceinline__ long long sst_resolve(const SigStore& st, int32_t c, int32_t s, const Slot& first) {
+  if constexpr (DENSE)
+    return first.val;
+  else
+    return hash_get_from(st.h, pack_cs(c, s), first);
+}
+
+// Enumeration of the non-zero entries: index i in [0, ss_span).
+__device__ __forceinline__ uint64_t ss_span(const SigStore& st) {
+  return st.d ? (uint64_t)st.rows * (uint64_t)st.T : st.h.cap;
+}
+
+__device__ __forceinline__ bool ss_entry(const SigStore& st, uint64_t i, int32_t& c, int32_t& s, long long& v) {
+  if (st.d) {
+    v = st.d[i];
+    if (v == 0) return false;
+    c = (int32_t)(i / (uint64_t)st.T);
+    s = (int32_t)(i % (uint64_t)st.T);
+    return true;
+  }
+  const Slot sl = st.h.slots[i];
+  if (sl.key == EMPTY_KEY || sl.val == 0) return false;
+  c = (int32_t)(sl.key >> 32);
+  s = (int32_t)(sl.key & 0xffffffffu);
+  v = sl.val;
+  return true;
+}
+
+// -------------------------------------------------------------------------
 // Unsigned 128-bit accumulation into two 64-bit words with carry propagation.
 // Exact as long as the true sum stays below 2^128.
 __device__ __forceinline__ void atomic_add_u128(ull* lohi, u128 x) {

@@ -16,7 +16,7 @@
 // length is read on the device (no host round trip):
 //   tier 0  deg <= 16    4-lane groups, eight nodes per warp, 32-slot tables
 //   tier 1  deg <= 32    8-lane groups, four nodes per warp, 64-slot tables
-//   tier 2  deg <= 128   one warp per node, 256-slot table
+//   tier 2  deg <= 256   one warp per node, 512-slot table
 //   tier 3  deg <= 1024  one 256-thread block per node, shared table of
 //                        2*deg slots rounded up to a power of two
 //   tier 4  larger       one block per node, table in global scratch
@@ -44,15 +44,19 @@ namespace mslice {
 #ifndef MSLICE_GROUP_MIN_BLOCKS
 #define MSLICE_GROUP_MIN_BLOCKS 4
 #endif
+// entries loaded per lane per round by the warp-per-node tier
+#ifndef MSLICE_T2_EPL
+#define MSLICE_T2_EPL 2
+#endif
 
 constexpr int NTIERS = 5;
-constexpr int TIER_MAX[NTIERS - 1] = {16, 32, 128, 1024};
+constexpr int TIER_MAX[NTIERS - 1] = {16, 32, 256, 1024};
 constexpr int TIER3_BITS = 11;  // 2 * 1024 slots
 constexpr int BLOCK_THREADS = 256;
 constexpr int GROUP_THREADS = 256;
 
 __host__ __device__ __forceinline__ int degree_tier(int64_t d) {
-  return d <= 16 ? 0 : (d <= 32 ? 1 : (d <= 128 ? 2 : (d <= 1024 ? 3 : 4)));
+  return d <= 16 ? 0 : (d <= 32 ? 1 : (d <= 256 ? 2 : (d <= 1024 ? 3 : 4)));
 }
 
 __device__ __forceinline__ uint32_t small_hash(int32_t key, int bits) {
@@ -125,15 +129,16 @@ __device__ __forceinline__ int table_add_slot(int32_t* hk, long long* hv, int bi
   return -1;
 }
 
-// Tiers 0-2: G lanes per node, EPL entries per lane (deg <= G*EPL), 2^BITS
-// table slots per group in shared memory.  The distinct keys of a node are
+// Tiers 0-2: G lanes per node, entries loaded EPL per lane at a time
+// (deg <= 2^BITS / 2), 2^BITS table slots per group in shared memory.  The distinct keys of a node are
 // listed as their slots are claimed, so scoring touches only real
 // candidates and only those slots are reset afterwards (the table is cleared
 // once per block, not once per node).
 template <class Pol, int G, int BITS, int EPL>
 __global__ void __launch_bounds__(GROUP_THREADS, MSLICE_GROUP_MIN_BLOCKS)
     k_decide_groups(Pol pol, const int32_t* list, const int32_t* count_ptr) {
-  constexpr int WARPS = GROUP_THREADS / 32, GPW = 32 / G, SLOTS = 1 << BITS, MAXC = G * EPL;
+  constexpr int WARPS = GROUP_THREADS / 32, GPW = 32 / G, SLOTS = 1 << BITS, MAXC = SLOTS / 2;
+  constexpr bool ONE_CHUNK = MAXC <= G * EPL;  // every row fits one load round
   constexpr int NG = WARPS * GPW;
   __shared__ int32_t hk[NG][SLOTS];
   __shared__ long long hv[NG][SLOTS];
@@ -165,25 +170,34 @@ __global__ void __launch_bounds__(GROUP_THREADS, MSLICE_GROUP_MIN_BLOCKS)
     int64_t nbeg = 0, nend = 0;
     if (pol.begin(v)) {
       const typename Pol::VCtx vc = pol.vctx(v);
-      int32_t keys[EPL];
-      long long ws[EPL];
-      bool ok[EPL];
+      // one load round: all of a lane's entries (and gathers) in flight
+      // before any insert
+      auto load_insert = [&](int64_t base) {
+        int32_t keys[EPL];
+        long long ws[EPL];
+        bool ok[EPL];
 #pragma unroll
-      for (int j = 0; j < EPL; ++j) {
-        const int64_t e = beg + j * G + gl;
-        ok[j] = e < end && pol.edge(v, e, keys[j], ws[j]);
+        for (int j = 0; j < EPL; ++j) {
+          const int64_t e = base + j * G + gl;
+          ok[j] = e < end && pol.edge(v, e, keys[j], ws[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < EPL; ++j) {
+          if (ok[j]) {
+            bool fresh;
+            const int slot = table_add_slot(K, V, BITS, keys[j], ws[j], fresh);
+            if (fresh) CL[atomicAdd(&ncand[gx], 1)] = (uint16_t)slot;
+          }
+        }
+      };
+      if constexpr (ONE_CHUNK) {
+        load_insert(beg);
+      } else {
+        for (int64_t base = beg; base < end; base += G * EPL) load_insert(base);
       }
       if (more) {
         nbeg = pol.g.rowptr[nv];
         nend = pol.g.rowptr[nv + 1];
-      }
-#pragma unroll
-      for (int j = 0; j < EPL; ++j) {
-        if (ok[j]) {
-          bool fresh;
-          const int slot = table_add_slot(K, V, BITS, keys[j], ws[j], fresh);
-          if (fresh) CL[atomicAdd(&ncand[gx], 1)] = (uint16_t)slot;
-        }
       }
       __syncwarp(gmask);
       const int n = ncand[gx];
@@ -247,15 +261,24 @@ __device__ __forceinline__ Cand score_range(const Pol& pol, int32_t v, const typ
   return c;
 }
 
-// Tier 3: one block per node, shared table of 2*deg (rounded up) slots.
+// Tier 3: one block per node, shared table of 2*deg (rounded up) slots; the
+// node's distinct keys are listed as their slots are claimed.
 template <class Pol>
 __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_block(Pol pol, const int32_t* list, const int32_t* count_ptr) {
   constexpr int SLOTS = 1 << TIER3_BITS;
   __shared__ int32_t hk[SLOTS];
   __shared__ long long hv[SLOTS];
+  __shared__ uint16_t cl[SLOTS / 2];
+  __shared__ int32_t ncand;
   __shared__ Cand red[BLOCK_THREADS / 32];
   __shared__ i128 own_sm;
   const int count = *count_ptr;
+  for (int i = threadIdx.x; i < SLOTS; i += BLOCK_THREADS) {
+    hk[i] = -1;
+    hv[i] = 0;
+  }
+  if (threadIdx.x == 0) ncand = 0;
+  __syncthreads();
   for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
     const int32_t v = list[idx];
     if (!pol.begin(v)) {
@@ -265,25 +288,40 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_block(Pol pol, const i
     const typename Pol::VCtx vc = pol.vctx(v);
     const int64_t beg = pol.g.rowptr[v], end = pol.g.rowptr[v + 1];
     const int bits = table_bits_for_degree(end - beg);
-    const int S = 1 << bits;
-    for (int i = threadIdx.x; i < S; i += BLOCK_THREADS) {
-      hk[i] = -1;
-      hv[i] = 0;
-    }
-    __syncthreads();
     for (int64_t e = beg + threadIdx.x; e < end; e += BLOCK_THREADS) {
       int32_t key;
       long long w;
-      if (pol.edge(v, e, key, w)) table_add(hk, hv, bits, key, w);
+      if (pol.edge(v, e, key, w)) {
+        bool fresh;
+        const int slot = table_add_slot(hk, hv, bits, key, w, fresh);
+        if (fresh) cl[atomicAdd(&ncand, 1)] = (uint16_t)slot;
+      }
     }
     __syncthreads();
+    const int n = ncand;
     const int32_t own = pol.own_key(v);
+    Cand c{0, INT32_MAX};
+    for (int j = threadIdx.x; j < n; j += BLOCK_THREADS) {
+      const int slot = cl[j];
+      const int32_t k = hk[slot];
+      if (k != own) {
+        const Cand x = pol.cand(v, vc, k, hv[slot], pol.probe(v, vc, k));
+        if (better(x, c)) c = x;
+      }
+    }
     if (threadIdx.x == 0) own_sm = pol.own(v, vc, table_get(hk, hv, bits, own));
-    const Cand best = block_best<BLOCK_THREADS / 32>(score_range(pol, v, vc, own, hk, hv, S), red);
+    const Cand best = block_best<BLOCK_THREADS / 32>(c, red);
     if (threadIdx.x == 0) {
       const long long Wb = best.label != INT32_MAX ? table_get(hk, hv, bits, best.label) : 0;
       pol.finish(v, best, Wb, own_sm, vc);
     }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += BLOCK_THREADS) {
+      const int slot = cl[j];
+      hk[slot] = -1;
+      hv[slot] = 0;
+    }
+    if (threadIdx.x == 0) ncand = 0;
     __syncthreads();
   }
 }
@@ -361,7 +399,8 @@ void decide_all(Ctx& c, const Pol& pol, const TierSegs& sg, const int32_t* tier_
   if (tier_cnt[1] > 0)
     launch(c, k_decide_groups<Pol, 8, 6, 4>, dim3(152 * 4), dim3(GROUP_THREADS), 0, pol, sg.list[1], sg.count[1]);
   if (tier_cnt[2] > 0)
-    launch(c, k_decide_groups<Pol, 32, 8, 4>, dim3(152 * 4), dim3(GROUP_THREADS), 0, pol, sg.list[2], sg.count[2]);
+    launch(c, k_decide_groups<Pol, 32, 9, MSLICE_T2_EPL>, dim3(152 * 4), dim3(GROUP_THREADS), 0, pol, sg.list[2],
+           sg.count[2]);
   if (tier_cnt[3] > 0)
     launch(c, k_decide_block<Pol>, dim3(152 * 4), dim3(BLOCK_THREADS), 0, pol, sg.list[3], sg.count[3]);
   if (tier_cnt[4] > 0)

@@ -21,6 +21,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 
 #include "decide.cuh"
@@ -90,7 +91,7 @@ __global__ void k_hash_clear(Slot* slots, uint64_t cap) {
     slots[i] = Slot{EMPTY_KEY, 0};
 }
 
-__global__ void k_sigma_insert(LevelDev g, const int32_t* labels, HashView h, int32_t* size) {
+__global__ void k_sigma_insert(LevelDev g, const int32_t* labels, SigStore h, int32_t* size) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += (int64_t)gridDim.x * blockDim.x) {
     const int32_t c = labels[v];
     if (size) atomicAdd(&size[c], 1);
@@ -100,13 +101,14 @@ __global__ void k_sigma_insert(LevelDev g, const int32_t* labels, HashView h, in
       int32_t s;
       long long k;
       slice_entry(g, (int32_t)v, j, s, k);
-      hash_add(h, pack_cs(c, s), k);
+      ss_add(h, c, s, k);
     }
   }
 }
 
 // sum_s Lambda_s k_{v,s} (X_s - self*k_{v,s}) with X_s = table(c, s).
-__device__ __forceinline__ u128 null_sum(const LevelDev& g, const u128* lam, const HashView& h, int32_t v, int32_t c,
+template <bool DENSE>
+__device__ __forceinline__ u128 null_sum(const LevelDev& g, const u128* lam, const SigStore& h, int32_t v, int32_t c,
                                          bool self) {
   int64_t b, e;
   slice_range(g, v, b, e);
@@ -115,18 +117,19 @@ __device__ __forceinline__ u128 null_sum(const LevelDev& g, const u128* lam, con
     int32_t s;
     long long k;
     slice_entry(g, v, j, s, k);
-    long long x = hash_get(h, pack_cs(c, s));
+    long long x = sst_get<DENSE>(h, c, s);
     if (self) x -= k;
     t += lam[s] * (u128)(ull)k * (u128)(ull)x;
   }
   return t;
 }
 
+template <bool DENSE>
 struct LMPolicy {
   LevelDev g;
   const int32_t* labels;
   const int32_t* size;
-  HashView sig;
+  SigStore sig;
   const u128* lam;
   int32_t* target;
   long long od;
@@ -167,23 +170,23 @@ struct LMPolicy {
   }
   __device__ int32_t own_key(int32_t v) const { return labels[v]; }
   __device__ i128 key_of(int32_t v, int32_t c, long long W, bool self) const {
-    const u128 ns = null_sum(g, lam, sig, v, c, self);
+    const u128 ns = null_sum<DENSE>(g, lam, sig, v, c, self);
     return (((i128)W) << P_BITS) - (i128)((u128)(ull)od * ns);
   }
   __device__ Probe probe(int32_t, const VCtx& vc, int32_t c) const {
-    if (vc.single && vc.k > 0) return hash_first(sig, pack_cs(c, vc.s));
+    if (vc.single && vc.k > 0) return sst_first<DENSE>(sig, c, vc.s);
     return Slot{EMPTY_KEY, 0};
   }
   __device__ Cand cand(int32_t v, const VCtx& vc, int32_t c, long long W, const Probe& pr) const {
     if (vc.single) {
-      const long long x = vc.k > 0 ? hash_get_from(sig, pack_cs(c, vc.s), pr) : 0;
+      const long long x = vc.k > 0 ? sst_resolve<DENSE>(sig, c, vc.s, pr) : 0;
       return Cand{(((i128)W) << P_BITS) - (i128)(vc.A * (u128)(ull)x), c};
     }
     return Cand{key_of(v, c, W, false), c};
   }
   __device__ i128 own(int32_t v, const VCtx& vc, long long Wown) const {
     if (vc.single) {
-      const long long x = vc.k > 0 ? hash_get(sig, pack_cs(vc.a, vc.s)) - vc.k : 0;
+      const long long x = vc.k > 0 ? sst_get<DENSE>(sig, vc.a, vc.s) - vc.k : 0;
       return (((i128)Wown) << P_BITS) - (i128)(vc.A * (u128)(ull)x);
     }
     return key_of(v, vc.a, Wown, true);
@@ -227,7 +230,7 @@ __device__ __forceinline__ int seg_total(const Segs& sg) {
 // Applies the sub-round's decisions: labels, community sizes and Sigma, and
 // resets each applied decision.  Moves to an empty community only leave here
 // (their label is assigned by k_empty_pass).
-__global__ void k_lm_apply(LevelDev g, Segs sg, int32_t* labels, int32_t* size, HashView sig, int32_t* target,
+__global__ void k_lm_apply(LevelDev g, Segs sg, int32_t* labels, int32_t* size, SigStore sig, int32_t* target,
                            int32_t* counters) {
   const int total = seg_total(sg);
   int local = 0, local_empty = 0;
@@ -245,8 +248,8 @@ __global__ void k_lm_apply(LevelDev g, Segs sg, int32_t* labels, int32_t* size, 
       int32_t s;
       long long k;
       slice_entry(g, v, j, s, k);
-      hash_add(sig, pack_cs(a, s), -k);
-      if (t >= 0) hash_add(sig, pack_cs(t, s), k);
+      ss_add(sig, a, s, -k);
+      if (t >= 0) ss_add(sig, t, s, k);
     }
     if (t >= 0) {
       atomicAdd(&size[t], 1);
@@ -300,7 +303,7 @@ __device__ __forceinline__ T block_scan_excl(T x, T* sm, T& total) {
 // ascending labels that are free once every other move is applied and the
 // movers have left.  blk: 2*gridDim.x ints.
 __global__ void __launch_bounds__(EMPTY_THREADS) k_empty_pass(LevelDev g, int32_t* target, int32_t* labels,
-                                                              int32_t* size, HashView sig, int32_t* counters,
+                                                              int32_t* size, SigStore sig, int32_t* counters,
                                                               int32_t* blk, int32_t* freelist) {
   const int n_empty = counters[2];
   if (n_empty == 0) return;
@@ -357,7 +360,7 @@ __global__ void __launch_bounds__(EMPTY_THREADS) k_empty_pass(LevelDev g, int32_
         int32_t s;
         long long k;
         slice_entry(g, (int32_t)v, j, s, k);
-        hash_add(sig, pack_cs(L, s), k);
+        ss_add(sig, L, s, k);
       }
       target[v] = NO_MOVE;
     }
@@ -408,11 +411,7 @@ void solver_alloc(Solver& S) {
   S.rhs = c.ws->get<ull>("s_rhs", 2 * N);
   S.elig = c.ws->get<uint8_t>("s_elig", N);
   S.wc = c.ws->get<uint8_t>("s_wc", N);
-  // hash tables keyed by (label, snapshot): at most one live key per
-  // (node, snapshot) entry; a rebuild is triggered when taken slots pass half
-  const uint64_t cap = (uint64_t)(2 * N + 2 * ((N + S.p.K - 1) / S.p.K) + 64);
-  S.sig = HashView{c.ws->get<Slot>("s_sig", cap), cap, c.d_status, S.sig_used};
-  S.kr = HashView{c.ws->get<Slot>("s_kr", cap), cap, c.d_status, nullptr};
+  configure_stores(S, S.N0);
   int max_blocks = 0;
   check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_blocks, k_empty_pass, EMPTY_THREADS, 0), "occupancy");
   int dev = 0, sms = 0;
@@ -427,6 +426,7 @@ void solver_alloc(Solver& S) {
 void prepare_level(Solver& S, const Level& L) {
   Ctx& c = *S.c;
   const int32_t N = L.d.N;
+  configure_stores(S, N);
   int32_t* cnt = S.cursors;  // reused: tier counts
   check_cuda(cudaMemsetAsync(cnt, 0, NTIERS * sizeof(int32_t), c.stream), "memset");
   int64_t* gsize = reinterpret_cast<int64_t*>(c.ws->get<int64_t>("s_gsize", (size_t)(N > 0 ? N : 1)));
@@ -457,13 +457,59 @@ void prepare_level(Solver& S, const Level& L) {
   }
 }
 
+void configure_stores(Solver& S, int64_t N) {
+  Ctx& c = *S.c;
+  const int64_t T = S.G0 ? S.G0->T : 1;
+  if (!S.sig_h.slots) {
+    // hash tables keyed by (label, snapshot), sized for level 0: at most one
+    // live key per (node, snapshot) entry plus the keys created by one round
+    // of moves; a rebuild is triggered when taken slots pass half
+    const int64_t N0 = S.N0 > 0 ? S.N0 : 1;
+    const uint64_t cap = (uint64_t)(2 * N0 + 2 * ((N0 + S.p.K - 1) / S.p.K) + 64);
+    S.sig_h = HashView{nullptr, cap, c.d_status, S.sig_used};
+    S.kr_h = HashView{nullptr, cap, c.d_status, nullptr};
+  }
+  S.sig = SigStore{};
+  S.kr = SigStore{};
+  S.sig.T = S.kr.T = (int32_t)T;
+  const int64_t need = (N > 0 ? N : 1) * T;
+  int64_t limit = DENSE_LIMIT;
+  if (const char* e = std::getenv("MSLICE_DENSE_LIMIT")) limit = std::atoll(e);
+  if (need <= limit) {
+    if (need > S.dense_cap) {
+      S.sig_d = c.ws->get<long long>("s_sig_d", need);
+      S.kr_d = c.ws->get<long long>("s_kr_d", need);
+      S.dense_cap = need;
+    }
+    S.sig.d = S.sig_d;
+    S.kr.d = S.kr_d;
+    S.sig.rows = S.kr.rows = (N > 0 ? N : 1);
+  } else {
+    if (!S.sig_h.slots) {
+      S.sig_h.slots = c.ws->get<Slot>("s_sig", S.sig_h.cap);
+      S.kr_h.slots = c.ws->get<Slot>("s_kr", S.kr_h.cap);
+    }
+    S.sig.h = S.sig_h;
+    S.kr.h = S.kr_h;
+  }
+}
+
+// Empties a store (dense rows zeroed, hash slots freed).
+void clear_store(Solver& S, const SigStore& st) {
+  Ctx& c = *S.c;
+  if (st.d)
+    check_cuda(cudaMemsetAsync(st.d, 0, (size_t)st.rows * st.T * sizeof(long long), c.stream), "memset");
+  else
+    launch(c, k_hash_clear, dim3(fixed_grid(8)), dim3(256), 0, st.h.slots, st.h.cap);
+}
+
 // Sigma (and, optionally, the community sizes) from the labels.
 static void rebuild_sigma(Solver& S, const Level& L, const int32_t* labels, bool sizes) {
   Ctx& c = *S.c;
   const int32_t N = L.d.N;
   if (sizes) check_cuda(cudaMemsetAsync(S.size, 0, (N > 0 ? N : 1) * sizeof(int32_t), c.stream), "memset");
   if (S.sig_used) check_cuda(cudaMemsetAsync(S.sig_used, 0, sizeof(ull), c.stream), "memset");
-  launch(c, k_hash_clear, dim3(fixed_grid(8)), dim3(256), 0, S.sig.slots, S.sig.cap);
+  clear_store(S, S.sig);
   if (N > 0)
     launch(c, k_sigma_insert, dim3(grid_for(N, 256)), dim3(256), 0, L.d, labels, S.sig, sizes ? S.size : nullptr);
 }
@@ -505,7 +551,7 @@ MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, 
   // reads Sigma even when no round runs)
   rebuild_sigma(S, L, labels, true);
   if (max_rounds <= 0) return out;
-  LMPolicy pol;
+  LMPolicy<true> pol;
   pol.g = L.d;
   pol.labels = labels;
   pol.size = S.size;
@@ -513,6 +559,20 @@ MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, 
   pol.lam = S.lam;
   pol.target = S.target;
   pol.od = S.p.od;
+  LMPolicy<false> polh;
+  polh.g = pol.g;
+  polh.labels = pol.labels;
+  polh.size = pol.size;
+  polh.sig = pol.sig;
+  polh.lam = pol.lam;
+  polh.target = pol.target;
+  polh.od = pol.od;
+  auto decide = [&](const TierSegs& sg) {
+    if (S.sig.d)
+      decide_all(c, pol, sg, S.tier_cnt, S.gkeys, S.gvals, S.goff);
+    else
+      decide_all(c, polh, sg, S.tier_cnt, S.gkeys, S.gvals, S.goff);
+  };
   bool rebuild = false;
   for (int r = 0; r < max_rounds; ++r) {
     if (rebuild) rebuild_sigma(S, L, labels, false);
@@ -528,11 +588,11 @@ MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, 
         check_cuda(cudaEventCreate(&e0), "event");
         check_cuda(cudaEventCreate(&e1), "event");
         check_cuda(cudaEventRecord(e0, c.stream), "event");
-        decide_all(c, pol, sg, S.tier_cnt, S.gkeys, S.gvals, S.goff);
+        decide(sg);
         check_cuda(cudaEventRecord(e1, c.stream), "event");
         c.prof_spans->push_back({e0, e1});
       } else {
-        decide_all(c, pol, sg, S.tier_cnt, S.gkeys, S.gvals, S.goff);
+        decide(sg);
       }
       launch(c, k_lm_apply, dim3(fixed_grid(4)), dim3(APPLY_THREADS), 0, L.d, sg, labels, S.size, S.sig, S.target,
              S.counters);
@@ -549,7 +609,7 @@ MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, 
     sync(c);
     std::memcpy(&rb, c.pinned, sizeof(rb));
     check_status(c, "local moving");
-    rebuild = rb.used * 2 > S.sig.cap;
+    rebuild = !S.sig.d && rb.used * 2 > S.sig.h.cap;
     out.rounds++;
     out.moves += rb.moved;
     if (rb.moved == 0) break;

@@ -43,18 +43,19 @@ __global__ void k_IJ(LevelDev g, const int32_t* labels, ull* IJ) {
 
 // S_s += Sigma_{c,s}^2 over the table; per-block partial sums in shared
 // memory when T is small enough, global 128-bit atomics otherwise.
-__global__ void k_S(HashView h, int32_t T, ull* S) {
+__global__ void k_S(SigStore h, int32_t T, ull* S) {
   extern __shared__ ull sm[];  // 2*T words when used
   const bool use_sm = T <= 1024;
   if (use_sm) {
     for (int i = threadIdx.x; i < 2 * T; i += blockDim.x) sm[i] = 0;
     __syncthreads();
   }
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < h.cap; i += (uint64_t)gridDim.x * blockDim.x) {
-    const Slot sl = h.slots[i];
-    if (sl.key == EMPTY_KEY || sl.val == 0) continue;
-    const int32_t s = (int32_t)(sl.key & 0xffffffffu);
-    const u128 sq = (u128)(ull)sl.val * (u128)(ull)sl.val;
+  const uint64_t span = ss_span(h);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < span; i += (uint64_t)gridDim.x * blockDim.x) {
+    int32_t cc, s;
+    long long val;
+    if (!ss_entry(h, i, cc, s, val)) continue;
+    const u128 sq = (u128)(ull)val * (u128)(ull)val;
     if (use_sm)
       atomic_add_u128(&sm[2 * s], sq);
     else
@@ -137,13 +138,15 @@ void modularity(Solver& S, const int32_t* labels0, double* Q) {
   Ctx& c = *S.c;
   const SupraGraph& G = *S.G0;
   const LevelDev g = level0_view(G, S.p.on, S.p.od);
+  configure_stores(S, G.N);
   sigma_rebuild(S, Level{g}, labels0);
   ull* acc = c.ws->get<ull>("q_acc", 2 + 2 * (size_t)G.T);
   double* dQ = c.ws->get<double>("q_out", 1);
   check_cuda(cudaMemsetAsync(acc, 0, (2 + 2 * (size_t)G.T) * sizeof(ull), c.stream), "memset");
   if (G.N > 0) launch(c, k_IJ, dim3(gsz(G.N * 32)), dim3(256), 0, g, labels0, acc);
   const size_t smem = G.T <= 1024 ? 2 * (size_t)G.T * sizeof(ull) : 0;
-  launch(c, k_S, dim3(gsz((int64_t)S.sig.cap)), dim3(256), smem, S.sig, G.T, acc + 2);
+  const int64_t span = S.sig.d ? S.sig.rows * S.sig.T : (int64_t)S.sig.h.cap;
+  launch(c, k_S, dim3(gsz(span)), dim3(256), smem, S.sig, G.T, acc + 2);
   launch(c, k_Q, dim3(1), dim3(1), 0, (const ull*)acc, (const ull*)(acc + 2), (const int64_t*)G.two_m, G.T, G.n,
          S.p.gn, S.p.gd, S.p.on, S.p.od, dQ);
   *Q = *static_cast<const double*>(readback(c, dQ, sizeof(double)));

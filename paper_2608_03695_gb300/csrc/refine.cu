@@ -28,8 +28,8 @@ __device__ __forceinline__ u128 lam_k_x(const u128* lam, int32_t s, long long k,
 }
 
 // Per node: W(v,C\v), eligibility, initial sub-community state.
-__global__ void k_ref_init(LevelDev g, const int32_t* P, HashView sig, const u128* lam, long long od, int32_t* R,
-                           int32_t* sizeR, long long* Wc, long long* Wout, uint8_t* elig, HashView kr) {
+__global__ void k_ref_init(LevelDev g, const int32_t* P, SigStore sig, const u128* lam, long long od, int32_t* R,
+                           int32_t* sizeR, long long* Wc, long long* Wout, uint8_t* elig, SigStore kr) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t v = (((int64_t)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); v < g.N; v += warps) {
@@ -53,8 +53,8 @@ __global__ void k_ref_init(LevelDev g, const int32_t* P, HashView sig, const u12
         int32_t s;
         long long k;
         slice_entry(g, (int32_t)v, j, s, k);
-        rhs += lam_k_x(lam, s, k, hash_get(sig, pack_cs(C, s)) - k);
-        hash_add(kr, pack_cs((int32_t)v, s), k);
+        rhs += lam_k_x(lam, s, k, ss_get(sig, C, s) - k);
+        ss_add(kr, (int32_t)v, s, k);
       }
       elig[v] = ((((i128)w) << P_BITS) - (i128)((u128)(ull)od * rhs)) >= 0 ? 1 : 0;
     }
@@ -66,11 +66,6 @@ __global__ void k_classes(int32_t N, uint64_t seed, uint64_t it, uint64_t lvl, i
     cls[v] = (uint8_t)vertex_class(seed, 1, it, lvl, 0, (uint64_t)v, K);
 }
 
-__global__ void k_hash_clear2(Slot* slots, uint64_t cap) {
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += (uint64_t)gridDim.x * blockDim.x)
-    slots[i] = Slot{EMPTY_KEY, 0};
-}
-
 __global__ void k_zero_rhs(ull* rhs, int64_t n2) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x)
     rhs[i] = 0;
@@ -78,16 +73,16 @@ __global__ void k_zero_rhs(ull* rhs, int64_t n2) {
 
 // sum_s Lambda_s K_{R,s} (K_{C,s} - K_{R,s}) for every sub-community with
 // more than one node (singletons reuse their eligibility).
-__global__ void k_rhs_accum(HashView kr, const int32_t* sizeR, const int32_t* P, HashView sig, const u128* lam,
+__global__ void k_rhs_accum(SigStore kr, const int32_t* sizeR, const int32_t* P, SigStore sig, const u128* lam,
                             ull* rhs) {
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < kr.cap; i += (uint64_t)gridDim.x * blockDim.x) {
-    const Slot sl = kr.slots[i];
-    if (sl.key == EMPTY_KEY || sl.val == 0) continue;
-    const int32_t Rl = (int32_t)(sl.key >> 32);
-    const int32_t s = (int32_t)(sl.key & 0xffffffffu);
+  const uint64_t span = ss_span(kr);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < span; i += (uint64_t)gridDim.x * blockDim.x) {
+    int32_t Rl, s;
+    long long K;
+    if (!ss_entry(kr, i, Rl, s, K)) continue;
     if (sizeR[Rl] <= 1) continue;
-    const long long KC = hash_get(sig, pack_cs(P[Rl], s));
-    atomic_add_u128(&rhs[2 * (int64_t)Rl], lam_k_x(lam, s, sl.val, KC - sl.val));
+    const long long KC = ss_get(sig, P[Rl], s);
+    atomic_add_u128(&rhs[2 * (int64_t)Rl], lam_k_x(lam, s, K, KC - K));
   }
 }
 
@@ -106,6 +101,7 @@ __global__ void k_wc(int32_t N, const int32_t* sizeR, const long long* Wout, con
   }
 }
 
+template <bool DENSE>
 struct RefPolicy {
   LevelDev g;
   const int32_t* P;
@@ -114,7 +110,7 @@ struct RefPolicy {
   const uint8_t* elig;
   const uint8_t* wc;
   const uint8_t* cls;
-  HashView kr;
+  SigStore kr;
   const u128* lam;
   int32_t* target;
   long long* Wsel;
@@ -163,7 +159,7 @@ struct RefPolicy {
     p.size = sizeR[X];
     p.cls = cls[X];
     p.wc = wc[X];
-    p.first = (vc.single && vc.k > 0) ? hash_first(kr, pack_cs(X, vc.s)) : Slot{EMPTY_KEY, 0};
+    p.first = (vc.single && vc.k > 0) ? sst_first<DENSE>(kr, X, vc.s) : Slot{EMPTY_KEY, 0};
     return p;
   }
   // A singleton sub-community's label is its node, so cls[X] is the class of
@@ -173,7 +169,7 @@ struct RefPolicy {
     if (!p.wc) return Cand{0, INT32_MAX};
     i128 G;
     if (vc.single) {
-      const long long x = vc.k > 0 ? hash_get_from(kr, pack_cs(X, vc.s), p.first) : 0;
+      const long long x = vc.k > 0 ? sst_resolve<DENSE>(kr, X, vc.s, p.first) : 0;
       G = (((i128)W) << P_BITS) - (i128)(vc.A * (u128)(ull)x);
     } else {
       int64_t b, e;
@@ -183,7 +179,7 @@ struct RefPolicy {
         int32_t s;
         long long k;
         slice_entry(g, v, j, s, k);
-        ns += lam_k_x(lam, s, k, hash_get(kr, pack_cs(X, s)));
+        ns += lam_k_x(lam, s, k, sst_get<DENSE>(kr, X, s));
       }
       G = (((i128)W) << P_BITS) - (i128)((u128)(ull)od * ns);
     }
@@ -224,7 +220,7 @@ __device__ __forceinline__ bool seg3_item(const Segs3& sg, int64_t idx, int32_t&
 // One warp per active node: movers compute W(v, M_t \ v) over their edges to
 // other movers with the same target, then update sizes, K_{R,s} and W(R,C\R).
 __global__ void k_ref_apply(LevelDev g, Segs3 sg, const int32_t* P, const int32_t* target, const long long* Wc,
-                            const long long* Wsel, int32_t* R, int32_t* sizeR, long long* Wout, HashView kr) {
+                            const long long* Wsel, int32_t* R, int32_t* sizeR, long long* Wout, SigStore kr) {
   const int lane = threadIdx.x & 31;
   const int total = seg3_total(sg);
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -252,8 +248,8 @@ __global__ void k_ref_apply(LevelDev g, Segs3 sg, const int32_t* P, const int32_
         int32_t s;
         long long k;
         slice_entry(g, v, j, s, k);
-        hash_add(kr, pack_cs(v, s), -k);
-        hash_add(kr, pack_cs(t, s), k);
+        ss_add(kr, v, s, -k);
+        ss_add(kr, t, s, k);
       }
     }
   }
@@ -275,15 +271,16 @@ unsigned fixed_grid(int per_sm) { return 152u * (unsigned)per_sm; }
 void bucket(Solver& S, const Level& L, uint64_t tag, int it, int lvl, int r);
 TierSegs bucket_segments(Solver& S, int q);
 
-void refine(Solver& S, const Level& L, const int32_t* P, int it, int lvl) {
+template <bool DENSE>
+static void refine_impl(Solver& S, const Level& L, const int32_t* P, int it, int lvl) {
   Ctx& c = *S.c;
   const int32_t N = L.d.N;
   if (N == 0) return;
-  launch(c, k_hash_clear2, dim3(fixed_grid(8)), dim3(256), 0, S.kr.slots, S.kr.cap);
+  clear_store(S, S.kr);
   launch(c, k_ref_init, dim3(fixed_grid(8)), dim3(256), 0, L.d, P, S.sig, (const u128*)S.lam, S.p.od, S.R, S.sizeR,
          S.Wc, S.Wout, S.elig, S.kr);
   bucket(S, L, 1, it, lvl, 0);
-  RefPolicy pol;
+  RefPolicy<DENSE> pol;
   pol.g = L.d;
   pol.P = P;
   pol.R = S.R;
@@ -313,6 +310,13 @@ void refine(Solver& S, const Level& L, const int32_t* P, int it, int lvl) {
            (const long long*)S.Wc, (const long long*)S.Wsel, S.R, S.sizeR, S.Wout, S.kr);
     launch(c, k_ref_reset, dim3(fixed_grid(4)), dim3(256), 0, sg, S.target);
   }
+}
+
+void refine(Solver& S, const Level& L, const int32_t* P, int it, int lvl) {
+  if (S.kr.d)
+    refine_impl<true>(S, L, P, it, lvl);
+  else
+    refine_impl<false>(S, L, P, it, lvl);
 }
 
 }  // namespace mslice

@@ -39,8 +39,14 @@ struct Solver {
   long long* gvals = nullptr;
   int64_t gcap = 0;
 
-  // community slice sums Sigma_{c,s}
-  HashView sig{};
+  // community slice sums Sigma_{c,s} and sub-community sums K_{R,s} of the
+  // current level (dense or hashed, see configure_stores)
+  SigStore sig{};
+  SigStore kr{};
+  HashView sig_h{}, kr_h{};
+  long long* sig_d = nullptr;
+  long long* kr_d = nullptr;
+  int64_t dense_cap = 0;
   // refinement state
   int32_t* R = nullptr;
   int32_t* sizeR = nullptr;
@@ -50,7 +56,6 @@ struct Solver {
   ull* rhs = nullptr;  // 2 words per node
   uint8_t* elig = nullptr;
   uint8_t* wc = nullptr;
-  HashView kr{};
 
   int32_t tier_off[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int32_t tier_cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -60,6 +65,16 @@ struct Solver {
 };
 
 void solver_alloc(Solver& S);
+
+// Dense Sigma/K tables are used while labels x T stays within this many
+// entries per table (the environment variable MSLICE_DENSE_LIMIT overrides
+// it; 0 forces the hashed tables).
+constexpr int64_t DENSE_LIMIT = (int64_t)1 << 27;
+
+// Points sig/kr at dense rows (allocated on demand) or the hash tables for a
+// level of N nodes.
+void configure_stores(Solver& S, int64_t N);
+void clear_store(Solver& S, const SigStore& st);
 
 // Degree tiers, global-tier scratch; once per level.
 void prepare_level(Solver& S, const Level& L);

@@ -233,3 +233,28 @@ def test_invalid_inputs_rejected():
         with pytest.raises(pkg.MsliceError) as e:
             h.mslice_leiden(omega=(1, 2 ** 31))
         assert e.value.code == pkg.MSLICE_EOVERFLOW
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_hashed_tables_path(seed, monkeypatch):
+    """The hashed (label, snapshot) tables used when labels x T exceeds the
+    dense budget give the same bits as the dense rows."""
+    monkeypatch.setenv("MSLICE_DENSE_LIMIT", "0")
+    rng = np.random.default_rng(40 + seed)
+    T = int(rng.integers(1, 6))
+    snaps, _ = synth.planted_partition_temporal(int(rng.integers(30, 200)), T, n_blocks=3, p_in=0.2, p_out=0.02,
+                                                switch_frac=0.1, w_max=5, seed=seed)
+    gamma = [(1, 1), (3, 2), (2, 1)][seed % 3]
+    omega = [(1, 1), (1, 10), (0, 1)][seed % 3]
+    g, o = solve_both(snaps, gamma, omega, K=[4, 2, 3][seed % 3], seed=seed)
+    assert_same(g, o)
+    if seed == 0:
+        g, o = solve_both(snaps, gamma, omega, stop_level=1, stop_stage=3)
+        assert np.array_equal(g[0], o[0]) and g[2]["next_checksum"] == o[2]["next_checksum"]
+
+
+def test_hashed_tables_medium(monkeypatch):
+    monkeypatch.setenv("MSLICE_DENSE_LIMIT", "0")
+    snaps = synth.config_graph({**synth.CONFIGS[2], "n": 6000, "T": 5})
+    g, o = solve_both(snaps)
+    assert_same(g, o)
