@@ -29,8 +29,8 @@ MSLICE_ORDINAL = 0
 
 # every symbol include/mslice.h declares
 EXPORTS = ["mslice_default_opts", "mslice_build", "mslice_build_ex", "mslice_leiden", "mslice_leiden_ex",
-           "mslice_modularity", "mslice_modularity_ex", "mslice_info", "mslice_kernel_launches", "mslice_free",
-           "mslice_last_error"]
+           "mslice_modularity", "mslice_modularity_ex", "mslice_modularity_noalloc", "mslice_info",
+           "mslice_kernel_launches", "mslice_free", "mslice_last_error"]
 
 
 class LibraryMissing(RuntimeError):
@@ -88,6 +88,7 @@ def lib():
         L.mslice_leiden_ex.argtypes = [P, P, P, P, P, P]
         L.mslice_modularity.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, P]
         L.mslice_modularity_ex.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int32, P]
+        L.mslice_modularity_noalloc.argtypes = [P, C.c_int32, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, P, P]
         L.mslice_info.argtypes = [P, P, P, P, P]
         L.mslice_kernel_launches.argtypes = [P]
         L.mslice_kernel_launches.restype = C.c_int64
