@@ -67,9 +67,11 @@ struct Solver {
 void solver_alloc(Solver& S);
 
 // Dense Sigma/K tables are used while labels x T stays within this many
-// entries per table (the environment variable MSLICE_DENSE_LIMIT overrides
-// it; 0 forces the hashed tables).
-constexpr int64_t DENSE_LIMIT = (int64_t)1 << 27;
+// entries per table (32 MB, so the table stays resident in L2 next to the
+// labels); larger levels use the hash, whose footprint follows the number of
+// (node, snapshot) entries instead.  The environment variable
+// MSLICE_DENSE_LIMIT overrides it; 0 forces the hashed tables.
+constexpr int64_t DENSE_LIMIT = (int64_t)1 << 22;
 
 // Points sig/kr at dense rows (allocated on demand) or the hash tables for a
 // level of N nodes.
