@@ -258,7 +258,7 @@ def main():
     traffic = decide_traffic()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (traffic if traffic is None else traffic), "peak_source": peak_kind,
-                "kernel": "local-moving decision (all tiers)",
+                "kernel": "local-moving decision, level-0 sub-round (all degree tiers)",
                 "launches": stp["decide_launches"], "bytes_per_launch": stp["decide_bytes"] / max(1, stp["decide_launches"]),
                 "ms_per_launch": stp["ms_decide"] / max(1, stp["decide_launches"])}
 

@@ -51,9 +51,9 @@ extern "C" {
 /* Input/output pointers are device pointers (build: the snapshot arrays;
  * leiden/modularity: labels). */
 #define MSLICE_DEVICE_PTRS 1
-/* leiden: time every local-moving decision kernel with CUDA events on the
- * handle's stream (fills ms_decide / decide_launches / decide_bytes; adds a
- * little host overhead per launch). */
+/* leiden: time the local-moving decision kernels of every level-0 round with
+ * CUDA events on the handle's stream, one span per sub-round (fills ms_decide
+ * / decide_launches / decide_bytes; adds a little host overhead). */
 #define MSLICE_PROFILE 2
 
 typedef struct {
@@ -108,8 +108,8 @@ typedef struct {
   double ms_refine;          /* ... refinement */
   double ms_aggregate;       /* ... aggregation */
   double ms_modularity;      /* ... Q evaluation */
-  double ms_decide;          /* MSLICE_PROFILE: summed durations of the local-moving decision kernels */
-  int64_t decide_launches;   /* MSLICE_PROFILE: number of those launches */
+  double ms_decide;          /* MSLICE_PROFILE: summed durations of the level-0 decision sub-rounds */
+  int64_t decide_launches;   /* MSLICE_PROFILE: number of those sub-rounds (all degree tiers of one) */
   int64_t decide_bytes;      /* MSLICE_PROFILE: algorithmic bytes those launches move, per round
                                 12 B per directed entry (column, weight, neighbour label) and 40 B
                                 per node (row pointer, own label, strength, decision, the own

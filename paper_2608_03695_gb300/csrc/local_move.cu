@@ -580,10 +580,11 @@ MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, 
     bucket(S, L, 0, it, lvl, r);
     S.lm_rounds++;
     S.lm_edges += L.nnz_eff;
-    if (c.profile) c.prof_bytes += 12 * L.nnz_eff + 40 * (int64_t)N;
+    const bool prof = c.profile && lvl == 0;
+    if (prof) c.prof_bytes += 12 * L.nnz_eff + 40 * (int64_t)N;
     for (int q = 0; q < S.p.K; ++q) {
       const Segs sg = bucket_segments(S, q);
-      if (c.profile) {
+      if (prof) {
         cudaEvent_t e0, e1;
         check_cuda(cudaEventCreate(&e0), "event");
         check_cuda(cudaEventCreate(&e1), "event");
