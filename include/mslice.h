@@ -184,6 +184,68 @@ int mslice_modularity_noalloc(const mslice_csr* slices, int32_t T, const int32_t
                               int64_t gamma_den, int64_t omega_num, int64_t omega_den, void* stream,
                               double* Q_out);
 
+/* ---- Batches: many (graph, gamma, omega) solves in one pass ----
+ *
+ * The paper applies the method to many snapshot windows and parameter
+ * choices (Sec. 4 sweeps gamma and omega; Sec. 5 notes that small graphs
+ * leave the GPU underused).  A batch solves B independent instances together:
+ * their supra-graphs are laid out one after another as the diagonal blocks of
+ * one graph, every kernel launch of the level loop covers all instances, and
+ * each instance keeps its own gamma, omega, snapshot masses and class hash
+ * (computed on instance-local node ids).  No edge joins two instances and an
+ * instance that has converged (all singletons, nothing merged, labels
+ * unchanged over an iteration) is frozen while the others continue, so every
+ * instance's labels and Q are bit-identical to those of mslice_leiden_ex on
+ * that graph alone with the same options, gamma and omega.
+ *
+ * The batch keeps a device copy of the concatenated graphs (rebuilt by
+ * mslice_batch_run only when the list of graphs changed) and solver scratch
+ * for all instances: about the sum of the graphs' handle memory plus
+ * ~120 bytes per supra-node.  The same graph may be added several times (a
+ * gamma/omega sweep). */
+typedef struct mslice_batch_s* mslice_batch;
+
+/* Empty batch on stream (cudaStream_t; NULL = default).  flags =
+ * MSLICE_DEVICE_PTRS when init_labels / labels_out of the calls below are
+ * device pointers.  Errors: EINVAL, ENOMEM, ECUDA. */
+int mslice_batch_create(int32_t flags, void* stream, mslice_batch* out);
+
+/* Appends the instance (graph g, gamma, omega).  g must stay alive until the
+ * next mslice_batch_run returns.  init_labels (nullable): warm start,
+ * int32[N_g] in [0, N_g), copied during the call.  *index_out (nullable)
+ * receives the instance index (add order, from 0).  Errors: EINVAL (bad
+ * rationals or labels, more than 2^31 - 1 supra-nodes in the batch),
+ * EOVERFLOW (the bound of the conventions for this graph, gamma and omega). */
+int mslice_batch_add(mslice_batch b, mslice_handle g, int64_t gamma_num, int64_t gamma_den, int64_t omega_num,
+                     int64_t omega_den, const int32_t* init_labels, int32_t* index_out);
+
+/* Solves every instance.  o: schedule options shared by all instances
+ * (n_iterations, K, max_rounds, max_levels, seed; MSLICE_PROFILE honoured);
+ * its gamma/omega/init fields are not used and stop_level must be -1.
+ * st (nullable): counters summed over the batch and phase times of the
+ * pass.  Errors: EINVAL (empty batch, bad options), ENOMEM, ECUDA. */
+int mslice_batch_run(mslice_batch b, const mslice_opts* o, mslice_stats* st);
+
+/* Results of the last run.  i in [0, B): labels_out gets instance i's N_i
+ * canonical labels (numbered from 0 within the instance) and *Q_out its Q_MS;
+ * i = -1: labels_out gets all instances' labels one after another (sum N_i
+ * entries, instance i at offsets[i] of mslice_batch_info) and Q_out B values.
+ * Errors: EINVAL (bad index, not run since the last add/clear). */
+int mslice_batch_results(mslice_batch b, int32_t i, int32_t* labels_out, double* Q_out);
+
+/* Instances B, total supra-nodes N, and offsets (nullable, B+1 entries):
+ * first supra-node of every instance in the concatenated labels. */
+int mslice_batch_info(mslice_batch b, int32_t* B, int64_t* N, int64_t* offsets);
+
+/* Removes every instance; device memory is kept for the next runs. */
+int mslice_batch_clear(mslice_batch b);
+
+/* Kernels launched by this batch's runs; -1 for NULL. */
+int64_t mslice_batch_kernel_launches(mslice_batch b);
+
+/* Releases the batch and its device memory (NULL is ignored). */
+void mslice_batch_free(mslice_batch b);
+
 /* Sizes of a built handle: N supra-nodes, T, n, stored level-0 entries
  * (intra + coupling, both directions). Any pointer may be NULL. */
 int mslice_info(mslice_handle h, int64_t* N, int32_t* T, int64_t* n, int64_t* nnz);

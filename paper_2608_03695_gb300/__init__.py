@@ -11,6 +11,8 @@ The entry points mirror ``include/mslice.h``:
 * :meth:`Handle.mslice_leiden` -- Leiden on multislice modularity (Sec. 3.2)
 * :meth:`Handle.mslice_modularity` -- Q_MS of a labelling
   (Eq. multislice-modularity)
+* :class:`Batch` -- many (graph, gamma, omega) solves in one pass
+  (``mslice_batch_create/add/run/results``)
 """
 from __future__ import annotations
 
@@ -30,7 +32,9 @@ MSLICE_ORDINAL = 0
 # every symbol include/mslice.h declares
 EXPORTS = ["mslice_default_opts", "mslice_build", "mslice_build_ex", "mslice_leiden", "mslice_leiden_ex",
            "mslice_modularity", "mslice_modularity_ex", "mslice_modularity_noalloc", "mslice_info",
-           "mslice_kernel_launches", "mslice_free", "mslice_last_error"]
+           "mslice_kernel_launches", "mslice_free", "mslice_last_error", "mslice_batch_create",
+           "mslice_batch_add", "mslice_batch_run", "mslice_batch_results", "mslice_batch_info",
+           "mslice_batch_clear", "mslice_batch_kernel_launches", "mslice_batch_free"]
 
 
 class LibraryMissing(RuntimeError):
@@ -95,6 +99,16 @@ def lib():
         L.mslice_free.argtypes = [P]
         L.mslice_free.restype = None
         L.mslice_last_error.restype = C.c_char_p
+        L.mslice_batch_create.argtypes = [C.c_int32, P, P]
+        L.mslice_batch_add.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, P, P]
+        L.mslice_batch_run.argtypes = [P, P, P]
+        L.mslice_batch_results.argtypes = [P, C.c_int32, P, P]
+        L.mslice_batch_info.argtypes = [P, P, P, P]
+        L.mslice_batch_clear.argtypes = [P]
+        L.mslice_batch_kernel_launches.argtypes = [P]
+        L.mslice_batch_kernel_launches.restype = C.c_int64
+        L.mslice_batch_free.argtypes = [P]
+        L.mslice_batch_free.restype = None
         _lib = L
     return _lib
 
@@ -189,6 +203,92 @@ class Handle:
     # short aliases
     leiden = mslice_leiden
     modularity = mslice_modularity
+
+
+class Batch:
+    """A batch of independent (graph, gamma, omega) instances solved together
+    (``mslice_batch_*``).  Each instance's labels and Q equal those of
+    :meth:`Handle.mslice_leiden` on its graph alone."""
+
+    def __init__(self, stream=None, device_ptrs=False):
+        b = C.c_void_p()
+        _check(lib().mslice_batch_create(MSLICE_DEVICE_PTRS if device_ptrs else 0,
+                                         C.c_void_p(stream) if stream is not None else None, C.byref(b)),
+               "mslice_batch_create")
+        self._b = b
+        self._dev = device_ptrs
+        self._graphs = []
+
+    def close(self):
+        if self._b:
+            lib().mslice_batch_free(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def mslice_batch_add(self, graph: "Handle", gamma=(1, 1), omega=(1, 1), init=None) -> int:
+        init_a = init
+        if init is not None and not hasattr(init, "data_ptr"):
+            init_a = np.ascontiguousarray(init, dtype=np.int32)
+        idx = C.c_int32(-1)
+        _check(lib().mslice_batch_add(self._b, graph._h, gamma[0], gamma[1], omega[0], omega[1], _ptr(init_a),
+                                      C.byref(idx)), "mslice_batch_add")
+        self._graphs.append(graph)
+        return idx.value
+
+    def mslice_batch_run(self, n_iterations=2, K=4, max_rounds=100, max_levels=32, seed=0, profile=False) -> dict:
+        o = default_opts()
+        o.n_iterations, o.K, o.max_rounds, o.max_levels, o.seed = n_iterations, K, max_rounds, max_levels, seed
+        if profile:
+            o.flags |= MSLICE_PROFILE
+        st = Stats()
+        _check(lib().mslice_batch_run(self._b, C.byref(o), C.byref(st)), "mslice_batch_run")
+        return {f: getattr(st, f) for f, _ in Stats._fields_}
+
+    def mslice_batch_info(self):
+        B, N = C.c_int32(), C.c_int64()
+        _check(lib().mslice_batch_info(self._b, C.byref(B), C.byref(N), None), "mslice_batch_info")
+        off = np.zeros(B.value + 1, dtype=np.int64)
+        _check(lib().mslice_batch_info(self._b, None, None, _ptr(off)), "mslice_batch_info")
+        return B.value, N.value, off
+
+    def mslice_batch_results(self, i=-1, out=None):
+        """(labels, Q) of instance i; i = -1: all labels one after another and
+        the B values of Q."""
+        B, N, off = self.mslice_batch_info()
+        n = int(N if i < 0 else (off[i + 1] - off[i] if i < B else 0))  # a bad index is the library's to reject
+        labels = out if out is not None else np.zeros(max(n, 1), dtype=np.int32)
+        if i < 0:
+            Q = np.zeros(max(B, 1), dtype=np.float64)
+            _check(lib().mslice_batch_results(self._b, -1, _ptr(labels), _ptr(Q)), "mslice_batch_results")
+            return (labels if out is not None else labels[:n]), Q[:B]
+        Q = C.c_double(0.0)
+        _check(lib().mslice_batch_results(self._b, i, _ptr(labels), C.byref(Q)), "mslice_batch_results")
+        return (labels if out is not None else labels[:n]), Q.value
+
+    def mslice_batch_clear(self):
+        _check(lib().mslice_batch_clear(self._b), "mslice_batch_clear")
+        self._graphs = []
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(lib().mslice_batch_kernel_launches(self._b))
+
+    add = mslice_batch_add
+    run = mslice_batch_run
+    results = mslice_batch_results
+    info = mslice_batch_info
+    clear = mslice_batch_clear
 
 
 def mslice_build(snaps, omega=(1, 1), stream=None, device_ptrs=False, host_tensors=False) -> Handle:

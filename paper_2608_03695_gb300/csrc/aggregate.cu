@@ -25,6 +25,7 @@ __global__ void k_emit_edges(LevelDev g, const int32_t* R, const int32_t* newid,
   for (int64_t v = (((int64_t)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); v < g.N; v += warps) {
     const uint64_t x = (uint64_t)newid[R[v]];
     const int64_t b = g.rowptr[v], e = g.rowptr[v + 1];
+    const Omega om = node_omega(g, (int32_t)v);
     for (int64_t base = b; base < e; base += 32) {
       const int64_t i = base + lane;
       bool keep = false;
@@ -32,7 +33,7 @@ __global__ void k_emit_edges(LevelDev g, const int32_t* R, const int32_t* newid,
       long long W = 0;
       if (i < e) {
         int32_t u;
-        if (edge_at(g, i, u, W)) {
+        if (edge_at(g, i, u, W, om)) {
           const uint64_t y = (uint64_t)newid[R[u]];
           if (y != x) {
             keep = true;
@@ -160,6 +161,16 @@ __global__ void k_next_labels(const int32_t* P, const int32_t* R, const int32_t*
     next[newid[R[v]]] = minid[P[v]];
 }
 
+// Batches: instance of every new node and the first new id of every instance.
+__global__ void k_next_inst(LevelDev g, const int32_t* R, const int32_t* newid, int32_t* inst_next, int32_t* off_next) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t x = newid[R[v]];
+    const int32_t i = g.inst[v];
+    inst_next[x] = i;
+    atomicMin(&off_next[i], x);
+  }
+}
+
 __global__ void k_compose(const int32_t* R, const int32_t* newid, int64_t N0, int32_t* node_of0) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N0; v += (int64_t)gridDim.x * blockDim.x)
     node_of0[v] = newid[R[node_of0[v]]];
@@ -228,8 +239,19 @@ bool aggregate(Solver& S, const Level& L, const int32_t* P, Level& next, const s
   next.d = LevelDev{};
   next.d.N = Np;
   next.d.is0 = 0;
-  next.d.on = S.p.on;
-  next.d.od = S.p.od;
+  next.d.on = L.d.on;
+  next.d.od = L.d.od;
+  next.d.on_i = L.d.on_i;
+  next.d.od_i = L.d.od_i;
+  if (L.d.inst) {
+    int32_t* inst_next = c.ws->get<int32_t>(slot + "_inst", (size_t)Np);
+    int32_t* off_next = c.ws->get<int32_t>(slot + "_ioff", (size_t)S.B + 1);
+    fill_i32(c, off_next, Np, (int64_t)S.B + 1);
+    launch(c, k_next_inst, dim3(gsz(N)), dim3(256), 0, L.d, (const int32_t*)S.R, (const int32_t*)newid, inst_next,
+           off_next);
+    next.d.inst = inst_next;
+    next.d.inst_off = off_next;
+  }
   int64_t* rowptr = c.ws->get<int64_t>(slot + "_rowptr", (size_t)Np + 1);
   int32_t* col = c.ws->get<int32_t>(slot + "_col", mu);
   long long* W = c.ws->get<long long>(slot + "_W", mu);

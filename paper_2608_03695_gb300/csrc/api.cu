@@ -1,19 +1,12 @@
-// C ABI of the mslice library (include/mslice.h) and the Leiden driver.
-//
-// Driver (Sec. 3.2: Leiden = local moving, refinement, aggregation):
-//   for it in 0..n_iterations-1 (the paper caps runs at two passes, Sec. 4):
-//     level 0 starts from the warm-start / previous labels (singletons first)
-//     per level: local moving; stop if every community is one node or at
-//     max_levels; refinement; stop if it merged nothing; aggregation
-//     flatten the last level's labels to supra-nodes, canonicalise,
-//     stop early when an iteration returns the labels it started from
-//   Q of the final labels (exact gamma).
+// C ABI of the mslice library (include/mslice.h): argument checks, host and
+// device buffers, handles and batches around the driver (driver.cu).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <map>
 #include <functional>
 #include <new>
@@ -135,70 +128,13 @@ void check_status(Ctx& c, const char* where) {
   fail(MSLICE_ECUDA, std::string(where) + ": internal error");
 }
 
-namespace {
-
-__global__ void k_check_labels(const int32_t* x, int64_t N, int64_t hi, unsigned* status) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    if (x[i] < 0 || x[i] >= hi) atomicOr(status, ERR_BAD_INPUT);
-}
-
-__global__ void k_gather(const int32_t* labels, const int32_t* node_of0, int64_t N0, int32_t* out) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N0; v += (int64_t)gridDim.x * blockDim.x)
-    out[v] = labels[node_of0[v]];
-}
-
-__global__ void k_differs(const int32_t* a, const int32_t* b, int64_t N, int32_t* flag) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x)
-    if (a[v] != b[v]) *flag = 1;
-}
-
-unsigned gsz(int64_t n) {
-  int64_t g = (n + 255) / 256;
-  if (g > 152 * 16) g = 152 * 16;
-  return (unsigned)(g < 1 ? 1 : g);
-}
-
-// CUDA-event phase timing: events recorded on the handle's stream.
-struct PhaseClock {
-  Ctx& c;
-  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> spans;
-  explicit PhaseClock(Ctx& cc) : c(cc) {}
-  ~PhaseClock() {
-    for (auto& s : spans) {
-      cudaEventDestroy(s.second.first);
-      cudaEventDestroy(s.second.second);
-    }
-  }
-  cudaEvent_t begin() {
-    cudaEvent_t e;
-    check_cuda(cudaEventCreate(&e), "event");
-    check_cuda(cudaEventRecord(e, c.stream), "event");
-    return e;
-  }
-  void end(int phase, cudaEvent_t b) {
-    cudaEvent_t e;
-    check_cuda(cudaEventCreate(&e), "event");
-    check_cuda(cudaEventRecord(e, c.stream), "event");
-    spans.push_back({phase, {b, e}});
-  }
-  void totals(double out[5]) {
-    sync(c);
-    for (int i = 0; i < 5; ++i) out[i] = 0;
-    for (auto& s : spans) {
-      float ms = 0;
-      check_cuda(cudaEventElapsedTime(&ms, s.second.first, s.second.second), "event time");
-      out[s.first] += ms;
-    }
-  }
-};
-
-}  // namespace
 }  // namespace mslice
 
 using namespace mslice;
 
 struct mslice_graph {
   SupraGraph G;
+  uint64_t serial = 0;  // unique per built graph (batches cache their concatenation by it)
   Workspace ws;
   cudaStream_t stream = nullptr;
   unsigned* d_status = nullptr;
@@ -214,6 +150,40 @@ struct mslice_graph {
     return c;
   }
   ~mslice_graph() {
+    ws.release_all();
+    G.mem.release_all();
+    if (pinned) cudaFreeHost(pinned);
+  }
+};
+
+
+struct mslice_batch_s {
+  cudaStream_t stream = nullptr;
+  Workspace ws;
+  unsigned* d_status = nullptr;
+  void* pinned = nullptr;
+  int32_t flags = 0;
+  // instances, in add order
+  std::vector<mslice_graph*> graphs;
+  std::vector<InstParams> jobs;
+  std::vector<int64_t> off{0};     // first supra-node of every instance (B+1)
+  std::vector<int32_t> init;       // warm starts (local ids), filled with singletons where none was given
+  bool any_init = false;
+  // concatenated supra-graph and the graph serials it was built from
+  SupraGraph G;
+  std::vector<uint64_t> G_serials;
+  bool solved = false;
+  std::vector<double> Q;
+  int64_t launches = 0;
+  Ctx ctx() {
+    Ctx c;
+    c.stream = stream;
+    c.ws = &ws;
+    c.d_status = d_status;
+    c.pinned = pinned;
+    return c;
+  }
+  ~mslice_batch_s() {
     ws.release_all();
     G.mem.release_all();
     if (pinned) cudaFreeHost(pinned);
@@ -256,10 +226,10 @@ bool rational_ok(int64_t num, int64_t den, bool allow_zero) {
   return den >= 1 && den <= lim && num >= (allow_zero ? 0 : 1) && num <= lim;
 }
 
-void check_bounds(const SupraGraph& G, long long gn, long long gd, long long on, long long od) {
+void check_bounds(int64_t n, int32_t T, const int64_t* two_m, long long gn, long long gd, long long on, long long od) {
   u128 sum2m = 0;
-  for (int64_t t : G.two_m_host) sum2m += (u128)(ull)t;
-  const u128 ncpl = (u128)(ull)G.n * (u128)(ull)(G.T - 1);
+  for (int32_t s = 0; s < T; ++s) sum2m += (u128)(ull)two_m[s];
+  const u128 ncpl = (u128)(ull)n * (u128)(ull)(T > 0 ? T - 1 : 0);
   const u128 lim = (u128)1 << 61;
   if ((u128)(ull)od * sum2m + 2 * (u128)(ull)on * ncpl >= lim)
     fail(MSLICE_EOVERFLOW, "omega_den*sum(2m_s) + 2*omega_num*n*(T-1) must stay below 2^61");
@@ -267,11 +237,62 @@ void check_bounds(const SupraGraph& G, long long gn, long long gd, long long on,
     fail(MSLICE_EOVERFLOW, "gamma*omega_den*sum(2m_s) must stay below 2^61");
 }
 
-void check_labels(Ctx& c, const int32_t* d, int64_t N) {
-  if (N == 0) return;
-  check_cuda(cudaMemsetAsync(c.d_status, 0, sizeof(unsigned), c.stream), "memset");
-  launch(c, k_check_labels, dim3(gsz(N)), dim3(256), 0, d, N, N, c.d_status);
-  check_status(c, "labels");
+void sync_stream(cudaStream_t s) { check_cuda(cudaStreamSynchronize(s), "stream synchronize"); }
+
+void check_opts(const mslice_opts& opt) {
+  if (opt.n_iterations < 1 || opt.K < 1 || opt.max_rounds < 1 || opt.max_levels < 1)
+    fail(MSLICE_EINVAL, "n_iterations, K, max_rounds and max_levels must be >= 1");
+  if (opt.K > 64) fail(MSLICE_EINVAL, "K must be at most 64");
+}
+
+// One solve (a single instance or a batch) with the options' schedule;
+// fills the stats, prints the MSLICE_TRACE kernel table when set.
+void run_solve(Ctx& c, const SupraGraph& G, const std::vector<InstParams>& jobs, const mslice_opts& opt,
+               const int32_t* init, int32_t* out, Solver& S, RunOut& ro, mslice_stats& stats) {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_spans;
+  c.profile = (opt.flags & MSLICE_PROFILE) != 0;
+  c.prof_spans = &prof_spans;
+  std::vector<std::pair<const void*, std::pair<cudaEvent_t, cudaEvent_t>>> trace;
+  if (std::getenv("MSLICE_TRACE")) c.trace = &trace;
+  SolveParams p;
+  p.K = opt.K;
+  p.max_rounds = opt.max_rounds;
+  p.max_levels = opt.max_levels;
+  p.n_iterations = opt.n_iterations;
+  p.seed = opt.seed;
+  run_leiden(c, G, jobs, p, opt.stop_level, opt.stop_stage, opt.stop_rounds, init, out, S, ro);
+  std::memset(&stats, 0, sizeof(stats));
+  stats.iterations = (int32_t)ro.iterations;
+  stats.levels = (int32_t)ro.levels;
+  stats.out_n = ro.out_n;
+  stats.next_n = ro.next_n;
+  stats.next_nnz = ro.next_nnz;
+  stats.next_checksum = ro.next_checksum;
+  stats.stop_reason = (int32_t)ro.stop_reason;
+  stats.last_level0_moves = ro.last_level0_moves;
+  stats.ms_total = ro.ms[0];
+  stats.ms_local_move = ro.ms[1];
+  stats.ms_refine = ro.ms[2];
+  stats.ms_aggregate = ro.ms[3];
+  stats.ms_modularity = ro.ms[4];
+  stats.lm_rounds = S.lm_rounds;
+  stats.lm_edges = S.lm_edges;
+  stats.lm_moves = S.lm_moves;
+  stats.kernel_launches = c.launches;
+  if (c.trace) trace_report(c);
+  if (c.profile) {
+    double dms = 0;
+    for (auto& sp : prof_spans) {
+      float ms = 0;
+      check_cuda(cudaEventElapsedTime(&ms, sp.first, sp.second), "event time");
+      dms += ms;
+      cudaEventDestroy(sp.first);
+      cudaEventDestroy(sp.second);
+    }
+    stats.ms_decide = dms;
+    stats.decide_launches = (int64_t)prof_spans.size();
+    stats.decide_bytes = c.prof_bytes;
+  }
 }
 
 }  // namespace
@@ -312,6 +333,8 @@ int mslice_build_ex(const mslice_csr* slices, int32_t T, mslice_coupling cpl, in
     for (int32_t s = 0; s < T; ++s)
       if (slices[s].n != n) fail(MSLICE_EINVAL, "snapshots must have the same n");
     h = new mslice_graph();
+    static std::atomic<uint64_t> next_serial{1};
+    h->serial = next_serial++;
     h->stream = static_cast<cudaStream_t>(stream);
     h->ws.stream = h->stream;
     h->G.mem.stream = h->stream;
@@ -408,205 +431,38 @@ int mslice_leiden_ex(mslice_handle h, const mslice_opts* o, const int32_t* init_
     mslice_opts opt;
     mslice_default_opts(&opt);
     if (o) opt = *o;
-    if (opt.n_iterations < 1 || opt.K < 1 || opt.max_rounds < 1 || opt.max_levels < 1)
-      fail(MSLICE_EINVAL, "n_iterations, K, max_rounds and max_levels must be >= 1");
-    if (opt.K > 64) fail(MSLICE_EINVAL, "K must be at most 64");
+    check_opts(opt);
     if (!rational_ok(opt.gamma_num, opt.gamma_den, false)) fail(MSLICE_EINVAL, "gamma must be a rational > 0");
     if (!rational_ok(opt.omega_num, opt.omega_den, true)) fail(MSLICE_EINVAL, "omega must be a rational >= 0");
     if (!labels_out && h->G.N > 0) fail(MSLICE_EINVAL, "null labels_out");
     const bool dev = (opt.flags & MSLICE_DEVICE_PTRS) != 0;
     const SupraGraph& G = h->G;
-    check_bounds(G, opt.gamma_num, opt.gamma_den, opt.omega_num, opt.omega_den);
-    Ctx c = h->ctx();
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_spans;
-    c.profile = (opt.flags & MSLICE_PROFILE) != 0;
-    c.prof_spans = &prof_spans;
-    std::vector<std::pair<const void*, std::pair<cudaEvent_t, cudaEvent_t>>> trace;
-    if (std::getenv("MSLICE_TRACE")) c.trace = &trace;
-    PhaseClock clock(c);
-    cudaEvent_t t_all = clock.begin();
-
-    Solver S;
-    S.c = &c;
-    S.G0 = &G;
-    S.p.gn = opt.gamma_num;
-    S.p.gd = opt.gamma_den;
-    S.p.on = opt.omega_num;
-    S.p.od = opt.omega_den;
-    S.p.K = opt.K;
-    S.p.max_rounds = opt.max_rounds;
-    S.p.max_levels = opt.max_levels;
-    S.p.n_iterations = opt.n_iterations;
-    S.p.seed = opt.seed;
-    S.N0 = G.N;
+    check_bounds(G.n, G.T, G.two_m_host.data(), opt.gamma_num, opt.gamma_den, opt.omega_num, opt.omega_den);
     const int64_t N0 = G.N;
-    solver_alloc(S);
-    S.lam = h->ws.get<u128>("lam", G.T);
-    compute_lambda(c, G, S.p.gn, S.p.gd, S.lam);
-
-    int32_t* labA = h->ws.get<int32_t>("lab_A", N0);
-    int32_t* labB = h->ws.get<int32_t>("lab_B", N0);
-    int32_t* lab0 = h->ws.get<int32_t>("lab_0", N0);
-    int32_t* prev = h->ws.get<int32_t>("lab_prev", N0);
-    int32_t* outc = h->ws.get<int32_t>("lab_out", N0);
-    int32_t* node_of0 = h->ws.get<int32_t>("node_of0", N0);
-    int32_t* dflag = h->ws.get<int32_t>("diff_flag", 1);
-    if (init_labels) {
-      if (dev)
-        check_cuda(cudaMemcpyAsync(lab0, init_labels, N0 * sizeof(int32_t), cudaMemcpyDeviceToDevice, c.stream), "copy");
-      else
-        check_cuda(cudaMemcpyAsync(lab0, init_labels, N0 * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream), "copy");
-      check_labels(c, lab0, N0);
-    } else {
-      iota_i32(c, lab0, N0);
+    Ctx c = h->ctx();
+    const int32_t* init = nullptr;
+    if (init_labels && N0 > 0) {
+      if (dev) {
+        init = init_labels;
+      } else {
+        int32_t* d = h->ws.get<int32_t>("in_init", N0);
+        check_cuda(cudaMemcpyAsync(d, init_labels, N0 * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream), "copy");
+        init = d;
+      }
     }
-
+    int32_t* out = dev ? labels_out : h->ws.get<int32_t>("out_lab", N0 > 0 ? N0 : 1);
     mslice_stats stats;
-    std::memset(&stats, 0, sizeof(stats));
-    const LevelDev d0 = level0_view(G, S.p.on, S.p.od);
-    Level L0;
-    L0.d = d0;
-    L0.nnz = G.nnz;
-    L0.nnz_eff = S.p.on > 0 ? G.nnz : G.nnz_intra;
-    L0.ns = N0;
-
-    bool debug_done = false;
-    bool have_prev = false;
-    for (int it = 0; it < opt.n_iterations && !debug_done; ++it) {
-      stats.iterations = it + 1;
-      Level cur = L0;
-      int32_t* lab = labA;
-      int32_t* lab_next = labB;
-      check_cuda(cudaMemcpyAsync(lab, lab0, N0 * sizeof(int32_t), cudaMemcpyDeviceToDevice, c.stream), "copy");
-      iota_i32(c, node_of0, N0);
-      int lvl = 0;
-      for (;; ++lvl) {
-        const bool stop_here = (it == 0 && opt.stop_level == lvl);
-        int rounds = opt.max_rounds;
-        if (stop_here && opt.stop_rounds > 0) rounds = opt.stop_rounds;
-        if (stop_here && opt.stop_rounds < 0) rounds = 0;
-        prepare_level(S, cur);
-        cudaEvent_t t0 = clock.begin();
-        const MoveOut mo = local_move(S, cur, lab, it, lvl, rounds);
-        clock.end(1, t0);
-        if (c.trace) {
-          sync(c);
-          float ms = 0;
-          cudaEventElapsedTime(&ms, t0, clock.spans.back().second.second);
-          fprintf(stderr, "[mslice level] it=%d lvl=%d N=%d nnz=%lld rounds=%lld moves=%lld lm_ms=%.3f tiers=%d/%d/%d/%d/%d\n",
-                  it, lvl, cur.d.N, (long long)cur.nnz, (long long)mo.rounds, (long long)mo.moves, ms, S.tier_cnt[0],
-                  S.tier_cnt[1], S.tier_cnt[2], S.tier_cnt[3], S.tier_cnt[4]);
-        }
-        if (lvl == 0) stats.last_level0_moves = mo.moves;
-        if (stop_here && opt.stop_stage == 1) {
-          check_cuda(cudaMemcpyAsync(labels_out, lab, cur.d.N * sizeof(int32_t),
-                                     dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c.stream), "copy");
-          stats.out_n = cur.d.N;
-          stats.levels = lvl + 1;
-          debug_done = true;
-          break;
-        }
-        if (count_distinct(S, lab, cur.d.N) == cur.d.N) {
-          stats.stop_reason = 1;
-          break;
-        }
-        if (lvl + 1 >= opt.max_levels) {
-          stats.stop_reason = 2;
-          break;
-        }
-        cudaEvent_t t1 = clock.begin();
-        refine(S, cur, lab, it, lvl);
-        clock.end(2, t1);
-        if (stop_here && opt.stop_stage == 2) {
-          check_cuda(cudaMemcpyAsync(labels_out, S.R, cur.d.N * sizeof(int32_t),
-                                     dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c.stream), "copy");
-          stats.out_n = cur.d.N;
-          stats.levels = lvl + 1;
-          debug_done = true;
-          break;
-        }
-        Level nxt;
-        int64_t ck = 0;
-        cudaEvent_t t2 = clock.begin();
-        const bool shrunk = aggregate(S, cur, lab, nxt, (lvl % 2 == 0) ? "LA" : "LB", lab_next, node_of0,
-                                      (stop_here && opt.stop_stage == 3) ? &ck : nullptr);
-        clock.end(3, t2);
-        if (!shrunk) {
-          stats.stop_reason = 3;
-          break;
-        }
-        if (stop_here && opt.stop_stage == 3) {
-          check_cuda(cudaMemcpyAsync(labels_out, lab_next, nxt.d.N * sizeof(int32_t),
-                                     dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c.stream), "copy");
-          stats.out_n = nxt.d.N;
-          stats.next_n = nxt.d.N;
-          stats.next_nnz = nxt.nnz;
-          stats.next_checksum = (uint64_t)ck;
-          stats.levels = lvl + 1;
-          debug_done = true;
-          break;
-        }
-        cur = nxt;
-        std::swap(lab, lab_next);
-      }
-      if (debug_done) break;
-      stats.levels = lvl + 1;
-      // flatten to supra-nodes and canonicalise
-      int32_t* flat = lab_next;  // free buffer of size N0
-      if (N0 > 0) launch(c, k_gather, dim3(gsz(N0)), dim3(256), 0, (const int32_t*)lab, (const int32_t*)node_of0, N0, flat);
-      canonicalise(S, flat, outc, N0);
-      bool same = false;
-      if (have_prev && N0 > 0) {
-        check_cuda(cudaMemsetAsync(dflag, 0, sizeof(int32_t), c.stream), "memset");
-        launch(c, k_differs, dim3(gsz(N0)), dim3(256), 0, (const int32_t*)outc, (const int32_t*)prev, N0, dflag);
-        same = *static_cast<const int32_t*>(readback(c, dflag, sizeof(int32_t))) == 0;
-      } else if (have_prev) {
-        same = true;
-      }
-      std::swap(prev, outc);
-      have_prev = true;
-      check_cuda(cudaMemcpyAsync(lab0, prev, N0 * sizeof(int32_t), cudaMemcpyDeviceToDevice, c.stream), "copy");
-      if (same) break;
+    RunOut ro;
+    Solver S;
+    run_solve(c, G, {InstParams{opt.gamma_num, opt.gamma_den, opt.omega_num, opt.omega_den}}, opt, init, out, S, ro,
+              stats);
+    if (!dev && ro.out_n > 0) {
+      check_cuda(cudaMemcpyAsync(labels_out, out, ro.out_n * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream),
+                 "copy");
+      sync(c);
     }
-    if (!debug_done) {
-      double Q = 0.0;
-      cudaEvent_t t3 = clock.begin();
-      modularity(S, prev, &Q);
-      clock.end(4, t3);
-      if (N0 > 0)
-        check_cuda(cudaMemcpyAsync(labels_out, prev, N0 * sizeof(int32_t),
-                                   dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c.stream), "copy");
-      stats.out_n = N0;
-      if (Q_out) *Q_out = Q;
-    }
-    clock.end(0, t_all);
-    double ms[5];
-    clock.totals(ms);
-    check_status(c, "leiden");
-    stats.ms_total = ms[0];
-    stats.ms_local_move = ms[1];
-    stats.ms_refine = ms[2];
-    stats.ms_aggregate = ms[3];
-    stats.ms_modularity = ms[4];
-    stats.lm_rounds = S.lm_rounds;
-    stats.lm_edges = S.lm_edges;
-    stats.lm_moves = S.lm_moves;
-    stats.kernel_launches = c.launches;
     h->launches += c.launches;
-    if (c.trace) trace_report(c);
-    if (c.profile) {
-      double dms = 0;
-      for (auto& sp : prof_spans) {
-        float ms = 0;
-        check_cuda(cudaEventElapsedTime(&ms, sp.first, sp.second), "event time");
-        dms += ms;
-        cudaEventDestroy(sp.first);
-        cudaEventDestroy(sp.second);
-      }
-      stats.ms_decide = dms;
-      stats.decide_launches = (int64_t)prof_spans.size();
-      stats.decide_bytes = c.prof_bytes;
-    }
+    if (Q_out && !ro.Q.empty()) *Q_out = ro.Q[0];
     if (st) *st = stats;
   });
 }
@@ -632,16 +488,13 @@ int mslice_modularity_ex(mslice_handle h, const int32_t* labels, int64_t gamma_n
     if (!rational_ok(omega_num, omega_den, true)) fail(MSLICE_EINVAL, "omega must be a rational >= 0");
     const SupraGraph& G = h->G;
     if (!labels && G.N > 0) fail(MSLICE_EINVAL, "null labels");
-    check_bounds(G, gamma_num, gamma_den, omega_num, omega_den);
+    check_bounds(G.n, G.T, G.two_m_host.data(), gamma_num, gamma_den, omega_num, omega_den);
     Ctx c = h->ctx();
     Solver S;
     S.c = &c;
     S.G0 = &G;
-    S.p.gn = gamma_num;
-    S.p.gd = gamma_den;
-    S.p.on = omega_num;
-    S.p.od = omega_den;
     S.N0 = G.N;
+    set_instances(c, S, {InstParams{gamma_num, gamma_den, omega_num, omega_den}});
     const int64_t N = G.N > 0 ? G.N : 1;
     S.sig_used = h->ws.get<ull>("m_used", 1);
     int32_t* lab = h->ws.get<int32_t>("m_lab", N);
@@ -649,7 +502,7 @@ int mslice_modularity_ex(mslice_handle h, const int32_t* labels, int64_t gamma_n
       const bool dev = (flags & MSLICE_DEVICE_PTRS) != 0;
       check_cuda(cudaMemcpyAsync(lab, labels, G.N * sizeof(int32_t),
                                  dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c.stream), "copy");
-      check_labels(c, lab, G.N);
+      check_label_ranges(c, G, lab);
     }
     double Q = 0.0;
     modularity(S, lab, &Q);
@@ -663,5 +516,150 @@ int mslice_modularity(mslice_handle h, const int32_t* labels, int64_t gamma_num,
                       int64_t omega_num, int64_t omega_den, double* Q_out) {
   return mslice_modularity_ex(h, labels, gamma_num, gamma_den, omega_num, omega_den, 0, Q_out);
 }
+
+int mslice_batch_create(int32_t flags, void* stream, mslice_batch* out) {
+  mslice_batch b = nullptr;
+  const int rc = guard([&] {
+    if (!out) fail(MSLICE_EINVAL, "null output batch");
+    *out = nullptr;
+    b = new mslice_batch_s();
+    b->flags = flags;
+    b->stream = static_cast<cudaStream_t>(stream);
+    b->ws.stream = b->stream;
+    b->G.mem.stream = b->stream;
+    keep_pool_memory();
+    check_cuda(cudaMallocHost(&b->pinned, 4096), "pinned buffer");
+    b->d_status = b->ws.get<unsigned>("status", 4);
+    check_cuda(cudaMemsetAsync(b->d_status, 0, 16, b->stream), "memset");
+    sync_stream(b->stream);
+    *out = b;
+  });
+  if (rc != MSLICE_OK && b) delete b;
+  return rc;
+}
+
+int mslice_batch_add(mslice_batch b, mslice_handle g, int64_t gamma_num, int64_t gamma_den, int64_t omega_num,
+                     int64_t omega_den, const int32_t* init_labels, int32_t* index_out) {
+  return guard([&] {
+    if (!b || !g) fail(MSLICE_EINVAL, "null batch or graph");
+    if (!rational_ok(gamma_num, gamma_den, false)) fail(MSLICE_EINVAL, "gamma must be a rational > 0");
+    if (!rational_ok(omega_num, omega_den, true)) fail(MSLICE_EINVAL, "omega must be a rational >= 0");
+    const SupraGraph& G = g->G;
+    check_bounds(G.n, G.T, G.two_m_host.data(), gamma_num, gamma_den, omega_num, omega_den);
+    const int64_t N = G.N;
+    if (b->off.back() + N > INT32_MAX) fail(MSLICE_EINVAL, "the batch must hold fewer than 2^31 supra-nodes");
+    if ((int64_t)b->graphs.size() >= INT32_MAX) fail(MSLICE_EINVAL, "too many instances");
+    std::vector<int32_t> lab(N);
+    if (init_labels && N > 0) {
+      if (b->flags & MSLICE_DEVICE_PTRS)
+        check_cuda(cudaMemcpy(lab.data(), init_labels, N * sizeof(int32_t), cudaMemcpyDeviceToHost), "copy");
+      else
+        std::memcpy(lab.data(), init_labels, N * sizeof(int32_t));
+      for (int64_t v = 0; v < N; ++v)
+        if (lab[v] < 0 || lab[v] >= N) fail(MSLICE_EINVAL, "init labels must lie in [0, N)");
+    } else {
+      for (int64_t v = 0; v < N; ++v) lab[v] = (int32_t)v;
+    }
+    b->init.insert(b->init.end(), lab.begin(), lab.end());
+    b->any_init = b->any_init || init_labels != nullptr;
+    b->graphs.push_back(g);
+    b->jobs.push_back(InstParams{gamma_num, gamma_den, omega_num, omega_den});
+    b->off.push_back(b->off.back() + N);
+    b->solved = false;
+    if (index_out) *index_out = (int32_t)b->graphs.size() - 1;
+  });
+}
+
+int mslice_batch_run(mslice_batch b, const mslice_opts* o, mslice_stats* st) {
+  return guard([&] {
+    if (!b) fail(MSLICE_EINVAL, "null batch");
+    if (b->graphs.empty()) fail(MSLICE_EINVAL, "empty batch");
+    mslice_opts opt;
+    mslice_default_opts(&opt);
+    if (o) opt = *o;
+    check_opts(opt);
+    if (opt.stop_level >= 0) fail(MSLICE_EINVAL, "debug stops apply to single solves only");
+    Ctx c = b->ctx();
+    std::vector<uint64_t> serials;
+    for (mslice_graph* g : b->graphs) serials.push_back(g->serial);
+    if (serials != b->G_serials) {
+      std::vector<const SupraGraph*> parts;
+      for (mslice_graph* g : b->graphs) parts.push_back(&g->G);
+      b->G_serials.clear();
+      concat_instances(c, parts, b->G);
+      b->G_serials = serials;
+    }
+    const int64_t N = b->G.N;
+    int32_t* init = nullptr;
+    if (b->any_init && N > 0) {
+      init = b->ws.get<int32_t>("b_init", N);
+      check_cuda(cudaMemcpyAsync(init, b->init.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream), "copy");
+    }
+    int32_t* out = b->ws.get<int32_t>("b_out", N > 0 ? N : 1);
+    opt.flags &= MSLICE_PROFILE;
+    mslice_stats stats;
+    RunOut ro;
+    Solver S;
+    b->solved = false;
+    run_solve(c, b->G, b->jobs, opt, init, out, S, ro, stats);
+    b->Q = ro.Q;
+    b->solved = true;
+    b->launches += c.launches;
+    if (st) *st = stats;
+  });
+}
+
+int mslice_batch_results(mslice_batch b, int32_t i, int32_t* labels_out, double* Q_out) {
+  return guard([&] {
+    if (!b) fail(MSLICE_EINVAL, "null batch");
+    if (!b->solved) fail(MSLICE_EINVAL, "the batch has not been run since its last change");
+    const int32_t B = (int32_t)b->graphs.size();
+    if (i < -1 || i >= B) fail(MSLICE_EINVAL, "instance index out of range");
+    const int64_t lo = i < 0 ? 0 : b->off[i], hi = i < 0 ? b->off[B] : b->off[i + 1];
+    if (hi > lo) {
+      if (!labels_out) fail(MSLICE_EINVAL, "null labels_out");
+      const int32_t* out = b->ws.get<int32_t>("b_out", b->G.N > 0 ? b->G.N : 1);
+      const bool dev = (b->flags & MSLICE_DEVICE_PTRS) != 0;
+      check_cuda(cudaMemcpyAsync(labels_out, out + lo, (hi - lo) * sizeof(int32_t),
+                                 dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream), "copy");
+      sync_stream(b->stream);
+    }
+    if (Q_out) {
+      if (i < 0)
+        std::memcpy(Q_out, b->Q.data(), B * sizeof(double));
+      else
+        *Q_out = b->Q[i];
+    }
+  });
+}
+
+int mslice_batch_info(mslice_batch b, int32_t* B, int64_t* N, int64_t* offsets) {
+  if (!b) {
+    g_last_error = "null batch";
+    return MSLICE_EINVAL;
+  }
+  if (B) *B = (int32_t)b->graphs.size();
+  if (N) *N = b->off.back();
+  if (offsets) std::memcpy(offsets, b->off.data(), b->off.size() * sizeof(int64_t));
+  return MSLICE_OK;
+}
+
+int mslice_batch_clear(mslice_batch b) {
+  if (!b) {
+    g_last_error = "null batch";
+    return MSLICE_EINVAL;
+  }
+  b->graphs.clear();
+  b->jobs.clear();
+  b->off.assign(1, 0);
+  b->init.clear();
+  b->any_init = false;
+  b->solved = false;
+  return MSLICE_OK;
+}
+
+int64_t mslice_batch_kernel_launches(mslice_batch b) { return b ? b->launches : -1; }
+
+void mslice_batch_free(mslice_batch b) { delete b; }
 
 }  // extern "C"

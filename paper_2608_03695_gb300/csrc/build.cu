@@ -125,11 +125,34 @@ __global__ void k_slice_mass(const int64_t* k, int64_t n, ull* two_m) {
   }
 }
 
-__global__ void k_lambda(const int64_t* two_m, int32_t T, long long gn, long long gd, u128* lam) {
+__global__ void k_lambda(const int64_t* two_m, int32_t T, const int32_t* slice_inst, const long long* gn,
+                         const long long* gd, u128* lam) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= T) return;
+  const int32_t i = slice_inst ? slice_inst[s] : 0;
   const long long t = two_m[s];
-  lam[s] = t > 0 ? (((u128)(ull)gn) << P_BITS) / ((u128)(ull)gd * (u128)(ull)t) : (u128)0;
+  lam[s] = t > 0 ? (((u128)(ull)gn[i]) << P_BITS) / ((u128)(ull)gd[i] * (u128)(ull)t) : (u128)0;
+}
+
+// Copies one instance into the concatenated arrays.
+__global__ void k_append(int64_t Ni, const int64_t* rowptr, const int2* adj, const int64_t* k, int64_t n, int32_t inst,
+                         int64_t noff, int64_t eoff, int32_t soff, int64_t* rowptr_o, int2* adj_o, int64_t* k_o,
+                         int32_t* slice0, int32_t* inst0) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < Ni; v += (int64_t)gridDim.x * blockDim.x) {
+    rowptr_o[noff + v] = rowptr[v] + eoff;
+    k_o[noff + v] = k[v];
+    slice0[noff + v] = soff + (int32_t)(v / n);
+    inst0[noff + v] = inst;
+  }
+  const int64_t nnz = rowptr[Ni];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    const int2 x = adj[e];
+    adj_o[eoff + e] = make_int2(x.x + (int32_t)noff, x.y);
+  }
+}
+
+__global__ void k_slice_inst(int32_t* slice_inst, int32_t soff, int32_t T, int32_t inst) {
+  for (int s = threadIdx.x; s < T; s += blockDim.x) slice_inst[soff + s] = inst;
 }
 
 unsigned gs(int64_t n, int per) {
@@ -185,10 +208,64 @@ void build_supra(Ctx& c, const std::vector<const int64_t*>& indptr, const std::v
              "copy");
   sync(c);
   g.nnz_intra = g.nnz - 2 * n * (int64_t)(T - 1);
+  g.B = 1;
+  g.inst.assign(1, InstInfo{n, 0, T, 0});
 }
 
-void compute_lambda(Ctx& c, const SupraGraph& g, long long gn, long long gd, u128* lam) {
-  launch(c, k_lambda, dim3(grid_for(g.T, 128)), dim3(128), 0, (const int64_t*)g.two_m, g.T, gn, gd, lam);
+void compute_lambda(Ctx& c, const SupraGraph& g, const long long* gn, const long long* gd, u128* lam) {
+  launch(c, k_lambda, dim3(grid_for(g.T, 128)), dim3(128), 0, (const int64_t*)g.two_m, g.T,
+         (const int32_t*)g.slice_inst, gn, gd, lam);
+}
+
+void concat_instances(Ctx& c, const std::vector<const SupraGraph*>& parts, SupraGraph& out) {
+  const int32_t B = (int32_t)parts.size();
+  out.B = B;
+  out.inst.assign(B, InstInfo{});
+  int64_t N = 0, nnz = 0, nnz_intra = 0;
+  int32_t T = 0;
+  for (int32_t i = 0; i < B; ++i) {
+    out.inst[i] = InstInfo{parts[i]->n, N, parts[i]->T, T};
+    N += parts[i]->N;
+    nnz += parts[i]->nnz;
+    nnz_intra += parts[i]->nnz_intra;
+    T += parts[i]->T;
+  }
+  out.N = N;
+  out.T = T;
+  out.n = parts.empty() ? 0 : parts[0]->n;
+  out.nnz = nnz;
+  out.nnz_intra = nnz_intra;
+  out.rowptr = static_cast<int64_t*>(out.mem.get_bytes("rowptr0", (N + 1) * sizeof(int64_t)));
+  out.adj = static_cast<int2*>(out.mem.get_bytes("adj0", (nnz ? nnz : 1) * sizeof(int2)));
+  out.k = static_cast<int64_t*>(out.mem.get_bytes("k0", (N ? N : 1) * sizeof(int64_t)));
+  out.two_m = static_cast<int64_t*>(out.mem.get_bytes("two_m", (T ? T : 1) * sizeof(int64_t)));
+  out.slice0 = static_cast<int32_t*>(out.mem.get_bytes("slice0", (N ? N : 1) * sizeof(int32_t)));
+  out.inst0 = static_cast<int32_t*>(out.mem.get_bytes("inst0", (N ? N : 1) * sizeof(int32_t)));
+  out.inst_off0 = static_cast<int32_t*>(out.mem.get_bytes("inst_off0", (B + 1) * sizeof(int32_t)));
+  out.slice_inst = static_cast<int32_t*>(out.mem.get_bytes("slice_inst", (T ? T : 1) * sizeof(int32_t)));
+  std::vector<int32_t> offs(B + 1);
+  int64_t eoff = 0;
+  out.two_m_host.clear();
+  for (int32_t i = 0; i < B; ++i) {
+    const SupraGraph& p = *parts[i];
+    offs[i] = (int32_t)out.inst[i].noff;
+    if (p.N > 0)
+      launch(c, k_append, dim3(gs(std::max<int64_t>(p.N, p.nnz), 256)), dim3(256), 0, p.N, (const int64_t*)p.rowptr,
+             (const int2*)p.adj, (const int64_t*)p.k, p.n, i, out.inst[i].noff, eoff, out.inst[i].soff, out.rowptr,
+             out.adj, out.k, out.slice0, out.inst0);
+    if (p.T > 0) {
+      check_cuda(cudaMemcpyAsync(out.two_m + out.inst[i].soff, p.two_m, p.T * sizeof(int64_t),
+                                 cudaMemcpyDeviceToDevice, c.stream), "copy");
+      launch(c, k_slice_inst, dim3(1), dim3(256), 0, out.slice_inst, out.inst[i].soff, p.T, i);
+    }
+    for (int64_t t : p.two_m_host) out.two_m_host.push_back(t);
+    eoff += p.nnz;
+  }
+  offs[B] = (int32_t)N;
+  check_cuda(cudaMemcpyAsync(out.rowptr + N, &nnz, sizeof(int64_t), cudaMemcpyHostToDevice, c.stream), "copy");
+  check_cuda(cudaMemcpyAsync(out.inst_off0, offs.data(), (B + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream),
+             "copy");
+  sync(c);
 }
 
 }  // namespace mslice

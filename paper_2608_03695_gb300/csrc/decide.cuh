@@ -26,7 +26,7 @@
 //   VCtx vctx(v)                       per-node values computed once (and
 //                                      loads issued early for finish())
 //   void skip(v)                       record "no move" for a non-participant
-//   bool edge(v, e, key&, w&)          entry e contributes w to key
+//   bool edge(v, vc, e, key&, w&)      entry e contributes w to key
 //   Probe probe(v, vc, key)            first table load(s) for scoring key
 //   Cand cand(v, vc, key, W, probe)    score of moving to key (INT32_MAX = not allowed)
 //   int32_t own_key(v)                 the node's current key (-1 none)
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(GROUP_THREADS, MSLICE_GROUP_MIN_BLOCKS)
 #pragma unroll
         for (int j = 0; j < EPL; ++j) {
           const int64_t e = base + j * G + gl;
-          ok[j] = e < end && pol.edge(v, e, keys[j], ws[j]);
+          ok[j] = e < end && pol.edge(v, vc, e, keys[j], ws[j]);
         }
 #pragma unroll
         for (int j = 0; j < EPL; ++j) {
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_block(Pol pol, const i
     for (int64_t e = beg + threadIdx.x; e < end; e += BLOCK_THREADS) {
       int32_t key;
       long long w;
-      if (pol.edge(v, e, key, w)) {
+      if (pol.edge(v, vc, e, key, w)) {
         bool fresh;
         const int slot = table_add_slot(hk, hv, bits, key, w, fresh);
         if (fresh) cl[atomicAdd(&ncand, 1)] = (uint16_t)slot;
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_global(Pol pol, const 
     for (int64_t e = beg + threadIdx.x; e < end; e += BLOCK_THREADS) {
       int32_t key;
       long long w;
-      if (pol.edge(v, e, key, w)) gtable_add(hk, hv, bits, key, w, status);
+      if (pol.edge(v, vc, e, key, w)) gtable_add(hk, hv, bits, key, w, status);
     }
     __syncthreads();
     const int32_t own = pol.own_key(v);

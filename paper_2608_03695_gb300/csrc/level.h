@@ -2,6 +2,12 @@
 // supra-graph itself ({col, w} entries, coupling flagged by w = 0, one
 // snapshot per node); aggregated levels hold int64 weights already scaled to
 // units of 1/omega_den and per-node lists of (snapshot, strength).
+//
+// A level may hold several independent instances (a batch): disjoint blocks
+// of node ids, each with its own omega, gamma (through Lambda of its
+// snapshots) and snapshot range.  No edge joins two instances, so no
+// community ever spans two, and every per-node rule below reads only the
+// node's own instance.
 #pragma once
 #include "internal.h"
 
@@ -9,7 +15,7 @@ namespace mslice {
 
 struct LevelDev {
   int32_t N = 0;
-  int32_t n = 1;  // level 0: nodes per snapshot
+  int32_t n = 1;  // level 0, single instance: nodes per snapshot
   int32_t is0 = 1;
   const int64_t* rowptr = nullptr;
   const int2* adj0 = nullptr;   // level 0
@@ -19,20 +25,51 @@ struct LevelDev {
   const int64_t* sptr = nullptr;
   const int32_t* sidx = nullptr;
   const long long* sval = nullptr;
-  long long on = 1, od = 1;
+  long long on = 1, od = 1;     // single instance
+  // batches (all nullptr for a single instance)
+  const int32_t* slice0 = nullptr;    // level 0: global snapshot of every node
+  const int32_t* inst = nullptr;      // instance of every node
+  const int32_t* inst_off = nullptr;  // first node id of every instance at this level
+  const long long* on_i = nullptr;    // omega of every instance
+  const long long* od_i = nullptr;
 };
 
+struct Omega {
+  long long on, od;
+};
+
+__device__ __forceinline__ int32_t node_inst(const LevelDev& g, int32_t v) { return g.inst ? g.inst[v] : 0; }
+
+__device__ __forceinline__ Omega node_omega(const LevelDev& g, int32_t v) {
+  if (g.od_i) {
+    const int32_t i = node_inst(g, v);
+    return Omega{g.on_i[i], g.od_i[i]};
+  }
+  return Omega{g.on, g.od};
+}
+
+// Node id within its instance (the schedule's hash reads this, so a batched
+// instance draws the same classes as when solved alone).
+__device__ __forceinline__ uint64_t local_id(const LevelDev& g, int32_t v) {
+  return g.inst_off ? (uint64_t)(v - g.inst_off[node_inst(g, v)]) : (uint64_t)v;
+}
+
+__device__ __forceinline__ int32_t node_slice0(const LevelDev& g, int32_t v) {
+  return g.slice0 ? g.slice0[v] : v / g.n;
+}
+
 // Entry e of the adjacency: neighbour u and weight W in units of 1/od.
-// A coupling entry has weight on and is absent when on = 0.
-__device__ __forceinline__ bool edge_at(const LevelDev& g, int64_t e, int32_t& u, long long& W) {
+// A coupling entry has weight on and is absent when on = 0.  (om: the
+// omega of the row's instance.)
+__device__ __forceinline__ bool edge_at(const LevelDev& g, int64_t e, int32_t& u, long long& W, const Omega& om) {
   if (g.is0) {
     const int2 x = __ldcs(&g.adj0[e]);
     u = x.x;
     if (x.y == 0) {
-      W = g.on;
-      return g.on > 0;
+      W = om.on;
+      return om.on > 0;
     }
-    W = (long long)x.y * g.od;
+    W = (long long)x.y * om.od;
     return true;
   }
   u = __ldcs(&g.col[e]);
@@ -53,7 +90,7 @@ __device__ __forceinline__ void slice_range(const LevelDev& g, int32_t v, int64_
 
 __device__ __forceinline__ void slice_entry(const LevelDev& g, int32_t v, int64_t j, int32_t& s, long long& k) {
   if (g.is0) {
-    s = v / g.n;
+    s = node_slice0(g, v);
     k = g.k0[v];
   } else {
     s = g.sidx[j];

@@ -66,14 +66,17 @@ struct TierOff {
   int32_t off[NTIERS];
 };
 
-__global__ void k_bucket(int32_t N, const uint8_t* tier, uint64_t seed, uint64_t tag, uint64_t it, uint64_t lvl,
-                         uint64_t r, int K, int32_t* lists, int64_t row_stride, TierOff tier_off, int32_t* cursors) {
+__global__ void k_bucket(LevelDev g, const uint8_t* tier, uint64_t seed, uint64_t tag, uint64_t it, uint64_t lvl,
+                         uint64_t r, int K, int32_t* lists, int64_t row_stride, TierOff tier_off, int32_t* cursors,
+                         const int32_t* active) {
   const int lane = threadIdx.x & 31;
+  const int32_t N = g.N;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < N; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t v = base + threadIdx.x;
-    const bool ok = v < N;
+    bool ok = v < N;
+    if (ok && active && !active[node_inst(g, (int32_t)v)]) ok = false;  // converged instance: frozen
     int seg = -1;
-    if (ok) seg = vertex_class(seed, tag, it, lvl, r, (uint64_t)v, K) * NTIERS + tier[v];
+    if (ok) seg = vertex_class(seed, tag, it, lvl, r, local_id(g, (int32_t)v), K) * NTIERS + tier[v];
     const unsigned peers = __match_any_sync(0xffffffffu, seg);
     const int leader = __ffs(peers) - 1;
     int pos = 0;
@@ -107,6 +110,7 @@ __global__ void k_sigma_insert(LevelDev g, const int32_t* labels, SigStore h, in
 }
 
 // sum_s Lambda_s k_{v,s} (X_s - self*k_{v,s}) with X_s = table(c, s).
+// (od is applied by the caller.)
 template <bool DENSE>
 __device__ __forceinline__ u128 null_sum(const LevelDev& g, const u128* lam, const SigStore& h, int32_t v, int32_t c,
                                          bool self) {
@@ -132,7 +136,6 @@ struct LMPolicy {
   SigStore sig;
   const u128* lam;
   int32_t* target;
-  long long od;
 
   typedef Slot Probe;
   // Per node: own community and its size; at level 0 the node's snapshot s,
@@ -142,6 +145,7 @@ struct LMPolicy {
     int32_t a, size_a, s;
     bool single;
     long long k;
+    Omega om;
     u128 A;
   };
 
@@ -154,24 +158,25 @@ struct LMPolicy {
     c.s = 0;
     c.k = 0;
     c.A = 0;
+    c.om = node_omega(g, v);
     if (c.single) {
       c.k = g.k0[v];
-      c.s = v / g.n;
-      if (c.k > 0) c.A = (u128)(ull)od * lam[c.s] * (u128)(ull)c.k;
+      c.s = node_slice0(g, v);
+      if (c.k > 0) c.A = (u128)(ull)c.om.od * lam[c.s] * (u128)(ull)c.k;
     }
     return c;
   }
   __device__ void skip(int32_t v) const { target[v] = NO_MOVE; }
-  __device__ bool edge(int32_t, int64_t e, int32_t& key, long long& w) const {
+  __device__ bool edge(int32_t, const VCtx& vc, int64_t e, int32_t& key, long long& w) const {
     int32_t u;
-    if (!edge_at(g, e, u, w)) return false;
+    if (!edge_at(g, e, u, w, vc.om)) return false;
     key = labels[u];
     return true;
   }
   __device__ int32_t own_key(int32_t v) const { return labels[v]; }
-  __device__ i128 key_of(int32_t v, int32_t c, long long W, bool self) const {
+  __device__ i128 key_of(int32_t v, const VCtx& vc, int32_t c, long long W, bool self) const {
     const u128 ns = null_sum<DENSE>(g, lam, sig, v, c, self);
-    return (((i128)W) << P_BITS) - (i128)((u128)(ull)od * ns);
+    return (((i128)W) << P_BITS) - (i128)((u128)(ull)vc.om.od * ns);
   }
   __device__ Probe probe(int32_t, const VCtx& vc, int32_t c) const {
     if (vc.single && vc.k > 0) return sst_first<DENSE>(sig, c, vc.s);
@@ -182,14 +187,14 @@ struct LMPolicy {
       const long long x = vc.k > 0 ? sst_resolve<DENSE>(sig, c, vc.s, pr) : 0;
       return Cand{(((i128)W) << P_BITS) - (i128)(vc.A * (u128)(ull)x), c};
     }
-    return Cand{key_of(v, c, W, false), c};
+    return Cand{key_of(v, vc, c, W, false), c};
   }
   __device__ i128 own(int32_t v, const VCtx& vc, long long Wown) const {
     if (vc.single) {
       const long long x = vc.k > 0 ? sst_get<DENSE>(sig, vc.a, vc.s) - vc.k : 0;
       return (((i128)Wown) << P_BITS) - (i128)(vc.A * (u128)(ull)x);
     }
-    return key_of(v, vc.a, Wown, true);
+    return key_of(v, vc, vc.a, Wown, true);
   }
   __device__ void finish(int32_t v, const Cand& best, long long, const i128& Ga, const VCtx& vc) const {
     const int32_t a = vc.a;
@@ -299,12 +304,17 @@ __device__ __forceinline__ T block_scan_excl(T x, T* sm, T& total) {
 }
 
 // Moves to an empty community (one cooperative launch; returns at once when
-// the sub-round has none).  In ascending node order, the movers take the
-// ascending labels that are free once every other move is applied and the
-// movers have left.  blk: 2*gridDim.x ints.
-__global__ void __launch_bounds__(EMPTY_THREADS) k_empty_pass(LevelDev g, int32_t* target, int32_t* labels,
+// the sub-round has none).  Within each instance, in ascending node order,
+// the movers take the ascending labels of that instance that are free once
+// every other move is applied and the movers have left.
+//   blk:      2*gridDim.x ints (per-chunk counts)
+//   freelist: all free labels in ascending order; mrank: movers' global ranks
+//   icnt:     4*B + 2 ints (per-instance counts, then their prefixes); zero
+//             on entry and left zero on exit
+__global__ void __launch_bounds__(EMPTY_THREADS) k_empty_pass(LevelDev g, int32_t B, int32_t* target, int32_t* labels,
                                                               int32_t* size, SigStore sig, int32_t* counters,
-                                                              int32_t* blk, int32_t* freelist) {
+                                                              int32_t* blk, int32_t* freelist, int32_t* mrank,
+                                                              int32_t* icnt) {
   const int n_empty = counters[2];
   if (n_empty == 0) return;
   __shared__ int32_t sm[33];
@@ -312,10 +322,19 @@ __global__ void __launch_bounds__(EMPTY_THREADS) k_empty_pass(LevelDev g, int32_
   const int64_t N = g.N, nb = gridDim.x;
   const int64_t chunk = (N + nb - 1) / nb;
   const int64_t lo = min(N, (int64_t)blockIdx.x * chunk), hi = min(N, lo + chunk);
+  int32_t* fcnt = icnt;           // free labels per instance
+  int32_t* mcnt = icnt + B;       // movers per instance
+  int32_t* fbase = icnt + 2 * B;  // exclusive prefixes (B + 1 each)
+  int32_t* mbase = icnt + 3 * B + 1;
   int cf = 0, ce = 0;
   for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    cf += size[i] == 0;
-    ce += target[i] == TO_EMPTY;
+    const bool f = size[i] == 0, m = target[i] == TO_EMPTY;
+    cf += f;
+    ce += m;
+    if (B > 1) {
+      if (f) atomicAdd(&fcnt[node_inst(g, (int32_t)i)], 1);
+      if (m) atomicAdd(&mcnt[node_inst(g, (int32_t)i)], 1);
+    }
   }
   int tf, te;
   block_scan_excl(cf, sm, tf);
@@ -325,6 +344,19 @@ __global__ void __launch_bounds__(EMPTY_THREADS) k_empty_pass(LevelDev g, int32_
     blk[nb + blockIdx.x] = te;
   }
   grid.sync();
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    int32_t a = 0, b = 0;
+    for (int32_t i = 0; i < B; ++i) {
+      fbase[i] = a;
+      mbase[i] = b;
+      if (B > 1) {
+        a += fcnt[i];
+        b += mcnt[i];
+      }
+    }
+    fbase[B] = a;
+    mbase[B] = b;
+  }
   int pf = 0, pe = 0;
   for (int b = threadIdx.x; b < blockIdx.x; b += blockDim.x) {
     pf += blk[b];
@@ -335,41 +367,42 @@ __global__ void __launch_bounds__(EMPTY_THREADS) k_empty_pass(LevelDev g, int32_
   block_scan_excl(pe, sm, tot_pe);
   pf = tot_pf;
   pe = tot_pe;
-  // the first n_empty free labels, in order
-  for (int64_t base = lo; base < hi && pf < n_empty; base += blockDim.x) {
+  for (int64_t base = lo; base < hi; base += blockDim.x) {
     const int64_t i = base + threadIdx.x;
     const int f = (i < hi && size[i] == 0) ? 1 : 0;
-    int tot;
-    const int r = block_scan_excl(f, sm, tot);
-    if (f && pf + r < n_empty) freelist[pf + r] = (int32_t)i;
-    pf += tot;
+    const int m = (i < hi && target[i] == TO_EMPTY) ? 1 : 0;
+    int totf, totm;
+    const int rf = block_scan_excl(f, sm, totf);
+    const int rm = block_scan_excl(m, sm, totm);
+    if (f) freelist[pf + rf] = (int32_t)i;
+    if (m) mrank[i] = pe + rm;
+    pf += totf;
+    pe += totm;
   }
   grid.sync();
-  for (int64_t base = lo; base < hi; base += blockDim.x) {
-    const int64_t v = base + threadIdx.x;
-    const int e = (v < hi && target[v] == TO_EMPTY) ? 1 : 0;
-    int tot;
-    const int r = block_scan_excl(e, sm, tot);
-    if (e) {
-      const int32_t L = freelist[pe + r];
-      labels[v] = L;
-      size[L] = 1;
-      int64_t b, en;
-      slice_range(g, (int32_t)v, b, en);
-      for (int64_t j = b; j < en; ++j) {
-        int32_t s;
-        long long k;
-        slice_entry(g, (int32_t)v, j, s, k);
-        ss_add(sig, L, s, k);
-      }
-      target[v] = NO_MOVE;
+  for (int64_t v = lo + threadIdx.x; v < hi; v += blockDim.x) {
+    if (target[v] != TO_EMPTY) continue;
+    const int32_t inst = B > 1 ? node_inst(g, (int32_t)v) : 0;
+    const int32_t L = freelist[fbase[inst] + (mrank[v] - mbase[inst])];
+    labels[v] = L;
+    size[L] = 1;
+    int64_t b, en;
+    slice_range(g, (int32_t)v, b, en);
+    for (int64_t j = b; j < en; ++j) {
+      int32_t s;
+      long long k;
+      slice_entry(g, (int32_t)v, j, s, k);
+      ss_add(sig, L, s, k);
     }
-    pe += tot;
+    target[v] = NO_MOVE;
   }
   grid.sync();
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    atomicAdd((ull*)counters, (ull)n_empty);
-    counters[2] = 0;
+  if (blockIdx.x == 0) {
+    for (int32_t i = threadIdx.x; i < 4 * B + 2; i += blockDim.x) icnt[i] = 0;
+    if (threadIdx.x == 0) {
+      atomicAdd((ull*)counters, (ull)n_empty);
+      counters[2] = 0;
+    }
   }
 }
 
@@ -388,6 +421,18 @@ LevelDev level0_view(const SupraGraph& G, long long on, long long od) {
   return d;
 }
 
+LevelDev level0_view(const SupraGraph& G, const Solver& S) {
+  LevelDev d = level0_view(G, S.p.on, S.p.od);
+  if (G.B > 1) {
+    d.slice0 = G.slice0;
+    d.inst = G.inst0;
+    d.inst_off = G.inst_off0;
+    d.on_i = S.on_d;
+    d.od_i = S.od_d;
+  }
+  return d;
+}
+
 void solver_alloc(Solver& S) {
   Ctx& c = *S.c;
   const int64_t N = S.N0 > 0 ? S.N0 : 1;
@@ -395,7 +440,7 @@ void solver_alloc(Solver& S) {
   S.size = c.ws->get<int32_t>("s_size", N);
   S.tmp32a = c.ws->get<int32_t>("s_tmpa", N + 1);
   S.tmp32b = c.ws->get<int32_t>("s_tmpb", N + 1);
-  S.freelist = c.ws->get<int32_t>("s_free", N);
+  S.freelist = c.ws->get<int32_t>("s_free", N + 1);
   S.tier = c.ws->get<uint8_t>("s_tier", N);
   S.cls = c.ws->get<uint8_t>("s_cls", N);
   S.lists = c.ws->get<int32_t>("s_lists", (size_t)N * S.p.K);
@@ -419,6 +464,8 @@ void solver_alloc(Solver& S) {
   check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attribute");
   S.empty_grid = std::max(1, std::min(max_blocks, 2) * sms);
   S.empty_blk = c.ws->get<int32_t>("s_empty_blk", 2 * S.empty_grid);
+  S.inst_cnt = c.ws->get<int32_t>("s_inst_cnt", 4 * (size_t)S.B + 2);
+  check_cuda(cudaMemsetAsync(S.inst_cnt, 0, (4 * (size_t)S.B + 2) * sizeof(int32_t), c.stream), "memset");
   fill_i32(c, S.target, NO_MOVE, N);
   check_cuda(cudaMemsetAsync(S.counters, 0, 8 * sizeof(int32_t), c.stream), "memset");
 }
@@ -531,8 +578,9 @@ void bucket(Solver& S, const Level& L, uint64_t tag, int it, int lvl, int r) {
   TierOff to;
   for (int t = 0; t < NTIERS; ++t) to.off[t] = S.tier_off[t];
   if (L.d.N > 0)
-    launch(c, k_bucket, dim3(grid_for(L.d.N, 256)), dim3(256), 0, L.d.N, (const uint8_t*)S.tier, S.p.seed, tag,
-           (uint64_t)it, (uint64_t)lvl, (uint64_t)r, S.p.K, S.lists, (int64_t)S.N0, to, S.cursors);
+    launch(c, k_bucket, dim3(grid_for(L.d.N, 256)), dim3(256), 0, L.d, (const uint8_t*)S.tier, S.p.seed, tag,
+           (uint64_t)it, (uint64_t)lvl, (uint64_t)r, S.p.K, S.lists, (int64_t)S.N0, to, S.cursors,
+           (const int32_t*)S.inst_active);
 }
 
 MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, int max_rounds) {
@@ -558,7 +606,6 @@ MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, 
   pol.sig = S.sig;
   pol.lam = S.lam;
   pol.target = S.target;
-  pol.od = S.p.od;
   LMPolicy<false> polh;
   polh.g = pol.g;
   polh.labels = pol.labels;
@@ -566,7 +613,6 @@ MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, 
   polh.sig = pol.sig;
   polh.lam = pol.lam;
   polh.target = pol.target;
-  polh.od = pol.od;
   auto decide = [&](const TierSegs& sg) {
     if (S.sig.d)
       decide_all(c, pol, sg, S.tier_cnt, S.gkeys, S.gvals, S.goff);
@@ -597,8 +643,8 @@ MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, 
       }
       launch(c, k_lm_apply, dim3(fixed_grid(4)), dim3(APPLY_THREADS), 0, L.d, sg, labels, S.size, S.sig, S.target,
              S.counters);
-      launch_coop(c, k_empty_pass, dim3(S.empty_grid), dim3(EMPTY_THREADS), 0, L.d, S.target, labels, S.size, S.sig,
-                  S.counters, S.empty_blk, S.freelist);
+      launch_coop(c, k_empty_pass, dim3(S.empty_grid), dim3(EMPTY_THREADS), 0, L.d, S.B, S.target, labels, S.size,
+                  S.sig, S.counters, S.empty_blk, S.freelist, S.tmp32b, S.inst_cnt);
     }
     struct {
       int64_t moved;

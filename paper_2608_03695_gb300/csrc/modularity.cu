@@ -11,33 +11,53 @@
 //
 // Also: canonical relabelling (first occurrence order), distinct counting
 // and the order-free level checksum used by the step-level tests.
+#include <cstring>
+#include <vector>
+
 #include "solver.h"
 
 namespace mslice {
 
 namespace {
 
-__global__ void k_IJ(LevelDev g, const int32_t* labels, ull* IJ) {
+// I and J of every instance (IJ: 2 words per instance).  A single instance
+// accumulates per warp before one atomic; batches add per row.
+__global__ void k_IJ(LevelDev g, const int32_t* labels, ull* IJ, int32_t B) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   ull I = 0, J = 0;
   for (int64_t v = (((int64_t)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); v < g.N; v += warps) {
     const int32_t c = labels[v];
+    ull Iv = 0, Jv = 0;
     for (int64_t e = g.rowptr[v] + lane; e < g.rowptr[v + 1]; e += 32) {
       const int2 x = g.adj0[e];
       if (labels[x.x] == c) {
         if (x.y > 0)
-          I += (ull)x.y;
+          Iv += (ull)x.y;
         else
-          J += 1;
+          Jv += 1;
+      }
+    }
+    if (B == 1) {
+      I += Iv;
+      J += Jv;
+    } else {
+      Iv = warp_sum(Iv);
+      Jv = warp_sum(Jv);
+      if (lane == 0) {
+        const int32_t i = node_inst(g, (int32_t)v);
+        if (Iv) atomicAdd(&IJ[2 * i], Iv);
+        if (Jv) atomicAdd(&IJ[2 * i + 1], Jv);
       }
     }
   }
-  I = warp_sum(I);
-  J = warp_sum(J);
-  if (lane == 0) {
-    if (I) atomicAdd(&IJ[0], I);
-    if (J) atomicAdd(&IJ[1], J);
+  if (B == 1) {
+    I = warp_sum(I);
+    J = warp_sum(J);
+    if (lane == 0) {
+      if (I) atomicAdd(&IJ[0], I);
+      if (J) atomicAdd(&IJ[1], J);
+    }
   }
 }
 
@@ -70,11 +90,20 @@ __global__ void k_S(SigStore h, int32_t T, ull* S) {
   }
 }
 
-__global__ void k_Q(const ull* IJ, const ull* S, const int64_t* two_m, int32_t T, int64_t n, long long gn,
-                    long long gd, long long on, long long od, double* Q) {
+struct QInst {
+  int64_t n;
+  int32_t T, soff;
+  long long gn, gd, on, od;
+};
+
+// Q of every instance (one thread each), in the fixed FP64 order.
+__global__ void k_Q(const ull* IJ, const ull* S, const int64_t* two_m, const QInst* qi, int32_t B, double* Q) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B) return;
+  const QInst p = qi[i];
   double nullsum = 0.0;
   long long sum2m = 0;
-  for (int s = 0; s < T; ++s) {
+  for (int s = p.soff; s < p.soff + p.T; ++s) {
     const long long t = two_m[s];
     sum2m += t;
     if (t > 0) {
@@ -82,16 +111,16 @@ __global__ void k_Q(const ull* IJ, const ull* S, const int64_t* two_m, int32_t T
       nullsum = __dadd_rn(nullsum, __ddiv_rn(u128_to_double(x), __ll2double_rn(t)));
     }
   }
-  const double wJ = __ddiv_rn(__dmul_rn(__ll2double_rn(on), __ull2double_rn(IJ[1])), __ll2double_rn(od));
-  const double gam = __ddiv_rn(__ll2double_rn(gn), __ll2double_rn(gd));
-  const long long twomu_num = od * sum2m + 2 * on * n * (long long)(T - 1);
+  const double wJ = __ddiv_rn(__dmul_rn(__ll2double_rn(p.on), __ull2double_rn(IJ[2 * i + 1])), __ll2double_rn(p.od));
+  const double gam = __ddiv_rn(__ll2double_rn(p.gn), __ll2double_rn(p.gd));
+  const long long twomu_num = p.od * sum2m + 2 * p.on * p.n * (long long)(p.T - 1);
   if (twomu_num == 0) {
-    *Q = 0.0;
+    Q[i] = 0.0;
     return;
   }
-  const double twomu = __ddiv_rn(__ll2double_rn(twomu_num), __ll2double_rn(od));
-  const double num = __dsub_rn(__dadd_rn(__ull2double_rn(IJ[0]), wJ), __dmul_rn(gam, nullsum));
-  *Q = __ddiv_rn(num, twomu);
+  const double twomu = __ddiv_rn(__ll2double_rn(twomu_num), __ll2double_rn(p.od));
+  const double num = __dsub_rn(__dadd_rn(__ull2double_rn(IJ[2 * i]), wJ), __dmul_rn(gam, nullsum));
+  Q[i] = __ddiv_rn(num, twomu);
 }
 
 __global__ void k_first(const int32_t* x, int64_t N, int32_t* first) {
@@ -104,9 +133,11 @@ __global__ void k_first_flag(const int32_t* x, const int32_t* first, int64_t N, 
     flag[v] = first[x[v]] == (int32_t)v ? 1 : 0;
 }
 
-__global__ void k_canon(const int32_t* x, const int32_t* first, const int32_t* rank, int64_t N, int32_t* out) {
+// Renumbered labels, counted from the instance's first community.
+__global__ void k_canon(const int32_t* x, const int32_t* first, const int32_t* rank, int64_t N, const int32_t* inst,
+                        const int32_t* inst_off, int32_t* out) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x)
-    out[v] = rank[first[x[v]]];
+    out[v] = rank[first[x[v]]] - (inst ? rank[inst_off[inst[v]]] : 0);
 }
 
 __global__ void k_mark(const int32_t* x, int64_t N, int32_t* flag) {
@@ -137,19 +168,29 @@ unsigned gsz(int64_t n) {
 void modularity(Solver& S, const int32_t* labels0, double* Q) {
   Ctx& c = *S.c;
   const SupraGraph& G = *S.G0;
-  const LevelDev g = level0_view(G, S.p.on, S.p.od);
+  const int32_t B = G.B;
+  LevelDev g = level0_view(G, S);
   configure_stores(S, G.N);
   sigma_rebuild(S, Level{g}, labels0);
-  ull* acc = c.ws->get<ull>("q_acc", 2 + 2 * (size_t)G.T);
-  double* dQ = c.ws->get<double>("q_out", 1);
-  check_cuda(cudaMemsetAsync(acc, 0, (2 + 2 * (size_t)G.T) * sizeof(ull), c.stream), "memset");
-  if (G.N > 0) launch(c, k_IJ, dim3(gsz(G.N * 32)), dim3(256), 0, g, labels0, acc);
+  ull* acc = c.ws->get<ull>("q_acc", 2 * (size_t)B + 2 * (size_t)G.T);
+  double* dQ = c.ws->get<double>("q_out", B);
+  QInst* dqi = c.ws->get<QInst>("q_inst", B);
+  std::vector<QInst> qi(B);
+  for (int32_t i = 0; i < B; ++i) {
+    const InstInfo& in = G.inst[i];
+    qi[i] = QInst{in.n, in.T, in.soff, S.gn_h[i], S.gd_h[i], S.on_h[i], S.od_h[i]};
+  }
+  check_cuda(cudaMemcpyAsync(dqi, qi.data(), B * sizeof(QInst), cudaMemcpyHostToDevice, c.stream), "copy");
+  check_cuda(cudaMemsetAsync(acc, 0, (2 * (size_t)B + 2 * (size_t)G.T) * sizeof(ull), c.stream), "memset");
+  if (G.N > 0) launch(c, k_IJ, dim3(gsz(G.N * 32)), dim3(256), 0, g, labels0, acc, B);
   const size_t smem = G.T <= 1024 ? 2 * (size_t)G.T * sizeof(ull) : 0;
   const int64_t span = S.sig.d ? S.sig.rows * S.sig.T : (int64_t)S.sig.h.cap;
-  launch(c, k_S, dim3(gsz(span)), dim3(256), smem, S.sig, G.T, acc + 2);
-  launch(c, k_Q, dim3(1), dim3(1), 0, (const ull*)acc, (const ull*)(acc + 2), (const int64_t*)G.two_m, G.T, G.n,
-         S.p.gn, S.p.gd, S.p.on, S.p.od, dQ);
-  *Q = *static_cast<const double*>(readback(c, dQ, sizeof(double)));
+  launch(c, k_S, dim3(gsz(span)), dim3(256), smem, S.sig, G.T, acc + 2 * B);
+  launch(c, k_Q, dim3(grid_for(B, 128)), dim3(128), 0, (const ull*)acc, (const ull*)(acc + 2 * B),
+         (const int64_t*)G.two_m, (const QInst*)dqi, B, dQ);
+  check_cuda(cudaMemcpyAsync(c.pinned, dQ, B * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "copy");
+  sync(c);
+  std::memcpy(Q, c.pinned, B * sizeof(double));
 }
 
 void canonicalise(Solver& S, const int32_t* x, int32_t* out, int64_t N) {
@@ -161,8 +202,12 @@ void canonicalise(Solver& S, const int32_t* x, int32_t* out, int64_t N) {
   launch(c, k_first, dim3(gsz(N)), dim3(256), 0, x, N, first);
   int32_t* flag = S.freelist;
   launch(c, k_first_flag, dim3(gsz(N)), dim3(256), 0, x, (const int32_t*)first, N, flag);
-  scan_excl(c, flag, rank, N, (int32_t*)nullptr);
-  launch(c, k_canon, dim3(gsz(N)), dim3(256), 0, x, (const int32_t*)first, (const int32_t*)rank, N, out);
+  // rank has N + 1 entries: rank[N] counts every community
+  check_cuda(cudaMemsetAsync(flag + N, 0, sizeof(int32_t), c.stream), "memset");
+  scan_excl(c, flag, rank, N + 1, (int32_t*)nullptr);
+  const SupraGraph& G = *S.G0;
+  launch(c, k_canon, dim3(gsz(N)), dim3(256), 0, x, (const int32_t*)first, (const int32_t*)rank, N,
+         (const int32_t*)G.inst0, (const int32_t*)G.inst_off0, out);
 }
 
 int64_t count_distinct(Solver& S, const int32_t* x, int64_t N) {

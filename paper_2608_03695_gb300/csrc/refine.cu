@@ -28,17 +28,18 @@ __device__ __forceinline__ u128 lam_k_x(const u128* lam, int32_t s, long long k,
 }
 
 // Per node: W(v,C\v), eligibility, initial sub-community state.
-__global__ void k_ref_init(LevelDev g, const int32_t* P, SigStore sig, const u128* lam, long long od, int32_t* R,
-                           int32_t* sizeR, long long* Wc, long long* Wout, uint8_t* elig, SigStore kr) {
+__global__ void k_ref_init(LevelDev g, const int32_t* P, SigStore sig, const u128* lam, int32_t* R, int32_t* sizeR,
+                           long long* Wc, long long* Wout, uint8_t* elig, SigStore kr) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t v = (((int64_t)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); v < g.N; v += warps) {
     const int32_t C = P[v];
+    const Omega om = node_omega(g, (int32_t)v);
     long long w = 0;
     for (int64_t e = g.rowptr[v] + lane; e < g.rowptr[v + 1]; e += 32) {
       int32_t u;
       long long W;
-      if (edge_at(g, e, u, W) && P[u] == C) w += W;
+      if (edge_at(g, e, u, W, om) && P[u] == C) w += W;
     }
     w = warp_sum(w);
     if (lane == 0) {
@@ -56,14 +57,14 @@ __global__ void k_ref_init(LevelDev g, const int32_t* P, SigStore sig, const u12
         rhs += lam_k_x(lam, s, k, ss_get(sig, C, s) - k);
         ss_add(kr, (int32_t)v, s, k);
       }
-      elig[v] = ((((i128)w) << P_BITS) - (i128)((u128)(ull)od * rhs)) >= 0 ? 1 : 0;
+      elig[v] = ((((i128)w) << P_BITS) - (i128)((u128)(ull)om.od * rhs)) >= 0 ? 1 : 0;
     }
   }
 }
 
-__global__ void k_classes(int32_t N, uint64_t seed, uint64_t it, uint64_t lvl, int K, uint8_t* cls) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x)
-    cls[v] = (uint8_t)vertex_class(seed, 1, it, lvl, 0, (uint64_t)v, K);
+__global__ void k_classes(LevelDev g, uint64_t seed, uint64_t it, uint64_t lvl, int K, uint8_t* cls) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += (int64_t)gridDim.x * blockDim.x)
+    cls[v] = (uint8_t)vertex_class(seed, 1, it, lvl, 0, local_id(g, (int32_t)v), K);
 }
 
 __global__ void k_zero_rhs(ull* rhs, int64_t n2) {
@@ -86,15 +87,18 @@ __global__ void k_rhs_accum(SigStore kr, const int32_t* sizeR, const int32_t* P,
   }
 }
 
-__global__ void k_wc(int32_t N, const int32_t* sizeR, const long long* Wout, const ull* rhs, const uint8_t* elig,
-                     long long od, uint8_t* wc) {
-  for (int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; L < N; L += (int64_t)gridDim.x * blockDim.x) {
+// (A sub-community label L is a node of the level, so its omega is that
+// node's instance's.)
+__global__ void k_wc(LevelDev g, const int32_t* sizeR, const long long* Wout, const ull* rhs, const uint8_t* elig,
+                     uint8_t* wc) {
+  for (int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; L < g.N; L += (int64_t)gridDim.x * blockDim.x) {
     const int32_t sz = sizeR[L];
     uint8_t f = 0;
     if (sz == 1) {
       f = elig[L];
     } else if (sz > 1) {
       const u128 x = ((u128)rhs[2 * L + 1] << 64) | rhs[2 * L];
+      const long long od = node_omega(g, (int32_t)L).od;
       f = ((((i128)Wout[L]) << P_BITS) - (i128)((u128)(ull)od * x)) >= 0 ? 1 : 0;
     }
     wc[L] = f;
@@ -114,7 +118,6 @@ struct RefPolicy {
   const u128* lam;
   int32_t* target;
   long long* Wsel;
-  long long od;
   int q;
 
   struct Probe {
@@ -127,6 +130,7 @@ struct RefPolicy {
     int32_t s;
     bool single;
     long long k;
+    Omega om;
     u128 A;
   };
 
@@ -137,17 +141,18 @@ struct RefPolicy {
     c.s = 0;
     c.k = 0;
     c.A = 0;
+    c.om = node_omega(g, v);
     if (c.single) {
       c.k = g.k0[v];
-      c.s = v / g.n;
-      if (c.k > 0) c.A = (u128)(ull)od * lam[c.s] * (u128)(ull)c.k;
+      c.s = node_slice0(g, v);
+      if (c.k > 0) c.A = (u128)(ull)c.om.od * lam[c.s] * (u128)(ull)c.k;
     }
     return c;
   }
   __device__ void skip(int32_t v) const { target[v] = NO_MOVE; }
-  __device__ bool edge(int32_t v, int64_t e, int32_t& key, long long& w) const {
+  __device__ bool edge(int32_t v, const VCtx& vc, int64_t e, int32_t& key, long long& w) const {
     int32_t u;
-    if (!edge_at(g, e, u, w)) return false;
+    if (!edge_at(g, e, u, w, vc.om)) return false;
     if (P[u] != P[v]) return false;
     key = R[u];
     return true;
@@ -181,7 +186,7 @@ struct RefPolicy {
         slice_entry(g, v, j, s, k);
         ns += lam_k_x(lam, s, k, sst_get<DENSE>(kr, X, s));
       }
-      G = (((i128)W) << P_BITS) - (i128)((u128)(ull)od * ns);
+      G = (((i128)W) << P_BITS) - (i128)((u128)(ull)vc.om.od * ns);
     }
     if (G <= 0) return Cand{0, INT32_MAX};
     return Cand{G, X};
@@ -230,10 +235,11 @@ __global__ void k_ref_apply(LevelDev g, Segs3 sg, const int32_t* P, const int32_
     const int32_t t = target[v];
     if (t < 0) continue;
     long long wp = 0;
+    const Omega om = node_omega(g, v);
     for (int64_t e = g.rowptr[v] + lane; e < g.rowptr[v + 1]; e += 32) {
       int32_t u;
       long long W;
-      if (edge_at(g, e, u, W) && target[u] == t && P[u] == P[v]) wp += W;
+      if (edge_at(g, e, u, W, om) && target[u] == t && P[u] == P[v]) wp += W;
     }
     wp = warp_sum(wp);
     if (lane == 0) {
@@ -277,8 +283,8 @@ static void refine_impl(Solver& S, const Level& L, const int32_t* P, int it, int
   const int32_t N = L.d.N;
   if (N == 0) return;
   clear_store(S, S.kr);
-  launch(c, k_ref_init, dim3(fixed_grid(8)), dim3(256), 0, L.d, P, S.sig, (const u128*)S.lam, S.p.od, S.R, S.sizeR,
-         S.Wc, S.Wout, S.elig, S.kr);
+  launch(c, k_ref_init, dim3(fixed_grid(8)), dim3(256), 0, L.d, P, S.sig, (const u128*)S.lam, S.R, S.sizeR, S.Wc,
+         S.Wout, S.elig, S.kr);
   bucket(S, L, 1, it, lvl, 0);
   RefPolicy<DENSE> pol;
   pol.g = L.d;
@@ -291,9 +297,8 @@ static void refine_impl(Solver& S, const Level& L, const int32_t* P, int it, int
   pol.lam = S.lam;
   pol.target = S.target;
   pol.Wsel = S.Wsel;
-  pol.od = S.p.od;
   pol.cls = S.cls;
-  launch(c, k_classes, dim3(fixed_grid(8)), dim3(256), 0, N, S.p.seed, (uint64_t)it, (uint64_t)lvl, S.p.K, S.cls);
+  launch(c, k_classes, dim3(fixed_grid(8)), dim3(256), 0, L.d, S.p.seed, (uint64_t)it, (uint64_t)lvl, S.p.K, S.cls);
   for (int q = 0; q < S.p.K; ++q) {
     // well-connectedness of every sub-community at the sub-round start
     if (q > 0) {
@@ -301,8 +306,8 @@ static void refine_impl(Solver& S, const Level& L, const int32_t* P, int it, int
       launch(c, k_rhs_accum, dim3(fixed_grid(8)), dim3(256), 0, S.kr, (const int32_t*)S.sizeR, P, S.sig,
              (const u128*)S.lam, S.rhs);
     }
-    launch(c, k_wc, dim3(fixed_grid(8)), dim3(256), 0, N, (const int32_t*)S.sizeR, (const long long*)S.Wout,
-           (const ull*)S.rhs, (const uint8_t*)S.elig, S.p.od, S.wc);
+    launch(c, k_wc, dim3(fixed_grid(8)), dim3(256), 0, L.d, (const int32_t*)S.sizeR, (const long long*)S.Wout,
+           (const ull*)S.rhs, (const uint8_t*)S.elig, S.wc);
     pol.q = q;
     const Segs3 sg = bucket_segments(S, q);
     decide_all(c, pol, sg, S.tier_cnt, S.gkeys, S.gvals, S.goff);

@@ -1,5 +1,7 @@
 // Per-call solver state and the phases of one Leiden solve.
 #pragma once
+#include <vector>
+
 #include "build.h"
 #include "level.h"
 
@@ -11,7 +13,16 @@ struct SolveParams {
   uint64_t seed = 0;
 };
 
-struct PhaseTimer;
+// CUDA-event phase timing: events recorded on the context's stream.
+struct PhaseClock {
+  Ctx& c;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> spans;
+  explicit PhaseClock(Ctx& cc) : c(cc) {}
+  ~PhaseClock();
+  cudaEvent_t begin();
+  void end(int phase, cudaEvent_t b);
+  void totals(double out[5]);  // total ms per phase
+};
 
 struct Solver {
   Ctx* c = nullptr;
@@ -34,6 +45,14 @@ struct Solver {
   ull* sig_used = nullptr;      // Sigma slots taken since its last rebuild
   int32_t empty_grid = 0;       // co-resident grid of the empty-community pass
   int32_t* empty_blk = nullptr;
+  int32_t* inst_cnt = nullptr;  // per-instance counts of the empty-community pass
+
+  // batch: B independent instances (1 for a single solve) and their
+  // resolution / coupling rationals (host copies; device copies below)
+  int32_t B = 1;
+  std::vector<long long> gn_h, gd_h, on_h, od_h;
+  long long *gn_d = nullptr, *gd_d = nullptr, *on_d = nullptr, *od_d = nullptr;
+  int32_t* inst_active = nullptr;  // per instance: 1 while not converged (nullptr: all active)
   int64_t* goff = nullptr;      // global-tier table offsets
   int32_t* gkeys = nullptr;
   long long* gvals = nullptr;
@@ -100,15 +119,50 @@ bool aggregate(Solver& S, const Level& L, const int32_t* P, Level& next, const s
 // Rebuilds Sigma_{c,s} of `labels` at level L.
 void sigma_rebuild(Solver& S, const Level& L, const int32_t* labels);
 
-// Canonical labels (first occurrence order) of x[0, N) into out.
+// Canonical labels (first occurrence order within each instance) of x[0, N)
+// into out.
 void canonicalise(Solver& S, const int32_t* x, int32_t* out, int64_t N);
 
-// Q_MS of level-0 labels with the true gamma; result in *Q (host).
+// Q_MS of level-0 labels with the true gamma, one value per instance (host
+// array of B doubles).
 void modularity(Solver& S, const int32_t* labels0, double* Q);
 
 // Order-free checksum of a level (debug stage 3).
 uint64_t level_checksum(Solver& S, const Level& L);
 
 LevelDev level0_view(const SupraGraph& G, long long on, long long od);
+// The level-0 view of a solve: batch maps and per-instance omega included.
+LevelDev level0_view(const SupraGraph& G, const Solver& S);
+
+// Fails with MSLICE_EINVAL unless every level-0 label d[v] (device) lies in
+// [0, size of v's instance).
+void check_label_ranges(Ctx& c, const SupraGraph& G, const int32_t* d);
+
+// Per-instance resolution and coupling of a solve.
+struct InstParams {
+  long long gn = 1, gd = 1, on = 1, od = 1;
+};
+
+// Output of run_leiden.
+struct RunOut {
+  std::vector<double> Q;  // per instance
+  int64_t out_n = 0;      // labels written (N, or a debug level's size)
+  int64_t levels = 0, iterations = 0, stop_reason = 0, last_level0_moves = 0;
+  int64_t next_n = 0, next_nnz = 0;
+  uint64_t next_checksum = 0;
+  double ms[5] = {0, 0, 0, 0, 0};  // total, local moving, refinement, aggregation, Q
+};
+
+// Per-instance rationals of a solve into S (host and device copies); B =
+// jobs.size() must equal the instance count of the graph.
+void set_instances(Ctx& c, Solver& S, const std::vector<InstParams>& jobs);
+
+// Leiden over the instances of G (each with its InstParams).  init (device,
+// nullable): level-0 labels, numbered from 0 within each instance.  out
+// (device, N): canonical labels, numbered from 0 within each instance.  Debug stops
+// (single instance) write a level's raw labels instead.
+void run_leiden(Ctx& c, const SupraGraph& G, const std::vector<InstParams>& jobs, const SolveParams& p,
+                int stop_level, int stop_stage, int stop_rounds, const int32_t* init, int32_t* out, Solver& S,
+                RunOut& ro);
 
 }  // namespace mslice

@@ -52,6 +52,15 @@ def test_host_side_rejections_need_no_gpu():
     assert L.mslice_leiden_ex(None, None, None, None, None, None) == pkg.MSLICE_EINVAL
     assert b"handle" in L.mslice_last_error()
     L.mslice_free(None)
+    # batch entry points: null batches are rejected before any CUDA call
+    assert L.mslice_batch_add(None, None, 1, 1, 1, 1, None, None) == pkg.MSLICE_EINVAL
+    assert L.mslice_batch_run(None, None, None) == pkg.MSLICE_EINVAL
+    assert L.mslice_batch_results(None, 0, None, None) == pkg.MSLICE_EINVAL
+    assert L.mslice_batch_info(None, None, None, None) == pkg.MSLICE_EINVAL
+    assert L.mslice_batch_clear(None) == pkg.MSLICE_EINVAL
+    assert L.mslice_batch_kernel_launches(None) == -1
+    assert L.mslice_batch_create(0, None, None) == pkg.MSLICE_EINVAL
+    L.mslice_batch_free(None)
 
 
 def test_struct_layouts_match_header():
