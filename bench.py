@@ -11,6 +11,14 @@ local-moving rounds of the level's directed entries, divided by the whole
 step's device time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mslice|reference]
+  python bench.py --workload batched [--scale S]
+
+The batched workload (64 temporal planted-partition graphs of uneven n and
+T, each solved at 6 gammas x 3 omegas = 1,152 solves) is timed twice on the
+same GPU: every solve as its own call (the plain path) and the solves packed
+into batches (mslice_batch_*).  Both report the plain path's local-moving
+supra-edges per second of wall time, and the batched labels and Q must equal
+the plain ones bit for bit.
 
 The reference arm is the CPU oracle (single thread) on a bounded sample of
 the same recipe.  With N > 1 (torchrun) every rank solves its own replica;
@@ -25,6 +33,8 @@ import statistics
 import subprocess
 import sys
 import time
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -46,6 +56,9 @@ def parse():
     ap.add_argument("--impl", default="mslice", choices=["mslice", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched"])
+    ap.add_argument("--scale", type=float, default=1.0, help="batched workload: node-count scale of every graph")
+    ap.add_argument("--graphs", type=int, default=None, help="batched workload: first G graphs only")
     ap.add_argument("--profile-run", action="store_true",
                     help="one solve of the workload and exit (a short target for ncu captures)")
     return ap.parse_args()
@@ -167,10 +180,113 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _gen_batched(spec):
+    from paper_2608_03695_gb300 import synth
+    return synth.batched_graph(spec)
+
+
+# per batch: at most this many supra-nodes and stored entries (about 250 B per
+# supra-node and 52 B per entry of device memory while solving)
+BATCH_MAX_NODES = 1 << 27
+BATCH_MAX_ENTRIES = 1 << 30
+
+
+def run_batched(args):
+    import multiprocessing as mp
+    import hashlib
+    from paper_2608_03695_gb300 import synth
+    specs = synth.batched_specs(args.scale, args.graphs)
+    t = time.perf_counter()
+    # the pool starts (spawn) before this process touches CUDA
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        graphs = pool.map(_gen_batched, specs, chunksize=1)
+    t_gen = time.perf_counter() - t
+    import torch
+    import paper_2608_03695_gb300 as pkg
+    torch.cuda.set_device(0)
+    handles = [pkg.mslice_build(g) for g in graphs]
+    solves = [(gi, gm, om) for gi in range(len(graphs)) for gm in synth.BATCHED_GAMMAS for om in synth.BATCHED_OMEGAS]
+    N_sum = sum(h.N for h in handles) * len(synth.BATCHED_GAMMAS) * len(synth.BATCHED_OMEGAS)
+
+    def digest(lab, Q):
+        return hashlib.sha1(np.ascontiguousarray(lab, dtype=np.int32).tobytes()).hexdigest(), Q
+
+    # warm-up: one small solve each way
+    handles[0].mslice_leiden()
+    with pkg.Batch() as b:
+        b.add(handles[0])
+        b.run()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    # plain path: one call per solve
+    t = time.perf_counter()
+    plain, work, launches_plain = [], 0, 0
+    for gi, gm, om in solves:
+        lab, Q, st = handles[gi].mslice_leiden(gamma=gm, omega=om)
+        plain.append(digest(lab, Q))
+        work += st["lm_edges"]
+        launches_plain += st["kernel_launches"]
+    t_plain = time.perf_counter() - t
+    # batched path: solves packed in add order under the per-batch budget
+    chunks, cur, cn, ce = [], [], 0, 0
+    for k, (gi, gm, om) in enumerate(solves):
+        h = handles[gi]
+        if cur and (cn + h.N > BATCH_MAX_NODES or ce + h.nnz > BATCH_MAX_ENTRIES):
+            chunks.append(cur)
+            cur, cn, ce = [], 0, 0
+        cur.append(k)
+        cn += h.N
+        ce += h.nnz
+    if cur:
+        chunks.append(cur)
+    t = time.perf_counter()
+    batched, launches_b = [None] * len(solves), 0
+    ms_dev = 0.0
+    for ch in chunks:
+        with pkg.Batch() as b:
+            for k in ch:
+                gi, gm, om = solves[k]
+                b.add(handles[gi], gm, om)
+            st = b.run()
+            launches_b += st["kernel_launches"]
+            ms_dev += st["ms_total"]
+            labs, Qs = b.results()
+            _, _, off = b.info()
+        for j, k in enumerate(ch):
+            batched[k] = digest(labs[off[j]:off[j + 1]], float(Qs[j]))
+    t_batch = time.perf_counter() - t
+    clk = clocks.stop()
+    same = all(a == b for a, b in zip(plain, batched))
+    for h in handles:
+        h.close()
+    v_plain, v_batch = work / t_plain, work / t_batch
+    cfg = {"workload": "batched multislice Leiden: 64 temporal planted-partition graphs x 6 gamma x 3 omega",
+           "graphs": len(graphs), "solves": len(solves), "n": "log-uniform 1k-200k" + (f" x {args.scale}" if args.scale != 1 else ""),
+           "T": "uniform 2-32", "mean_deg": "uniform 8-32", "weights": "1-8",
+           "gamma": [f"{a}/{b}" for a, b in synth.BATCHED_GAMMAS], "omega": [f"{a}/{b}" for a, b in synth.BATCHED_OMEGAS],
+           "supra_nodes_per_graph_sum": sum(g[0].n * len(g) for g in graphs),
+           "supra_nodes_solved": N_sum, "batches": len(chunks), "n_iterations": 2, "K": 4, "seed": 0,
+           "parallelism": "single", "l2": "inputs larger than L2"}
+    line = {"metric": "supra-edges/s in Leiden local-move, batched vs plain", "value": v_batch, "unit": UNIT,
+            "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * t_batch, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic", "config": cfg,
+            "plain": {"value": v_plain, "unit": UNIT, "seconds": t_plain, "gpu_launches": launches_plain},
+            "batched": {"value": v_batch, "unit": UNIT, "seconds": t_batch, "gpu_launches": launches_b,
+                        "device_ms": ms_dev},
+            "batched_over_plain": v_batch / v_plain, "identical_results": same,
+            "work_supra_edges": work, "generate_s": t_gen, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    if not same:
+        raise SystemExit("batched results differ from the plain solves")
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     import torch
     import paper_2608_03695_gb300 as pkg
     from paper_2608_03695_gb300 import synth

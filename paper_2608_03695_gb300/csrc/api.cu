@@ -114,6 +114,7 @@ static void trace_report(Ctx& c) {
 }
 
 void* readback(Ctx& c, const void* dptr, size_t bytes) {
+  if (bytes > PINNED_BYTES) fail(MSLICE_ECUDA, "readback larger than the pinned staging buffer");
   check_cuda(cudaMemcpyAsync(c.pinned, dptr, bytes, cudaMemcpyDeviceToHost, c.stream), "readback");
   sync(c);
   return c.pinned;
@@ -341,7 +342,7 @@ int mslice_build_ex(const mslice_csr* slices, int32_t T, mslice_coupling cpl, in
     keep_pool_memory();
     h->on = omega_num;
     h->od = omega_den;
-    check_cuda(cudaMallocHost(&h->pinned, 4096), "pinned buffer");
+    check_cuda(cudaMallocHost(&h->pinned, PINNED_BYTES), "pinned buffer");
     h->d_status = h->ws.get<unsigned>("status", 4);
     Ctx c = h->ctx();
     check_cuda(cudaMemsetAsync(h->d_status, 0, 16, c.stream), "memset");
@@ -528,7 +529,7 @@ int mslice_batch_create(int32_t flags, void* stream, mslice_batch* out) {
     b->ws.stream = b->stream;
     b->G.mem.stream = b->stream;
     keep_pool_memory();
-    check_cuda(cudaMallocHost(&b->pinned, 4096), "pinned buffer");
+    check_cuda(cudaMallocHost(&b->pinned, PINNED_BYTES), "pinned buffer");
     b->d_status = b->ws.get<unsigned>("status", 4);
     check_cuda(cudaMemsetAsync(b->d_status, 0, 16, b->stream), "memset");
     sync_stream(b->stream);

@@ -85,7 +85,11 @@ inline unsigned grid_for(int64_t n, int per_block) {
   return (unsigned)(g < 1 ? 0 : g);
 }
 
-// Reads `bytes` from device memory into the pinned buffer and synchronises.
+// Size of every handle's pinned staging buffer (Ctx::pinned).
+constexpr size_t PINNED_BYTES = 4096;
+
+// Reads `bytes` (at most PINNED_BYTES) from device memory into the pinned
+// buffer and synchronises.
 void* readback(Ctx& c, const void* dptr, size_t bytes);
 void sync(Ctx& c);
 // Synchronises and throws if the device status word holds an error bit.

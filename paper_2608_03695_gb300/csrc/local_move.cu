@@ -235,8 +235,18 @@ __device__ __forceinline__ int seg_total(const Segs& sg) {
 // Applies the sub-round's decisions: labels, community sizes and Sigma, and
 // resets each applied decision.  Moves to an empty community only leave here
 // (their label is assigned by k_empty_pass).
+// lm_active[i] stays 1 only for instances that moved in the round; clears
+// the flags for the next round.
+__global__ void k_round_freeze(int32_t* lm_active, int32_t* inst_moved, int32_t B) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < B) {
+    if (!inst_moved[i]) lm_active[i] = 0;
+    inst_moved[i] = 0;
+  }
+}
+
 __global__ void k_lm_apply(LevelDev g, Segs sg, int32_t* labels, int32_t* size, SigStore sig, int32_t* target,
-                           int32_t* counters) {
+                           int32_t* counters, int32_t* inst_moved) {
   const int total = seg_total(sg);
   int local = 0, local_empty = 0;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -245,6 +255,7 @@ __global__ void k_lm_apply(LevelDev g, Segs sg, int32_t* labels, int32_t* size, 
     if (!seg_item(sg, idx, v)) break;
     const int32_t t = target[v];
     if (t == NO_MOVE) continue;
+    if (inst_moved) inst_moved[node_inst(g, v)] = 1;
     const int32_t a = labels[v];
     atomicSub(&size[a], 1);
     int64_t b, e;
@@ -464,6 +475,9 @@ void solver_alloc(Solver& S) {
   check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attribute");
   S.empty_grid = std::max(1, std::min(max_blocks, 2) * sms);
   S.empty_blk = c.ws->get<int32_t>("s_empty_blk", 2 * S.empty_grid);
+  S.lm_active = c.ws->get<int32_t>("s_lm_active", S.B);
+  S.inst_moved = c.ws->get<int32_t>("s_inst_moved", S.B);
+  check_cuda(cudaMemsetAsync(S.inst_moved, 0, S.B * sizeof(int32_t), c.stream), "memset");
   S.inst_cnt = c.ws->get<int32_t>("s_inst_cnt", 4 * (size_t)S.B + 2);
   check_cuda(cudaMemsetAsync(S.inst_cnt, 0, (4 * (size_t)S.B + 2) * sizeof(int32_t), c.stream), "memset");
   fill_i32(c, S.target, NO_MOVE, N);
@@ -572,15 +586,14 @@ TierSegs bucket_segments(Solver& S, int q) {
   return sg;
 }
 
-void bucket(Solver& S, const Level& L, uint64_t tag, int it, int lvl, int r) {
+void bucket(Solver& S, const Level& L, uint64_t tag, int it, int lvl, int r, const int32_t* active) {
   Ctx& c = *S.c;
   check_cuda(cudaMemsetAsync(S.cursors, 0, NTIERS * S.p.K * sizeof(int32_t), c.stream), "memset");
   TierOff to;
   for (int t = 0; t < NTIERS; ++t) to.off[t] = S.tier_off[t];
   if (L.d.N > 0)
     launch(c, k_bucket, dim3(grid_for(L.d.N, 256)), dim3(256), 0, L.d, (const uint8_t*)S.tier, S.p.seed, tag,
-           (uint64_t)it, (uint64_t)lvl, (uint64_t)r, S.p.K, S.lists, (int64_t)S.N0, to, S.cursors,
-           (const int32_t*)S.inst_active);
+           (uint64_t)it, (uint64_t)lvl, (uint64_t)r, S.p.K, S.lists, (int64_t)S.N0, to, S.cursors, active);
 }
 
 MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, int max_rounds) {
@@ -619,11 +632,18 @@ MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, 
     else
       decide_all(c, polh, sg, S.tier_cnt, S.gkeys, S.gvals, S.goff);
   };
+  // Batch: an instance whose round moved nothing is at a fixed point of
+  // this level (its decisions read only its own state, which no longer
+  // changes), so it is left out of the remaining rounds.
+  const bool batch = S.B > 1;
+  if (batch)
+    check_cuda(cudaMemcpyAsync(S.lm_active, S.inst_active, S.B * sizeof(int32_t), cudaMemcpyDeviceToDevice, c.stream),
+               "copy");
   bool rebuild = false;
   for (int r = 0; r < max_rounds; ++r) {
     if (rebuild) rebuild_sigma(S, L, labels, false);
     check_cuda(cudaMemsetAsync(S.counters, 0, 3 * sizeof(int32_t), c.stream), "memset");
-    bucket(S, L, 0, it, lvl, r);
+    bucket(S, L, 0, it, lvl, r, batch ? S.lm_active : S.inst_active);
     S.lm_rounds++;
     S.lm_edges += L.nnz_eff;
     const bool prof = c.profile && lvl == 0;
@@ -642,10 +662,12 @@ MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, 
         decide(sg);
       }
       launch(c, k_lm_apply, dim3(fixed_grid(4)), dim3(APPLY_THREADS), 0, L.d, sg, labels, S.size, S.sig, S.target,
-             S.counters);
+             S.counters, batch ? S.inst_moved : nullptr);
       launch_coop(c, k_empty_pass, dim3(S.empty_grid), dim3(EMPTY_THREADS), 0, L.d, S.B, S.target, labels, S.size,
                   S.sig, S.counters, S.empty_blk, S.freelist, S.tmp32b, S.inst_cnt);
     }
+    if (batch)
+      launch(c, k_round_freeze, dim3(grid_for(S.B, 256)), dim3(256), 0, S.lm_active, S.inst_moved, S.B);
     struct {
       int64_t moved;
       ull used;

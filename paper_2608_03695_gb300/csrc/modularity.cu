@@ -188,9 +188,9 @@ void modularity(Solver& S, const int32_t* labels0, double* Q) {
   launch(c, k_S, dim3(gsz(span)), dim3(256), smem, S.sig, G.T, acc + 2 * B);
   launch(c, k_Q, dim3(grid_for(B, 128)), dim3(128), 0, (const ull*)acc, (const ull*)(acc + 2 * B),
          (const int64_t*)G.two_m, (const QInst*)dqi, B, dQ);
-  check_cuda(cudaMemcpyAsync(c.pinned, dQ, B * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "copy");
+  // B values go straight to the caller's (pageable) array
+  check_cuda(cudaMemcpyAsync(Q, dQ, B * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "copy");
   sync(c);
-  std::memcpy(Q, c.pinned, B * sizeof(double));
 }
 
 void canonicalise(Solver& S, const int32_t* x, int32_t* out, int64_t N) {

@@ -274,7 +274,7 @@ unsigned fixed_grid(int per_sm) { return 152u * (unsigned)per_sm; }
 
 }  // namespace
 
-void bucket(Solver& S, const Level& L, uint64_t tag, int it, int lvl, int r);
+void bucket(Solver& S, const Level& L, uint64_t tag, int it, int lvl, int r, const int32_t* active);
 TierSegs bucket_segments(Solver& S, int q);
 
 template <bool DENSE>
@@ -285,7 +285,7 @@ static void refine_impl(Solver& S, const Level& L, const int32_t* P, int it, int
   clear_store(S, S.kr);
   launch(c, k_ref_init, dim3(fixed_grid(8)), dim3(256), 0, L.d, P, S.sig, (const u128*)S.lam, S.R, S.sizeR, S.Wc,
          S.Wout, S.elig, S.kr);
-  bucket(S, L, 1, it, lvl, 0);
+  bucket(S, L, 1, it, lvl, 0, S.inst_active);
   RefPolicy<DENSE> pol;
   pol.g = L.d;
   pol.P = P;

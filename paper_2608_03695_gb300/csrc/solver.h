@@ -53,6 +53,8 @@ struct Solver {
   std::vector<long long> gn_h, gd_h, on_h, od_h;
   long long *gn_d = nullptr, *gd_d = nullptr, *on_d = nullptr, *od_d = nullptr;
   int32_t* inst_active = nullptr;  // per instance: 1 while not converged (nullptr: all active)
+  int32_t* lm_active = nullptr;    // per instance: still moving in this level's local moving
+  int32_t* inst_moved = nullptr;   // per instance: moved in the current round
   int64_t* goff = nullptr;      // global-tier table offsets
   int32_t* gkeys = nullptr;
   long long* gvals = nullptr;

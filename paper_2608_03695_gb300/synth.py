@@ -56,7 +56,8 @@ def csr_from_edges(n: int, u: np.ndarray, v: np.ndarray, w: np.ndarray) -> Snaps
     src = np.concatenate([u, v])
     dst = np.concatenate([v, u])
     ww = np.concatenate([w, w])
-    order = np.lexsort((dst, src))
+    # (src, dst) pairs are distinct, so one sort of src*n + dst orders them
+    order = np.argsort(src * max(n, 1) + dst)
     src, dst, ww = src[order], dst[order], ww[order]
     counts = np.bincount(src, minlength=n) if n > 0 else np.zeros(0, np.int64)
     indptr = np.zeros(n + 1, dtype=np.int64)
@@ -103,6 +104,24 @@ def _tri_decode(k: np.ndarray):
     return i, j
 
 
+def _distinct_ints(rng, possible: int, m: int) -> np.ndarray:
+    """m distinct integers drawn uniformly from [0, possible).  Small
+    populations use numpy's sampler without replacement; large sparse ones
+    draw with replacement, drop repeats and draw again for the shortfall (the
+    same distribution: every m-subset is equally likely), then keep a random
+    m of them."""
+    if possible <= (1 << 22) or m * 4 > possible:
+        return rng.choice(possible, size=m, replace=False)
+    out = np.zeros(0, np.int64)
+    while len(out) < m:
+        need = m - len(out)
+        x = rng.integers(0, possible, size=need + need // 50 + 16, dtype=np.int64)
+        out = _sorted_unique(np.concatenate([out, x]))
+    if len(out) > m:
+        out = out[rng.permutation(len(out))[:m]]
+    return out
+
+
 def _sample_block_pairs(rng, members_a, members_b, p, same):
     """Distinct node pairs between two blocks, each present with prob. p."""
     na, nb = len(members_a), len(members_b)
@@ -112,7 +131,7 @@ def _sample_block_pairs(rng, members_a, members_b, p, same):
     m = int(rng.binomial(possible, min(p, 1.0)))
     if m == 0:
         return np.zeros(0, np.int64), np.zeros(0, np.int64)
-    idx = rng.choice(possible, size=m, replace=False)
+    idx = _distinct_ints(rng, possible, m)
     if same:
         i, j = _tri_decode(idx)
         return members_a[i], members_a[j]
@@ -362,6 +381,40 @@ CONFIGS = {
     4: dict(kind="dcsbm", n=1_000_000, T=64, deg_exp=2.3, mean_deg=16.0, size_exp=1.5, size_min=20,
             size_max=5000, mixing=0.4, churn=0.05, w_max=16, seed=4, gamma=(1, 1), omega=(1, 1)),
 }
+
+
+# Batched workload: 64 independent temporal planted-partition graphs (the
+# generator of config 1: 4 equal blocks, p_out = p_in / 10, 10% of the nodes
+# switch block between snapshots), n log-uniform in [1k, 200k], T uniform in
+# [2, 32], mean degree uniform in [8, 32], weights 1..8; every graph is solved
+# at each (gamma, omega) of the grid below (1,152 solves).
+BATCHED = dict(n_graphs=64, n_lo=1000, n_hi=200_000, T_lo=2, T_hi=32, deg_lo=8.0, deg_hi=32.0, w_max=8, seed=3)
+BATCHED_GAMMAS = [(1, 2), (3, 4), (1, 1), (5, 4), (3, 2), (2, 1)]
+BATCHED_OMEGAS = [(1, 10), (1, 1), (10, 1)]
+
+
+def batched_specs(scale_n: float = 1.0, n_graphs: int | None = None):
+    """(n, T, p_in, seed) of every graph of the batched workload (n scaled by
+    scale_n, at least 8)."""
+    c = BATCHED
+    rng = np.random.default_rng(c["seed"])
+    specs = []
+    for g in range(c["n_graphs"] if n_graphs is None else n_graphs):
+        n = float(np.exp(rng.uniform(np.log(c["n_lo"]), np.log(c["n_hi"]))))
+        T = int(rng.integers(c["T_lo"], c["T_hi"] + 1))
+        d = float(rng.uniform(c["deg_lo"], c["deg_hi"]))
+        n = max(8, int(round(n * scale_n)))
+        # expected degree with 4 equal blocks and p_out = p_in/10:
+        # p_in (n/4 - 1) + (p_in/10)(3n/4)
+        p_in = min(1.0, d / (n / 4 - 1 + 0.075 * n))
+        specs.append((n, T, p_in, 1000 * c["seed"] + g))
+    return specs
+
+
+def batched_graph(spec):
+    n, T, p_in, seed = spec
+    snaps, _ = planted_partition_temporal(n, T, 4, p_in, p_in / 10, 0.10, None, BATCHED["w_max"], seed)
+    return snaps
 
 
 def config_graph(cfg: int | dict, scale_n: int | None = None, T: int | None = None):

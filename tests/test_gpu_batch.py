@@ -190,3 +190,20 @@ def test_batch_rejects_bad_input():
         b.run()
         lab, Q = b.results(0)
         assert np.array_equal(lab, oracle.leiden(snaps)[0])
+
+
+def test_many_tiny_instances():
+    """More instances than fit any fixed host staging area (600 Q values),
+    each against the oracle."""
+    handles, instances = [], []
+    rng = np.random.default_rng(77)
+    for k in range(600):
+        n, T = int(rng.integers(1, 25)), int(rng.integers(1, 4))
+        snaps = synth.random_temporal(n, T, p=float(rng.uniform(0.05, 0.5)), w_max=3, seed=k)
+        h = pkg.mslice_build(snaps)
+        handles.append(h)
+        instances.append((h, snaps, [(1, 1), (3, 2), (1, 2)][k % 3], [(1, 1), (0, 1), (2, 1)][(k // 3) % 3], None))
+    out, _ = run_batch(instances)
+    check_against_oracle(instances, out)
+    for h in handles:
+        h.close()
