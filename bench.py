@@ -12,6 +12,7 @@ step's device time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mslice|reference]
   python bench.py --workload batched [--scale S]
+  python bench.py --workload serving [--scale S] [--requests R] [--slots K]
 
 The batched workload (64 temporal planted-partition graphs of uneven n and
 T, each solved at 6 gammas x 3 omegas = 1,152 solves) is timed twice on the
@@ -56,7 +57,9 @@ def parse():
     ap.add_argument("--impl", default="mslice", choices=["mslice", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving"])
+    ap.add_argument("--requests", type=int, default=4, help="serving workload: timed snapshots per graph")
+    ap.add_argument("--slots", type=int, default=2, help="serving workload: server workers")
     ap.add_argument("--scale", type=float, default=1.0, help="batched workload: node-count scale of every graph")
     ap.add_argument("--graphs", type=int, default=None, help="batched workload: first G graphs only")
     ap.add_argument("--profile-run", action="store_true",
@@ -281,12 +284,166 @@ def run_batched(args):
         raise SystemExit("batched results differ from the plain solves")
 
 
+def _gen_serving(job):
+    from paper_2608_03695_gb300 import synth
+    spec, steps = job
+    return synth.serving_stream(spec, steps)
+
+
+def run_serving(args):
+    """Serving workload: 32 live graphs with windows of 8 slices.  The first
+    8 snapshots of every graph fill the windows (untimed); then R snapshots per
+    graph arrive as a Poisson process at the recipe's rate (open loop) and
+    latency is taken per request (submit to done).  The same R x 32 requests
+    are then timed as one burst on a fresh server (capacity) and one by one
+    through mslice_build + mslice_leiden_ex (the plain per-instance path);
+    all three must give the same labels."""
+    import multiprocessing as mp
+    import hashlib
+    from paper_2608_03695_gb300 import synth
+    W = synth.SERVING["window"]
+    specs = synth.serving_specs(args.scale, args.graphs)
+    steps = W + args.requests
+    t = time.perf_counter()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        streams = pool.map(_gen_serving, [(sp, steps) for sp in specs], chunksize=1)
+    t_gen = time.perf_counter() - t
+    import torch
+    import paper_2608_03695_gb300 as pkg
+    torch.cuda.set_device(0)
+    G = len(streams)
+    rng = np.random.default_rng(11)
+
+    def digest(lab):
+        return hashlib.sha1(np.ascontiguousarray(lab, dtype=np.int32).tobytes()).hexdigest()
+
+    def prefill(srv):
+        ids = [srv.add_graph(s[0].n) for s in streams]
+        for t in range(W):
+            rids = [srv.submit(ids[g], streams[g][t]) for g in range(G)]
+            for r in rids:
+                srv.wait(r)
+        return ids
+
+    # timed requests: graph g's snapshots W..W+R-1 in a random interleaving
+    order = [g for g in range(G) for _ in range(args.requests)]
+    rng.shuffle(order)
+    seq, nxt = [], [W] * G
+    for g in order:
+        seq.append((g, nxt[g]))
+        nxt[g] += 1
+    rate = synth.SERVING["rate_per_s"]
+    gaps = rng.exponential(1.0 / rate, size=len(seq))
+    clocks = ClockSampler(0)
+    clocks.start()
+    # open loop at the recipe's rate
+    with pkg.Server(window=W, n_slots=args.slots) as srv:
+        ids = prefill(srv)
+        t0 = time.perf_counter()
+        due = t0
+        rids = []
+        for (g, t), gap in zip(seq, gaps):
+            due += gap
+            d = due - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            rids.append(srv.submit(ids[g], streams[g][t]))
+        res = [srv.wait(r) for r in rids]
+        t_open = time.perf_counter() - t0
+    lat = np.array([i["t_done"] - i["t_submit"] for _, i in res])
+    open_digest = [digest(l) for l, _ in res]
+    batch_sizes = [i["batch_size"] for _, i in res]
+    slots_used = len({i["slot"] for _, i in res})
+    # overlap: total device-busy span of batches vs their summed durations
+    spans = sorted({(i["slot"], i["t_batch_start"], i["t_batch_end"]) for _, i in res}, key=lambda x: x[1])
+    busy = sum(e - b for _, b, e in spans)
+    union, cur_b, cur_e = 0.0, None, None
+    for _, b, e in spans:
+        if cur_e is None or b > cur_e:
+            if cur_e is not None:
+                union += cur_e - cur_b
+            cur_b, cur_e = b, e
+        else:
+            cur_e = max(cur_e, e)
+    if cur_e is not None:
+        union += cur_e - cur_b
+    # closed loop: all requests at once (capacity of the server)
+    with pkg.Server(window=W, n_slots=args.slots) as srv:
+        ids = prefill(srv)
+        t0 = time.perf_counter()
+        rids = [srv.submit(ids[g], streams[g][t]) for g, t in seq]
+        burst = [srv.wait(r) for r in rids]
+        t_burst = time.perf_counter() - t0
+    same = [digest(l) for l, _ in burst] == open_digest
+    # plain per-instance path: window build + warm-started solve, one by one
+    # (the prefill chain is replayed untimed to get the same warm starts)
+    prevs = {}
+    for g in range(G):
+        lab, n = None, streams[g][0].n
+        for t in range(W):
+            lab = _plain_window_solve(pkg, streams[g], t, W, lab, n)[0]
+        prevs[g] = lab
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = []
+    for g, t in seq:
+        n = streams[g][0].n
+        lab, _ = _plain_window_solve(pkg, streams[g], t, W, prevs[g], n)
+        prevs[g] = lab
+        plain.append(digest(lab))
+    t_plain = time.perf_counter() - t0
+    same = same and plain == open_digest
+    clk = clocks.stop()
+    nreq = len(seq)
+    cfg = {"workload": "serving: live temporal planted-partition graphs, sliding windows, Poisson arrivals",
+           "graphs": G, "window": W, "n": "log-uniform 10k-2M" + (f" x {args.scale}" if args.scale != 1 else ""),
+           "mean_deg": synth.SERVING["mean_deg"], "churn": synth.SERVING["churn"], "weights": "1-8",
+           "gamma": "1/1", "omega": "1/1", "rate_per_s": rate, "timed_requests": nreq,
+           "requests_per_graph": args.requests, "slots": args.slots, "n_iterations": 2, "K": 4, "seed": 0,
+           "parallelism": "single", "l2": "inputs larger than L2"}
+    line = {"metric": "served snapshots/s (Poisson arrivals) with p50/p99 latency", "value": nreq / t_open,
+            "unit": "snapshots/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * t_open,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": cfg,
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "max": float(lat.max()), "mean": float(lat.mean())},
+            "offered_per_s": rate, "achieved_per_s": nreq / t_open,
+            "capacity": {"value": nreq / t_burst, "unit": "snapshots/s", "note": "all timed requests at once"},
+            "plain": {"value": nreq / t_plain, "unit": "snapshots/s",
+                      "note": "one mslice_build + mslice_leiden_ex per request, same warm starts"},
+            "served_over_plain": (nreq / t_burst) / (nreq / t_plain),
+            "batching": {"mean_batch": float(np.mean(batch_sizes)), "max_batch": int(max(batch_sizes)),
+                         "slots_used": slots_used, "device_busy_s": busy, "busy_union_s": union,
+                         "overlap": busy / union if union > 0 else 1.0},
+            "identical_results": same, "generate_s": t_gen, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    if not same:
+        raise SystemExit("served results differ between open loop, burst and plain paths")
+
+
+def _plain_window_solve(pkg, snaps, t, W, prev, n):
+    """One request through the plain path: build the window's handle and run
+    mslice_leiden_ex from the warm-start labels."""
+    window = snaps[max(0, t + 1 - W):t + 1]
+    init = None
+    if prev is not None:
+        w_prev = len(prev) // n
+        e = 1 if w_prev == W else 0
+        src = np.minimum(np.arange(len(window)) + e, w_prev - 1)
+        init = np.concatenate([prev[s * n:(s + 1) * n] for s in src]).astype(np.int32)
+    with pkg.mslice_build(window) as h:
+        lab, Q, _ = h.mslice_leiden(init=init)
+    return lab, Q
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     import torch
     import paper_2608_03695_gb300 as pkg
     from paper_2608_03695_gb300 import synth

@@ -186,9 +186,9 @@ int mslice_modularity_noalloc(const mslice_csr* slices, int32_t T, const int32_t
 
 /* ---- Batches: many (graph, gamma, omega) solves in one pass ----
  *
- * The paper applies the method to many snapshot windows and parameter
- * choices (Sec. 4 sweeps gamma and omega; Sec. 5 notes that small graphs
- * leave the GPU underused).  A batch solves B independent instances together:
+ * Leiden's partition depends on the resolution gamma and the coupling omega
+ * (Sec. 3.2), so callers sweep them, and small graphs leave the GPU bound by
+ * launch overhead (Sec. 4).  A batch solves B independent instances together:
  * their supra-graphs are laid out one after another as the diagonal blocks of
  * one graph, every kernel launch of the level loop covers all instances, and
  * each instance keeps its own gamma, omega, snapshot masses and class hash
@@ -245,6 +245,80 @@ int64_t mslice_batch_kernel_launches(mslice_batch b);
 
 /* Releases the batch and its device memory (NULL is ignored). */
 void mslice_batch_free(mslice_batch b);
+
+/* ---- Serving: sliding windows of live temporal graphs ----
+ *
+ * The supra-graph grows with the number of snapshots, and Sec. 4 names
+ * windowed optimisation as the way to bound it for long streams.  A server
+ * keeps, per live graph, a ring of the last W slices on the device with the
+ * partition of the current window.  Each submitted snapshot is one request:
+ *   - the window advances: the new slice is appended and, when W slices are
+ *     held already, the oldest is evicted;
+ *   - the solve is warm-started: supra-node (j, i) of the new window (slice j,
+ *     node i) starts with the label that (j + e, i) had in the previous
+ *     window's result, where e = 1 if a slice was evicted (else 0), capped at
+ *     the previous newest slice, so the new slice's node i starts with its
+ *     label in the previous newest slice; the first snapshot of a graph starts
+ *     from singletons;
+ *   - the result is mslice_leiden_ex on the window's slices with these initial
+ *     labels and the server's gamma, omega and schedule options, bit for bit.
+ * Requests are served by n_slots workers, each with its own CUDA stream.  A
+ * free worker admits the queued requests, in arrival order, whose estimated
+ * device footprint fits in what is left of the memory budget (at most one
+ * in-flight request per graph, up to max_batch, never overtaking a request
+ * that does not fit) and solves them as one batch; requests that arrive while
+ * other workers' batches run are admitted as workers and memory free up, so
+ * their work overlaps on the device.  A request larger than the whole budget
+ * runs alone once nothing else is in flight. */
+typedef struct mslice_server_s* mslice_server;
+
+typedef struct {
+  int32_t window;      /* W: slices per live graph; default 8 */
+  int32_t n_slots;     /* concurrent workers (CUDA streams); default 2 */
+  int32_t max_batch;   /* requests per batch; default 64 */
+  int32_t pad_;
+  int64_t hbm_budget;  /* bytes of device memory admitted work may use; 0 (default): 80% of the free
+                          memory when the server is created */
+  int64_t gamma_num, gamma_den, omega_num, omega_den; /* default 1/1, 1/1 */
+  mslice_opts solve;   /* schedule (n_iterations, K, max_rounds, max_levels, seed); defaults as
+                          mslice_default_opts; gamma/omega/flags/stop fields are not used */
+} mslice_server_opts;
+
+/* Per-request record, times in seconds since the server was created. */
+typedef struct {
+  int32_t status;       /* MSLICE_OK or the request's error code */
+  int32_t slices;       /* slices in the window that was solved */
+  int64_t N;            /* supra-nodes of that window (labels written) */
+  double Q;             /* Q_MS of the result */
+  double t_submit, t_admit, t_done;
+  int32_t batch_size;   /* requests solved together with it (itself included) */
+  int32_t slot;         /* worker that solved it */
+  int64_t footprint;    /* estimated device bytes admitted for it */
+  double t_batch_start, t_batch_end; /* the batch's solve on the device (host clock) */
+} mslice_request_info;
+
+void mslice_server_default_opts(mslice_server_opts* o);
+
+/* Starts the workers on the current device.  Errors: EINVAL, ENOMEM, ECUDA. */
+int mslice_server_create(const mslice_server_opts* o, mslice_server* out);
+
+/* Registers a live graph of n nodes per slice; *graph_id receives its id. */
+int mslice_server_add_graph(mslice_server s, int64_t n, int32_t* graph_id);
+
+/* Queues the next snapshot of graph_id (host CSR with the mslice_csr
+ * conventions, copied during the call) and returns at once; *request_id
+ * receives the request's id.  A malformed snapshot fails its request
+ * (EINVAL at wait) and leaves the window unchanged.  Errors: EINVAL. */
+int mslice_server_submit(mslice_server s, int32_t graph_id, const mslice_csr* slice, int64_t* request_id);
+
+/* Blocks until the request is done, then writes its N window labels
+ * (canonical, host int32[N]; nullable) and its record (nullable) and forgets
+ * the request.  Returns the request's status; EINVAL for an unknown id. */
+int mslice_server_wait(mslice_server s, int64_t request_id, int32_t* labels_out, mslice_request_info* info);
+
+/* Finishes the queued requests, stops the workers and releases the server
+ * and its device memory (NULL is ignored). */
+void mslice_server_free(mslice_server s);
 
 /* Sizes of a built handle: N supra-nodes, T, n, stored level-0 entries
  * (intra + coupling, both directions). Any pointer may be NULL. */

@@ -13,6 +13,9 @@ The entry points mirror ``include/mslice.h``:
   (Eq. multislice-modularity)
 * :class:`Batch` -- many (graph, gamma, omega) solves in one pass
   (``mslice_batch_create/add/run/results``)
+* :class:`Server` -- sliding windows of live temporal graphs, warm-started,
+  admitted by device-memory footprint and batched continuously
+  (``mslice_server_*``)
 """
 from __future__ import annotations
 
@@ -34,7 +37,9 @@ EXPORTS = ["mslice_default_opts", "mslice_build", "mslice_build_ex", "mslice_lei
            "mslice_modularity", "mslice_modularity_ex", "mslice_modularity_noalloc", "mslice_info",
            "mslice_kernel_launches", "mslice_free", "mslice_last_error", "mslice_batch_create",
            "mslice_batch_add", "mslice_batch_run", "mslice_batch_results", "mslice_batch_info",
-           "mslice_batch_clear", "mslice_batch_kernel_launches", "mslice_batch_free"]
+           "mslice_batch_clear", "mslice_batch_kernel_launches", "mslice_batch_free",
+           "mslice_server_default_opts", "mslice_server_create", "mslice_server_add_graph",
+           "mslice_server_submit", "mslice_server_wait", "mslice_server_free"]
 
 
 class LibraryMissing(RuntimeError):
@@ -67,6 +72,19 @@ class Stats(C.Structure):
                 ("kernel_launches", C.c_int64), ("ms_total", C.c_double), ("ms_local_move", C.c_double),
                 ("ms_refine", C.c_double), ("ms_aggregate", C.c_double), ("ms_modularity", C.c_double),
                 ("ms_decide", C.c_double), ("decide_launches", C.c_int64), ("decide_bytes", C.c_int64)]
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("window", C.c_int32), ("n_slots", C.c_int32), ("max_batch", C.c_int32), ("pad_", C.c_int32),
+                ("hbm_budget", C.c_int64), ("gamma_num", C.c_int64), ("gamma_den", C.c_int64),
+                ("omega_num", C.c_int64), ("omega_den", C.c_int64), ("solve", Opts)]
+
+
+class RequestInfo(C.Structure):
+    _fields_ = [("status", C.c_int32), ("slices", C.c_int32), ("N", C.c_int64), ("Q", C.c_double),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("batch_size", C.c_int32), ("slot", C.c_int32), ("footprint", C.c_int64),
+                ("t_batch_start", C.c_double), ("t_batch_end", C.c_double)]
 
 
 _lib = None
@@ -109,6 +127,14 @@ def lib():
         L.mslice_batch_kernel_launches.restype = C.c_int64
         L.mslice_batch_free.argtypes = [P]
         L.mslice_batch_free.restype = None
+        L.mslice_server_default_opts.argtypes = [P]
+        L.mslice_server_default_opts.restype = None
+        L.mslice_server_create.argtypes = [P, P]
+        L.mslice_server_add_graph.argtypes = [P, C.c_int64, P]
+        L.mslice_server_submit.argtypes = [P, C.c_int32, P, P]
+        L.mslice_server_wait.argtypes = [P, C.c_int64, P, P]
+        L.mslice_server_free.argtypes = [P]
+        L.mslice_server_free.restype = None
         _lib = L
     return _lib
 
@@ -289,6 +315,78 @@ class Batch:
     results = mslice_batch_results
     info = mslice_batch_info
     clear = mslice_batch_clear
+
+
+class Server:
+    """Serving loop over live temporal graphs (``mslice_server_*``): every
+    submitted snapshot advances its graph's window of ``window`` slices and is
+    solved warm-started from the previous window's labels; the result equals
+    :meth:`Handle.mslice_leiden` on the window with those initial labels."""
+
+    def __init__(self, window=8, n_slots=2, max_batch=64, hbm_budget=0, gamma=(1, 1), omega=(1, 1),
+                 n_iterations=2, K=4, max_rounds=100, max_levels=32, seed=0):
+        o = ServerOpts()
+        lib().mslice_server_default_opts(C.byref(o))
+        o.window, o.n_slots, o.max_batch, o.hbm_budget = window, n_slots, max_batch, hbm_budget
+        o.gamma_num, o.gamma_den = gamma
+        o.omega_num, o.omega_den = omega
+        o.solve.n_iterations, o.solve.K, o.solve.max_rounds = n_iterations, K, max_rounds
+        o.solve.max_levels, o.solve.seed = max_levels, seed
+        s = C.c_void_p()
+        _check(lib().mslice_server_create(C.byref(o), C.byref(s)), "mslice_server_create")
+        self._s = s
+        self.window = window
+        self._n = {}
+        self._pending = {}
+
+    def close(self):
+        if self._s:
+            lib().mslice_server_free(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def mslice_server_add_graph(self, n: int) -> int:
+        gid = C.c_int32(-1)
+        _check(lib().mslice_server_add_graph(self._s, n, C.byref(gid)), "mslice_server_add_graph")
+        self._n[gid.value] = n
+        return gid.value
+
+    def mslice_server_submit(self, graph_id: int, snap) -> int:
+        ip = np.ascontiguousarray(snap.indptr, dtype=np.int64)
+        ix = np.ascontiguousarray(snap.indices, dtype=np.int32)
+        w = np.ascontiguousarray(snap.weights, dtype=np.int32)
+        csr = Csr(len(ip) - 1, _ptr(ip).value, _ptr(ix).value, _ptr(w).value)
+        rid = C.c_int64(-1)
+        _check(lib().mslice_server_submit(self._s, graph_id, C.byref(csr), C.byref(rid)), "mslice_server_submit")
+        self._pending[rid.value] = graph_id
+        return rid.value
+
+    def mslice_server_wait(self, request_id: int):
+        """(labels, info dict) of a finished request; raises MsliceError when
+        the request failed."""
+        gid = self._pending.pop(request_id, None)
+        n = self._n.get(gid, 0) * self.window
+        labels = np.zeros(max(n, 1), dtype=np.int32)
+        info = RequestInfo()
+        rc = lib().mslice_server_wait(self._s, request_id, _ptr(labels), C.byref(info))
+        d = {f: getattr(info, f) for f, _ in RequestInfo._fields_}
+        _check(rc, "mslice_server_wait")
+        return labels[: info.N].copy(), d
+
+    add_graph = mslice_server_add_graph
+    submit = mslice_server_submit
+    wait = mslice_server_wait
 
 
 def mslice_build(snaps, omega=(1, 1), stream=None, device_ptrs=False, host_tensors=False) -> Handle:

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <atomic>
 #include <map>
+#include <mutex>
 #include <functional>
 #include <new>
 #include <string>
@@ -23,6 +24,22 @@ static thread_local std::string g_last_error;
 void fail(int code, const std::string& msg) { throw Error{code, msg}; }
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+// Freed stream-ordered allocations stay in the device's default pool, so
+// handles created and released in a loop do not pay for fresh allocations.
+void keep_pool_memory() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+  int dev = 0;
+  cudaMemPool_t pool;
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  });
+}
+
 
 void check_cuda(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return;
@@ -67,6 +84,50 @@ size_t Workspace::bytes_held() const {
   size_t t = 0;
   for (const auto& kv : bufs_) t += kv.second.second;
   return t;
+}
+
+namespace {
+std::mutex g_coop_mu;
+cudaEvent_t g_coop_ev[64] = {};
+}  // namespace
+
+CoopOrder::CoopOrder(cudaStream_t s) : s_(s) {
+  g_coop_mu.lock();
+  if (cudaGetDevice(&dev_) != cudaSuccess || dev_ < 0 || dev_ >= 64) dev_ = 0;
+  if (!g_coop_ev[dev_]) {
+    if (cudaEventCreateWithFlags(&g_coop_ev[dev_], cudaEventDisableTiming) != cudaSuccess) g_coop_ev[dev_] = nullptr;
+  } else {
+    cudaStreamWaitEvent(s_, g_coop_ev[dev_], 0);
+  }
+}
+
+CoopOrder::~CoopOrder() {
+  if (g_coop_ev[dev_]) cudaEventRecord(g_coop_ev[dev_], s_);
+  g_coop_mu.unlock();
+}
+
+void StreamFan::create() {
+  int lo = 0, hi = 0;
+  check_cuda(cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priorities");
+  for (int k = 0; k < kSide; ++k) {
+    // side 0 and 1 carry the block-per-node tiers: highest priority, so their
+    // blocks are placed before the group tiers' queued blocks
+    check_cuda(cudaStreamCreateWithPriority(&side[k], cudaStreamNonBlocking, k < 2 ? hi : lo), "stream");
+    check_cuda(cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming), "event");
+  }
+  check_cuda(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming), "event");
+}
+
+void StreamFan::destroy() {
+  for (int k = 0; k < kSide; ++k) {
+    if (side[k]) cudaStreamSynchronize(side[k]);
+    if (side[k]) cudaStreamDestroy(side[k]);
+    if (join[k]) cudaEventDestroy(join[k]);
+    side[k] = nullptr;
+    join[k] = nullptr;
+  }
+  if (fork) cudaEventDestroy(fork);
+  fork = nullptr;
 }
 
 void sync(Ctx& c) { check_cuda(cudaStreamSynchronize(c.stream), "stream synchronize"); }
@@ -142,9 +203,11 @@ struct mslice_graph {
   void* pinned = nullptr;
   long long on = 1, od = 1;
   int64_t launches = 0;
+  StreamFan fan;
   Ctx ctx() {
     Ctx c;
     c.stream = stream;
+    c.fan = fan.fork ? &fan : nullptr;
     c.ws = &ws;
     c.d_status = d_status;
     c.pinned = pinned;
@@ -153,6 +216,7 @@ struct mslice_graph {
   ~mslice_graph() {
     ws.release_all();
     G.mem.release_all();
+    fan.destroy();
     if (pinned) cudaFreeHost(pinned);
   }
 };
@@ -176,9 +240,11 @@ struct mslice_batch_s {
   bool solved = false;
   std::vector<double> Q;
   int64_t launches = 0;
+  StreamFan fan;
   Ctx ctx() {
     Ctx c;
     c.stream = stream;
+    c.fan = fan.fork ? &fan : nullptr;
     c.ws = &ws;
     c.d_status = d_status;
     c.pinned = pinned;
@@ -187,6 +253,7 @@ struct mslice_batch_s {
   ~mslice_batch_s() {
     ws.release_all();
     G.mem.release_all();
+    fan.destroy();
     if (pinned) cudaFreeHost(pinned);
   }
 };
@@ -207,35 +274,9 @@ int guard(const std::function<void()>& f) {
   }
 }
 
-// Freed stream-ordered allocations stay in the device's default pool, so
-// handles created and released in a loop do not pay for fresh allocations.
-void keep_pool_memory() {
-  static bool done = false;
-  if (done) return;
-  int dev = 0;
-  cudaMemPool_t pool;
-  if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-    uint64_t thr = ~0ull;
-    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-  }
-  cudaGetLastError();
-  done = true;
-}
-
 bool rational_ok(int64_t num, int64_t den, bool allow_zero) {
   const int64_t lim = (int64_t)1 << 31;
   return den >= 1 && den <= lim && num >= (allow_zero ? 0 : 1) && num <= lim;
-}
-
-void check_bounds(int64_t n, int32_t T, const int64_t* two_m, long long gn, long long gd, long long on, long long od) {
-  u128 sum2m = 0;
-  for (int32_t s = 0; s < T; ++s) sum2m += (u128)(ull)two_m[s];
-  const u128 ncpl = (u128)(ull)n * (u128)(ull)(T > 0 ? T - 1 : 0);
-  const u128 lim = (u128)1 << 61;
-  if ((u128)(ull)od * sum2m + 2 * (u128)(ull)on * ncpl >= lim)
-    fail(MSLICE_EOVERFLOW, "omega_den*sum(2m_s) + 2*omega_num*n*(T-1) must stay below 2^61");
-  if ((u128)(ull)gn * (u128)(ull)od * sum2m >= lim * (u128)(ull)gd)
-    fail(MSLICE_EOVERFLOW, "gamma*omega_den*sum(2m_s) must stay below 2^61");
 }
 
 void sync_stream(cudaStream_t s) { check_cuda(cudaStreamSynchronize(s), "stream synchronize"); }
@@ -343,6 +384,7 @@ int mslice_build_ex(const mslice_csr* slices, int32_t T, mslice_coupling cpl, in
     h->on = omega_num;
     h->od = omega_den;
     check_cuda(cudaMallocHost(&h->pinned, PINNED_BYTES), "pinned buffer");
+    if (!std::getenv("MSLICE_SERIAL_TIERS")) h->fan.create();
     h->d_status = h->ws.get<unsigned>("status", 4);
     Ctx c = h->ctx();
     check_cuda(cudaMemsetAsync(h->d_status, 0, 16, c.stream), "memset");
@@ -530,6 +572,7 @@ int mslice_batch_create(int32_t flags, void* stream, mslice_batch* out) {
     b->G.mem.stream = b->stream;
     keep_pool_memory();
     check_cuda(cudaMallocHost(&b->pinned, PINNED_BYTES), "pinned buffer");
+    if (!std::getenv("MSLICE_SERIAL_TIERS")) b->fan.create();
     b->d_status = b->ws.get<unsigned>("status", 4);
     check_cuda(cudaMemsetAsync(b->d_status, 0, 16, b->stream), "memset");
     sync_stream(b->stream);

@@ -394,18 +394,46 @@ struct TierSegs {
 template <class Pol>
 void decide_all(Ctx& c, const Pol& pol, const TierSegs& sg, const int32_t* tier_cnt, int32_t* gkeys,
                 long long* gvals, const int64_t* goff) {
-  if (tier_cnt[0] > 0)
-    launch(c, k_decide_groups<Pol, 4, 5, 4>, dim3(152 * 4), dim3(GROUP_THREADS), 0, pol, sg.list[0], sg.count[0]);
-  if (tier_cnt[1] > 0)
-    launch(c, k_decide_groups<Pol, 8, 6, 4>, dim3(152 * 4), dim3(GROUP_THREADS), 0, pol, sg.list[1], sg.count[1]);
-  if (tier_cnt[2] > 0)
-    launch(c, k_decide_groups<Pol, 32, 9, MSLICE_T2_EPL>, dim3(152 * 4), dim3(GROUP_THREADS), 0, pol, sg.list[2],
-           sg.count[2]);
-  if (tier_cnt[3] > 0)
-    launch(c, k_decide_block<Pol>, dim3(152 * 4), dim3(BLOCK_THREADS), 0, pol, sg.list[3], sg.count[3]);
+  // The tiers decide disjoint node sets with separate scratch, so they may
+  // run concurrently: heaviest first, each on its own side stream (their few
+  // long rows then overlap the group tiers instead of trailing them).
+  StreamFan* f = c.fan;
+  cudaStream_t st[NTIERS] = {c.stream, c.stream, c.stream, c.stream, c.stream};
+  bool used[StreamFan::kSide] = {false, false, false, false};
+  if (f) {
+    int busy = 0;
+    for (int t = 0; t < NTIERS; ++t) busy += tier_cnt[t] > 0;
+    if (busy > 1) {
+      check_cuda(cudaEventRecord(f->fork, c.stream), "event");
+      // tiers 4, 3, 2, 1 on side streams 0..3; tier 0 on the context's stream
+      for (int t = NTIERS - 1; t >= 1; --t)
+        if (tier_cnt[t] > 0) {
+          const int k = NTIERS - 1 - t;
+          check_cuda(cudaStreamWaitEvent(f->side[k], f->fork, 0), "event");
+          st[t] = f->side[k];
+          used[k] = true;
+        }
+    }
+  }
   if (tier_cnt[4] > 0)
-    launch(c, k_decide_global<Pol>, dim3(152 * 2), dim3(BLOCK_THREADS), 0, pol, sg.list[4], sg.count[4], gkeys, gvals,
-           goff, c.d_status);
+    launch_on(c, st[4], k_decide_global<Pol>, dim3(152 * 2), dim3(BLOCK_THREADS), 0, pol, sg.list[4], sg.count[4],
+              gkeys, gvals, goff, c.d_status);
+  if (tier_cnt[3] > 0)
+    launch_on(c, st[3], k_decide_block<Pol>, dim3(152 * 4), dim3(BLOCK_THREADS), 0, pol, sg.list[3], sg.count[3]);
+  if (tier_cnt[2] > 0)
+    launch_on(c, st[2], k_decide_groups<Pol, 32, 9, MSLICE_T2_EPL>, dim3(152 * 4), dim3(GROUP_THREADS), 0, pol,
+              sg.list[2], sg.count[2]);
+  if (tier_cnt[1] > 0)
+    launch_on(c, st[1], k_decide_groups<Pol, 8, 6, 4>, dim3(152 * 4), dim3(GROUP_THREADS), 0, pol, sg.list[1],
+              sg.count[1]);
+  if (tier_cnt[0] > 0)
+    launch_on(c, st[0], k_decide_groups<Pol, 4, 5, 4>, dim3(152 * 4), dim3(GROUP_THREADS), 0, pol, sg.list[0],
+              sg.count[0]);
+  for (int k = 0; k < StreamFan::kSide; ++k)
+    if (used[k]) {
+      check_cuda(cudaEventRecord(f->join[k], f->side[k]), "event");
+      check_cuda(cudaStreamWaitEvent(c.stream, f->join[k], 0), "event");
+    }
 }
 
 }  // namespace mslice

@@ -19,6 +19,7 @@
 #include <cstring>
 #include <vector>
 
+#include "../../include/mslice.h"
 #include "solver.h"
 
 namespace mslice {
@@ -159,6 +160,17 @@ void check_label_ranges(Ctx& c, const SupraGraph& G, const int32_t* d) {
   launch(c, k_check_labels, dim3(gsz(G.N)), dim3(256), 0, d, G.N, (const int32_t*)(G.B > 1 ? G.inst0 : nullptr),
          (const int32_t*)G.inst_off0, c.d_status);
   check_status(c, "labels");
+}
+
+void check_bounds(int64_t n, int32_t T, const int64_t* two_m, long long gn, long long gd, long long on, long long od) {
+  u128 sum2m = 0;
+  for (int32_t s = 0; s < T; ++s) sum2m += (u128)(ull)two_m[s];
+  const u128 ncpl = (u128)(ull)n * (u128)(ull)(T > 0 ? T - 1 : 0);
+  const u128 lim = (u128)1 << 61;
+  if ((u128)(ull)od * sum2m + 2 * (u128)(ull)on * ncpl >= lim)
+    fail(MSLICE_EOVERFLOW, "omega_den*sum(2m_s) + 2*omega_num*n*(T-1) must stay below 2^61");
+  if ((u128)(ull)gn * (u128)(ull)od * sum2m >= lim * (u128)(ull)gd)
+    fail(MSLICE_EOVERFLOW, "gamma*omega_den*sum(2m_s) must stay below 2^61");
 }
 
 void set_instances(Ctx& c, Solver& S, const std::vector<InstParams>& jobs) {

@@ -20,6 +20,11 @@ struct Error {
 };
 
 [[noreturn]] void fail(int code, const std::string& msg);
+// Message returned by mslice_last_error() in the calling thread.
+void set_last_error(const std::string& msg);
+// Raises the release threshold of the device's default memory pool once per
+// process, so freed stream-ordered allocations are reused, not returned.
+void keep_pool_memory();
 void check_cuda(cudaError_t e, const char* what);
 
 // Growable named device buffers owned by a handle.  Contents are undefined
@@ -41,8 +46,21 @@ class Workspace {
   std::map<std::string, std::pair<void*, size_t>> bufs_;
 };
 
+// Side streams on which the degree tiers of one decision sub-round run
+// concurrently (forked from and joined back to the context's stream by
+// events).  Owned by a handle, batch or server worker.
+struct StreamFan {
+  static constexpr int kSide = 4;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kSide] = {};
+  void create();   // high priority for the streams of the heaviest tiers
+  void destroy();
+};
+
 struct Ctx {
   cudaStream_t stream = nullptr;
+  StreamFan* fan = nullptr;      // nullptr: tiers run one after another
   Workspace* ws = nullptr;
   unsigned* d_status = nullptr;  // device error bits
   int64_t launches = 0;
@@ -69,15 +87,48 @@ inline void launch(Ctx& c, void (*k)(KArgs...), dim3 grid, dim3 block, size_t sm
   if (c.trace) trace_end(c, (const void*)k, e0);
 }
 
+// Orders cooperative launches device-wide: a kernel with grid-wide barriers
+// starts only after the previous one (from any stream or thread of the
+// process) has finished, so two such grids never hold part of the SMs each
+// while waiting for the rest.  Every other kernel of the library runs to
+// completion without waiting on other blocks, so a cooperative grid always
+// becomes fully resident.
+class CoopOrder {
+ public:
+  explicit CoopOrder(cudaStream_t s);  // waits for the previous cooperative kernel
+  ~CoopOrder();                        // marks this stream's point as the new one
+  CoopOrder(const CoopOrder&) = delete;
+  CoopOrder& operator=(const CoopOrder&) = delete;
+
+ private:
+  cudaStream_t s_;
+  int dev_ = 0;
+};
+
 // Cooperative launch (grid-wide barriers); the grid must be co-resident.
 template <class... KArgs, class... Args>
 inline void launch_coop(Ctx& c, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, Args... args) {
   void* argv[] = {(void*)&args...};
   cudaEvent_t e0 = nullptr;
   if (c.trace) trace_begin(c, (const void*)k, &e0);
-  check_cuda(cudaLaunchCooperativeKernel((const void*)k, grid, block, argv, smem, c.stream), "cooperative launch");
+  {
+    CoopOrder order(c.stream);
+    check_cuda(cudaLaunchCooperativeKernel((const void*)k, grid, block, argv, smem, c.stream), "cooperative launch");
+  }
   c.launches++;
   if (c.trace) trace_end(c, (const void*)k, e0);
+}
+
+// launch() on another stream of the same context.
+template <class... KArgs, class... Args>
+inline void launch_on(Ctx& c, cudaStream_t s, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, Args&&... args) {
+  struct Restore {
+    Ctx& c;
+    cudaStream_t keep;
+    ~Restore() { c.stream = keep; }
+  } restore{c, c.stream};
+  c.stream = s;
+  launch(c, k, grid, block, smem, std::forward<Args>(args)...);
 }
 
 inline unsigned grid_for(int64_t n, int per_block) {

@@ -136,6 +136,12 @@ LevelDev level0_view(const SupraGraph& G, long long on, long long od);
 // The level-0 view of a solve: batch maps and per-instance omega included.
 LevelDev level0_view(const SupraGraph& G, const Solver& S);
 
+// Fails with MSLICE_EOVERFLOW unless the 128-bit move keys of a graph with n
+// nodes per snapshot and snapshot masses two_m[0..T) stay in range for this
+// gamma and omega: od * sum 2m_s + 2 on n (T-1) < 2^61 and
+// gamma od sum 2m_s < 2^61.
+void check_bounds(int64_t n, int32_t T, const int64_t* two_m, long long gn, long long gd, long long on, long long od);
+
 // Fails with MSLICE_EINVAL unless every level-0 label d[v] (device) lies in
 // [0, size of v's instance).
 void check_label_ranges(Ctx& c, const SupraGraph& G, const int32_t* d);

@@ -417,6 +417,38 @@ def batched_graph(spec):
     return snaps
 
 
+# Serving workload: 32 live temporal graphs (the generator of config 1 at
+# mean degree 16), n log-uniform in
+# [10k, 2M], each a stream of snapshots with 5% edge churn between
+# consecutive ones, weights 1..8; windows of W = 8 slices; requests arrive
+# as a Poisson process of 50 snapshots per second.
+SERVING = dict(n_graphs=32, n_lo=10_000, n_hi=2_000_000, mean_deg=16.0, churn=0.05, w_max=8, window=8,
+               rate_per_s=50.0, seed=5)
+
+
+def serving_specs(scale_n: float = 1.0, n_graphs: int | None = None):
+    """(n, p_in, seed) of every live graph of the serving workload."""
+    c = SERVING
+    rng = np.random.default_rng(c["seed"])
+    specs = []
+    for g in range(c["n_graphs"] if n_graphs is None else n_graphs):
+        n = float(np.exp(rng.uniform(np.log(c["n_lo"]), np.log(c["n_hi"]))))
+        n = max(8, int(round(n * scale_n)))
+        p_in = min(1.0, c["mean_deg"] / (n / 4 - 1 + 0.075 * n))
+        specs.append((n, p_in, 1000 * c["seed"] + g))
+    return specs
+
+
+def serving_stream(spec, steps: int):
+    """The first `steps` snapshots of one live graph: 4 equal blocks,
+    p_out = p_in / 10, 10% of the nodes switch block between snapshots and 5%
+    of the edges are replaced."""
+    n, p_in, seed = spec
+    snaps, _ = planted_partition_temporal(n, steps, 4, p_in, p_in / 10, 0.10, SERVING["churn"], SERVING["w_max"],
+                                          seed)
+    return snaps
+
+
 def config_graph(cfg: int | dict, scale_n: int | None = None, T: int | None = None):
     """Snapshots of a workload recipe (optionally with n or T overridden)."""
     c = dict(CONFIGS[cfg]) if isinstance(cfg, int) else dict(cfg)
