@@ -188,10 +188,12 @@ def _gen_batched(spec):
     return synth.batched_graph(spec)
 
 
-# per batch: at most this many supra-nodes and stored entries (about 250 B per
-# supra-node and 52 B per entry of device memory while solving)
-BATCH_MAX_NODES = 1 << 27
-BATCH_MAX_ENTRIES = 1 << 30
+# Packing of the batched path: a batch holds at most 2^21 supra-nodes and 2^26
+# stored entries, so its randomly accessed state (labels, sizes, the hashed
+# community tables: ~50 B per supra-node) stays in the 129 MB L2; a graph
+# larger than that is solved as a batch of one.
+BATCH_MAX_NODES = 1 << 21
+BATCH_MAX_ENTRIES = 1 << 26
 
 
 def run_batched(args):

@@ -626,14 +626,17 @@ int mslice_batch_run(mslice_batch b, const mslice_opts* o, mslice_stats* st) {
     Ctx c = b->ctx();
     std::vector<uint64_t> serials;
     for (mslice_graph* g : b->graphs) serials.push_back(g->serial);
-    if (serials != b->G_serials) {
+    // one instance: solved on its handle's graph, no copy
+    const bool single = b->graphs.size() == 1;
+    if (!single && serials != b->G_serials) {
       std::vector<const SupraGraph*> parts;
       for (mslice_graph* g : b->graphs) parts.push_back(&g->G);
       b->G_serials.clear();
       concat_instances(c, parts, b->G);
       b->G_serials = serials;
     }
-    const int64_t N = b->G.N;
+    const SupraGraph& G = single ? b->graphs[0]->G : b->G;
+    const int64_t N = G.N;
     int32_t* init = nullptr;
     if (b->any_init && N > 0) {
       init = b->ws.get<int32_t>("b_init", N);
@@ -645,7 +648,7 @@ int mslice_batch_run(mslice_batch b, const mslice_opts* o, mslice_stats* st) {
     RunOut ro;
     Solver S;
     b->solved = false;
-    run_solve(c, b->G, b->jobs, opt, init, out, S, ro, stats);
+    run_solve(c, G, b->jobs, opt, init, out, S, ro, stats);
     b->Q = ro.Q;
     b->solved = true;
     b->launches += c.launches;
@@ -662,7 +665,7 @@ int mslice_batch_results(mslice_batch b, int32_t i, int32_t* labels_out, double*
     const int64_t lo = i < 0 ? 0 : b->off[i], hi = i < 0 ? b->off[B] : b->off[i + 1];
     if (hi > lo) {
       if (!labels_out) fail(MSLICE_EINVAL, "null labels_out");
-      const int32_t* out = b->ws.get<int32_t>("b_out", b->G.N > 0 ? b->G.N : 1);
+      const int32_t* out = b->ws.get<int32_t>("b_out", b->off.back() > 0 ? b->off.back() : 1);
       const bool dev = (b->flags & MSLICE_DEVICE_PTRS) != 0;
       check_cuda(cudaMemcpyAsync(labels_out, out + lo, (hi - lo) * sizeof(int32_t),
                                  dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream), "copy");
