@@ -1,10 +1,18 @@
 // Aggregation (Louvain/Leiden, Sec. 3.2): one node per refined
-// sub-community, numbered by ascending sub-community label.  Edges between
-// different new nodes are keyed (x*N' + y), radix-sorted and reduced by key
-// (weights summed); self-loops are dropped because no key or check reads
-// them and Q is always evaluated on level 0.  Snapshot strengths k_{x,s} are
-// the refinement's K_{R,s} table, sorted by (x, s).  The initial label of a
-// new node is the smallest new id inside its local-moving community.
+// sub-community, numbered by ascending sub-community label.  Contraction
+// without a sort: the level's nodes are bucketed by new id (member lists),
+// then one warp or block per new node walks its members' rows and sums the
+// weights per neighbouring new node in a table (shared memory, or global
+// scratch for rows with more than 4096 entries), dropping self-loops since
+// no key or check reads them and Q is always evaluated on level 0; the same
+// pass sums the members' snapshot strengths k_{x,s}.  Rows are written once
+// to an upper-bound layout and compacted.  The order of a row's entries is
+// not defined; nothing that reads a level depends on it (sums are exact
+// integers and every scan is order-free).  The initial label of a new node
+// is the smallest new id inside its local-moving community.
+#include <cstring>
+
+#include "../../include/mslice.h"
 #include "solver.h"
 
 namespace mslice {
@@ -16,137 +24,307 @@ __global__ void k_present(const int32_t* sizeR, int32_t N, int32_t* flag) {
     flag[i] = sizeR[i] > 0 ? 1 : 0;
 }
 
-// One warp per row; surviving entries are compacted with one atomic per warp
-// step (their order is fixed afterwards by the sort).
-__global__ void k_emit_edges(LevelDev g, const int32_t* R, const int32_t* newid, uint64_t Np, uint64_t* keys,
-                             long long* vals, ull* cursor) {
+constexpr int CW_BITS = 9;        // warp tier: rows with at most 256 entries / snapshot entries
+constexpr int CW_WARPS = 8;
+constexpr int CB_BITS = 13;       // block tier: at most 4096
+constexpr int CB_THREADS = 256;
+constexpr int CW_MAX = 1 << (CW_BITS - 1), CB_MAX = 1 << (CB_BITS - 1);
+
+// Per node: its new id; per new node: members, stored entries and snapshot
+// entries (upper bounds of its output).
+__global__ void k_contract_prep(LevelDev g, const int32_t* R, const int32_t* newid, int32_t* xmap, int32_t* mcnt,
+                                long long* dsum, int32_t* scnt) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t x = newid[R[v]];
+    xmap[v] = x;
+    atomicAdd(&mcnt[x], 1);
+    atomicAdd((ull*)&dsum[x], (ull)(g.rowptr[v + 1] - g.rowptr[v]));
+    int64_t b, e;
+    slice_range(g, (int32_t)v, b, e);
+    if (e > b) atomicAdd(&scnt[x], (int32_t)(e - b));
+  }
+}
+
+__global__ void k_contract_members(int32_t N, const int32_t* xmap, const int64_t* moff, int32_t* mfill, int32_t* mem) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t x = xmap[v];
+    mem[moff[x] + atomicAdd(&mfill[x], 1)] = (int32_t)v;
+  }
+}
+
+__device__ __forceinline__ int64_t pow2_at_least(int64_t x) {
+  int64_t p = 2;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// Rows by size: tier 0 (<= CW_MAX), 1 (<= CB_MAX), 2 (larger; its table of
+// pow2(2 * size) slots in global scratch).
+__global__ void k_contract_tier(int32_t Np, const long long* dsum, const int32_t* scnt, int32_t* lists,
+                                int32_t* tcnt, int64_t* gsize) {
   const int lane = threadIdx.x & 31;
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t v = (((int64_t)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); v < g.N; v += warps) {
-    const uint64_t x = (uint64_t)newid[R[v]];
-    const int64_t b = g.rowptr[v], e = g.rowptr[v + 1];
-    const Omega om = node_omega(g, (int32_t)v);
-    for (int64_t base = b; base < e; base += 32) {
-      const int64_t i = base + lane;
-      bool keep = false;
-      uint64_t key = 0;
-      long long W = 0;
-      if (i < e) {
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < Np; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = base + threadIdx.x;
+    int t = -1;
+    if (x < Np) {
+      const long long need = max(dsum[x], (long long)scnt[x]);
+      t = need <= CW_MAX ? 0 : (need <= CB_MAX ? 1 : 2);
+      gsize[x] = t == 2 ? pow2_at_least(2 * need) : 0;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, t);
+    const int leader = __ffs(peers) - 1;
+    int pos = 0;
+    if (t >= 0 && lane == leader) pos = atomicAdd(&tcnt[t], __popc(peers));
+    pos = __shfl_sync(peers, pos, leader);
+    if (t >= 0) lists[(int64_t)t * Np + pos + __popc(peers & ((1u << lane) - 1u))] = (int32_t)x;
+  }
+}
+
+// Insert-or-add into a table of `cap` (a power of two) slots.
+__device__ __forceinline__ int64_t ctab_add(int32_t* hk, long long* hv, int64_t cap, int32_t key, long long w,
+                                            bool& fresh) {
+  const uint64_t mask = (uint64_t)cap - 1;
+  const int bits = 63 - __clzll((long long)cap);
+  uint64_t i = ((uint64_t)(uint32_t)key * 0x9E3779B97F4A7C15ull) >> (64 - bits);
+  for (uint64_t p = 0; p <= mask; ++p) {
+    const int32_t prev = atomicCAS(&hk[i], -1, key);
+    if (prev == -1 || prev == key) {
+      atomicAdd((ull*)&hv[i], (ull)w);
+      fresh = prev == -1;
+      return (int64_t)i;
+    }
+    i = (i + 1) & mask;
+  }
+  fresh = false;
+  return -1;
+}
+
+// One warp per new node x (tier 0).  Members are fetched 32 at a time with
+// their row bounds; lanes stride over each member's entries.
+__global__ void __launch_bounds__(CW_WARPS * 32)
+    k_contract_warp(LevelDev g, const int32_t* xmap, const int64_t* moff, const int32_t* mem, const int32_t* list,
+                    const int32_t* count_ptr, const int64_t* eoff, const int64_t* soff, int32_t* tcol, long long* tw,
+                    int32_t* ecnt, int32_t* tsidx, long long* tsval, int32_t* scnt_out) {
+  constexpr int SLOTS = 1 << CW_BITS;
+  __shared__ int32_t hk[CW_WARPS][SLOTS];
+  __shared__ long long hv[CW_WARPS][SLOTS];
+  __shared__ uint16_t cl[CW_WARPS][SLOTS / 2];
+  __shared__ int32_t ncl[CW_WARPS];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t* K = hk[w];
+  long long* V = hv[w];
+  uint16_t* CL = cl[w];
+  for (int i = lane; i < SLOTS; i += 32) {
+    K[i] = -1;
+    V[i] = 0;
+  }
+  if (lane == 0) ncl[w] = 0;
+  __syncwarp();
+  const int count = *count_ptr;
+  const int64_t warps = (int64_t)gridDim.x * CW_WARPS;
+  for (int64_t idx = (int64_t)blockIdx.x * CW_WARPS + w; idx < count; idx += warps) {
+    const int32_t x = list[idx];
+    const int64_t mb = moff[x], me = moff[x + 1];
+    int n = 0;
+    for (int64_t j0 = mb; j0 < me; j0 += 32) {
+      const int64_t jj = j0 + lane;
+      int32_t mv = 0;
+      int64_t rb = 0, re = 0;
+      if (jj < me) {
+        mv = mem[jj];
+        rb = g.rowptr[mv];
+        re = g.rowptr[mv + 1];
+      }
+      const int cm = (int)min((int64_t)32, me - j0);
+      for (int t = 0; t < cm; ++t) {
+        const int32_t v = __shfl_sync(0xffffffffu, mv, t);
+        const int64_t b = __shfl_sync(0xffffffffu, rb, t), e = __shfl_sync(0xffffffffu, re, t);
+        const Omega om = node_omega(g, v);
+        for (int64_t base = b; base < e; base += 32) {
+          const int64_t i = base + lane;
+          bool fresh = false;
+          int64_t slot = 0;
+          if (i < e) {
+            int32_t u;
+            long long W;
+            if (edge_at(g, i, u, W, om)) {
+              const int32_t y = xmap[u];
+              if (y != x) slot = ctab_add(K, V, SLOTS, y, W, fresh);
+            }
+          }
+          const unsigned bal = __ballot_sync(0xffffffffu, fresh);
+          if (fresh) CL[n + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)slot;
+          n += __popc(bal);
+        }
+      }
+    }
+    __syncwarp();
+    const int64_t eo = eoff[x];
+    for (int k = lane; k < n; k += 32) {
+      const int slot = CL[k];
+      tcol[eo + k] = K[slot];
+      tw[eo + k] = V[slot];
+      K[slot] = -1;
+      V[slot] = 0;
+    }
+    if (lane == 0) ecnt[x] = n;
+    __syncwarp();
+    // snapshot strengths: lane per member
+    for (int64_t j = mb + lane; j < me; j += 32) {
+      const int32_t v = mem[j];
+      int64_t b, e;
+      slice_range(g, v, b, e);
+      for (int64_t q = b; q < e; ++q) {
+        int32_t sl;
+        long long k;
+        slice_entry(g, v, q, sl, k);
+        bool fresh;
+        const int64_t slot = ctab_add(K, V, SLOTS, sl, k, fresh);
+        if (fresh) CL[atomicAdd(&ncl[w], 1)] = (uint16_t)slot;
+      }
+    }
+    __syncwarp();
+    const int ns = ncl[w];
+    const int64_t so = soff[x];
+    for (int k = lane; k < ns; k += 32) {
+      const int slot = CL[k];
+      tsidx[so + k] = K[slot];
+      tsval[so + k] = V[slot];
+      K[slot] = -1;
+      V[slot] = 0;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      scnt_out[x] = ns;
+      ncl[w] = 0;
+    }
+    __syncwarp();
+  }
+}
+
+// One block per new node x (tiers 1 and 2): the table is in shared memory
+// (GLOBAL = false, 2^CB_BITS slots) or at gofs[x] in global scratch with
+// gsize[x] slots.  Warps take members in turn; lanes stride over entries.
+template <bool GLOBAL>
+__global__ void __launch_bounds__(CB_THREADS)
+    k_contract_block(LevelDev g, const int32_t* xmap, const int64_t* moff, const int32_t* mem, const int32_t* list,
+                     const int32_t* count_ptr, const int64_t* eoff, const int64_t* soff, int32_t* tcol, long long* tw,
+                     int32_t* ecnt, int32_t* tsidx, long long* tsval, int32_t* scnt_out, const int64_t* gofs,
+                     const int64_t* gsize, int32_t* gk, long long* gv, int32_t* gl) {
+  extern __shared__ __align__(16) unsigned char csm[];
+  __shared__ int32_t ncnt;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  constexpr int NW = CB_THREADS / 32;
+  const int count = *count_ptr;
+  int32_t* K;
+  long long* V;
+  int32_t* CL;
+  int64_t cap = (int64_t)1 << CB_BITS;
+  if (!GLOBAL) {
+    V = reinterpret_cast<long long*>(csm);
+    K = reinterpret_cast<int32_t*>(V + cap);
+    CL = K + cap;
+    for (int64_t i = threadIdx.x; i < cap; i += blockDim.x) {
+      K[i] = -1;
+      V[i] = 0;
+    }
+  }
+  for (int64_t idx = blockIdx.x; idx < count; idx += gridDim.x) {
+    const int32_t x = list[idx];
+    if (GLOBAL) {
+      cap = gsize[x];
+      K = gk + gofs[x];
+      V = gv + gofs[x];
+      CL = gl + gofs[x];
+      for (int64_t i = threadIdx.x; i < cap; i += blockDim.x) {
+        K[i] = -1;
+        V[i] = 0;
+      }
+    }
+    if (threadIdx.x == 0) ncnt = 0;
+    __syncthreads();
+    const int64_t mb = moff[x], me = moff[x + 1];
+    for (int64_t j = mb + w; j < me; j += NW) {
+      const int32_t v = mem[j];
+      const int64_t b = g.rowptr[v], e = g.rowptr[v + 1];
+      const Omega om = node_omega(g, v);
+      for (int64_t i = b + lane; i < e; i += 32) {
         int32_t u;
+        long long W;
         if (edge_at(g, i, u, W, om)) {
-          const uint64_t y = (uint64_t)newid[R[u]];
+          const int32_t y = xmap[u];
           if (y != x) {
-            keep = true;
-            key = x * Np + y;
+            bool fresh;
+            const int64_t slot = ctab_add(K, V, cap, y, W, fresh);
+            if (fresh) CL[atomicAdd(&ncnt, 1)] = (int32_t)slot;
           }
         }
       }
-      const unsigned m = __ballot_sync(0xffffffffu, keep);
-      if (m == 0) continue;
-      ull pos = 0;
-      if (lane == 0) pos = atomicAdd(cursor, (ull)__popc(m));
-      pos = __shfl_sync(0xffffffffu, pos, 0);
-      if (keep) {
-        const ull o = pos + __popc(m & ((1u << lane) - 1u));
-        keys[o] = key;
-        vals[o] = W;
+    }
+    __syncthreads();
+    const int n = ncnt;
+    const int64_t eo = eoff[x];
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const int32_t slot = CL[k];
+      tcol[eo + k] = K[slot];
+      tw[eo + k] = V[slot];
+      K[slot] = -1;
+      V[slot] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      ecnt[x] = n;
+      ncnt = 0;
+    }
+    __syncthreads();
+    for (int64_t j = mb + threadIdx.x; j < me; j += blockDim.x) {
+      const int32_t v = mem[j];
+      int64_t b, e;
+      slice_range(g, v, b, e);
+      for (int64_t q = b; q < e; ++q) {
+        int32_t sl;
+        long long k;
+        slice_entry(g, v, q, sl, k);
+        bool fresh;
+        const int64_t slot = ctab_add(K, V, cap, sl, k, fresh);
+        if (fresh) CL[atomicAdd(&ncnt, 1)] = (int32_t)slot;
       }
     }
+    __syncthreads();
+    const int ns = ncnt;
+    const int64_t so = soff[x];
+    for (int k = threadIdx.x; k < ns; k += blockDim.x) {
+      const int32_t slot = CL[k];
+      tsidx[so + k] = K[slot];
+      tsval[so + k] = V[slot];
+      K[slot] = -1;
+      V[slot] = 0;
+    }
+    if (threadIdx.x == 0) scnt_out[x] = ns;
+    __syncthreads();
   }
 }
 
-// Hashed K_{R,s}: entries in table order, sorted afterwards.
-__global__ void k_emit_slices(SigStore kr, const int32_t* newid, uint64_t T, uint64_t* keys, long long* vals,
-                              ull* cursor) {
+// Rows from the upper-bound layout to their final places (warp per row).
+__global__ void k_contract_compact(int32_t Np, const int64_t* eoff, const int32_t* ecnt, const int64_t* rowptr,
+                                   const int32_t* tcol, const long long* tw, int32_t* col, long long* W,
+                                   const int64_t* soff, const int32_t* scnt, const int64_t* sptr,
+                                   const int32_t* tsidx, const long long* tsval, int32_t* sidx, long long* sval) {
   const int lane = threadIdx.x & 31;
-  const uint64_t span = ss_span(kr);
-  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < span; base += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t i = base + threadIdx.x;
-    bool keep = false;
-    uint64_t key = 0;
-    long long val = 0;
-    if (i < span) {
-      int32_t Rl, s;
-      if (ss_entry(kr, i, Rl, s, val)) {
-        keep = true;
-        key = (uint64_t)newid[Rl] * T + (uint64_t)s;
-      }
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t x = (((int64_t)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); x < Np; x += warps) {
+    const int64_t a = eoff[x], o = rowptr[x];
+    const int n = ecnt[x];
+    for (int k = lane; k < n; k += 32) {
+      col[o + k] = tcol[a + k];
+      W[o + k] = tw[a + k];
     }
-    const unsigned m = __ballot_sync(0xffffffffu, keep);
-    if (m == 0) continue;
-    ull pos = 0;
-    if (lane == 0) pos = atomicAdd(cursor, (ull)__popc(m));
-    pos = __shfl_sync(0xffffffffu, pos, 0);
-    if (keep) {
-      const ull o = pos + __popc(m & ((1u << lane) - 1u));
-      keys[o] = key;
-      vals[o] = val;
+    const int64_t sa = soff[x], so = sptr[x];
+    const int ns = scnt[x];
+    for (int k = lane; k < ns; k += 32) {
+      sidx[so + k] = tsidx[sa + k];
+      sval[so + k] = tsval[sa + k];
     }
-  }
-}
-
-// Dense K_{R,s}: rows are already in (new id, snapshot) order, since new ids
-// rank the present labels; count and copy the non-zero entries row by row.
-__global__ void k_dense_slice_counts(const long long* d, int32_t T, const int32_t* sizeR, const int32_t* newid,
-                                     int32_t N, int32_t* cnt) {
-  for (int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; L < N; L += (int64_t)gridDim.x * blockDim.x) {
-    if (sizeR[L] <= 0) continue;
-    int32_t c = 0;
-    for (int32_t s = 0; s < T; ++s) c += d[L * T + s] != 0;
-    cnt[newid[L]] = c;
-  }
-}
-
-__global__ void k_dense_slice_fill(const long long* d, int32_t T, const int32_t* sizeR, const int32_t* newid,
-                                   int32_t N, const int64_t* sptr, int32_t* sidx, long long* sval) {
-  for (int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; L < N; L += (int64_t)gridDim.x * blockDim.x) {
-    if (sizeR[L] <= 0) continue;
-    int64_t o = sptr[newid[L]];
-    for (int32_t s = 0; s < T; ++s) {
-      const long long x = d[L * T + s];
-      if (x != 0) {
-        sidx[o] = s;
-        sval[o] = x;
-        ++o;
-      }
-    }
-  }
-}
-
-__global__ void k_seg_flags(const uint64_t* keys, int64_t m, int32_t* flag) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
-    flag[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
-}
-
-__global__ void k_zero_ll(long long* p, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = 0;
-}
-
-__global__ void k_seg_reduce(const uint64_t* keys, const long long* vals, const int32_t* flag, const int64_t* pos,
-                             int64_t m, uint64_t* ukeys, long long* usum) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t id = pos[i] + flag[i] - 1;
-    if (flag[i]) ukeys[id] = keys[i];
-    atomicAdd((ull*)&usum[id], (ull)vals[i]);
-  }
-}
-
-// Unique (row, col) keys -> per-row counts and the column array.
-__global__ void k_rows_of(const uint64_t* ukeys, int64_t mu, uint64_t div, int32_t* cnt, int32_t* col) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < mu; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t k = ukeys[i];
-    atomicAdd(&cnt[k / div], 1);
-    col[i] = (int32_t)(k % div);
-  }
-}
-
-__global__ void k_slices_of(const uint64_t* keys, const long long* vals, int64_t ms, uint64_t T, int32_t* cnt,
-                            int32_t* sidx, long long* sval) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ms; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t k = keys[i];
-    atomicAdd(&cnt[k / T], 1);
-    sidx[i] = (int32_t)(k % T);
-    sval[i] = vals[i];
   }
 }
 
@@ -190,12 +368,6 @@ unsigned gsz(int64_t n) {
   return (unsigned)(g < 1 ? 1 : g);
 }
 
-int bits_for(uint64_t maxval) {
-  int b = 0;
-  while (b < 64 && (maxval >> b) != 0) ++b;
-  return b < 1 ? 1 : b;
-}
-
 }  // namespace
 
 bool aggregate(Solver& S, const Level& L, const int32_t* P, Level& next, const std::string& slot,
@@ -211,30 +383,94 @@ bool aggregate(Solver& S, const Level& L, const int32_t* P, Level& next, const s
   const int32_t Np = *static_cast<const int32_t*>(readback(c, d_np, sizeof(int32_t)));
   if (Np == N) return false;
 
-  // ---- edges ----
+  // ---- contraction: member lists, rows summed per neighbouring new node ----
+  const int64_t np1 = (int64_t)Np + 1;
+  int32_t* xmap = c.ws->get<int32_t>("ag_xmap", N);
+  int32_t* mcnt = c.ws->get<int32_t>("ag_mcnt", np1);
+  int32_t* scnt = c.ws->get<int32_t>("ag_scnt", np1);
+  long long* dsum = c.ws->get<long long>("ag_dsum", np1);
+  check_cuda(cudaMemsetAsync(mcnt, 0, np1 * sizeof(int32_t), c.stream), "memset");
+  check_cuda(cudaMemsetAsync(scnt, 0, np1 * sizeof(int32_t), c.stream), "memset");
+  check_cuda(cudaMemsetAsync(dsum, 0, np1 * sizeof(long long), c.stream), "memset");
+  launch(c, k_contract_prep, dim3(gsz(N)), dim3(256), 0, L.d, (const int32_t*)S.R, (const int32_t*)newid, xmap, mcnt,
+         dsum, scnt);
+  int64_t* moff = c.ws->get<int64_t>("ag_moff", np1);
+  int64_t* eoff = c.ws->get<int64_t>("ag_eoff", np1);
+  int64_t* soff = c.ws->get<int64_t>("ag_soff", np1);
+  scan_excl(c, (const int32_t*)mcnt, moff, np1, (int64_t*)nullptr);
+  scan_excl(c, (const int64_t*)dsum, eoff, np1, (int64_t*)nullptr);
+  scan_excl(c, (const int32_t*)scnt, soff, np1, (int64_t*)nullptr);
+  int32_t* mem = c.ws->get<int32_t>("ag_mem", N);
+  check_cuda(cudaMemsetAsync(mcnt, 0, np1 * sizeof(int32_t), c.stream), "memset");
+  launch(c, k_contract_members, dim3(gsz(N)), dim3(256), 0, N, (const int32_t*)xmap, (const int64_t*)moff, mcnt, mem);
+  int32_t* lists = c.ws->get<int32_t>("ag_lists", 3 * (size_t)Np);
+  int32_t* tcnt = c.ws->get<int32_t>("ag_tcnt", 4);
+  int64_t* gsize = c.ws->get<int64_t>("ag_gsize", np1);
+  int64_t* gofs = c.ws->get<int64_t>("ag_gofs", np1);
+  check_cuda(cudaMemsetAsync(tcnt, 0, 4 * sizeof(int32_t), c.stream), "memset");
+  check_cuda(cudaMemsetAsync(gsize + Np, 0, sizeof(int64_t), c.stream), "memset");
+  launch(c, k_contract_tier, dim3(gsz(Np)), dim3(256), 0, Np, (const long long*)dsum, (const int32_t*)scnt, lists, tcnt,
+         gsize);
+  int64_t* d_gtot = c.ws->get<int64_t>("ag_gtot", 1);
+  scan_excl(c, (const int64_t*)gsize, gofs, np1, d_gtot);
+  struct {
+    int32_t t[4];
+    int64_t gtot;
+  } hd;
+  check_cuda(cudaMemcpyAsync(c.pinned, tcnt, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream), "copy");
+  check_cuda(cudaMemcpyAsync(static_cast<char*>(c.pinned) + 16, d_gtot, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                             c.stream), "copy");
+  sync(c);
+  std::memcpy(&hd, c.pinned, sizeof(hd));
   const int64_t cap = L.nnz > 0 ? L.nnz : 1;
-  uint64_t* k0 = c.ws->get<uint64_t>("ag_k0", cap);
-  long long* v0 = c.ws->get<long long>("ag_v0", cap);
-  uint64_t* k1 = c.ws->get<uint64_t>("ag_k1", cap);
-  long long* v1 = c.ws->get<long long>("ag_v1", cap);
-  ull* cursor = c.ws->get<ull>("ag_cursor", 2);
-  check_cuda(cudaMemsetAsync(cursor, 0, 2 * sizeof(ull), c.stream), "memset");
-  launch(c, k_emit_edges, dim3(gsz((int64_t)N * 32)), dim3(256), 0, L.d, (const int32_t*)S.R, (const int32_t*)newid,
-         (uint64_t)Np, k0, v0, cursor);
-  const int64_t m = (int64_t) * static_cast<const ull*>(readback(c, cursor, sizeof(ull)));
-  const SortBufs sorted = radix_sort_pairs(c, k0, v0, k1, v1, m, bits_for((uint64_t)Np * (uint64_t)Np - 1));
-  int32_t* sflag = c.ws->get<int32_t>("ag_flag", m + 1);
-  int64_t* spos = c.ws->get<int64_t>("ag_pos", m + 1);
-  int64_t* d_mu = c.ws->get<int64_t>("ag_mu", 1);
-  launch(c, k_seg_flags, dim3(gsz(m)), dim3(256), 0, (const uint64_t*)sorted.keys, m, sflag);
-  scan_excl(c, sflag, spos, m, d_mu);
-  const int64_t mu = m > 0 ? *static_cast<const int64_t*>(readback(c, d_mu, sizeof(int64_t))) : 0;
-  // unique keys/sums go to the buffers the sort did not leave its result in
-  uint64_t* ukeys = sorted.keys == k0 ? k1 : k0;
-  long long* usum = sorted.vals == v0 ? v1 : v0;
-  launch(c, k_zero_ll, dim3(gsz(mu)), dim3(256), 0, usum, mu);
-  launch(c, k_seg_reduce, dim3(gsz(m)), dim3(256), 0, (const uint64_t*)sorted.keys, (const long long*)sorted.vals,
-         (const int32_t*)sflag, (const int64_t*)spos, m, ukeys, usum);
+  const int64_t scap = L.ns > 0 ? L.ns : 1;
+  int32_t* tcol = c.ws->get<int32_t>("ag_tcol", cap);
+  long long* tw = c.ws->get<long long>("ag_tw", cap);
+  int32_t* tsidx = c.ws->get<int32_t>("ag_tsidx", scap);
+  long long* tsval = c.ws->get<long long>("ag_tsval", scap);
+  int32_t* ecnt = c.ws->get<int32_t>("ag_ecnt", np1);
+  int32_t* scnt_out = c.ws->get<int32_t>("ag_scnt_out", np1);
+  check_cuda(cudaMemsetAsync(ecnt + Np, 0, sizeof(int32_t), c.stream), "memset");
+  check_cuda(cudaMemsetAsync(scnt_out + Np, 0, sizeof(int32_t), c.stream), "memset");
+  if (hd.t[0] > 0)
+    launch(c, k_contract_warp, dim3(152 * 4), dim3(CW_WARPS * 32), 0, L.d, (const int32_t*)xmap, (const int64_t*)moff,
+           (const int32_t*)mem, (const int32_t*)lists, (const int32_t*)tcnt, (const int64_t*)eoff,
+           (const int64_t*)soff, tcol, tw, ecnt, tsidx, tsval, scnt_out);
+  const size_t cb_smem = ((size_t)1 << CB_BITS) * (sizeof(long long) + sizeof(int32_t)) +
+                         (size_t)CB_MAX * sizeof(int32_t);
+  if (hd.t[1] > 0) {
+    check_cuda(cudaFuncSetAttribute(k_contract_block<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cb_smem),
+               "attribute");
+    launch(c, k_contract_block<false>, dim3(152 * 2), dim3(CB_THREADS), cb_smem, L.d, (const int32_t*)xmap,
+           (const int64_t*)moff, (const int32_t*)mem, (const int32_t*)(lists + Np), (const int32_t*)(tcnt + 1),
+           (const int64_t*)eoff, (const int64_t*)soff, tcol, tw, ecnt, tsidx, tsval, scnt_out, (const int64_t*)gofs,
+           (const int64_t*)gsize, (int32_t*)nullptr, (long long*)nullptr, (int32_t*)nullptr);
+  }
+  if (hd.t[2] > 0) {
+    if (hd.gtot > ((int64_t)1 << 31) * 8) fail(MSLICE_ENOMEM, "aggregation scratch too large");
+    int32_t* gk = c.ws->get<int32_t>("ag_gk", hd.gtot);
+    long long* gv = c.ws->get<long long>("ag_gv", hd.gtot);
+    int32_t* gl = c.ws->get<int32_t>("ag_gl", hd.gtot);
+    launch(c, k_contract_block<true>, dim3(152 * 2), dim3(CB_THREADS), 0, L.d, (const int32_t*)xmap,
+           (const int64_t*)moff, (const int32_t*)mem, (const int32_t*)(lists + 2 * (int64_t)Np),
+           (const int32_t*)(tcnt + 2), (const int64_t*)eoff, (const int64_t*)soff, tcol, tw, ecnt, tsidx, tsval,
+           scnt_out, (const int64_t*)gofs, (const int64_t*)gsize, gk, gv, gl);
+  }
+  int64_t* rowptr = c.ws->get<int64_t>(slot + "_rowptr", (size_t)np1);
+  int64_t* sptr = c.ws->get<int64_t>(slot + "_sptr", (size_t)np1);
+  int64_t* d_tot = c.ws->get<int64_t>("ag_tot", 2);
+  scan_excl(c, (const int32_t*)ecnt, rowptr, np1, d_tot);
+  scan_excl(c, (const int32_t*)scnt_out, sptr, np1, d_tot + 1);
+  const int64_t* tots = static_cast<const int64_t*>(readback(c, d_tot, 2 * sizeof(int64_t)));
+  const int64_t mu = tots[0], ms = tots[1];
+  int32_t* col = c.ws->get<int32_t>(slot + "_col", mu);
+  long long* W = c.ws->get<long long>(slot + "_W", mu);
+  int32_t* sidx = c.ws->get<int32_t>(slot + "_sidx", ms);
+  long long* sval = c.ws->get<long long>(slot + "_sval", ms);
+  launch(c, k_contract_compact, dim3(gsz((int64_t)Np * 32)), dim3(256), 0, Np, (const int64_t*)eoff,
+         (const int32_t*)ecnt, (const int64_t*)rowptr, (const int32_t*)tcol, (const long long*)tw, col, W,
+         (const int64_t*)soff, (const int32_t*)scnt_out, (const int64_t*)sptr, (const int32_t*)tsidx,
+         (const long long*)tsval, sidx, sval);
 
   next.d = LevelDev{};
   next.d.N = Np;
@@ -252,52 +488,11 @@ bool aggregate(Solver& S, const Level& L, const int32_t* P, Level& next, const s
     next.d.inst = inst_next;
     next.d.inst_off = off_next;
   }
-  int64_t* rowptr = c.ws->get<int64_t>(slot + "_rowptr", (size_t)Np + 1);
-  int32_t* col = c.ws->get<int32_t>(slot + "_col", mu);
-  long long* W = c.ws->get<long long>(slot + "_W", mu);
-  int32_t* cnt = c.ws->get<int32_t>("ag_cnt", (size_t)Np + 1);
-  check_cuda(cudaMemsetAsync(cnt, 0, ((size_t)Np + 1) * sizeof(int32_t), c.stream), "memset");
-  launch(c, k_rows_of, dim3(gsz(mu)), dim3(256), 0, (const uint64_t*)ukeys, mu, (uint64_t)Np, cnt, col);
-  scan_excl(c, cnt, rowptr, (int64_t)Np + 1, (int64_t*)nullptr);
-  check_cuda(cudaMemcpyAsync(W, usum, mu * sizeof(long long), cudaMemcpyDeviceToDevice, c.stream), "copy");
   next.d.rowptr = rowptr;
   next.d.col = col;
   next.d.W = W;
   next.nnz = mu;
   next.nnz_eff = mu;
-
-  // ---- snapshot strengths ----
-  const uint64_t T = (uint64_t)S.G0->T;
-  int64_t* sptr = c.ws->get<int64_t>(slot + "_sptr", (size_t)Np + 1);
-  int64_t ms = 0;
-  int32_t* sidx = nullptr;
-  long long* sval = nullptr;
-  check_cuda(cudaMemsetAsync(cnt, 0, ((size_t)Np + 1) * sizeof(int32_t), c.stream), "memset");
-  if (S.kr.d) {
-    launch(c, k_dense_slice_counts, dim3(gsz(N)), dim3(256), 0, (const long long*)S.kr.d, (int32_t)T,
-           (const int32_t*)S.sizeR, (const int32_t*)newid, N, cnt);
-    int64_t* d_ms = c.ws->get<int64_t>("ag_ms", 1);
-    scan_excl(c, cnt, sptr, (int64_t)Np + 1, d_ms);
-    ms = *static_cast<const int64_t*>(readback(c, d_ms, sizeof(int64_t)));
-    sidx = c.ws->get<int32_t>(slot + "_sidx", ms);
-    sval = c.ws->get<long long>(slot + "_sval", ms);
-    launch(c, k_dense_slice_fill, dim3(gsz(N)), dim3(256), 0, (const long long*)S.kr.d, (int32_t)T,
-           (const int32_t*)S.sizeR, (const int32_t*)newid, N, (const int64_t*)sptr, sidx, sval);
-  } else {
-    const int64_t scap = (int64_t)S.kr.h.cap;
-    uint64_t* sk0 = c.ws->get<uint64_t>("ag_sk0", scap);
-    long long* sv0 = c.ws->get<long long>("ag_sv0", scap);
-    uint64_t* sk1 = c.ws->get<uint64_t>("ag_sk1", scap);
-    long long* sv1 = c.ws->get<long long>("ag_sv1", scap);
-    launch(c, k_emit_slices, dim3(gsz(scap)), dim3(256), 0, S.kr, (const int32_t*)newid, T, sk0, sv0, cursor + 1);
-    ms = (int64_t) * static_cast<const ull*>(readback(c, cursor + 1, sizeof(ull)));
-    const SortBufs ss = radix_sort_pairs(c, sk0, sv0, sk1, sv1, ms, bits_for((uint64_t)Np * T - 1));
-    sidx = c.ws->get<int32_t>(slot + "_sidx", ms);
-    sval = c.ws->get<long long>(slot + "_sval", ms);
-    launch(c, k_slices_of, dim3(gsz(ms)), dim3(256), 0, (const uint64_t*)ss.keys, (const long long*)ss.vals, ms, T,
-           cnt, sidx, sval);
-    scan_excl(c, cnt, sptr, (int64_t)Np + 1, (int64_t*)nullptr);
-  }
   next.d.sptr = sptr;
   next.d.sidx = sidx;
   next.d.sval = sval;

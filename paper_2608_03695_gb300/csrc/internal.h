@@ -158,16 +158,6 @@ void scan_excl(Ctx& c, const int64_t* in, int64_t* out, int64_t n, int64_t* d_to
 void scan_excl(Ctx& c, const int32_t* in, int32_t* out, int64_t n, int32_t* d_total,
                const int32_t* cond = nullptr);
 
-// Stable LSD radix sort of (key, value) pairs on the low `key_bits` bits.
-// Returns the buffer pair that holds the result (either the inputs or the
-// alternates).
-struct SortBufs {
-  uint64_t* keys;
-  long long* vals;
-};
-SortBufs radix_sort_pairs(Ctx& c, uint64_t* keys, long long* vals, uint64_t* keys_alt, long long* vals_alt,
-                          int64_t n, int key_bits);
-
 void fill_i32(Ctx& c, int32_t* p, int32_t v, int64_t n);
 void fill_i64(Ctx& c, int64_t* p, int64_t v, int64_t n);
 void iota_i32(Ctx& c, int32_t* p, int64_t n);

@@ -1,7 +1,5 @@
 // Device-wide primitives: exclusive scan (reduce-then-scan over 4096-element
-// tiles) and a stable LSD radix sort of 64-bit keys with 64-bit payloads
-// (8-bit digits; per-block histograms, one scan of the digit-major histogram
-// table, and a stable scatter ranked with warp match/ballot operations).
+// tiles), fills.
 #include "internal.h"
 
 namespace mslice {
@@ -102,62 +100,6 @@ void scan_impl(Ctx& c, const In* in, Out* out, int64_t n, Out* d_total, int dept
   launch(c, k_tile_scan<In, Out, Acc>, dim3(nb), dim3(SCAN_THREADS), 0, in, out, n, (const Acc*)bsum, d_total, cond);
 }
 
-// ------------------------------------------------------------------ radix sort
-constexpr int RS_THREADS = 256;
-constexpr int RS_ITEMS = 16;
-constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
-constexpr int RS_WARPS = RS_THREADS / 32;
-
-__global__ void k_rs_hist(const uint64_t* keys, int64_t n, int shift, int64_t* hist, int nb) {
-  __shared__ unsigned h[256];
-  h[threadIdx.x] = 0;
-  __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
-#pragma unroll 4
-  for (int j = 0; j < RS_ITEMS; ++j) {
-    int64_t i = base + (int64_t)j * RS_THREADS + threadIdx.x;
-    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
-  }
-  __syncthreads();
-  hist[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
-}
-
-__global__ void k_rs_scatter(const uint64_t* keys, const long long* vals, uint64_t* okeys, long long* ovals,
-                             int64_t n, int shift, const int64_t* offs, int nb) {
-  __shared__ unsigned wcnt[RS_WARPS][256];
-  __shared__ int64_t run[256];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  run[threadIdx.x] = offs[(int64_t)threadIdx.x * nb + blockIdx.x];
-  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
-  const unsigned lt = (1u << lane) - 1u;
-  for (int j = 0; j < RS_ITEMS; ++j) {
-    for (int q = 0; q < RS_WARPS; ++q) wcnt[q][threadIdx.x] = 0;
-    __syncthreads();
-    const int64_t i = base + (int64_t)j * RS_THREADS + threadIdx.x;
-    const bool ok = i < n;
-    uint64_t k = ok ? keys[i] : 0;
-    long long v = ok ? vals[i] : 0;
-    unsigned d = ok ? (unsigned)((k >> shift) & 255u) : 256u;
-    unsigned peers = __match_any_sync(0xffffffffu, d);
-    unsigned rank = __popc(peers & lt);
-    if (ok && rank == 0) wcnt[w][d] = __popc(peers);
-    __syncthreads();
-    if (ok) {
-      int64_t pos = run[d] + rank;
-      for (int q = 0; q < w; ++q) pos += wcnt[q][d];
-      okeys[pos] = k;
-      ovals[pos] = v;
-    }
-    __syncthreads();
-    {
-      unsigned add = 0;
-      for (int q = 0; q < RS_WARPS; ++q) add += wcnt[q][threadIdx.x];
-      run[threadIdx.x] += add;
-    }
-    __syncthreads();
-  }
-}
-
 __global__ void k_fill_i32(int32_t* p, int32_t v, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = v;
@@ -187,22 +129,6 @@ void scan_excl(Ctx& c, const int64_t* in, int64_t* out, int64_t n, int64_t* d_to
 }
 void scan_excl(Ctx& c, const int32_t* in, int32_t* out, int64_t n, int32_t* d_total, const int32_t* cond) {
   scan_impl<int32_t, int32_t, long long>(c, in, out, n, d_total, 0, cond);
-}
-
-SortBufs radix_sort_pairs(Ctx& c, uint64_t* keys, long long* vals, uint64_t* keys_alt, long long* vals_alt,
-                          int64_t n, int key_bits) {
-  SortBufs cur{keys, vals}, alt{keys_alt, vals_alt};
-  if (n <= 1) return cur;
-  const int nb = (int)grid_for(n, RS_TILE);
-  int64_t* hist = c.ws->get<int64_t>("rs_hist", (size_t)256 * nb);
-  for (int shift = 0; shift < key_bits; shift += 8) {
-    launch(c, k_rs_hist, dim3(nb), dim3(RS_THREADS), 0, (const uint64_t*)cur.keys, n, shift, hist, nb);
-    scan_excl(c, hist, hist, (int64_t)256 * nb, nullptr, nullptr);
-    launch(c, k_rs_scatter, dim3(nb), dim3(RS_THREADS), 0, (const uint64_t*)cur.keys, (const long long*)cur.vals,
-           alt.keys, alt.vals, n, shift, (const int64_t*)hist, nb);
-    std::swap(cur, alt);
-  }
-  return cur;
 }
 
 void fill_i32(Ctx& c, int32_t* p, int32_t v, int64_t n) {

@@ -131,8 +131,8 @@ struct mslice_server_s {
 
   // Device bytes a request holds while solved: the window's supra-graph
   // (24 B per supra-node, 8 B per entry), the solver's per-node scratch and
-  // hash tables (~250 B per supra-node) and the aggregation's sort buffers
-  // (~44 B per entry).
+  // hash tables (~250 B per supra-node) and the aggregation's row buffers and
+  // large-row tables (~44 B per entry).
   int64_t footprint(const SrvRequest& r) const {
     const SrvGraph& g = *graphs[r.graph];
     const int W = opt.window;
