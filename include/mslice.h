@@ -55,6 +55,10 @@ extern "C" {
  * CUDA events on the handle's stream, one span per sub-round (fills ms_decide
  * / decide_launches / decide_bytes; adds a little host overhead). */
 #define MSLICE_PROFILE 2
+/* leiden / batch run: choose the degree cuts between the decision kernels'
+ * tiers by timing the candidates on round 0 of level 0 (decisions only, so
+ * the result is unchanged); the cuts used are returned in mslice_stats. */
+#define MSLICE_AUTOTUNE 4
 
 typedef struct {
   int64_t n;              /* nodes of the snapshot (equal for all snapshots) */
@@ -88,6 +92,12 @@ typedef struct {
   int32_t stop_level;
   int32_t stop_stage;
   int32_t stop_rounds;
+  /* Degree cuts between the five decision tiers (4-lane groups, 8-lane
+   * groups, a warp, a block, a block with a global table): tier t takes
+   * degrees in (tier_cuts[t-1], tier_cuts[t]].  All zero (the default): 16,
+   * 32, 256, 1024.  Otherwise 0 <= c0 <= 16, c0 <= c1 <= 32, c1 <= c2 <= 256,
+   * c2 <= c3 <= 1024.  They change the speed only, never the result. */
+  int32_t tier_cuts[4];
 } mslice_opts;
 
 typedef struct {
@@ -115,6 +125,7 @@ typedef struct {
                                 per node (row pointer, own label, strength, decision, the own
                                 community's 16-byte table slot); probes of other candidate
                                 communities are not counted, so this is a lower bound */
+  int32_t tier_cuts[4];      /* degree cuts the decision tiers used (chosen by MSLICE_AUTOTUNE) */
 } mslice_stats;
 
 /* Defaults above; stop_level = -1. */

@@ -30,6 +30,7 @@ LIB_PATH = os.path.join(HERE, "libmslice.so")
 MSLICE_OK, MSLICE_EINVAL, MSLICE_ENOMEM, MSLICE_EOVERFLOW, MSLICE_ECUDA, MSLICE_ETIMEOUT = 0, -1, -2, -3, -4, -5
 MSLICE_DEVICE_PTRS = 1
 MSLICE_PROFILE = 2
+MSLICE_AUTOTUNE = 4
 MSLICE_ORDINAL = 0
 
 # every symbol include/mslice.h declares
@@ -61,7 +62,7 @@ class Opts(C.Structure):
                 ("max_levels", C.c_int32), ("seed", C.c_uint64), ("gamma_num", C.c_int64),
                 ("gamma_den", C.c_int64), ("omega_num", C.c_int64), ("omega_den", C.c_int64),
                 ("flags", C.c_int32), ("stop_level", C.c_int32), ("stop_stage", C.c_int32),
-                ("stop_rounds", C.c_int32)]
+                ("stop_rounds", C.c_int32), ("tier_cuts", C.c_int32 * 4)]
 
 
 class Stats(C.Structure):
@@ -71,7 +72,8 @@ class Stats(C.Structure):
                 ("next_checksum", C.c_uint64), ("stop_reason", C.c_int32), ("pad_", C.c_int32),
                 ("kernel_launches", C.c_int64), ("ms_total", C.c_double), ("ms_local_move", C.c_double),
                 ("ms_refine", C.c_double), ("ms_aggregate", C.c_double), ("ms_modularity", C.c_double),
-                ("ms_decide", C.c_double), ("decide_launches", C.c_int64), ("decide_bytes", C.c_int64)]
+                ("ms_decide", C.c_double), ("decide_launches", C.c_int64), ("decide_bytes", C.c_int64),
+                ("tier_cuts", C.c_int32 * 4)]
 
 
 class ServerOpts(C.Structure):
@@ -152,6 +154,12 @@ def _ptr(a):
     return a.ctypes.data_as(C.c_void_p)
 
 
+def _stats_dict(st) -> dict:
+    d = {f: getattr(st, f) for f, _ in Stats._fields_}
+    d["tier_cuts"] = tuple(st.tier_cuts)
+    return d
+
+
 def default_opts() -> Opts:
     o = Opts()
     lib().mslice_default_opts(C.byref(o))
@@ -191,7 +199,7 @@ class Handle:
 
     def mslice_leiden(self, gamma=(1, 1), omega=(1, 1), max_levels=32, seed=0, n_iterations=2, K=4,
                       max_rounds=100, init=None, stop_level=-1, stop_stage=0, stop_rounds=0, out=None,
-                      profile=False):
+                      profile=False, tier_cuts=None, autotune=False):
         """Returns (labels, Q, stats).  With ``out`` a device tensor (int32[N])
         the labels stay on the device (MSLICE_DEVICE_PTRS); ``init`` may then
         be a device tensor as well."""
@@ -203,6 +211,10 @@ class Handle:
         dev = out is not None and hasattr(out, "is_cuda") and out.is_cuda
         if profile:
             o.flags |= MSLICE_PROFILE
+        if autotune:
+            o.flags |= MSLICE_AUTOTUNE
+        if tier_cuts is not None:
+            o.tier_cuts[:] = list(tier_cuts)
         if dev:
             o.flags |= MSLICE_DEVICE_PTRS
         labels = out if out is not None else np.zeros(max(self.N, 1), dtype=np.int32)
@@ -213,7 +225,7 @@ class Handle:
         st = Stats()
         _check(lib().mslice_leiden_ex(self._h, C.byref(o), _ptr(init_a), _ptr(labels), C.byref(Q), C.byref(st)),
                "mslice_leiden_ex")
-        stats = {f: getattr(st, f) for f, _ in Stats._fields_}
+        stats = _stats_dict(st)
         if out is not None:
             return labels, Q.value, stats
         return labels[: st.out_n].copy(), Q.value, stats
@@ -272,14 +284,19 @@ class Batch:
         self._graphs.append(graph)
         return idx.value
 
-    def mslice_batch_run(self, n_iterations=2, K=4, max_rounds=100, max_levels=32, seed=0, profile=False) -> dict:
+    def mslice_batch_run(self, n_iterations=2, K=4, max_rounds=100, max_levels=32, seed=0, profile=False,
+                         tier_cuts=None, autotune=False) -> dict:
         o = default_opts()
         o.n_iterations, o.K, o.max_rounds, o.max_levels, o.seed = n_iterations, K, max_rounds, max_levels, seed
         if profile:
             o.flags |= MSLICE_PROFILE
+        if autotune:
+            o.flags |= MSLICE_AUTOTUNE
+        if tier_cuts is not None:
+            o.tier_cuts[:] = list(tier_cuts)
         st = Stats()
         _check(lib().mslice_batch_run(self._b, C.byref(o), C.byref(st)), "mslice_batch_run")
-        return {f: getattr(st, f) for f, _ in Stats._fields_}
+        return _stats_dict(st)
 
     def mslice_batch_info(self):
         B, N = C.c_int32(), C.c_int64()

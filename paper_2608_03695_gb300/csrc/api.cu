@@ -285,6 +285,22 @@ void check_opts(const mslice_opts& opt) {
   if (opt.n_iterations < 1 || opt.K < 1 || opt.max_rounds < 1 || opt.max_levels < 1)
     fail(MSLICE_EINVAL, "n_iterations, K, max_rounds and max_levels must be >= 1");
   if (opt.K > 64) fail(MSLICE_EINVAL, "K must be at most 64");
+  const int32_t* t = opt.tier_cuts;
+  if (t[0] || t[1] || t[2] || t[3]) {
+    int32_t lo = 0;
+    for (int k = 0; k < 4; ++k) {
+      if (t[k] < lo || t[k] > TIER_MAX[k]) fail(MSLICE_EINVAL, "tier cuts must be ascending and within 16, 32, 256, 1024");
+      lo = t[k];
+    }
+  }
+}
+
+TierCuts cuts_of(const mslice_opts& opt) {
+  TierCuts c;
+  const int32_t* t = opt.tier_cuts;
+  if (t[0] || t[1] || t[2] || t[3])
+    for (int k = 0; k < 4; ++k) c.t[k] = t[k];
+  return c;
 }
 
 // One solve (a single instance or a batch) with the options' schedule;
@@ -302,6 +318,8 @@ void run_solve(Ctx& c, const SupraGraph& G, const std::vector<InstParams>& jobs,
   p.max_levels = opt.max_levels;
   p.n_iterations = opt.n_iterations;
   p.seed = opt.seed;
+  p.cuts = cuts_of(opt);
+  p.autotune = (opt.flags & MSLICE_AUTOTUNE) != 0;
   run_leiden(c, G, jobs, p, opt.stop_level, opt.stop_stage, opt.stop_rounds, init, out, S, ro);
   std::memset(&stats, 0, sizeof(stats));
   stats.iterations = (int32_t)ro.iterations;
@@ -321,6 +339,7 @@ void run_solve(Ctx& c, const SupraGraph& G, const std::vector<InstParams>& jobs,
   stats.lm_edges = S.lm_edges;
   stats.lm_moves = S.lm_moves;
   stats.kernel_launches = c.launches;
+  for (int k = 0; k < 4; ++k) stats.tier_cuts[k] = S.p.cuts.t[k];
   if (c.trace) trace_report(c);
   if (c.profile) {
     double dms = 0;
@@ -643,7 +662,7 @@ int mslice_batch_run(mslice_batch b, const mslice_opts* o, mslice_stats* st) {
       check_cuda(cudaMemcpyAsync(init, b->init.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream), "copy");
     }
     int32_t* out = b->ws.get<int32_t>("b_out", N > 0 ? N : 1);
-    opt.flags &= MSLICE_PROFILE;
+    opt.flags &= MSLICE_PROFILE | MSLICE_AUTOTUNE;
     mslice_stats stats;
     RunOut ro;
     Solver S;

@@ -50,13 +50,21 @@ namespace mslice {
 #endif
 
 constexpr int NTIERS = 5;
+// Largest degree each of tiers 0-3 can take (their table capacities); the
+// cuts in use may be lower (TierCuts), the rest go to the next tier.
 constexpr int TIER_MAX[NTIERS - 1] = {16, 32, 256, 1024};
+
+// Degree cuts between the tiers: tier t takes degrees in (t[t-1], t[t]].
+// Which tier decides a node never changes its decision, only the speed.
+struct TierCuts {
+  int32_t t[NTIERS - 1] = {16, 32, 256, 1024};
+};
 constexpr int TIER3_BITS = 11;  // 2 * 1024 slots
 constexpr int BLOCK_THREADS = 256;
 constexpr int GROUP_THREADS = 256;
 
-__host__ __device__ __forceinline__ int degree_tier(int64_t d) {
-  return d <= 16 ? 0 : (d <= 32 ? 1 : (d <= 256 ? 2 : (d <= 1024 ? 3 : 4)));
+__host__ __device__ __forceinline__ int degree_tier(int64_t d, const TierCuts& c) {
+  return d <= c.t[0] ? 0 : (d <= c.t[1] ? 1 : (d <= c.t[2] ? 2 : (d <= c.t[3] ? 3 : 4)));
 }
 
 __device__ __forceinline__ uint32_t small_hash(int32_t key, int bits) {

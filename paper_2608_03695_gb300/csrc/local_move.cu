@@ -38,14 +38,14 @@ constexpr int EMPTY_THREADS = 512;
 
 unsigned fixed_grid(int per_sm) { return 152u * (unsigned)per_sm; }
 
-__global__ void k_tier(const int64_t* rowptr, int32_t N, uint8_t* tier, int32_t* cnt, int64_t* gsize) {
+__global__ void k_tier(const int64_t* rowptr, int32_t N, TierCuts cuts, uint8_t* tier, int32_t* cnt, int64_t* gsize) {
   const int lane = threadIdx.x & 31;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < N; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t v = base + threadIdx.x;
     int t = -1;
     if (v < N) {
       const int64_t d = rowptr[v + 1] - rowptr[v];
-      t = degree_tier(d);
+      t = degree_tier(d, cuts);
       tier[v] = (uint8_t)t;
       int64_t S = 0;
       if (t == NTIERS - 1) {
@@ -492,8 +492,8 @@ void prepare_level(Solver& S, const Level& L) {
   check_cuda(cudaMemsetAsync(cnt, 0, NTIERS * sizeof(int32_t), c.stream), "memset");
   int64_t* gsize = reinterpret_cast<int64_t*>(c.ws->get<int64_t>("s_gsize", (size_t)(N > 0 ? N : 1)));
   if (N > 0)
-    launch(c, k_tier, dim3(grid_for(N, 256) < 4096 ? grid_for(N, 256) : 4096), dim3(256), 0, L.d.rowptr, N, S.tier,
-           cnt, gsize);
+    launch(c, k_tier, dim3(grid_for(N, 256) < 4096 ? grid_for(N, 256) : 4096), dim3(256), 0, L.d.rowptr, N, S.p.cuts,
+           S.tier, cnt, gsize);
   int64_t* gtotal = c.ws->get<int64_t>("s_gtotal", 1);
   scan_excl(c, gsize, S.goff, N, gtotal);
   check_cuda(cudaMemcpyAsync(S.goff + N, gtotal, sizeof(int64_t), cudaMemcpyDeviceToDevice, c.stream), "copy");
@@ -596,6 +596,49 @@ void bucket(Solver& S, const Level& L, uint64_t tag, int it, int lvl, int r, con
            (uint64_t)it, (uint64_t)lvl, (uint64_t)r, S.p.K, S.lists, (int64_t)S.N0, to, S.cursors, active);
 }
 
+// Chooses the degree cuts of the decision tiers for this solve: every
+// candidate decides the K sub-rounds of round r twice (decisions only,
+// nothing is applied, so the state is untouched) and the candidate with the
+// fastest pass is kept.  Decisions do not depend on the tier that makes
+// them, so neither does the result.
+template <class Decide>
+static void autotune_cuts(Solver& S, const Level& L, int it, int r, const int32_t* active, Decide&& decide) {
+  Ctx& c = *S.c;
+  static const TierCuts kCand[] = {{{16, 32, 256, 1024}}, {{12, 32, 256, 1024}}, {{16, 24, 256, 1024}},
+                                   {{16, 32, 256, 512}},  {{12, 24, 256, 512}},  {{16, 32, 192, 1024}}};
+  cudaEvent_t e0, e1;
+  check_cuda(cudaEventCreate(&e0), "event");
+  check_cuda(cudaEventCreate(&e1), "event");
+  float best = 0;
+  TierCuts chosen = kCand[0];
+  // the first pass warms the caches and is not counted
+  for (int k = -1; k < (int)(sizeof(kCand) / sizeof(kCand[0])); ++k) {
+    S.p.cuts = kCand[k < 0 ? 0 : k];
+    prepare_level(S, L);
+    bucket(S, L, 0, it, 0, r, active);
+    float ms = 0;
+    for (int rep = 0; rep < 2; ++rep) {
+      check_cuda(cudaEventRecord(e0, c.stream), "event");
+      for (int q = 0; q < S.p.K; ++q) decide(bucket_segments(S, q));
+      check_cuda(cudaEventRecord(e1, c.stream), "event");
+      check_cuda(cudaEventSynchronize(e1), "event");
+      float x = 0;
+      check_cuda(cudaEventElapsedTime(&x, e0, e1), "event time");
+      ms = rep == 0 ? x : std::min(ms, x);
+    }
+    if (k >= 0 && (k == 0 || ms < best)) {
+      best = ms;
+      chosen = kCand[k];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  S.p.cuts = chosen;
+  S.p.autotune = false;
+  prepare_level(S, L);
+  fill_i32(c, S.target, NO_MOVE, L.d.N);
+}
+
 MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, int max_rounds) {
   Ctx& c = *S.c;
   MoveOut out;
@@ -642,6 +685,8 @@ MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, 
   bool rebuild = false;
   for (int r = 0; r < max_rounds; ++r) {
     if (rebuild) rebuild_sigma(S, L, labels, false);
+    // tuning waits for round 2, when the partition looks like the later rounds'
+    if (S.p.autotune && lvl == 0 && r == 2) autotune_cuts(S, L, it, r, batch ? S.lm_active : S.inst_active, decide);
     check_cuda(cudaMemsetAsync(S.counters, 0, 3 * sizeof(int32_t), c.stream), "memset");
     bucket(S, L, 0, it, lvl, r, batch ? S.lm_active : S.inst_active);
     S.lm_rounds++;

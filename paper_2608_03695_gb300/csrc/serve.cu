@@ -262,6 +262,10 @@ void run_batch(mslice_server_s* s, Worker& slot, std::vector<SrvRequest*>& batch
     sp.max_levels = s->opt.solve.max_levels;
     sp.n_iterations = s->opt.solve.n_iterations;
     sp.seed = s->opt.solve.seed;
+    for (int k = 0; k < 4; ++k)
+      if (s->opt.solve.tier_cuts[0] || s->opt.solve.tier_cuts[1] || s->opt.solve.tier_cuts[2] ||
+          s->opt.solve.tier_cuts[3])
+        sp.cuts.t[k] = s->opt.solve.tier_cuts[k];
     Solver S;
     RunOut ro;
     const double tb = s->now();
@@ -395,6 +399,13 @@ int mslice_server_create(const mslice_server_opts* o, mslice_server* out) {
     const mslice_opts& so = opt.solve;
     if (so.n_iterations < 1 || so.K < 1 || so.K > 64 || so.max_rounds < 1 || so.max_levels < 1)
       fail(MSLICE_EINVAL, "bad schedule options");
+    if (so.tier_cuts[0] || so.tier_cuts[1] || so.tier_cuts[2] || so.tier_cuts[3]) {
+      int32_t lo = 0;
+      for (int k = 0; k < 4; ++k) {
+        if (so.tier_cuts[k] < lo || so.tier_cuts[k] > TIER_MAX[k]) fail(MSLICE_EINVAL, "bad tier cuts");
+        lo = so.tier_cuts[k];
+      }
+    }
     const int64_t lim = (int64_t)1 << 31;
     if (opt.gamma_num < 1 || opt.gamma_num > lim || opt.gamma_den < 1 || opt.gamma_den > lim || opt.omega_num < 0 ||
         opt.omega_num > lim || opt.omega_den < 1 || opt.omega_den > lim)

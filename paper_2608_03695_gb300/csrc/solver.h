@@ -3,6 +3,7 @@
 #include <vector>
 
 #include "build.h"
+#include "decide.cuh"
 #include "level.h"
 
 namespace mslice {
@@ -11,6 +12,8 @@ struct SolveParams {
   long long gn = 1, gd = 1, on = 1, od = 1;
   int32_t K = 4, max_rounds = 100, max_levels = 32, n_iterations = 2;
   uint64_t seed = 0;
+  TierCuts cuts;          // degree cuts between the decision tiers
+  bool autotune = false;  // choose the cuts by timing round 0 of level 0
 };
 
 // CUDA-event phase timing: events recorded on the context's stream.

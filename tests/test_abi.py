@@ -78,5 +78,34 @@ def test_struct_layouts_match_header():
     assert C.sizeof(pkg.Csr) == 32
     assert C.sizeof(pkg.ServerOpts) == 16 + 8 + 32 + C.sizeof(pkg.Opts)
     assert C.sizeof(pkg.RequestInfo) == 8 + 8 + 8 + 24 + 8 + 8 + 16
-    assert C.sizeof(pkg.Opts) == 4 * 4 + 8 + 4 * 8 + 4 * 4
-    assert C.sizeof(pkg.Stats) == 4 + 4 + 8 * 7 + 8 + 4 + 4 + 8 + 8 * 5 + 8 * 3
+    assert C.sizeof(pkg.Opts) == 4 * 4 + 8 + 4 * 8 + 4 * 4 + 4 * 4
+    assert C.sizeof(pkg.Stats) == 4 + 4 + 8 * 7 + 8 + 4 + 4 + 8 + 8 * 5 + 8 * 3 + 4 * 4
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """Sizes and field offsets of every ABI struct, as gcc lays them out from
+    include/mslice.h, equal the ctypes mirrors of the binding."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    mirrors = {"mslice_csr": pkg.Csr, "mslice_opts": pkg.Opts, "mslice_stats": pkg.Stats,
+               "mslice_server_opts": pkg.ServerOpts, "mslice_request_info": pkg.RequestInfo}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mslice.h"', 'int main(void) {']
+    for cname, cls in mirrors.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = {}
+    for line in subprocess.check_output([str(exe)]).decode().splitlines():
+        cname, field, val = line.split()
+        got[(cname, field)] = int(val)
+    for cname, cls in mirrors.items():
+        assert got[(cname, "size")] == C.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)

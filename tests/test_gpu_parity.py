@@ -258,3 +258,21 @@ def test_hashed_tables_medium(monkeypatch):
     snaps = synth.config_graph({**synth.CONFIGS[2], "n": 6000, "T": 5})
     g, o = solve_both(snaps)
     assert_same(g, o)
+
+
+def test_tier_cuts_and_autotune_do_not_change_results():
+    """The degree cuts decide only which kernel decides a node: any valid
+    cuts, and the autotuner's choice, give the same bits."""
+    snaps = synth.config_graph({**synth.CONFIGS[2], "n": 6000, "T": 5})
+    ref, Qref, _ = oracle.leiden(snaps)
+    with pkg.mslice_build(snaps) as h:
+        for cuts in [(16, 32, 256, 1024), (0, 0, 0, 0), (4, 8, 16, 32), (16, 16, 64, 64), (0, 32, 256, 1024)]:
+            lab, Q, st = h.mslice_leiden(tier_cuts=cuts)
+            assert np.array_equal(lab, ref) and Q == Qref, cuts
+        lab, Q, st = h.mslice_leiden(autotune=True)
+        assert np.array_equal(lab, ref) and Q == Qref
+        c = st["tier_cuts"]
+        assert 0 <= c[0] <= 16 and c[0] <= c[1] <= 32 and c[1] <= c[2] <= 256 and c[2] <= c[3] <= 1024
+        for bad in [(17, 32, 256, 1024), (16, 8, 256, 1024), (16, 32, 256, 2048), (-1, 32, 256, 1024)]:
+            with pytest.raises(pkg.MsliceError):
+                h.mslice_leiden(tier_cuts=bad)
