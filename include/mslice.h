@@ -276,8 +276,9 @@ void mslice_batch_free(mslice_batch b);
  * Requests are served by n_slots workers, each with its own CUDA stream.  A
  * free worker admits the queued requests, in arrival order, whose estimated
  * device footprint fits in what is left of the memory budget (at most one
- * in-flight request per graph, up to max_batch, never overtaking a request
- * that does not fit) and solves them as one batch; requests that arrive while
+ * in-flight request per graph, up to max_batch requests and max_batch_nodes
+ * supra-nodes, never overtaking a request that does not fit) and solves them
+ * as one batch; requests that arrive while
  * other workers' batches run are admitted as workers and memory free up, so
  * their work overlaps on the device.  A request larger than the whole budget
  * runs alone once nothing else is in flight. */
@@ -288,6 +289,9 @@ typedef struct {
   int32_t n_slots;     /* concurrent workers (CUDA streams); default 2 */
   int32_t max_batch;   /* requests per batch; default 64 */
   int32_t pad_;
+  int64_t max_batch_nodes; /* supra-nodes per batch; default 2^21, which keeps a batch's randomly
+                              accessed state (~50 B per supra-node) in L2; a larger request runs
+                              alone */
   int64_t hbm_budget;  /* bytes of device memory admitted work may use; 0 (default): 80% of the free
                           memory when the server is created */
   int64_t gamma_num, gamma_den, omega_num, omega_den; /* default 1/1, 1/1 */

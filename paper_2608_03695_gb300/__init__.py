@@ -78,7 +78,7 @@ class Stats(C.Structure):
 
 class ServerOpts(C.Structure):
     _fields_ = [("window", C.c_int32), ("n_slots", C.c_int32), ("max_batch", C.c_int32), ("pad_", C.c_int32),
-                ("hbm_budget", C.c_int64), ("gamma_num", C.c_int64), ("gamma_den", C.c_int64),
+                ("max_batch_nodes", C.c_int64), ("hbm_budget", C.c_int64), ("gamma_num", C.c_int64), ("gamma_den", C.c_int64),
                 ("omega_num", C.c_int64), ("omega_den", C.c_int64), ("solve", Opts)]
 
 
@@ -341,10 +341,12 @@ class Server:
     :meth:`Handle.mslice_leiden` on the window with those initial labels."""
 
     def __init__(self, window=8, n_slots=2, max_batch=64, hbm_budget=0, gamma=(1, 1), omega=(1, 1),
-                 n_iterations=2, K=4, max_rounds=100, max_levels=32, seed=0):
+                 n_iterations=2, K=4, max_rounds=100, max_levels=32, seed=0, max_batch_nodes=None):
         o = ServerOpts()
         lib().mslice_server_default_opts(C.byref(o))
         o.window, o.n_slots, o.max_batch, o.hbm_budget = window, n_slots, max_batch, hbm_budget
+        if max_batch_nodes is not None:
+            o.max_batch_nodes = max_batch_nodes
         o.gamma_num, o.gamma_den = gamma
         o.omega_num, o.omega_den = omega
         o.solve.n_iterations, o.solve.K, o.solve.max_rounds = n_iterations, K, max_rounds

@@ -133,6 +133,12 @@ struct mslice_server_s {
   // (24 B per supra-node, 8 B per entry), the solver's per-node scratch and
   // hash tables (~250 B per supra-node) and the aggregation's row buffers and
   // large-row tables (~44 B per entry).
+  // Supra-nodes of the window a request will solve.
+  int64_t window_nodes(const SrvRequest& r) const {
+    const SrvGraph& g = *graphs[r.graph];
+    return g.n * std::min<int64_t>((int64_t)g.window.size() + 1, opt.window);
+  }
+
   int64_t footprint(const SrvRequest& r) const {
     const SrvGraph& g = *graphs[r.graph];
     const int W = opt.window;
@@ -304,7 +310,7 @@ void worker_loop(mslice_server_s* s, Worker* slot) {
   cudaSetDevice(s->device);
   for (;;) {
     std::vector<SrvRequest*> batch;
-    int64_t fp_total = 0;
+    int64_t fp_total = 0, nodes_total = 0;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       for (;;) {
@@ -319,6 +325,9 @@ void worker_loop(mslice_server_s* s, Worker* slot) {
           const int64_t fp = s->footprint(*r);
           const bool alone = s->used == 0 && fp_total == 0;
           if (!alone && s->used + fp_total + fp > s->opt.hbm_budget) break;
+          const int64_t nodes = s->window_nodes(*r);
+          if (!batch.empty() && nodes_total + nodes > s->opt.max_batch_nodes) break;
+          nodes_total += nodes;
           r->info.footprint = fp;
           fp_total += fp;
           batch.push_back(r);
@@ -381,6 +390,7 @@ void mslice_server_default_opts(mslice_server_opts* o) {
   o->window = 8;
   o->n_slots = 2;
   o->max_batch = 64;
+  o->max_batch_nodes = (int64_t)1 << 21;
   o->hbm_budget = 0;
   o->gamma_num = o->gamma_den = o->omega_num = o->omega_den = 1;
   mslice_default_opts(&o->solve);
@@ -394,8 +404,9 @@ int mslice_server_create(const mslice_server_opts* o, mslice_server* out) {
     mslice_server_opts opt;
     mslice_server_default_opts(&opt);
     if (o) opt = *o;
-    if (opt.window < 1 || opt.n_slots < 1 || opt.n_slots > 64 || opt.max_batch < 1 || opt.hbm_budget < 0)
-      fail(MSLICE_EINVAL, "window, n_slots (<= 64) and max_batch must be >= 1, hbm_budget >= 0");
+    if (opt.window < 1 || opt.n_slots < 1 || opt.n_slots > 64 || opt.max_batch < 1 || opt.hbm_budget < 0 ||
+        opt.max_batch_nodes < 1)
+      fail(MSLICE_EINVAL, "window, n_slots (<= 64), max_batch and max_batch_nodes must be >= 1, hbm_budget >= 0");
     const mslice_opts& so = opt.solve;
     if (so.n_iterations < 1 || so.K < 1 || so.K > 64 || so.max_rounds < 1 || so.max_levels < 1)
       fail(MSLICE_EINVAL, "bad schedule options");

@@ -69,14 +69,14 @@ def test_host_side_rejections_need_no_gpu():
     L.mslice_server_free(None)
     o = pkg.ServerOpts()
     L.mslice_server_default_opts(C.byref(o))
-    assert (o.window, o.n_slots, o.max_batch, o.hbm_budget) == (8, 2, 64, 0)
+    assert (o.window, o.n_slots, o.max_batch, o.hbm_budget, o.max_batch_nodes) == (8, 2, 64, 0, 1 << 21)
     assert (o.solve.n_iterations, o.solve.K, o.solve.stop_level) == (2, 4, -1)
 
 
 def test_struct_layouts_match_header():
     # field order and sizes of the ctypes mirrors follow include/mslice.h
     assert C.sizeof(pkg.Csr) == 32
-    assert C.sizeof(pkg.ServerOpts) == 16 + 8 + 32 + C.sizeof(pkg.Opts)
+    assert C.sizeof(pkg.ServerOpts) == 16 + 8 + 8 + 32 + C.sizeof(pkg.Opts)
     assert C.sizeof(pkg.RequestInfo) == 8 + 8 + 8 + 24 + 8 + 8 + 16
     assert C.sizeof(pkg.Opts) == 4 * 4 + 8 + 4 * 8 + 4 * 4 + 4 * 4
     assert C.sizeof(pkg.Stats) == 4 + 4 + 8 * 7 + 8 + 4 + 4 + 8 + 8 * 5 + 8 * 3 + 4 * 4
