@@ -13,6 +13,7 @@ step's device time.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mslice|reference]
   python bench.py --workload batched [--scale S]
   python bench.py --workload serving [--scale S] [--requests R] [--slots K]
+  python bench.py --workload large [--scale S]
 
 The batched workload (64 temporal planted-partition graphs of uneven n and
 T, each solved at 6 gammas x 3 omegas = 1,152 solves) is timed twice on the
@@ -57,7 +58,7 @@ def parse():
     ap.add_argument("--impl", default="mslice", choices=["mslice", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving", "large"])
     ap.add_argument("--requests", type=int, default=4, help="serving workload: timed snapshots per graph")
     ap.add_argument("--slots", type=int, default=2, help="serving workload: server workers")
     ap.add_argument("--scale", type=float, default=1.0, help="batched workload: node-count scale of every graph")
@@ -444,6 +445,71 @@ def _plain_window_solve(pkg, snaps, t, W, prev, n):
     return lab, Q
 
 
+def run_large(args):
+    """The T=64, n=1,000,000 power-law recipe (64M supra-nodes, ~1.15G stored
+    entries) at omega = 1/10, 1 and 10: three plain solves on one handle, then
+    the same three as one batch when the device has room for it; both must
+    give the same labels and Q."""
+    import hashlib
+    import torch
+    import paper_2608_03695_gb300 as pkg
+    from paper_2608_03695_gb300 import synth
+    n = int(synth.CONFIGS[4]["n"] * args.scale)
+    t = time.perf_counter()
+    snaps = synth.config_graph(4, scale_n=n)
+    t_gen = time.perf_counter() - t
+    torch.cuda.set_device(0)
+    omegas = [(1, 10), (1, 1), (10, 1)]
+    clocks = ClockSampler(0)
+    clocks.start()
+    t = time.perf_counter()
+    h = pkg.mslice_build(snaps)
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t
+    del snaps
+
+    def digest(lab):
+        return hashlib.sha1(np.ascontiguousarray(lab, dtype=np.int32).tobytes()).hexdigest()
+
+    plain, work, ms_plain = [], 0, 0.0
+    t = time.perf_counter()
+    for om in omegas:
+        lab, Q, st = h.mslice_leiden(omega=om)
+        plain.append((digest(lab), Q))
+        work += st["lm_edges"]
+        ms_plain += st["ms_total"]
+    t_plain = time.perf_counter() - t
+    free, _ = torch.cuda.mem_get_info()
+    need = 3 * (300 * h.N + 60 * h.nnz)
+    batched = None
+    if free > need:
+        t = time.perf_counter()
+        with pkg.Batch() as b:
+            for om in omegas:
+                b.add(h, (1, 1), om)
+            st = b.run()
+            batched = [(digest(b.results(i)[0]), b.results(i)[1]) for i in range(3)]
+        t_batch = time.perf_counter() - t
+    clk = clocks.stop()
+    same = batched is None or batched == plain
+    line = {"metric": "supra-edges/s in Leiden local-move (large)", "value": work / t_plain, "unit": UNIT,
+            "n_gpus": 1, "steps": 3, "warmup": 0, "ms_per_step": 1e3 * t_plain / 3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "multislice Leiden, power-law temporal DC-SBM, T=64", "n": n, "T": 64,
+                       "deg_exp": 2.3, "mean_deg": 16, "mixing": 0.4, "churn": 0.05, "weights": "1-16",
+                       "gamma": "1/1", "omega": ["1/10", "1/1", "10/1"], "supra_nodes": h.N, "entries": h.nnz,
+                       "parallelism": "single", "l2": "inputs larger than L2"},
+            "plain": {"seconds": t_plain, "device_ms": ms_plain, "Q": [q for _, q in plain]},
+            "batched": (None if batched is None else
+                        {"value": work / t_batch, "unit": UNIT, "seconds": t_batch, "device_ms": st["ms_total"]}),
+            "batched_note": None if batched is not None else f"skipped: {free / 1e9:.0f} GB free, ~{need / 1e9:.0f} GB needed",
+            "identical_results": same, "build_s": t_build, "generate_s": t_gen, "clocks": clk}
+    h.close()
+    print(json.dumps(line), flush=True)
+    if not same:
+        raise SystemExit("batched results differ from the plain solves")
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -452,6 +518,8 @@ def main():
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "large":
+        return run_large(args)
     import torch
     import paper_2608_03695_gb300 as pkg
     from paper_2608_03695_gb300 import synth
