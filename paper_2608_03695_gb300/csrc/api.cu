@@ -49,6 +49,24 @@ void check_cuda(cudaError_t e, const char* what) {
 
 Workspace::~Workspace() { release_all(); }
 
+// Host-side fault injection for the tests: with MSLICE_FAIL_ALLOC_AFTER=k in
+// the environment, every device allocation after the first k (counted since
+// the variable last changed) fails as if the device were out of memory.
+static bool injected_alloc_failure() {
+  static std::mutex mu;
+  static std::string last;
+  static long long count = 0;
+  const char* e = std::getenv("MSLICE_FAIL_ALLOC_AFTER");
+  std::lock_guard<std::mutex> lk(mu);
+  const std::string cur = e ? e : "";
+  if (cur != last) {
+    last = cur;
+    count = 0;
+  }
+  if (cur.empty()) return false;
+  return count++ >= std::atoll(cur.c_str());
+}
+
 void* Workspace::get_bytes(const std::string& name, size_t bytes) {
   bytes = (bytes + 255) & ~(size_t)255;
   auto it = bufs_.find(name);
@@ -57,6 +75,8 @@ void* Workspace::get_bytes(const std::string& name, size_t bytes) {
     cudaFreeAsync(it->second.first, stream);
     bufs_.erase(it);
   }
+  if (injected_alloc_failure())
+    fail(MSLICE_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes for " + name + " failed (injected)");
   void* p = nullptr;
   cudaError_t e = cudaMallocAsync(&p, bytes, stream);
   if (e != cudaSuccess) {
