@@ -331,6 +331,27 @@ int mslice_server_submit(mslice_server s, int32_t graph_id, const mslice_csr* sl
  * the request.  Returns the request's status; EINVAL for an unknown id. */
 int mslice_server_wait(mslice_server s, int64_t request_id, int32_t* labels_out, mslice_request_info* info);
 
+/* Checkpoint and resume of a live graph's window: the snapshots it holds and
+ * the labels of its last result, which is all the state the next request
+ * reads.  The graph must be idle (no request of it queued or in flight), else
+ * MSLICE_EINVAL.
+ * window_info: *slices = snapshots held (0..W); nnz (nullable, one entry per
+ *   snapshot held, oldest first) = their stored entries.
+ * window_read: k in [0, slices): snapshot k (oldest = 0) into host indptr
+ *   (n+1), indices and weights (nnz[k] each); k = -1: the window's labels into
+ *   host int32[n * slices].
+ * window_restore: replaces the window with nslices (1..W) host snapshots,
+ *   oldest first, and their labels (host int32[n * nslices], values in
+ *   [0, n * nslices)), as a previous result would have left them; the next
+ *   submitted snapshot is solved from them exactly as if the server had
+ *   produced them.  The snapshots are validated like a build; on any error
+ *   the window is left as it was.  Errors: EINVAL, ENOMEM, ECUDA. */
+int mslice_server_window_info(mslice_server s, int32_t graph_id, int32_t* slices, int64_t* nnz);
+int mslice_server_window_read(mslice_server s, int32_t graph_id, int32_t k, int64_t* indptr, int32_t* indices,
+                              int32_t* weights, int32_t* labels);
+int mslice_server_window_restore(mslice_server s, int32_t graph_id, const mslice_csr* slices, int32_t nslices,
+                                 const int32_t* labels);
+
 /* Finishes the queued requests, stops the workers and releases the server
  * and its device memory (NULL is ignored). */
 void mslice_server_free(mslice_server s);

@@ -40,7 +40,8 @@ EXPORTS = ["mslice_default_opts", "mslice_build", "mslice_build_ex", "mslice_lei
            "mslice_batch_add", "mslice_batch_run", "mslice_batch_results", "mslice_batch_info",
            "mslice_batch_clear", "mslice_batch_kernel_launches", "mslice_batch_free",
            "mslice_server_default_opts", "mslice_server_create", "mslice_server_add_graph",
-           "mslice_server_submit", "mslice_server_wait", "mslice_server_free"]
+           "mslice_server_submit", "mslice_server_wait", "mslice_server_free", "mslice_server_window_info",
+           "mslice_server_window_read", "mslice_server_window_restore"]
 
 
 class LibraryMissing(RuntimeError):
@@ -137,6 +138,9 @@ def lib():
         L.mslice_server_wait.argtypes = [P, C.c_int64, P, P]
         L.mslice_server_free.argtypes = [P]
         L.mslice_server_free.restype = None
+        L.mslice_server_window_info.argtypes = [P, C.c_int32, P, P]
+        L.mslice_server_window_read.argtypes = [P, C.c_int32, C.c_int32, P, P, P, P]
+        L.mslice_server_window_restore.argtypes = [P, C.c_int32, P, C.c_int32, P]
         _lib = L
     return _lib
 
@@ -403,9 +407,46 @@ class Server:
         _check(rc, "mslice_server_wait")
         return labels[: info.N].copy(), d
 
+    def mslice_server_checkpoint(self, graph_id: int):
+        """(snapshots, labels) of an idle graph's window: the state its next
+        request reads (snapshots oldest first, as Snapshot-like objects)."""
+        from .synth import Snapshot
+        w = C.c_int32(0)
+        _check(lib().mslice_server_window_info(self._s, graph_id, C.byref(w), None), "mslice_server_window_info")
+        nnz = np.zeros(max(w.value, 1), dtype=np.int64)
+        _check(lib().mslice_server_window_info(self._s, graph_id, C.byref(w), _ptr(nnz)), "mslice_server_window_info")
+        n = self._n[graph_id]
+        snaps = []
+        for k in range(w.value):
+            ip = np.zeros(n + 1, dtype=np.int64)
+            ix = np.zeros(max(int(nnz[k]), 1), dtype=np.int32)
+            wt = np.zeros(max(int(nnz[k]), 1), dtype=np.int32)
+            _check(lib().mslice_server_window_read(self._s, graph_id, k, _ptr(ip), _ptr(ix), _ptr(wt), None),
+                   "mslice_server_window_read")
+            snaps.append(Snapshot(ip, ix[: nnz[k]], wt[: nnz[k]]))
+        labels = np.zeros(max(n * w.value, 1), dtype=np.int32)
+        _check(lib().mslice_server_window_read(self._s, graph_id, -1, None, None, None, _ptr(labels)),
+               "mslice_server_window_read")
+        return snaps, labels[: n * w.value]
+
+    def mslice_server_restore(self, graph_id: int, snaps, labels):
+        arr = (Csr * len(snaps))()
+        keep = []
+        for k, sn in enumerate(snaps):
+            ip = np.ascontiguousarray(sn.indptr, dtype=np.int64)
+            ix = np.ascontiguousarray(sn.indices, dtype=np.int32)
+            wt = np.ascontiguousarray(sn.weights, dtype=np.int32)
+            keep += [ip, ix, wt]
+            arr[k] = Csr(len(ip) - 1, _ptr(ip).value, _ptr(ix).value, _ptr(wt).value)
+        lab = np.ascontiguousarray(labels, dtype=np.int32)
+        _check(lib().mslice_server_window_restore(self._s, graph_id, C.cast(arr, C.c_void_p), len(snaps), _ptr(lab)),
+               "mslice_server_window_restore")
+
     add_graph = mslice_server_add_graph
     submit = mslice_server_submit
     wait = mslice_server_wait
+    checkpoint = mslice_server_checkpoint
+    restore = mslice_server_restore
 
 
 def mslice_build(snaps, omega=(1, 1), stream=None, device_ptrs=False, host_tensors=False) -> Handle:

@@ -532,6 +532,178 @@ int mslice_server_wait(mslice_server s, int64_t request_id, int32_t* labels_out,
   return MSLICE_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Marks an idle graph busy for a checkpoint or restore (no request of it may
+// be queued or in flight); released by the destructor.
+struct IdleGraph {
+  mslice_server_s* s;
+  SrvGraph* g = nullptr;
+  IdleGraph(mslice_server_s* srv, int32_t graph_id) : s(srv) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (graph_id < 0 || graph_id >= (int32_t)s->graphs.size()) fail(MSLICE_EINVAL, "unknown graph");
+    SrvGraph* gg = s->graphs[graph_id].get();
+    if (gg->busy) fail(MSLICE_EINVAL, "the graph has a request in flight");
+    for (int64_t id : s->queue)
+      if (s->reqs[id]->graph == graph_id) fail(MSLICE_EINVAL, "the graph has queued requests");
+    gg->busy = true;
+    g = gg;
+  }
+  ~IdleGraph() {
+    if (!g) return;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      g->busy = false;
+    }
+    s->cv_work.notify_all();
+  }
+};
+
+// A private stream, scratch and status word for work done on the caller's
+// thread.
+struct CallerCtx {
+  cudaStream_t stream = nullptr;
+  Workspace ws;
+  unsigned* d_status = nullptr;
+  void* pinned = nullptr;
+  Ctx c;
+  CallerCtx() {
+    check_cuda(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking), "stream");
+    ws.stream = stream;
+    check_cuda(cudaMallocHost(&pinned, PINNED_BYTES), "pinned buffer");
+    d_status = ws.get<unsigned>("status", 4);
+    check_cuda(cudaMemsetAsync(d_status, 0, 16, stream), "memset");
+    c.stream = stream;
+    c.ws = &ws;
+    c.d_status = d_status;
+    c.pinned = pinned;
+  }
+  ~CallerCtx() {
+    ws.release_all();
+    if (pinned) cudaFreeHost(pinned);
+    if (stream) cudaStreamDestroy(stream);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+int mslice_server_window_info(mslice_server s, int32_t graph_id, int32_t* slices, int64_t* nnz) {
+  return guard_srv([&] {
+    if (!s) fail(MSLICE_EINVAL, "null server");
+    IdleGraph ig(s, graph_id);
+    if (slices) *slices = (int32_t)ig.g->window.size();
+    if (nnz)
+      for (size_t k = 0; k < ig.g->window.size(); ++k) nnz[k] = ig.g->nnz[ig.g->window[k]];
+  });
+}
+
+int mslice_server_window_read(mslice_server s, int32_t graph_id, int32_t k, int64_t* indptr, int32_t* indices,
+                              int32_t* weights, int32_t* labels) {
+  return guard_srv([&] {
+    if (!s) fail(MSLICE_EINVAL, "null server");
+    IdleGraph ig(s, graph_id);
+    SrvGraph& g = *ig.g;
+    const int32_t w = (int32_t)g.window.size();
+    check_cuda(cudaSetDevice(s->device), "device");
+    if (k == -1) {
+      if (w > 0) {
+        if (!labels) fail(MSLICE_EINVAL, "null labels");
+        check_cuda(cudaMemcpy(labels, g.labels, g.n * w * sizeof(int32_t), cudaMemcpyDeviceToHost), "copy");
+      }
+      return;
+    }
+    if (k < 0 || k >= w) fail(MSLICE_EINVAL, "no such snapshot in the window");
+    const int b = g.window[k];
+    if (!indptr || (g.nnz[b] > 0 && (!indices || !weights))) fail(MSLICE_EINVAL, "null output arrays");
+    check_cuda(cudaMemcpy(indptr, g.ip[b], (g.n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost), "copy");
+    if (g.nnz[b] > 0) {
+      check_cuda(cudaMemcpy(indices, g.ix[b], g.nnz[b] * sizeof(int32_t), cudaMemcpyDeviceToHost), "copy");
+      check_cuda(cudaMemcpy(weights, g.wt[b], g.nnz[b] * sizeof(int32_t), cudaMemcpyDeviceToHost), "copy");
+    }
+  });
+}
+
+int mslice_server_window_restore(mslice_server s, int32_t graph_id, const mslice_csr* slices, int32_t nslices,
+                                 const int32_t* labels) {
+  return guard_srv([&] {
+    if (!s) fail(MSLICE_EINVAL, "null server");
+    if (!slices || !labels || nslices < 1 || nslices > s->opt.window)
+      fail(MSLICE_EINVAL, "need 1..window snapshots and their labels");
+    IdleGraph ig(s, graph_id);
+    SrvGraph& g = *ig.g;
+    const int64_t n = g.n, N = n * nslices;
+    for (int32_t k = 0; k < nslices; ++k) {
+      if (slices[k].n != n || !slices[k].indptr) fail(MSLICE_EINVAL, "snapshot n differs from the graph's");
+      const int64_t z = slices[k].indptr[n];
+      if (slices[k].indptr[0] != 0 || z < 0) fail(MSLICE_EINVAL, "malformed row pointers");
+      if (z > 0 && (!slices[k].indices || !slices[k].weights)) fail(MSLICE_EINVAL, "null indices/weights");
+    }
+    for (int64_t v = 0; v < N; ++v)
+      if (labels[v] < 0 || labels[v] >= N) fail(MSLICE_EINVAL, "labels must lie in [0, n * nslices)");
+    check_cuda(cudaSetDevice(s->device), "device");
+    CallerCtx cc;
+    Ctx& c = cc.c;
+    // upload to scratch and validate as a build would, before touching the ring
+    std::vector<const int64_t*> ip(nslices);
+    std::vector<const int32_t*> ix(nslices), wt(nslices);
+    std::vector<int64_t> nnz(nslices);
+    for (int32_t k = 0; k < nslices; ++k) {
+      const std::string tag = std::to_string(k);
+      nnz[k] = slices[k].indptr[n];
+      int64_t* dip = cc.ws.get<int64_t>("r_ip" + tag, n + 1);
+      int32_t* dix = cc.ws.get<int32_t>("r_ix" + tag, nnz[k]);
+      int32_t* dwt = cc.ws.get<int32_t>("r_wt" + tag, nnz[k]);
+      check_cuda(cudaMemcpyAsync(dip, slices[k].indptr, (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c.stream),
+                 "copy");
+      if (nnz[k] > 0) {
+        check_cuda(cudaMemcpyAsync(dix, slices[k].indices, nnz[k] * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                   c.stream), "copy");
+        check_cuda(cudaMemcpyAsync(dwt, slices[k].weights, nnz[k] * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                   c.stream), "copy");
+      }
+      ip[k] = dip;
+      ix[k] = dix;
+      wt[k] = dwt;
+    }
+    {
+      SupraGraph check;
+      check.mem.stream = c.stream;
+      build_supra(c, ip, ix, wt, nnz, n, check);
+      check_bounds(n, check.T, check.two_m_host.data(), s->opt.gamma_num, s->opt.gamma_den, s->opt.omega_num,
+                   s->opt.omega_den);
+    }
+    // valid: the ring's buffers 0..nslices-1 take the snapshots
+    g.mem.stream = c.stream;
+    for (int32_t k = 0; k < nslices; ++k) {
+      const std::string tag = std::to_string(k);
+      g.ip[k] = g.mem.get<int64_t>("ip" + tag, n + 1);
+      if (nnz[k] > g.cap_ix[k] || !g.ix[k]) {
+        g.ix[k] = g.mem.get<int32_t>("ix" + tag, nnz[k]);
+        g.wt[k] = g.mem.get<int32_t>("wt" + tag, nnz[k]);
+        g.cap_ix[k] = std::max<int64_t>(nnz[k], 1);
+      }
+      check_cuda(cudaMemcpyAsync(g.ip[k], ip[k], (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, c.stream), "copy");
+      if (nnz[k] > 0) {
+        check_cuda(cudaMemcpyAsync(g.ix[k], ix[k], nnz[k] * sizeof(int32_t), cudaMemcpyDeviceToDevice, c.stream),
+                   "copy");
+        check_cuda(cudaMemcpyAsync(g.wt[k], wt[k], nnz[k] * sizeof(int32_t), cudaMemcpyDeviceToDevice, c.stream),
+                   "copy");
+      }
+      g.nnz[k] = nnz[k];
+    }
+    g.labels = g.mem.get<int32_t>("labels", N);
+    check_cuda(cudaMemcpyAsync(g.labels, labels, N * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream), "copy");
+    check_cuda(cudaStreamSynchronize(c.stream), "stream synchronize");
+    g.mem.stream = nullptr;  // the private stream ends with this call
+    g.window.clear();
+    for (int32_t k = 0; k < nslices; ++k) g.window.push_back(k);
+  });
+}
+
 void mslice_server_free(mslice_server s) {
   if (!s) return;
   {

@@ -66,6 +66,9 @@ def test_host_side_rejections_need_no_gpu():
     assert L.mslice_server_add_graph(None, 10, None) == pkg.MSLICE_EINVAL
     assert L.mslice_server_submit(None, 0, None, None) == pkg.MSLICE_EINVAL
     assert L.mslice_server_wait(None, 1, None, None) == pkg.MSLICE_EINVAL
+    assert L.mslice_server_window_info(None, 0, None, None) == pkg.MSLICE_EINVAL
+    assert L.mslice_server_window_read(None, 0, 0, None, None, None, None) == pkg.MSLICE_EINVAL
+    assert L.mslice_server_window_restore(None, 0, None, 0, None) == pkg.MSLICE_EINVAL
     L.mslice_server_free(None)
     o = pkg.ServerOpts()
     L.mslice_server_default_opts(C.byref(o))

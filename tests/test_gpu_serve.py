@@ -155,3 +155,52 @@ def test_server_rejects_bad_arguments():
             srv.submit(g, stream(12, 1, 0)[0])  # n differs
         with pytest.raises(pkg.MsliceError):
             srv.wait(12345)
+
+
+def test_checkpoint_and_resume_give_identical_bits():
+    """A window checkpointed after some requests and restored into a new
+    server continues exactly as the uninterrupted server does."""
+    W, n = 3, 120
+    snaps = stream(n, 8, seed=41)
+    with pkg.Server(window=W, n_slots=2) as srv:
+        g = srv.add_graph(n)
+        whole = [srv.wait(srv.submit(g, sn)) for sn in snaps]
+    with pkg.Server(window=W, n_slots=1) as srv:
+        g = srv.add_graph(n)
+        for t in range(5):
+            srv.wait(srv.submit(g, snaps[t]))
+        saved, labels = srv.checkpoint(g)
+    assert len(saved) == W and len(labels) == W * n
+    for k, sn in enumerate(saved):  # the window holds the last W snapshots
+        ref = snaps[5 - W + k]
+        assert np.array_equal(sn.indptr, ref.indptr) and np.array_equal(sn.indices, ref.indices)
+    assert np.array_equal(labels, whole[4][0])
+    with pkg.Server(window=W, n_slots=2) as srv:
+        g = srv.add_graph(n)
+        srv.restore(g, saved, labels)
+        for t in range(5, 8):
+            lab, info = srv.wait(srv.submit(g, snaps[t]))
+            assert np.array_equal(lab, whole[t][0]) and info["Q"] == whole[t][1]["Q"], t
+
+
+def test_restore_rejects_bad_state_and_keeps_the_window():
+    W, n = 3, 60
+    snaps = stream(n, 5, seed=43)
+    expect = oracle_chain(snaps, W)
+    with pkg.Server(window=W, n_slots=1) as srv:
+        g = srv.add_graph(n)
+        for t in range(3):
+            srv.wait(srv.submit(g, snaps[t]))
+        saved, labels = srv.checkpoint(g)
+        bad_w = saved[1].weights.copy()
+        bad_w[0] += 1
+        bad = synth.Snapshot(saved[1].indptr, saved[1].indices, bad_w)
+        with pytest.raises(pkg.MsliceError):
+            srv.restore(g, [saved[0], bad, saved[2]], labels)  # asymmetric snapshot
+        with pytest.raises(pkg.MsliceError):
+            srv.restore(g, saved, np.full(len(labels), len(labels), np.int32))  # labels out of range
+        with pytest.raises(pkg.MsliceError):
+            srv.restore(g, saved + saved, np.zeros(6 * n, np.int32))  # more than W snapshots
+        for t in (3, 4):  # the window is the one before the failed restores
+            lab, _ = srv.wait(srv.submit(g, snaps[t]))
+            assert np.array_equal(lab, expect[t][0]), t
