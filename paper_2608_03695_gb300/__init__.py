@@ -25,7 +25,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libmslice.so")
+# MSLICE_LIBRARY=checked loads the bounds-checked build (build(checked=True))
+LIB_PATH = os.path.join(HERE, "libmslice_checked.so" if os.environ.get("MSLICE_LIBRARY") == "checked"
+                        else "libmslice.so")
 
 MSLICE_OK, MSLICE_EINVAL, MSLICE_ENOMEM, MSLICE_EOVERFLOW, MSLICE_ECUDA, MSLICE_ETIMEOUT = 0, -1, -2, -3, -4, -5
 MSLICE_DEVICE_PTRS = 1
@@ -93,10 +95,11 @@ class RequestInfo(C.Structure):
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compiles libmslice.so in-tree (nvcc, sm_103a)."""
+def build(force: bool = False, checked: bool = False) -> str:
+    """Compiles libmslice.so (or, checked=True, libmslice_checked.so) in-tree
+    (nvcc, sm_103a)."""
     from . import build_lib
-    return build_lib.build(force=force)
+    return build_lib.build(force=force, checked=checked)
 
 
 def lib():

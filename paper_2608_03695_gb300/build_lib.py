@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmslice.so")
+CHECKED_LIB = os.path.join(HERE, "libmslice_checked.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
@@ -38,8 +39,8 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(src, extra):
-    obj = os.path.join(OBJ_DIR, os.path.basename(src) + ".o")
+def _compile(src, extra, obj_dir=OBJ_DIR):
+    obj = os.path.join(obj_dir, os.path.basename(src) + ".o")
     if _stale(obj, [src] + _headers()):
         cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -49,25 +50,31 @@ def _compile(src, extra):
     return obj
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    os.makedirs(OBJ_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), checked: bool = False) -> str:
+    """Builds libmslice.so, or with checked=True libmslice_checked.so: the
+    same sources with -DMSLICE_CHECKED=1 (index and table bounds tested on the
+    hot paths, violations reported as an error instead of accessed)."""
+    obj_dir = OBJ_DIR + ("_checked" if checked else "")
+    lib = CHECKED_LIB if checked else LIB
+    extra = list(extra) + (["-DMSLICE_CHECKED=1"] if checked else [])
+    os.makedirs(obj_dir, exist_ok=True)
     srcs = _sources()
     if force:
-        for f in glob.glob(os.path.join(OBJ_DIR, "*.o")):
+        for f in glob.glob(os.path.join(obj_dir, "*.o")):
             os.remove(f)
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, list(extra)), srcs))
-    if _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, extra, obj_dir), srcs))
+    if _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
     if verbose:
-        print(LIB)
-    return LIB
+        print(lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True)
+    build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv)

@@ -150,6 +150,9 @@ __global__ void __launch_bounds__(CW_WARPS * 32)
             if (edge_at(g, i, u, W, om)) {
               const int32_t y = xmap[u];
               if (y != x) slot = ctab_add(K, V, SLOTS, y, W, fresh);
+#if MSLICE_CHECKED
+              if (y != x && slot < 0) atomicOr(g.chk, ERR_BOUNDS);
+#endif
             }
           }
           const unsigned bal = __ballot_sync(0xffffffffu, fresh);
@@ -180,6 +183,9 @@ __global__ void __launch_bounds__(CW_WARPS * 32)
         slice_entry(g, v, q, sl, k);
         bool fresh;
         const int64_t slot = ctab_add(K, V, SLOTS, sl, k, fresh);
+#if MSLICE_CHECKED
+            if (slot < 0) atomicOr(g.chk, ERR_BOUNDS);
+#endif
         if (fresh) CL[atomicAdd(&ncl[w], 1)] = (uint16_t)slot;
       }
     }
@@ -256,6 +262,9 @@ __global__ void __launch_bounds__(CB_THREADS)
           if (y != x) {
             bool fresh;
             const int64_t slot = ctab_add(K, V, cap, y, W, fresh);
+#if MSLICE_CHECKED
+            if (slot < 0) atomicOr(g.chk, ERR_BOUNDS);
+#endif
             if (fresh) CL[atomicAdd(&ncnt, 1)] = (int32_t)slot;
           }
         }
@@ -287,6 +296,9 @@ __global__ void __launch_bounds__(CB_THREADS)
         slice_entry(g, v, q, sl, k);
         bool fresh;
         const int64_t slot = ctab_add(K, V, cap, sl, k, fresh);
+#if MSLICE_CHECKED
+            if (slot < 0) atomicOr(g.chk, ERR_BOUNDS);
+#endif
         if (fresh) CL[atomicAdd(&ncnt, 1)] = (int32_t)slot;
       }
     }
@@ -479,6 +491,7 @@ bool aggregate(Solver& S, const Level& L, const int32_t* P, Level& next, const s
   next.d.od = L.d.od;
   next.d.on_i = L.d.on_i;
   next.d.od_i = L.d.od_i;
+  next.d.chk = L.d.chk;
   if (L.d.inst) {
     int32_t* inst_next = c.ws->get<int32_t>(slot + "_inst", (size_t)Np);
     int32_t* off_next = c.ws->get<int32_t>(slot + "_ioff", (size_t)S.B + 1);

@@ -207,6 +207,7 @@ void check_status(Ctx& c, const char* where) {
   check_cuda(cudaMemsetAsync(c.d_status, 0, sizeof(unsigned), c.stream), "memset");
   if (st & ERR_BAD_INPUT) fail(MSLICE_EINVAL, std::string(where) + ": malformed input");
   if (st & ERR_HASH_FULL) fail(MSLICE_ECUDA, std::string(where) + ": internal hash table overflow");
+  if (st & ERR_BOUNDS) fail(MSLICE_ECUDA, std::string(where) + ": bound check failed (checked build)");
   fail(MSLICE_ECUDA, std::string(where) + ": internal error");
 }
 

@@ -18,6 +18,14 @@ constexpr ull EMPTY_KEY = ~0ull;     // free hash slot
 constexpr unsigned ERR_HASH_FULL = 1u;   // a probe sequence exceeded the table
 constexpr unsigned ERR_BAD_INPUT = 2u;   // validation of a snapshot failed
 constexpr unsigned ERR_INTERNAL = 4u;    // an internal consistency check failed
+constexpr unsigned ERR_BOUNDS = 8u;      // checked builds: an index or table bound was violated
+
+// Checked builds (-DMSLICE_CHECKED=1) test indices and table capacities on
+// the hot paths and record violations in the status word instead of making
+// the access; the tests run them against the oracle.
+#ifndef MSLICE_CHECKED
+#define MSLICE_CHECKED 0
+#endif
 
 // SplitMix64 output finaliser (Steele, Lea & Flood, OOPSLA 2014), written from
 // its published definition.  Drives the vertex classes of the schedule.

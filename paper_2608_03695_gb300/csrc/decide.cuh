@@ -71,21 +71,6 @@ __device__ __forceinline__ uint32_t small_hash(int32_t key, int bits) {
   return ((uint32_t)key * 2654435769u) >> (32 - bits);
 }
 
-// Insert-or-add into a table of 2^bits slots (keys -1 = free).  Callers size
-// the table to at least twice the number of keys, so a free slot exists.
-__device__ __forceinline__ void table_add(int32_t* hk, long long* hv, int bits, int32_t key, long long w) {
-  const uint32_t mask = (1u << bits) - 1u;
-  uint32_t i = small_hash(key, bits);
-  for (uint32_t p = 0; p <= mask; ++p) {
-    const int32_t prev = atomicCAS(&hk[i], -1, key);
-    if (prev == -1 || prev == key) {
-      atomicAdd((ull*)&hv[i], (ull)w);
-      return;
-    }
-    i = (i + 1) & mask;
-  }
-}
-
 __device__ __forceinline__ long long table_get(const int32_t* hk, const long long* hv, int bits, int32_t key) {
   if (key < 0) return 0;
   const uint32_t mask = (1u << bits) - 1u;
@@ -194,6 +179,9 @@ __global__ void __launch_bounds__(GROUP_THREADS, MSLICE_GROUP_MIN_BLOCKS)
           if (ok[j]) {
             bool fresh;
             const int slot = table_add_slot(K, V, BITS, keys[j], ws[j], fresh);
+#if MSLICE_CHECKED
+            if (slot < 0) atomicOr(pol.g.chk, ERR_BOUNDS);
+#endif
             if (fresh) CL[atomicAdd(&ncand[gx], 1)] = (uint16_t)slot;
           }
         }
@@ -302,6 +290,9 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_block(Pol pol, const i
       if (pol.edge(v, vc, e, key, w)) {
         bool fresh;
         const int slot = table_add_slot(hk, hv, bits, key, w, fresh);
+#if MSLICE_CHECKED
+        if (slot < 0) atomicOr(pol.g.chk, ERR_BOUNDS);
+#endif
         if (fresh) cl[atomicAdd(&ncand, 1)] = (uint16_t)slot;
       }
     }

@@ -238,6 +238,7 @@ void run_leiden(Ctx& c, const SupraGraph& G, const std::vector<InstParams>& jobs
 
   Level L0;
   L0.d = level0_view(G, S);
+  if (MSLICE_CHECKED) L0.d.chk = c.d_status;
   L0.nnz = G.nnz;
   L0.nnz_eff = G.nnz_intra;
   for (int32_t i = 0; i < B; ++i)

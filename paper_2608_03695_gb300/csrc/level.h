@@ -32,6 +32,7 @@ struct LevelDev {
   const int32_t* inst_off = nullptr;  // first node id of every instance at this level
   const long long* on_i = nullptr;    // omega of every instance
   const long long* od_i = nullptr;
+  unsigned* chk = nullptr;            // checked builds: status word for bound violations
 };
 
 struct Omega {
@@ -62,6 +63,21 @@ __device__ __forceinline__ int32_t node_slice0(const LevelDev& g, int32_t v) {
 // A coupling entry has weight on and is absent when on = 0.  (om: the
 // omega of the row's instance.)
 __device__ __forceinline__ bool edge_at(const LevelDev& g, int64_t e, int32_t& u, long long& W, const Omega& om) {
+#if MSLICE_CHECKED
+  if (e < 0 || e >= g.rowptr[g.N]) {
+    atomicOr(g.chk, ERR_BOUNDS);
+    u = 0;
+    W = 0;
+    return false;
+  }
+  const int32_t cu = g.is0 ? g.adj0[e].x : g.col[e];
+  if (cu < 0 || cu >= g.N) {
+    atomicOr(g.chk, ERR_BOUNDS);
+    u = 0;
+    W = 0;
+    return false;
+  }
+#endif
   if (g.is0) {
     const int2 x = __ldcs(&g.adj0[e]);
     u = x.x;

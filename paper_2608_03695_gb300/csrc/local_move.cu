@@ -255,6 +255,12 @@ __global__ void k_lm_apply(LevelDev g, Segs sg, int32_t* labels, int32_t* size, 
     if (!seg_item(sg, idx, v)) break;
     const int32_t t = target[v];
     if (t == NO_MOVE) continue;
+#if MSLICE_CHECKED
+    if (t >= g.N || (t < 0 && t != TO_EMPTY)) {
+      atomicOr(g.chk, ERR_BOUNDS);
+      continue;
+    }
+#endif
     if (inst_moved) inst_moved[node_inst(g, v)] = 1;
     const int32_t a = labels[v];
     atomicSub(&size[a], 1);
