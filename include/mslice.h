@@ -28,8 +28,9 @@
  *   - Ownership: inputs belong to the caller and are read only during the
  *     call.  A handle owns all device memory it allocates.  Outputs are
  *     written to caller buffers (host memory unless MSLICE_DEVICE_PTRS).
- *   - Streams: work runs on the stream given at build time (NULL = the
- *     legacy default stream); calls return after that stream is synchronised.
+ *   - Streams: work runs on the stream given at build time (NULL: a stream of
+ *     the handle's own that waits for the legacy default stream's work, as
+ *     that stream would); calls return after that stream is synchronised.
  *     Calls on one handle must not overlap; different handles are
  *     independent.
  */

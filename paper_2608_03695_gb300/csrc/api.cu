@@ -225,6 +225,7 @@ struct mslice_graph {
   long long on = 1, od = 1;
   int64_t launches = 0;
   StreamFan fan;
+  bool own_stream = false;
   Ctx ctx() {
     Ctx c;
     c.stream = stream;
@@ -239,6 +240,7 @@ struct mslice_graph {
     G.mem.release_all();
     fan.destroy();
     if (pinned) cudaFreeHost(pinned);
+    if (own_stream && stream) cudaStreamDestroy(stream);
   }
 };
 
@@ -262,6 +264,7 @@ struct mslice_batch_s {
   std::vector<double> Q;
   int64_t launches = 0;
   StreamFan fan;
+  bool own_stream = false;
   Ctx ctx() {
     Ctx c;
     c.stream = stream;
@@ -276,6 +279,7 @@ struct mslice_batch_s {
     G.mem.release_all();
     fan.destroy();
     if (pinned) cudaFreeHost(pinned);
+    if (own_stream && stream) cudaStreamDestroy(stream);
   }
 };
 
@@ -418,6 +422,12 @@ int mslice_build_ex(const mslice_csr* slices, int32_t T, mslice_coupling cpl, in
     static std::atomic<uint64_t> next_serial{1};
     h->serial = next_serial++;
     h->stream = static_cast<cudaStream_t>(stream);
+    if (!h->stream) {
+      // a stream of the handle's own that, like the legacy default stream it
+      // stands for, waits for the legacy stream's work (and can be captured)
+      check_cuda(cudaStreamCreate(&h->stream), "stream");
+      h->own_stream = true;
+    }
     h->ws.stream = h->stream;
     h->G.mem.stream = h->stream;
     keep_pool_memory();
@@ -608,6 +618,10 @@ int mslice_batch_create(int32_t flags, void* stream, mslice_batch* out) {
     b = new mslice_batch_s();
     b->flags = flags;
     b->stream = static_cast<cudaStream_t>(stream);
+    if (!b->stream) {
+      check_cuda(cudaStreamCreate(&b->stream), "stream");
+      b->own_stream = true;
+    }
     b->ws.stream = b->stream;
     b->G.mem.stream = b->stream;
     keep_pool_memory();

@@ -61,6 +61,7 @@ struct StreamFan {
 struct Ctx {
   cudaStream_t stream = nullptr;
   StreamFan* fan = nullptr;      // nullptr: tiers run one after another
+  bool capturing = false;        // launches are being captured into a graph
   Workspace* ws = nullptr;
   unsigned* d_status = nullptr;  // device error bits
   int64_t launches = 0;
@@ -111,7 +112,10 @@ inline void launch_coop(Ctx& c, void (*k)(KArgs...), dim3 grid, dim3 block, size
   void* argv[] = {(void*)&args...};
   cudaEvent_t e0 = nullptr;
   if (c.trace) trace_begin(c, (const void*)k, &e0);
-  {
+  if (c.capturing) {
+    // ordered as a whole by the graph's launch
+    check_cuda(cudaLaunchCooperativeKernel((const void*)k, grid, block, argv, smem, c.stream), "cooperative launch");
+  } else {
     CoopOrder order(c.stream);
     check_cuda(cudaLaunchCooperativeKernel((const void*)k, grid, block, argv, smem, c.stream), "cooperative launch");
   }

@@ -34,6 +34,7 @@ namespace mslice {
 namespace {
 
 constexpr int APPLY_THREADS = 256;
+constexpr int GRAPH_FROM_ROUND = 4;
 constexpr int EMPTY_THREADS = 512;
 
 unsigned fixed_grid(int per_sm) { return 152u * (unsigned)per_sm; }
@@ -68,9 +69,10 @@ struct TierOff {
 
 __global__ void k_bucket(LevelDev g, const uint8_t* tier, uint64_t seed, uint64_t tag, uint64_t it, uint64_t lvl,
                          uint64_t r, int K, int32_t* lists, int64_t row_stride, TierOff tier_off, int32_t* cursors,
-                         const int32_t* active) {
+                         const int32_t* active, const int32_t* r_dev) {
   const int lane = threadIdx.x & 31;
   const int32_t N = g.N;
+  if (r_dev) r = (uint64_t)*r_dev;  // a graph replay reads its round here
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < N; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t v = base + threadIdx.x;
     bool ok = v < N;
@@ -235,6 +237,8 @@ __device__ __forceinline__ int seg_total(const Segs& sg) {
 // Applies the sub-round's decisions: labels, community sizes and Sigma, and
 // resets each applied decision.  Moves to an empty community only leave here
 // (their label is assigned by k_empty_pass).
+__global__ void k_round_next(int32_t* r_dev) { *r_dev += 1; }
+
 // lm_active[i] stays 1 only for instances that moved in the round; clears
 // the flags for the next round.
 __global__ void k_round_freeze(int32_t* lm_active, int32_t* inst_moved, int32_t B) {
@@ -481,6 +485,7 @@ void solver_alloc(Solver& S) {
   check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attribute");
   S.empty_grid = std::max(1, std::min(max_blocks, 2) * sms);
   S.empty_blk = c.ws->get<int32_t>("s_empty_blk", 2 * S.empty_grid);
+  S.round_dev = c.ws->get<int32_t>("s_round", 1);
   S.lm_active = c.ws->get<int32_t>("s_lm_active", S.B);
   S.inst_moved = c.ws->get<int32_t>("s_inst_moved", S.B);
   check_cuda(cudaMemsetAsync(S.inst_moved, 0, S.B * sizeof(int32_t), c.stream), "memset");
@@ -592,14 +597,15 @@ TierSegs bucket_segments(Solver& S, int q) {
   return sg;
 }
 
-void bucket(Solver& S, const Level& L, uint64_t tag, int it, int lvl, int r, const int32_t* active) {
+void bucket(Solver& S, const Level& L, uint64_t tag, int it, int lvl, int r, const int32_t* active,
+            const int32_t* r_dev) {
   Ctx& c = *S.c;
   check_cuda(cudaMemsetAsync(S.cursors, 0, NTIERS * S.p.K * sizeof(int32_t), c.stream), "memset");
   TierOff to;
   for (int t = 0; t < NTIERS; ++t) to.off[t] = S.tier_off[t];
   if (L.d.N > 0)
     launch(c, k_bucket, dim3(grid_for(L.d.N, 256)), dim3(256), 0, L.d, (const uint8_t*)S.tier, S.p.seed, tag,
-           (uint64_t)it, (uint64_t)lvl, (uint64_t)r, S.p.K, S.lists, (int64_t)S.N0, to, S.cursors, active);
+           (uint64_t)it, (uint64_t)lvl, (uint64_t)r, S.p.K, S.lists, (int64_t)S.N0, to, S.cursors, active, r_dev);
 }
 
 // Chooses the degree cuts of the decision tiers for this solve: every
@@ -621,7 +627,7 @@ static void autotune_cuts(Solver& S, const Level& L, int it, int r, const int32_
   for (int k = -1; k < (int)(sizeof(kCand) / sizeof(kCand[0])); ++k) {
     S.p.cuts = kCand[k < 0 ? 0 : k];
     prepare_level(S, L);
-    bucket(S, L, 0, it, 0, r, active);
+    bucket(S, L, 0, it, 0, r, active, nullptr);
     float ms = 0;
     for (int rep = 0; rep < 2; ++rep) {
       check_cuda(cudaEventRecord(e0, c.stream), "event");
@@ -643,6 +649,35 @@ static void autotune_cuts(Solver& S, const Level& L, int it, int r, const int32_
   S.p.autotune = false;
   prepare_level(S, L);
   fill_i32(c, S.target, NO_MOVE, L.d.N);
+}
+
+// Captures body() on the context's stream into an executable graph; returns
+// nullptr (and leaves the stream usable) when capture is not possible.
+// kernels: how many kernel launches one replay makes.
+template <class Body>
+static cudaGraphExec_t capture_round(Ctx& c, Body&& body, int64_t& kernels) {
+  const int64_t before = c.launches;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  c.capturing = true;
+  bool ok = true;
+  try {
+    body();
+  } catch (const Error&) {
+    ok = false;
+  }
+  c.capturing = false;
+  const cudaError_t e = cudaStreamEndCapture(c.stream, &graph);
+  if (!ok || e != cudaSuccess || !graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();
+  kernels = c.launches - before;
+  c.launches = before;
+  return exec;
 }
 
 MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, int max_rounds) {
@@ -688,17 +723,14 @@ MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, 
   if (batch)
     check_cuda(cudaMemcpyAsync(S.lm_active, S.inst_active, S.B * sizeof(int32_t), cudaMemcpyDeviceToDevice, c.stream),
                "copy");
-  bool rebuild = false;
-  for (int r = 0; r < max_rounds; ++r) {
-    if (rebuild) rebuild_sigma(S, L, labels, false);
-    // tuning waits for round 2, when the partition looks like the later rounds'
-    if (S.p.autotune && lvl == 0 && r == 2) autotune_cuts(S, L, it, r, batch ? S.lm_active : S.inst_active, decide);
+  const int32_t* active = batch ? S.lm_active : S.inst_active;
+  // One round: buckets, K sub-rounds of decisions, applies and moves to
+  // empty communities, then the moved count, the hash fill and the status
+  // word copied to the pinned buffer.  r_dev (graph replays): the round is
+  // read from and advanced on the device.
+  auto round_body = [&](int r, const int32_t* r_dev, bool prof) {
     check_cuda(cudaMemsetAsync(S.counters, 0, 3 * sizeof(int32_t), c.stream), "memset");
-    bucket(S, L, 0, it, lvl, r, batch ? S.lm_active : S.inst_active);
-    S.lm_rounds++;
-    S.lm_edges += L.nnz_eff;
-    const bool prof = c.profile && lvl == 0;
-    if (prof) c.prof_bytes += 12 * L.nnz_eff + 40 * (int64_t)N;
+    bucket(S, L, 0, it, lvl, r, active, r_dev);
     for (int q = 0; q < S.p.K; ++q) {
       const Segs sg = bucket_segments(S, q);
       if (prof) {
@@ -719,21 +751,72 @@ MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, 
     }
     if (batch)
       launch(c, k_round_freeze, dim3(grid_for(S.B, 256)), dim3(256), 0, S.lm_active, S.inst_moved, S.B);
-    struct {
-      int64_t moved;
-      ull used;
-    } rb;
     check_cuda(cudaMemcpyAsync(c.pinned, S.counters, sizeof(int64_t), cudaMemcpyDeviceToHost, c.stream), "copy");
     check_cuda(cudaMemcpyAsync(static_cast<char*>(c.pinned) + 8, S.sig_used, sizeof(ull), cudaMemcpyDeviceToHost,
                                c.stream), "copy");
+    check_cuda(cudaMemcpyAsync(static_cast<char*>(c.pinned) + 16, c.d_status, sizeof(unsigned),
+                               cudaMemcpyDeviceToHost, c.stream), "copy");
+    if (r_dev) launch(c, k_round_next, dim3(1), dim3(1), 0, S.round_dev);
+  };
+  // A level still moving after GRAPH_FROM_ROUND rounds replays one captured
+  // graph per round (one launch instead of ~7K+3 kernels and copies); capture
+  // and instantiation cost more than they save on levels that settle sooner.
+  // Not while profiling or tracing, nor on a level whose tier cuts are still
+  // being tuned.
+  // Measured: ~1% faster for batches of small instances, ~1.7% slower for a
+  // single 1.6M-node solve (its large levels keep the GPU busy between
+  // launches), so batches use graphs and single solves only on request
+  // (MSLICE_GRAPHS=1; MSLICE_NO_GRAPHS=1 turns them off).
+  const bool want = (batch || std::getenv("MSLICE_GRAPHS")) && !std::getenv("MSLICE_NO_GRAPHS");
+  const bool graphs = want && c.stream != nullptr && !c.profile && !c.trace && !(S.p.autotune && lvl == 0);
+  cudaGraphExec_t exec = nullptr;
+  int64_t graph_kernels = 0;
+  bool graph_failed = false;
+  bool rebuild = false;
+  for (int r = 0; r < max_rounds; ++r) {
+    if (rebuild) rebuild_sigma(S, L, labels, false);
+    // tuning waits for round 2, when the partition looks like the later rounds'
+    if (S.p.autotune && lvl == 0 && r == 2) autotune_cuts(S, L, it, r, active, decide);
+    S.lm_rounds++;
+    S.lm_edges += L.nnz_eff;
+    const bool prof = c.profile && lvl == 0;
+    if (prof) c.prof_bytes += 12 * L.nnz_eff + 40 * (int64_t)N;
+    if (graphs && r >= GRAPH_FROM_ROUND && !graph_failed) {
+      if (!exec) {
+        const int32_t r32 = r;
+        check_cuda(cudaMemcpyAsync(S.round_dev, &r32, sizeof(int32_t), cudaMemcpyHostToDevice, c.stream), "copy");
+        sync(c);  // r32 is pageable
+        exec = capture_round(c, [&] { round_body(r, S.round_dev, false); }, graph_kernels);
+        if (!exec) graph_failed = true;
+      }
+      if (exec) {
+        CoopOrder order(c.stream);
+        check_cuda(cudaGraphLaunch(exec, c.stream), "graph launch");
+        c.launches += graph_kernels;
+      } else {
+        round_body(r, nullptr, prof);
+      }
+    } else {
+      round_body(r, nullptr, prof);
+    }
     sync(c);
+    struct {
+      int64_t moved;
+      ull used;
+      unsigned status;
+    } rb;
     std::memcpy(&rb, c.pinned, sizeof(rb));
-    check_status(c, "local moving");
+    if (rb.status) {
+      if (exec) cudaGraphExecDestroy(exec);
+      exec = nullptr;
+      check_status(c, "local moving");
+    }
     rebuild = !S.sig.d && rb.used * 2 > S.sig.h.cap;
     out.rounds++;
     out.moves += rb.moved;
     if (rb.moved == 0) break;
   }
+  if (exec) cudaGraphExecDestroy(exec);
   S.lm_moves += out.moves;
   return out;
 }

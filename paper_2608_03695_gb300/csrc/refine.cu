@@ -274,7 +274,8 @@ unsigned fixed_grid(int per_sm) { return 152u * (unsigned)per_sm; }
 
 }  // namespace
 
-void bucket(Solver& S, const Level& L, uint64_t tag, int it, int lvl, int r, const int32_t* active);
+void bucket(Solver& S, const Level& L, uint64_t tag, int it, int lvl, int r, const int32_t* active,
+            const int32_t* r_dev = nullptr);
 TierSegs bucket_segments(Solver& S, int q);
 
 template <bool DENSE>

@@ -58,6 +58,7 @@ struct Solver {
   int32_t* inst_active = nullptr;  // per instance: 1 while not converged (nullptr: all active)
   int32_t* lm_active = nullptr;    // per instance: still moving in this level's local moving
   int32_t* inst_moved = nullptr;   // per instance: moved in the current round
+  int32_t* round_dev = nullptr;    // the round a captured round graph is replaying
   int64_t* goff = nullptr;      // global-tier table offsets
   int32_t* gkeys = nullptr;
   long long* gvals = nullptr;

@@ -276,3 +276,15 @@ def test_tier_cuts_and_autotune_do_not_change_results():
         for bad in [(17, 32, 256, 1024), (16, 8, 256, 1024), (16, 32, 256, 2048), (-1, 32, 256, 1024)]:
             with pytest.raises(pkg.MsliceError):
                 h.mslice_leiden(tier_cuts=bad)
+
+
+def test_round_graphs_give_the_same_bits(monkeypatch):
+    """Rounds replayed from a captured CUDA graph (forced on for a single
+    solve) give the oracle's bits, on dense and hashed tables."""
+    monkeypatch.setenv("MSLICE_GRAPHS", "1")
+    for limit in (None, "0"):
+        if limit is not None:
+            monkeypatch.setenv("MSLICE_DENSE_LIMIT", limit)
+        snaps = synth.config_graph({**synth.CONFIGS[2], "n": 4000, "T": 4})
+        g, o = solve_both(snaps, (1, 1), (1, 2), K=3, seed=4)
+        assert_same(g, o)
