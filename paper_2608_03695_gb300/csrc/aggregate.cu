@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(CB_THREADS)
     k_contract_block(LevelDev g, const int32_t* xmap, const int64_t* moff, const int32_t* mem, const int32_t* list,
                      const int32_t* count_ptr, const int64_t* eoff, const int64_t* soff, int32_t* tcol, long long* tw,
                      int32_t* ecnt, int32_t* tsidx, long long* tsval, int32_t* scnt_out, const int64_t* gofs,
-                     const int64_t* gsize, int32_t* gk, long long* gv, int32_t* gl) {
+                     const int64_t* gsize, int32_t* gk, long long* gv, uint32_t* gl) {
   extern __shared__ __align__(16) unsigned char csm[];
   __shared__ int32_t ncnt;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -224,12 +224,12 @@ __global__ void __launch_bounds__(CB_THREADS)
   const int count = *count_ptr;
   int32_t* K;
   long long* V;
-  int32_t* CL;
+  uint32_t* CL;  // listed slots (a global table holds up to 2^32)
   int64_t cap = (int64_t)1 << CB_BITS;
   if (!GLOBAL) {
     V = reinterpret_cast<long long*>(csm);
     K = reinterpret_cast<int32_t*>(V + cap);
-    CL = K + cap;
+    CL = reinterpret_cast<uint32_t*>(K + cap);
     for (int64_t i = threadIdx.x; i < cap; i += blockDim.x) {
       K[i] = -1;
       V[i] = 0;
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(CB_THREADS)
 #if MSLICE_CHECKED
             if (slot < 0) atomicOr(g.chk, ERR_BOUNDS);
 #endif
-            if (fresh) CL[atomicAdd(&ncnt, 1)] = (int32_t)slot;
+            if (fresh) CL[atomicAdd(&ncnt, 1)] = (uint32_t)slot;
           }
         }
       }
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(CB_THREADS)
     const int n = ncnt;
     const int64_t eo = eoff[x];
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
-      const int32_t slot = CL[k];
+      const uint32_t slot = CL[k];
       tcol[eo + k] = K[slot];
       tw[eo + k] = V[slot];
       K[slot] = -1;
@@ -299,14 +299,14 @@ __global__ void __launch_bounds__(CB_THREADS)
 #if MSLICE_CHECKED
             if (slot < 0) atomicOr(g.chk, ERR_BOUNDS);
 #endif
-        if (fresh) CL[atomicAdd(&ncnt, 1)] = (int32_t)slot;
+        if (fresh) CL[atomicAdd(&ncnt, 1)] = (uint32_t)slot;
       }
     }
     __syncthreads();
     const int ns = ncnt;
     const int64_t so = soff[x];
     for (int k = threadIdx.x; k < ns; k += blockDim.x) {
-      const int32_t slot = CL[k];
+      const uint32_t slot = CL[k];
       tsidx[so + k] = K[slot];
       tsval[so + k] = V[slot];
       K[slot] = -1;
@@ -456,13 +456,13 @@ bool aggregate(Solver& S, const Level& L, const int32_t* P, Level& next, const s
     launch(c, k_contract_block<false>, dim3(152 * 2), dim3(CB_THREADS), cb_smem, L.d, (const int32_t*)xmap,
            (const int64_t*)moff, (const int32_t*)mem, (const int32_t*)(lists + Np), (const int32_t*)(tcnt + 1),
            (const int64_t*)eoff, (const int64_t*)soff, tcol, tw, ecnt, tsidx, tsval, scnt_out, (const int64_t*)gofs,
-           (const int64_t*)gsize, (int32_t*)nullptr, (long long*)nullptr, (int32_t*)nullptr);
+           (const int64_t*)gsize, (int32_t*)nullptr, (long long*)nullptr, (uint32_t*)nullptr);
   }
   if (hd.t[2] > 0) {
     if (hd.gtot > ((int64_t)1 << 31) * 8) fail(MSLICE_ENOMEM, "aggregation scratch too large");
     int32_t* gk = c.ws->get<int32_t>("ag_gk", hd.gtot);
     long long* gv = c.ws->get<long long>("ag_gv", hd.gtot);
-    int32_t* gl = c.ws->get<int32_t>("ag_gl", hd.gtot);
+    uint32_t* gl = c.ws->get<uint32_t>("ag_gl", hd.gtot);
     launch(c, k_contract_block<true>, dim3(152 * 2), dim3(CB_THREADS), 0, L.d, (const int32_t*)xmap,
            (const int64_t*)moff, (const int32_t*)mem, (const int32_t*)(lists + 2 * (int64_t)Np),
            (const int32_t*)(tcnt + 2), (const int64_t*)eoff, (const int64_t*)soff, tcol, tw, ecnt, tsidx, tsval,
