@@ -83,7 +83,7 @@ def measured_peak():
 def decide_traffic():
     """DRAM bytes per launch of the decision kernel from the committed ncu
     summary (None when absent)."""
-    p = os.path.join(ROOT, "profiles", "local_move_decide_config2.md")
+    p = os.path.join(ROOT, "profiles", "local_move_decide_powerlaw_t16_n100k.md")
     try:
         for line in open(p):
             if line.startswith("traffic_bytes_per_launch:"):
@@ -102,7 +102,9 @@ class ClockSampler:
     def __init__(self, gpu):
         self.gpu = gpu
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # the raw samples go to MSLICE_BENCH_OUT (default: the temp directory)
+        out = os.environ.get("MSLICE_BENCH_OUT") or __import__("tempfile").gettempdir()
+        self.path = os.path.join(out, f"clocks_bench_{os.getpid()}.csv")
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -146,7 +148,7 @@ class ClockSampler:
 def cpu_baseline():
     import oracle
     from paper_2608_03695_gb300 import synth
-    snaps = synth.config_graph(2, scale_n=ORACLE_SAMPLE_N)
+    snaps = synth.recipe_graph("powerlaw_t16_n100k", scale_n=ORACLE_SAMPLE_N)
     t = time.perf_counter()
     _, _, st = oracle.leiden(snaps)
     el = time.perf_counter() - t
@@ -162,7 +164,7 @@ def run_reference(args):
     import oracle
     from paper_2608_03695_gb300 import synth
     oracle.build()
-    snaps = synth.config_graph(2, scale_n=ORACLE_SAMPLE_N)
+    snaps = synth.recipe_graph("powerlaw_t16_n100k", scale_n=ORACLE_SAMPLE_N)
     for _ in range(args.warmup):
         oracle.leiden(snaps, n_iterations=1, max_rounds=2)  # short warm-up (page-in, caches)
     edges, secs = 0, 0.0
@@ -454,9 +456,9 @@ def run_large(args):
     import torch
     import paper_2608_03695_gb300 as pkg
     from paper_2608_03695_gb300 import synth
-    n = int(synth.CONFIGS[4]["n"] * args.scale)
+    n = int(synth.RECIPES["powerlaw_t64_n1m"]["n"] * args.scale)
     t = time.perf_counter()
-    snaps = synth.config_graph(4, scale_n=n)
+    snaps = synth.recipe_graph("powerlaw_t64_n1m", scale_n=n)
     t_gen = time.perf_counter() - t
     torch.cuda.set_device(0)
     omegas = [(1, 10), (1, 1), (10, 1)]
@@ -549,7 +551,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
         return float(t.item())
 
-    snaps = synth.config_graph(2)
+    snaps = synth.recipe_graph("powerlaw_t16_n100k")
     stream = torch.cuda.Stream()
     if args.profile_run:
         with pkg.mslice_build(snaps) as h:

@@ -29,7 +29,7 @@ __all__ = [
     "random_temporal",
     "cliques_temporal",
     "config_graph",
-    "CONFIGS",
+    "RECIPES",
 ]
 
 
@@ -373,18 +373,21 @@ def cliques_temporal(clique_sizes, T: int, w: int = 1):
 
 
 # Workload recipes.  Rationals are (numerator, denominator) pairs.
-CONFIGS = {
-    1: dict(kind="planted", n=1000, T=4, n_blocks=4, p_in=0.05, p_out=0.005, switch_frac=0.10,
+# Named recipes: a planted partition (T=4, n=1,000), the power-law temporal
+# graph of the benchmark (T=16, n=100,000) and its large T=64, n=1,000,000
+# form.
+RECIPES = {
+    "planted_t4_n1000": dict(kind="planted", n=1000, T=4, n_blocks=4, p_in=0.05, p_out=0.005, switch_frac=0.10,
             w_max=1, seed=1, gamma=(1, 1), omega=(1, 1)),
-    2: dict(kind="dcsbm", n=100_000, T=16, deg_exp=2.5, mean_deg=20.0, size_exp=1.5, size_min=20,
+    "powerlaw_t16_n100k": dict(kind="dcsbm", n=100_000, T=16, deg_exp=2.5, mean_deg=20.0, size_exp=1.5, size_min=20,
             size_max=5000, mixing=0.3, churn=0.05, w_max=8, seed=2, gamma=(1, 1), omega=(1, 1)),
-    4: dict(kind="dcsbm", n=1_000_000, T=64, deg_exp=2.3, mean_deg=16.0, size_exp=1.5, size_min=20,
+    "powerlaw_t64_n1m": dict(kind="dcsbm", n=1_000_000, T=64, deg_exp=2.3, mean_deg=16.0, size_exp=1.5, size_min=20,
             size_max=5000, mixing=0.4, churn=0.05, w_max=16, seed=4, gamma=(1, 1), omega=(1, 1)),
 }
 
 
 # Batched workload: 64 independent temporal planted-partition graphs (the
-# generator of config 1: 4 equal blocks, p_out = p_in / 10, 10% of the nodes
+# planted-partition generator of planted_t4_n1000: 4 equal blocks, p_out = p_in / 10, 10% of the nodes
 # switch block between snapshots), n log-uniform in [1k, 200k], T uniform in
 # [2, 32], mean degree uniform in [8, 32], weights 1..8; every graph is solved
 # at each (gamma, omega) of the grid below (1,152 solves).
@@ -417,7 +420,7 @@ def batched_graph(spec):
     return snaps
 
 
-# Serving workload: 32 live temporal graphs (the generator of config 1 at
+# Serving workload: 32 live temporal graphs (the planted-partition generator at
 # mean degree 16), n log-uniform in
 # [10k, 2M], each a stream of snapshots with 5% edge churn between
 # consecutive ones, weights 1..8; windows of W = 8 slices; requests arrive
@@ -449,9 +452,10 @@ def serving_stream(spec, steps: int):
     return snaps
 
 
-def config_graph(cfg: int | dict, scale_n: int | None = None, T: int | None = None):
-    """Snapshots of a workload recipe (optionally with n or T overridden)."""
-    c = dict(CONFIGS[cfg]) if isinstance(cfg, int) else dict(cfg)
+def recipe_graph(recipe: str | dict, scale_n: int | None = None, T: int | None = None):
+    """Snapshots of a named recipe (or a recipe dict), optionally with n or T
+    overridden."""
+    c = dict(RECIPES[recipe]) if isinstance(recipe, str) else dict(recipe)
     n = scale_n if scale_n is not None else c["n"]
     TT = T if T is not None else c["T"]
     if c["kind"] == "planted":

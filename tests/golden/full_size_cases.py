@@ -9,7 +9,7 @@ digest matches the stored one they compare with the stored result, otherwise
 run the oracle live.
 
     python tests/golden/full_size_cases.py            # all cases (~20 min, one core)
-    python tests/golden/full_size_cases.py config2    # cases whose name starts so
+    python tests/golden/full_size_cases.py powerlaw   # cases whose name starts so
 """
 from __future__ import annotations
 
@@ -66,18 +66,18 @@ def cases():
     snaps, gamma, omega and optional init."""
     out = {}
 
-    def config2():
-        return [dict(snaps=synth.config_graph(2), gamma=(1, 1), omega=(1, 1))]
+    def powerlaw_t16():
+        return [dict(snaps=synth.recipe_graph("powerlaw_t16_n100k"), gamma=(1, 1), omega=(1, 1))]
 
-    out["config2_full"] = config2
+    out["powerlaw_t16_n100k"] = powerlaw_t16
 
-    def config4_n20k():
-        snaps = synth.config_graph(4, scale_n=20000)
+    def powerlaw_t64_n20k():
+        snaps = synth.recipe_graph("powerlaw_t64_n1m", scale_n=20000)
         return [dict(snaps=snaps, gamma=(1, 1), omega=om) for om in [(1, 10), (1, 1), (10, 1)]]
 
-    out["config4_T64_n20k"] = config4_n20k
+    out["powerlaw_t64_n20k"] = powerlaw_t64_n20k
 
-    def config3_sample():
+    def batched_sample():
         specs = synth.batched_specs()
         picks = [0, 1, 2, 5]  # full-size graphs of the batched workload (n 1.6k-22k, T 7-21)
         solves = []
@@ -88,15 +88,15 @@ def cases():
                 solves.append(dict(snaps=snaps, gamma=gm, omega=om, graph=k))
         return solves
 
-    out["config3_sample"] = config3_sample
+    out["batched_sample"] = batched_sample
 
-    def config5_chain():
+    def serving_chain():
         W = synth.SERVING["window"]
         spec = sorted(synth.serving_specs(), key=lambda s: s[0])[0]  # the smallest live graph (n ~ 10k)
         stream = synth.serving_stream(spec, W + 3)
         return [dict(stream=stream, W=W)]
 
-    out["config5_chain"] = config5_chain
+    out["serving_chain"] = serving_chain
     return out
 
 

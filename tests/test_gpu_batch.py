@@ -86,7 +86,7 @@ def test_mixed_small_instances(opts):
 
 
 def test_gamma_omega_sweep_one_graph():
-    snaps = synth.config_graph(1)
+    snaps = synth.recipe_graph("planted_t4_n1000")
     with pkg.mslice_build(snaps) as h:
         grid = [((g, 4), (w, 4)) for g in (2, 4, 6) for w in (0, 1, 4)]
         instances = [(h, snaps, gamma, omega, None) for gamma, omega in grid]
@@ -98,7 +98,7 @@ def test_gamma_omega_sweep_one_graph():
 
 
 def test_warm_starts_and_repeat_runs():
-    snaps = synth.config_graph(1)
+    snaps = synth.recipe_graph("planted_t4_n1000")
     ref, _, _ = oracle.leiden(snaps)
     rng = np.random.default_rng(5)
     small = [small_instance(s) for s in (3, 7)]
@@ -132,7 +132,7 @@ def test_degenerate_instances():
     empty = [synth.Snapshot(np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int32))]
     single = synth.random_temporal(1, 3, p=0.0, seed=0)
     edgeless = [synth.random_temporal(5, 1, p=0.0, seed=0)[0]]
-    planted = synth.config_graph(1)
+    planted = synth.recipe_graph("planted_t4_n1000")
     graphs = [empty, single, planted, edgeless, planted]
     handles = [pkg.mslice_build(s) for s in graphs]
     instances = [(h, s, (1, 1), (1, 1), None) for h, s in zip(handles, graphs)]
@@ -160,9 +160,9 @@ def test_batch_medium_graphs_match_single_solves():
     """Larger instances (several degree tiers, several levels): each equals
     the standalone GPU solve, which the parity suite ties to the oracle; one
     of them is checked against the oracle directly."""
-    graphs = [synth.config_graph({**synth.CONFIGS[2], "n": 6000, "T": 5}),
-              synth.config_graph({**synth.CONFIGS[2], "n": 3000, "T": 3, "seed": 7}),
-              synth.config_graph(1)]
+    graphs = [synth.recipe_graph({**synth.RECIPES["powerlaw_t16_n100k"], "n": 6000, "T": 5}),
+              synth.recipe_graph({**synth.RECIPES["powerlaw_t16_n100k"], "n": 3000, "T": 3, "seed": 7}),
+              synth.recipe_graph("planted_t4_n1000")]
     handles = [pkg.mslice_build(s) for s in graphs]
     params = [((1, 1), (1, 1)), ((3, 2), (1, 4)), ((1, 2), (2, 1)), ((1, 1), (0, 1))]
     instances = [(handles[i % 3], graphs[i % 3], g, w, None) for i, (g, w) in enumerate(params)]

@@ -42,7 +42,7 @@ for seed in range(16):
     ref, Qref, _ = oracle.leiden(snaps, gamma, omega, K=1 + seed % 4, seed=seed)
     assert np.array_equal(lab, ref) and np.array_equal(lab2, lab) and Q2 == Q, seed
     assert abs(Q - Qref) <= 1e-12 * max(1.0, abs(Qref)), seed
-snaps = synth.config_graph({**synth.CONFIGS[2], "n": 3000, "T": 4})
+snaps = synth.recipe_graph({**synth.RECIPES["powerlaw_t16_n100k"], "n": 3000, "T": 4})
 with pkg.mslice_build(snaps) as h, pkg.Batch() as b:
     for gm in [(1, 1), (3, 2), (1, 2)]:
         b.add(h, gm, (1, 1))

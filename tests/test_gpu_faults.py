@@ -43,7 +43,7 @@ def inject(monkeypatch):
 
 def test_allocation_failures_in_build_and_solve(inject):
     on, off = inject
-    snaps = synth.config_graph(1)
+    snaps = synth.recipe_graph("planted_t4_n1000")
     ref, Qref, _ = oracle.leiden(snaps)
     failures = 0
     for k in [0, 1, 3, 8, 16, 32, 64, 128]:
@@ -65,7 +65,7 @@ def test_allocation_failures_in_build_and_solve(inject):
 
 def test_handle_survives_a_failed_solve(inject):
     on, off = inject
-    snaps = synth.config_graph({**synth.CONFIGS[2], "n": 3000, "T": 4})
+    snaps = synth.recipe_graph({**synth.RECIPES["powerlaw_t16_n100k"], "n": 3000, "T": 4})
     ref, Qref, _ = oracle.leiden(snaps)
     other, Qo, _ = oracle.leiden(snaps, gamma=(3, 2))
     with pkg.mslice_build(snaps) as h:
@@ -88,7 +88,7 @@ def test_handle_survives_a_failed_solve(inject):
 
 def test_batch_survives_a_failed_run(inject):
     on, off = inject
-    snaps = synth.config_graph(1)
+    snaps = synth.recipe_graph("planted_t4_n1000")
     params = [((1, 1), (1, 1)), ((3, 2), (1, 4)), ((1, 2), (2, 1))]
     with pkg.mslice_build(snaps) as h, pkg.Batch() as b:
         for gm, om in params:

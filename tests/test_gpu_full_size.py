@@ -64,8 +64,8 @@ def q_ok(q, ref):
 
 
 def test_power_law_full_size():
-    solves = fsc.cases()["config2_full"]()
-    exp = expected("config2_full", solves)
+    solves = fsc.cases()["powerlaw_t16_n100k"]()
+    exp = expected("powerlaw_t16_n100k", solves)
     s = solves[0]
     with pkg.mslice_build(s["snaps"]) as h:
         lab, Q, st = h.mslice_leiden(gamma=s["gamma"], omega=s["omega"])
@@ -76,8 +76,8 @@ def test_power_law_full_size():
 
 
 def test_T64_recipe_plain_and_batched():
-    solves = fsc.cases()["config4_T64_n20k"]()
-    exp = expected("config4_T64_n20k", solves)
+    solves = fsc.cases()["powerlaw_t64_n20k"]()
+    exp = expected("powerlaw_t64_n20k", solves)
     with pkg.mslice_build(solves[0]["snaps"]) as h:
         for s, e in zip(solves, exp):
             lab, Q, _ = h.mslice_leiden(gamma=s["gamma"], omega=s["omega"])
@@ -94,8 +94,8 @@ def test_T64_recipe_plain_and_batched():
 
 
 def test_batched_workload_graphs_in_one_batch():
-    solves = fsc.cases()["config3_sample"]()
-    exp = expected("config3_sample", solves)
+    solves = fsc.cases()["batched_sample"]()
+    exp = expected("batched_sample", solves)
     handles = {}
     with pkg.Batch() as b:
         for s in solves:
@@ -112,8 +112,8 @@ def test_batched_workload_graphs_in_one_batch():
 
 
 def test_serving_chain_full_size():
-    s = fsc.cases()["config5_chain"]()[0]
-    exp = expected("config5_chain", [s])[0]["chain"]
+    s = fsc.cases()["serving_chain"]()[0]
+    exp = expected("serving_chain", [s])[0]["chain"]
     stream, W = s["stream"], s["W"]
     with pkg.Server(window=W, n_slots=2) as srv:
         g = srv.add_graph(stream[0].n)

@@ -52,8 +52,8 @@ def assert_same(g, o):
         assert gs[k] == os_[k], (k, gs[k], os_[k])
 
 
-def test_config1_planted_partition():
-    snaps = synth.config_graph(1)
+def test_planted_t4_n1000():
+    snaps = synth.recipe_graph("planted_t4_n1000")
     g, o = solve_both(snaps)
     assert_same(g, o)
     assert g[1] == o[1]  # same FP64 operation order: bit-equal Q
@@ -80,8 +80,8 @@ def test_random_small(seed):
 
 @pytest.mark.parametrize("stage", [1, 2, 3])
 @pytest.mark.parametrize("level", [0, 1])
-def test_stages_config1(stage, level):
-    snaps = synth.config_graph(1)
+def test_stages_planted_t4_n1000(stage, level):
+    snaps = synth.recipe_graph("planted_t4_n1000")
     g, o = solve_both(snaps, stop_level=level, stop_stage=stage)
     assert np.array_equal(g[0], o[0])
     if stage == 3:
@@ -91,7 +91,7 @@ def test_stages_config1(stage, level):
 
 @pytest.mark.parametrize("rounds", [1, 2, -1])
 def test_stage_rounds(rounds):
-    snaps = synth.config_graph(1)
+    snaps = synth.recipe_graph("planted_t4_n1000")
     for stage in (1, 2):
         g, o = solve_both(snaps, stop_level=0, stop_stage=stage, stop_rounds=rounds, K=3, seed=5)
         assert np.array_equal(g[0], o[0])
@@ -128,7 +128,7 @@ def test_degree_tiers():
 
 
 def test_modularity_parity():
-    snaps = synth.config_graph(1)
+    snaps = synth.recipe_graph("planted_t4_n1000")
     rng = np.random.default_rng(0)
     with pkg.mslice_build(snaps) as h:
         for trial in range(6):
@@ -153,7 +153,7 @@ def test_hand_worked_cases_on_gpu():
 
 def test_warm_start_and_device_pointers():
     torch = _cuda()
-    snaps = synth.config_graph(1)
+    snaps = synth.recipe_graph("planted_t4_n1000")
     ref, Qref, _ = oracle.leiden(snaps)
     init = np.roll(ref, 7).astype(np.int32)
     o = oracle.leiden(snaps, init=init, n_iterations=1)
@@ -168,7 +168,7 @@ def test_warm_start_and_device_pointers():
 
 def test_device_pointer_build():
     torch = _cuda()
-    snaps = synth.config_graph(1)
+    snaps = synth.recipe_graph("planted_t4_n1000")
 
     class DSnap:
         def __init__(self, s):
@@ -184,7 +184,7 @@ def test_device_pointer_build():
 
 
 def test_repeatable_bits():
-    snaps = synth.config_graph({**synth.CONFIGS[2], "n": 20000, "T": 4})
+    snaps = synth.recipe_graph({**synth.RECIPES["powerlaw_t16_n100k"], "n": 20000, "T": 4})
     with pkg.mslice_build(snaps) as h:
         a = h.mslice_leiden()
         b = h.mslice_leiden()
@@ -192,7 +192,7 @@ def test_repeatable_bits():
 
 
 def test_medium_dcsbm_parity():
-    snaps = synth.config_graph({**synth.CONFIGS[2], "n": 6000, "T": 5})
+    snaps = synth.recipe_graph({**synth.RECIPES["powerlaw_t16_n100k"], "n": 6000, "T": 5})
     g, o = solve_both(snaps)
     assert_same(g, o)
 
@@ -255,7 +255,7 @@ def test_hashed_tables_path(seed, monkeypatch):
 
 def test_hashed_tables_medium(monkeypatch):
     monkeypatch.setenv("MSLICE_DENSE_LIMIT", "0")
-    snaps = synth.config_graph({**synth.CONFIGS[2], "n": 6000, "T": 5})
+    snaps = synth.recipe_graph({**synth.RECIPES["powerlaw_t16_n100k"], "n": 6000, "T": 5})
     g, o = solve_both(snaps)
     assert_same(g, o)
 
@@ -263,7 +263,7 @@ def test_hashed_tables_medium(monkeypatch):
 def test_tier_cuts_and_autotune_do_not_change_results():
     """The degree cuts decide only which kernel decides a node: any valid
     cuts, and the autotuner's choice, give the same bits."""
-    snaps = synth.config_graph({**synth.CONFIGS[2], "n": 6000, "T": 5})
+    snaps = synth.recipe_graph({**synth.RECIPES["powerlaw_t16_n100k"], "n": 6000, "T": 5})
     ref, Qref, _ = oracle.leiden(snaps)
     with pkg.mslice_build(snaps) as h:
         for cuts in [(16, 32, 256, 1024), (0, 0, 0, 0), (4, 8, 16, 32), (16, 16, 64, 64), (0, 32, 256, 1024)]:
@@ -285,6 +285,6 @@ def test_round_graphs_give_the_same_bits(monkeypatch):
     for limit in (None, "0"):
         if limit is not None:
             monkeypatch.setenv("MSLICE_DENSE_LIMIT", limit)
-        snaps = synth.config_graph({**synth.CONFIGS[2], "n": 4000, "T": 4})
+        snaps = synth.recipe_graph({**synth.RECIPES["powerlaw_t16_n100k"], "n": 4000, "T": 4})
         g, o = solve_both(snaps, (1, 1), (1, 2), K=3, seed=4)
         assert_same(g, o)

@@ -253,7 +253,7 @@ def test_move_key_is_scaled_delta_Q(seed):
 
 
 def test_quantised_gamma_is_close():
-    snaps = synth.config_graph(1)
+    snaps = synth.recipe_graph("planted_t4_n1000")
     lam, m2 = oracle.lambdas(snaps, (1, 1))
     for s in range(len(snaps)):
         g = Fraction(lam[s] * m2[s], 1 << 64)
@@ -345,7 +345,7 @@ def test_converged_invariants_not_vacuous():
 
 
 def test_canonical_labels_and_stats():
-    snaps = synth.config_graph(1)
+    snaps = synth.recipe_graph("planted_t4_n1000")
     labels, Q, st = oracle.leiden(snaps)
     first = {}
     for v, c in enumerate(labels.tolist()):
@@ -358,7 +358,7 @@ def test_canonical_labels_and_stats():
 
 
 def test_debug_stages_consistent():
-    snaps = synth.config_graph(1)
+    snaps = synth.recipe_graph("planted_t4_n1000")
     N = 4000
     p1, _, s1 = oracle.leiden(snaps, stop_level=0, stop_stage=1)
     r2, _, s2 = oracle.leiden(snaps, stop_level=0, stop_stage=2)
@@ -373,7 +373,7 @@ def test_debug_stages_consistent():
 
 
 def test_warm_start_identity():
-    snaps = synth.config_graph(1)
+    snaps = synth.recipe_graph("planted_t4_n1000")
     labels, Q, _ = oracle.leiden(snaps)
     l2, Q2, st = oracle.leiden(snaps, init=labels, n_iterations=1)
     assert Q2 >= Q - 1e-12

@@ -58,9 +58,9 @@ def test_noalloc_matches_handle_path_twice(case):
     pkg.build()
     rng = np.random.default_rng(case)
     if case == 0:
-        snaps = synth.config_graph(1)
+        snaps = synth.recipe_graph("planted_t4_n1000")
     elif case == 1:
-        snaps = synth.config_graph({**synth.CONFIGS[2], "n": 5000, "T": 6})
+        snaps = synth.recipe_graph({**synth.RECIPES["powerlaw_t16_n100k"], "n": 5000, "T": 6})
     else:
         snaps = synth.random_temporal(40, 3, p=0.2, w_max=5, seed=7, p_empty=0.3)
     N = snaps[0].n * len(snaps)
@@ -78,7 +78,7 @@ def test_noalloc_matches_handle_path_twice(case):
 def test_noalloc_rejects_oversize_and_bad_labels():
     torch = _torch()
     pkg.build()
-    snaps = synth.config_graph(1)
+    snaps = synth.recipe_graph("planted_t4_n1000")
     bad = np.full(4000, 4000, np.int32)
     rc, _ = _noalloc_q(torch, snaps, bad, (1, 1), (1, 1))
     assert rc == pkg.MSLICE_EINVAL
