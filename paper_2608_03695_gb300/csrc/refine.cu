@@ -29,7 +29,7 @@ __device__ __forceinline__ u128 lam_k_x(const u128* lam, int32_t s, long long k,
 
 // Per node: W(v,C\v), eligibility, initial sub-community state.
 __global__ void k_ref_init(LevelDev g, const int32_t* P, SigStore sig, const u128* lam, int32_t* R, int32_t* sizeR,
-                           long long* Wc, long long* Wout, uint8_t* elig, SigStore kr) {
+                           long long* Wc, long long* Wout, uint8_t* elig, SigStore kr, long long* PR) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t v = (((int64_t)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); v < g.N; v += warps) {
@@ -44,6 +44,7 @@ __global__ void k_ref_init(LevelDev g, const int32_t* P, SigStore sig, const u12
     w = warp_sum(w);
     if (lane == 0) {
       R[v] = (int32_t)v;
+      PR[v] = (long long)(((unsigned long long)(uint32_t)C << 32) | (uint32_t)v);
       sizeR[v] = 1;
       Wc[v] = w;
       Wout[v] = w;
@@ -89,8 +90,10 @@ __global__ void k_rhs_accum(SigStore kr, const int32_t* sizeR, const int32_t* P,
 
 // (A sub-community label L is a node of the level, so its omega is that
 // node's instance's.)
+// Also packs what a candidate probe reads of sub-community L, as of the
+// sub-round start, into one word: size | class << 32 | well-connected << 40.
 __global__ void k_wc(LevelDev g, const int32_t* sizeR, const long long* Wout, const ull* rhs, const uint8_t* elig,
-                     uint8_t* wc) {
+                     const uint8_t* cls, uint8_t* wc, unsigned long long* desc) {
   for (int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; L < g.N; L += (int64_t)gridDim.x * blockDim.x) {
     const int32_t sz = sizeR[L];
     uint8_t f = 0;
@@ -102,6 +105,7 @@ __global__ void k_wc(LevelDev g, const int32_t* sizeR, const long long* Wout, co
       f = ((((i128)Wout[L]) << P_BITS) - (i128)((u128)(ull)od * x)) >= 0 ? 1 : 0;
     }
     wc[L] = f;
+    desc[L] = (unsigned long long)(uint32_t)sz | ((unsigned long long)cls[L] << 32) | ((unsigned long long)f << 40);
   }
 }
 
@@ -110,6 +114,8 @@ struct RefPolicy {
   LevelDev g;
   const int32_t* P;
   const int32_t* R;
+  const unsigned long long* desc;  // size, class, well-connectedness (k_wc)
+  const long long* PR;  // (P << 32) | R of every node, kept with R
   const int32_t* sizeR;
   const uint8_t* elig;
   const uint8_t* wc;
@@ -127,7 +133,7 @@ struct RefPolicy {
   };
   // Per node: at level 0 the snapshot s and A = od * Lambda_s * k.
   struct VCtx {
-    int32_t s;
+    int32_t s, Pv;
     bool single;
     long long k;
     Omega om;
@@ -141,6 +147,7 @@ struct RefPolicy {
     c.s = 0;
     c.k = 0;
     c.A = 0;
+    c.Pv = P[v];
     c.om = node_omega(g, v);
     if (c.single) {
       c.k = g.k0[v];
@@ -153,17 +160,19 @@ struct RefPolicy {
   __device__ bool edge(int32_t v, const VCtx& vc, int64_t e, int32_t& key, long long& w) const {
     int32_t u;
     if (!edge_at(g, e, u, w, vc.om)) return false;
-    if (P[u] != P[v]) return false;
-    key = R[u];
+    const unsigned long long pr = (unsigned long long)PR[u];  // (P[u], R[u]) in one load
+    if ((int32_t)(pr >> 32) != vc.Pv) return false;
+    key = (int32_t)(uint32_t)pr;
     return true;
   }
   __device__ int32_t own_key(int32_t) const { return -1; }
   __device__ i128 own(int32_t, const VCtx&, long long) const { return 0; }
   __device__ Probe probe(int32_t, const VCtx& vc, int32_t X) const {
     Probe p;
-    p.size = sizeR[X];
-    p.cls = cls[X];
-    p.wc = wc[X];
+    const unsigned long long d = desc[X];
+    p.size = (int32_t)(uint32_t)d;
+    p.cls = (uint8_t)(d >> 32);
+    p.wc = (uint8_t)(d >> 40);
     p.first = (vc.single && vc.k > 0) ? sst_first<DENSE>(kr, X, vc.s) : Slot{EMPTY_KEY, 0};
     return p;
   }
@@ -225,7 +234,8 @@ __device__ __forceinline__ bool seg3_item(const Segs3& sg, int64_t idx, int32_t&
 // One warp per active node: movers compute W(v, M_t \ v) over their edges to
 // other movers with the same target, then update sizes, K_{R,s} and W(R,C\R).
 __global__ void k_ref_apply(LevelDev g, Segs3 sg, const int32_t* P, const int32_t* target, const long long* Wc,
-                            const long long* Wsel, int32_t* R, int32_t* sizeR, long long* Wout, SigStore kr) {
+                            const long long* Wsel, int32_t* R, int32_t* sizeR, long long* Wout, SigStore kr,
+                            long long* PR) {
   const int lane = threadIdx.x & 31;
   const int total = seg3_total(sg);
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -239,11 +249,14 @@ __global__ void k_ref_apply(LevelDev g, Segs3 sg, const int32_t* P, const int32_
     for (int64_t e = g.rowptr[v] + lane; e < g.rowptr[v + 1]; e += 32) {
       int32_t u;
       long long W;
-      if (edge_at(g, e, u, W, om) && target[u] == t && P[u] == P[v]) wp += W;
+      // a target lies in the mover's own community, so target[u] == t
+      // implies P[u] == P[v]
+      if (edge_at(g, e, u, W, om) && target[u] == t) wp += W;
     }
     wp = warp_sum(wp);
     if (lane == 0) {
       R[v] = t;
+      PR[v] = (long long)(((unsigned long long)(uint32_t)P[v] << 32) | (uint32_t)t);
       atomicSub(&sizeR[v], 1);
       atomicAdd(&sizeR[t], 1);
       atomicAdd((ull*)&Wout[t], (ull)(Wc[v] - 2 * Wsel[v] - wp));
@@ -284,13 +297,17 @@ static void refine_impl(Solver& S, const Level& L, const int32_t* P, int it, int
   const int32_t N = L.d.N;
   if (N == 0) return;
   clear_store(S, S.kr);
+  long long* PR = c.ws->get<long long>("ref_PR", N);
   launch(c, k_ref_init, dim3(fixed_grid(8)), dim3(256), 0, L.d, P, S.sig, (const u128*)S.lam, S.R, S.sizeR, S.Wc,
-         S.Wout, S.elig, S.kr);
+         S.Wout, S.elig, S.kr, PR);
   bucket(S, L, 1, it, lvl, 0, S.inst_active);
   RefPolicy<DENSE> pol;
   pol.g = L.d;
   pol.P = P;
   pol.R = S.R;
+  pol.PR = PR;
+  unsigned long long* desc = c.ws->get<unsigned long long>("ref_desc", N);
+  pol.desc = desc;
   pol.sizeR = S.sizeR;
   pol.elig = S.elig;
   pol.wc = S.wc;
@@ -308,12 +325,12 @@ static void refine_impl(Solver& S, const Level& L, const int32_t* P, int it, int
              (const u128*)S.lam, S.rhs);
     }
     launch(c, k_wc, dim3(fixed_grid(8)), dim3(256), 0, L.d, (const int32_t*)S.sizeR, (const long long*)S.Wout,
-           (const ull*)S.rhs, (const uint8_t*)S.elig, S.wc);
+           (const ull*)S.rhs, (const uint8_t*)S.elig, (const uint8_t*)S.cls, S.wc, desc);
     pol.q = q;
     const Segs3 sg = bucket_segments(S, q);
     decide_all(c, pol, sg, S.tier_cnt, S.gkeys, S.gvals, S.goff);
     launch(c, k_ref_apply, dim3(fixed_grid(8)), dim3(256), 0, L.d, sg, P, (const int32_t*)S.target,
-           (const long long*)S.Wc, (const long long*)S.Wsel, S.R, S.sizeR, S.Wout, S.kr);
+           (const long long*)S.Wc, (const long long*)S.Wsel, S.R, S.sizeR, S.Wout, S.kr, PR);
     launch(c, k_ref_reset, dim3(fixed_grid(4)), dim3(256), 0, sg, S.target);
   }
 }
