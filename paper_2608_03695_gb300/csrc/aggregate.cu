@@ -2,14 +2,16 @@
 // sub-community, numbered by ascending sub-community label.  Contraction
 // without a sort: the level's nodes are bucketed by new id (member lists),
 // then one warp or block per new node walks its members' rows and sums the
-// weights per neighbouring new node in a table (shared memory, or global
-// scratch for rows with more than 4096 entries), dropping self-loops since
-// no key or check reads them and Q is always evaluated on level 0; the same
-// pass sums the members' snapshot strengths k_{x,s}.  Rows are written once
-// to an upper-bound layout and compacted.  The order of a row's entries is
-// not defined; nothing that reads a level depends on it (sums are exact
-// integers and every scan is order-free).  The initial label of a new node
-// is the smallest new id inside its local-moving community.
+// weights per neighbouring new node in a shared-memory table; rows with more
+// than 4096 entries use tables in global scratch and are spread over the
+// whole grid.  Self-loops are dropped: no key or check reads them, and Q is
+// always evaluated on level 0.  The same pass sums the members' snapshot
+// strengths k_{x,s}.  Rows are written once to an upper-bound layout and
+// compacted.  The order of a row's entries is not defined; nothing that
+// reads a level depends on it (sums are exact integers and every scan is
+// order-free).  The initial label of a new node is the smallest new id
+// inside its local-moving community.
+#include <algorithm>
 #include <cstring>
 
 #include "../../include/mslice.h"
@@ -61,7 +63,7 @@ __device__ __forceinline__ int64_t pow2_at_least(int64_t x) {
 // Rows by size: tier 0 (<= CW_MAX), 1 (<= CB_MAX), 2 (larger; its table of
 // pow2(2 * size) slots in global scratch).
 __global__ void k_contract_tier(int32_t Np, const long long* dsum, const int32_t* scnt, int32_t* lists,
-                                int32_t* tcnt, int64_t* gsize) {
+                                int32_t* tcnt, int64_t* gsize, int64_t* ssize) {
   const int lane = threadIdx.x & 31;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < Np; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t x = base + threadIdx.x;
@@ -69,7 +71,8 @@ __global__ void k_contract_tier(int32_t Np, const long long* dsum, const int32_t
     if (x < Np) {
       const long long need = max(dsum[x], (long long)scnt[x]);
       t = need <= CW_MAX ? 0 : (need <= CB_MAX ? 1 : 2);
-      gsize[x] = t == 2 ? pow2_at_least(2 * need) : 0;
+      gsize[x] = t == 2 ? pow2_at_least(2 * dsum[x]) : 0;
+      ssize[x] = t == 2 ? pow2_at_least(2 * (int64_t)scnt[x]) : 0;
     }
     const unsigned peers = __match_any_sync(0xffffffffu, t);
     const int leader = __ffs(peers) - 1;
@@ -208,45 +211,27 @@ __global__ void __launch_bounds__(CW_WARPS * 32)
   }
 }
 
-// One block per new node x (tiers 1 and 2): the table is in shared memory
-// (GLOBAL = false, 2^CB_BITS slots) or at gofs[x] in global scratch with
-// gsize[x] slots.  Warps take members in turn; lanes stride over entries.
-template <bool GLOBAL>
+// One block per new node x of tier 1: a table of 2^CB_BITS slots in shared
+// memory.  Warps take members in turn; lanes stride over entries.
 __global__ void __launch_bounds__(CB_THREADS)
     k_contract_block(LevelDev g, const int32_t* xmap, const int64_t* moff, const int32_t* mem, const int32_t* list,
                      const int32_t* count_ptr, const int64_t* eoff, const int64_t* soff, int32_t* tcol, long long* tw,
-                     int32_t* ecnt, int32_t* tsidx, long long* tsval, int32_t* scnt_out, const int64_t* gofs,
-                     const int64_t* gsize, int32_t* gk, long long* gv, uint32_t* gl) {
+                     int32_t* ecnt, int32_t* tsidx, long long* tsval, int32_t* scnt_out) {
   extern __shared__ __align__(16) unsigned char csm[];
   __shared__ int32_t ncnt;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   constexpr int NW = CB_THREADS / 32;
   const int count = *count_ptr;
-  int32_t* K;
-  long long* V;
-  uint32_t* CL;  // listed slots (a global table holds up to 2^32)
-  int64_t cap = (int64_t)1 << CB_BITS;
-  if (!GLOBAL) {
-    V = reinterpret_cast<long long*>(csm);
-    K = reinterpret_cast<int32_t*>(V + cap);
-    CL = reinterpret_cast<uint32_t*>(K + cap);
-    for (int64_t i = threadIdx.x; i < cap; i += blockDim.x) {
-      K[i] = -1;
-      V[i] = 0;
-    }
+  constexpr int64_t cap = (int64_t)1 << CB_BITS;
+  long long* V = reinterpret_cast<long long*>(csm);
+  int32_t* K = reinterpret_cast<int32_t*>(V + cap);
+  uint32_t* CL = reinterpret_cast<uint32_t*>(K + cap);  // listed slots
+  for (int64_t i = threadIdx.x; i < cap; i += blockDim.x) {
+    K[i] = -1;
+    V[i] = 0;
   }
   for (int64_t idx = blockIdx.x; idx < count; idx += gridDim.x) {
     const int32_t x = list[idx];
-    if (GLOBAL) {
-      cap = gsize[x];
-      K = gk + gofs[x];
-      V = gv + gofs[x];
-      CL = gl + gofs[x];
-      for (int64_t i = threadIdx.x; i < cap; i += blockDim.x) {
-        K[i] = -1;
-        V[i] = 0;
-      }
-    }
     if (threadIdx.x == 0) ncnt = 0;
     __syncthreads();
     const int64_t mb = moff[x], me = moff[x + 1];
@@ -314,6 +299,97 @@ __global__ void __launch_bounds__(CB_THREADS)
     }
     if (threadIdx.x == 0) scnt_out[x] = ns;
     __syncthreads();
+  }
+}
+
+// Tier 2 (rows of more than CB_MAX entries) is spread over the whole grid:
+// warps take the members of all such rows in turn and insert into the row's
+// tables in global scratch (edges and snapshot strengths in separate tables,
+// pre-filled with free slots), listing claimed slots with per-row counters;
+// a second kernel writes each row out.  big: the tier's rows; mpre: prefix of
+// their member counts (nbig + 1 entries).
+__global__ void k_big_members(const int32_t* big, const int32_t* nbig_ptr, const int64_t* moff, int64_t* cnt) {
+  const int nbig = *nbig_ptr;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nbig; i += (int64_t)gridDim.x * blockDim.x)
+    cnt[i] = moff[big[i] + 1] - moff[big[i]];
+}
+
+__global__ void k_big_insert(LevelDev g, const int32_t* xmap, const int64_t* moff, const int32_t* mem,
+                             const int32_t* big, const int32_t* nbig_ptr, const int64_t* mpre, const int64_t* gofs,
+                             const int64_t* gsize, int32_t* gk, long long* gv, uint32_t* gl, int32_t* gcnt,
+                             const int64_t* sofs, const int64_t* ssize, int32_t* sk, long long* sv, uint32_t* sl,
+                             int32_t* scnt) {
+  const int lane = threadIdx.x & 31;
+  const int nbig = *nbig_ptr;
+  const int64_t total = mpre[nbig];
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t f = (((int64_t)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); f < total; f += warps) {
+    int lo = 0, hi = nbig - 1;  // the big row holding member f
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (mpre[mid] <= f) lo = mid; else hi = mid - 1;
+    }
+    const int32_t x = big[lo];
+    const int32_t v = mem[moff[x] + (f - mpre[lo])];
+    const int64_t o = gofs[x], cap = gsize[x];
+    const Omega om = node_omega(g, v);
+    for (int64_t i = g.rowptr[v] + lane; i < g.rowptr[v + 1]; i += 32) {
+      int32_t u;
+      long long W;
+      if (edge_at(g, i, u, W, om)) {
+        const int32_t y = xmap[u];
+        if (y != x) {
+          bool fresh;
+          const int64_t slot = ctab_add(gk + o, gv + o, cap, y, W, fresh);
+#if MSLICE_CHECKED
+          if (slot < 0) atomicOr(g.chk, ERR_BOUNDS);
+#endif
+          if (fresh) gl[o + atomicAdd(&gcnt[lo], 1)] = (uint32_t)slot;
+        }
+      }
+    }
+    int64_t b, e;
+    slice_range(g, v, b, e);
+    const int64_t so = sofs[x], scap = ssize[x];
+    for (int64_t q = b + lane; q < e; q += 32) {
+      int32_t s;
+      long long k;
+      slice_entry(g, v, q, s, k);
+      bool fresh;
+      const int64_t slot = ctab_add(sk + so, sv + so, scap, s, k, fresh);
+#if MSLICE_CHECKED
+      if (slot < 0) atomicOr(g.chk, ERR_BOUNDS);
+#endif
+      if (fresh) sl[so + atomicAdd(&scnt[lo], 1)] = (uint32_t)slot;
+    }
+  }
+}
+
+__global__ void k_big_output(const int32_t* big, const int32_t* nbig_ptr, const int64_t* gofs, const int32_t* gk,
+                             const long long* gv, const uint32_t* gl, const int32_t* gcnt, const int64_t* sofs,
+                             const int32_t* sk,
+                             const long long* sv, const uint32_t* sl, const int32_t* scnt, const int64_t* eoff,
+                             const int64_t* soff, int32_t* tcol, long long* tw, int32_t* ecnt, int32_t* tsidx,
+                             long long* tsval, int32_t* scnt_out) {
+  const int nbig = *nbig_ptr;
+  for (int i = blockIdx.x; i < nbig; i += gridDim.x) {
+    const int32_t x = big[i];
+    const int64_t o = gofs[x], eo = eoff[x], so = soff[x], sb = sofs[x];
+    const int n = gcnt[i], ns = scnt[i];
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const uint32_t slot = gl[o + k];
+      tcol[eo + k] = gk[o + slot];
+      tw[eo + k] = gv[o + slot];
+    }
+    for (int k = threadIdx.x; k < ns; k += blockDim.x) {
+      const uint32_t slot = sl[sb + k];
+      tsidx[so + k] = sk[sb + slot];
+      tsval[so + k] = sv[sb + slot];
+    }
+    if (threadIdx.x == 0) {
+      ecnt[x] = n;
+      scnt_out[x] = ns;
+    }
   }
 }
 
@@ -419,18 +495,22 @@ bool aggregate(Solver& S, const Level& L, const int32_t* P, Level& next, const s
   int32_t* tcnt = c.ws->get<int32_t>("ag_tcnt", 4);
   int64_t* gsize = c.ws->get<int64_t>("ag_gsize", np1);
   int64_t* gofs = c.ws->get<int64_t>("ag_gofs", np1);
+  int64_t* ssize = c.ws->get<int64_t>("ag_ssize", np1);
+  int64_t* sofs = c.ws->get<int64_t>("ag_sofs", np1);
   check_cuda(cudaMemsetAsync(tcnt, 0, 4 * sizeof(int32_t), c.stream), "memset");
   check_cuda(cudaMemsetAsync(gsize + Np, 0, sizeof(int64_t), c.stream), "memset");
+  check_cuda(cudaMemsetAsync(ssize + Np, 0, sizeof(int64_t), c.stream), "memset");
   launch(c, k_contract_tier, dim3(gsz(Np)), dim3(256), 0, Np, (const long long*)dsum, (const int32_t*)scnt, lists, tcnt,
-         gsize);
-  int64_t* d_gtot = c.ws->get<int64_t>("ag_gtot", 1);
+         gsize, ssize);
+  int64_t* d_gtot = c.ws->get<int64_t>("ag_gtot", 2);
   scan_excl(c, (const int64_t*)gsize, gofs, np1, d_gtot);
+  scan_excl(c, (const int64_t*)ssize, sofs, np1, d_gtot + 1);
   struct {
     int32_t t[4];
-    int64_t gtot;
+    int64_t gtot, stot;
   } hd;
   check_cuda(cudaMemcpyAsync(c.pinned, tcnt, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream), "copy");
-  check_cuda(cudaMemcpyAsync(static_cast<char*>(c.pinned) + 16, d_gtot, sizeof(int64_t), cudaMemcpyDeviceToHost,
+  check_cuda(cudaMemcpyAsync(static_cast<char*>(c.pinned) + 16, d_gtot, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost,
                              c.stream), "copy");
   sync(c);
   std::memcpy(&hd, c.pinned, sizeof(hd));
@@ -451,23 +531,44 @@ bool aggregate(Solver& S, const Level& L, const int32_t* P, Level& next, const s
   const size_t cb_smem = ((size_t)1 << CB_BITS) * (sizeof(long long) + sizeof(int32_t)) +
                          (size_t)CB_MAX * sizeof(int32_t);
   if (hd.t[1] > 0) {
-    check_cuda(cudaFuncSetAttribute(k_contract_block<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cb_smem),
+    check_cuda(cudaFuncSetAttribute(k_contract_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cb_smem),
                "attribute");
-    launch(c, k_contract_block<false>, dim3(152 * 2), dim3(CB_THREADS), cb_smem, L.d, (const int32_t*)xmap,
+    launch(c, k_contract_block, dim3(152 * 2), dim3(CB_THREADS), cb_smem, L.d, (const int32_t*)xmap,
            (const int64_t*)moff, (const int32_t*)mem, (const int32_t*)(lists + Np), (const int32_t*)(tcnt + 1),
-           (const int64_t*)eoff, (const int64_t*)soff, tcol, tw, ecnt, tsidx, tsval, scnt_out, (const int64_t*)gofs,
-           (const int64_t*)gsize, (int32_t*)nullptr, (long long*)nullptr, (uint32_t*)nullptr);
+           (const int64_t*)eoff, (const int64_t*)soff, tcol, tw, ecnt, tsidx, tsval, scnt_out);
   }
   if (hd.t[2] > 0) {
     if (hd.gtot > ((int64_t)1 << 31) * 8) fail(MSLICE_ENOMEM, "aggregation scratch too large");
+    const int32_t nbig = hd.t[2];
+    const int32_t* big = lists + 2 * (int64_t)Np;
+    const int32_t* nbig_d = tcnt + 2;
     int32_t* gk = c.ws->get<int32_t>("ag_gk", hd.gtot);
     long long* gv = c.ws->get<long long>("ag_gv", hd.gtot);
     uint32_t* gl = c.ws->get<uint32_t>("ag_gl", hd.gtot);
-    launch(c, k_contract_block<true>, dim3(152 * 2), dim3(CB_THREADS), 0, L.d, (const int32_t*)xmap,
-           (const int64_t*)moff, (const int32_t*)mem, (const int32_t*)(lists + 2 * (int64_t)Np),
-           (const int32_t*)(tcnt + 2), (const int64_t*)eoff, (const int64_t*)soff, tcol, tw, ecnt, tsidx, tsval,
-           scnt_out, (const int64_t*)gofs, (const int64_t*)gsize, gk, gv, gl);
+    int32_t* sk = c.ws->get<int32_t>("ag_sk", hd.stot);
+    long long* sv = c.ws->get<long long>("ag_sv", hd.stot);
+    uint32_t* sl = c.ws->get<uint32_t>("ag_sl", hd.stot);
+    int32_t* cnts = c.ws->get<int32_t>("ag_bigcnt", 2 * (size_t)nbig);
+    int64_t* mcnt_big = c.ws->get<int64_t>("ag_bigm", (size_t)nbig + 1);
+    int64_t* mpre = c.ws->get<int64_t>("ag_bigpre", (size_t)nbig + 1);
+    check_cuda(cudaMemsetAsync(gk, 0xff, hd.gtot * sizeof(int32_t), c.stream), "memset");
+    check_cuda(cudaMemsetAsync(gv, 0, hd.gtot * sizeof(long long), c.stream), "memset");
+    check_cuda(cudaMemsetAsync(sk, 0xff, hd.stot * sizeof(int32_t), c.stream), "memset");
+    check_cuda(cudaMemsetAsync(sv, 0, hd.stot * sizeof(long long), c.stream), "memset");
+    check_cuda(cudaMemsetAsync(cnts, 0, 2 * (size_t)nbig * sizeof(int32_t), c.stream), "memset");
+    check_cuda(cudaMemsetAsync(mcnt_big + nbig, 0, sizeof(int64_t), c.stream), "memset");
+    launch(c, k_big_members, dim3(gsz(nbig)), dim3(256), 0, big, nbig_d, (const int64_t*)moff, mcnt_big);
+    scan_excl(c, (const int64_t*)mcnt_big, mpre, (int64_t)nbig + 1, (int64_t*)nullptr);
+    launch(c, k_big_insert, dim3(152 * 8), dim3(256), 0, L.d, (const int32_t*)xmap, (const int64_t*)moff,
+           (const int32_t*)mem, big, nbig_d, (const int64_t*)mpre, (const int64_t*)gofs, (const int64_t*)gsize, gk,
+           gv, gl, cnts, (const int64_t*)sofs, (const int64_t*)ssize, sk, sv, sl, cnts + nbig);
+    launch(c, k_big_output, dim3(std::min<int32_t>(nbig, 152 * 4)), dim3(256), 0, big, nbig_d,
+           (const int64_t*)gofs, (const int32_t*)gk, (const long long*)gv, (const uint32_t*)gl,
+           (const int32_t*)cnts, (const int64_t*)sofs, (const int32_t*)sk, (const long long*)sv, (const uint32_t*)sl,
+           (const int32_t*)(cnts + nbig), (const int64_t*)eoff, (const int64_t*)soff, tcol, tw, ecnt, tsidx, tsval,
+           scnt_out);
   }
+
   int64_t* rowptr = c.ws->get<int64_t>(slot + "_rowptr", (size_t)np1);
   int64_t* sptr = c.ws->get<int64_t>(slot + "_sptr", (size_t)np1);
   int64_t* d_tot = c.ws->get<int64_t>("ag_tot", 2);
