@@ -17,6 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liboracle.so")
 
 OK, EINVAL, EOVERFLOW = 0, -1, -3
+NULL_MULTISLICE, NULL_GLOBAL = 0, 1
+_NULLS = {"multislice": NULL_MULTISLICE, "global": NULL_GLOBAL}
 
 
 class OracleError(RuntimeError):
@@ -32,7 +34,7 @@ class _Csr(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("n_iterations", C.c_int32), ("K", C.c_int32), ("max_rounds", C.c_int32),
                 ("max_levels", C.c_int32), ("seed", C.c_uint64), ("stop_level", C.c_int32),
-                ("stop_stage", C.c_int32), ("stop_rounds", C.c_int32)]
+                ("stop_stage", C.c_int32), ("stop_rounds", C.c_int32), ("null_model", C.c_int32)]
 
 
 class _Stats(C.Structure):
@@ -64,11 +66,12 @@ def lib():
         P = C.c_void_p
         L.orc_leiden.argtypes = [P, C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_int64, P, P, P, C.c_int64,
                                  P, P]
-        L.orc_modularity.argtypes = [P, C.c_int32, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, P]
-        L.orc_move_key.argtypes = [P, C.c_int32, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int64,
-                                   C.c_int64, P]
+        L.orc_modularity.argtypes = [P, C.c_int32, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int32, P]
+        L.orc_move_key.argtypes = [P, C.c_int32, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
+                                   C.c_int64, C.c_int64, P]
         L.orc_lambda.argtypes = [P, C.c_int32, C.c_int64, C.c_int64, P, P]
-        L.orc_count_improving.argtypes = [P, C.c_int32, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, P]
+        L.orc_count_improving.argtypes = [P, C.c_int32, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
+                                          P]
         L.orc_mix64.argtypes = [C.c_uint64]
         L.orc_mix64.restype = C.c_uint64
         L.orc_default_opts.argtypes = [P]
@@ -105,11 +108,17 @@ def _check(rc, what):
         raise OracleError(rc, what)
 
 
+def _null(null) -> int:
+    """'multislice' (Q_MS's per-slice null term) or 'global' (plain modularity
+    of the supra-graph); an int passes through unchanged."""
+    return _NULLS[null] if isinstance(null, str) else int(null)
+
+
 def leiden(snaps, gamma=(1, 1), omega=(1, 1), n_iterations=2, K=4, max_rounds=100, max_levels=32, seed=0,
-           init=None, stop_level=-1, stop_stage=0, stop_rounds=0):
+           init=None, stop_level=-1, stop_stage=0, stop_rounds=0, null="multislice"):
     """Returns (labels int32[...], Q, stats dict)."""
     S = _Slices(snaps)
-    o = _Opts(n_iterations, K, max_rounds, max_levels, seed, stop_level, stop_stage, stop_rounds)
+    o = _Opts(n_iterations, K, max_rounds, max_levels, seed, stop_level, stop_stage, stop_rounds, _null(null))
     cap = max(S.N, 1)
     out = np.zeros(cap, dtype=np.int32)
     Q = C.c_double(0.0)
@@ -122,21 +131,21 @@ def leiden(snaps, gamma=(1, 1), omega=(1, 1), n_iterations=2, K=4, max_rounds=10
     return out[: st.out_n].copy(), Q.value, stats
 
 
-def modularity(snaps, labels, gamma=(1, 1), omega=(1, 1)):
+def modularity(snaps, labels, gamma=(1, 1), omega=(1, 1), null="multislice"):
     S = _Slices(snaps)
     lab = np.ascontiguousarray(labels, dtype=np.int32)
     Q = C.c_double(0.0)
-    _check(lib().orc_modularity(S.ptr, S.T, _ptr(lab), gamma[0], gamma[1], omega[0], omega[1], C.byref(Q)),
-           "orc_modularity")
+    _check(lib().orc_modularity(S.ptr, S.T, _ptr(lab), gamma[0], gamma[1], omega[0], omega[1], _null(null),
+                                C.byref(Q)), "orc_modularity")
     return Q.value
 
 
-def move_key(snaps, labels, v, c, gamma=(1, 1), omega=(1, 1)) -> int:
+def move_key(snaps, labels, v, c, gamma=(1, 1), omega=(1, 1), null="multislice") -> int:
     S = _Slices(snaps)
     lab = np.ascontiguousarray(labels, dtype=np.int32)
     out = (C.c_uint64 * 2)()
-    _check(lib().orc_move_key(S.ptr, S.T, _ptr(lab), gamma[0], gamma[1], omega[0], omega[1], v, c, out),
-           "orc_move_key")
+    _check(lib().orc_move_key(S.ptr, S.T, _ptr(lab), gamma[0], gamma[1], omega[0], omega[1], _null(null), v, c,
+                              out), "orc_move_key")
     x = out[0] | (out[1] << 64)
     return x - (1 << 128) if x >> 127 else x
 
@@ -149,11 +158,11 @@ def lambdas(snaps, gamma=(1, 1)):
     return [int(lam[2 * s]) | (int(lam[2 * s + 1]) << 64) for s in range(S.T)], [int(x) for x in tm]
 
 
-def count_improving(snaps, labels, gamma=(1, 1), omega=(1, 1)) -> int:
+def count_improving(snaps, labels, gamma=(1, 1), omega=(1, 1), null="multislice") -> int:
     S = _Slices(snaps)
     lab = np.ascontiguousarray(labels, dtype=np.int32)
     cnt = C.c_int64(0)
-    _check(lib().orc_count_improving(S.ptr, S.T, _ptr(lab), gamma[0], gamma[1], omega[0], omega[1],
+    _check(lib().orc_count_improving(S.ptr, S.T, _ptr(lab), gamma[0], gamma[1], omega[0], omega[1], _null(null),
                                      C.byref(cnt)), "orc_count_improving")
     return cnt.value
 

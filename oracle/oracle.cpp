@@ -57,12 +57,23 @@ struct Level {
   }
 };
 
+// Null models.  ORC_NULL_MULTISLICE: the per-slice null term of Eq.
+// multislice-modularity.  ORC_NULL_GLOBAL: plain modularity (Eq. modularity)
+// on the supra-adjacency of Eq. supra-adjacency, the proxy Sec. 3.2 runs with
+// cuGraph's Leiden: coupling edges count in the degrees and one null term
+// covers the whole supra-graph.  For the global model the strengths and sums
+// below are kept in units of 1/od (k' = od*k + on*c, c = the node's coupling
+// edges), the null "slice" is single (index 0) and the key's null scale is 1
+// instead of od.
 struct Problem {
   int32_t T = 0;
   int64_t n = 0;
   int64_t gn = 1, gd = 1, on = 1, od = 1;
-  std::vector<int64_t> two_m;  // 2m_s
-  std::vector<u128> lambda;    // Lambda_s
+  int32_t null_model = ORC_NULL_MULTISLICE;
+  int64_t ns = 1;              // null scale of the key: od (multislice) or 1 (global)
+  std::vector<int64_t> two_m;  // 2m_s of every snapshot
+  std::vector<int64_t> two_m_null;  // masses of the null slices: 2m_s, or {2M'} (global)
+  std::vector<u128> lambda;    // Lambda of every null slice
 };
 
 bool valid_rational(int64_t num, int64_t den, bool allow_zero) {
@@ -112,13 +123,28 @@ int validate(const orc_csr* slices, int32_t T) {
 // multi-slice nodes would need lcm(2m_s); both implementations instead
 // compare keys built from Lambda_s, i.e. they optimise Q_MS with
 // gamma'_s = Lambda_s*2m_s/2^P, within 2m_s/2^64 of gamma (relative).
+// Global model: one null slice of mass 2M' = od*sum(2m_s) + 2*on*n*(T-1) (the
+// supra-graph's total weight in units of 1/od) and
+//   Lambda' = floor(gn * 2^P / (gd * 2M')).
 void slice_masses(const orc_csr* slices, Problem& p) {
   p.two_m.assign(p.T, 0);
-  p.lambda.assign(p.T, 0);
   for (int32_t s = 0; s < p.T; ++s) {
     int64_t t = 0;
     for (int64_t e = 0; e < (p.n > 0 ? slices[s].indptr[p.n] : 0); ++e) t += slices[s].weights[e];
     p.two_m[s] = t;
+  }
+  if (p.null_model == ORC_NULL_GLOBAL) {
+    int64_t sum2m = 0;
+    for (int64_t t : p.two_m) sum2m += t;
+    p.two_m_null.assign(1, p.od * sum2m + 2 * p.on * p.n * (int64_t)(p.T - 1));
+    p.ns = 1;
+  } else {
+    p.two_m_null = p.two_m;
+    p.ns = p.od;
+  }
+  p.lambda.assign(p.two_m_null.size(), 0);
+  for (size_t s = 0; s < p.two_m_null.size(); ++s) {
+    const int64_t t = p.two_m_null[s];
     if (t > 0) p.lambda[s] = (((u128)(uint64_t)p.gn) << P_BITS) / ((u128)(uint64_t)p.gd * (u128)(uint64_t)t);
   }
 }
@@ -130,8 +156,11 @@ int check_bounds(const Problem& p) {
   for (int64_t t : p.two_m) sum2m += (u128)(uint64_t)t;
   u128 ncpl = (u128)(uint64_t)p.n * (u128)(uint64_t)(p.T - 1);
   u128 lim = (u128)1 << 61;
-  if ((u128)(uint64_t)p.od * sum2m + 2 * (u128)(uint64_t)p.on * ncpl >= lim) return ORC_EOVERFLOW;
-  if ((u128)(uint64_t)p.gn * (u128)(uint64_t)p.od * sum2m >= lim * (u128)(uint64_t)p.gd) return ORC_EOVERFLOW;
+  const u128 twoM = (u128)(uint64_t)p.od * sum2m + 2 * (u128)(uint64_t)p.on * ncpl;
+  if (twoM >= lim) return ORC_EOVERFLOW;
+  // global model: the null term's strengths include coupling, so gamma*2M'
+  const u128 null_mass = p.null_model == ORC_NULL_GLOBAL ? twoM : (u128)(uint64_t)p.od * sum2m;
+  if ((u128)(uint64_t)p.gn * null_mass >= lim * (u128)(uint64_t)p.gd) return ORC_EOVERFLOW;
   return ORC_OK;
 }
 
@@ -154,7 +183,14 @@ Level build_level0(const orc_csr* slices, const Problem& p) {
         k += slices[s].weights[e];
       }
       if (s < p.T - 1 && p.on > 0) a.push_back({(int32_t)(v + p.n), p.on});
-      if (k > 0) L.kvec[v].push_back({s, k});
+      if (p.null_model == ORC_NULL_GLOBAL) {
+        // k' = od*k + on*(coupling edges of v), one null slice
+        const int64_t c = (s > 0 ? 1 : 0) + (s < p.T - 1 ? 1 : 0);
+        const int64_t kp = p.od * k + p.on * c;
+        if (kp > 0) L.kvec[v].push_back({0, kp});
+      } else if (k > 0) {
+        L.kvec[v].push_back({s, k});
+      }
     }
   }
   return L;
@@ -177,8 +213,11 @@ u128 null_sum(const Problem& p, const std::vector<std::pair<int32_t, int64_t>>& 
 //   g(v,c) = W(v,c\v)/od - sum_s gamma k_{v,s} Sigma_{c\v,s} / 2m_s).
 // Scaled by od*2^P and with gamma/2m_s quantised to Lambda_s/2^P:
 //   G(v,c) = 2^P W(v,c\v) - od * sum_s Lambda_s k_{v,s} Sigma_{c\v,s}.
+// Global model (Eq. modularity on the supra-graph, all in units of 1/od):
+// g(v,c) = W(v,c\v) - gamma k'_v Sigma'_{c\v} / 2M', so
+//   G(v,c) = 2^P W(v,c\v) - Lambda' k'_v Sigma'_{c\v}   (null scale 1).
 i128 key(const Problem& p, int64_t W, u128 nullsum) {
-  return (((i128)W) << P_BITS) - (i128)((u128)(uint64_t)p.od * nullsum);
+  return (((i128)W) << P_BITS) - (i128)((u128)(uint64_t)p.ns * nullsum);
 }
 
 typedef std::map<int32_t, int64_t> SliceMap;  // slice -> sum
@@ -468,7 +507,51 @@ double u128_to_double(u128 x) { return (double)x; }
 // Fixed evaluation order (reading, shared by both implementations): slice
 // terms as (double)S_s/(double)2m_s summed in ascending s, then omega*J as
 // ((double)on*(double)J)/(double)od, then the numerator, then the division.
+// Global model, Eq. modularity on the supra-graph with total weight 2mu:
+//   Q = (I + omega*J) / 2mu - gamma * S' / (2mu)^2,
+//   S' = sum_c (sum_{v in c} k'_v)^2 in units of 1/od^2, so the second term is
+//   evaluated as S' / (2M')^2 with 2M' = od*2mu.
+// Fixed order: I + omega*J as above, divided by 2mu; S' (double) divided by
+// ((double)2M' * (double)2M'); times gamma; subtracted.
+double modularity_global(const orc_csr* slices, const Problem& p, const std::vector<int32_t>& labels) {
+  const int64_t n = p.n;
+  int64_t I = 0, J = 0;
+  std::map<int32_t, u128> sig;  // Sigma'_c
+  for (int32_t s = 0; s < p.T; ++s) {
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t v = (int64_t)s * n + i;
+      int64_t k = 0;
+      for (int64_t e = slices[s].indptr[i]; e < slices[s].indptr[i + 1]; ++e) {
+        const int64_t u = (int64_t)s * n + slices[s].indices[e];
+        if (labels[u] == labels[v]) I += slices[s].weights[e];
+        k += slices[s].weights[e];
+      }
+      int64_t c = 0;
+      if (s > 0) {
+        c++;
+        if (labels[v - n] == labels[v]) J++;
+      }
+      if (s < p.T - 1) {
+        c++;
+        if (labels[v + n] == labels[v]) J++;
+      }
+      sig[labels[v]] += (u128)(uint64_t)(p.od * k + p.on * c);
+    }
+  }
+  u128 S = 0;
+  for (const auto& cs : sig) S += cs.second * cs.second;
+  const int64_t twoM = p.two_m_null[0];
+  if (twoM == 0) return 0.0;  // reading: no edges and no coupling -> Q = 0
+  const double wJ = ((double)p.on * (double)J) / (double)p.od;
+  const double gam = (double)p.gn / (double)p.gd;
+  const double twomu = (double)twoM / (double)p.od;
+  const double first = ((double)I + wJ) / twomu;
+  const double null = u128_to_double(S) / ((double)twoM * (double)twoM);
+  return first - gam * null;
+}
+
 double modularity_of(const orc_csr* slices, const Problem& p, const std::vector<int32_t>& labels) {
+  if (p.null_model == ORC_NULL_GLOBAL) return modularity_global(slices, p, labels);
   const int64_t n = p.n;
   int64_t I = 0, J = 0;
   std::map<int32_t, SliceMap> sig;
@@ -503,10 +586,13 @@ double modularity_of(const orc_csr* slices, const Problem& p, const std::vector<
   return num / twomu;
 }
 
-int setup(const orc_csr* slices, int32_t T, int64_t gn, int64_t gd, int64_t on, int64_t od, Problem& p) {
+int setup(const orc_csr* slices, int32_t T, int64_t gn, int64_t gd, int64_t on, int64_t od, Problem& p,
+          int32_t null_model = ORC_NULL_MULTISLICE) {
   int rc = validate(slices, T);
   if (rc) return rc;
   if (!valid_rational(gn, gd, false) || !valid_rational(on, od, true)) return ORC_EINVAL;
+  if (null_model != ORC_NULL_MULTISLICE && null_model != ORC_NULL_GLOBAL) return ORC_EINVAL;
+  p.null_model = null_model;
   p.T = T;
   p.n = slices[0].n;
   p.gn = gn;
@@ -532,6 +618,7 @@ void orc_default_opts(orc_opts* o) {
   o->stop_level = -1;
   o->stop_stage = 0;
   o->stop_rounds = 0;
+  o->null_model = ORC_NULL_MULTISLICE;
 }
 
 int orc_lambda(const orc_csr* slices, int32_t T, int64_t gn, int64_t gd, uint64_t* lam, int64_t* two_m) {
@@ -547,9 +634,9 @@ int orc_lambda(const orc_csr* slices, int32_t T, int64_t gn, int64_t gd, uint64_
 }
 
 int orc_modularity(const orc_csr* slices, int32_t T, const int32_t* labels, int64_t gn, int64_t gd, int64_t on,
-                   int64_t od, double* Q_out) {
+                   int64_t od, int32_t null_model, double* Q_out) {
   Problem p;
-  int rc = setup(slices, T, gn, gd, on, od, p);
+  int rc = setup(slices, T, gn, gd, on, od, p, null_model);
   if (rc) return rc;
   const int64_t N = p.n * T;
   std::vector<int32_t> lab(labels, labels + N);
@@ -560,9 +647,9 @@ int orc_modularity(const orc_csr* slices, int32_t T, const int32_t* labels, int6
 }
 
 int orc_move_key(const orc_csr* slices, int32_t T, const int32_t* labels, int64_t gn, int64_t gd, int64_t on,
-                 int64_t od, int64_t v, int64_t c, uint64_t out[2]) {
+                 int64_t od, int32_t null_model, int64_t v, int64_t c, uint64_t out[2]) {
   Problem p;
-  int rc = setup(slices, T, gn, gd, on, od, p);
+  int rc = setup(slices, T, gn, gd, on, od, p, null_model);
   if (rc) return rc;
   Level G = build_level0(slices, p);
   if (v < 0 || v >= G.N) return ORC_EINVAL;
@@ -583,9 +670,9 @@ int orc_move_key(const orc_csr* slices, int32_t T, const int32_t* labels, int64_
 }
 
 int orc_count_improving(const orc_csr* slices, int32_t T, const int32_t* labels, int64_t gn, int64_t gd, int64_t on,
-                        int64_t od, int64_t* count) {
+                        int64_t od, int32_t null_model, int64_t* count) {
   Problem p;
-  int rc = setup(slices, T, gn, gd, on, od, p);
+  int rc = setup(slices, T, gn, gd, on, od, p, null_model);
   if (rc) return rc;
   Level G = build_level0(slices, p);
   std::vector<int64_t> size(G.N, 0);
@@ -622,12 +709,12 @@ int orc_count_improving(const orc_csr* slices, int32_t T, const int32_t* labels,
 
 int orc_leiden(const orc_csr* slices, int32_t T, int64_t gn, int64_t gd, int64_t on, int64_t od, const orc_opts* o,
                const int32_t* init_labels, int32_t* labels_out, int64_t labels_cap, double* Q_out, orc_stats* st) {
-  Problem p;
-  int rc = setup(slices, T, gn, gd, on, od, p);
-  if (rc) return rc;
   orc_opts opt;
   orc_default_opts(&opt);
   if (o) opt = *o;
+  Problem p;
+  int rc = setup(slices, T, gn, gd, on, od, p, opt.null_model);
+  if (rc) return rc;
   if (opt.n_iterations < 1 || opt.K < 1 || opt.max_rounds < 1 || opt.max_levels < 1) return ORC_EINVAL;
   orc_stats local{};
   if (!st) st = &local;

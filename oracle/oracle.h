@@ -40,6 +40,14 @@ extern "C" {
 #define ORC_EINVAL (-1)
 #define ORC_EOVERFLOW (-3)
 
+/* Null models.  MULTISLICE: Q_MS's per-slice term gamma*k_is*k_js/2m_s.
+ * GLOBAL: plain modularity (Eq. modularity) of the supra-adjacency, coupling
+ * edges included in the strengths and in 2mu, one null term for the whole
+ * supra-graph (the model cuGraph's Leiden optimises when it is handed the
+ * supra-graph, Sec. 3.2). */
+#define ORC_NULL_MULTISLICE 0
+#define ORC_NULL_GLOBAL 1
+
 /* One snapshot: symmetric CSR, sorted columns, no self-loops, weights >= 1. */
 typedef struct {
   int64_t n;
@@ -64,6 +72,7 @@ typedef struct {
   int32_t stop_level;
   int32_t stop_stage;
   int32_t stop_rounds;
+  int32_t null_model;  /* ORC_NULL_MULTISLICE (default) or ORC_NULL_GLOBAL */
 } orc_opts;
 
 typedef struct {
@@ -91,16 +100,18 @@ int orc_leiden(const orc_csr* slices, int32_t T, int64_t gamma_num, int64_t gamm
                int64_t omega_num, int64_t omega_den, const orc_opts* o, const int32_t* init_labels,
                int32_t* labels_out, int64_t labels_cap, double* Q_out, orc_stats* st);
 
-/* Q_MS of a level-0 labelling (labels in [0, N)). */
+/* Q of a level-0 labelling (labels in [0, N)) under null_model: Q_MS, or the
+ * supra-graph's plain modularity. */
 int orc_modularity(const orc_csr* slices, int32_t T, const int32_t* labels, int64_t gamma_num,
-                   int64_t gamma_den, int64_t omega_num, int64_t omega_den, double* Q_out);
+                   int64_t gamma_den, int64_t omega_num, int64_t omega_den, int32_t null_model,
+                   double* Q_out);
 
 /* Exact integer key G(v, c) of the level-0 supra-node v for community c under
  * `labels` (c = -1 means an empty community).  Written as a signed 128-bit
  * integer in out[0] (low) / out[1] (high). */
 int orc_move_key(const orc_csr* slices, int32_t T, const int32_t* labels, int64_t gamma_num,
-                 int64_t gamma_den, int64_t omega_num, int64_t omega_den, int64_t v, int64_t c,
-                 uint64_t out[2]);
+                 int64_t gamma_den, int64_t omega_num, int64_t omega_den, int32_t null_model, int64_t v,
+                 int64_t c, uint64_t out[2]);
 
 /* Quantised null coefficients Lambda_s, as 128-bit (lo, hi) pairs, and 2m_s. */
 int orc_lambda(const orc_csr* slices, int32_t T, int64_t gamma_num, int64_t gamma_den,
@@ -110,7 +121,8 @@ int orc_lambda(const orc_csr* slices, int32_t T, int64_t gamma_num, int64_t gamm
  * community, or to an empty one when not alone) with a strictly larger key
  * than staying. */
 int orc_count_improving(const orc_csr* slices, int32_t T, const int32_t* labels, int64_t gamma_num,
-                        int64_t gamma_den, int64_t omega_num, int64_t omega_den, int64_t* count);
+                        int64_t gamma_den, int64_t omega_num, int64_t omega_den, int32_t null_model,
+                        int64_t* count);
 
 /* The counter-based hash used to draw vertex classes (SplitMix64 finaliser). */
 uint64_t orc_mix64(uint64_t x);

@@ -454,3 +454,241 @@ def test_hand_worked_steps(name):
                                  init=np.array(d["init"], np.int32) if "init" in d else None,
                                  stop_level=lvl, stop_stage=stage, stop_rounds=rounds)
     assert labels.tolist() == d["expect"]
+
+
+# ----------------------------------------------------------------- global null model
+# Plain modularity (Eq. modularity) of the supra-graph of Eq. supra-adjacency,
+# the objective cuGraph's Leiden optimises when it is handed the supra-graph
+# (Sec. 3.2).  Pinned to networkx on the supra-graph, to an exact-rational
+# dense statement of Eq. modularity, to Q_MS at T=1 (the two objectives agree
+# there), and through brute force, local optimality and connectivity.
+def supra_nx(snaps, omega):
+    nx = pytest.importorskip("networkx")
+    T, n = len(snaps), snaps[0].n
+    G = nx.Graph()
+    G.add_nodes_from(range(n * T))
+    for s, sn in enumerate(snaps):
+        for i in range(n):
+            for e in range(sn.indptr[i], sn.indptr[i + 1]):
+                j = int(sn.indices[e])
+                if i < j:
+                    G.add_edge(s * n + i, s * n + j, weight=float(sn.weights[e]))
+    w = omega[0] / omega[1]
+    if w > 0:
+        for s in range(T - 1):
+            for i in range(n):
+                G.add_edge(s * n + i, (s + 1) * n + i, weight=w)
+    return G
+
+
+def global_Q_exact(snaps, labels, gamma, omega):
+    """Eq. modularity on the dense supra-adjacency B (Eq. supra-adjacency),
+    exact rationals: (1/2mu) sum_ab [B_ab - gamma k_a k_b / 2mu] delta(c_a, c_b),
+    k_a the row sums of B (coupling included)."""
+    A = dense_slices(snaps)
+    T, n = len(A), A[0].shape[0]
+    N = n * T
+    w = Fraction(omega[0], omega[1])
+    g = gamma if isinstance(gamma, Fraction) else Fraction(gamma[0], gamma[1])
+    B = [[Fraction(0)] * N for _ in range(N)]
+    for s in range(T):
+        for i in range(n):
+            for j in range(n):
+                B[s * n + i][s * n + j] = Fraction(int(A[s][i, j]))
+            if s + 1 < T:
+                B[s * n + i][(s + 1) * n + i] = w
+                B[(s + 1) * n + i][s * n + i] = w
+    k = [sum(row) for row in B]
+    two_mu = sum(k)
+    if two_mu == 0:
+        return Fraction(0)
+    tot = Fraction(0)
+    for a in range(N):
+        for b in range(N):
+            if labels[a] == labels[b]:
+                tot += B[a][b] - g * k[a] * k[b] / two_mu
+    return tot / two_mu
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_global_Q_equals_networkx_on_supra_graph(seed):
+    nx = pytest.importorskip("networkx")
+    rng = np.random.default_rng(1200 + seed)
+    T = int(rng.integers(1, 5))
+    n = int(rng.integers(3, 30))
+    snaps = synth.random_temporal(n, T, p=0.3, w_max=6, seed=seed, p_empty=0.1)
+    gamma = rand_rational(rng)
+    omega = rand_rational(rng, lo_num=0)
+    G = supra_nx(snaps, omega)
+    for trial in range(4):
+        labels = rng.integers(0, max(1, (n * T) // (trial + 1)), size=n * T).astype(np.int32)
+        q = oracle.modularity(snaps, labels, gamma, omega, null="global")
+        if G.size(weight="weight") == 0:
+            assert q == 0.0
+            continue
+        want = nx.community.modularity(G, communities_of(labels), weight="weight",
+                                       resolution=gamma[0] / gamma[1])
+        assert q == pytest.approx(want, rel=1e-12, abs=1e-14)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_global_Q_exact_rational(seed):
+    rng = np.random.default_rng(1300 + seed)
+    T = int(rng.integers(1, 4))
+    n = int(rng.integers(2, 6))
+    snaps = synth.random_temporal(n, T, p=0.5, w_max=5, seed=seed)
+    gamma, omega = rand_rational(rng), rand_rational(rng, lo_num=0)
+    for _ in range(3):
+        labels = rng.integers(0, n * T, size=n * T).astype(np.int32)
+        q = oracle.modularity(snaps, labels, gamma, omega, null="global")
+        assert q == pytest.approx(float(global_Q_exact(snaps, labels, gamma, omega)), rel=1e-12, abs=1e-15)
+
+
+def test_global_equals_multislice_at_T1_and_differs_with_coupling():
+    rng = np.random.default_rng(7)
+    one = synth.random_temporal(25, 1, p=0.2, w_max=4, seed=3)
+    many = synth.random_temporal(25, 3, p=0.2, w_max=4, seed=3)
+    differs = 0
+    for _ in range(5):
+        lab1 = rng.integers(0, 8, size=25).astype(np.int32)
+        for gamma in [(1, 1), (3, 2)]:
+            a = oracle.modularity(one, lab1, gamma, (1, 1), null="global")
+            b = oracle.modularity(one, lab1, gamma, (1, 1))
+            assert a == pytest.approx(b, rel=1e-12, abs=1e-15)
+        lab3 = rng.integers(0, 8, size=75).astype(np.int32)
+        differs += oracle.modularity(many, lab3, (1, 1), (1, 1), null="global") != \
+            pytest.approx(oracle.modularity(many, lab3, (1, 1), (1, 1)), rel=1e-9)
+    assert differs == 5
+
+
+def test_global_closed_forms():
+    """Singletons: Q = -gamma sum_a k_a^2 / (2mu)^2.  One community holding
+    everything: Q = 1 - gamma."""
+    snaps = synth.random_temporal(9, 3, p=0.4, w_max=3, seed=11)
+    T, n = 3, 9
+    omega, gamma = (2, 3), (5, 4)
+    k = []
+    for s, sn in enumerate(snaps):
+        for i in range(n):
+            c = (s > 0) + (s < T - 1)
+            k.append(Fraction(int(sn.weights[sn.indptr[i]:sn.indptr[i + 1]].sum())) + Fraction(2, 3) * c)
+    two_mu = sum(k)
+    g = Fraction(5, 4)
+    want = -g * sum(x * x for x in k) / (two_mu * two_mu)
+    q = oracle.modularity(snaps, np.arange(n * T, dtype=np.int32), gamma, omega, null="global")
+    assert q == pytest.approx(float(want), rel=1e-13)
+    q1 = oracle.modularity(snaps, np.zeros(n * T, np.int32), gamma, omega, null="global")
+    assert q1 == pytest.approx(1 - 5 / 4, rel=1e-13)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_global_move_key_is_scaled_delta_Q(seed):
+    """(G(v,c) - G(v,a)) * 2 / (2mu * od * 2^64) equals the exact change of
+    the supra-graph's modularity under the quantised resolution
+    gamma' = Lambda' 2M' / 2^64, Lambda' = floor(gamma 2^64 / 2M'),
+    2M' = od * 2mu (the integer total weight of the supra-graph)."""
+    rng = np.random.default_rng(1400 + seed)
+    T = int(rng.integers(1, 4))
+    n = int(rng.integers(2, 5))
+    snaps = synth.random_temporal(n, T, p=0.6, w_max=5, seed=seed, p_empty=0.15)
+    gamma = rand_rational(rng)
+    omega = rand_rational(rng, lo_num=0)
+    N = n * T
+    two_mu = Fraction(sum(int(sn.weights.sum()) for sn in snaps)) + 2 * Fraction(omega[0], omega[1]) * n * (T - 1)
+    if two_mu == 0:
+        return
+    twoM = int(two_mu * omega[1])
+    lam = (gamma[0] << 64) // (gamma[1] * twoM)
+    gq = Fraction(lam * twoM, 1 << 64)
+    labels = rng.integers(0, max(2, N // 2), size=N).astype(np.int32)
+    base = global_Q_exact(snaps, labels, gq, omega)
+    for _ in range(6):
+        v = int(rng.integers(0, N))
+        a = int(labels[v])
+        choices = [int(x) for x in set(labels.tolist())] + [-1]
+        c = choices[int(rng.integers(0, len(choices)))]
+        new = labels.copy()
+        new[v] = c if c >= 0 else N + 7
+        after = global_Q_exact(snaps, new, gq, omega)
+        Gc = oracle.move_key(snaps, labels, v, c, gamma, omega, null="global")
+        Ga = oracle.move_key(snaps, labels, v, a, gamma, omega, null="global")
+        assert Fraction(2 * (Gc - Ga), 1) / (two_mu * omega[1] * (1 << 64)) == after - base
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_global_bruteforce_bound_and_local_optimum(seed):
+    rng = np.random.default_rng(1500 + seed)
+    T = int(rng.integers(1, 3))
+    n = int(rng.integers(3, 5 if T == 2 else 9))
+    snaps = synth.random_temporal(n, T, p=0.5, w_max=3, seed=seed)
+    gamma, omega = (1, 1), (1, 2)
+    N = n * T
+    best = -1.0
+    for part in set_partitions(N):
+        best = max(best, oracle.modularity(snaps, np.array(part, np.int32), gamma, omega, null="global"))
+    labels, Q, st = oracle.leiden(snaps, gamma, omega, n_iterations=20, null="global")
+    assert Q <= best + 1e-12
+    assert Q == pytest.approx(oracle.modularity(snaps, labels, gamma, omega, null="global"), rel=1e-15)
+    if st["last_level0_moves"] == 0:
+        assert oracle.count_improving(snaps, labels, gamma, omega, null="global") == 0
+
+
+def test_global_converged_invariants():
+    hits = 0
+    for seed in range(8):
+        rng = np.random.default_rng(seed)
+        T = int(rng.integers(1, 5))
+        snaps, _ = synth.planted_partition_temporal(int(rng.integers(20, 80)), T, n_blocks=3, p_in=0.25,
+                                                    p_out=0.04, switch_frac=0.1, w_max=4, seed=seed)
+        omega = [(1, 1), (1, 10), (10, 1), (0, 1)][seed % 4]
+        labels, Q, st = oracle.leiden(snaps, (1, 1), omega, n_iterations=30, null="global")
+        assert Q == pytest.approx(oracle.modularity(snaps, labels, (1, 1), omega, null="global"), rel=1e-15)
+        if st["last_level0_moves"] == 0:
+            assert oracle.count_improving(snaps, labels, (1, 1), omega, null="global") == 0
+            hits += 1
+        if st["stop_reason"] == 1:
+            assert components_ok(snaps, labels, omega)
+    assert hits >= 6
+
+
+def test_global_disjoint_cliques():
+    """Every slice's cliques are recovered, and the result scores at least as
+    well as both natural candidates: one community per clique across all
+    slices, and one per clique and slice.  (Unlike Q_MS at omega=1, the single
+    null term of the supra-graph may prefer the second: the penalty grows with
+    the square of a community's total strength.)"""
+    nx = pytest.importorskip("networkx")
+    snaps = synth.cliques_temporal([5, 6, 7, 4], T=3, w=2)
+    labels, Q, _ = oracle.leiden(snaps, (1, 1), (1, 1), null="global")
+    n = 22
+    want = np.repeat(np.arange(4), [5, 6, 7, 4])
+    for s in range(3):
+        got = labels[s * n:(s + 1) * n]
+        assert len(set(zip(got.tolist(), want.tolist()))) == 4
+    tubes = np.tile(want, 3).astype(np.int32)
+    per_slice = np.concatenate([want + 4 * s for s in range(3)]).astype(np.int32)
+    G = supra_nx(snaps, (1, 1))
+    for cand in (tubes, per_slice):
+        qc = nx.community.modularity(G, communities_of(cand), weight="weight")
+        assert Q >= qc - 1e-12
+
+
+def test_global_overflow_guard_counts_coupling():
+    """The global null term's strengths include coupling, so gamma * 2M' must
+    stay below 2^61 where the multislice bound (gamma * od * sum 2m_s) holds."""
+    sn = synth.random_temporal(6, 1, p=0.5, seed=1)[0]
+    sn = synth.Snapshot(sn.indptr, sn.indices, np.full(sn.nnz, 2 ** 30, np.int32))
+    snaps = [sn] * 4
+    on = 2 ** 31
+    sum2m = 4 * sn.nnz * 2 ** 30
+    twoM = sum2m + 2 * on * 6 * 3
+    g = -(-(2 ** 61) // twoM)  # smallest integer gamma with gamma * 2M' >= 2^61
+    assert g * sum2m < 2 ** 61 and twoM < 2 ** 61 and g <= 2 ** 31
+    oracle.leiden(snaps, (g, 1), (on, 1), n_iterations=1, max_rounds=1, max_levels=1)
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.leiden(snaps, (g, 1), (on, 1), null="global")
+    assert e.value.code == oracle.EOVERFLOW
+    oracle.leiden(snaps, (g - 1, 1), (on, 1), null="global", n_iterations=1, max_rounds=1, max_levels=1)
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.leiden(snaps, null=2)
+    assert e.value.code == oracle.EINVAL
