@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving", "large"])
+    ap.add_argument("--null", default="multislice", choices=["multislice", "global"],
+                    help="plain workload: Q_MS (default) or the supra-graph's plain modularity")
     ap.add_argument("--requests", type=int, default=4, help="serving workload: timed snapshots per graph")
     ap.add_argument("--slots", type=int, default=2, help="serving workload: server workers")
     ap.add_argument("--scale", type=float, default=1.0, help="batched workload: node-count scale of every graph")
@@ -145,12 +147,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline():
+def workload(args):
+    """The plain workload's config; the null model is named when it is not Q_MS."""
+    if args.null == "multislice":
+        return dict(WORKLOAD)
+    return {**WORKLOAD, "workload": WORKLOAD["workload"] + ", global null model (plain modularity of the supra-graph)",
+            "null_model": args.null}
+
+
+def cpu_baseline(null="multislice"):
     import oracle
     from paper_2608_03695_gb300 import synth
     snaps = synth.recipe_graph("powerlaw_t16_n100k", scale_n=ORACLE_SAMPLE_N)
     t = time.perf_counter()
-    _, _, st = oracle.leiden(snaps)
+    _, _, st = oracle.leiden(snaps, null=null)
     el = time.perf_counter() - t
     return {"value": st["lm_edges"] / el, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"one oracle solve of the same recipe at n={ORACLE_SAMPLE_N}, T=16 "
@@ -166,11 +176,11 @@ def run_reference(args):
     oracle.build()
     snaps = synth.recipe_graph("powerlaw_t16_n100k", scale_n=ORACLE_SAMPLE_N)
     for _ in range(args.warmup):
-        oracle.leiden(snaps, n_iterations=1, max_rounds=2)  # short warm-up (page-in, caches)
+        oracle.leiden(snaps, n_iterations=1, max_rounds=2, null=args.null)  # short warm-up (page-in, caches)
     edges, secs = 0, 0.0
     for _ in range(args.steps):
         t = time.perf_counter()
-        _, _, st = oracle.leiden(snaps)
+        _, _, st = oracle.leiden(snaps, null=args.null)
         secs += time.perf_counter() - t
         edges += st["lm_edges"]
     v = edges / secs
@@ -178,7 +188,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic",
-            "config": {**WORKLOAD, "n": ORACLE_SAMPLE_N, "supra_nodes": ORACLE_SAMPLE_N * 16,
+            "config": {**workload(args), "n": ORACLE_SAMPLE_N, "supra_nodes": ORACLE_SAMPLE_N * 16,
                        "note": "bounded sample of the same recipe (n scaled) for the single-thread CPU oracle"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} oracle solves at n={ORACLE_SAMPLE_N}, T=16"},
@@ -555,7 +565,7 @@ def main():
     stream = torch.cuda.Stream()
     if args.profile_run:
         with pkg.mslice_build(snaps) as h:
-            _, Q, st = h.mslice_leiden()
+            _, Q, st = h.mslice_leiden(null=args.null)
         print(json.dumps({"profile_run": True, "Q": Q, "kernel_launches": st["kernel_launches"],
                           "ms_total": st["ms_total"]}), flush=True)
         return
@@ -572,7 +582,7 @@ def main():
 
     def step_device(profile=False):
         h = pkg.mslice_build(dsnaps, device_ptrs=True, stream=stream.cuda_stream)
-        _, Q, st = h.mslice_leiden(out=dlabels, profile=profile)
+        _, Q, st = h.mslice_leiden(out=dlabels, profile=profile, null=args.null)
         launches = h.kernel_launches
         h.close()
         return st, launches, Q
@@ -606,7 +616,7 @@ def main():
     stp, _, _ = step_device(profile=True)
     peak, peak_kind = measured_peak()
     achieved = stp["decide_bytes"] / (stp["ms_decide"] / 1e3) / 1e9 if stp["ms_decide"] > 0 else 0.0
-    traffic = decide_traffic()
+    traffic = decide_traffic() if args.null == "multislice" else None  # counters taken under Q_MS only
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (traffic if traffic is None else traffic), "peak_source": peak_kind,
                 "kernel": "local-moving decision, level-0 sub-round (all degree tiers)",
@@ -623,7 +633,7 @@ def main():
 
         def step_e2e():
             h = pkg.mslice_build(hsnaps, host_tensors=True, stream=stream.cuda_stream)
-            _, Q, st = h.mslice_leiden(out=hlabels)
+            _, Q, st = h.mslice_leiden(out=hlabels, null=args.null)
             h.close()
             return st
 
@@ -643,14 +653,14 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {**WORKLOAD, "parallelism": f"replicas{world}" if world > 1 else "single",
+            "config": {**workload(args), "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "inputs larger than L2 (level-0 supra-CSR 280 MB vs 129 MB L2)"},
             "Q": Qs[-1] if Qs else None, "gpu_launches": int(sum_over_ranks(launches)),
             "local_move_only": {"value": stp["lm_edges"] / (stp["ms_local_move"] / 1e3), "unit": UNIT,
                                 "note": "same edges over local-moving device time only (profiled step)"},
             "roofline": roofline, "clocks": clk, "e2e": e2e}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(args.null)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -60,6 +60,17 @@ extern "C" {
  * tiers by timing the candidates on round 0 of level 0 (decisions only, so
  * the result is unchanged); the cuts used are returned in mslice_stats. */
 #define MSLICE_AUTOTUNE 4
+/* leiden / batch run / modularity_ex / server: optimise and report the plain
+ * modularity (Eq. modularity) of the supra-graph of Eq. supra-adjacency
+ * instead of Q_MS -- the objective cuGraph's Leiden optimises when it is
+ * handed the supra-graph (Sec. 3.2).  Coupling edges then count in the
+ * strengths (k'_v = k_v + omega * coupling edges of v) and a single null term
+ * gamma k'_u k'_v / 2mu covers the whole supra-graph (of one instance).  The
+ * resolution is quantised once: Lambda' = floor(gamma 2^64 / 2M'), 2M' =
+ * omega_den * 2mu, and the exact key's null scale is 1 instead of omega_den.
+ * Bound: gamma * 2M' < 2^61 (EOVERFLOW otherwise).  Not available to
+ * mslice_modularity_noalloc. */
+#define MSLICE_NULL_GLOBAL 8
 
 typedef struct {
   int64_t n;              /* nodes of the snapshot (equal for all snapshots) */
@@ -83,7 +94,8 @@ typedef struct {
   uint64_t seed;        /* seed of the counter-based class hash; default 0 */
   int64_t gamma_num, gamma_den; /* resolution; default 1/1 */
   int64_t omega_num, omega_den; /* coupling; default 1/1 (overrides the build value) */
-  int32_t flags;        /* MSLICE_DEVICE_PTRS: init/labels_out are device pointers */
+  int32_t flags;        /* MSLICE_DEVICE_PTRS: init/labels_out are device pointers;
+                           MSLICE_PROFILE, MSLICE_AUTOTUNE, MSLICE_NULL_GLOBAL: above */
   /* Step-level debugging (the library's own tests compare it stage by stage):
    * when stop_level >= 0 the first iteration stops at that level after
    * stop_stage (1 local moving, 2 refinement, 3 aggregation) and labels_out
@@ -167,7 +179,8 @@ int mslice_leiden_ex(mslice_handle h, const mslice_opts* o, const int32_t* init_
 int mslice_modularity(mslice_handle h, const int32_t* labels, int64_t gamma_num, int64_t gamma_den,
                       int64_t omega_num, int64_t omega_den, double* Q_out);
 
-/* As mslice_modularity; flags = MSLICE_DEVICE_PTRS for a device pointer. */
+/* As mslice_modularity; flags = MSLICE_DEVICE_PTRS for a device pointer,
+ * MSLICE_NULL_GLOBAL for the supra-graph's plain modularity instead of Q_MS. */
 int mslice_modularity_ex(mslice_handle h, const int32_t* labels, int64_t gamma_num, int64_t gamma_den,
                          int64_t omega_num, int64_t omega_den, int32_t flags, double* Q_out);
 
@@ -232,14 +245,17 @@ int mslice_batch_add(mslice_batch b, mslice_handle g, int64_t gamma_num, int64_t
                      int64_t omega_den, const int32_t* init_labels, int32_t* index_out);
 
 /* Solves every instance.  o: schedule options shared by all instances
- * (n_iterations, K, max_rounds, max_levels, seed; MSLICE_PROFILE honoured);
- * its gamma/omega/init fields are not used and stop_level must be -1.
- * st (nullable): counters summed over the batch and phase times of the
- * pass.  Errors: EINVAL (empty batch, bad options), ENOMEM, ECUDA. */
+ * (n_iterations, K, max_rounds, max_levels, seed; MSLICE_PROFILE,
+ * MSLICE_AUTOTUNE and MSLICE_NULL_GLOBAL honoured, the last for every
+ * instance); its gamma/omega/init fields are not used and stop_level must be
+ * -1.  st (nullable): counters summed over the batch and phase times of the
+ * pass.  Errors: EINVAL (empty batch, bad options), EOVERFLOW (an instance
+ * outside the global model's bound), ENOMEM, ECUDA. */
 int mslice_batch_run(mslice_batch b, const mslice_opts* o, mslice_stats* st);
 
 /* Results of the last run.  i in [0, B): labels_out gets instance i's N_i
- * canonical labels (numbered from 0 within the instance) and *Q_out its Q_MS;
+ * canonical labels (numbered from 0 within the instance) and *Q_out its Q_MS
+ * (its supra-graph modularity when run with MSLICE_NULL_GLOBAL);
  * i = -1: labels_out gets all instances' labels one after another (sum N_i
  * entries, instance i at offsets[i] of mslice_batch_info) and Q_out B values.
  * Errors: EINVAL (bad index, not run since the last add/clear). */
@@ -296,8 +312,9 @@ typedef struct {
   int64_t hbm_budget;  /* bytes of device memory admitted work may use; 0 (default): 80% of the free
                           memory when the server is created */
   int64_t gamma_num, gamma_den, omega_num, omega_den; /* default 1/1, 1/1 */
-  mslice_opts solve;   /* schedule (n_iterations, K, max_rounds, max_levels, seed); defaults as
-                          mslice_default_opts; gamma/omega/flags/stop fields are not used */
+  mslice_opts solve;   /* schedule (n_iterations, K, max_rounds, max_levels, seed, tier_cuts) and
+                          the MSLICE_NULL_GLOBAL flag; defaults as mslice_default_opts;
+                          gamma/omega/stop fields and the other flags are not used */
 } mslice_server_opts;
 
 /* Per-request record, times in seconds since the server was created. */
@@ -305,7 +322,7 @@ typedef struct {
   int32_t status;       /* MSLICE_OK or the request's error code */
   int32_t slices;       /* slices in the window that was solved */
   int64_t N;            /* supra-nodes of that window (labels written) */
-  double Q;             /* Q_MS of the result */
+  double Q;             /* Q_MS of the result (the supra-graph's modularity under MSLICE_NULL_GLOBAL) */
   double t_submit, t_admit, t_done;
   int32_t batch_size;   /* requests solved together with it (itself included) */
   int32_t slot;         /* worker that solved it */

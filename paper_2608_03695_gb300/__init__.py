@@ -33,6 +33,8 @@ MSLICE_OK, MSLICE_EINVAL, MSLICE_ENOMEM, MSLICE_EOVERFLOW, MSLICE_ECUDA, MSLICE_
 MSLICE_DEVICE_PTRS = 1
 MSLICE_PROFILE = 2
 MSLICE_AUTOTUNE = 4
+MSLICE_NULL_GLOBAL = 8
+_NULLS = {"multislice": 0, "global": MSLICE_NULL_GLOBAL}
 MSLICE_ORDINAL = 0
 
 # every symbol include/mslice.h declares
@@ -206,10 +208,11 @@ class Handle:
 
     def mslice_leiden(self, gamma=(1, 1), omega=(1, 1), max_levels=32, seed=0, n_iterations=2, K=4,
                       max_rounds=100, init=None, stop_level=-1, stop_stage=0, stop_rounds=0, out=None,
-                      profile=False, tier_cuts=None, autotune=False):
+                      profile=False, tier_cuts=None, autotune=False, null="multislice"):
         """Returns (labels, Q, stats).  With ``out`` a device tensor (int32[N])
         the labels stay on the device (MSLICE_DEVICE_PTRS); ``init`` may then
-        be a device tensor as well."""
+        be a device tensor as well.  ``null="global"`` optimises the plain
+        modularity of the supra-graph instead of Q_MS (MSLICE_NULL_GLOBAL)."""
         o = default_opts()
         o.gamma_num, o.gamma_den = gamma
         o.omega_num, o.omega_den = omega
@@ -220,6 +223,7 @@ class Handle:
             o.flags |= MSLICE_PROFILE
         if autotune:
             o.flags |= MSLICE_AUTOTUNE
+        o.flags |= _NULLS[null]
         if tier_cuts is not None:
             o.tier_cuts[:] = list(tier_cuts)
         if dev:
@@ -237,12 +241,13 @@ class Handle:
             return labels, Q.value, stats
         return labels[: st.out_n].copy(), Q.value, stats
 
-    def mslice_modularity(self, labels, gamma=(1, 1), omega=(1, 1)):
+    def mslice_modularity(self, labels, gamma=(1, 1), omega=(1, 1), null="multislice"):
         dev = hasattr(labels, "is_cuda") and labels.is_cuda
         lab = labels if dev else np.ascontiguousarray(labels, dtype=np.int32)
         Q = C.c_double(0.0)
-        _check(lib().mslice_modularity_ex(self._h, _ptr(lab), gamma[0], gamma[1], omega[0], omega[1],
-                                          MSLICE_DEVICE_PTRS if dev else 0, C.byref(Q)), "mslice_modularity_ex")
+        flags = (MSLICE_DEVICE_PTRS if dev else 0) | _NULLS[null]
+        _check(lib().mslice_modularity_ex(self._h, _ptr(lab), gamma[0], gamma[1], omega[0], omega[1], flags,
+                                          C.byref(Q)), "mslice_modularity_ex")
         return Q.value
 
     # short aliases
@@ -292,13 +297,14 @@ class Batch:
         return idx.value
 
     def mslice_batch_run(self, n_iterations=2, K=4, max_rounds=100, max_levels=32, seed=0, profile=False,
-                         tier_cuts=None, autotune=False) -> dict:
+                         tier_cuts=None, autotune=False, null="multislice") -> dict:
         o = default_opts()
         o.n_iterations, o.K, o.max_rounds, o.max_levels, o.seed = n_iterations, K, max_rounds, max_levels, seed
         if profile:
             o.flags |= MSLICE_PROFILE
         if autotune:
             o.flags |= MSLICE_AUTOTUNE
+        o.flags |= _NULLS[null]
         if tier_cuts is not None:
             o.tier_cuts[:] = list(tier_cuts)
         st = Stats()
@@ -348,7 +354,8 @@ class Server:
     :meth:`Handle.mslice_leiden` on the window with those initial labels."""
 
     def __init__(self, window=8, n_slots=2, max_batch=64, hbm_budget=0, gamma=(1, 1), omega=(1, 1),
-                 n_iterations=2, K=4, max_rounds=100, max_levels=32, seed=0, max_batch_nodes=None):
+                 n_iterations=2, K=4, max_rounds=100, max_levels=32, seed=0, max_batch_nodes=None,
+                 null="multislice"):
         o = ServerOpts()
         lib().mslice_server_default_opts(C.byref(o))
         o.window, o.n_slots, o.max_batch, o.hbm_budget = window, n_slots, max_batch, hbm_budget
@@ -358,6 +365,7 @@ class Server:
         o.omega_num, o.omega_den = omega
         o.solve.n_iterations, o.solve.K, o.solve.max_rounds = n_iterations, K, max_rounds
         o.solve.max_levels, o.solve.seed = max_levels, seed
+        o.solve.flags = _NULLS[null]
         s = C.c_void_p()
         _check(lib().mslice_server_create(C.byref(o), C.byref(s)), "mslice_server_create")
         self._s = s

@@ -590,6 +590,7 @@ bool aggregate(Solver& S, const Level& L, const int32_t* P, Level& next, const s
   next.d.is0 = 0;
   next.d.on = L.d.on;
   next.d.od = L.d.od;
+  next.d.global_null = L.d.global_null;
   next.d.on_i = L.d.on_i;
   next.d.od_i = L.d.od_i;
   next.d.chk = L.d.chk;

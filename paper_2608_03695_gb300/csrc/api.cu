@@ -345,6 +345,7 @@ void run_solve(Ctx& c, const SupraGraph& G, const std::vector<InstParams>& jobs,
   p.seed = opt.seed;
   p.cuts = cuts_of(opt);
   p.autotune = (opt.flags & MSLICE_AUTOTUNE) != 0;
+  p.global_null = (opt.flags & MSLICE_NULL_GLOBAL) != 0;
   run_leiden(c, G, jobs, p, opt.stop_level, opt.stop_stage, opt.stop_rounds, init, out, S, ro);
   std::memset(&stats, 0, sizeof(stats));
   stats.iterations = (int32_t)ro.iterations;
@@ -530,7 +531,8 @@ int mslice_leiden_ex(mslice_handle h, const mslice_opts* o, const int32_t* init_
     if (!labels_out && h->G.N > 0) fail(MSLICE_EINVAL, "null labels_out");
     const bool dev = (opt.flags & MSLICE_DEVICE_PTRS) != 0;
     const SupraGraph& G = h->G;
-    check_bounds(G.n, G.T, G.two_m_host.data(), opt.gamma_num, opt.gamma_den, opt.omega_num, opt.omega_den);
+    check_bounds(G.n, G.T, G.two_m_host.data(), opt.gamma_num, opt.gamma_den, opt.omega_num, opt.omega_den,
+                 (opt.flags & MSLICE_NULL_GLOBAL) != 0);
     const int64_t N0 = G.N;
     Ctx c = h->ctx();
     const int32_t* init = nullptr;
@@ -581,13 +583,16 @@ int mslice_modularity_ex(mslice_handle h, const int32_t* labels, int64_t gamma_n
     if (!rational_ok(omega_num, omega_den, true)) fail(MSLICE_EINVAL, "omega must be a rational >= 0");
     const SupraGraph& G = h->G;
     if (!labels && G.N > 0) fail(MSLICE_EINVAL, "null labels");
-    check_bounds(G.n, G.T, G.two_m_host.data(), gamma_num, gamma_den, omega_num, omega_den);
+    const bool global = (flags & MSLICE_NULL_GLOBAL) != 0;
+    check_bounds(G.n, G.T, G.two_m_host.data(), gamma_num, gamma_den, omega_num, omega_den, global);
     Ctx c = h->ctx();
     Solver S;
     S.c = &c;
     S.G0 = &G;
     S.N0 = G.N;
+    S.p.global_null = global;
     set_instances(c, S, {InstParams{gamma_num, gamma_den, omega_num, omega_den}});
+    setup_null_model(S);
     const int64_t N = G.N > 0 ? G.N : 1;
     S.sig_used = h->ws.get<ull>("m_used", 1);
     int32_t* lab = h->ws.get<int32_t>("m_lab", N);
@@ -677,6 +682,12 @@ int mslice_batch_run(mslice_batch b, const mslice_opts* o, mslice_stats* st) {
     if (o) opt = *o;
     check_opts(opt);
     if (opt.stop_level >= 0) fail(MSLICE_EINVAL, "debug stops apply to single solves only");
+    if (opt.flags & MSLICE_NULL_GLOBAL)
+      for (size_t i = 0; i < b->graphs.size(); ++i) {
+        const SupraGraph& Gi = b->graphs[i]->G;
+        const InstParams& j = b->jobs[i];
+        check_bounds(Gi.n, Gi.T, Gi.two_m_host.data(), j.gn, j.gd, j.on, j.od, true);
+      }
     Ctx c = b->ctx();
     std::vector<uint64_t> serials;
     for (mslice_graph* g : b->graphs) serials.push_back(g->serial);
@@ -697,7 +708,7 @@ int mslice_batch_run(mslice_batch b, const mslice_opts* o, mslice_stats* st) {
       check_cuda(cudaMemcpyAsync(init, b->init.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream), "copy");
     }
     int32_t* out = b->ws.get<int32_t>("b_out", N > 0 ? N : 1);
-    opt.flags &= MSLICE_PROFILE | MSLICE_AUTOTUNE;
+    opt.flags &= MSLICE_PROFILE | MSLICE_AUTOTUNE | MSLICE_NULL_GLOBAL;
     mslice_stats stats;
     RunOut ro;
     Solver S;

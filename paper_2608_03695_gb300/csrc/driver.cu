@@ -162,15 +162,76 @@ void check_label_ranges(Ctx& c, const SupraGraph& G, const int32_t* d) {
   check_status(c, "labels");
 }
 
-void check_bounds(int64_t n, int32_t T, const int64_t* two_m, long long gn, long long gd, long long on, long long od) {
+void check_bounds(int64_t n, int32_t T, const int64_t* two_m, long long gn, long long gd, long long on, long long od,
+                  bool global_null) {
   u128 sum2m = 0;
   for (int32_t s = 0; s < T; ++s) sum2m += (u128)(ull)two_m[s];
   const u128 ncpl = (u128)(ull)n * (u128)(ull)(T > 0 ? T - 1 : 0);
   const u128 lim = (u128)1 << 61;
-  if ((u128)(ull)od * sum2m + 2 * (u128)(ull)on * ncpl >= lim)
-    fail(MSLICE_EOVERFLOW, "omega_den*sum(2m_s) + 2*omega_num*n*(T-1) must stay below 2^61");
-  if ((u128)(ull)gn * (u128)(ull)od * sum2m >= lim * (u128)(ull)gd)
+  const u128 twoM = (u128)(ull)od * sum2m + 2 * (u128)(ull)on * ncpl;
+  if (twoM >= lim) fail(MSLICE_EOVERFLOW, "omega_den*sum(2m_s) + 2*omega_num*n*(T-1) must stay below 2^61");
+  if (global_null) {
+    if ((u128)(ull)gn * twoM >= lim * (u128)(ull)gd)
+      fail(MSLICE_EOVERFLOW, "global null model: gamma*(omega_den*sum(2m_s) + 2*omega_num*n*(T-1)) must stay below 2^61");
+  } else if ((u128)(ull)gn * (u128)(ull)od * sum2m >= lim * (u128)(ull)gd) {
     fail(MSLICE_EOVERFLOW, "gamma*omega_den*sum(2m_s) must stay below 2^61");
+  }
+}
+
+namespace {
+
+// k'_v = od*k_v + on*c_v, c_v = coupling edges of v (to the same node in the
+// previous and next snapshot of its instance).  Batches: slice0 gives the
+// node's global snapshot and slice_inst the instance of every snapshot.
+__global__ void k_null_strength(const int64_t* k, int64_t N, int64_t n, int32_t T, const int32_t* slice0,
+                                const int32_t* slice_inst, const int32_t* inst0, const long long* on,
+                                const long long* od, int64_t* kn) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
+    int32_t i = 0, c = 0;
+    if (slice0) {
+      i = inst0[v];
+      const int32_t s = slice0[v];
+      c = (s > 0 && slice_inst[s - 1] == i ? 1 : 0) + (s + 1 < T && slice_inst[s + 1] == i ? 1 : 0);
+    } else {
+      const int64_t s = v / n;
+      c = (s > 0 ? 1 : 0) + (s < T - 1 ? 1 : 0);
+    }
+    kn[v] = od[i] * k[v] + on[i] * c;
+  }
+}
+
+}  // namespace
+
+void setup_null_model(Solver& S) {
+  Ctx& c = *S.c;
+  const SupraGraph& G = *S.G0;
+  if (!S.p.global_null) {
+    S.Tn = G.T > 0 ? G.T : 1;
+    S.lam = c.ws->get<u128>("lam", S.Tn);
+    if (G.T > 0) compute_lambda(c, G, S.gn_d, S.gd_d, S.lam);
+    return;
+  }
+  // one null slice per instance, 2M' = od*sum 2m_s + 2*on*n*(T-1) in units of 1/od
+  S.Tn = G.B;
+  std::vector<u128> lam(G.B);
+  for (int32_t i = 0; i < G.B; ++i) {
+    const InstInfo& in = G.inst[i];
+    long long sum2m = 0;
+    for (int32_t s = in.soff; s < in.soff + in.T; ++s) sum2m += G.two_m_host[s];
+    const long long twoM = S.od_h[i] * sum2m + 2 * S.on_h[i] * in.n * (long long)(in.T > 0 ? in.T - 1 : 0);
+    lam[i] = twoM > 0 ? (((u128)(ull)S.gn_h[i]) << P_BITS) / ((u128)(ull)S.gd_h[i] * (u128)(ull)twoM) : (u128)0;
+  }
+  S.lam = c.ws->get<u128>("lam", S.Tn);
+  check_cuda(cudaMemcpyAsync(S.lam, lam.data(), G.B * sizeof(u128), cudaMemcpyHostToDevice, c.stream), "copy");
+  S.kn = c.ws->get<int64_t>("k_null", S.N0 > 0 ? S.N0 : 1);
+  if (G.N > 0) {
+    const bool batch = G.B > 1;
+    launch(c, k_null_strength, dim3(grid_for(G.N, 256) < 4096 ? grid_for(G.N, 256) : 4096), dim3(256), 0,
+           (const int64_t*)G.k, G.N, G.n > 0 ? G.n : 1, G.T, (const int32_t*)(batch ? G.slice0 : nullptr),
+           (const int32_t*)(batch ? G.slice_inst : nullptr), (const int32_t*)(batch ? G.inst0 : nullptr),
+           (const long long*)S.on_d, (const long long*)S.od_d, S.kn);
+  }
+  sync(c);  // lam is pageable host memory
 }
 
 void set_instances(Ctx& c, Solver& S, const std::vector<InstParams>& jobs) {
@@ -216,8 +277,7 @@ void run_leiden(Ctx& c, const SupraGraph& G, const std::vector<InstParams>& jobs
   S.inst_active = c.ws->get<int32_t>("s_active", B);
   int32_t* iter_active = c.ws->get<int32_t>("s_iter_active", B);
   fill_i32(c, iter_active, 1, B);
-  S.lam = c.ws->get<u128>("lam", G.T > 0 ? G.T : 1);
-  if (G.T > 0) compute_lambda(c, G, S.gn_d, S.gd_d, S.lam);
+  setup_null_model(S);
 
   int32_t* labA = c.ws->get<int32_t>("lab_A", N0);
   int32_t* labB = c.ws->get<int32_t>("lab_B", N0);

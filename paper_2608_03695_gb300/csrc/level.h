@@ -26,6 +26,12 @@ struct LevelDev {
   const int32_t* sidx = nullptr;
   const long long* sval = nullptr;
   long long on = 1, od = 1;     // single instance
+  // Null model: 0 = per-snapshot term of Q_MS; 1 = one term over the whole
+  // supra-graph (plain modularity of the supra-graph).  Under 1 the
+  // "snapshot" of a strength entry is the instance (one null slice each),
+  // strengths are k' = od*k + on*(coupling edges) and the key's null scale is
+  // 1 instead of od.
+  int32_t global_null = 0;
   // batches (all nullptr for a single instance)
   const int32_t* slice0 = nullptr;    // level 0: global snapshot of every node
   const int32_t* inst = nullptr;      // instance of every node
@@ -35,8 +41,10 @@ struct LevelDev {
   unsigned* chk = nullptr;            // checked builds: status word for bound violations
 };
 
+// Coupling omega = on/od of a node's instance and the scale of the key's
+// null term (od, or 1 under the global null model).
 struct Omega {
-  long long on, od;
+  long long on, od, nd;
 };
 
 __device__ __forceinline__ int32_t node_inst(const LevelDev& g, int32_t v) { return g.inst ? g.inst[v] : 0; }
@@ -44,9 +52,9 @@ __device__ __forceinline__ int32_t node_inst(const LevelDev& g, int32_t v) { ret
 __device__ __forceinline__ Omega node_omega(const LevelDev& g, int32_t v) {
   if (g.od_i) {
     const int32_t i = node_inst(g, v);
-    return Omega{g.on_i[i], g.od_i[i]};
+    return Omega{g.on_i[i], g.od_i[i], g.global_null ? 1 : g.od_i[i]};
   }
-  return Omega{g.on, g.od};
+  return Omega{g.on, g.od, g.global_null ? 1 : g.od};
 }
 
 // Node id within its instance (the schedule's hash reads this, so a batched

@@ -15,6 +15,12 @@
 // in its community joins another singleton community only if that label is
 // smaller (otherwise two neighbouring singletons could swap forever).
 //
+// Global null model (plain modularity of the supra-graph, Eq. modularity):
+// one null slice per instance, strengths k' = od*k + on*(coupling edges),
+// Lambda' = floor(gn 2^64 / (gd 2M')), 2M' = od*2mu, and the null term's
+// scale od becomes 1 (Omega::nd):  G(v,c) = 2^64 W(v,c\v) - Lambda' k'_v
+// Sigma'_{c\v}.
+//
 // Sigma_{c,s} lives in a hash keyed (c, s) and is kept exact by the integer
 // atomics of every move; it is rebuilt from the labels only at the start of
 // a level and when tombstone keys fill half of the table.
@@ -141,7 +147,8 @@ struct LMPolicy {
 
   typedef Slot Probe;
   // Per node: own community and its size; at level 0 the node's snapshot s,
-  // strength k and A = od * Lambda_s * k, so a candidate costs one probe and
+  // strength k and A = nd * Lambda_s * k (nd: od, or 1 for the global null
+  // model), so a candidate costs one probe and
   // one 128x64-bit product.
   struct VCtx {
     int32_t a, size_a, s;
@@ -164,7 +171,7 @@ struct LMPolicy {
     if (c.single) {
       c.k = g.k0[v];
       c.s = node_slice0(g, v);
-      if (c.k > 0) c.A = (u128)(ull)c.om.od * lam[c.s] * (u128)(ull)c.k;
+      if (c.k > 0) c.A = (u128)(ull)c.om.nd * lam[c.s] * (u128)(ull)c.k;
     }
     return c;
   }
@@ -178,7 +185,7 @@ struct LMPolicy {
   __device__ int32_t own_key(int32_t v) const { return labels[v]; }
   __device__ i128 key_of(int32_t v, const VCtx& vc, int32_t c, long long W, bool self) const {
     const u128 ns = null_sum<DENSE>(g, lam, sig, v, c, self);
-    return (((i128)W) << P_BITS) - (i128)((u128)(ull)vc.om.od * ns);
+    return (((i128)W) << P_BITS) - (i128)((u128)(ull)vc.om.nd * ns);
   }
   __device__ Probe probe(int32_t, const VCtx& vc, int32_t c) const {
     if (vc.single && vc.k > 0) return sst_first<DENSE>(sig, c, vc.s);
@@ -451,6 +458,15 @@ LevelDev level0_view(const SupraGraph& G, const Solver& S) {
     d.on_i = S.on_d;
     d.od_i = S.od_d;
   }
+  if (S.p.global_null) {
+    // one null slice per instance: the instance id (batches) or 0 (v / N)
+    d.global_null = 1;
+    d.k0 = S.kn;
+    if (G.B > 1)
+      d.slice0 = G.inst0;
+    else
+      d.n = (int32_t)(G.N > 0 ? G.N : 1);
+  }
   return d;
 }
 
@@ -531,7 +547,7 @@ void prepare_level(Solver& S, const Level& L) {
 
 void configure_stores(Solver& S, int64_t N) {
   Ctx& c = *S.c;
-  const int64_t T = S.G0 ? S.G0->T : 1;
+  const int64_t T = S.Tn;
   if (!S.sig_h.slots) {
     // hash tables keyed by (label, snapshot), sized for level 0: at most one
     // live key per (node, snapshot) entry plus the keys created by one round

@@ -9,6 +9,12 @@
 // then omega*J, the numerator, the division), with explicitly rounded
 // operations so no contraction changes the result.
 //
+// Global null model (plain modularity of the supra-graph, Eq. modularity):
+//   Q = (I + omega*J) / 2mu - gamma * S' / (2M')^2,
+//   S' = sum_c Sigma'_c^2 with Sigma' in units of 1/od, 2M' = od*2mu;
+// FP64 order: I + omega*J, divided by 2mu; S' divided by the product
+// 2M'*2M' (each converted first); times gamma; subtracted.
+//
 // Also: canonical relabelling (first occurrence order), distinct counting
 // and the order-free level checksum used by the step-level tests.
 #include <cstring>
@@ -96,11 +102,32 @@ struct QInst {
   long long gn, gd, on, od;
 };
 
-// Q of every instance (one thread each), in the fixed FP64 order.
-__global__ void k_Q(const ull* IJ, const ull* S, const int64_t* two_m, const QInst* qi, int32_t B, double* Q) {
+// Q of every instance (one thread each), in the fixed FP64 order.  S holds
+// one 128-bit sum per null slice: per snapshot (Q_MS) or per instance
+// (global model).
+__global__ void k_Q(const ull* IJ, const ull* S, const int64_t* two_m, const QInst* qi, int32_t B, int32_t global,
+                    double* Q) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B) return;
   const QInst p = qi[i];
+  if (global) {
+    long long sum2m = 0;
+    for (int s = p.soff; s < p.soff + p.T; ++s) sum2m += two_m[s];
+    const long long twoM = p.od * sum2m + 2 * p.on * p.n * (long long)(p.T - 1);
+    if (twoM == 0) {
+      Q[i] = 0.0;
+      return;
+    }
+    const u128 x = ((u128)S[2 * i + 1] << 64) | S[2 * i];
+    const double wJ = __ddiv_rn(__dmul_rn(__ll2double_rn(p.on), __ull2double_rn(IJ[2 * i + 1])), __ll2double_rn(p.od));
+    const double gam = __ddiv_rn(__ll2double_rn(p.gn), __ll2double_rn(p.gd));
+    const double twomu = __ddiv_rn(__ll2double_rn(twoM), __ll2double_rn(p.od));
+    const double first = __ddiv_rn(__dadd_rn(__ull2double_rn(IJ[2 * i]), wJ), twomu);
+    const double tM = __ll2double_rn(twoM);
+    const double null = __ddiv_rn(u128_to_double(x), __dmul_rn(tM, tM));
+    Q[i] = __dsub_rn(first, __dmul_rn(gam, null));
+    return;
+  }
   double nullsum = 0.0;
   long long sum2m = 0;
   for (int s = p.soff; s < p.soff + p.T; ++s) {
@@ -169,10 +196,11 @@ void modularity(Solver& S, const int32_t* labels0, double* Q) {
   Ctx& c = *S.c;
   const SupraGraph& G = *S.G0;
   const int32_t B = G.B;
-  LevelDev g = level0_view(G, S);
+  LevelDev g = level0_view(G, S);  // (S.Tn / S.kn set up by setup_null_model)
   configure_stores(S, G.N);
   sigma_rebuild(S, Level{g}, labels0);
-  ull* acc = c.ws->get<ull>("q_acc", 2 * (size_t)B + 2 * (size_t)G.T);
+  const int32_t Tn = S.Tn;
+  ull* acc = c.ws->get<ull>("q_acc", 2 * (size_t)B + 2 * (size_t)Tn);
   double* dQ = c.ws->get<double>("q_out", B);
   QInst* dqi = c.ws->get<QInst>("q_inst", B);
   std::vector<QInst> qi(B);
@@ -181,13 +209,13 @@ void modularity(Solver& S, const int32_t* labels0, double* Q) {
     qi[i] = QInst{in.n, in.T, in.soff, S.gn_h[i], S.gd_h[i], S.on_h[i], S.od_h[i]};
   }
   check_cuda(cudaMemcpyAsync(dqi, qi.data(), B * sizeof(QInst), cudaMemcpyHostToDevice, c.stream), "copy");
-  check_cuda(cudaMemsetAsync(acc, 0, (2 * (size_t)B + 2 * (size_t)G.T) * sizeof(ull), c.stream), "memset");
+  check_cuda(cudaMemsetAsync(acc, 0, (2 * (size_t)B + 2 * (size_t)Tn) * sizeof(ull), c.stream), "memset");
   if (G.N > 0) launch(c, k_IJ, dim3(gsz(G.N * 32)), dim3(256), 0, g, labels0, acc, B);
-  const size_t smem = G.T <= 1024 ? 2 * (size_t)G.T * sizeof(ull) : 0;
+  const size_t smem = Tn <= 1024 ? 2 * (size_t)Tn * sizeof(ull) : 0;
   const int64_t span = S.sig.d ? S.sig.rows * S.sig.T : (int64_t)S.sig.h.cap;
-  launch(c, k_S, dim3(gsz(span)), dim3(256), smem, S.sig, G.T, acc + 2 * B);
+  launch(c, k_S, dim3(gsz(span)), dim3(256), smem, S.sig, Tn, acc + 2 * B);
   launch(c, k_Q, dim3(grid_for(B, 128)), dim3(128), 0, (const ull*)acc, (const ull*)(acc + 2 * B),
-         (const int64_t*)G.two_m, (const QInst*)dqi, B, dQ);
+         (const int64_t*)G.two_m, (const QInst*)dqi, B, (int32_t)(S.p.global_null ? 1 : 0), dQ);
   // B values go straight to the caller's (pageable) array
   check_cuda(cudaMemcpyAsync(Q, dQ, B * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "copy");
   sync(c);

@@ -58,7 +58,7 @@ __global__ void k_ref_init(LevelDev g, const int32_t* P, SigStore sig, const u12
         rhs += lam_k_x(lam, s, k, ss_get(sig, C, s) - k);
         ss_add(kr, (int32_t)v, s, k);
       }
-      elig[v] = ((((i128)w) << P_BITS) - (i128)((u128)(ull)om.od * rhs)) >= 0 ? 1 : 0;
+      elig[v] = ((((i128)w) << P_BITS) - (i128)((u128)(ull)om.nd * rhs)) >= 0 ? 1 : 0;
     }
   }
 }
@@ -101,8 +101,8 @@ __global__ void k_wc(LevelDev g, const int32_t* sizeR, const long long* Wout, co
       f = elig[L];
     } else if (sz > 1) {
       const u128 x = ((u128)rhs[2 * L + 1] << 64) | rhs[2 * L];
-      const long long od = node_omega(g, (int32_t)L).od;
-      f = ((((i128)Wout[L]) << P_BITS) - (i128)((u128)(ull)od * x)) >= 0 ? 1 : 0;
+      const long long nd = node_omega(g, (int32_t)L).nd;
+      f = ((((i128)Wout[L]) << P_BITS) - (i128)((u128)(ull)nd * x)) >= 0 ? 1 : 0;
     }
     wc[L] = f;
     desc[L] = (unsigned long long)(uint32_t)sz | ((unsigned long long)cls[L] << 32) | ((unsigned long long)f << 40);
@@ -131,7 +131,7 @@ struct RefPolicy {
     int32_t size;
     uint8_t cls, wc;
   };
-  // Per node: at level 0 the snapshot s and A = od * Lambda_s * k.
+  // Per node: at level 0 the snapshot s and A = nd * Lambda_s * k.
   struct VCtx {
     int32_t s, Pv;
     bool single;
@@ -152,7 +152,7 @@ struct RefPolicy {
     if (c.single) {
       c.k = g.k0[v];
       c.s = node_slice0(g, v);
-      if (c.k > 0) c.A = (u128)(ull)c.om.od * lam[c.s] * (u128)(ull)c.k;
+      if (c.k > 0) c.A = (u128)(ull)c.om.nd * lam[c.s] * (u128)(ull)c.k;
     }
     return c;
   }
@@ -195,7 +195,7 @@ struct RefPolicy {
         slice_entry(g, v, j, s, k);
         ns += lam_k_x(lam, s, k, sst_get<DENSE>(kr, X, s));
       }
-      G = (((i128)W) << P_BITS) - (i128)((u128)(ull)vc.om.od * ns);
+      G = (((i128)W) << P_BITS) - (i128)((u128)(ull)vc.om.nd * ns);
     }
     if (G <= 0) return Cand{0, INT32_MAX};
     return Cand{G, X};

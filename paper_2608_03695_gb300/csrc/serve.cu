@@ -148,7 +148,8 @@ struct mslice_server_s {
     const int64_t w = keep + 1;
     const int64_t N = g.n * w;
     nnz += 2 * g.n * (w - 1);
-    return 274 * N + 52 * nnz + (1 << 20);
+    const int64_t global = (opt.solve.flags & MSLICE_NULL_GLOBAL) ? 8 : 0;  // the strengths k'
+    return (274 + global) * N + 52 * nnz + (1 << 20);
   }
 };
 
@@ -225,7 +226,7 @@ void run_batch(mslice_server_s* s, Worker& slot, std::vector<SrvRequest*>& batch
       }
       build_supra(c, ip, ix, wt, nnz, g.n, *p.G);
       check_bounds(g.n, p.G->T, p.G->two_m_host.data(), s->opt.gamma_num, s->opt.gamma_den, s->opt.omega_num,
-                   s->opt.omega_den);
+                   s->opt.omega_den, (s->opt.solve.flags & MSLICE_NULL_GLOBAL) != 0);
       parts.push_back(std::move(p));
     } catch (const Error& e) {
       finish(s, r, e.code, e.msg);
@@ -268,6 +269,7 @@ void run_batch(mslice_server_s* s, Worker& slot, std::vector<SrvRequest*>& batch
     sp.max_levels = s->opt.solve.max_levels;
     sp.n_iterations = s->opt.solve.n_iterations;
     sp.seed = s->opt.solve.seed;
+    sp.global_null = (s->opt.solve.flags & MSLICE_NULL_GLOBAL) != 0;
     for (int k = 0; k < 4; ++k)
       if (s->opt.solve.tier_cuts[0] || s->opt.solve.tier_cuts[1] || s->opt.solve.tier_cuts[2] ||
           s->opt.solve.tier_cuts[3])
@@ -674,7 +676,7 @@ int mslice_server_window_restore(mslice_server s, int32_t graph_id, const mslice
       check.mem.stream = c.stream;
       build_supra(c, ip, ix, wt, nnz, n, check);
       check_bounds(n, check.T, check.two_m_host.data(), s->opt.gamma_num, s->opt.gamma_den, s->opt.omega_num,
-                   s->opt.omega_den);
+                   s->opt.omega_den, (s->opt.solve.flags & MSLICE_NULL_GLOBAL) != 0);
     }
     // valid: the ring's buffers 0..nslices-1 take the snapshots
     g.mem.stream = c.stream;

@@ -14,6 +14,7 @@ struct SolveParams {
   uint64_t seed = 0;
   TierCuts cuts;          // degree cuts between the decision tiers
   bool autotune = false;  // choose the cuts by timing round 0 of level 0
+  bool global_null = false;  // plain modularity of the supra-graph instead of Q_MS
 };
 
 // CUDA-event phase timing: events recorded on the context's stream.
@@ -31,7 +32,9 @@ struct Solver {
   Ctx* c = nullptr;
   const SupraGraph* G0 = nullptr;
   SolveParams p;
-  u128* lam = nullptr;  // Lambda_s, T entries
+  u128* lam = nullptr;  // Lambda of every null slice (Tn entries)
+  int32_t Tn = 1;       // null slices: the snapshots (Q_MS) or one per instance (global model)
+  int64_t* kn = nullptr;  // global model: level-0 strengths k' = od*k + on*(coupling edges)
   int64_t N0 = 0;
 
   // node-indexed scratch, sized for level 0 (every level is smaller)
@@ -142,9 +145,17 @@ LevelDev level0_view(const SupraGraph& G, const Solver& S);
 
 // Fails with MSLICE_EOVERFLOW unless the 128-bit move keys of a graph with n
 // nodes per snapshot and snapshot masses two_m[0..T) stay in range for this
-// gamma and omega: od * sum 2m_s + 2 on n (T-1) < 2^61 and
-// gamma od sum 2m_s < 2^61.
-void check_bounds(int64_t n, int32_t T, const int64_t* two_m, long long gn, long long gd, long long on, long long od);
+// gamma and omega: 2M' = od * sum 2m_s + 2 on n (T-1) < 2^61 and
+// gamma od sum 2m_s < 2^61 (gamma 2M' < 2^61 under the global null model,
+// whose strengths include the coupling).
+void check_bounds(int64_t n, int32_t T, const int64_t* two_m, long long gn, long long gd, long long on, long long od,
+                  bool global_null = false);
+
+// The null model of a solve: S.Tn, the quantised coefficients S.lam (one per
+// snapshot, or one per instance from 2M' for the global model) and, for the
+// global model, the level-0 strengths S.kn.  Needs S.G0, S.N0, S.p and the
+// instances (set_instances).
+void setup_null_model(Solver& S);
 
 // Fails with MSLICE_EINVAL unless every level-0 label d[v] (device) lies in
 // [0, size of v's instance).

@@ -71,6 +71,12 @@ def cases():
 
     out["powerlaw_t16_n100k"] = powerlaw_t16
 
+    def powerlaw_t16_global():
+        # the same graph under the global null model (plain modularity of the supra-graph)
+        return [dict(snaps=synth.recipe_graph("powerlaw_t16_n100k"), gamma=(1, 1), omega=(1, 1), null="global")]
+
+    out["powerlaw_t16_n100k_global"] = powerlaw_t16_global
+
     def powerlaw_t64_n20k():
         snaps = synth.recipe_graph("powerlaw_t64_n1m", scale_n=20000)
         return [dict(snaps=snaps, gamma=(1, 1), omega=om) for om in [(1, 10), (1, 1), (10, 1)]]
@@ -111,8 +117,9 @@ def run_solve(oracle, s):
             res.append({"labels": digest_labels(lab), "Q": repr(Q)})
             prev = lab
         return {"input": digest_snaps(stream), "chain": res}
-    lab, Q, st = oracle.leiden(s["snaps"], s["gamma"], s["omega"])
-    return {"input": digest_snaps(s["snaps"]), "gamma": list(s["gamma"]), "omega": list(s["omega"]),
+    null = s.get("null", "multislice")
+    lab, Q, st = oracle.leiden(s["snaps"], s["gamma"], s["omega"], null=null)
+    return {"input": digest_snaps(s["snaps"]), "gamma": list(s["gamma"]), "omega": list(s["omega"]), "null": null,
             "labels": digest_labels(lab), "Q": repr(Q),
             "stats": {k: int(st[k]) for k in ("iterations", "levels", "lm_rounds", "lm_edges", "lm_moves")}}
 

@@ -112,3 +112,15 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
         assert got[(cname, "size")] == C.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def test_header_constants_match_the_binding():
+    """Every MSLICE_* status code and flag the header defines has the same
+    value in the Python binding."""
+    text = open(os.path.join(ROOT, "include", "mslice.h")).read()
+    defs = dict(re.findall(r"#define\s+(MSLICE_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", text))
+    assert {"MSLICE_DEVICE_PTRS", "MSLICE_PROFILE", "MSLICE_AUTOTUNE", "MSLICE_NULL_GLOBAL"} <= set(defs)
+    for name, value in defs.items():
+        assert getattr(pkg, name) == int(value), name
+    flags = [int(defs[k]) for k in ("MSLICE_DEVICE_PTRS", "MSLICE_PROFILE", "MSLICE_AUTOTUNE", "MSLICE_NULL_GLOBAL")]
+    assert all(f & (f - 1) == 0 for f in flags) and len(set(flags)) == len(flags)  # distinct single bits

@@ -5,7 +5,8 @@ The expected labels (as digests) and Q come from the oracle alone, written by
 their digest differs from the stored one (a platform whose floating-point
 library changes the generated graph) the oracle is run live instead.
 
-* power-law workload at full size (T=16, n=100,000), the benchmark's solve;
+* power-law workload at full size (T=16, n=100,000), the benchmark's solve,
+  under Q_MS and under the global null model;
 * the T=64 power-law recipe at n=20,000 for omega in {1/10, 1, 10}, solved
   one by one and as one batch;
 * four full-size graphs of the batched workload at two (gamma, omega) each,
@@ -69,6 +70,18 @@ def test_power_law_full_size():
     s = solves[0]
     with pkg.mslice_build(s["snaps"]) as h:
         lab, Q, st = h.mslice_leiden(gamma=s["gamma"], omega=s["omega"])
+    assert fsc.digest_labels(lab) == exp[0]["labels"]
+    assert q_ok(Q, exp[0]["Q"])
+    for k in ("iterations", "levels", "lm_rounds", "lm_edges", "lm_moves"):
+        assert st[k] == exp[0]["stats"][k], k
+
+
+def test_power_law_full_size_global_null():
+    solves = fsc.cases()["powerlaw_t16_n100k_global"]()
+    exp = expected("powerlaw_t16_n100k_global", solves)
+    s = solves[0]
+    with pkg.mslice_build(s["snaps"]) as h:
+        lab, Q, st = h.mslice_leiden(gamma=s["gamma"], omega=s["omega"], null="global")
     assert fsc.digest_labels(lab) == exp[0]["labels"]
     assert q_ok(Q, exp[0]["Q"])
     for k in ("iterations", "levels", "lm_rounds", "lm_edges", "lm_moves"):
