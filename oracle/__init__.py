@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(HERE, "liboracle.so")
 OK, EINVAL, EOVERFLOW = 0, -1, -3
 NULL_MULTISLICE, NULL_GLOBAL = 0, 1
 _NULLS = {"multislice": NULL_MULTISLICE, "global": NULL_GLOBAL}
+ORDINAL, CATEGORICAL = 0, 1
+_COUPLINGS = {"ordinal": ORDINAL, "categorical": CATEGORICAL}
 
 
 class OracleError(RuntimeError):
@@ -35,6 +37,38 @@ class _Opts(C.Structure):
     _fields_ = [("n_iterations", C.c_int32), ("K", C.c_int32), ("max_rounds", C.c_int32),
                 ("max_levels", C.c_int32), ("seed", C.c_uint64), ("stop_level", C.c_int32),
                 ("stop_stage", C.c_int32), ("stop_rounds", C.c_int32), ("null_model", C.c_int32)]
+
+
+class _General(C.Structure):
+    _fields_ = [("coupling", C.c_int32), ("pad_", C.c_int32), ("omega_num", C.c_void_p), ("gamma_num", C.c_void_p),
+                ("gamma_den", C.c_void_p)]
+
+
+class _Gen:
+    """The general form (coupling pattern, per-pair omega numerators over the
+    call's omega denominator, per-slice gamma as (num, den) pairs); None when
+    every part takes its default, so the plain path is exercised."""
+
+    def __init__(self, coupling="ordinal", omegas=None, gammas=None):
+        self.arrays = []
+        self.struct = None
+        if coupling == "ordinal" and omegas is None and gammas is None:
+            return
+        g = _General(_COUPLINGS[coupling] if isinstance(coupling, str) else int(coupling), 0, None, None, None)
+        if omegas is not None:
+            om = np.ascontiguousarray(np.asarray(omegas, dtype=np.int64).ravel())
+            self.arrays.append(om)
+            g.omega_num = _ptr(om)
+        if gammas is not None:
+            gn = np.ascontiguousarray([int(x[0]) for x in gammas], dtype=np.int64)
+            gd = np.ascontiguousarray([int(x[1]) for x in gammas], dtype=np.int64)
+            self.arrays += [gn, gd]
+            g.gamma_num, g.gamma_den = _ptr(gn), _ptr(gd)
+        self.struct = g
+
+    @property
+    def ptr(self):
+        return C.byref(self.struct) if self.struct is not None else None
 
 
 class _Stats(C.Structure):
@@ -64,14 +98,15 @@ def lib():
         build()
         L = C.CDLL(LIB_PATH)
         P = C.c_void_p
-        L.orc_leiden.argtypes = [P, C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_int64, P, P, P, C.c_int64,
-                                 P, P]
-        L.orc_modularity.argtypes = [P, C.c_int32, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int32, P]
-        L.orc_move_key.argtypes = [P, C.c_int32, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
+        L.orc_leiden.argtypes = [P, C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_int64, P, P, P, P,
+                                 C.c_int64, P, P]
+        L.orc_modularity.argtypes = [P, C.c_int32, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int32, P,
+                                     P]
+        L.orc_move_key.argtypes = [P, C.c_int32, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int32, P,
                                    C.c_int64, C.c_int64, P]
         L.orc_lambda.argtypes = [P, C.c_int32, C.c_int64, C.c_int64, P, P]
         L.orc_count_improving.argtypes = [P, C.c_int32, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
-                                          P]
+                                          P, P]
         L.orc_mix64.argtypes = [C.c_uint64]
         L.orc_mix64.restype = C.c_uint64
         L.orc_default_opts.argtypes = [P]
@@ -115,8 +150,11 @@ def _null(null) -> int:
 
 
 def leiden(snaps, gamma=(1, 1), omega=(1, 1), n_iterations=2, K=4, max_rounds=100, max_levels=32, seed=0,
-           init=None, stop_level=-1, stop_stage=0, stop_rounds=0, null="multislice"):
-    """Returns (labels int32[...], Q, stats dict)."""
+           init=None, stop_level=-1, stop_stage=0, stop_rounds=0, null="multislice", coupling="ordinal",
+           omegas=None, gammas=None):
+    """Returns (labels int32[...], Q, stats dict).  coupling / omegas /
+    gammas: the general form (omega^(sr) numerators over omega[1], per-slice
+    gamma pairs)."""
     S = _Slices(snaps)
     o = _Opts(n_iterations, K, max_rounds, max_levels, seed, stop_level, stop_stage, stop_rounds, _null(null))
     cap = max(S.N, 1)
@@ -124,28 +162,33 @@ def leiden(snaps, gamma=(1, 1), omega=(1, 1), n_iterations=2, K=4, max_rounds=10
     Q = C.c_double(0.0)
     st = _Stats()
     init_a = None if init is None else np.ascontiguousarray(init, dtype=np.int32)
-    rc = lib().orc_leiden(S.ptr, S.T, gamma[0], gamma[1], omega[0], omega[1], C.byref(o), _ptr(init_a),
+    gen = _Gen(coupling, omegas, gammas)
+    rc = lib().orc_leiden(S.ptr, S.T, gamma[0], gamma[1], omega[0], omega[1], C.byref(o), gen.ptr, _ptr(init_a),
                           _ptr(out), cap, C.byref(Q), C.byref(st))
     _check(rc, "orc_leiden")
     stats = {f: getattr(st, f) for f, _ in _Stats._fields_}
     return out[: st.out_n].copy(), Q.value, stats
 
 
-def modularity(snaps, labels, gamma=(1, 1), omega=(1, 1), null="multislice"):
+def modularity(snaps, labels, gamma=(1, 1), omega=(1, 1), null="multislice", coupling="ordinal", omegas=None,
+               gammas=None):
     S = _Slices(snaps)
     lab = np.ascontiguousarray(labels, dtype=np.int32)
     Q = C.c_double(0.0)
+    gen = _Gen(coupling, omegas, gammas)
     _check(lib().orc_modularity(S.ptr, S.T, _ptr(lab), gamma[0], gamma[1], omega[0], omega[1], _null(null),
-                                C.byref(Q)), "orc_modularity")
+                                gen.ptr, C.byref(Q)), "orc_modularity")
     return Q.value
 
 
-def move_key(snaps, labels, v, c, gamma=(1, 1), omega=(1, 1), null="multislice") -> int:
+def move_key(snaps, labels, v, c, gamma=(1, 1), omega=(1, 1), null="multislice", coupling="ordinal",
+             omegas=None, gammas=None) -> int:
     S = _Slices(snaps)
     lab = np.ascontiguousarray(labels, dtype=np.int32)
     out = (C.c_uint64 * 2)()
-    _check(lib().orc_move_key(S.ptr, S.T, _ptr(lab), gamma[0], gamma[1], omega[0], omega[1], _null(null), v, c,
-                              out), "orc_move_key")
+    gen = _Gen(coupling, omegas, gammas)
+    _check(lib().orc_move_key(S.ptr, S.T, _ptr(lab), gamma[0], gamma[1], omega[0], omega[1], _null(null), gen.ptr,
+                              v, c, out), "orc_move_key")
     x = out[0] | (out[1] << 64)
     return x - (1 << 128) if x >> 127 else x
 
@@ -158,12 +201,14 @@ def lambdas(snaps, gamma=(1, 1)):
     return [int(lam[2 * s]) | (int(lam[2 * s + 1]) << 64) for s in range(S.T)], [int(x) for x in tm]
 
 
-def count_improving(snaps, labels, gamma=(1, 1), omega=(1, 1), null="multislice") -> int:
+def count_improving(snaps, labels, gamma=(1, 1), omega=(1, 1), null="multislice", coupling="ordinal",
+                    omegas=None, gammas=None) -> int:
     S = _Slices(snaps)
     lab = np.ascontiguousarray(labels, dtype=np.int32)
     cnt = C.c_int64(0)
+    gen = _Gen(coupling, omegas, gammas)
     _check(lib().orc_count_improving(S.ptr, S.T, _ptr(lab), gamma[0], gamma[1], omega[0], omega[1], _null(null),
-                                     C.byref(cnt)), "orc_count_improving")
+                                     gen.ptr, C.byref(cnt)), "orc_count_improving")
     return cnt.value
 
 

@@ -65,10 +65,23 @@ struct Level {
 // below are kept in units of 1/od (k' = od*k + on*c, c = the node's coupling
 // edges), the null "slice" is single (index 0) and the key's null scale is 1
 // instead of od.
+//
+// General coupling (the omega^(sr) and gamma^(s) of Eq. multislice-modularity):
+// omega^(sr) = cw[pair]/od, with pair = min(s,r) for ORDINAL coupling (only
+// |s-r| = 1 coupled) and pair = s*T + r for CATEGORICAL coupling (every pair
+// s != r).  Without a table every coupled pair has numerator on.  gamma^(s)
+// = gsn[s]/gsd[s], or gn/gd for every slice without a table.  cstr[s] is the
+// coupling strength of one node of slice s, sum_r omega_num^(sr).
 struct Problem {
   int32_t T = 0;
   int64_t n = 0;
   int64_t gn = 1, gd = 1, on = 1, od = 1;
+  int32_t coupling = ORC_ORDINAL;
+  bool omega_table = false;
+  std::vector<int64_t> cw;
+  bool gamma_table = false;
+  std::vector<int64_t> gsn, gsd;
+  std::vector<int64_t> cstr;
   int32_t null_model = ORC_NULL_MULTISLICE;
   int64_t ns = 1;              // null scale of the key: od (multislice) or 1 (global)
   std::vector<int64_t> two_m;  // 2m_s of every snapshot
@@ -81,6 +94,54 @@ bool valid_rational(int64_t num, int64_t den, bool allow_zero) {
   if (den < 1 || den > lim) return false;
   if (num < (allow_zero ? 0 : 1) || num > lim) return false;
   return true;
+}
+
+// Numerator of omega^(sr) over od (0 when s and r are not coupled).
+int64_t coupling_num(const Problem& p, int32_t s, int32_t r) {
+  if (s == r) return 0;
+  if (p.coupling == ORC_ORDINAL) return (s - r == 1 || r - s == 1) ? p.cw[std::min(s, r)] : 0;
+  return p.cw[(int64_t)s * p.T + r];
+}
+
+// The coupling table and the per-slice resolutions from the optional
+// general specification (EINVAL for a bad one).
+int setup_general(const orc_general* g, Problem& p) {
+  const int32_t T = p.T;
+  p.coupling = g ? g->coupling : ORC_ORDINAL;
+  if (p.coupling != ORC_ORDINAL && p.coupling != ORC_CATEGORICAL) return ORC_EINVAL;
+  const int64_t npairs = p.coupling == ORC_ORDINAL ? (T > 1 ? T - 1 : 0) : (int64_t)T * T;
+  p.omega_table = g && g->omega_num;
+  p.cw.assign(npairs, p.on);
+  if (p.coupling == ORC_CATEGORICAL)
+    for (int32_t s = 0; s < T; ++s) p.cw[(int64_t)s * T + s] = 0;
+  if (p.omega_table) {
+    for (int64_t q = 0; q < npairs; ++q) {
+      if (!valid_rational(g->omega_num[q], p.od, true)) return ORC_EINVAL;
+      p.cw[q] = g->omega_num[q];
+    }
+    if (p.coupling == ORC_CATEGORICAL)
+      for (int32_t s = 0; s < T; ++s) {
+        if (p.cw[(int64_t)s * T + s] != 0) return ORC_EINVAL;
+        for (int32_t r = 0; r < s; ++r)
+          if (p.cw[(int64_t)s * T + r] != p.cw[(int64_t)r * T + s]) return ORC_EINVAL;
+      }
+  }
+  p.gamma_table = g && (g->gamma_num || g->gamma_den);
+  p.gsn.assign(T, p.gn);
+  p.gsd.assign(T, p.gd);
+  if (p.gamma_table) {
+    if (!g->gamma_num || !g->gamma_den) return ORC_EINVAL;
+    if (p.null_model == ORC_NULL_GLOBAL) return ORC_EINVAL;  // one null term: one resolution
+    for (int32_t s = 0; s < T; ++s) {
+      if (!valid_rational(g->gamma_num[s], g->gamma_den[s], false)) return ORC_EINVAL;
+      p.gsn[s] = g->gamma_num[s];
+      p.gsd[s] = g->gamma_den[s];
+    }
+  }
+  p.cstr.assign(T, 0);
+  for (int32_t s = 0; s < T; ++s)
+    for (int32_t r = 0; r < T; ++r) p.cstr[s] += coupling_num(p, s, r);
+  return ORC_OK;
 }
 
 // Input validation (reading: the paper takes simple undirected snapshots; this
@@ -123,9 +184,10 @@ int validate(const orc_csr* slices, int32_t T) {
 // multi-slice nodes would need lcm(2m_s); both implementations instead
 // compare keys built from Lambda_s, i.e. they optimise Q_MS with
 // gamma'_s = Lambda_s*2m_s/2^P, within 2m_s/2^64 of gamma (relative).
-// Global model: one null slice of mass 2M' = od*sum(2m_s) + 2*on*n*(T-1) (the
-// supra-graph's total weight in units of 1/od) and
+// Global model: one null slice of mass 2M' = od*sum(2m_s) + n*sum_s cstr[s]
+// (the supra-graph's total weight in units of 1/od) and
 //   Lambda' = floor(gn * 2^P / (gd * 2M')).
+// Per-slice resolutions: Lambda_s = floor(gsn[s] * 2^P / (gsd[s] * 2m_s)).
 void slice_masses(const orc_csr* slices, Problem& p) {
   p.two_m.assign(p.T, 0);
   for (int32_t s = 0; s < p.T; ++s) {
@@ -136,37 +198,50 @@ void slice_masses(const orc_csr* slices, Problem& p) {
   if (p.null_model == ORC_NULL_GLOBAL) {
     int64_t sum2m = 0;
     for (int64_t t : p.two_m) sum2m += t;
-    p.two_m_null.assign(1, p.od * sum2m + 2 * p.on * p.n * (int64_t)(p.T - 1));
+    int64_t csum = 0;
+    for (int64_t c : p.cstr) csum += c;
+    p.two_m_null.assign(1, p.od * sum2m + p.n * csum);
     p.ns = 1;
   } else {
     p.two_m_null = p.two_m;
     p.ns = p.od;
   }
   p.lambda.assign(p.two_m_null.size(), 0);
+  const bool global = p.null_model == ORC_NULL_GLOBAL;
   for (size_t s = 0; s < p.two_m_null.size(); ++s) {
     const int64_t t = p.two_m_null[s];
-    if (t > 0) p.lambda[s] = (((u128)(uint64_t)p.gn) << P_BITS) / ((u128)(uint64_t)p.gd * (u128)(uint64_t)t);
+    const int64_t num = global ? p.gn : p.gsn[s], den = global ? p.gd : p.gsd[s];
+    if (t > 0) p.lambda[s] = (((u128)(uint64_t)num) << P_BITS) / ((u128)(uint64_t)den * (u128)(uint64_t)t);
   }
 }
 
 // Overflow guard: every key below stays inside a signed 128-bit integer when
-//   od*sum(2m_s) + 2*on*n_cpl < 2^61   and   gamma*od*sum(2m_s) < 2^61.
+//   2M' = od*sum(2m_s) + n*sum_s cstr[s] < 2^61   and   gamma_s*od*sum(2m_s) < 2^61
+// for every s (gamma*2M' < 2^61 for the global model, whose strengths include
+// the coupling).
 int check_bounds(const Problem& p) {
   u128 sum2m = 0;
   for (int64_t t : p.two_m) sum2m += (u128)(uint64_t)t;
-  u128 ncpl = (u128)(uint64_t)p.n * (u128)(uint64_t)(p.T - 1);
+  u128 csum = 0;
+  for (int64_t c : p.cstr) csum += (u128)(uint64_t)c;
   u128 lim = (u128)1 << 61;
-  const u128 twoM = (u128)(uint64_t)p.od * sum2m + 2 * (u128)(uint64_t)p.on * ncpl;
+  const u128 twoM = (u128)(uint64_t)p.od * sum2m + (u128)(uint64_t)p.n * csum;
   if (twoM >= lim) return ORC_EOVERFLOW;
-  // global model: the null term's strengths include coupling, so gamma*2M'
-  const u128 null_mass = p.null_model == ORC_NULL_GLOBAL ? twoM : (u128)(uint64_t)p.od * sum2m;
-  if ((u128)(uint64_t)p.gn * null_mass >= lim * (u128)(uint64_t)p.gd) return ORC_EOVERFLOW;
+  if (p.null_model == ORC_NULL_GLOBAL) {
+    if ((u128)(uint64_t)p.gn * twoM >= lim * (u128)(uint64_t)p.gd) return ORC_EOVERFLOW;
+    return ORC_OK;
+  }
+  for (int32_t s = 0; s < p.T; ++s)
+    if ((u128)(uint64_t)p.gsn[s] * (u128)(uint64_t)p.od * sum2m >= lim * (u128)(uint64_t)p.gsd[s])
+      return ORC_EOVERFLOW;
   return ORC_OK;
 }
 
 // Level 0: the supra-graph of Eq. supra-adjacency.  Supra-node v = s*n + i.
 // Intra-slice edge (i,j) of snapshot s -> (s*n+i, s*n+j) with W = od*w.
-// Ordinal coupling (i,s)-(i,s+1) for s < T-1 with W = on (omitted when on=0).
+// Coupling (i,s)-(i,r) with W = omega_num^(sr), omitted when that is 0:
+// ordinal r = s-1 and s+1 with W = on unless a table is given; categorical
+// every r != s.
 Level build_level0(const orc_csr* slices, const Problem& p) {
   Level L;
   L.N = p.n * p.T;
@@ -176,17 +251,18 @@ Level build_level0(const orc_csr* slices, const Problem& p) {
     for (int64_t i = 0; i < p.n; ++i) {
       int64_t v = (int64_t)s * p.n + i;
       auto& a = L.adj[v];
-      if (s > 0 && p.on > 0) a.push_back({(int32_t)(v - p.n), p.on});
+      for (int32_t r = 0; r < s; ++r)
+        if (coupling_num(p, s, r) > 0) a.push_back({(int32_t)((int64_t)r * p.n + i), coupling_num(p, s, r)});
       int64_t k = 0;
       for (int64_t e = slices[s].indptr[i]; e < slices[s].indptr[i + 1]; ++e) {
         a.push_back({(int32_t)((int64_t)s * p.n + slices[s].indices[e]), p.od * (int64_t)slices[s].weights[e]});
         k += slices[s].weights[e];
       }
-      if (s < p.T - 1 && p.on > 0) a.push_back({(int32_t)(v + p.n), p.on});
+      for (int32_t r = s + 1; r < p.T; ++r)
+        if (coupling_num(p, s, r) > 0) a.push_back({(int32_t)((int64_t)r * p.n + i), coupling_num(p, s, r)});
       if (p.null_model == ORC_NULL_GLOBAL) {
-        // k' = od*k + on*(coupling edges of v), one null slice
-        const int64_t c = (s > 0 ? 1 : 0) + (s < p.T - 1 ? 1 : 0);
-        const int64_t kp = p.od * k + p.on * c;
+        // k' = od*k + (coupling strength of v), one null slice
+        const int64_t kp = p.od * k + p.cstr[s];
         if (kp > 0) L.kvec[v].push_back({0, kp});
       } else if (k > 0) {
         L.kvec[v].push_back({s, k});
@@ -499,53 +575,73 @@ void canonicalise(std::vector<int32_t>& x) {
 // u128 -> double, round to nearest (the compiler's conversion).
 double u128_to_double(u128 x) { return (double)x; }
 
-// Q_MS in FP64 (Eq. multislice-modularity with ordinal coupling):
-//   2mu Q = I + omega*J - gamma * sum_s (sum_c Sigma_{c,s}^2) / 2m_s,
+// Q_MS in FP64 (Eq. multislice-modularity):
+//   2mu Q = I + omega*J - sum_s gamma_s (sum_c Sigma_{c,s}^2) / 2m_s,
 //   I = sum of intra-slice weights over ordered pairs in one community,
-//   J = number of ordered coupling pairs in one community,
-//   2mu = sum_s 2m_s + 2*omega*n*(T-1).
+//   omega*J = sum of omega^(sr) over ordered coupling pairs in one community
+//             (J counts them when every coupled pair has the same omega),
+//   2mu = sum_s 2m_s + n * sum_s sum_r omega^(sr).
 // Fixed evaluation order (reading, shared by both implementations): slice
 // terms as (double)S_s/(double)2m_s summed in ascending s, then omega*J as
-// ((double)on*(double)J)/(double)od, then the numerator, then the division.
+// ((double)on*(double)J)/(double)od (uniform omega) or (double)Jw/(double)od
+// (Jw = the integer sum of the pairs' numerators), then the numerator
+// (I + omega*J) - gamma*sum, then the division.  With per-slice resolutions
+// each slice term is first multiplied by (double)gsn/(double)gsd and the
+// products are summed ascending instead.
 // Global model, Eq. modularity on the supra-graph with total weight 2mu:
 //   Q = (I + omega*J) / 2mu - gamma * S' / (2mu)^2,
 //   S' = sum_c (sum_{v in c} k'_v)^2 in units of 1/od^2, so the second term is
 //   evaluated as S' / (2M')^2 with 2M' = od*2mu.
 // Fixed order: I + omega*J as above, divided by 2mu; S' (double) divided by
 // ((double)2M' * (double)2M'); times gamma; subtracted.
-double modularity_global(const orc_csr* slices, const Problem& p, const std::vector<int32_t>& labels) {
+struct PairSums {
+  int64_t I = 0, J = 0, Jw = 0;
+};
+
+// I, J and Jw of a level-0 labelling; calls per_node(v, s, k) for every node.
+template <class F>
+PairSums pair_sums(const orc_csr* slices, const Problem& p, const std::vector<int32_t>& labels, F per_node) {
+  PairSums ps;
   const int64_t n = p.n;
-  int64_t I = 0, J = 0;
-  std::map<int32_t, u128> sig;  // Sigma'_c
   for (int32_t s = 0; s < p.T; ++s) {
     for (int64_t i = 0; i < n; ++i) {
       const int64_t v = (int64_t)s * n + i;
       int64_t k = 0;
       for (int64_t e = slices[s].indptr[i]; e < slices[s].indptr[i + 1]; ++e) {
         const int64_t u = (int64_t)s * n + slices[s].indices[e];
-        if (labels[u] == labels[v]) I += slices[s].weights[e];
+        if (labels[u] == labels[v]) ps.I += slices[s].weights[e];
         k += slices[s].weights[e];
       }
-      int64_t c = 0;
-      if (s > 0) {
-        c++;
-        if (labels[v - n] == labels[v]) J++;
+      for (int32_t r = 0; r < p.T; ++r) {
+        const bool coupled = p.coupling == ORC_ORDINAL ? (r == s - 1 || r == s + 1) : r != s;
+        if (!coupled || labels[(int64_t)r * n + i] != labels[v]) continue;
+        ps.J++;
+        ps.Jw += coupling_num(p, s, r);
       }
-      if (s < p.T - 1) {
-        c++;
-        if (labels[v + n] == labels[v]) J++;
-      }
-      sig[labels[v]] += (u128)(uint64_t)(p.od * k + p.on * c);
+      per_node(v, s, k);
     }
   }
+  return ps;
+}
+
+double omega_J(const Problem& p, const PairSums& ps) {
+  if (p.omega_table) return (double)ps.Jw / (double)p.od;
+  return ((double)p.on * (double)ps.J) / (double)p.od;
+}
+
+double modularity_global(const orc_csr* slices, const Problem& p, const std::vector<int32_t>& labels) {
+  std::map<int32_t, u128> sig;  // Sigma'_c
+  const PairSums ps = pair_sums(slices, p, labels, [&](int64_t v, int32_t s, int64_t k) {
+    sig[labels[v]] += (u128)(uint64_t)(p.od * k + p.cstr[s]);
+  });
   u128 S = 0;
   for (const auto& cs : sig) S += cs.second * cs.second;
   const int64_t twoM = p.two_m_null[0];
   if (twoM == 0) return 0.0;  // reading: no edges and no coupling -> Q = 0
-  const double wJ = ((double)p.on * (double)J) / (double)p.od;
+  const double wJ = omega_J(p, ps);
   const double gam = (double)p.gn / (double)p.gd;
   const double twomu = (double)twoM / (double)p.od;
-  const double first = ((double)I + wJ) / twomu;
+  const double first = ((double)ps.I + wJ) / twomu;
   const double null = u128_to_double(S) / ((double)twoM * (double)twoM);
   return first - gam * null;
 }
@@ -553,41 +649,32 @@ double modularity_global(const orc_csr* slices, const Problem& p, const std::vec
 double modularity_of(const orc_csr* slices, const Problem& p, const std::vector<int32_t>& labels) {
   if (p.null_model == ORC_NULL_GLOBAL) return modularity_global(slices, p, labels);
   const int64_t n = p.n;
-  int64_t I = 0, J = 0;
   std::map<int32_t, SliceMap> sig;
-  for (int32_t s = 0; s < p.T; ++s) {
-    for (int64_t i = 0; i < n; ++i) {
-      const int64_t v = (int64_t)s * n + i;
-      int64_t k = 0;
-      for (int64_t e = slices[s].indptr[i]; e < slices[s].indptr[i + 1]; ++e) {
-        const int64_t u = (int64_t)s * n + slices[s].indices[e];
-        if (labels[u] == labels[v]) I += slices[s].weights[e];
-        k += slices[s].weights[e];
-      }
-      if (s > 0 && labels[v - n] == labels[v]) J++;
-      if (s < p.T - 1 && labels[v + n] == labels[v]) J++;
-      sig[labels[v]][s] += k;
-    }
-  }
+  const PairSums ps =
+      pair_sums(slices, p, labels, [&](int64_t v, int32_t s, int64_t k) { sig[labels[v]][s] += k; });
   std::vector<u128> S(p.T, 0);
   for (const auto& cs : sig)
     for (const auto& sk : cs.second) S[sk.first] += (u128)(uint64_t)sk.second * (u128)(uint64_t)sk.second;
   double nullsum = 0.0;
-  for (int32_t s = 0; s < p.T; ++s)
-    if (p.two_m[s] > 0) nullsum += u128_to_double(S[s]) / (double)p.two_m[s];
-  const double wJ = ((double)p.on * (double)J) / (double)p.od;
+  for (int32_t s = 0; s < p.T; ++s) {
+    if (p.two_m[s] == 0) continue;
+    const double term = u128_to_double(S[s]) / (double)p.two_m[s];
+    nullsum += p.gamma_table ? ((double)p.gsn[s] / (double)p.gsd[s]) * term : term;
+  }
+  const double wJ = omega_J(p, ps);
   const double gam = (double)p.gn / (double)p.gd;
-  int64_t sum2m = 0;
+  int64_t sum2m = 0, csum = 0;
   for (int64_t t : p.two_m) sum2m += t;
-  const int64_t twomu_num = p.od * sum2m + 2 * p.on * n * (int64_t)(p.T - 1);
+  for (int64_t c : p.cstr) csum += c;
+  const int64_t twomu_num = p.od * sum2m + n * csum;
   if (twomu_num == 0) return 0.0;  // reading: no edges and no coupling -> Q = 0
   const double twomu = (double)twomu_num / (double)p.od;
-  const double num = ((double)I + wJ) - gam * nullsum;
+  const double num = ((double)ps.I + wJ) - (p.gamma_table ? nullsum : gam * nullsum);
   return num / twomu;
 }
 
 int setup(const orc_csr* slices, int32_t T, int64_t gn, int64_t gd, int64_t on, int64_t od, Problem& p,
-          int32_t null_model = ORC_NULL_MULTISLICE) {
+          int32_t null_model, const orc_general* gen) {
   int rc = validate(slices, T);
   if (rc) return rc;
   if (!valid_rational(gn, gd, false) || !valid_rational(on, od, true)) return ORC_EINVAL;
@@ -599,6 +686,8 @@ int setup(const orc_csr* slices, int32_t T, int64_t gn, int64_t gd, int64_t on, 
   p.gd = gd;
   p.on = on;
   p.od = od;
+  rc = setup_general(gen, p);
+  if (rc) return rc;
   slice_masses(slices, p);
   return check_bounds(p);
 }
@@ -623,7 +712,7 @@ void orc_default_opts(orc_opts* o) {
 
 int orc_lambda(const orc_csr* slices, int32_t T, int64_t gn, int64_t gd, uint64_t* lam, int64_t* two_m) {
   Problem p;
-  int rc = setup(slices, T, gn, gd, 1, 1, p);
+  int rc = setup(slices, T, gn, gd, 1, 1, p, ORC_NULL_MULTISLICE, nullptr);
   if (rc) return rc;
   for (int32_t s = 0; s < T; ++s) {
     lam[2 * s] = (uint64_t)p.lambda[s];
@@ -634,9 +723,9 @@ int orc_lambda(const orc_csr* slices, int32_t T, int64_t gn, int64_t gd, uint64_
 }
 
 int orc_modularity(const orc_csr* slices, int32_t T, const int32_t* labels, int64_t gn, int64_t gd, int64_t on,
-                   int64_t od, int32_t null_model, double* Q_out) {
+                   int64_t od, int32_t null_model, const orc_general* gen, double* Q_out) {
   Problem p;
-  int rc = setup(slices, T, gn, gd, on, od, p, null_model);
+  int rc = setup(slices, T, gn, gd, on, od, p, null_model, gen);
   if (rc) return rc;
   const int64_t N = p.n * T;
   std::vector<int32_t> lab(labels, labels + N);
@@ -647,9 +736,9 @@ int orc_modularity(const orc_csr* slices, int32_t T, const int32_t* labels, int6
 }
 
 int orc_move_key(const orc_csr* slices, int32_t T, const int32_t* labels, int64_t gn, int64_t gd, int64_t on,
-                 int64_t od, int32_t null_model, int64_t v, int64_t c, uint64_t out[2]) {
+                 int64_t od, int32_t null_model, const orc_general* gen, int64_t v, int64_t c, uint64_t out[2]) {
   Problem p;
-  int rc = setup(slices, T, gn, gd, on, od, p, null_model);
+  int rc = setup(slices, T, gn, gd, on, od, p, null_model, gen);
   if (rc) return rc;
   Level G = build_level0(slices, p);
   if (v < 0 || v >= G.N) return ORC_EINVAL;
@@ -670,9 +759,9 @@ int orc_move_key(const orc_csr* slices, int32_t T, const int32_t* labels, int64_
 }
 
 int orc_count_improving(const orc_csr* slices, int32_t T, const int32_t* labels, int64_t gn, int64_t gd, int64_t on,
-                        int64_t od, int32_t null_model, int64_t* count) {
+                        int64_t od, int32_t null_model, const orc_general* gen, int64_t* count) {
   Problem p;
-  int rc = setup(slices, T, gn, gd, on, od, p, null_model);
+  int rc = setup(slices, T, gn, gd, on, od, p, null_model, gen);
   if (rc) return rc;
   Level G = build_level0(slices, p);
   std::vector<int64_t> size(G.N, 0);
@@ -708,12 +797,13 @@ int orc_count_improving(const orc_csr* slices, int32_t T, const int32_t* labels,
 }
 
 int orc_leiden(const orc_csr* slices, int32_t T, int64_t gn, int64_t gd, int64_t on, int64_t od, const orc_opts* o,
-               const int32_t* init_labels, int32_t* labels_out, int64_t labels_cap, double* Q_out, orc_stats* st) {
+               const orc_general* gen, const int32_t* init_labels, int32_t* labels_out, int64_t labels_cap,
+               double* Q_out, orc_stats* st) {
   orc_opts opt;
   orc_default_opts(&opt);
   if (o) opt = *o;
   Problem p;
-  int rc = setup(slices, T, gn, gd, on, od, p, opt.null_model);
+  int rc = setup(slices, T, gn, gd, on, od, p, opt.null_model, gen);
   if (rc) return rc;
   if (opt.n_iterations < 1 || opt.K < 1 || opt.max_rounds < 1 || opt.max_levels < 1) return ORC_EINVAL;
   orc_stats local{};

@@ -10,7 +10,10 @@
  * with cuGraph", Sec. 3.2):
  *   - objective: multislice modularity Q_MS (Eq. multislice-modularity) with
  *     ordinal coupling omega between copies of a node in adjacent snapshots
- *     and the per-slice null model gamma*k_is*k_js/2m_s;
+ *     and the per-slice null model gamma*k_is*k_js/2m_s; or its general form
+ *     (omega^(sr) per pair of slices, ordinal or categorical, and gamma^(s)
+ *     per slice: orc_general); or the global null model (plain modularity of
+ *     the supra-graph);
  *   - supra-graph: Eq. supra-adjacency (A^(t) blocks on the diagonal, omega*I
  *     on the first off-diagonals);
  *   - optimiser: Leiden (local moving, refinement, aggregation), as named in
@@ -22,6 +25,9 @@
  * form Tr(C^T M C)/2mu (Sec. 3.2), to Newman-Girvan modularity at T=1
  * (Eq. modularity) and to the omega=0 per-slice decomposition.  The move key
  * (orc_move_key) is pinned to exact rational differences of Q_MS.  The
+ * general form and the global model are pinned the same ways (exact-rational
+ * dense forms, networkx on the supra-graph, exact key differences, brute
+ * force, reduction to the uniform model).  The
  * partition returned by orc_leiden is "parity unpinned" by the paper (it
  * prints no partitions); it is checked against invariants only: brute-force
  * optimum bound, local optimality at convergence, connected communities,
@@ -47,6 +53,27 @@ extern "C" {
  * supra-graph, Sec. 3.2). */
 #define ORC_NULL_MULTISLICE 0
 #define ORC_NULL_GLOBAL 1
+
+/* Coupling patterns: ORDINAL couples (i,s) with (i,s+1); CATEGORICAL couples
+ * (i,s) with (i,r) for every r != s. */
+#define ORC_ORDINAL 0
+#define ORC_CATEGORICAL 1
+
+/* General form of Eq. multislice-modularity (nullable everywhere it is
+ * taken; NULL = ordinal coupling with the uniform omega and gamma).
+ * omega_num (nullable): numerators of omega^(sr) over the call's omega_den,
+ *   each in [0, 2^31]; ORDINAL: T-1 entries, entry s for the pair (s, s+1);
+ *   CATEGORICAL: a T*T row-major matrix, symmetric with a zero diagonal.
+ *   NULL: every coupled pair has the call's omega_num.
+ * gamma_num, gamma_den (both or neither): T per-slice resolutions gamma^(s);
+ *   not with the global null model (one null term has one resolution). */
+typedef struct {
+  int32_t coupling;
+  int32_t pad_;
+  const int64_t* omega_num;
+  const int64_t* gamma_num;
+  const int64_t* gamma_den;
+} orc_general;
 
 /* One snapshot: symmetric CSR, sorted columns, no self-loops, weights >= 1. */
 typedef struct {
@@ -97,21 +124,22 @@ void orc_default_opts(orc_opts* o);
  * (renumbered by first occurrence), Q_out the FP64 Q_MS with the true gamma.
  * init_labels (nullable) must lie in [0, N). */
 int orc_leiden(const orc_csr* slices, int32_t T, int64_t gamma_num, int64_t gamma_den,
-               int64_t omega_num, int64_t omega_den, const orc_opts* o, const int32_t* init_labels,
-               int32_t* labels_out, int64_t labels_cap, double* Q_out, orc_stats* st);
+               int64_t omega_num, int64_t omega_den, const orc_opts* o, const orc_general* gen,
+               const int32_t* init_labels, int32_t* labels_out, int64_t labels_cap, double* Q_out,
+               orc_stats* st);
 
 /* Q of a level-0 labelling (labels in [0, N)) under null_model: Q_MS, or the
  * supra-graph's plain modularity. */
 int orc_modularity(const orc_csr* slices, int32_t T, const int32_t* labels, int64_t gamma_num,
                    int64_t gamma_den, int64_t omega_num, int64_t omega_den, int32_t null_model,
-                   double* Q_out);
+                   const orc_general* gen, double* Q_out);
 
 /* Exact integer key G(v, c) of the level-0 supra-node v for community c under
  * `labels` (c = -1 means an empty community).  Written as a signed 128-bit
  * integer in out[0] (low) / out[1] (high). */
 int orc_move_key(const orc_csr* slices, int32_t T, const int32_t* labels, int64_t gamma_num,
-                 int64_t gamma_den, int64_t omega_num, int64_t omega_den, int32_t null_model, int64_t v,
-                 int64_t c, uint64_t out[2]);
+                 int64_t gamma_den, int64_t omega_num, int64_t omega_den, int32_t null_model,
+                 const orc_general* gen, int64_t v, int64_t c, uint64_t out[2]);
 
 /* Quantised null coefficients Lambda_s, as 128-bit (lo, hi) pairs, and 2m_s. */
 int orc_lambda(const orc_csr* slices, int32_t T, int64_t gamma_num, int64_t gamma_den,
@@ -122,7 +150,7 @@ int orc_lambda(const orc_csr* slices, int32_t T, int64_t gamma_num, int64_t gamm
  * than staying. */
 int orc_count_improving(const orc_csr* slices, int32_t T, const int32_t* labels, int64_t gamma_num,
                         int64_t gamma_den, int64_t omega_num, int64_t omega_den, int32_t null_model,
-                        int64_t* count);
+                        const orc_general* gen, int64_t* count);
 
 /* The counter-based hash used to draw vertex classes (SplitMix64 finaliser). */
 uint64_t orc_mix64(uint64_t x);

@@ -692,3 +692,306 @@ def test_global_overflow_guard_counts_coupling():
     with pytest.raises(oracle.OracleError) as e:
         oracle.leiden(snaps, null=2)
     assert e.value.code == oracle.EINVAL
+
+
+# ----------------------------------------------------------------- general coupling
+# The general form of Eq. multislice-modularity: omega^(sr) for any pair of
+# slices (ordinal pairs with their own weights, or categorical: every pair)
+# and a resolution gamma^(s) per slice.  Pinned to the exact-rational dense
+# form, to networkx on the supra-graph (global null model), to the uniform
+# model where the tables are uniform, to the decomposition at a zero
+# coupling, and through brute force and local optimality.
+def coupling_matrix(T, coupling, omega, omegas):
+    """omega^(sr) as exact rationals (T x T)."""
+    w = [[Fraction(0)] * T for _ in range(T)]
+    for s in range(T):
+        for r in range(T):
+            if s == r:
+                continue
+            if coupling == "ordinal" and abs(s - r) != 1:
+                continue
+            if omegas is None:
+                num = omega[0]
+            elif coupling == "ordinal":
+                num = omegas[min(s, r)]
+            else:
+                num = omegas[s * T + r]
+            w[s][r] = Fraction(int(num), omega[1])
+    return w
+
+
+def general_Q_exact(snaps, labels, gammas, W):
+    """(1/2mu) sum_{ijsr} [(A_ijs - gamma_s k_is k_js / 2m_s) delta_sr + delta_ij omega^(sr)]
+    delta(c_is, c_jr), exact rationals; gammas: T Fractions."""
+    A = dense_slices(snaps)
+    T, n = len(A), A[0].shape[0]
+    two_mu = Fraction(0)
+    tot = Fraction(0)
+    for s in range(T):
+        k = A[s].sum(axis=1)
+        m2 = int(k.sum())
+        two_mu += m2
+        for i in range(n):
+            for j in range(n):
+                if labels[s * n + i] != labels[s * n + j]:
+                    continue
+                x = Fraction(int(A[s][i, j]))
+                if m2 > 0:
+                    x -= gammas[s] * int(k[i]) * int(k[j]) / m2
+                tot += x
+        for r in range(T):
+            two_mu += n * W[s][r]
+            for i in range(n):
+                if labels[s * n + i] == labels[r * n + i]:
+                    tot += W[s][r]
+    return tot / two_mu if two_mu else Fraction(0)
+
+
+def rand_general(rng, T, coupling, omega_den):
+    """Random omega numerators (with zeros) in the layout the library takes."""
+    if coupling == "ordinal":
+        return [int(x) for x in rng.integers(0, 5, size=max(T - 1, 0))]
+    M = np.zeros((T, T), dtype=np.int64)
+    for s in range(T):
+        for r in range(s + 1, T):
+            M[s, r] = M[r, s] = int(rng.integers(0, 5))
+    return [int(x) for x in M.ravel()]
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_general_Q_exact_rational(seed):
+    rng = np.random.default_rng(1600 + seed)
+    T = int(rng.integers(1, 5))
+    n = int(rng.integers(2, 6))
+    snaps = synth.random_temporal(n, T, p=0.5, w_max=5, seed=seed, p_empty=0.1)
+    coupling = ["ordinal", "categorical"][seed % 2]
+    omega = rand_rational(rng, lo_num=0)
+    omegas = rand_general(rng, T, coupling, omega[1]) if seed % 3 != 2 else None
+    gammas = [rand_rational(rng) for _ in range(T)] if seed % 4 < 2 else None
+    W = coupling_matrix(T, coupling, omega, omegas)
+    gq = [Fraction(*g) for g in gammas] if gammas else [Fraction(1)] * T
+    for _ in range(3):
+        labels = rng.integers(0, n * T, size=n * T).astype(np.int32)
+        q = oracle.modularity(snaps, labels, (1, 1), omega, coupling=coupling, omegas=omegas, gammas=gammas)
+        want = general_Q_exact(snaps, labels, gq, W)
+        assert q == pytest.approx(float(want), rel=1e-12, abs=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_general_global_Q_equals_networkx(seed):
+    nx = pytest.importorskip("networkx")
+    rng = np.random.default_rng(1700 + seed)
+    T = int(rng.integers(2, 5))
+    n = int(rng.integers(3, 20))
+    snaps = synth.random_temporal(n, T, p=0.3, w_max=6, seed=seed)
+    coupling = ["ordinal", "categorical"][seed % 2]
+    omega = rand_rational(rng, lo_num=1)
+    omegas = rand_general(rng, T, coupling, omega[1]) if seed % 3 else None
+    W = coupling_matrix(T, coupling, omega, omegas)
+    G = nx.Graph()
+    G.add_nodes_from(range(n * T))
+    for s, sn in enumerate(snaps):
+        for i in range(n):
+            for e in range(sn.indptr[i], sn.indptr[i + 1]):
+                if i < int(sn.indices[e]):
+                    G.add_edge(s * n + i, s * n + int(sn.indices[e]), weight=float(sn.weights[e]))
+    for s in range(T):
+        for r in range(s + 1, T):
+            if W[s][r] > 0:
+                for i in range(n):
+                    G.add_edge(s * n + i, r * n + i, weight=float(W[s][r]))
+    for trial in range(3):
+        labels = rng.integers(0, max(1, (n * T) // (trial + 1)), size=n * T).astype(np.int32)
+        q = oracle.modularity(snaps, labels, (3, 2), omega, null="global", coupling=coupling, omegas=omegas)
+        want = nx.community.modularity(G, communities_of(labels), weight="weight", resolution=1.5)
+        assert q == pytest.approx(want, rel=1e-12, abs=1e-14)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_general_move_key_is_scaled_delta_Q(seed):
+    """2(G(v,c) - G(v,a)) / (2mu od 2^64) equals the exact change of the general
+    Q under the quantised resolutions gamma'_s = Lambda_s 2m_s / 2^64,
+    Lambda_s = floor(gamma_s 2^64 / 2m_s)."""
+    rng = np.random.default_rng(1800 + seed)
+    T = int(rng.integers(2, 4))
+    n = int(rng.integers(2, 5))
+    snaps = synth.random_temporal(n, T, p=0.6, w_max=5, seed=seed, p_empty=0.15)
+    coupling = ["ordinal", "categorical"][seed % 2]
+    omega = rand_rational(rng, lo_num=0)
+    omegas = rand_general(rng, T, coupling, omega[1])
+    gammas = [rand_rational(rng) for _ in range(T)]
+    W = coupling_matrix(T, coupling, omega, omegas)
+    m2 = [int(sn.weights.sum()) for sn in snaps]
+    gq = [Fraction(((g[0] << 64) // (g[1] * m)) * m, 1 << 64) if m else Fraction(0) for g, m in zip(gammas, m2)]
+    two_mu = Fraction(sum(m2)) + sum(n * W[s][r] for s in range(T) for r in range(T))
+    if two_mu == 0:
+        return
+    N = n * T
+    labels = rng.integers(0, max(2, N // 2), size=N).astype(np.int32)
+    base = general_Q_exact(snaps, labels, gq, W)
+    kw = dict(coupling=coupling, omegas=omegas, gammas=gammas)
+    for _ in range(6):
+        v = int(rng.integers(0, N))
+        a = int(labels[v])
+        choices = [int(x) for x in set(labels.tolist())] + [-1]
+        c = choices[int(rng.integers(0, len(choices)))]
+        new = labels.copy()
+        new[v] = c if c >= 0 else N + 7
+        after = general_Q_exact(snaps, new, gq, W)
+        Gc = oracle.move_key(snaps, labels, v, c, (1, 1), omega, **kw)
+        Ga = oracle.move_key(snaps, labels, v, a, (1, 1), omega, **kw)
+        assert Fraction(2 * (Gc - Ga), 1) / (two_mu * omega[1] * (1 << 64)) == after - base
+
+
+def test_uniform_tables_reduce_to_the_uniform_model():
+    """Tables that hold the uniform values give the uniform solve: identical
+    labels and counters, Q equal up to the order of the FP64 sum."""
+    snaps, _ = synth.planted_partition_temporal(90, 4, n_blocks=3, p_in=0.25, p_out=0.03, switch_frac=0.1, w_max=4,
+                                                seed=2)
+    ref, Qr, sr = oracle.leiden(snaps, (3, 2), (1, 2))
+    for kw in (dict(omegas=[1, 1, 1]), dict(gammas=[(3, 2)] * 4), dict(omegas=[1, 1, 1], gammas=[(6, 4)] * 4)):
+        lab, Q, st = oracle.leiden(snaps, (3, 2), (1, 2), **kw)
+        assert np.array_equal(lab, ref), kw
+        assert Q == pytest.approx(Qr, rel=1e-14)
+        assert st["lm_edges"] == sr["lm_edges"] and st["lm_moves"] == sr["lm_moves"]
+    # T = 2: categorical coupling is the ordinal one
+    two = snaps[:2]
+    a = oracle.leiden(two, (1, 1), (2, 1))
+    b = oracle.leiden(two, (1, 1), (2, 1), coupling="categorical")
+    assert np.array_equal(a[0], b[0]) and a[1] == b[1]
+
+
+def test_zero_coupling_splits_the_objective():
+    """With omega^(1,2) = 0 (T = 4, ordinal) and no community crossing that
+    cut, 2mu Q = 2mu_a Q_a + 2mu_b Q_b for the two halves."""
+    snaps = synth.random_temporal(12, 4, p=0.3, w_max=4, seed=5)
+    rng = np.random.default_rng(9)
+    omegas = [3, 0, 2]
+    n = 12
+    for _ in range(4):
+        la = rng.integers(0, 10, size=2 * n).astype(np.int32)
+        lb = (rng.integers(0, 10, size=2 * n) + 10).astype(np.int32)
+        labels = np.concatenate([la, lb])
+        q = oracle.modularity(snaps, labels, (1, 1), (1, 2), omegas=omegas)
+        qa = oracle.modularity(snaps[:2], la, (1, 1), (3, 2))
+        qb = oracle.modularity(snaps[2:], lb - 10, (1, 1), (2, 2))
+        ma = sum(int(s.weights.sum()) for s in snaps[:2]) + 2 * n * 1.5
+        mb = sum(int(s.weights.sum()) for s in snaps[2:]) + 2 * n * 1.0
+        assert q == pytest.approx((ma * qa + mb * qb) / (ma + mb), rel=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_general_bruteforce_bound_and_local_optimum(seed):
+    rng = np.random.default_rng(1900 + seed)
+    T = int(rng.integers(2, 4))
+    n = 3 if T == 3 else int(rng.integers(3, 5))
+    snaps = synth.random_temporal(n, T, p=0.5, w_max=3, seed=seed)
+    coupling = ["ordinal", "categorical"][seed % 2]
+    omegas = rand_general(rng, T, coupling, 2)
+    gammas = [rand_rational(rng) for _ in range(T)] if seed % 3 else None
+    kw = dict(coupling=coupling, omegas=omegas, gammas=gammas)
+    N = n * T
+    best = max(oracle.modularity(snaps, np.array(part, np.int32), (1, 1), (1, 2), **kw) for part in set_partitions(N))
+    labels, Q, st = oracle.leiden(snaps, (1, 1), (1, 2), n_iterations=20, **kw)
+    assert Q <= best + 1e-12
+    assert Q == pytest.approx(oracle.modularity(snaps, labels, (1, 1), (1, 2), **kw), rel=1e-15)
+    if st["last_level0_moves"] == 0:
+        assert oracle.count_improving(snaps, labels, (1, 1), (1, 2), **kw) == 0
+
+
+def test_general_converged_invariants():
+    hits = 0
+    for seed in range(6):
+        rng = np.random.default_rng(seed + 40)
+        T = int(rng.integers(2, 6))
+        snaps, _ = synth.planted_partition_temporal(int(rng.integers(20, 70)), T, n_blocks=3, p_in=0.25, p_out=0.04,
+                                                    switch_frac=0.1, w_max=4, seed=seed)
+        coupling = ["ordinal", "categorical"][seed % 2]
+        kw = dict(coupling=coupling, omegas=rand_general(rng, T, coupling, 3),
+                  gammas=[rand_rational(rng) for _ in range(T)])
+        labels, Q, st = oracle.leiden(snaps, (1, 1), (1, 3), n_iterations=30, **kw)
+        if st["last_level0_moves"] == 0:
+            assert oracle.count_improving(snaps, labels, (1, 1), (1, 3), **kw) == 0
+            hits += 1
+    assert hits >= 4
+
+
+def test_general_validation():
+    snaps = synth.random_temporal(6, 3, p=0.5, seed=1)
+    M = [0, 1, 2, 1, 0, 1, 3, 1, 0]  # (0,2) = 2 but (2,0) = 3
+    with pytest.raises(oracle.OracleError):
+        oracle.leiden(snaps, coupling="categorical", omegas=M)
+    with pytest.raises(oracle.OracleError):
+        oracle.leiden(snaps, coupling="categorical", omegas=[1, 1, 1, 1, 0, 1, 1, 1, 0])  # diagonal
+    with pytest.raises(oracle.OracleError):
+        oracle.leiden(snaps, omegas=[1, -1])
+    with pytest.raises(oracle.OracleError):
+        oracle.leiden(snaps, gammas=[(1, 1), (0, 1), (1, 1)])
+    with pytest.raises(oracle.OracleError):
+        oracle.leiden(snaps, gammas=[(1, 1)] * 3, null="global")
+    with pytest.raises(oracle.OracleError):
+        oracle.leiden(snaps, coupling=7)
+    oracle.leiden(snaps, coupling="categorical", omegas=[0, 1, 2, 1, 0, 1, 2, 1, 0])  # symmetric: accepted
+    # the bound takes the largest gamma_s
+    sn = synth.Snapshot(snaps[0].indptr, snaps[0].indices, np.full(snaps[0].nnz, 2 ** 30, np.int32))
+    big = [sn] * 3
+    sum2m = 3 * sn.nnz * 2 ** 30
+    g = -(-(2 ** 61) // sum2m)
+    oracle.leiden(big, (1, 1), (1, 1), gammas=[(1, 1), (g - 1, 1), (1, 1)], n_iterations=1, max_rounds=1,
+                  max_levels=1)
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.leiden(big, (1, 1), (1, 1), gammas=[(1, 1), (g, 1), (1, 1)])
+    assert e.value.code == oracle.EOVERFLOW
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_general_global_move_key_and_bruteforce(seed):
+    """Global null model with general coupling: the key's differences are the
+    exact change of the supra-graph's modularity (k' including every coupling
+    weight), and Leiden's Q is bounded by brute force."""
+    rng = np.random.default_rng(2000 + seed)
+    T = int(rng.integers(2, 4))
+    n = 3 if T == 3 else int(rng.integers(3, 5))
+    snaps = synth.random_temporal(n, T, p=0.5, w_max=4, seed=seed)
+    coupling = ["ordinal", "categorical"][seed % 2]
+    omega = (1, 2)
+    omegas = rand_general(rng, T, coupling, 2)
+    kw = dict(null="global", coupling=coupling, omegas=omegas)
+    W = coupling_matrix(T, coupling, omega, omegas)
+    two_mu = Fraction(sum(int(sn.weights.sum()) for sn in snaps)) + sum(n * W[s][r] for s in range(T)
+                                                                         for r in range(T))
+    twoM = int(two_mu * omega[1])
+    gamma = (3, 2)
+    gq = Fraction(((gamma[0] << 64) // (gamma[1] * twoM)) * twoM, 1 << 64)
+
+    def exact(lab):
+        A = dense_slices(snaps)
+        N = n * T
+        B = [[Fraction(0)] * N for _ in range(N)]
+        for s in range(T):
+            for i in range(n):
+                for j in range(n):
+                    B[s * n + i][s * n + j] = Fraction(int(A[s][i, j]))
+                for r in range(T):
+                    B[s * n + i][r * n + i] += W[s][r]
+        k = [sum(row) for row in B]
+        tot = sum(B[a][b] - gq * k[a] * k[b] / two_mu for a in range(N) for b in range(N) if lab[a] == lab[b])
+        return tot / two_mu
+
+    N = n * T
+    labels = rng.integers(0, max(2, N // 2), size=N).astype(np.int32)
+    base = exact(labels)
+    for _ in range(4):
+        v = int(rng.integers(0, N))
+        choices = [int(x) for x in set(labels.tolist())] + [-1]
+        c = choices[int(rng.integers(0, len(choices)))]
+        new = labels.copy()
+        new[v] = c if c >= 0 else N + 7
+        Gc = oracle.move_key(snaps, labels, v, c, gamma, omega, **kw)
+        Ga = oracle.move_key(snaps, labels, v, int(labels[v]), gamma, omega, **kw)
+        assert Fraction(2 * (Gc - Ga), 1) / (two_mu * omega[1] * (1 << 64)) == exact(new) - base
+    best = max(oracle.modularity(snaps, np.array(p, np.int32), gamma, omega, **kw) for p in set_partitions(N))
+    lab, Q, st = oracle.leiden(snaps, gamma, omega, n_iterations=20, **kw)
+    assert Q <= best + 1e-12
+    if st["last_level0_moves"] == 0:
+        assert oracle.count_improving(snaps, lab, gamma, omega, **kw) == 0
