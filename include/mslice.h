@@ -80,8 +80,30 @@ typedef struct {
 } mslice_csr;
 
 /* Coupling between snapshots (Eq. multislice-modularity, omega^(sr)):
- * ORDINAL links (i,s) and (i,s+1) with weight omega. */
-typedef enum { MSLICE_ORDINAL = 0 } mslice_coupling;
+ * ORDINAL links (i,s) and (i,s+1) (Eq. supra-adjacency); CATEGORICAL links
+ * (i,s) and (i,r) for every r != s (needs T*T < 2^31).  The weights are
+ * omega (uniform), or per pair through mslice_general. */
+typedef enum { MSLICE_ORDINAL = 0, MSLICE_CATEGORICAL = 1 } mslice_coupling;
+
+/* The general form of Eq. multislice-modularity for one solve (host arrays,
+ * read during the call; every pointer nullable).
+ *   omega_num: numerators of omega^(sr) over the call's omega_den, each in
+ *              [0, 2^31], one per coupling slot of the handle's pattern:
+ *              ORDINAL T-1 slots, slot s for the pair (s, s+1); CATEGORICAL
+ *              a T*T row-major matrix, symmetric with a zero diagonal.  A
+ *              pair of weight 0 is not an edge.  NULL: omega for every pair.
+ *   gamma_num, gamma_den: both or neither; T per-snapshot resolutions
+ *              gamma^(s), each a rational in (0, 2^31]/[1, 2^31].  NULL:
+ *              gamma for every snapshot.  Not with MSLICE_NULL_GLOBAL (one
+ *              null term, one resolution).
+ * Keys use Lambda_s = floor(gamma^(s) 2^64 / 2m_s); the bound becomes
+ * omega_den*sum 2m_s + n*sum_{s,r} omega_num^(sr) < 2^61 and
+ * gamma^(s)*omega_den*sum 2m_s < 2^61 for every s (EOVERFLOW). */
+typedef struct {
+  const int64_t* omega_num;
+  const int64_t* gamma_num;
+  const int64_t* gamma_den;
+} mslice_general;
 
 typedef struct mslice_graph* mslice_handle;
 
@@ -174,6 +196,13 @@ int mslice_leiden(mslice_handle h, int64_t gamma_num, int64_t gamma_den, int64_t
 int mslice_leiden_ex(mslice_handle h, const mslice_opts* o, const int32_t* init_labels,
                      int32_t* labels_out, double* Q_out, mslice_stats* st);
 
+/* As mslice_leiden_ex with the general form gen (nullable: the uniform
+ * model).  Q_out is Q_MS with the tables' omega^(sr) and gamma^(s).  Errors:
+ * EINVAL (bad tables, or per-snapshot gamma with MSLICE_NULL_GLOBAL), as
+ * mslice_leiden_ex otherwise. */
+int mslice_leiden_general(mslice_handle h, const mslice_opts* o, const mslice_general* gen,
+                          const int32_t* init_labels, int32_t* labels_out, double* Q_out, mslice_stats* st);
+
 /* Q_MS (Eq. multislice-modularity, ordinal coupling) of int32[N] labels in
  * [0, N) (host pointer).  Errors: EINVAL, EOVERFLOW, ENOMEM, ECUDA. */
 int mslice_modularity(mslice_handle h, const int32_t* labels, int64_t gamma_num, int64_t gamma_den,
@@ -183,6 +212,12 @@ int mslice_modularity(mslice_handle h, const int32_t* labels, int64_t gamma_num,
  * MSLICE_NULL_GLOBAL for the supra-graph's plain modularity instead of Q_MS. */
 int mslice_modularity_ex(mslice_handle h, const int32_t* labels, int64_t gamma_num, int64_t gamma_den,
                          int64_t omega_num, int64_t omega_den, int32_t flags, double* Q_out);
+
+/* Q of int32[N] labels in [0, N) under the general form gen (nullable); o
+ * gives gamma, omega and flags (MSLICE_DEVICE_PTRS, MSLICE_NULL_GLOBAL; o
+ * nullable: the defaults).  Errors as mslice_modularity_ex. */
+int mslice_modularity_general(mslice_handle h, const int32_t* labels, const mslice_opts* o,
+                              const mslice_general* gen, double* Q_out);
 
 /* Q_MS of int32[N] labels in [0, N), read straight from device snapshot
  * arrays, for callers that cannot allocate device memory: code that runs
@@ -243,6 +278,13 @@ int mslice_batch_create(int32_t flags, void* stream, mslice_batch* out);
  * EOVERFLOW (the bound of the conventions for this graph, gamma and omega). */
 int mslice_batch_add(mslice_batch b, mslice_handle g, int64_t gamma_num, int64_t gamma_den, int64_t omega_num,
                      int64_t omega_den, const int32_t* init_labels, int32_t* index_out);
+
+/* As mslice_batch_add with the general form gen (nullable) for this
+ * instance; its tables are copied during the call.  Instances of one batch
+ * may mix coupling patterns, tables and uniform parameters. */
+int mslice_batch_add_general(mslice_batch b, mslice_handle g, int64_t gamma_num, int64_t gamma_den,
+                             int64_t omega_num, int64_t omega_den, const mslice_general* gen,
+                             const int32_t* init_labels, int32_t* index_out);
 
 /* Solves every instance.  o: schedule options shared by all instances
  * (n_iterations, K, max_rounds, max_levels, seed; MSLICE_PROFILE,

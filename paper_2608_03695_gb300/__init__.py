@@ -36,10 +36,13 @@ MSLICE_AUTOTUNE = 4
 MSLICE_NULL_GLOBAL = 8
 _NULLS = {"multislice": 0, "global": MSLICE_NULL_GLOBAL}
 MSLICE_ORDINAL = 0
+MSLICE_CATEGORICAL = 1
+_COUPLINGS = {"ordinal": MSLICE_ORDINAL, "categorical": MSLICE_CATEGORICAL}
 
 # every symbol include/mslice.h declares
 EXPORTS = ["mslice_default_opts", "mslice_build", "mslice_build_ex", "mslice_leiden", "mslice_leiden_ex",
-           "mslice_modularity", "mslice_modularity_ex", "mslice_modularity_noalloc", "mslice_info",
+           "mslice_leiden_general", "mslice_modularity", "mslice_modularity_ex", "mslice_modularity_general",
+           "mslice_modularity_noalloc", "mslice_info", "mslice_batch_add_general",
            "mslice_kernel_launches", "mslice_free", "mslice_last_error", "mslice_batch_create",
            "mslice_batch_add", "mslice_batch_run", "mslice_batch_results", "mslice_batch_info",
            "mslice_batch_clear", "mslice_batch_kernel_launches", "mslice_batch_free",
@@ -116,6 +119,9 @@ def lib():
         L.mslice_build_ex.argtypes = [P, C.c_int32, C.c_int, C.c_int64, C.c_int64, C.c_int32, P, P]
         L.mslice_leiden.argtypes = [P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_uint64, P, P]
         L.mslice_leiden_ex.argtypes = [P, P, P, P, P, P]
+        L.mslice_leiden_general.argtypes = [P, P, P, P, P, P, P]
+        L.mslice_modularity_general.argtypes = [P, P, P, P, P]
+        L.mslice_batch_add_general.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, P, P, P]
         L.mslice_modularity.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, P]
         L.mslice_modularity_ex.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int32, P]
         L.mslice_modularity_noalloc.argtypes = [P, C.c_int32, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, P, P]
@@ -148,6 +154,39 @@ def lib():
         L.mslice_server_window_restore.argtypes = [P, C.c_int32, P, C.c_int32, P]
         _lib = L
     return _lib
+
+
+class General(C.Structure):
+    """``mslice_general``: per-pair omega numerators and per-snapshot gamma."""
+    _fields_ = [("omega_num", C.c_void_p), ("gamma_num", C.c_void_p), ("gamma_den", C.c_void_p)]
+
+
+class _Gen:
+    """Marshals ``omegas`` (omega^(sr) numerators over the call's omega
+    denominator, in the handle's slot layout: T-1 for ordinal coupling, a
+    T x T matrix for categorical) and ``gammas`` (T (num, den) pairs); None
+    when neither is given."""
+
+    def __init__(self, omegas=None, gammas=None):
+        self.arrays = []
+        self.struct = None
+        if omegas is None and gammas is None:
+            return
+        g = General(None, None, None)
+        if omegas is not None:
+            om = np.ascontiguousarray(np.asarray(omegas, dtype=np.int64).ravel())
+            self.arrays.append(om)
+            g.omega_num = om.ctypes.data
+        if gammas is not None:
+            gn = np.ascontiguousarray([int(x[0]) for x in gammas], dtype=np.int64)
+            gd = np.ascontiguousarray([int(x[1]) for x in gammas], dtype=np.int64)
+            self.arrays += [gn, gd]
+            g.gamma_num, g.gamma_den = gn.ctypes.data, gd.ctypes.data
+        self.struct = g
+
+    @property
+    def ptr(self):
+        return C.byref(self.struct) if self.struct is not None else None
 
 
 def _check(rc, what):
@@ -208,11 +247,12 @@ class Handle:
 
     def mslice_leiden(self, gamma=(1, 1), omega=(1, 1), max_levels=32, seed=0, n_iterations=2, K=4,
                       max_rounds=100, init=None, stop_level=-1, stop_stage=0, stop_rounds=0, out=None,
-                      profile=False, tier_cuts=None, autotune=False, null="multislice"):
+                      profile=False, tier_cuts=None, autotune=False, null="multislice", omegas=None, gammas=None):
         """Returns (labels, Q, stats).  With ``out`` a device tensor (int32[N])
         the labels stay on the device (MSLICE_DEVICE_PTRS); ``init`` may then
         be a device tensor as well.  ``null="global"`` optimises the plain
-        modularity of the supra-graph instead of Q_MS (MSLICE_NULL_GLOBAL)."""
+        modularity of the supra-graph instead of Q_MS (MSLICE_NULL_GLOBAL).
+        ``omegas`` / ``gammas``: the general form (mslice_leiden_general)."""
         o = default_opts()
         o.gamma_num, o.gamma_den = gamma
         o.omega_num, o.omega_den = omega
@@ -234,20 +274,30 @@ class Handle:
             init_a = np.ascontiguousarray(init, dtype=np.int32)
         Q = C.c_double(0.0)
         st = Stats()
-        _check(lib().mslice_leiden_ex(self._h, C.byref(o), _ptr(init_a), _ptr(labels), C.byref(Q), C.byref(st)),
-               "mslice_leiden_ex")
+        gen = _Gen(omegas, gammas)
+        _check(lib().mslice_leiden_general(self._h, C.byref(o), gen.ptr, _ptr(init_a), _ptr(labels), C.byref(Q),
+                                           C.byref(st)), "mslice_leiden_general")
         stats = _stats_dict(st)
         if out is not None:
             return labels, Q.value, stats
         return labels[: st.out_n].copy(), Q.value, stats
 
-    def mslice_modularity(self, labels, gamma=(1, 1), omega=(1, 1), null="multislice"):
+    def mslice_modularity(self, labels, gamma=(1, 1), omega=(1, 1), null="multislice", omegas=None, gammas=None):
         dev = hasattr(labels, "is_cuda") and labels.is_cuda
         lab = labels if dev else np.ascontiguousarray(labels, dtype=np.int32)
         Q = C.c_double(0.0)
         flags = (MSLICE_DEVICE_PTRS if dev else 0) | _NULLS[null]
-        _check(lib().mslice_modularity_ex(self._h, _ptr(lab), gamma[0], gamma[1], omega[0], omega[1], flags,
-                                          C.byref(Q)), "mslice_modularity_ex")
+        if omegas is None and gammas is None:
+            _check(lib().mslice_modularity_ex(self._h, _ptr(lab), gamma[0], gamma[1], omega[0], omega[1], flags,
+                                              C.byref(Q)), "mslice_modularity_ex")
+            return Q.value
+        o = default_opts()
+        o.gamma_num, o.gamma_den = gamma
+        o.omega_num, o.omega_den = omega
+        o.flags = flags
+        gen = _Gen(omegas, gammas)
+        _check(lib().mslice_modularity_general(self._h, _ptr(lab), C.byref(o), gen.ptr, C.byref(Q)),
+               "mslice_modularity_general")
         return Q.value
 
     # short aliases
@@ -286,13 +336,19 @@ class Batch:
     def __exit__(self, *a):
         self.close()
 
-    def mslice_batch_add(self, graph: "Handle", gamma=(1, 1), omega=(1, 1), init=None) -> int:
+    def mslice_batch_add(self, graph: "Handle", gamma=(1, 1), omega=(1, 1), init=None, omegas=None,
+                         gammas=None) -> int:
         init_a = init
         if init is not None and not hasattr(init, "data_ptr"):
             init_a = np.ascontiguousarray(init, dtype=np.int32)
         idx = C.c_int32(-1)
-        _check(lib().mslice_batch_add(self._b, graph._h, gamma[0], gamma[1], omega[0], omega[1], _ptr(init_a),
-                                      C.byref(idx)), "mslice_batch_add")
+        if omegas is None and gammas is None:
+            _check(lib().mslice_batch_add(self._b, graph._h, gamma[0], gamma[1], omega[0], omega[1], _ptr(init_a),
+                                          C.byref(idx)), "mslice_batch_add")
+        else:
+            gen = _Gen(omegas, gammas)
+            _check(lib().mslice_batch_add_general(self._b, graph._h, gamma[0], gamma[1], omega[0], omega[1],
+                                                  gen.ptr, _ptr(init_a), C.byref(idx)), "mslice_batch_add_general")
         self._graphs.append(graph)
         return idx.value
 
@@ -460,11 +516,13 @@ class Server:
     restore = mslice_server_restore
 
 
-def mslice_build(snaps, omega=(1, 1), stream=None, device_ptrs=False, host_tensors=False) -> Handle:
+def mslice_build(snaps, omega=(1, 1), stream=None, device_ptrs=False, host_tensors=False,
+                 coupling="ordinal") -> Handle:
     """Builds a handle from T snapshots.  ``snaps`` holds objects with
     ``indptr``/``indices``/``weights`` arrays: numpy host arrays, torch host
     tensors (``host_tensors=True``, e.g. pinned memory) or torch device
-    tensors (``device_ptrs=True``)."""
+    tensors (``device_ptrs=True``).  ``coupling``: "ordinal" (adjacent
+    snapshots) or "categorical" (every pair of snapshots)."""
     T = len(snaps)
     arr = (Csr * max(T, 1))()
     keep = []
@@ -482,7 +540,7 @@ def mslice_build(snaps, omega=(1, 1), stream=None, device_ptrs=False, host_tenso
                      _ptr(w).value if _ptr(w) is not None else None)
     h = C.c_void_p()
     st = C.c_void_p(stream) if stream is not None else None
-    _check(lib().mslice_build_ex(C.cast(arr, C.c_void_p), T, MSLICE_ORDINAL, omega[0], omega[1],
+    _check(lib().mslice_build_ex(C.cast(arr, C.c_void_p), T, _COUPLINGS[coupling], omega[0], omega[1],
                                  MSLICE_DEVICE_PTRS if device_ptrs else 0, st, C.byref(h)), "mslice_build_ex")
     return Handle(h, keep)
 

@@ -320,6 +320,39 @@ void check_opts(const mslice_opts& opt) {
   }
 }
 
+// The instance parameters of a solve on graph G: the uniform rationals and,
+// when gen gives them, the validated tables (EINVAL for bad ones).
+InstParams inst_params(const SupraGraph& G, int64_t gn, int64_t gd, int64_t on, int64_t od, const mslice_general* gen,
+                       bool global_null) {
+  if (!rational_ok(gn, gd, false)) fail(MSLICE_EINVAL, "gamma must be a rational > 0");
+  if (!rational_ok(on, od, true)) fail(MSLICE_EINVAL, "omega must be a rational >= 0");
+  InstParams j{gn, gd, on, od};
+  if (!gen) return j;
+  const int32_t T = G.T;
+  if (gen->omega_num) {
+    const int64_t slots = coupling_slots(G.coupling, T);
+    j.cw.assign(gen->omega_num, gen->omega_num + slots);
+    for (long long x : j.cw)
+      if (!rational_ok(x, od, true)) fail(MSLICE_EINVAL, "omega^(sr) numerators must lie in [0, 2^31]");
+    if (G.coupling != 0)
+      for (int32_t s = 0; s < T; ++s) {
+        if (j.cw[(int64_t)s * T + s] != 0) fail(MSLICE_EINVAL, "categorical omega^(ss) must be 0");
+        for (int32_t r = 0; r < s; ++r)
+          if (j.cw[(int64_t)s * T + r] != j.cw[(int64_t)r * T + s])
+            fail(MSLICE_EINVAL, "categorical omega^(sr) must be symmetric");
+      }
+  }
+  if (gen->gamma_num || gen->gamma_den) {
+    if (!gen->gamma_num || !gen->gamma_den) fail(MSLICE_EINVAL, "gamma_num and gamma_den go together");
+    if (global_null) fail(MSLICE_EINVAL, "per-snapshot gamma does not apply to the global null model");
+    j.gsn.assign(gen->gamma_num, gen->gamma_num + T);
+    j.gsd.assign(gen->gamma_den, gen->gamma_den + T);
+    for (int32_t s = 0; s < T; ++s)
+      if (!rational_ok(j.gsn[s], j.gsd[s], false)) fail(MSLICE_EINVAL, "gamma^(s) must be rationals > 0");
+  }
+  return j;
+}
+
 TierCuts cuts_of(const mslice_opts& opt) {
   TierCuts c;
   const int32_t* t = opt.tier_cuts;
@@ -413,7 +446,7 @@ int mslice_build_ex(const mslice_csr* slices, int32_t T, mslice_coupling cpl, in
     if (!out) fail(MSLICE_EINVAL, "null output handle");
     *out = nullptr;
     if (!slices || T < 1) fail(MSLICE_EINVAL, "need T >= 1 snapshots");
-    if (cpl != MSLICE_ORDINAL) fail(MSLICE_EINVAL, "unsupported coupling");
+    if (cpl != MSLICE_ORDINAL && cpl != MSLICE_CATEGORICAL) fail(MSLICE_EINVAL, "unsupported coupling");
     if (!rational_ok(omega_num, omega_den, true)) fail(MSLICE_EINVAL, "omega must be a rational >= 0");
     const int64_t n = slices[0].n;
     if (n < 0 || n > INT32_MAX || n * (int64_t)T > INT32_MAX) fail(MSLICE_EINVAL, "n*T must fit in int32");
@@ -481,7 +514,7 @@ int mslice_build_ex(const mslice_csr* slices, int32_t T, mslice_coupling cpl, in
         wt[s] = dwt;
       }
     }
-    build_supra(c, ip, ix, wt, nnz, n, h->G);
+    build_supra(c, ip, ix, wt, nnz, n, h->G, (int32_t)cpl);
     h->launches += c.launches;
     // staged host copies are not needed after the build
     if (!dev)
@@ -520,19 +553,23 @@ int64_t mslice_kernel_launches(mslice_handle h) { return h ? h->launches : -1; }
 
 int mslice_leiden_ex(mslice_handle h, const mslice_opts* o, const int32_t* init_labels, int32_t* labels_out,
                      double* Q_out, mslice_stats* st) {
+  return mslice_leiden_general(h, o, nullptr, init_labels, labels_out, Q_out, st);
+}
+
+int mslice_leiden_general(mslice_handle h, const mslice_opts* o, const mslice_general* gen, const int32_t* init_labels,
+                          int32_t* labels_out, double* Q_out, mslice_stats* st) {
   return guard([&] {
     if (!h) fail(MSLICE_EINVAL, "null handle");
     mslice_opts opt;
     mslice_default_opts(&opt);
     if (o) opt = *o;
     check_opts(opt);
-    if (!rational_ok(opt.gamma_num, opt.gamma_den, false)) fail(MSLICE_EINVAL, "gamma must be a rational > 0");
-    if (!rational_ok(opt.omega_num, opt.omega_den, true)) fail(MSLICE_EINVAL, "omega must be a rational >= 0");
+    const bool global = (opt.flags & MSLICE_NULL_GLOBAL) != 0;
+    const SupraGraph& G = h->G;
+    const InstParams job = inst_params(G, opt.gamma_num, opt.gamma_den, opt.omega_num, opt.omega_den, gen, global);
     if (!labels_out && h->G.N > 0) fail(MSLICE_EINVAL, "null labels_out");
     const bool dev = (opt.flags & MSLICE_DEVICE_PTRS) != 0;
-    const SupraGraph& G = h->G;
-    check_bounds(G.n, G.T, G.two_m_host.data(), opt.gamma_num, opt.gamma_den, opt.omega_num, opt.omega_den,
-                 (opt.flags & MSLICE_NULL_GLOBAL) != 0);
+    check_bounds(G.n, G.T, G.coupling, G.two_m_host.data(), job, global);
     const int64_t N0 = G.N;
     Ctx c = h->ctx();
     const int32_t* init = nullptr;
@@ -549,8 +586,7 @@ int mslice_leiden_ex(mslice_handle h, const mslice_opts* o, const int32_t* init_
     mslice_stats stats;
     RunOut ro;
     Solver S;
-    run_solve(c, G, {InstParams{opt.gamma_num, opt.gamma_den, opt.omega_num, opt.omega_den}}, opt, init, out, S, ro,
-              stats);
+    run_solve(c, G, {job}, opt, init, out, S, ro, stats);
     if (!dev && ro.out_n > 0) {
       check_cuda(cudaMemcpyAsync(labels_out, out, ro.out_n * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream),
                  "copy");
@@ -577,21 +613,36 @@ int mslice_leiden(mslice_handle h, int64_t gamma_num, int64_t gamma_den, int64_t
 
 int mslice_modularity_ex(mslice_handle h, const int32_t* labels, int64_t gamma_num, int64_t gamma_den,
                          int64_t omega_num, int64_t omega_den, int32_t flags, double* Q_out) {
+  mslice_opts o;
+  mslice_default_opts(&o);
+  o.gamma_num = gamma_num;
+  o.gamma_den = gamma_den;
+  o.omega_num = omega_num;
+  o.omega_den = omega_den;
+  o.flags = flags;
+  return mslice_modularity_general(h, labels, &o, nullptr, Q_out);
+}
+
+int mslice_modularity_general(mslice_handle h, const int32_t* labels, const mslice_opts* o, const mslice_general* gen,
+                              double* Q_out) {
   return guard([&] {
     if (!h) fail(MSLICE_EINVAL, "null handle");
-    if (!rational_ok(gamma_num, gamma_den, false)) fail(MSLICE_EINVAL, "gamma must be a rational > 0");
-    if (!rational_ok(omega_num, omega_den, true)) fail(MSLICE_EINVAL, "omega must be a rational >= 0");
+    mslice_opts opt;
+    mslice_default_opts(&opt);
+    if (o) opt = *o;
+    const int32_t flags = opt.flags;
     const SupraGraph& G = h->G;
-    if (!labels && G.N > 0) fail(MSLICE_EINVAL, "null labels");
     const bool global = (flags & MSLICE_NULL_GLOBAL) != 0;
-    check_bounds(G.n, G.T, G.two_m_host.data(), gamma_num, gamma_den, omega_num, omega_den, global);
+    const InstParams job = inst_params(G, opt.gamma_num, opt.gamma_den, opt.omega_num, opt.omega_den, gen, global);
+    if (!labels && G.N > 0) fail(MSLICE_EINVAL, "null labels");
+    check_bounds(G.n, G.T, G.coupling, G.two_m_host.data(), job, global);
     Ctx c = h->ctx();
     Solver S;
     S.c = &c;
     S.G0 = &G;
     S.N0 = G.N;
     S.p.global_null = global;
-    set_instances(c, S, {InstParams{gamma_num, gamma_den, omega_num, omega_den}});
+    set_instances(c, S, {job});
     setup_null_model(S);
     const int64_t N = G.N > 0 ? G.N : 1;
     S.sig_used = h->ws.get<ull>("m_used", 1);
@@ -643,12 +694,17 @@ int mslice_batch_create(int32_t flags, void* stream, mslice_batch* out) {
 
 int mslice_batch_add(mslice_batch b, mslice_handle g, int64_t gamma_num, int64_t gamma_den, int64_t omega_num,
                      int64_t omega_den, const int32_t* init_labels, int32_t* index_out) {
+  return mslice_batch_add_general(b, g, gamma_num, gamma_den, omega_num, omega_den, nullptr, init_labels, index_out);
+}
+
+int mslice_batch_add_general(mslice_batch b, mslice_handle g, int64_t gamma_num, int64_t gamma_den,
+                             int64_t omega_num, int64_t omega_den, const mslice_general* gen,
+                             const int32_t* init_labels, int32_t* index_out) {
   return guard([&] {
     if (!b || !g) fail(MSLICE_EINVAL, "null batch or graph");
-    if (!rational_ok(gamma_num, gamma_den, false)) fail(MSLICE_EINVAL, "gamma must be a rational > 0");
-    if (!rational_ok(omega_num, omega_den, true)) fail(MSLICE_EINVAL, "omega must be a rational >= 0");
     const SupraGraph& G = g->G;
-    check_bounds(G.n, G.T, G.two_m_host.data(), gamma_num, gamma_den, omega_num, omega_den);
+    const InstParams job = inst_params(G, gamma_num, gamma_den, omega_num, omega_den, gen, false);
+    check_bounds(G.n, G.T, G.coupling, G.two_m_host.data(), job, false);
     const int64_t N = G.N;
     if (b->off.back() + N > INT32_MAX) fail(MSLICE_EINVAL, "the batch must hold fewer than 2^31 supra-nodes");
     if ((int64_t)b->graphs.size() >= INT32_MAX) fail(MSLICE_EINVAL, "too many instances");
@@ -666,7 +722,7 @@ int mslice_batch_add(mslice_batch b, mslice_handle g, int64_t gamma_num, int64_t
     b->init.insert(b->init.end(), lab.begin(), lab.end());
     b->any_init = b->any_init || init_labels != nullptr;
     b->graphs.push_back(g);
-    b->jobs.push_back(InstParams{gamma_num, gamma_den, omega_num, omega_den});
+    b->jobs.push_back(job);
     b->off.push_back(b->off.back() + N);
     b->solved = false;
     if (index_out) *index_out = (int32_t)b->graphs.size() - 1;
@@ -686,7 +742,8 @@ int mslice_batch_run(mslice_batch b, const mslice_opts* o, mslice_stats* st) {
       for (size_t i = 0; i < b->graphs.size(); ++i) {
         const SupraGraph& Gi = b->graphs[i]->G;
         const InstParams& j = b->jobs[i];
-        check_bounds(Gi.n, Gi.T, Gi.two_m_host.data(), j.gn, j.gd, j.on, j.od, true);
+        if (!j.gsn.empty()) fail(MSLICE_EINVAL, "per-snapshot gamma does not apply to the global null model");
+        check_bounds(Gi.n, Gi.T, Gi.coupling, Gi.two_m_host.data(), j, true);
       }
     Ctx c = b->ctx();
     std::vector<uint64_t> serials;

@@ -1,10 +1,16 @@
 // Supra-graph builder (Eq. supra-adjacency): the level-0 CSR over N = n*T
 // supra-nodes.  Row v = s*n + i holds, in ascending column order, the
-// coupling entry to v-n (s > 0), the snapshot-s row of i shifted by s*n, and
-// the coupling entry to v+n (s < T-1).  Entries are 8-byte {col, w} pairs;
-// w = 0 flags a coupling entry, so the coupling weight omega is applied at
-// solve time and an omega sweep needs no rebuild.
+// coupling entries to the copies of i in earlier snapshots, the snapshot-s row
+// of i shifted by s*n, and the coupling entries to later copies.  Ordinal
+// coupling (Eq. supra-adjacency) couples s with s-1 and s+1; categorical
+// coupling (the all-pairs omega^(sr) of Eq. multislice-modularity) with every
+// other snapshot.  Entries are 8-byte {col, w} pairs; w <= 0 flags a coupling
+// entry and names its pair's slot (-w-1) in a table of omega numerators, so
+// omega (uniform or per pair) is applied at solve time and a sweep needs no
+// rebuild.
 #include "build.h"
+
+#include "../../include/mslice.h"
 
 #include <algorithm>
 
@@ -70,18 +76,32 @@ __global__ void k_check_rows(SliceTable st, int32_t T, int64_t n, unsigned* stat
   }
 }
 
-__global__ void k_row_len(SliceTable st, int32_t T, int64_t n, int64_t* len) {
+// Coupled snapshots of snapshot s: [lo, s) below and (s, hi) above.
+__device__ __forceinline__ void coupled_range(int32_t coupling, int32_t T, int32_t s, int32_t& lo, int32_t& hi) {
+  lo = coupling == 0 ? (s > 0 ? s - 1 : 0) : 0;
+  hi = coupling == 0 ? (s + 2 < T ? s + 2 : T) : T;
+}
+
+// The flag of the coupling entry from snapshot s to r: -(slot + 1).
+__device__ __forceinline__ int32_t coupling_flag(int32_t coupling, int32_t T, int32_t s, int32_t r) {
+  return coupling == 0 ? -((s < r ? s : r) + 1) : -(s * T + r + 1);
+}
+
+__global__ void k_row_len(SliceTable st, int32_t T, int64_t n, int32_t coupling, int64_t* len) {
   const int64_t total = n * (int64_t)T;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < total; v += (int64_t)gridDim.x * blockDim.x) {
     const int32_t s = (int32_t)(v / n);
     const int64_t i = v - (int64_t)s * n;
-    len[v] = (st.indptr[s][i + 1] - st.indptr[s][i]) + (s > 0 ? 1 : 0) + (s < T - 1 ? 1 : 0);
+    int32_t lo, hi;
+    coupled_range(coupling, T, s, lo, hi);
+    len[v] = (st.indptr[s][i + 1] - st.indptr[s][i]) + (s - lo) + (hi - s - 1);
   }
 }
 
 // One warp per supra-row: copies the shifted snapshot row, adds the coupling
 // flags, and writes k_v = sum of the row's intra weights.
-__global__ void k_fill_rows(SliceTable st, int32_t T, int64_t n, const int64_t* rowptr, int2* adj, int64_t* k) {
+__global__ void k_fill_rows(SliceTable st, int32_t T, int64_t n, int32_t coupling, const int64_t* rowptr, int2* adj,
+                            int64_t* k) {
   const int64_t total = n * (int64_t)T;
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -89,11 +109,12 @@ __global__ void k_fill_rows(SliceTable st, int32_t T, int64_t n, const int64_t* 
     const int32_t s = (int32_t)(v / n);
     const int64_t i = v - (int64_t)s * n;
     const int64_t a = st.indptr[s][i], b = st.indptr[s][i + 1];
+    int32_t lo, hi;
+    coupled_range(coupling, T, s, lo, hi);
     int64_t out = rowptr[v];
-    if (s > 0) {
-      if (lane == 0) adj[out] = make_int2((int32_t)(v - n), 0);
-      out += 1;
-    }
+    for (int32_t r = lo + lane; r < s; r += 32)
+      adj[out + (r - lo)] = make_int2((int32_t)((int64_t)r * n + i), coupling_flag(coupling, T, s, r));
+    out += s - lo;
     const int32_t off = (int32_t)((int64_t)s * n);
     long long ksum = 0;
     for (int64_t e = a + lane; e < b; e += 32) {
@@ -102,7 +123,8 @@ __global__ void k_fill_rows(SliceTable st, int32_t T, int64_t n, const int64_t* 
       ksum += w;
     }
     ksum = warp_sum(ksum);
-    if (s < T - 1 && lane == 0) adj[out + (b - a)] = make_int2((int32_t)(v + n), 0);
+    for (int32_t r = s + 1 + lane; r < hi; r += 32)
+      adj[out + (b - a) + (r - s - 1)] = make_int2((int32_t)((int64_t)r * n + i), coupling_flag(coupling, T, s, r));
     if (lane == 0) k[v] = ksum;
   }
 }
@@ -134,10 +156,11 @@ __global__ void k_lambda(const int64_t* two_m, int32_t T, const int32_t* slice_i
   lam[s] = t > 0 ? (((u128)(ull)gn[i]) << P_BITS) / ((u128)(ull)gd[i] * (u128)(ull)t) : (u128)0;
 }
 
-// Copies one instance into the concatenated arrays.
+// Copies one instance into the concatenated arrays (coupling flags move to
+// the instance's slots of the batch's table).
 __global__ void k_append(int64_t Ni, const int64_t* rowptr, const int2* adj, const int64_t* k, int64_t n, int32_t inst,
-                         int64_t noff, int64_t eoff, int32_t soff, int64_t* rowptr_o, int2* adj_o, int64_t* k_o,
-                         int32_t* slice0, int32_t* inst0) {
+                         int64_t noff, int64_t eoff, int32_t soff, int32_t cwoff, int64_t* rowptr_o, int2* adj_o,
+                         int64_t* k_o, int32_t* slice0, int32_t* inst0) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < Ni; v += (int64_t)gridDim.x * blockDim.x) {
     rowptr_o[noff + v] = rowptr[v] + eoff;
     k_o[noff + v] = k[v];
@@ -147,7 +170,7 @@ __global__ void k_append(int64_t Ni, const int64_t* rowptr, const int2* adj, con
   const int64_t nnz = rowptr[Ni];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
     const int2 x = adj[e];
-    adj_o[eoff + e] = make_int2(x.x + (int32_t)noff, x.y);
+    adj_o[eoff + e] = make_int2(x.x + (int32_t)noff, x.y <= 0 ? x.y - cwoff : x.y);
   }
 }
 
@@ -165,9 +188,12 @@ unsigned gs(int64_t n, int per) {
 
 void build_supra(Ctx& c, const std::vector<const int64_t*>& indptr, const std::vector<const int32_t*>& indices,
                  const std::vector<const int32_t*>& weights, const std::vector<int64_t>& nnz, int64_t n,
-                 SupraGraph& g) {
+                 SupraGraph& g, int32_t coupling) {
   const int32_t T = (int32_t)indptr.size();
+  if (coupling != 0 && (int64_t)T * T >= INT32_MAX) fail(MSLICE_EINVAL, "categorical coupling needs T*T < 2^31");
   g.T = T;
+  g.coupling = coupling;
+  g.ncw = coupling_slots(coupling, T);
   g.n = n;
   g.N = n * T;
   // device table of snapshot pointers
@@ -189,7 +215,7 @@ void build_supra(Ctx& c, const std::vector<const int64_t*>& indptr, const std::v
   }
   int64_t* len = c.ws->get<int64_t>("b_len", g.N + 1);
   g.rowptr = static_cast<int64_t*>(g.mem.get_bytes("rowptr0", (g.N + 1) * sizeof(int64_t)));
-  if (g.N > 0) launch(c, k_row_len, dim3(gs(g.N, 256)), dim3(256), 0, st, T, n, len);
+  if (g.N > 0) launch(c, k_row_len, dim3(gs(g.N, 256)), dim3(256), 0, st, T, n, coupling, len);
   int64_t* d_total = c.ws->get<int64_t>("b_total", 1);
   scan_excl(c, len, g.rowptr, g.N, d_total);
   check_cuda(cudaMemcpyAsync(g.rowptr + g.N, d_total, sizeof(int64_t), cudaMemcpyDeviceToDevice, c.stream), "copy");
@@ -199,7 +225,8 @@ void build_supra(Ctx& c, const std::vector<const int64_t*>& indptr, const std::v
   g.two_m = static_cast<int64_t*>(g.mem.get_bytes("two_m", T * sizeof(int64_t)));
   check_cuda(cudaMemsetAsync(g.two_m, 0, T * sizeof(int64_t), c.stream), "memset");
   if (g.N > 0) {
-    launch(c, k_fill_rows, dim3(gs(g.N * 32, 256)), dim3(256), 0, st, T, n, (const int64_t*)g.rowptr, g.adj, g.k);
+    launch(c, k_fill_rows, dim3(gs(g.N * 32, 256)), dim3(256), 0, st, T, n, coupling, (const int64_t*)g.rowptr,
+           g.adj, g.k);
     unsigned gx = (unsigned)std::min<int64_t>((n + 255) / 256, 64);
     launch(c, k_slice_mass, dim3(gx, T), dim3(256), 0, (const int64_t*)g.k, n, (ull*)g.two_m);
   }
@@ -207,9 +234,9 @@ void build_supra(Ctx& c, const std::vector<const int64_t*>& indptr, const std::v
   check_cuda(cudaMemcpyAsync(g.two_m_host.data(), g.two_m, T * sizeof(int64_t), cudaMemcpyDeviceToHost, c.stream),
              "copy");
   sync(c);
-  g.nnz_intra = g.nnz - 2 * n * (int64_t)(T - 1);
+  g.nnz_intra = g.nnz - coupling_entries(coupling, n, T);
   g.B = 1;
-  g.inst.assign(1, InstInfo{n, 0, T, 0});
+  g.inst.assign(1, InstInfo{n, 0, T, 0, coupling, 0});
 }
 
 void compute_lambda(Ctx& c, const SupraGraph& g, const long long* gn, const long long* gd, u128* lam) {
@@ -221,15 +248,19 @@ void concat_instances(Ctx& c, const std::vector<const SupraGraph*>& parts, Supra
   const int32_t B = (int32_t)parts.size();
   out.B = B;
   out.inst.assign(B, InstInfo{});
-  int64_t N = 0, nnz = 0, nnz_intra = 0;
+  int64_t N = 0, nnz = 0, nnz_intra = 0, ncw = 0;
   int32_t T = 0;
   for (int32_t i = 0; i < B; ++i) {
-    out.inst[i] = InstInfo{parts[i]->n, N, parts[i]->T, T};
+    out.inst[i] = InstInfo{parts[i]->n, N, parts[i]->T, T, parts[i]->coupling, ncw};
     N += parts[i]->N;
     nnz += parts[i]->nnz;
     nnz_intra += parts[i]->nnz_intra;
     T += parts[i]->T;
+    ncw += parts[i]->ncw;
   }
+  if (ncw >= INT32_MAX) fail(MSLICE_EINVAL, "the batch's coupling tables need fewer than 2^31 slots");
+  out.ncw = ncw;
+  out.coupling = -1;  // per instance
   out.N = N;
   out.T = T;
   out.n = parts.empty() ? 0 : parts[0]->n;
@@ -251,8 +282,8 @@ void concat_instances(Ctx& c, const std::vector<const SupraGraph*>& parts, Supra
     offs[i] = (int32_t)out.inst[i].noff;
     if (p.N > 0)
       launch(c, k_append, dim3(gs(std::max<int64_t>(p.N, p.nnz), 256)), dim3(256), 0, p.N, (const int64_t*)p.rowptr,
-             (const int2*)p.adj, (const int64_t*)p.k, p.n, i, out.inst[i].noff, eoff, out.inst[i].soff, out.rowptr,
-             out.adj, out.k, out.slice0, out.inst0);
+             (const int2*)p.adj, (const int64_t*)p.k, p.n, i, out.inst[i].noff, eoff, out.inst[i].soff,
+             (int32_t)out.inst[i].cwoff, out.rowptr, out.adj, out.k, out.slice0, out.inst0);
     if (p.T > 0) {
       check_cuda(cudaMemcpyAsync(out.two_m + out.inst[i].soff, p.two_m, p.T * sizeof(int64_t),
                                  cudaMemcpyDeviceToDevice, c.stream), "copy");

@@ -178,25 +178,44 @@ void check_bounds(int64_t n, int32_t T, const int64_t* two_m, long long gn, long
   }
 }
 
+long long pair_num(const InstParams& j, int32_t coupling, int32_t T, int32_t s, int32_t r) {
+  if (s == r) return 0;
+  if (coupling == 0 && s - r != 1 && r - s != 1) return 0;
+  if (j.cw.empty()) return j.on;
+  return j.cw[coupling == 0 ? std::min(s, r) : (int64_t)s * T + r];
+}
+
+void check_bounds(int64_t n, int32_t T, int32_t coupling, const int64_t* two_m, const InstParams& j, bool global_null) {
+  u128 sum2m = 0, csum = 0;
+  for (int32_t s = 0; s < T; ++s) {
+    sum2m += (u128)(ull)two_m[s];
+    for (int32_t r = 0; r < T; ++r) csum += (u128)(ull)pair_num(j, coupling, T, s, r);
+  }
+  const u128 lim = (u128)1 << 61;
+  const u128 twoM = (u128)(ull)j.od * sum2m + (u128)(ull)n * csum;
+  if (twoM >= lim) fail(MSLICE_EOVERFLOW, "omega_den*sum(2m_s) + n*sum(omega_num^(sr)) must stay below 2^61");
+  if (global_null) {
+    if ((u128)(ull)j.gn * twoM >= lim * (u128)(ull)j.gd)
+      fail(MSLICE_EOVERFLOW, "global null model: gamma*(omega_den*sum(2m_s) + n*sum(omega_num^(sr))) must stay below 2^61");
+    return;
+  }
+  for (int32_t s = 0; s < (j.gsn.empty() ? 1 : T); ++s) {
+    const long long gn = j.gsn.empty() ? j.gn : j.gsn[s], gd = j.gsn.empty() ? j.gd : j.gsd[s];
+    if ((u128)(ull)gn * (u128)(ull)j.od * sum2m >= lim * (u128)(ull)gd)
+      fail(MSLICE_EOVERFLOW, "gamma*omega_den*sum(2m_s) must stay below 2^61");
+  }
+}
+
 namespace {
 
-// k'_v = od*k_v + on*c_v, c_v = coupling edges of v (to the same node in the
-// previous and next snapshot of its instance).  Batches: slice0 gives the
-// node's global snapshot and slice_inst the instance of every snapshot.
-__global__ void k_null_strength(const int64_t* k, int64_t N, int64_t n, int32_t T, const int32_t* slice0,
-                                const int32_t* slice_inst, const int32_t* inst0, const long long* on,
-                                const long long* od, int64_t* kn) {
+// k'_v = od*k_v + cstr[s], s the snapshot of v (batches: slice0 gives it;
+// cstr is indexed by global snapshot).
+__global__ void k_null_strength(const int64_t* k, int64_t N, int64_t n, const int32_t* slice0, const int32_t* inst0,
+                                const long long* cstr, const long long* od, int64_t* kn) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
-    int32_t i = 0, c = 0;
-    if (slice0) {
-      i = inst0[v];
-      const int32_t s = slice0[v];
-      c = (s > 0 && slice_inst[s - 1] == i ? 1 : 0) + (s + 1 < T && slice_inst[s + 1] == i ? 1 : 0);
-    } else {
-      const int64_t s = v / n;
-      c = (s > 0 ? 1 : 0) + (s < T - 1 ? 1 : 0);
-    }
-    kn[v] = od[i] * k[v] + on[i] * c;
+    const int32_t i = inst0 ? inst0[v] : 0;
+    const int64_t s = slice0 ? (int64_t)slice0[v] : v / n;
+    kn[v] = od[i] * k[v] + cstr[s];
   }
 }
 
@@ -205,33 +224,50 @@ __global__ void k_null_strength(const int64_t* k, int64_t N, int64_t n, int32_t 
 void setup_null_model(Solver& S) {
   Ctx& c = *S.c;
   const SupraGraph& G = *S.G0;
+  bool any_gs = false;
+  for (uint8_t x : S.has_gs_h) any_gs = any_gs || x;
   if (!S.p.global_null) {
     S.Tn = G.T > 0 ? G.T : 1;
     S.lam = c.ws->get<u128>("lam", S.Tn);
-    if (G.T > 0) compute_lambda(c, G, S.gn_d, S.gd_d, S.lam);
+    if (G.T > 0 && !any_gs) {
+      compute_lambda(c, G, S.gn_d, S.gd_d, S.lam);
+    } else if (G.T > 0) {
+      // per-snapshot gamma: Lambda_s = floor(gsn 2^64 / (gsd 2m_s)), from the host table
+      std::vector<u128> lam(G.T);
+      const std::vector<long long>& gs = S.gs_h;
+      for (int32_t s = 0; s < G.T; ++s) {
+        const long long t = G.two_m_host[s];
+        lam[s] = t > 0 ? (((u128)(ull)gs[2 * s]) << P_BITS) / ((u128)(ull)gs[2 * s + 1] * (u128)(ull)t) : (u128)0;
+      }
+      check_cuda(cudaMemcpyAsync(S.lam, lam.data(), G.T * sizeof(u128), cudaMemcpyHostToDevice, c.stream), "copy");
+      sync(c);  // lam is pageable host memory
+    }
     return;
   }
-  // one null slice per instance, 2M' = od*sum 2m_s + 2*on*n*(T-1) in units of 1/od
+  // one null slice per instance, 2M' = od*sum 2m_s + n*sum cstr in units of 1/od
   S.Tn = G.B;
   std::vector<u128> lam(G.B);
   for (int32_t i = 0; i < G.B; ++i) {
     const InstInfo& in = G.inst[i];
     long long sum2m = 0;
     for (int32_t s = in.soff; s < in.soff + in.T; ++s) sum2m += G.two_m_host[s];
-    const long long twoM = S.od_h[i] * sum2m + 2 * S.on_h[i] * in.n * (long long)(in.T > 0 ? in.T - 1 : 0);
+    const long long twoM = S.od_h[i] * sum2m + S.csum_h[i];
     lam[i] = twoM > 0 ? (((u128)(ull)S.gn_h[i]) << P_BITS) / ((u128)(ull)S.gd_h[i] * (u128)(ull)twoM) : (u128)0;
   }
   S.lam = c.ws->get<u128>("lam", S.Tn);
   check_cuda(cudaMemcpyAsync(S.lam, lam.data(), G.B * sizeof(u128), cudaMemcpyHostToDevice, c.stream), "copy");
+  long long* cstr = c.ws->get<long long>("cstr", G.T > 0 ? G.T : 1);
+  if (G.T > 0)
+    check_cuda(cudaMemcpyAsync(cstr, S.cstr_h.data(), G.T * sizeof(long long), cudaMemcpyHostToDevice, c.stream),
+               "copy");
   S.kn = c.ws->get<int64_t>("k_null", S.N0 > 0 ? S.N0 : 1);
   if (G.N > 0) {
     const bool batch = G.B > 1;
     launch(c, k_null_strength, dim3(grid_for(G.N, 256) < 4096 ? grid_for(G.N, 256) : 4096), dim3(256), 0,
-           (const int64_t*)G.k, G.N, G.n > 0 ? G.n : 1, G.T, (const int32_t*)(batch ? G.slice0 : nullptr),
-           (const int32_t*)(batch ? G.slice_inst : nullptr), (const int32_t*)(batch ? G.inst0 : nullptr),
-           (const long long*)S.on_d, (const long long*)S.od_d, S.kn);
+           (const int64_t*)G.k, G.N, G.n > 0 ? G.n : 1, (const int32_t*)(batch ? G.slice0 : nullptr),
+           (const int32_t*)(batch ? G.inst0 : nullptr), (const long long*)cstr, (const long long*)S.od_d, S.kn);
   }
-  sync(c);  // lam is pageable host memory
+  sync(c);  // lam and cstr are pageable host memory
 }
 
 void set_instances(Ctx& c, Solver& S, const std::vector<InstParams>& jobs) {
@@ -258,7 +294,63 @@ void set_instances(Ctx& c, Solver& S, const std::vector<InstParams>& jobs) {
   S.on_d = par + 2 * B;
   S.od_d = par + 3 * B;
   check_cuda(cudaMemcpyAsync(par, hp.data(), hp.size() * sizeof(long long), cudaMemcpyHostToDevice, c.stream), "copy");
-  sync(c);  // hp is pageable host memory
+  // coupling sums of every snapshot and instance; the tables when any
+  // instance has one (the others' slots then hold their uniform omega)
+  const SupraGraph& G = *S.G0;
+  S.cstr_h.assign(G.T, 0);
+  S.csum_h.assign(B, 0);
+  S.has_cw_h.assign(B, 0);
+  S.has_gs_h.assign(B, 0);
+  S.cpl_edges = 0;
+  bool any_cw = false, any_gs = false;
+  for (int32_t i = 0; i < B; ++i) {
+    const InstInfo& in = G.inst[i];
+    S.has_cw_h[i] = !jobs[i].cw.empty();
+    S.has_gs_h[i] = !jobs[i].gsn.empty();
+    any_cw = any_cw || S.has_cw_h[i];
+    any_gs = any_gs || S.has_gs_h[i];
+    long long sum = 0;
+    for (int32_t s = 0; s < in.T; ++s)
+      for (int32_t r = 0; r < in.T; ++r) {
+        const long long x = pair_num(jobs[i], in.coupling, in.T, s, r);
+        S.cstr_h[in.soff + s] += x;
+        sum += x;
+        if (x > 0) S.cpl_edges += in.n;
+      }
+    S.csum_h[i] = in.n * sum;
+  }
+  std::vector<long long> cw;
+  std::vector<long long>& gs = S.gs_h;
+  gs.clear();
+  S.cw_d = nullptr;
+  S.gs_d = nullptr;
+  if (any_cw && G.ncw > 0) {
+    cw.assign(G.ncw, 0);
+    for (int32_t i = 0; i < B; ++i) {
+      const InstInfo& in = G.inst[i];
+      for (int32_t s = 0; s < in.T; ++s)
+        for (int32_t r = 0; r < in.T; ++r)
+          if (in.coupling != 0 || r == s + 1)
+            cw[in.cwoff + (in.coupling == 0 ? s : (int64_t)s * in.T + r)] = pair_num(jobs[i], in.coupling, in.T, s, r);
+    }
+    S.cw_d = c.ws->get<long long>("s_cw", G.ncw);
+    check_cuda(cudaMemcpyAsync(S.cw_d, cw.data(), G.ncw * sizeof(long long), cudaMemcpyHostToDevice, c.stream),
+               "copy");
+  }
+  if (any_gs && G.T > 0) {
+    gs.assign(2 * (size_t)G.T, 0);
+    for (int32_t i = 0; i < B; ++i) {
+      const InstInfo& in = G.inst[i];
+      for (int32_t s = 0; s < in.T; ++s) {
+        gs[2 * (in.soff + s)] = S.has_gs_h[i] ? jobs[i].gsn[s] : jobs[i].gn;
+        gs[2 * (in.soff + s) + 1] = S.has_gs_h[i] ? jobs[i].gsd[s] : jobs[i].gd;
+      }
+    }
+    S.gs_d = c.ws->get<long long>("s_gs", 2 * (size_t)G.T);
+    check_cuda(cudaMemcpyAsync(S.gs_d, gs.data(), gs.size() * sizeof(long long), cudaMemcpyHostToDevice, c.stream),
+               "copy");
+  }
+  sync(c);  // hp, cw and gs are pageable host memory
 }
 
 void run_leiden(Ctx& c, const SupraGraph& G, const std::vector<InstParams>& jobs, const SolveParams& p,
@@ -300,9 +392,7 @@ void run_leiden(Ctx& c, const SupraGraph& G, const std::vector<InstParams>& jobs
   L0.d = level0_view(G, S);
   if (MSLICE_CHECKED) L0.d.chk = c.d_status;
   L0.nnz = G.nnz;
-  L0.nnz_eff = G.nnz_intra;
-  for (int32_t i = 0; i < B; ++i)
-    if (S.on_h[i] > 0) L0.nnz_eff += 2 * G.inst[i].n * (int64_t)(G.inst[i].T > 0 ? G.inst[i].T - 1 : 0);
+  L0.nnz_eff = G.nnz_intra + S.cpl_edges;
   L0.ns = N0;
 
   bool debug_done = false;

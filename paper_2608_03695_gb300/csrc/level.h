@@ -19,6 +19,8 @@ struct LevelDev {
   int32_t is0 = 1;
   const int64_t* rowptr = nullptr;
   const int2* adj0 = nullptr;   // level 0
+  const long long* cw = nullptr;  // level 0: omega^(sr) numerators by slot (nullptr: omega uniform)
+  int64_t ncw = 0;
   const int64_t* k0 = nullptr;  // level 0
   const int32_t* col = nullptr; // aggregated levels
   const long long* W = nullptr;
@@ -68,8 +70,9 @@ __device__ __forceinline__ int32_t node_slice0(const LevelDev& g, int32_t v) {
 }
 
 // Entry e of the adjacency: neighbour u and weight W in units of 1/od.
-// A coupling entry has weight on and is absent when on = 0.  (om: the
-// omega of the row's instance.)
+// A coupling entry weighs on (uniform omega) or its pair's numerator in the
+// coupling table, and is absent when that is 0.  (om: the omega of the row's
+// instance.)
 __device__ __forceinline__ bool edge_at(const LevelDev& g, int64_t e, int32_t& u, long long& W, const Omega& om) {
 #if MSLICE_CHECKED
   if (e < 0 || e >= g.rowptr[g.N]) {
@@ -89,9 +92,16 @@ __device__ __forceinline__ bool edge_at(const LevelDev& g, int64_t e, int32_t& u
   if (g.is0) {
     const int2 x = __ldcs(&g.adj0[e]);
     u = x.x;
-    if (x.y == 0) {
-      W = om.on;
-      return om.on > 0;
+    if (x.y <= 0) {
+#if MSLICE_CHECKED
+      if (g.cw && (-(int64_t)x.y - 1) >= g.ncw) {
+        atomicOr(g.chk, ERR_BOUNDS);
+        W = 0;
+        return false;
+      }
+#endif
+      W = g.cw ? g.cw[-x.y - 1] : om.on;
+      return W > 0;
     }
     W = (long long)x.y * om.od;
     return true;

@@ -458,6 +458,10 @@ LevelDev level0_view(const SupraGraph& G, const Solver& S) {
     d.on_i = S.on_d;
     d.od_i = S.od_d;
   }
+  if (S.cw_d) {
+    d.cw = S.cw_d;
+    d.ncw = G.ncw;
+  }
   if (S.p.global_null) {
     // one null slice per instance: the instance id (batches) or 0 (v / N)
     d.global_null = 1;

@@ -1,10 +1,13 @@
-// Multislice modularity (Eq. multislice-modularity, ordinal coupling) of a
-// level-0 labelling, from exact integer sums:
+// Multislice modularity (Eq. multislice-modularity) of a level-0 labelling,
+// from exact integer sums:
 //   2mu Q = I + omega*J - gamma * sum_s S_s / 2m_s
 //   I   = intra-snapshot weight over ordered pairs inside one community,
-//   J   = ordered coupling pairs inside one community,
+//   J   = ordered coupling pairs inside one community (general coupling:
+//         omega*J = Jw/od, Jw the sum of the pairs' numerators),
 //   S_s = sum_c Sigma_{c,s}^2 (128-bit),
-//   2mu = sum_s 2m_s + 2*omega*n*(T-1).
+//   2mu = sum_s 2m_s + n * sum_{s,r} omega^(sr)  (2*omega*n*(T-1) ordinal).
+// Per-snapshot gamma: each slice term is multiplied by its gamma before the
+// ascending sum, and the sum is subtracted as it is.
 // The FP64 combination follows one fixed order (slice terms in ascending s,
 // then omega*J, the numerator, the division), with explicitly rounded
 // operations so no contraction changes the result.
@@ -41,7 +44,7 @@ __global__ void k_IJ(LevelDev g, const int32_t* labels, ull* IJ, int32_t B) {
         if (x.y > 0)
           Iv += (ull)x.y;
         else
-          Jv += 1;
+          Jv += g.cw ? (ull)g.cw[-x.y - 1] : 1ull;  // weighted by the pair's numerator with a table
       }
     }
     if (B == 1) {
@@ -100,26 +103,39 @@ struct QInst {
   int64_t n;
   int32_t T, soff;
   long long gn, gd, on, od;
+  long long csum;      // n * sum_{s,r} omega_num^(sr): the coupling part of 2mu, in units of 1/od
+  int32_t table, gtab;  // the instance has its own omega^(sr) table / per-snapshot gamma
 };
+
+// omega*J of an instance: with its own table, (double)Jw/od; otherwise
+// (on*J)/od.  IJ's second word holds Jw when the solve has a coupling table
+// (weighted) -- an instance without one then had every pair weigh on, so
+// J = Jw/on.
+__device__ __forceinline__ double omega_J(const QInst& p, ull Jword, int32_t weighted) {
+  if (p.table) return __ddiv_rn(__ull2double_rn(Jword), __ll2double_rn(p.od));
+  const ull J = weighted ? (p.on > 0 ? Jword / (ull)p.on : 0ull) : Jword;
+  return __ddiv_rn(__dmul_rn(__ll2double_rn(p.on), __ull2double_rn(J)), __ll2double_rn(p.od));
+}
 
 // Q of every instance (one thread each), in the fixed FP64 order.  S holds
 // one 128-bit sum per null slice: per snapshot (Q_MS) or per instance
-// (global model).
+// (global model).  gs: per-snapshot gamma (num, den) pairs, when any
+// instance has them.
 __global__ void k_Q(const ull* IJ, const ull* S, const int64_t* two_m, const QInst* qi, int32_t B, int32_t global,
-                    double* Q) {
+                    int32_t weighted, const long long* gs, double* Q) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B) return;
   const QInst p = qi[i];
   if (global) {
     long long sum2m = 0;
     for (int s = p.soff; s < p.soff + p.T; ++s) sum2m += two_m[s];
-    const long long twoM = p.od * sum2m + 2 * p.on * p.n * (long long)(p.T - 1);
+    const long long twoM = p.od * sum2m + p.csum;
     if (twoM == 0) {
       Q[i] = 0.0;
       return;
     }
     const u128 x = ((u128)S[2 * i + 1] << 64) | S[2 * i];
-    const double wJ = __ddiv_rn(__dmul_rn(__ll2double_rn(p.on), __ull2double_rn(IJ[2 * i + 1])), __ll2double_rn(p.od));
+    const double wJ = omega_J(p, IJ[2 * i + 1], weighted);
     const double gam = __ddiv_rn(__ll2double_rn(p.gn), __ll2double_rn(p.gd));
     const double twomu = __ddiv_rn(__ll2double_rn(twoM), __ll2double_rn(p.od));
     const double first = __ddiv_rn(__dadd_rn(__ull2double_rn(IJ[2 * i]), wJ), twomu);
@@ -135,18 +151,21 @@ __global__ void k_Q(const ull* IJ, const ull* S, const int64_t* two_m, const QIn
     sum2m += t;
     if (t > 0) {
       const u128 x = ((u128)S[2 * s + 1] << 64) | S[2 * s];
-      nullsum = __dadd_rn(nullsum, __ddiv_rn(u128_to_double(x), __ll2double_rn(t)));
+      const double term = __ddiv_rn(u128_to_double(x), __ll2double_rn(t));
+      nullsum = __dadd_rn(nullsum, p.gtab ? __dmul_rn(__ddiv_rn(__ll2double_rn(gs[2 * s]), __ll2double_rn(gs[2 * s + 1])),
+                                                      term)
+                                          : term);
     }
   }
-  const double wJ = __ddiv_rn(__dmul_rn(__ll2double_rn(p.on), __ull2double_rn(IJ[2 * i + 1])), __ll2double_rn(p.od));
+  const double wJ = omega_J(p, IJ[2 * i + 1], weighted);
   const double gam = __ddiv_rn(__ll2double_rn(p.gn), __ll2double_rn(p.gd));
-  const long long twomu_num = p.od * sum2m + 2 * p.on * p.n * (long long)(p.T - 1);
+  const long long twomu_num = p.od * sum2m + p.csum;
   if (twomu_num == 0) {
     Q[i] = 0.0;
     return;
   }
   const double twomu = __ddiv_rn(__ll2double_rn(twomu_num), __ll2double_rn(p.od));
-  const double num = __dsub_rn(__dadd_rn(__ull2double_rn(IJ[2 * i]), wJ), __dmul_rn(gam, nullsum));
+  const double num = __dsub_rn(__dadd_rn(__ull2double_rn(IJ[2 * i]), wJ), p.gtab ? nullsum : __dmul_rn(gam, nullsum));
   Q[i] = __ddiv_rn(num, twomu);
 }
 
@@ -206,7 +225,8 @@ void modularity(Solver& S, const int32_t* labels0, double* Q) {
   std::vector<QInst> qi(B);
   for (int32_t i = 0; i < B; ++i) {
     const InstInfo& in = G.inst[i];
-    qi[i] = QInst{in.n, in.T, in.soff, S.gn_h[i], S.gd_h[i], S.on_h[i], S.od_h[i]};
+    qi[i] = QInst{in.n, in.T, in.soff, S.gn_h[i], S.gd_h[i], S.on_h[i], S.od_h[i], S.csum_h[i],
+                  (int32_t)S.has_cw_h[i], (int32_t)S.has_gs_h[i]};
   }
   check_cuda(cudaMemcpyAsync(dqi, qi.data(), B * sizeof(QInst), cudaMemcpyHostToDevice, c.stream), "copy");
   check_cuda(cudaMemsetAsync(acc, 0, (2 * (size_t)B + 2 * (size_t)Tn) * sizeof(ull), c.stream), "memset");
@@ -215,7 +235,8 @@ void modularity(Solver& S, const int32_t* labels0, double* Q) {
   const int64_t span = S.sig.d ? S.sig.rows * S.sig.T : (int64_t)S.sig.h.cap;
   launch(c, k_S, dim3(gsz(span)), dim3(256), smem, S.sig, Tn, acc + 2 * B);
   launch(c, k_Q, dim3(grid_for(B, 128)), dim3(128), 0, (const ull*)acc, (const ull*)(acc + 2 * B),
-         (const int64_t*)G.two_m, (const QInst*)dqi, B, (int32_t)(S.p.global_null ? 1 : 0), dQ);
+         (const int64_t*)G.two_m, (const QInst*)dqi, B, (int32_t)(S.p.global_null ? 1 : 0),
+         (int32_t)(S.cw_d ? 1 : 0), (const long long*)S.gs_d, dQ);
   // B values go straight to the caller's (pageable) array
   check_cuda(cudaMemcpyAsync(Q, dQ, B * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "copy");
   sync(c);

@@ -34,7 +34,18 @@ struct Solver {
   SolveParams p;
   u128* lam = nullptr;  // Lambda of every null slice (Tn entries)
   int32_t Tn = 1;       // null slices: the snapshots (Q_MS) or one per instance (global model)
-  int64_t* kn = nullptr;  // global model: level-0 strengths k' = od*k + on*(coupling edges)
+  int64_t* kn = nullptr;  // global model: level-0 strengths k' = od*k + (coupling strength)
+  // general coupling: the omega^(sr) numerators of every instance by slot
+  // (nullptr when every instance has a uniform omega), per-snapshot gamma
+  // (num, den pairs; nullptr when every instance has one gamma), and host
+  // sums: coupling strength of one node of every snapshot, n * the sum of
+  // those per instance (the coupling part of 2mu, in units of 1/od), and the
+  // level-0 coupling entries that are edges
+  long long* cw_d = nullptr;
+  long long* gs_d = nullptr;
+  std::vector<long long> cstr_h, csum_h, gs_h;
+  std::vector<uint8_t> has_cw_h, has_gs_h;
+  int64_t cpl_edges = 0;
   int64_t N0 = 0;
 
   // node-indexed scratch, sized for level 0 (every level is smaller)
@@ -143,6 +154,20 @@ LevelDev level0_view(const SupraGraph& G, long long on, long long od);
 // The level-0 view of a solve: batch maps and per-instance omega included.
 LevelDev level0_view(const SupraGraph& G, const Solver& S);
 
+// Per-instance resolution and coupling of a solve: gamma = gn/gd and omega =
+// on/od, or the general form of Eq. multislice-modularity when the tables are
+// given: omega^(sr) = cw[slot]/od per coupling slot (coupling_slots()) and
+// gamma^(s) = gsn[s]/gsd[s] per snapshot.
+struct InstParams {
+  long long gn = 1, gd = 1, on = 1, od = 1;
+  std::vector<long long> cw;        // empty: on for every coupled pair
+  std::vector<long long> gsn, gsd;  // empty: gn/gd for every snapshot
+};
+
+// Numerator of omega^(sr) over od for an instance with this coupling pattern
+// and T snapshots (0 for uncoupled pairs).
+long long pair_num(const InstParams& j, int32_t coupling, int32_t T, int32_t s, int32_t r);
+
 // Fails with MSLICE_EOVERFLOW unless the 128-bit move keys of a graph with n
 // nodes per snapshot and snapshot masses two_m[0..T) stay in range for this
 // gamma and omega: 2M' = od * sum 2m_s + 2 on n (T-1) < 2^61 and
@@ -150,6 +175,10 @@ LevelDev level0_view(const SupraGraph& G, const Solver& S);
 // whose strengths include the coupling).
 void check_bounds(int64_t n, int32_t T, const int64_t* two_m, long long gn, long long gd, long long on, long long od,
                   bool global_null = false);
+// The same for the general form: 2M' = od * sum 2m_s + n * sum_{s,r} cw(s,r)
+// < 2^61, and gamma_s od sum 2m_s < 2^61 for every s (gamma 2M' < 2^61 under
+// the global null model).
+void check_bounds(int64_t n, int32_t T, int32_t coupling, const int64_t* two_m, const InstParams& j, bool global_null);
 
 // The null model of a solve: S.Tn, the quantised coefficients S.lam (one per
 // snapshot, or one per instance from 2M' for the global model) and, for the
@@ -160,11 +189,6 @@ void setup_null_model(Solver& S);
 // Fails with MSLICE_EINVAL unless every level-0 label d[v] (device) lies in
 // [0, size of v's instance).
 void check_label_ranges(Ctx& c, const SupraGraph& G, const int32_t* d);
-
-// Per-instance resolution and coupling of a solve.
-struct InstParams {
-  long long gn = 1, gd = 1, on = 1, od = 1;
-};
 
 // Output of run_leiden.
 struct RunOut {

@@ -93,7 +93,8 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
     if not shutil.which("gcc"):
         pytest.skip("no C compiler")
     mirrors = {"mslice_csr": pkg.Csr, "mslice_opts": pkg.Opts, "mslice_stats": pkg.Stats,
-               "mslice_server_opts": pkg.ServerOpts, "mslice_request_info": pkg.RequestInfo}
+               "mslice_server_opts": pkg.ServerOpts, "mslice_request_info": pkg.RequestInfo,
+               "mslice_general": pkg.General}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mslice.h"', 'int main(void) {']
     for cname, cls in mirrors.items():
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
@@ -119,6 +120,7 @@ def test_header_constants_match_the_binding():
     value in the Python binding."""
     text = open(os.path.join(ROOT, "include", "mslice.h")).read()
     defs = dict(re.findall(r"#define\s+(MSLICE_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", text))
+    defs.update(re.findall(r"(MSLICE_[A-Z]+)\s*=\s*(\d+)", text))  # enum members
     assert {"MSLICE_DEVICE_PTRS", "MSLICE_PROFILE", "MSLICE_AUTOTUNE", "MSLICE_NULL_GLOBAL"} <= set(defs)
     for name, value in defs.items():
         assert getattr(pkg, name) == int(value), name
