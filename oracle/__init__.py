@@ -17,8 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liboracle.so")
 
 OK, EINVAL, EOVERFLOW = 0, -1, -3
-NULL_MULTISLICE, NULL_GLOBAL = 0, 1
-_NULLS = {"multislice": NULL_MULTISLICE, "global": NULL_GLOBAL}
+NULL_MULTISLICE, NULL_GLOBAL, NULL_CPM = 0, 1, 2
+_NULLS = {"multislice": NULL_MULTISLICE, "global": NULL_GLOBAL, "cpm": NULL_CPM}
 ORDINAL, CATEGORICAL = 0, 1
 _COUPLINGS = {"ordinal": ORDINAL, "categorical": CATEGORICAL}
 

@@ -65,6 +65,13 @@ struct Level {
 // below are kept in units of 1/od (k' = od*k + on*c, c = the node's coupling
 // edges), the null "slice" is single (index 0) and the key's null scale is 1
 // instead of od.
+// ORC_NULL_CPM: the temporal Constant Potts Model Sec. 3.2 names as an
+// alternative quality function on the supra-graph (Traag et al.): the null
+// term of snapshot s is gamma_s per ordered pair of its nodes, i.e. Eq.
+// multislice-modularity with every node's null strength 1 and 2m_s replaced
+// by 1.  So every node has the entry (s, 1), the null slices are the
+// snapshots with mass 1, Lambda_s = floor(gamma_s 2^P), and the key's null
+// scale stays od.
 //
 // General coupling (the omega^(sr) and gamma^(s) of Eq. multislice-modularity):
 // omega^(sr) = cw[pair]/od, with pair = min(s,r) for ORDINAL coupling (only
@@ -202,6 +209,9 @@ void slice_masses(const orc_csr* slices, Problem& p) {
     for (int64_t c : p.cstr) csum += c;
     p.two_m_null.assign(1, p.od * sum2m + p.n * csum);
     p.ns = 1;
+  } else if (p.null_model == ORC_NULL_CPM) {
+    p.two_m_null.assign(p.T, 1);
+    p.ns = p.od;
   } else {
     p.two_m_null = p.two_m;
     p.ns = p.od;
@@ -218,7 +228,8 @@ void slice_masses(const orc_csr* slices, Problem& p) {
 // Overflow guard: every key below stays inside a signed 128-bit integer when
 //   2M' = od*sum(2m_s) + n*sum_s cstr[s] < 2^61   and   gamma_s*od*sum(2m_s) < 2^61
 // for every s (gamma*2M' < 2^61 for the global model, whose strengths include
-// the coupling).
+// the coupling; gamma_s*od*n*N < 2^61 for CPM, whose null sums count nodes:
+// sum_s k_{v,s} Sigma_{c,s} <= N*n).
 int check_bounds(const Problem& p) {
   u128 sum2m = 0;
   for (int64_t t : p.two_m) sum2m += (u128)(uint64_t)t;
@@ -231,8 +242,9 @@ int check_bounds(const Problem& p) {
     if ((u128)(uint64_t)p.gn * twoM >= lim * (u128)(uint64_t)p.gd) return ORC_EOVERFLOW;
     return ORC_OK;
   }
+  const u128 mass = p.null_model == ORC_NULL_CPM ? (u128)(uint64_t)p.n * (u128)(uint64_t)(p.n * p.T) : sum2m;
   for (int32_t s = 0; s < p.T; ++s)
-    if ((u128)(uint64_t)p.gsn[s] * (u128)(uint64_t)p.od * sum2m >= lim * (u128)(uint64_t)p.gsd[s])
+    if ((u128)(uint64_t)p.gsn[s] * (u128)(uint64_t)p.od * mass >= lim * (u128)(uint64_t)p.gsd[s])
       return ORC_EOVERFLOW;
   return ORC_OK;
 }
@@ -264,6 +276,8 @@ Level build_level0(const orc_csr* slices, const Problem& p) {
         // k' = od*k + (coupling strength of v), one null slice
         const int64_t kp = p.od * k + p.cstr[s];
         if (kp > 0) L.kvec[v].push_back({0, kp});
+      } else if (p.null_model == ORC_NULL_CPM) {
+        L.kvec[v].push_back({s, 1});  // every node weighs 1 in its snapshot's null term
       } else if (k > 0) {
         L.kvec[v].push_back({s, k});
       }
@@ -650,15 +664,16 @@ double modularity_of(const orc_csr* slices, const Problem& p, const std::vector<
   if (p.null_model == ORC_NULL_GLOBAL) return modularity_global(slices, p, labels);
   const int64_t n = p.n;
   std::map<int32_t, SliceMap> sig;
-  const PairSums ps =
-      pair_sums(slices, p, labels, [&](int64_t v, int32_t s, int64_t k) { sig[labels[v]][s] += k; });
+  const bool cpm = p.null_model == ORC_NULL_CPM;  // node counts over masses 1
+  const PairSums ps = pair_sums(slices, p, labels,
+                                [&](int64_t v, int32_t s, int64_t k) { sig[labels[v]][s] += cpm ? 1 : k; });
   std::vector<u128> S(p.T, 0);
   for (const auto& cs : sig)
     for (const auto& sk : cs.second) S[sk.first] += (u128)(uint64_t)sk.second * (u128)(uint64_t)sk.second;
   double nullsum = 0.0;
   for (int32_t s = 0; s < p.T; ++s) {
-    if (p.two_m[s] == 0) continue;
-    const double term = u128_to_double(S[s]) / (double)p.two_m[s];
+    if (p.two_m_null[s] == 0) continue;
+    const double term = u128_to_double(S[s]) / (double)p.two_m_null[s];
     nullsum += p.gamma_table ? ((double)p.gsn[s] / (double)p.gsd[s]) * term : term;
   }
   const double wJ = omega_J(p, ps);
@@ -678,7 +693,8 @@ int setup(const orc_csr* slices, int32_t T, int64_t gn, int64_t gd, int64_t on, 
   int rc = validate(slices, T);
   if (rc) return rc;
   if (!valid_rational(gn, gd, false) || !valid_rational(on, od, true)) return ORC_EINVAL;
-  if (null_model != ORC_NULL_MULTISLICE && null_model != ORC_NULL_GLOBAL) return ORC_EINVAL;
+  if (null_model != ORC_NULL_MULTISLICE && null_model != ORC_NULL_GLOBAL && null_model != ORC_NULL_CPM)
+    return ORC_EINVAL;
   p.null_model = null_model;
   p.T = T;
   p.n = slices[0].n;

@@ -53,6 +53,10 @@ extern "C" {
  * supra-graph, Sec. 3.2). */
 #define ORC_NULL_MULTISLICE 0
 #define ORC_NULL_GLOBAL 1
+/* CPM: the temporal Constant Potts Model (Sec. 3.2): snapshot s's null term
+ * is gamma_s per ordered pair of its nodes; Q_CPM = (I + omega*J -
+ * sum_s gamma_s sum_c n_{c,s}^2) / 2mu. */
+#define ORC_NULL_CPM 2
 
 /* Coupling patterns: ORDINAL couples (i,s) with (i,s+1); CATEGORICAL couples
  * (i,s) with (i,r) for every r != s. */

@@ -690,7 +690,7 @@ def test_global_overflow_guard_counts_coupling():
     assert e.value.code == oracle.EOVERFLOW
     oracle.leiden(snaps, (g - 1, 1), (on, 1), null="global", n_iterations=1, max_rounds=1, max_levels=1)
     with pytest.raises(oracle.OracleError) as e:
-        oracle.leiden(snaps, null=2)
+        oracle.leiden(snaps, null=3)
     assert e.value.code == oracle.EINVAL
 
 
@@ -995,3 +995,144 @@ def test_general_global_move_key_and_bruteforce(seed):
     assert Q <= best + 1e-12
     if st["last_level0_moves"] == 0:
         assert oracle.count_improving(snaps, lab, gamma, omega, **kw) == 0
+
+
+# ----------------------------------------------------------------- temporal CPM
+# The temporal Constant Potts Model (Sec. 3.2 names it as a quality function
+# the supra-graph strategy accepts): snapshot s's null term is gamma_s per
+# ordered pair of its nodes.  Q_CPM = (1/2mu) sum_{ijsr} [(A_ijs - gamma_s)
+# delta_sr + delta_ij omega^(sr)] delta(c_is, c_jr), pinned to that dense form
+# written out with exact rationals, closed forms, the key's exact
+# differences, brute force and the CPM threshold property.
+def cpm_Q_exact(snaps, labels, gammas, W):
+    A = dense_slices(snaps)
+    T, n = len(A), A[0].shape[0]
+    two_mu = Fraction(0)
+    tot = Fraction(0)
+    for s in range(T):
+        two_mu += int(A[s].sum())
+        for i in range(n):
+            for j in range(n):
+                if labels[s * n + i] == labels[s * n + j]:
+                    tot += int(A[s][i, j]) - gammas[s]
+        for r in range(T):
+            two_mu += n * W[s][r]
+            for i in range(n):
+                if labels[s * n + i] == labels[r * n + i]:
+                    tot += W[s][r]
+    return tot / two_mu if two_mu else Fraction(0)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_cpm_Q_exact_rational(seed):
+    rng = np.random.default_rng(2100 + seed)
+    T = int(rng.integers(1, 5))
+    n = int(rng.integers(2, 7))
+    snaps = synth.random_temporal(n, T, p=0.5, w_max=5, seed=seed, p_empty=0.1)
+    coupling = ["ordinal", "categorical"][seed % 2]
+    omega = rand_rational(rng, lo_num=0)
+    omegas = rand_general(rng, T, coupling, omega[1]) if seed % 3 == 2 else None
+    gamma = (int(rng.integers(1, 4)), int(rng.integers(1, 6)))
+    gammas = [rand_rational(rng) for _ in range(T)] if seed % 4 == 3 else None
+    W = coupling_matrix(T, coupling, omega, omegas)
+    gq = [Fraction(*g) for g in gammas] if gammas else [Fraction(*gamma)] * T
+    for _ in range(3):
+        labels = rng.integers(0, n * T, size=n * T).astype(np.int32)
+        q = oracle.modularity(snaps, labels, gamma, omega, null="cpm", coupling=coupling, omegas=omegas,
+                              gammas=gammas)
+        assert q == pytest.approx(float(cpm_Q_exact(snaps, labels, gq, W)), rel=1e-12, abs=1e-15)
+
+
+def test_cpm_closed_forms():
+    """Singletons: Q = -gamma N / 2mu.  One community per snapshot:
+    Q = (sum_s 2m_s - gamma sum_s n^2) / 2mu.  Everything in one community:
+    Q = 1 - gamma T n^2 / 2mu."""
+    snaps = synth.random_temporal(8, 3, p=0.4, w_max=3, seed=12)
+    n, T = 8, 3
+    sum2m = sum(int(s.weights.sum()) for s in snaps)
+    two_mu = sum2m + 2 * n * (T - 1) * 0.5
+    g = 0.75
+    q = oracle.modularity(snaps, np.arange(n * T, dtype=np.int32), (3, 4), (1, 2), null="cpm")
+    assert q == pytest.approx(-g * n * T / two_mu, rel=1e-13)
+    per_slice = np.repeat(np.arange(T), n).astype(np.int32)
+    q = oracle.modularity(snaps, per_slice, (3, 4), (1, 2), null="cpm")
+    assert q == pytest.approx((sum2m - g * T * n * n) / two_mu, rel=1e-13)
+    q = oracle.modularity(snaps, np.zeros(n * T, np.int32), (3, 4), (1, 2), null="cpm")
+    assert q == pytest.approx(1 - g * T * n * n / two_mu, rel=1e-13)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_cpm_move_key_is_scaled_delta_Q(seed):
+    """2(G(v,c) - G(v,a)) / (2mu od 2^64) equals the exact change of Q_CPM under
+    the quantised resolutions gamma'_s = floor(gamma_s 2^64) / 2^64."""
+    rng = np.random.default_rng(2200 + seed)
+    T = int(rng.integers(1, 4))
+    n = int(rng.integers(2, 5))
+    snaps = synth.random_temporal(n, T, p=0.6, w_max=5, seed=seed, p_empty=0.15)
+    omega = rand_rational(rng, lo_num=0)
+    gammas = [(int(rng.integers(1, 5)), int(rng.integers(1, 7))) for _ in range(T)]
+    gq = [Fraction((g[0] << 64) // g[1], 1 << 64) for g in gammas]
+    W = coupling_matrix(T, "ordinal", omega, None)
+    two_mu = Fraction(sum(int(sn.weights.sum()) for sn in snaps)) + sum(n * W[s][r] for s in range(T)
+                                                                         for r in range(T))
+    if two_mu == 0:
+        return
+    N = n * T
+    labels = rng.integers(0, max(2, N // 2), size=N).astype(np.int32)
+    base = cpm_Q_exact(snaps, labels, gq, W)
+    for _ in range(6):
+        v = int(rng.integers(0, N))
+        choices = [int(x) for x in set(labels.tolist())] + [-1]
+        c = choices[int(rng.integers(0, len(choices)))]
+        new = labels.copy()
+        new[v] = c if c >= 0 else N + 7
+        Gc = oracle.move_key(snaps, labels, v, c, (1, 1), omega, null="cpm", gammas=gammas)
+        Ga = oracle.move_key(snaps, labels, v, int(labels[v]), (1, 1), omega, null="cpm", gammas=gammas)
+        assert Fraction(2 * (Gc - Ga), 1) / (two_mu * omega[1] * (1 << 64)) == cpm_Q_exact(snaps, new, gq, W) - base
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_cpm_bruteforce_bound_and_local_optimum(seed):
+    rng = np.random.default_rng(2300 + seed)
+    T = int(rng.integers(1, 3))
+    n = int(rng.integers(3, 5 if T == 2 else 9))
+    snaps = synth.random_temporal(n, T, p=0.5, w_max=3, seed=seed)
+    gamma = [(1, 2), (1, 1), (3, 2)][seed % 3]
+    N = n * T
+    best = max(oracle.modularity(snaps, np.array(p, np.int32), gamma, (1, 2), null="cpm") for p in set_partitions(N))
+    labels, Q, st = oracle.leiden(snaps, gamma, (1, 2), n_iterations=20, null="cpm")
+    assert Q <= best + 1e-12
+    assert Q == pytest.approx(oracle.modularity(snaps, labels, gamma, (1, 2), null="cpm"), rel=1e-15)
+    if st["last_level0_moves"] == 0:
+        assert oracle.count_improving(snaps, labels, gamma, (1, 2), null="cpm") == 0
+
+
+def test_cpm_threshold_and_cliques():
+    """CPM's resolution is a density threshold: with gamma above every edge
+    weight and no coupling, merging any two nodes loses, so Leiden returns
+    singletons; disjoint cliques of weight w are recovered for gamma < w."""
+    snaps = synth.cliques_temporal([5, 6, 7, 4], T=3, w=2)
+    lab, Q, _ = oracle.leiden(snaps, (5, 2), (0, 1), null="cpm")
+    assert len(set(lab.tolist())) == len(lab)
+    lab, Q, _ = oracle.leiden(snaps, (3, 2), (1, 1), null="cpm")
+    n = 22
+    want = np.repeat(np.arange(4), [5, 6, 7, 4])
+    for s in range(3):
+        got = lab[s * n:(s + 1) * n]
+        assert len(set(zip(got.tolist(), want.tolist()))) == 4
+        assert (got == lab[:n]).all()
+
+
+def test_cpm_bound():
+    """CPM's null sums count nodes, so its bound is gamma*od*n*N < 2^61: a
+    sparse graph with many nodes passes Q_MS's bound and fails CPM's."""
+    u = np.array([0], np.int64)
+    v = np.array([1], np.int64)
+    sn = synth.csr_from_edges(64, u, v, np.ones(1, np.int32))
+    snaps = [sn] * 4  # n = 64, N = 256, sum 2m_s = 8
+    gamma, omega = (2 ** 24, 1), (1, 2 ** 24)  # gamma*od = 2^48: 2^51 for Q_MS, 2^62 for CPM
+    oracle.leiden(snaps, gamma, omega, n_iterations=1, max_rounds=1, max_levels=1)
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.leiden(snaps, gamma, omega, null="cpm")
+    assert e.value.code == oracle.EOVERFLOW
+    oracle.leiden(snaps, (2 ** 22, 1), omega, null="cpm", n_iterations=1, max_rounds=1, max_levels=1)
