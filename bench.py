@@ -59,8 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving", "large"])
-    ap.add_argument("--null", default="multislice", choices=["multislice", "global"],
-                    help="plain workload: Q_MS (default) or the supra-graph's plain modularity")
+    ap.add_argument("--null", default="multislice", choices=["multislice", "global", "cpm"],
+                    help="plain workload: Q_MS (default), the supra-graph's plain modularity, or temporal CPM")
     ap.add_argument("--requests", type=int, default=4, help="serving workload: timed snapshots per graph")
     ap.add_argument("--slots", type=int, default=2, help="serving workload: server workers")
     ap.add_argument("--scale", type=float, default=1.0, help="batched workload: node-count scale of every graph")
@@ -151,8 +151,9 @@ def workload(args):
     """The plain workload's config; the null model is named when it is not Q_MS."""
     if args.null == "multislice":
         return dict(WORKLOAD)
-    return {**WORKLOAD, "workload": WORKLOAD["workload"] + ", global null model (plain modularity of the supra-graph)",
-            "null_model": args.null}
+    what = {"global": "global null model (plain modularity of the supra-graph)",
+            "cpm": "temporal Constant Potts Model"}[args.null]
+    return {**WORKLOAD, "workload": WORKLOAD["workload"] + ", " + what, "null_model": args.null}
 
 
 def cpu_baseline(null="multislice"):

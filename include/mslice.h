@@ -71,6 +71,15 @@ extern "C" {
  * Bound: gamma * 2M' < 2^61 (EOVERFLOW otherwise).  Not available to
  * mslice_modularity_noalloc. */
 #define MSLICE_NULL_GLOBAL 8
+/* leiden / batch run / modularity / server: the temporal Constant Potts Model
+ * (Sec. 3.2 names it as a quality function the supra-graph strategy takes):
+ * snapshot s's null term is gamma^(s) per ordered pair of its nodes instead
+ * of gamma k_is k_js / 2m_s, so resolution is a density threshold.  Reported
+ * Q_CPM = (I + omega J - sum_s gamma^(s) sum_c n_{c,s}^2) / 2mu.  Keys use
+ * Lambda_s = floor(gamma^(s) 2^64) with node counts as strengths; bound:
+ * gamma^(s) * omega_den * n * N < 2^61 (EOVERFLOW).  Not together with
+ * MSLICE_NULL_GLOBAL (EINVAL); not available to mslice_modularity_noalloc. */
+#define MSLICE_NULL_CPM 16
 
 typedef struct {
   int64_t n;              /* nodes of the snapshot (equal for all snapshots) */

@@ -34,7 +34,8 @@ MSLICE_DEVICE_PTRS = 1
 MSLICE_PROFILE = 2
 MSLICE_AUTOTUNE = 4
 MSLICE_NULL_GLOBAL = 8
-_NULLS = {"multislice": 0, "global": MSLICE_NULL_GLOBAL}
+MSLICE_NULL_CPM = 16
+_NULLS = {"multislice": 0, "global": MSLICE_NULL_GLOBAL, "cpm": MSLICE_NULL_CPM}
 MSLICE_ORDINAL = 0
 MSLICE_CATEGORICAL = 1
 _COUPLINGS = {"ordinal": MSLICE_ORDINAL, "categorical": MSLICE_CATEGORICAL}

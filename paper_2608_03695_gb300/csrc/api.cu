@@ -320,6 +320,13 @@ void check_opts(const mslice_opts& opt) {
   }
 }
 
+// The null model the flags select (EINVAL for two at once).
+int null_model_of(int32_t flags) {
+  const bool g = (flags & MSLICE_NULL_GLOBAL) != 0, cpm = (flags & MSLICE_NULL_CPM) != 0;
+  if (g && cpm) fail(MSLICE_EINVAL, "MSLICE_NULL_GLOBAL and MSLICE_NULL_CPM exclude each other");
+  return g ? NULL_SUPRA_GLOBAL : cpm ? NULL_CPM : NULL_MULTISLICE;
+}
+
 // The instance parameters of a solve on graph G: the uniform rationals and,
 // when gen gives them, the validated tables (EINVAL for bad ones).
 InstParams inst_params(const SupraGraph& G, int64_t gn, int64_t gd, int64_t on, int64_t od, const mslice_general* gen,
@@ -378,7 +385,8 @@ void run_solve(Ctx& c, const SupraGraph& G, const std::vector<InstParams>& jobs,
   p.seed = opt.seed;
   p.cuts = cuts_of(opt);
   p.autotune = (opt.flags & MSLICE_AUTOTUNE) != 0;
-  p.global_null = (opt.flags & MSLICE_NULL_GLOBAL) != 0;
+  p.global_null = null_model_of(opt.flags) == NULL_SUPRA_GLOBAL;
+  p.cpm = null_model_of(opt.flags) == NULL_CPM;
   run_leiden(c, G, jobs, p, opt.stop_level, opt.stop_stage, opt.stop_rounds, init, out, S, ro);
   std::memset(&stats, 0, sizeof(stats));
   stats.iterations = (int32_t)ro.iterations;
@@ -564,12 +572,13 @@ int mslice_leiden_general(mslice_handle h, const mslice_opts* o, const mslice_ge
     mslice_default_opts(&opt);
     if (o) opt = *o;
     check_opts(opt);
-    const bool global = (opt.flags & MSLICE_NULL_GLOBAL) != 0;
+    const int nm = null_model_of(opt.flags);
     const SupraGraph& G = h->G;
-    const InstParams job = inst_params(G, opt.gamma_num, opt.gamma_den, opt.omega_num, opt.omega_den, gen, global);
+    const InstParams job =
+        inst_params(G, opt.gamma_num, opt.gamma_den, opt.omega_num, opt.omega_den, gen, nm == NULL_SUPRA_GLOBAL);
     if (!labels_out && h->G.N > 0) fail(MSLICE_EINVAL, "null labels_out");
     const bool dev = (opt.flags & MSLICE_DEVICE_PTRS) != 0;
-    check_bounds(G.n, G.T, G.coupling, G.two_m_host.data(), job, global);
+    check_bounds(G.n, G.T, G.coupling, G.two_m_host.data(), job, nm);
     const int64_t N0 = G.N;
     Ctx c = h->ctx();
     const int32_t* init = nullptr;
@@ -632,16 +641,18 @@ int mslice_modularity_general(mslice_handle h, const int32_t* labels, const msli
     if (o) opt = *o;
     const int32_t flags = opt.flags;
     const SupraGraph& G = h->G;
-    const bool global = (flags & MSLICE_NULL_GLOBAL) != 0;
-    const InstParams job = inst_params(G, opt.gamma_num, opt.gamma_den, opt.omega_num, opt.omega_den, gen, global);
+    const int nm = null_model_of(flags);
+    const InstParams job =
+        inst_params(G, opt.gamma_num, opt.gamma_den, opt.omega_num, opt.omega_den, gen, nm == NULL_SUPRA_GLOBAL);
     if (!labels && G.N > 0) fail(MSLICE_EINVAL, "null labels");
-    check_bounds(G.n, G.T, G.coupling, G.two_m_host.data(), job, global);
+    check_bounds(G.n, G.T, G.coupling, G.two_m_host.data(), job, nm);
     Ctx c = h->ctx();
     Solver S;
     S.c = &c;
     S.G0 = &G;
     S.N0 = G.N;
-    S.p.global_null = global;
+    S.p.global_null = nm == NULL_SUPRA_GLOBAL;
+    S.p.cpm = nm == NULL_CPM;
     set_instances(c, S, {job});
     setup_null_model(S);
     const int64_t N = G.N > 0 ? G.N : 1;
@@ -704,7 +715,7 @@ int mslice_batch_add_general(mslice_batch b, mslice_handle g, int64_t gamma_num,
     if (!b || !g) fail(MSLICE_EINVAL, "null batch or graph");
     const SupraGraph& G = g->G;
     const InstParams job = inst_params(G, gamma_num, gamma_den, omega_num, omega_den, gen, false);
-    check_bounds(G.n, G.T, G.coupling, G.two_m_host.data(), job, false);
+    check_bounds(G.n, G.T, G.coupling, G.two_m_host.data(), job, NULL_MULTISLICE);
     const int64_t N = G.N;
     if (b->off.back() + N > INT32_MAX) fail(MSLICE_EINVAL, "the batch must hold fewer than 2^31 supra-nodes");
     if ((int64_t)b->graphs.size() >= INT32_MAX) fail(MSLICE_EINVAL, "too many instances");
@@ -738,12 +749,14 @@ int mslice_batch_run(mslice_batch b, const mslice_opts* o, mslice_stats* st) {
     if (o) opt = *o;
     check_opts(opt);
     if (opt.stop_level >= 0) fail(MSLICE_EINVAL, "debug stops apply to single solves only");
-    if (opt.flags & MSLICE_NULL_GLOBAL)
+    const int nm = null_model_of(opt.flags);
+    if (nm != NULL_MULTISLICE)
       for (size_t i = 0; i < b->graphs.size(); ++i) {
         const SupraGraph& Gi = b->graphs[i]->G;
         const InstParams& j = b->jobs[i];
-        if (!j.gsn.empty()) fail(MSLICE_EINVAL, "per-snapshot gamma does not apply to the global null model");
-        check_bounds(Gi.n, Gi.T, Gi.coupling, Gi.two_m_host.data(), j, true);
+        if (nm == NULL_SUPRA_GLOBAL && !j.gsn.empty())
+          fail(MSLICE_EINVAL, "per-snapshot gamma does not apply to the global null model");
+        check_bounds(Gi.n, Gi.T, Gi.coupling, Gi.two_m_host.data(), j, nm);
       }
     Ctx c = b->ctx();
     std::vector<uint64_t> serials;
@@ -765,7 +778,7 @@ int mslice_batch_run(mslice_batch b, const mslice_opts* o, mslice_stats* st) {
       check_cuda(cudaMemcpyAsync(init, b->init.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream), "copy");
     }
     int32_t* out = b->ws.get<int32_t>("b_out", N > 0 ? N : 1);
-    opt.flags &= MSLICE_PROFILE | MSLICE_AUTOTUNE | MSLICE_NULL_GLOBAL;
+    opt.flags &= MSLICE_PROFILE | MSLICE_AUTOTUNE | MSLICE_NULL_GLOBAL | MSLICE_NULL_CPM;
     mslice_stats stats;
     RunOut ro;
     Solver S;

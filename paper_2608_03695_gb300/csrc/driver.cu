@@ -162,22 +162,6 @@ void check_label_ranges(Ctx& c, const SupraGraph& G, const int32_t* d) {
   check_status(c, "labels");
 }
 
-void check_bounds(int64_t n, int32_t T, const int64_t* two_m, long long gn, long long gd, long long on, long long od,
-                  bool global_null) {
-  u128 sum2m = 0;
-  for (int32_t s = 0; s < T; ++s) sum2m += (u128)(ull)two_m[s];
-  const u128 ncpl = (u128)(ull)n * (u128)(ull)(T > 0 ? T - 1 : 0);
-  const u128 lim = (u128)1 << 61;
-  const u128 twoM = (u128)(ull)od * sum2m + 2 * (u128)(ull)on * ncpl;
-  if (twoM >= lim) fail(MSLICE_EOVERFLOW, "omega_den*sum(2m_s) + 2*omega_num*n*(T-1) must stay below 2^61");
-  if (global_null) {
-    if ((u128)(ull)gn * twoM >= lim * (u128)(ull)gd)
-      fail(MSLICE_EOVERFLOW, "global null model: gamma*(omega_den*sum(2m_s) + 2*omega_num*n*(T-1)) must stay below 2^61");
-  } else if ((u128)(ull)gn * (u128)(ull)od * sum2m >= lim * (u128)(ull)gd) {
-    fail(MSLICE_EOVERFLOW, "gamma*omega_den*sum(2m_s) must stay below 2^61");
-  }
-}
-
 long long pair_num(const InstParams& j, int32_t coupling, int32_t T, int32_t s, int32_t r) {
   if (s == r) return 0;
   if (coupling == 0 && s - r != 1 && r - s != 1) return 0;
@@ -185,7 +169,7 @@ long long pair_num(const InstParams& j, int32_t coupling, int32_t T, int32_t s, 
   return j.cw[coupling == 0 ? std::min(s, r) : (int64_t)s * T + r];
 }
 
-void check_bounds(int64_t n, int32_t T, int32_t coupling, const int64_t* two_m, const InstParams& j, bool global_null) {
+void check_bounds(int64_t n, int32_t T, int32_t coupling, const int64_t* two_m, const InstParams& j, int nm) {
   u128 sum2m = 0, csum = 0;
   for (int32_t s = 0; s < T; ++s) {
     sum2m += (u128)(ull)two_m[s];
@@ -194,19 +178,27 @@ void check_bounds(int64_t n, int32_t T, int32_t coupling, const int64_t* two_m, 
   const u128 lim = (u128)1 << 61;
   const u128 twoM = (u128)(ull)j.od * sum2m + (u128)(ull)n * csum;
   if (twoM >= lim) fail(MSLICE_EOVERFLOW, "omega_den*sum(2m_s) + n*sum(omega_num^(sr)) must stay below 2^61");
-  if (global_null) {
+  if (nm == NULL_SUPRA_GLOBAL) {
     if ((u128)(ull)j.gn * twoM >= lim * (u128)(ull)j.gd)
       fail(MSLICE_EOVERFLOW, "global null model: gamma*(omega_den*sum(2m_s) + n*sum(omega_num^(sr))) must stay below 2^61");
     return;
   }
+  const u128 mass = nm == NULL_CPM ? (u128)(ull)n * (u128)(ull)(n * T) : sum2m;
   for (int32_t s = 0; s < (j.gsn.empty() ? 1 : T); ++s) {
     const long long gn = j.gsn.empty() ? j.gn : j.gsn[s], gd = j.gsn.empty() ? j.gd : j.gsd[s];
-    if ((u128)(ull)gn * (u128)(ull)j.od * sum2m >= lim * (u128)(ull)gd)
-      fail(MSLICE_EOVERFLOW, "gamma*omega_den*sum(2m_s) must stay below 2^61");
+    if ((u128)(ull)gn * (u128)(ull)j.od * mass >= lim * (u128)(ull)gd)
+      fail(MSLICE_EOVERFLOW, nm == NULL_CPM ? "CPM: gamma*omega_den*n*N must stay below 2^61"
+                                            : "gamma*omega_den*sum(2m_s) must stay below 2^61");
   }
 }
 
 namespace {
+
+// Every level-0 node weighs 1 in CPM's null term.
+__global__ void k_ones(int64_t* x, int64_t N) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x)
+    x[v] = 1;
+}
 
 // k'_v = od*k_v + cstr[s], s the snapshot of v (batches: slice0 gives it;
 // cstr is indexed by global snapshot).
@@ -226,6 +218,25 @@ void setup_null_model(Solver& S) {
   const SupraGraph& G = *S.G0;
   bool any_gs = false;
   for (uint8_t x : S.has_gs_h) any_gs = any_gs || x;
+  if (S.p.cpm) {
+    // node counts as strengths, masses 1: Lambda_s = floor(gamma_s 2^64)
+    S.Tn = G.T > 0 ? G.T : 1;
+    S.lam = c.ws->get<u128>("lam", S.Tn);
+    std::vector<u128> lam(G.T);
+    for (int32_t i = 0; i < G.B; ++i) {
+      const InstInfo& in = G.inst[i];
+      for (int32_t s = in.soff; s < in.soff + in.T; ++s) {
+        const long long gn = any_gs ? S.gs_h[2 * s] : S.gn_h[i], gd = any_gs ? S.gs_h[2 * s + 1] : S.gd_h[i];
+        lam[s] = (((u128)(ull)gn) << P_BITS) / (u128)(ull)gd;
+      }
+    }
+    if (G.T > 0)
+      check_cuda(cudaMemcpyAsync(S.lam, lam.data(), G.T * sizeof(u128), cudaMemcpyHostToDevice, c.stream), "copy");
+    S.kn = c.ws->get<int64_t>("k_null", S.N0 > 0 ? S.N0 : 1);
+    if (G.N > 0) launch(c, k_ones, dim3(grid_for(G.N, 256) < 4096 ? grid_for(G.N, 256) : 4096), dim3(256), 0, S.kn, G.N);
+    sync(c);  // lam is pageable host memory
+    return;
+  }
   if (!S.p.global_null) {
     S.Tn = G.T > 0 ? G.T : 1;
     S.lam = c.ws->get<u128>("lam", S.Tn);

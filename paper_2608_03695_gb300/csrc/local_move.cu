@@ -462,6 +462,7 @@ LevelDev level0_view(const SupraGraph& G, const Solver& S) {
     d.cw = S.cw_d;
     d.ncw = G.ncw;
   }
+  if (S.p.cpm) d.k0 = S.kn;  // CPM: every node weighs 1, snapshots as null slices
   if (S.p.global_null) {
     // one null slice per instance: the instance id (batches) or 0 (v / N)
     d.global_null = 1;

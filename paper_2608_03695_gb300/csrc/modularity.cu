@@ -8,6 +8,8 @@
 //   2mu = sum_s 2m_s + n * sum_{s,r} omega^(sr)  (2*omega*n*(T-1) ordinal).
 // Per-snapshot gamma: each slice term is multiplied by its gamma before the
 // ascending sum, and the sum is subtracted as it is.
+// Temporal CPM: S_s counts nodes (Sigma = node counts) and its slice term is
+// S_s itself (a mass of 1) for every snapshot.
 // The FP64 combination follows one fixed order (slice terms in ascending s,
 // then omega*J, the numerator, the division), with explicitly rounded
 // operations so no contraction changes the result.
@@ -122,7 +124,7 @@ __device__ __forceinline__ double omega_J(const QInst& p, ull Jword, int32_t wei
 // (global model).  gs: per-snapshot gamma (num, den) pairs, when any
 // instance has them.
 __global__ void k_Q(const ull* IJ, const ull* S, const int64_t* two_m, const QInst* qi, int32_t B, int32_t global,
-                    int32_t weighted, const long long* gs, double* Q) {
+                    int32_t cpm, int32_t weighted, const long long* gs, double* Q) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B) return;
   const QInst p = qi[i];
@@ -149,9 +151,10 @@ __global__ void k_Q(const ull* IJ, const ull* S, const int64_t* two_m, const QIn
   for (int s = p.soff; s < p.soff + p.T; ++s) {
     const long long t = two_m[s];
     sum2m += t;
-    if (t > 0) {
+    if (t > 0 || cpm) {
+      // CPM: node counts over a mass of 1
       const u128 x = ((u128)S[2 * s + 1] << 64) | S[2 * s];
-      const double term = __ddiv_rn(u128_to_double(x), __ll2double_rn(t));
+      const double term = cpm ? u128_to_double(x) : __ddiv_rn(u128_to_double(x), __ll2double_rn(t));
       nullsum = __dadd_rn(nullsum, p.gtab ? __dmul_rn(__ddiv_rn(__ll2double_rn(gs[2 * s]), __ll2double_rn(gs[2 * s + 1])),
                                                       term)
                                           : term);
@@ -235,7 +238,7 @@ void modularity(Solver& S, const int32_t* labels0, double* Q) {
   const int64_t span = S.sig.d ? S.sig.rows * S.sig.T : (int64_t)S.sig.h.cap;
   launch(c, k_S, dim3(gsz(span)), dim3(256), smem, S.sig, Tn, acc + 2 * B);
   launch(c, k_Q, dim3(grid_for(B, 128)), dim3(128), 0, (const ull*)acc, (const ull*)(acc + 2 * B),
-         (const int64_t*)G.two_m, (const QInst*)dqi, B, (int32_t)(S.p.global_null ? 1 : 0),
+         (const int64_t*)G.two_m, (const QInst*)dqi, B, (int32_t)(S.p.global_null ? 1 : 0), (int32_t)(S.p.cpm ? 1 : 0),
          (int32_t)(S.cw_d ? 1 : 0), (const long long*)S.gs_d, dQ);
   // B values go straight to the caller's (pageable) array
   check_cuda(cudaMemcpyAsync(Q, dQ, B * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "copy");

@@ -139,6 +139,12 @@ struct mslice_server_s {
     return g.n * std::min<int64_t>((int64_t)g.window.size() + 1, opt.window);
   }
 
+  int null_model() const {
+    return (opt.solve.flags & MSLICE_NULL_GLOBAL) ? NULL_SUPRA_GLOBAL
+           : (opt.solve.flags & MSLICE_NULL_CPM) ? NULL_CPM
+                                                  : NULL_MULTISLICE;
+  }
+
   int64_t footprint(const SrvRequest& r) const {
     const SrvGraph& g = *graphs[r.graph];
     const int W = opt.window;
@@ -148,8 +154,8 @@ struct mslice_server_s {
     const int64_t w = keep + 1;
     const int64_t N = g.n * w;
     nnz += 2 * g.n * (w - 1);
-    const int64_t global = (opt.solve.flags & MSLICE_NULL_GLOBAL) ? 8 : 0;  // the strengths k'
-    return (274 + global) * N + 52 * nnz + (1 << 20);
+    const int64_t strengths = null_model() != NULL_MULTISLICE ? 8 : 0;  // k' or CPM's node weights
+    return (274 + strengths) * N + 52 * nnz + (1 << 20);
   }
 };
 
@@ -225,8 +231,8 @@ void run_batch(mslice_server_s* s, Worker& slot, std::vector<SrvRequest*>& batch
         nnz.push_back(g.nnz[b]);
       }
       build_supra(c, ip, ix, wt, nnz, g.n, *p.G);
-      check_bounds(g.n, p.G->T, p.G->two_m_host.data(), s->opt.gamma_num, s->opt.gamma_den, s->opt.omega_num,
-                   s->opt.omega_den, (s->opt.solve.flags & MSLICE_NULL_GLOBAL) != 0);
+      check_bounds(g.n, p.G->T, 0, p.G->two_m_host.data(),
+                   InstParams{s->opt.gamma_num, s->opt.gamma_den, s->opt.omega_num, s->opt.omega_den}, s->null_model());
       parts.push_back(std::move(p));
     } catch (const Error& e) {
       finish(s, r, e.code, e.msg);
@@ -269,7 +275,8 @@ void run_batch(mslice_server_s* s, Worker& slot, std::vector<SrvRequest*>& batch
     sp.max_levels = s->opt.solve.max_levels;
     sp.n_iterations = s->opt.solve.n_iterations;
     sp.seed = s->opt.solve.seed;
-    sp.global_null = (s->opt.solve.flags & MSLICE_NULL_GLOBAL) != 0;
+    sp.global_null = s->null_model() == NULL_SUPRA_GLOBAL;
+    sp.cpm = s->null_model() == NULL_CPM;
     for (int k = 0; k < 4; ++k)
       if (s->opt.solve.tier_cuts[0] || s->opt.solve.tier_cuts[1] || s->opt.solve.tier_cuts[2] ||
           s->opt.solve.tier_cuts[3])
@@ -412,6 +419,8 @@ int mslice_server_create(const mslice_server_opts* o, mslice_server* out) {
     const mslice_opts& so = opt.solve;
     if (so.n_iterations < 1 || so.K < 1 || so.K > 64 || so.max_rounds < 1 || so.max_levels < 1)
       fail(MSLICE_EINVAL, "bad schedule options");
+    if ((so.flags & MSLICE_NULL_GLOBAL) && (so.flags & MSLICE_NULL_CPM))
+      fail(MSLICE_EINVAL, "MSLICE_NULL_GLOBAL and MSLICE_NULL_CPM exclude each other");
     if (so.tier_cuts[0] || so.tier_cuts[1] || so.tier_cuts[2] || so.tier_cuts[3]) {
       int32_t lo = 0;
       for (int k = 0; k < 4; ++k) {
@@ -675,8 +684,8 @@ int mslice_server_window_restore(mslice_server s, int32_t graph_id, const mslice
       SupraGraph check;
       check.mem.stream = c.stream;
       build_supra(c, ip, ix, wt, nnz, n, check);
-      check_bounds(n, check.T, check.two_m_host.data(), s->opt.gamma_num, s->opt.gamma_den, s->opt.omega_num,
-                   s->opt.omega_den, (s->opt.solve.flags & MSLICE_NULL_GLOBAL) != 0);
+      check_bounds(n, check.T, 0, check.two_m_host.data(),
+                   InstParams{s->opt.gamma_num, s->opt.gamma_den, s->opt.omega_num, s->opt.omega_den}, s->null_model());
     }
     // valid: the ring's buffers 0..nslices-1 take the snapshots
     g.mem.stream = c.stream;

@@ -15,7 +15,11 @@ struct SolveParams {
   TierCuts cuts;          // degree cuts between the decision tiers
   bool autotune = false;  // choose the cuts by timing round 0 of level 0
   bool global_null = false;  // plain modularity of the supra-graph instead of Q_MS
+  bool cpm = false;          // the temporal Constant Potts Model instead of Q_MS
 };
+
+// Null models of a solve (the check_bounds argument).
+enum NullModel { NULL_MULTISLICE = 0, NULL_SUPRA_GLOBAL = 1, NULL_CPM = 2 };
 
 // CUDA-event phase timing: events recorded on the context's stream.
 struct PhaseClock {
@@ -169,16 +173,13 @@ struct InstParams {
 long long pair_num(const InstParams& j, int32_t coupling, int32_t T, int32_t s, int32_t r);
 
 // Fails with MSLICE_EOVERFLOW unless the 128-bit move keys of a graph with n
-// nodes per snapshot and snapshot masses two_m[0..T) stay in range for this
-// gamma and omega: 2M' = od * sum 2m_s + 2 on n (T-1) < 2^61 and
-// gamma od sum 2m_s < 2^61 (gamma 2M' < 2^61 under the global null model,
-// whose strengths include the coupling).
-void check_bounds(int64_t n, int32_t T, const int64_t* two_m, long long gn, long long gd, long long on, long long od,
-                  bool global_null = false);
-// The same for the general form: 2M' = od * sum 2m_s + n * sum_{s,r} cw(s,r)
-// < 2^61, and gamma_s od sum 2m_s < 2^61 for every s (gamma 2M' < 2^61 under
-// the global null model).
-void check_bounds(int64_t n, int32_t T, int32_t coupling, const int64_t* two_m, const InstParams& j, bool global_null);
+// nodes per snapshot, snapshot masses two_m[0..T) and this coupling pattern
+// stay in range for the instance's gamma and omega under null model nm:
+// 2M' = od * sum 2m_s + n * sum_{s,r} omega_num^(sr) < 2^61, and
+// gamma_s od sum 2m_s < 2^61 for every s (Q_MS); gamma 2M' < 2^61 (global
+// model, whose strengths include the coupling); gamma_s od n N < 2^61 (CPM,
+// whose null sums count nodes).
+void check_bounds(int64_t n, int32_t T, int32_t coupling, const int64_t* two_m, const InstParams& j, int nm);
 
 // The null model of a solve: S.Tn, the quantised coefficients S.lam (one per
 // snapshot, or one per instance from 2M' for the global model) and, for the
