@@ -28,6 +28,7 @@ __all__ = [
     "dcsbm_powerlaw_temporal",
     "random_temporal",
     "cliques_temporal",
+    "contact_temporal",
     "config_graph",
     "RECIPES",
 ]
@@ -372,6 +373,37 @@ def cliques_temporal(clique_sizes, T: int, w: int = 1):
     return [Snapshot(snap.indptr.copy(), snap.indices.copy(), snap.weights.copy()) for _ in range(T)]
 
 
+def contact_temporal(n: int, T: int, n_groups: int, static_edges: int, contacts: int, within_frac: float,
+                     seed: int = 0):
+    """Face-to-face contact sequences, the shape of a school contact dataset
+    (a few hundred people in classes, thousands of very sparse snapshots):
+    n people in n_groups classes of near-equal size; a fixed pool of
+    static_edges distinct pairs, round(within_frac * static_edges) of them
+    inside a class (at most every such pair) and the rest between classes;
+    snapshot t holds Poisson(contacts / T) pairs drawn from the pool without
+    replacement, weight 1.  Returns (snapshots, class of every person)."""
+    if n > 20000:
+        raise ValueError("contact_temporal enumerates node pairs; keep n <= 20000")
+    rng = np.random.default_rng(seed)
+    group_of = rng.permutation(np.arange(n) % max(n_groups, 1))
+    iu, ju = np.triu_indices(n, k=1)
+    same = group_of[iu] == group_of[ju]
+    within = np.flatnonzero(same)
+    cross = np.flatnonzero(~same)
+    m_in = min(int(round(within_frac * static_edges)), len(within))
+    m_out = min(static_edges - m_in, len(cross))
+    pick = np.concatenate([within[rng.choice(len(within), m_in, replace=False)] if m_in else np.zeros(0, np.int64),
+                           cross[rng.choice(len(cross), m_out, replace=False)] if m_out else np.zeros(0, np.int64)])
+    pu, pv = iu[pick].astype(np.int64), ju[pick].astype(np.int64)
+    rate = contacts / max(T, 1)
+    snaps = []
+    for _ in range(T):
+        k = min(int(rng.poisson(rate)), len(pick))
+        idx = rng.choice(len(pick), k, replace=False) if k else np.zeros(0, np.int64)
+        snaps.append(csr_from_edges(n, pu[idx], pv[idx], np.ones(k, np.int32)))
+    return snaps, group_of
+
+
 # Workload recipes.  Rationals are (numerator, denominator) pairs.
 # Named recipes: a planted partition (T=4, n=1,000), the power-law temporal
 # graph of the benchmark (T=16, n=100,000) and its large T=64, n=1,000,000
@@ -383,6 +415,10 @@ RECIPES = {
             size_max=5000, mixing=0.3, churn=0.05, w_max=8, seed=2, gamma=(1, 1), omega=(1, 1)),
     "powerlaw_t64_n1m": dict(kind="dcsbm", n=1_000_000, T=64, deg_exp=2.3, mean_deg=16.0, size_exp=1.5, size_min=20,
             size_max=5000, mixing=0.4, churn=0.05, w_max=16, seed=4, gamma=(1, 1), omega=(1, 1)),
+    # the shape of the paper's School contact dataset (Table 1: 327 people, 7,004 static and 188,508
+    # temporal edges, 7,375 snapshots, 9 classes)
+    "school_t7375_n327": dict(kind="contact", n=327, T=7375, n_groups=9, static_edges=7004, contacts=188508,
+            within_frac=0.7, seed=6, gamma=(1, 1), omega=(1, 1)),
 }
 
 
@@ -458,6 +494,11 @@ def recipe_graph(recipe: str | dict, scale_n: int | None = None, T: int | None =
     c = dict(RECIPES[recipe]) if isinstance(recipe, str) else dict(recipe)
     n = scale_n if scale_n is not None else c["n"]
     TT = T if T is not None else c["T"]
+    if c["kind"] == "contact":
+        # fewer snapshots keep the contacts per snapshot
+        snaps, _ = contact_temporal(n, TT, c["n_groups"], c["static_edges"], int(round(c["contacts"] * TT / c["T"])),
+                                    c["within_frac"], c["seed"])
+        return snaps
     if c["kind"] == "planted":
         snaps, _ = planted_partition_temporal(n, TT, c["n_blocks"], c["p_in"], c["p_out"], c["switch_frac"],
                                               c.get("churn"), c["w_max"], c["seed"])

@@ -1136,3 +1136,67 @@ def test_cpm_bound():
         oracle.leiden(snaps, gamma, omega, null="cpm")
     assert e.value.code == oracle.EOVERFLOW
     oracle.leiden(snaps, (2 ** 22, 1), omega, null="cpm", n_iterations=1, max_rounds=1, max_levels=1)
+
+
+# ----------------------------------------------------------------- windowed optimisation
+# Windows of W snapshots over a long sequence, warm-started from the previous
+# window and stitched through the overlap (the oracle's leiden_windowed
+# states the procedure).  Pinned by: one window covering the sequence is the
+# plain solve; persistent cliques keep one label each across every window;
+# the final labels restricted to the snapshots each window wrote last are
+# that window's partition; window starts cover the sequence with overlaps.
+def test_window_starts():
+    assert oracle.window_starts(10, 32, 16) == [0]
+    assert oracle.window_starts(32, 32, 16) == [0]
+    assert oracle.window_starts(40, 32, 16) == [0, 8]
+    assert oracle.window_starts(100, 10, 3)[-1] == 90
+    for T, W, S in [(100, 10, 3), (57, 8, 7), (64, 8, 1), (300, 32, 16)]:
+        st = oracle.window_starts(T, W, S)
+        assert st[0] == 0 and st[-1] + W == T
+        assert all(0 < b - a <= S for a, b in zip(st, st[1:]))  # every pair overlaps
+
+
+def test_windowed_single_window_is_the_plain_solve():
+    snaps, _ = synth.planted_partition_temporal(60, 5, n_blocks=3, p_in=0.3, p_out=0.03, switch_frac=0.1, seed=3)
+    lab, Qs, nw = oracle.leiden_windowed(snaps, 8, 3, (3, 2), (1, 2))
+    ref, Q, _ = oracle.leiden(snaps, (3, 2), (1, 2))
+    assert nw == 1 and np.array_equal(lab, ref) and Qs == [Q]
+
+
+def test_windowed_persistent_cliques_keep_their_labels():
+    snaps = synth.cliques_temporal([5, 6, 7, 4], T=40, w=2)
+    for W, S in [(8, 4), (6, 5), (5, 1)]:
+        lab, Qs, nw = oracle.leiden_windowed(snaps, W, S)
+        full, _, _ = oracle.leiden(snaps)
+        assert nw > 1
+        assert np.array_equal(lab, full), (W, S)  # four labels over all 40 snapshots
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_windowed_regions_are_the_window_partitions(seed):
+    rng = np.random.default_rng(2400 + seed)
+    T = int(rng.integers(12, 40))
+    n = int(rng.integers(8, 40))
+    snaps, _ = synth.planted_partition_temporal(n, T, n_blocks=3, p_in=0.3, p_out=0.03, switch_frac=0.1,
+                                                churn=0.1, w_max=4, seed=seed)
+    W = int(rng.integers(3, 9))
+    S = int(rng.integers(1, W))
+    lab, Qs, nw = oracle.leiden_windowed(snaps, W, S)
+    starts = oracle.window_starts(T, W, S)
+    assert nw == len(starts) == len(Qs)
+    # re-solve every window from the same warm starts and compare, on the
+    # snapshots it wrote last, the partitions (as sets of supra-nodes)
+    prev = None
+    for k, a in enumerate(starts):
+        init = None
+        if prev is not None:
+            e = a - starts[k - 1]
+            init = np.concatenate([prev[min(j + e, W - 1) * n:(min(j + e, W - 1) + 1) * n]
+                                   for j in range(W)]).astype(np.int32)
+        part, Q, _ = oracle.leiden(snaps[a:a + W], init=init)
+        assert Q == Qs[k]
+        end = starts[k + 1] if k + 1 < len(starts) else T
+        region = slice(0, (end - a) * n)
+        got, want = lab[a * n:end * n], part[region]
+        assert len(set(zip(got.tolist(), want.tolist()))) == len(set(want.tolist())) == len(set(got.tolist()))
+        prev = part
