@@ -253,6 +253,38 @@ int mslice_modularity_noalloc(const mslice_csr* slices, int32_t T, const int32_t
                               int64_t gamma_den, int64_t omega_num, int64_t omega_den, void* stream,
                               double* Q_out);
 
+/* ---- Windowed optimisation of long snapshot sequences ----
+ *
+ * Sec. 4 names windowed optimisation for sequences whose supra-graph is too
+ * long to solve at once (its 7,375-snapshot case) and gives no procedure.
+ * This entry point solves windows of W snapshots one after another and
+ * stitches their labels:
+ *   - windows start at 0, stride, 2*stride, ..., the last start clamped to
+ *     T - W (every window holds W snapshots; one window [0, T) when T <= W);
+ *   - window 0 starts from singletons; window k is warm-started: its local
+ *     snapshot j takes the previous window's labels of local snapshot
+ *     min(j + e, W - 1), e = start_k - start_{k-1} (the serving rule);
+ *   - stitching: window k's communities in order of first occurrence; one
+ *     whose first supra-node lies in the overlap (its first W - e snapshots)
+ *     continues that supra-node's stitched label unless an earlier community
+ *     of the window took it; any other gets a fresh label; window k's labels
+ *     overwrite its snapshots' stitched labels;
+ *   - labels_out (host int32[n*T]) gets the stitched labels renumbered by
+ *     first occurrence.
+ * slices: T snapshots (host arrays, or device arrays with MSLICE_DEVICE_PTRS
+ * in o->flags); o: gamma, omega, schedule and null-model flags (nullable:
+ * defaults; stop_level must be -1); stream: cudaStream_t (NULL: a private
+ * one); Q_windows (nullable): the Q of each window's solve, at most q_cap of
+ * them; *n_windows (nullable): the number of windows; st (nullable):
+ * counters and phase times summed over the windows.  Every window is a full
+ * solve of n*W supra-nodes; the whole sequence is never built at once.
+ * Errors: EINVAL (T < 1, W < 1, stride outside [1, W) when T > W, n*W above
+ * 2^31 - 1, malformed snapshots, bad options), EOVERFLOW (a window outside
+ * the key bound), ENOMEM, ECUDA. */
+int mslice_leiden_windowed(const mslice_csr* slices, int32_t T, int32_t W, int32_t stride, const mslice_opts* o,
+                           void* stream, int32_t* labels_out, double* Q_windows, int32_t q_cap,
+                           int32_t* n_windows, mslice_stats* st);
+
 /* ---- Batches: many (graph, gamma, omega) solves in one pass ----
  *
  * Leiden's partition depends on the resolution gamma and the coupling omega

@@ -43,7 +43,7 @@ _COUPLINGS = {"ordinal": MSLICE_ORDINAL, "categorical": MSLICE_CATEGORICAL}
 # every symbol include/mslice.h declares
 EXPORTS = ["mslice_default_opts", "mslice_build", "mslice_build_ex", "mslice_leiden", "mslice_leiden_ex",
            "mslice_leiden_general", "mslice_modularity", "mslice_modularity_ex", "mslice_modularity_general",
-           "mslice_modularity_noalloc", "mslice_info", "mslice_batch_add_general",
+           "mslice_modularity_noalloc", "mslice_info", "mslice_batch_add_general", "mslice_leiden_windowed",
            "mslice_kernel_launches", "mslice_free", "mslice_last_error", "mslice_batch_create",
            "mslice_batch_add", "mslice_batch_run", "mslice_batch_results", "mslice_batch_info",
            "mslice_batch_clear", "mslice_batch_kernel_launches", "mslice_batch_free",
@@ -123,6 +123,7 @@ def lib():
         L.mslice_leiden_general.argtypes = [P, P, P, P, P, P, P]
         L.mslice_modularity_general.argtypes = [P, P, P, P, P]
         L.mslice_batch_add_general.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, P, P, P]
+        L.mslice_leiden_windowed.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, P, P, P, P, C.c_int32, P, P]
         L.mslice_modularity.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, P]
         L.mslice_modularity_ex.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int32, P]
         L.mslice_modularity_noalloc.argtypes = [P, C.c_int32, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, P, P]
@@ -547,3 +548,51 @@ def mslice_build(snaps, omega=(1, 1), stream=None, device_ptrs=False, host_tenso
 
 
 build_graph = mslice_build
+
+
+def _csr_array(snaps, device_ptrs=False, host_tensors=False):
+    T = len(snaps)
+    arr = (Csr * max(T, 1))()
+    keep = []
+    for s, sn in enumerate(snaps):
+        if device_ptrs or host_tensors:
+            ip, ix, w = sn.indptr, sn.indices, sn.weights
+            n = ip.numel() - 1
+        else:
+            ip = np.ascontiguousarray(sn.indptr, dtype=np.int64)
+            ix = np.ascontiguousarray(sn.indices, dtype=np.int32)
+            w = np.ascontiguousarray(sn.weights, dtype=np.int32)
+            n = len(ip) - 1
+        keep += [ip, ix, w]
+        arr[s] = Csr(n, _ptr(ip).value, _ptr(ix).value if _ptr(ix) is not None else None,
+                     _ptr(w).value if _ptr(w) is not None else None)
+    return arr, keep
+
+
+def mslice_leiden_windowed(snaps, W, stride, gamma=(1, 1), omega=(1, 1), null="multislice", n_iterations=2, K=4,
+                           max_rounds=100, max_levels=32, seed=0, stream=None, device_ptrs=False):
+    """Windowed optimisation of a long snapshot sequence
+    (``mslice_leiden_windowed``): windows of W snapshots at the given stride,
+    warm-started and stitched through their overlaps.  Returns (labels
+    int32[n*T], Q of every window, stats)."""
+    arr, keep = _csr_array(snaps, device_ptrs=device_ptrs)
+    T = len(snaps)
+    n = (snaps[0].indptr.numel() if device_ptrs else len(snaps[0].indptr)) - 1 if T else 0
+    o = default_opts()
+    o.gamma_num, o.gamma_den = gamma
+    o.omega_num, o.omega_den = omega
+    o.n_iterations, o.K, o.max_rounds, o.max_levels, o.seed = n_iterations, K, max_rounds, max_levels, seed
+    o.flags = _NULLS[null] | (MSLICE_DEVICE_PTRS if device_ptrs else 0)
+    labels = np.zeros(max(n * T, 1), dtype=np.int32)
+    cap = T + 1
+    Qw = np.zeros(cap, dtype=np.float64)
+    nw = C.c_int32(0)
+    st = Stats()
+    s = C.c_void_p(stream) if stream is not None else None
+    _check(lib().mslice_leiden_windowed(C.cast(arr, C.c_void_p), T, W, stride, C.byref(o), s, _ptr(labels),
+                                        _ptr(Qw), cap, C.byref(nw), C.byref(st)), "mslice_leiden_windowed")
+    del keep
+    return labels[: n * T].copy(), [float(x) for x in Qw[: nw.value]], _stats_dict(st)
+
+
+leiden_windowed = mslice_leiden_windowed

@@ -12,6 +12,7 @@
 #include <functional>
 #include <new>
 #include <string>
+#include <unordered_set>
 #include <vector>
 
 #include "../../include/mslice.h"
@@ -845,3 +846,232 @@ int64_t mslice_batch_kernel_launches(mslice_batch b) { return b ? b->launches : 
 void mslice_batch_free(mslice_batch b) { delete b; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Windowed optimisation of a long snapshot sequence.  Sec. 4 names windowed
+// optimisation for its 7,375-snapshot case and gives no procedure; the
+// reading:
+//   * windows of W snapshots start at 0, stride, 2*stride, ..., the last start
+//     clamped to T - W so every window holds W snapshots and the last ends at
+//     T (one window [0, T) when T <= W);
+//   * window 0 starts from singletons; window k is warm-started by the
+//     serving rule with the actual shift e = start_k - start_{k-1}: local
+//     snapshot j takes the previous window's labels of local snapshot
+//     min(j + e, W - 1);
+//   * stitching: window k's communities in order of first occurrence; one
+//     whose first supra-node lies in the overlap (the first W - e snapshots)
+//     continues the stitched label of that supra-node unless an earlier
+//     community of the window took it; any other gets the next fresh label;
+//     window k's labels then overwrite its snapshots' stitched labels;
+//   * the stitched labels are renumbered by first occurrence at the end.
+// Each window is a complete solve (build + Leiden + Q) on the caller's
+// stream; stitching runs on the host over the window's labels.
+
+namespace mslice {
+namespace windowed {
+
+__global__ void k_window_init(const int32_t* prev, int64_t n, int32_t w, int32_t shift, int32_t* init) {
+  const int64_t N = n * w;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = v / n, i = v - j * n;
+    init[v] = prev[min(j + shift, (int64_t)w - 1) * n + i];
+  }
+}
+
+std::vector<int32_t> window_starts(int32_t T, int32_t W, int32_t stride) {
+  std::vector<int32_t> st{0};
+  if (T <= W) return st;
+  while (st.back() + W < T) st.push_back(std::min(st.back() + stride, T - W));
+  return st;
+}
+
+}  // namespace windowed
+}  // namespace mslice
+
+extern "C" int mslice_leiden_windowed(const mslice_csr* slices, int32_t T, int32_t W, int32_t stride,
+                                      const mslice_opts* o, void* stream, int32_t* labels_out, double* Q_windows,
+                                      int32_t q_cap, int32_t* n_windows, mslice_stats* st) {
+  cudaStream_t own = nullptr;
+  Workspace ws;
+  SupraGraph G;
+  StreamFan fan;
+  void* pinned = nullptr;
+  const int rc = guard([&] {
+    if (!slices || T < 1) fail(MSLICE_EINVAL, "need T >= 1 snapshots");
+    if (W < 1) fail(MSLICE_EINVAL, "W must be >= 1");
+    if (T > W && (stride < 1 || stride >= W)) fail(MSLICE_EINVAL, "stride must lie in [1, W) so windows overlap");
+    mslice_opts opt;
+    mslice_default_opts(&opt);
+    if (o) opt = *o;
+    check_opts(opt);
+    if (opt.stop_level >= 0) fail(MSLICE_EINVAL, "debug stops apply to single solves only");
+    if (!rational_ok(opt.gamma_num, opt.gamma_den, false)) fail(MSLICE_EINVAL, "gamma must be a rational > 0");
+    if (!rational_ok(opt.omega_num, opt.omega_den, true)) fail(MSLICE_EINVAL, "omega must be a rational >= 0");
+    const int nm = null_model_of(opt.flags);
+    const int64_t n = slices[0].n;
+    const int32_t Wn = std::min(W, T);
+    if (n < 0 || n > INT32_MAX || n * (int64_t)Wn > INT32_MAX) fail(MSLICE_EINVAL, "n*W must fit in int32");
+    for (int32_t s = 0; s < T; ++s)
+      if (slices[s].n != n) fail(MSLICE_EINVAL, "snapshots must have the same n");
+    if (!labels_out && n > 0) fail(MSLICE_EINVAL, "null labels_out");
+    const bool dev = (opt.flags & MSLICE_DEVICE_PTRS) != 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!s) {
+      check_cuda(cudaStreamCreate(&own), "stream");
+      s = own;
+    }
+    ws.stream = s;
+    G.mem.stream = s;
+    keep_pool_memory();
+    check_cuda(cudaMallocHost(&pinned, PINNED_BYTES), "pinned buffer");
+    if (!std::getenv("MSLICE_SERIAL_TIERS")) fan.create();
+    Ctx c;
+    c.stream = s;
+    c.fan = fan.fork ? &fan : nullptr;
+    c.ws = &ws;
+    c.d_status = ws.get<unsigned>("status", 4);
+    c.pinned = pinned;
+    check_cuda(cudaMemsetAsync(c.d_status, 0, 16, s), "memset");
+    // snapshot arrays on the device: one staging copy per array kind
+    std::vector<int64_t> nnz(T), eoff(T + 1, 0);
+    for (int32_t t = 0; t < T; ++t) {
+      if (n > 0 && !slices[t].indptr) fail(MSLICE_EINVAL, "null indptr");
+      int64_t z = 0;
+      if (n > 0) {
+        if (dev)
+          check_cuda(cudaMemcpy(&z, slices[t].indptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost), "copy");
+        else
+          z = slices[t].indptr[n];
+      }
+      if (z < 0) fail(MSLICE_EINVAL, "negative nnz");
+      if (z > 0 && (!slices[t].indices || !slices[t].weights)) fail(MSLICE_EINVAL, "null indices/weights");
+      nnz[t] = z;
+      eoff[t + 1] = eoff[t] + z;
+    }
+    std::vector<const int64_t*> ip(T);
+    std::vector<const int32_t*> ix(T), wt(T);
+    if (dev) {
+      for (int32_t t = 0; t < T; ++t) {
+        ip[t] = slices[t].indptr;
+        ix[t] = slices[t].indices;
+        wt[t] = slices[t].weights;
+      }
+    } else {
+      std::vector<int64_t> hip((size_t)T * (n + 1));
+      std::vector<int32_t> hix(eoff[T]), hwt(eoff[T]);
+      for (int32_t t = 0; t < T; ++t) {
+        if (n > 0) std::memcpy(&hip[(size_t)t * (n + 1)], slices[t].indptr, (n + 1) * sizeof(int64_t));
+        if (nnz[t] > 0) {
+          std::memcpy(&hix[eoff[t]], slices[t].indices, nnz[t] * sizeof(int32_t));
+          std::memcpy(&hwt[eoff[t]], slices[t].weights, nnz[t] * sizeof(int32_t));
+        }
+      }
+      int64_t* dip = ws.get<int64_t>("w_ip", hip.size());
+      int32_t* dix = ws.get<int32_t>("w_ix", eoff[T]);
+      int32_t* dwt = ws.get<int32_t>("w_wt", eoff[T]);
+      if (!hip.empty())
+        check_cuda(cudaMemcpyAsync(dip, hip.data(), hip.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s), "copy");
+      if (eoff[T] > 0) {
+        check_cuda(cudaMemcpyAsync(dix, hix.data(), eoff[T] * sizeof(int32_t), cudaMemcpyHostToDevice, s), "copy");
+        check_cuda(cudaMemcpyAsync(dwt, hwt.data(), eoff[T] * sizeof(int32_t), cudaMemcpyHostToDevice, s), "copy");
+      }
+      sync(c);  // the host staging arrays go out of scope
+      for (int32_t t = 0; t < T; ++t) {
+        ip[t] = dip + (size_t)t * (n + 1);
+        ix[t] = dix + eoff[t];
+        wt[t] = dwt + eoff[t];
+      }
+    }
+    const std::vector<int32_t> starts = windowed::window_starts(T, W, stride);
+    if (n_windows) *n_windows = (int32_t)starts.size();
+    const InstParams job{opt.gamma_num, opt.gamma_den, opt.omega_num, opt.omega_den};
+    SolveParams sp;
+    sp.K = opt.K;
+    sp.max_rounds = opt.max_rounds;
+    sp.max_levels = opt.max_levels;
+    sp.n_iterations = opt.n_iterations;
+    sp.seed = opt.seed;
+    sp.cuts = cuts_of(opt);
+    sp.global_null = nm == NULL_SUPRA_GLOBAL;
+    sp.cpm = nm == NULL_CPM;
+    const int64_t Nw = n * Wn;
+    int32_t* prev = ws.get<int32_t>("w_prev", Nw);
+    int32_t* init = ws.get<int32_t>("w_init", Nw);
+    int32_t* out = ws.get<int32_t>("w_out", Nw);
+    std::vector<int64_t> stitched((size_t)n * T, -1);
+    std::vector<int32_t> lab(Nw);
+    std::vector<int64_t> first;
+    int64_t fresh = 0;
+    mslice_stats acc;
+    std::memset(&acc, 0, sizeof(acc));
+    for (size_t k = 0; k < starts.size(); ++k) {
+      const int32_t a = starts[k], b = std::min(a + W, T), w = b - a;
+      const int32_t e = k == 0 ? 0 : a - starts[k - 1];
+      build_supra(c, std::vector<const int64_t*>(ip.begin() + a, ip.begin() + b),
+                  std::vector<const int32_t*>(ix.begin() + a, ix.begin() + b),
+                  std::vector<const int32_t*>(wt.begin() + a, wt.begin() + b),
+                  std::vector<int64_t>(nnz.begin() + a, nnz.begin() + b), n, G);
+      check_bounds(n, w, 0, G.two_m_host.data(), job, nm);
+      const int64_t N = n * w;
+      if (k > 0 && N > 0)
+        launch(c, windowed::k_window_init, dim3(grid_for(N, 256) < 4096 ? grid_for(N, 256) : 4096), dim3(256), 0,
+               (const int32_t*)prev, n, w, e, init);
+      Solver S;
+      RunOut ro;
+      run_leiden(c, G, {job}, sp, -1, 0, 0, k > 0 ? init : nullptr, out, S, ro);
+      if (N > 0) {
+        check_cuda(cudaMemcpyAsync(lab.data(), out, N * sizeof(int32_t), cudaMemcpyDeviceToHost, s), "copy");
+        check_cuda(cudaMemcpyAsync(prev, out, N * sizeof(int32_t), cudaMemcpyDeviceToDevice, s), "copy");
+      }
+      sync(c);
+      if (Q_windows && (int32_t)k < q_cap && !ro.Q.empty()) Q_windows[k] = ro.Q[0];
+      acc.lm_rounds += S.lm_rounds;
+      acc.lm_edges += S.lm_edges;
+      acc.lm_moves += S.lm_moves;
+      acc.ms_total += ro.ms[0];
+      acc.ms_local_move += ro.ms[1];
+      acc.ms_refine += ro.ms[2];
+      acc.ms_aggregate += ro.ms[3];
+      acc.ms_modularity += ro.ms[4];
+      acc.iterations = std::max<int32_t>(acc.iterations, (int32_t)ro.iterations);
+      acc.levels = std::max<int32_t>(acc.levels, (int32_t)ro.levels);
+      // stitching (canonical labels: first occurrence order is label order)
+      int32_t ncomm = 0;
+      for (int64_t v = 0; v < N; ++v) ncomm = std::max(ncomm, lab[v] + 1);
+      first.assign(ncomm, N);
+      for (int64_t v = N - 1; v >= 0; --v) first[lab[v]] = v;
+      const int64_t overlap = k == 0 ? 0 : (int64_t)(w - e) * n;
+      std::vector<int64_t> map(ncomm);
+      std::unordered_set<int64_t> used;
+      for (int32_t cc = 0; cc < ncomm; ++cc) {
+        bool cont = false;
+        if (first[cc] < overlap) {
+          const int64_t L = stitched[(size_t)a * n + first[cc]];
+          if (used.insert(L).second) {
+            map[cc] = L;
+            cont = true;
+          }
+        }
+        if (!cont) map[cc] = fresh++;
+      }
+      for (int64_t v = 0; v < N; ++v) stitched[(size_t)a * n + v] = map[lab[v]];
+    }
+    // renumber by first occurrence
+    std::map<int64_t, int32_t> seen;
+    for (size_t v = 0; v < stitched.size(); ++v) {
+      auto it = seen.find(stitched[v]);
+      if (it == seen.end()) it = seen.emplace(stitched[v], (int32_t)seen.size()).first;
+      labels_out[v] = it->second;
+    }
+    acc.out_n = (int64_t)stitched.size();
+    acc.kernel_launches = c.launches;
+    for (int kk = 0; kk < 4; ++kk) acc.tier_cuts[kk] = sp.cuts.t[kk];
+    if (st) *st = acc;
+  });
+  ws.release_all();
+  G.mem.release_all();
+  fan.destroy();
+  if (pinned) cudaFreeHost(pinned);
+  if (own) cudaStreamDestroy(own);
+  return rc;
+}

@@ -103,6 +103,18 @@ def cases():
         return [dict(stream=stream, W=W)]
 
     out["serving_chain"] = serving_chain
+
+    def school_full():
+        # the school-shaped contact sequence (n = 327, T = 7,375) solved whole
+        return [dict(snaps=synth.recipe_graph("school_t7375_n327"), gamma=(1, 1), omega=(1, 1))]
+
+    out["school_t7375_full"] = school_full
+
+    def school_windowed():
+        # the same sequence in windows of 64 snapshots at stride 32
+        return [dict(snaps=synth.recipe_graph("school_t7375_n327"), W=64, stride=32)]
+
+    out["school_t7375_windowed"] = school_windowed
     return out
 
 
@@ -117,6 +129,10 @@ def run_solve(oracle, s):
             res.append({"labels": digest_labels(lab), "Q": repr(Q)})
             prev = lab
         return {"input": digest_snaps(stream), "chain": res}
+    if "W" in s:  # windowed optimisation: stitched labels and every window's Q
+        lab, Qs, nw = oracle.leiden_windowed(s["snaps"], s["W"], s["stride"])
+        return {"input": digest_snaps(s["snaps"]), "W": s["W"], "stride": s["stride"], "labels": digest_labels(lab),
+                "windows": nw, "Q_windows": [repr(q) for q in Qs], "Q": repr(oracle.modularity(s["snaps"], lab))}
     null = s.get("null", "multislice")
     lab, Q, st = oracle.leiden(s["snaps"], s["gamma"], s["omega"], null=null)
     return {"input": digest_snaps(s["snaps"]), "gamma": list(s["gamma"]), "omega": list(s["omega"]), "null": null,

@@ -70,6 +70,16 @@ def test_host_side_rejections_need_no_gpu():
     assert L.mslice_server_window_read(None, 0, 0, None, None, None, None) == pkg.MSLICE_EINVAL
     assert L.mslice_server_window_restore(None, 0, None, 0, None) == pkg.MSLICE_EINVAL
     L.mslice_server_free(None)
+    # general forms and windowed optimisation: null handles, bad windows
+    assert L.mslice_leiden_general(None, None, None, None, None, None, None) == pkg.MSLICE_EINVAL
+    assert L.mslice_modularity_general(None, None, None, None, None) == pkg.MSLICE_EINVAL
+    assert L.mslice_batch_add_general(None, None, 1, 1, 1, 1, None, None, None) == pkg.MSLICE_EINVAL
+    from paper_2608_03695_gb300 import synth
+    snaps = synth.random_temporal(5, 6, p=0.4, seed=1)
+    for W, S in [(0, 1), (3, 0), (3, 3)]:
+        with pytest.raises(pkg.MsliceError) as e:
+            pkg.leiden_windowed(snaps, W, S)
+        assert e.value.code == pkg.MSLICE_EINVAL
     o = pkg.ServerOpts()
     L.mslice_server_default_opts(C.byref(o))
     assert (o.window, o.n_slots, o.max_batch, o.hbm_budget, o.max_batch_nodes) == (8, 2, 64, 0, 1 << 21)

@@ -12,7 +12,9 @@ library changes the generated graph) the oracle is run live instead.
 * four full-size graphs of the batched workload at two (gamma, omega) each,
   as one batch;
 * a serving chain: the smallest live graph of the serving workload through
-  11 snapshots with windows of 8.
+  11 snapshots with windows of 8;
+* the school-shaped contact sequence (n = 327, T = 7,375) solved whole, and
+  in windows of 64 snapshots at stride 32.
 """
 import json
 import os
@@ -135,3 +137,22 @@ def test_serving_chain_full_size():
             lab, info = srv.wait(rid)
             assert fsc.digest_labels(lab) == exp[t]["labels"], t
             assert q_ok(info["Q"], exp[t]["Q"])
+
+
+def test_school_sequence_whole_and_windowed():
+    s = fsc.cases()["school_t7375_full"]()[0]
+    exp = expected("school_t7375_full", [s])[0]
+    with pkg.mslice_build(s["snaps"]) as h:
+        lab, Q, st = h.mslice_leiden()
+    assert fsc.digest_labels(lab) == exp["labels"]
+    assert q_ok(Q, exp["Q"])
+    for k in ("iterations", "levels", "lm_rounds", "lm_edges", "lm_moves"):
+        assert st[k] == exp["stats"][k], k
+    w = fsc.cases()["school_t7375_windowed"]()[0]
+    expw = expected("school_t7375_windowed", [w])[0]
+    lab, Qs, _ = pkg.leiden_windowed(w["snaps"], w["W"], w["stride"])
+    assert fsc.digest_labels(lab) == expw["labels"]
+    assert len(Qs) == expw["windows"]
+    assert all(q_ok(a, b) for a, b in zip(Qs, expw["Q_windows"]))
+    with pkg.mslice_build(w["snaps"]) as h:
+        assert q_ok(h.mslice_modularity(lab), expw["Q"])
