@@ -484,7 +484,7 @@ int mslice_build_ex(const mslice_csr* slices, int32_t T, mslice_coupling cpl, in
     const bool dev = (flags & MSLICE_DEVICE_PTRS) != 0;
     std::vector<const int64_t*> ip(T);
     std::vector<const int32_t*> ix(T), wt(T);
-    std::vector<int64_t> nnz(T);
+    std::vector<int64_t> nnz(T), eoff(T + 1, 0);
     for (int32_t s = 0; s < T; ++s) {
       if (n > 0 && !slices[s].indptr) fail(MSLICE_EINVAL, "null indptr");
       int64_t z = 0;
@@ -497,42 +497,68 @@ int mslice_build_ex(const mslice_csr* slices, int32_t T, mslice_coupling cpl, in
       if (z < 0) fail(MSLICE_EINVAL, "negative nnz");
       if (z > 0 && (!slices[s].indices || !slices[s].weights)) fail(MSLICE_EINVAL, "null indices/weights");
       nnz[s] = z;
+      eoff[s + 1] = eoff[s] + z;
       if (dev) {
         ip[s] = slices[s].indptr;
         ix[s] = slices[s].indices;
         wt[s] = slices[s].weights;
+      }
+    }
+    if (!dev) {
+      // host snapshots: one staging buffer per array kind.  Up to 64
+      // snapshots are copied one by one (pinned inputs stream straight in);
+      // longer sequences are packed on the host first, so many small
+      // snapshots cost three copies instead of 3T.
+      const size_t nip = (size_t)T * (n + 1);
+      int64_t* dip = h->ws.get<int64_t>("in_ip", nip);
+      int32_t* dix = h->ws.get<int32_t>("in_ix", eoff[T]);
+      int32_t* dwt = h->ws.get<int32_t>("in_wt", eoff[T]);
+      if (n == 0) {
+        check_cuda(cudaMemsetAsync(dip, 0, nip * sizeof(int64_t), c.stream), "memset");
+      } else if (T <= 64) {
+        for (int32_t s = 0; s < T; ++s) {
+          check_cuda(cudaMemcpyAsync(dip + (size_t)s * (n + 1), slices[s].indptr, (n + 1) * sizeof(int64_t),
+                                     cudaMemcpyHostToDevice, c.stream), "copy");
+          if (nnz[s] > 0) {
+            check_cuda(cudaMemcpyAsync(dix + eoff[s], slices[s].indices, nnz[s] * sizeof(int32_t),
+                                       cudaMemcpyHostToDevice, c.stream), "copy");
+            check_cuda(cudaMemcpyAsync(dwt + eoff[s], slices[s].weights, nnz[s] * sizeof(int32_t),
+                                       cudaMemcpyHostToDevice, c.stream), "copy");
+          }
+        }
       } else {
-        const std::string tag = std::to_string(s);
-        int64_t* dip = h->ws.get<int64_t>("in_ip" + tag, n + 1);
-        int32_t* dix = h->ws.get<int32_t>("in_ix" + tag, z);
-        int32_t* dwt = h->ws.get<int32_t>("in_wt" + tag, z);
-        if (n > 0) {
-          check_cuda(cudaMemcpyAsync(dip, slices[s].indptr, (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
-                                     c.stream), "copy");
-        } else {
-          check_cuda(cudaMemsetAsync(dip, 0, sizeof(int64_t), c.stream), "memset");
+        std::vector<int64_t> hip(nip);
+        std::vector<int32_t> hix(eoff[T]), hwt(eoff[T]);
+        for (int32_t s = 0; s < T; ++s) {
+          std::memcpy(&hip[(size_t)s * (n + 1)], slices[s].indptr, (n + 1) * sizeof(int64_t));
+          if (nnz[s] > 0) {
+            std::memcpy(&hix[eoff[s]], slices[s].indices, nnz[s] * sizeof(int32_t));
+            std::memcpy(&hwt[eoff[s]], slices[s].weights, nnz[s] * sizeof(int32_t));
+          }
         }
-        if (z > 0) {
-          check_cuda(cudaMemcpyAsync(dix, slices[s].indices, z * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream),
+        check_cuda(cudaMemcpyAsync(dip, hip.data(), nip * sizeof(int64_t), cudaMemcpyHostToDevice, c.stream), "copy");
+        if (eoff[T] > 0) {
+          check_cuda(cudaMemcpyAsync(dix, hix.data(), eoff[T] * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream),
                      "copy");
-          check_cuda(cudaMemcpyAsync(dwt, slices[s].weights, z * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream),
+          check_cuda(cudaMemcpyAsync(dwt, hwt.data(), eoff[T] * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream),
                      "copy");
         }
-        ip[s] = dip;
-        ix[s] = dix;
-        wt[s] = dwt;
+        sync(c);  // the host staging vectors go out of scope
+      }
+      for (int32_t s = 0; s < T; ++s) {
+        ip[s] = dip + (size_t)s * (n + 1);
+        ix[s] = dix + eoff[s];
+        wt[s] = dwt + eoff[s];
       }
     }
     build_supra(c, ip, ix, wt, nnz, n, h->G, (int32_t)cpl);
     h->launches += c.launches;
     // staged host copies are not needed after the build
-    if (!dev)
-      for (int32_t s = 0; s < T; ++s) {
-        const std::string tag = std::to_string(s);
-        h->ws.release("in_ip" + tag);
-        h->ws.release("in_ix" + tag);
-        h->ws.release("in_wt" + tag);
-      }
+    if (!dev) {
+      h->ws.release("in_ip");
+      h->ws.release("in_ix");
+      h->ws.release("in_wt");
+    }
     *out = h;
   });
   if (rc != MSLICE_OK && h) delete h;

@@ -287,6 +287,19 @@ __device__ __forceinline__ Cand block_best(Cand c, Cand* sm) {
   return r;
 }
 
+// Sum of one u128 per lane over the warp (every lane gets it).
+__device__ __forceinline__ u128 warp_sum_u128(u128 x) {
+  ull lo = (ull)x, hi = (ull)(x >> 64);
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    const ull l2 = __shfl_xor_sync(0xffffffffu, lo, m), h2 = __shfl_xor_sync(0xffffffffu, hi, m);
+    const ull nl = lo + l2;
+    hi += h2 + (nl < lo ? 1ull : 0ull);
+    lo = nl;
+  }
+  return ((u128)hi << 64) | lo;
+}
+
 template <class T>
 __device__ __forceinline__ T warp_sum(T x) {
 #pragma unroll

@@ -32,6 +32,12 @@
 //   int32_t own_key(v)                 the node's current key (-1 none)
 //   i128 own(v, vc, W_own)             score of staying
 //   void finish(v, best, W_best, G_own, vc)
+// and, for the block tiers' slice-parallel scoring of aggregated nodes:
+//   int64_t slice_count(v)             entries of v's (snapshot, strength) list (0 at level 0)
+//   u128 null_part(v, vc, key, self, t, nt)  the null sum over entries t, t+nt, ...
+//   Cand cand_ns(v, vc, key, W, ns)    cand() from a complete null sum
+//   bool own_walks_slices()            own() walks the list (else it is cheap)
+//   i128 own_ns(v, vc, W_own, ns)      own() from a complete null sum
 #pragma once
 #include "internal.h"
 #include "level.h"
@@ -65,6 +71,52 @@ constexpr int GROUP_THREADS = 256;
 
 __host__ __device__ __forceinline__ int degree_tier(int64_t d, const TierCuts& c) {
   return d <= c.t[0] ? 0 : (d <= c.t[1] ? 1 : (d <= c.t[2] ? 2 : (d <= c.t[3] ? 3 : 4)));
+}
+
+// Aggregated nodes carry a list of (snapshot, strength) entries, and scoring
+// one candidate walks that list once (the null term sums over snapshots).
+// On long sequences late-level nodes hold thousands of entries, so a node
+// whose (degree + 1) * entries reaches SLICE_WORK_BLOCK is decided by a
+// block-per-node tier, whose threads then split each candidate's walk
+// (slice_parallel) instead of taking one candidate each.
+constexpr int64_t SLICE_WORK_BLOCK = 4096;
+
+__host__ __device__ __forceinline__ int work_tier(int64_t d, int64_t nslices, const TierCuts& c) {
+  const int t = degree_tier(d, c);
+  if (t < NTIERS - 2 && nslices > 1 && (d + 1) * nslices >= SLICE_WORK_BLOCK) return NTIERS - 2;
+  return t;
+}
+
+// Block-per-node scoring takes a candidate per thread unless splitting each
+// candidate's slice walk over the block is cheaper: ceil(n/B) * ns
+// sequential entries against n * (ceil(ns/B) + 3) (the 3: a reduction).
+__device__ __forceinline__ bool slice_parallel(int64_t n, int64_t ns, int B) {
+  return ns > 1 && ((n + B - 1) / B) * ns > n * ((ns + B - 1) / B + 3);
+}
+
+// Sum of one u128 per thread over the block (every thread gets it); sm holds
+// 2 words per warp.
+template <int WARPS>
+__device__ __forceinline__ u128 block_sum_u128(u128 x, ull* sm) {
+  ull lo = (ull)x, hi = (ull)(x >> 64);
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    const ull l2 = __shfl_xor_sync(0xffffffffu, lo, m), h2 = __shfl_xor_sync(0xffffffffu, hi, m);
+    const ull nl = lo + l2;
+    hi += h2 + (nl < lo ? 1ull : 0ull);
+    lo = nl;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    sm[2 * w] = lo;
+    sm[2 * w + 1] = hi;
+  }
+  __syncthreads();
+  u128 t = 0;
+#pragma unroll
+  for (int k = 0; k < WARPS; ++k) t += ((u128)sm[2 * k + 1] << 64) | sm[2 * k];
+  __syncthreads();
+  return t;
 }
 
 __device__ __forceinline__ uint32_t small_hash(int32_t key, int bits) {
@@ -267,6 +319,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_block(Pol pol, const i
   __shared__ uint16_t cl[SLOTS / 2];
   __shared__ int32_t ncand;
   __shared__ Cand red[BLOCK_THREADS / 32];
+  __shared__ ull usm[2 * (BLOCK_THREADS / 32)];
   __shared__ i128 own_sm;
   const int count = *count_ptr;
   for (int i = threadIdx.x; i < SLOTS; i += BLOCK_THREADS) {
@@ -299,20 +352,49 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_block(Pol pol, const i
     __syncthreads();
     const int n = ncand;
     const int32_t own = pol.own_key(v);
-    Cand c{0, INT32_MAX};
-    for (int j = threadIdx.x; j < n; j += BLOCK_THREADS) {
-      const int slot = cl[j];
-      const int32_t k = hk[slot];
-      if (k != own) {
-        const Cand x = pol.cand(v, vc, k, hv[slot], pol.probe(v, vc, k));
-        if (better(x, c)) c = x;
+    if (slice_parallel(n, pol.slice_count(v), BLOCK_THREADS)) {
+      // every thread walks a share of the slice list for each candidate in
+      // turn; thread 0 keeps the best
+      Cand c{0, INT32_MAX};
+      for (int j = 0; j < n; ++j) {
+        const int slot = cl[j];
+        const int32_t k = hk[slot];
+        if (k == own) continue;
+        const u128 ns =
+            block_sum_u128<BLOCK_THREADS / 32>(pol.null_part(v, vc, k, false, threadIdx.x, BLOCK_THREADS), usm);
+        if (threadIdx.x == 0) {
+          const Cand x = pol.cand_ns(v, vc, k, hv[slot], ns);
+          if (better(x, c)) c = x;
+        }
       }
-    }
-    if (threadIdx.x == 0) own_sm = pol.own(v, vc, table_get(hk, hv, bits, own));
-    const Cand best = block_best<BLOCK_THREADS / 32>(c, red);
-    if (threadIdx.x == 0) {
-      const long long Wb = best.label != INT32_MAX ? table_get(hk, hv, bits, best.label) : 0;
-      pol.finish(v, best, Wb, own_sm, vc);
+      i128 Go = 0;
+      if (pol.own_walks_slices()) {
+        const u128 ns =
+            block_sum_u128<BLOCK_THREADS / 32>(pol.null_part(v, vc, own, true, threadIdx.x, BLOCK_THREADS), usm);
+        if (threadIdx.x == 0) Go = pol.own_ns(v, vc, table_get(hk, hv, bits, own), ns);
+      } else if (threadIdx.x == 0) {
+        Go = pol.own(v, vc, table_get(hk, hv, bits, own));
+      }
+      if (threadIdx.x == 0) {
+        const long long Wb = c.label != INT32_MAX ? table_get(hk, hv, bits, c.label) : 0;
+        pol.finish(v, c, Wb, Go, vc);
+      }
+    } else {
+      Cand c{0, INT32_MAX};
+      for (int j = threadIdx.x; j < n; j += BLOCK_THREADS) {
+        const int slot = cl[j];
+        const int32_t k = hk[slot];
+        if (k != own) {
+          const Cand x = pol.cand(v, vc, k, hv[slot], pol.probe(v, vc, k));
+          if (better(x, c)) c = x;
+        }
+      }
+      if (threadIdx.x == 0) own_sm = pol.own(v, vc, table_get(hk, hv, bits, own));
+      const Cand best = block_best<BLOCK_THREADS / 32>(c, red);
+      if (threadIdx.x == 0) {
+        const long long Wb = best.label != INT32_MAX ? table_get(hk, hv, bits, best.label) : 0;
+        pol.finish(v, best, Wb, own_sm, vc);
+      }
     }
     __syncthreads();
     for (int j = threadIdx.x; j < n; j += BLOCK_THREADS) {
@@ -346,6 +428,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_global(Pol pol, const 
                                                                  int32_t* gkeys, long long* gvals, const int64_t* goff,
                                                                  unsigned* status) {
   __shared__ Cand red[BLOCK_THREADS / 32];
+  __shared__ ull usm[2 * (BLOCK_THREADS / 32)];
   __shared__ i128 own_sm;
   const int count = *count_ptr;
   for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
@@ -372,11 +455,39 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_global(Pol pol, const 
     }
     __syncthreads();
     const int32_t own = pol.own_key(v);
-    if (threadIdx.x == 0) own_sm = pol.own(v, vc, table_get(hk, hv, bits, own));
-    const Cand best = block_best<BLOCK_THREADS / 32>(score_range(pol, v, vc, own, hk, hv, S), red);
-    if (threadIdx.x == 0) {
-      const long long Wb = best.label != INT32_MAX ? table_get(hk, hv, bits, best.label) : 0;
-      pol.finish(v, best, Wb, own_sm, vc);
+    if (slice_parallel(end - beg, pol.slice_count(v), BLOCK_THREADS)) {
+      // (the degree bounds the candidates) the block splits each
+      // candidate's slice walk; thread 0 keeps the best
+      Cand c{0, INT32_MAX};
+      for (int64_t i = 0; i < S; ++i) {
+        const int32_t k = hk[i];
+        if (k < 0 || k == own) continue;
+        const u128 ns =
+            block_sum_u128<BLOCK_THREADS / 32>(pol.null_part(v, vc, k, false, threadIdx.x, BLOCK_THREADS), usm);
+        if (threadIdx.x == 0) {
+          const Cand x = pol.cand_ns(v, vc, k, hv[i], ns);
+          if (better(x, c)) c = x;
+        }
+      }
+      i128 Go = 0;
+      if (pol.own_walks_slices()) {
+        const u128 ns =
+            block_sum_u128<BLOCK_THREADS / 32>(pol.null_part(v, vc, own, true, threadIdx.x, BLOCK_THREADS), usm);
+        if (threadIdx.x == 0) Go = pol.own_ns(v, vc, table_get(hk, hv, bits, own), ns);
+      } else if (threadIdx.x == 0) {
+        Go = pol.own(v, vc, table_get(hk, hv, bits, own));
+      }
+      if (threadIdx.x == 0) {
+        const long long Wb = c.label != INT32_MAX ? table_get(hk, hv, bits, c.label) : 0;
+        pol.finish(v, c, Wb, Go, vc);
+      }
+    } else {
+      if (threadIdx.x == 0) own_sm = pol.own(v, vc, table_get(hk, hv, bits, own));
+      const Cand best = block_best<BLOCK_THREADS / 32>(score_range(pol, v, vc, own, hk, hv, S), red);
+      if (threadIdx.x == 0) {
+        const long long Wb = best.label != INT32_MAX ? table_get(hk, hv, bits, best.label) : 0;
+        pol.finish(v, best, Wb, own_sm, vc);
+      }
     }
     __syncthreads();
   }

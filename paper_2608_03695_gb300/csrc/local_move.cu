@@ -41,18 +41,24 @@ namespace {
 
 constexpr int APPLY_THREADS = 256;
 constexpr int GRAPH_FROM_ROUND = 4;
+// Levels of at most this many nodes replay round graphs in single solves too
+// (their rounds are launch-bound).
+constexpr int64_t GRAPH_MAX_NODES = 0;
 constexpr int EMPTY_THREADS = 512;
 
 unsigned fixed_grid(int per_sm) { return 152u * (unsigned)per_sm; }
 
-__global__ void k_tier(const int64_t* rowptr, int32_t N, TierCuts cuts, uint8_t* tier, int32_t* cnt, int64_t* gsize) {
+// Tier of every node by degree, and by slice work at aggregated levels
+// (sptr non-null: see work_tier).
+__global__ void k_tier(const int64_t* rowptr, const int64_t* sptr, int32_t N, TierCuts cuts, uint8_t* tier,
+                       int32_t* cnt, int64_t* gsize) {
   const int lane = threadIdx.x & 31;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < N; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t v = base + threadIdx.x;
     int t = -1;
     if (v < N) {
       const int64_t d = rowptr[v + 1] - rowptr[v];
-      t = degree_tier(d, cuts);
+      t = work_tier(d, sptr ? sptr[v + 1] - sptr[v] : 0, cuts);
       tier[v] = (uint8_t)t;
       int64_t S = 0;
       if (t == NTIERS - 1) {
@@ -100,6 +106,24 @@ __global__ void k_bucket(LevelDev g, const uint8_t* tier, uint64_t seed, uint64_
 __global__ void k_hash_clear(Slot* slots, uint64_t cap) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += (uint64_t)gridDim.x * blockDim.x)
     slots[i] = Slot{EMPTY_KEY, 0};
+}
+
+// Aggregated levels: one warp per node, the lanes sharing its list.
+__global__ void k_sigma_insert_warp(LevelDev g, const int32_t* labels, SigStore h, int32_t* size) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = (((int64_t)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); v < g.N; v += warps) {
+    const int32_t c = labels[v];
+    if (size && lane == 0) atomicAdd(&size[c], 1);
+    int64_t b, e;
+    slice_range(g, (int32_t)v, b, e);
+    for (int64_t j = b + lane; j < e; j += 32) {
+      int32_t s;
+      long long k;
+      slice_entry(g, (int32_t)v, j, s, k);
+      ss_add(h, c, s, k);
+    }
+  }
 }
 
 __global__ void k_sigma_insert(LevelDev g, const int32_t* labels, SigStore h, int32_t* size) {
@@ -204,6 +228,29 @@ struct LMPolicy {
       return (((i128)Wown) << P_BITS) - (i128)(vc.A * (u128)(ull)x);
     }
     return key_of(v, vc, vc.a, Wown, true);
+  }
+  // slice-parallel scoring (block tiers, aggregated levels)
+  __device__ int64_t slice_count(int32_t v) const { return g.is0 ? 0 : g.sptr[v + 1] - g.sptr[v]; }
+  __device__ bool own_walks_slices() const { return true; }
+  __device__ u128 null_part(int32_t v, const VCtx&, int32_t c, bool self, int t, int nt) const {
+    int64_t b, e;
+    slice_range(g, v, b, e);
+    u128 acc = 0;
+    for (int64_t j = b + t; j < e; j += nt) {
+      int32_t s;
+      long long k;
+      slice_entry(g, v, j, s, k);
+      long long x = sst_get<DENSE>(sig, c, s);
+      if (self) x -= k;
+      acc += lam[s] * (u128)(ull)k * (u128)(ull)x;
+    }
+    return acc;
+  }
+  __device__ Cand cand_ns(int32_t, const VCtx& vc, int32_t c, long long W, const u128& ns) const {
+    return Cand{(((i128)W) << P_BITS) - (i128)((u128)(ull)vc.om.nd * ns), c};
+  }
+  __device__ i128 own_ns(int32_t, const VCtx& vc, long long Wown, const u128& ns) const {
+    return (((i128)Wown) << P_BITS) - (i128)((u128)(ull)vc.om.nd * ns);
   }
   __device__ void finish(int32_t v, const Cand& best, long long, const i128& Ga, const VCtx& vc) const {
     const int32_t a = vc.a;
@@ -524,8 +571,8 @@ void prepare_level(Solver& S, const Level& L) {
   check_cuda(cudaMemsetAsync(cnt, 0, NTIERS * sizeof(int32_t), c.stream), "memset");
   int64_t* gsize = reinterpret_cast<int64_t*>(c.ws->get<int64_t>("s_gsize", (size_t)(N > 0 ? N : 1)));
   if (N > 0)
-    launch(c, k_tier, dim3(grid_for(N, 256) < 4096 ? grid_for(N, 256) : 4096), dim3(256), 0, L.d.rowptr, N, S.p.cuts,
-           S.tier, cnt, gsize);
+    launch(c, k_tier, dim3(grid_for(N, 256) < 4096 ? grid_for(N, 256) : 4096), dim3(256), 0, L.d.rowptr,
+           (const int64_t*)(L.d.is0 ? nullptr : L.d.sptr), N, S.p.cuts, S.tier, cnt, gsize);
   int64_t* gtotal = c.ws->get<int64_t>("s_gtotal", 1);
   scan_excl(c, gsize, S.goff, N, gtotal);
   check_cuda(cudaMemcpyAsync(S.goff + N, gtotal, sizeof(int64_t), cudaMemcpyDeviceToDevice, c.stream), "copy");
@@ -604,7 +651,10 @@ static void rebuild_sigma(Solver& S, const Level& L, const int32_t* labels, bool
   if (S.sig_used) check_cuda(cudaMemsetAsync(S.sig_used, 0, sizeof(ull), c.stream), "memset");
   clear_store(S, S.sig);
   if (N > 0)
-    launch(c, k_sigma_insert, dim3(grid_for(N, 256)), dim3(256), 0, L.d, labels, S.sig, sizes ? S.size : nullptr);
+    if (L.d.is0)
+      launch(c, k_sigma_insert, dim3(grid_for(N, 256)), dim3(256), 0, L.d, labels, S.sig, sizes ? S.size : nullptr);
+    else
+      launch(c, k_sigma_insert_warp, dim3(fixed_grid(8)), dim3(256), 0, L.d, labels, S.sig, sizes ? S.size : nullptr);
 }
 
 void sigma_rebuild(Solver& S, const Level& L, const int32_t* labels) { rebuild_sigma(S, L, labels, false); }
@@ -788,7 +838,10 @@ MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, 
   // single 1.6M-node solve (its large levels keep the GPU busy between
   // launches), so batches use graphs and single solves only on request
   // (MSLICE_GRAPHS=1; MSLICE_NO_GRAPHS=1 turns them off).
-  const bool want = (batch || std::getenv("MSLICE_GRAPHS")) && !std::getenv("MSLICE_NO_GRAPHS");
+  int64_t graph_max_nodes = GRAPH_MAX_NODES;
+  if (const char* e = std::getenv("MSLICE_GRAPH_MAX_NODES")) graph_max_nodes = std::atoll(e);
+  const bool want =
+      (batch || N <= graph_max_nodes || std::getenv("MSLICE_GRAPHS")) && !std::getenv("MSLICE_NO_GRAPHS");
   const bool graphs = want && c.stream != nullptr && !c.profile && !c.trace && !(S.p.autotune && lvl == 0);
   cudaGraphExec_t exec = nullptr;
   int64_t graph_kernels = 0;

@@ -123,8 +123,27 @@ __device__ __forceinline__ double omega_J(const QInst& p, ull Jword, int32_t wei
 // one 128-bit sum per null slice: per snapshot (Q_MS) or per instance
 // (global model).  gs: per-snapshot gamma (num, den) pairs, when any
 // instance has them.
+// The slice terms of Q_MS, one thread per snapshot: S_s / 2m_s (CPM: S_s,
+// a mass of 1), times gamma_s when the instance has per-snapshot gamma.
+// k_Q adds them in ascending s, so the result is that of one sequential
+// evaluation.
+__global__ void k_slice_terms(const ull* S, const int64_t* two_m, int32_t T, const int32_t* slice_inst,
+                              const QInst* qi, int32_t cpm, const long long* gs, double* terms) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < T; s += gridDim.x * blockDim.x) {
+    const long long t = two_m[s];
+    double term = 0.0;
+    if (t > 0 || cpm) {
+      const u128 x = ((u128)S[2 * s + 1] << 64) | S[2 * s];
+      term = cpm ? u128_to_double(x) : __ddiv_rn(u128_to_double(x), __ll2double_rn(t));
+      if (qi[slice_inst ? slice_inst[s] : 0].gtab)
+        term = __dmul_rn(__ddiv_rn(__ll2double_rn(gs[2 * s]), __ll2double_rn(gs[2 * s + 1])), term);
+    }
+    terms[s] = term;
+  }
+}
+
 __global__ void k_Q(const ull* IJ, const ull* S, const int64_t* two_m, const QInst* qi, int32_t B, int32_t global,
-                    int32_t cpm, int32_t weighted, const long long* gs, double* Q) {
+                    int32_t cpm, int32_t weighted, const double* terms, double* Q) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B) return;
   const QInst p = qi[i];
@@ -151,14 +170,7 @@ __global__ void k_Q(const ull* IJ, const ull* S, const int64_t* two_m, const QIn
   for (int s = p.soff; s < p.soff + p.T; ++s) {
     const long long t = two_m[s];
     sum2m += t;
-    if (t > 0 || cpm) {
-      // CPM: node counts over a mass of 1
-      const u128 x = ((u128)S[2 * s + 1] << 64) | S[2 * s];
-      const double term = cpm ? u128_to_double(x) : __ddiv_rn(u128_to_double(x), __ll2double_rn(t));
-      nullsum = __dadd_rn(nullsum, p.gtab ? __dmul_rn(__ddiv_rn(__ll2double_rn(gs[2 * s]), __ll2double_rn(gs[2 * s + 1])),
-                                                      term)
-                                          : term);
-    }
+    if (t > 0 || cpm) nullsum = __dadd_rn(nullsum, terms[s]);  // ascending s
   }
   const double wJ = omega_J(p, IJ[2 * i + 1], weighted);
   const double gam = __ddiv_rn(__ll2double_rn(p.gn), __ll2double_rn(p.gd));
@@ -237,9 +249,14 @@ void modularity(Solver& S, const int32_t* labels0, double* Q) {
   const size_t smem = Tn <= 1024 ? 2 * (size_t)Tn * sizeof(ull) : 0;
   const int64_t span = S.sig.d ? S.sig.rows * S.sig.T : (int64_t)S.sig.h.cap;
   launch(c, k_S, dim3(gsz(span)), dim3(256), smem, S.sig, Tn, acc + 2 * B);
+  double* terms = c.ws->get<double>("q_terms", G.T > 0 ? G.T : 1);
+  if (!S.p.global_null && G.T > 0)
+    launch(c, k_slice_terms, dim3(grid_for(G.T, 256)), dim3(256), 0, (const ull*)(acc + 2 * B),
+           (const int64_t*)G.two_m, G.T, (const int32_t*)(G.B > 1 ? G.slice_inst : nullptr), (const QInst*)dqi,
+           (int32_t)(S.p.cpm ? 1 : 0), (const long long*)S.gs_d, terms);
   launch(c, k_Q, dim3(grid_for(B, 128)), dim3(128), 0, (const ull*)acc, (const ull*)(acc + 2 * B),
          (const int64_t*)G.two_m, (const QInst*)dqi, B, (int32_t)(S.p.global_null ? 1 : 0), (int32_t)(S.p.cpm ? 1 : 0),
-         (int32_t)(S.cw_d ? 1 : 0), (const long long*)S.gs_d, dQ);
+         (int32_t)(S.cw_d ? 1 : 0), (const double*)terms, dQ);
   // B values go straight to the caller's (pageable) array
   check_cuda(cudaMemcpyAsync(Q, dQ, B * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "copy");
   sync(c);

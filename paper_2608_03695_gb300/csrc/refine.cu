@@ -42,22 +42,24 @@ __global__ void k_ref_init(LevelDev g, const int32_t* P, SigStore sig, const u12
       if (edge_at(g, e, u, W, om) && P[u] == C) w += W;
     }
     w = warp_sum(w);
+    // the lanes share the node's (snapshot, strength) list
+    int64_t b, e;
+    slice_range(g, (int32_t)v, b, e);
+    u128 rhs = 0;
+    for (int64_t j = b + lane; j < e; j += 32) {
+      int32_t s;
+      long long k;
+      slice_entry(g, (int32_t)v, j, s, k);
+      rhs += lam_k_x(lam, s, k, ss_get(sig, C, s) - k);
+      ss_add(kr, (int32_t)v, s, k);
+    }
+    rhs = warp_sum_u128(rhs);
     if (lane == 0) {
       R[v] = (int32_t)v;
       PR[v] = (long long)(((unsigned long long)(uint32_t)C << 32) | (uint32_t)v);
       sizeR[v] = 1;
       Wc[v] = w;
       Wout[v] = w;
-      int64_t b, e;
-      slice_range(g, (int32_t)v, b, e);
-      u128 rhs = 0;
-      for (int64_t j = b; j < e; ++j) {
-        int32_t s;
-        long long k;
-        slice_entry(g, (int32_t)v, j, s, k);
-        rhs += lam_k_x(lam, s, k, ss_get(sig, C, s) - k);
-        ss_add(kr, (int32_t)v, s, k);
-      }
       elig[v] = ((((i128)w) << P_BITS) - (i128)((u128)(ull)om.nd * rhs)) >= 0 ? 1 : 0;
     }
   }
@@ -200,6 +202,30 @@ struct RefPolicy {
     if (G <= 0) return Cand{0, INT32_MAX};
     return Cand{G, X};
   }
+  // slice-parallel scoring (block tiers, aggregated levels); own() is 0
+  __device__ int64_t slice_count(int32_t v) const { return g.is0 ? 0 : g.sptr[v + 1] - g.sptr[v]; }
+  __device__ bool own_walks_slices() const { return false; }
+  __device__ u128 null_part(int32_t v, const VCtx&, int32_t X, bool, int t, int nt) const {
+    int64_t b, e;
+    slice_range(g, v, b, e);
+    u128 acc = 0;
+    for (int64_t j = b + t; j < e; j += nt) {
+      int32_t s;
+      long long k;
+      slice_entry(g, v, j, s, k);
+      acc += lam_k_x(lam, s, k, sst_get<DENSE>(kr, X, s));
+    }
+    return acc;
+  }
+  __device__ Cand cand_ns(int32_t, const VCtx& vc, int32_t X, long long W, const u128& ns) const {
+    const unsigned long long d = desc[X];
+    if ((int32_t)(uint32_t)d == 1 && (uint8_t)(d >> 32) == q) return Cand{0, INT32_MAX};
+    if (!(uint8_t)(d >> 40)) return Cand{0, INT32_MAX};
+    const i128 G = (((i128)W) << P_BITS) - (i128)((u128)(ull)vc.om.nd * ns);
+    if (G <= 0) return Cand{0, INT32_MAX};
+    return Cand{G, X};
+  }
+  __device__ i128 own_ns(int32_t, const VCtx&, long long, const u128&) const { return 0; }
   __device__ void finish(int32_t v, const Cand& best, long long Wb, const i128&, const VCtx&) const {
     if (best.label != INT32_MAX) {
       target[v] = best.label;
