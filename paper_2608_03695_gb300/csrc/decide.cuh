@@ -32,6 +32,7 @@
 //   int32_t own_key(v)                 the node's current key (-1 none)
 //   i128 own(v, vc, W_own)             score of staying
 //   void finish(v, best, W_best, G_own, vc)
+//   static constexpr int MIN_BLOCKS    resident blocks per SM the group tiers aim for
 // and, for the block tiers' slice-parallel scoring of aggregated nodes:
 //   int64_t slice_count(v)             entries of v's (snapshot, strength) list (0 at level 0)
 //   u128 null_part(v, vc, key, self, t, nt)  the null sum over entries t, t+nt, ...
@@ -49,6 +50,14 @@ namespace mslice {
 // per-warp parallelism for these latency-bound loops).
 #ifndef MSLICE_GROUP_MIN_BLOCKS
 #define MSLICE_GROUP_MIN_BLOCKS 4
+#endif
+// The same for policies on dense community tables (aggregated levels), whose
+// scoring code needs more registers: at 4 blocks (64 registers) their group
+// kernels spill ~280 bytes; 3 blocks cut the spills to ~100 bytes and the
+// power-law solve's local moving by ~1.7% (measured; 2 blocks: no spills,
+// no further gain).
+#ifndef MSLICE_DENSE_MIN_BLOCKS
+#define MSLICE_DENSE_MIN_BLOCKS 3
 #endif
 // entries loaded per lane per round by the warp-per-node tier
 #ifndef MSLICE_T2_EPL
@@ -180,7 +189,7 @@ __device__ __forceinline__ int table_add_slot(int32_t* hk, long long* hv, int bi
 // candidates and only those slots are reset afterwards (the table is cleared
 // once per block, not once per node).
 template <class Pol, int G, int BITS, int EPL>
-__global__ void __launch_bounds__(GROUP_THREADS, MSLICE_GROUP_MIN_BLOCKS)
+__global__ void __launch_bounds__(GROUP_THREADS, Pol::MIN_BLOCKS)
     k_decide_groups(Pol pol, const int32_t* list, const int32_t* count_ptr) {
   constexpr int WARPS = GROUP_THREADS / 32, GPW = 32 / G, SLOTS = 1 << BITS, MAXC = SLOTS / 2;
   constexpr bool ONE_CHUNK = MAXC <= G * EPL;  // every row fits one load round

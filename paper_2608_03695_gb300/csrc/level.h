@@ -43,10 +43,9 @@ struct LevelDev {
   unsigned* chk = nullptr;            // checked builds: status word for bound violations
 };
 
-// Coupling omega = on/od of a node's instance and the scale of the key's
-// null term (od, or 1 under the global null model).
+// Coupling omega = on/od of a node's instance.
 struct Omega {
-  long long on, od, nd;
+  long long on, od;
 };
 
 __device__ __forceinline__ int32_t node_inst(const LevelDev& g, int32_t v) { return g.inst ? g.inst[v] : 0; }
@@ -54,9 +53,15 @@ __device__ __forceinline__ int32_t node_inst(const LevelDev& g, int32_t v) { ret
 __device__ __forceinline__ Omega node_omega(const LevelDev& g, int32_t v) {
   if (g.od_i) {
     const int32_t i = node_inst(g, v);
-    return Omega{g.on_i[i], g.od_i[i], g.global_null ? 1 : g.od_i[i]};
+    return Omega{g.on_i[i], g.od_i[i]};
   }
-  return Omega{g.on, g.od, g.global_null ? 1 : g.od};
+  return Omega{g.on, g.od};
+}
+
+// Scale of the key's null term: od, or 1 under the global null model (whose
+// strengths are already in units of 1/od).
+__device__ __forceinline__ long long null_scale(const LevelDev& g, const Omega& om) {
+  return g.global_null ? 1 : om.od;
 }
 
 // Node id within its instance (the schedule's hash reads this, so a batched

@@ -162,6 +162,7 @@ __device__ __forceinline__ u128 null_sum(const LevelDev& g, const u128* lam, con
 
 template <bool DENSE>
 struct LMPolicy {
+  static constexpr int MIN_BLOCKS = DENSE ? MSLICE_DENSE_MIN_BLOCKS : MSLICE_GROUP_MIN_BLOCKS;
   LevelDev g;
   const int32_t* labels;
   const int32_t* size;
@@ -195,7 +196,7 @@ struct LMPolicy {
     if (c.single) {
       c.k = g.k0[v];
       c.s = node_slice0(g, v);
-      if (c.k > 0) c.A = (u128)(ull)c.om.nd * lam[c.s] * (u128)(ull)c.k;
+      if (c.k > 0) c.A = (u128)(ull)null_scale(g, c.om) * lam[c.s] * (u128)(ull)c.k;
     }
     return c;
   }
@@ -209,7 +210,7 @@ struct LMPolicy {
   __device__ int32_t own_key(int32_t v) const { return labels[v]; }
   __device__ i128 key_of(int32_t v, const VCtx& vc, int32_t c, long long W, bool self) const {
     const u128 ns = null_sum<DENSE>(g, lam, sig, v, c, self);
-    return (((i128)W) << P_BITS) - (i128)((u128)(ull)vc.om.nd * ns);
+    return (((i128)W) << P_BITS) - (i128)((u128)(ull)null_scale(g, vc.om) * ns);
   }
   __device__ Probe probe(int32_t, const VCtx& vc, int32_t c) const {
     if (vc.single && vc.k > 0) return sst_first<DENSE>(sig, c, vc.s);
@@ -247,10 +248,10 @@ struct LMPolicy {
     return acc;
   }
   __device__ Cand cand_ns(int32_t, const VCtx& vc, int32_t c, long long W, const u128& ns) const {
-    return Cand{(((i128)W) << P_BITS) - (i128)((u128)(ull)vc.om.nd * ns), c};
+    return Cand{(((i128)W) << P_BITS) - (i128)((u128)(ull)null_scale(g, vc.om) * ns), c};
   }
   __device__ i128 own_ns(int32_t, const VCtx& vc, long long Wown, const u128& ns) const {
-    return (((i128)Wown) << P_BITS) - (i128)((u128)(ull)vc.om.nd * ns);
+    return (((i128)Wown) << P_BITS) - (i128)((u128)(ull)null_scale(g, vc.om) * ns);
   }
   __device__ void finish(int32_t v, const Cand& best, long long, const i128& Ga, const VCtx& vc) const {
     const int32_t a = vc.a;

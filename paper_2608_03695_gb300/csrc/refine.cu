@@ -60,7 +60,7 @@ __global__ void k_ref_init(LevelDev g, const int32_t* P, SigStore sig, const u12
       sizeR[v] = 1;
       Wc[v] = w;
       Wout[v] = w;
-      elig[v] = ((((i128)w) << P_BITS) - (i128)((u128)(ull)om.nd * rhs)) >= 0 ? 1 : 0;
+      elig[v] = ((((i128)w) << P_BITS) - (i128)((u128)(ull)null_scale(g, om) * rhs)) >= 0 ? 1 : 0;
     }
   }
 }
@@ -103,7 +103,7 @@ __global__ void k_wc(LevelDev g, const int32_t* sizeR, const long long* Wout, co
       f = elig[L];
     } else if (sz > 1) {
       const u128 x = ((u128)rhs[2 * L + 1] << 64) | rhs[2 * L];
-      const long long nd = node_omega(g, (int32_t)L).nd;
+      const long long nd = null_scale(g, node_omega(g, (int32_t)L));
       f = ((((i128)Wout[L]) << P_BITS) - (i128)((u128)(ull)nd * x)) >= 0 ? 1 : 0;
     }
     wc[L] = f;
@@ -113,6 +113,7 @@ __global__ void k_wc(LevelDev g, const int32_t* sizeR, const long long* Wout, co
 
 template <bool DENSE>
 struct RefPolicy {
+  static constexpr int MIN_BLOCKS = DENSE ? MSLICE_DENSE_MIN_BLOCKS : MSLICE_GROUP_MIN_BLOCKS;
   LevelDev g;
   const int32_t* P;
   const int32_t* R;
@@ -154,7 +155,7 @@ struct RefPolicy {
     if (c.single) {
       c.k = g.k0[v];
       c.s = node_slice0(g, v);
-      if (c.k > 0) c.A = (u128)(ull)c.om.nd * lam[c.s] * (u128)(ull)c.k;
+      if (c.k > 0) c.A = (u128)(ull)null_scale(g, c.om) * lam[c.s] * (u128)(ull)c.k;
     }
     return c;
   }
@@ -197,7 +198,7 @@ struct RefPolicy {
         slice_entry(g, v, j, s, k);
         ns += lam_k_x(lam, s, k, sst_get<DENSE>(kr, X, s));
       }
-      G = (((i128)W) << P_BITS) - (i128)((u128)(ull)vc.om.nd * ns);
+      G = (((i128)W) << P_BITS) - (i128)((u128)(ull)null_scale(g, vc.om) * ns);
     }
     if (G <= 0) return Cand{0, INT32_MAX};
     return Cand{G, X};
@@ -221,7 +222,7 @@ struct RefPolicy {
     const unsigned long long d = desc[X];
     if ((int32_t)(uint32_t)d == 1 && (uint8_t)(d >> 32) == q) return Cand{0, INT32_MAX};
     if (!(uint8_t)(d >> 40)) return Cand{0, INT32_MAX};
-    const i128 G = (((i128)W) << P_BITS) - (i128)((u128)(ull)vc.om.nd * ns);
+    const i128 G = (((i128)W) << P_BITS) - (i128)((u128)(ull)null_scale(g, vc.om) * ns);
     if (G <= 0) return Cand{0, INT32_MAX};
     return Cand{G, X};
   }
