@@ -16,6 +16,7 @@
 // loop runs while some instance is unfrozen, and every instance's labels are
 // those of a solve of that instance alone.
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <vector>
 
@@ -162,6 +163,14 @@ void check_label_ranges(Ctx& c, const SupraGraph& G, const int32_t* d) {
   check_status(c, "labels");
 }
 
+// The snapshots coupled to s: [lo, s) and (s, hi) (ordinal: s-1 and s+1;
+// categorical: all), so loops over an instance's pairs cost T times the
+// partners, not T^2.
+static inline void partners(int32_t coupling, int32_t T, int32_t s, int32_t& lo, int32_t& hi) {
+  lo = coupling == 0 ? std::max(s - 1, 0) : 0;
+  hi = coupling == 0 ? std::min(s + 2, T) : T;
+}
+
 long long pair_num(const InstParams& j, int32_t coupling, int32_t T, int32_t s, int32_t r) {
   if (s == r) return 0;
   if (coupling == 0 && s - r != 1 && r - s != 1) return 0;
@@ -173,7 +182,9 @@ void check_bounds(int64_t n, int32_t T, int32_t coupling, const int64_t* two_m, 
   u128 sum2m = 0, csum = 0;
   for (int32_t s = 0; s < T; ++s) {
     sum2m += (u128)(ull)two_m[s];
-    for (int32_t r = 0; r < T; ++r) csum += (u128)(ull)pair_num(j, coupling, T, s, r);
+    int32_t lo, hi;
+    partners(coupling, T, s, lo, hi);
+    for (int32_t r = lo; r < hi; ++r) csum += (u128)(ull)pair_num(j, coupling, T, s, r);
   }
   const u128 lim = (u128)1 << 61;
   const u128 twoM = (u128)(ull)j.od * sum2m + (u128)(ull)n * csum;
@@ -321,13 +332,16 @@ void set_instances(Ctx& c, Solver& S, const std::vector<InstParams>& jobs) {
     any_cw = any_cw || S.has_cw_h[i];
     any_gs = any_gs || S.has_gs_h[i];
     long long sum = 0;
-    for (int32_t s = 0; s < in.T; ++s)
-      for (int32_t r = 0; r < in.T; ++r) {
+    for (int32_t s = 0; s < in.T; ++s) {
+      int32_t lo, hi;
+      partners(in.coupling, in.T, s, lo, hi);
+      for (int32_t r = lo; r < hi; ++r) {
         const long long x = pair_num(jobs[i], in.coupling, in.T, s, r);
         S.cstr_h[in.soff + s] += x;
         sum += x;
         if (x > 0) S.cpl_edges += in.n;
       }
+    }
     S.csum_h[i] = in.n * sum;
   }
   std::vector<long long> cw;
@@ -339,10 +353,12 @@ void set_instances(Ctx& c, Solver& S, const std::vector<InstParams>& jobs) {
     cw.assign(G.ncw, 0);
     for (int32_t i = 0; i < B; ++i) {
       const InstInfo& in = G.inst[i];
-      for (int32_t s = 0; s < in.T; ++s)
-        for (int32_t r = 0; r < in.T; ++r)
-          if (in.coupling != 0 || r == s + 1)
-            cw[in.cwoff + (in.coupling == 0 ? s : (int64_t)s * in.T + r)] = pair_num(jobs[i], in.coupling, in.T, s, r);
+      for (int32_t s = 0; s < in.T; ++s) {
+        int32_t lo, hi;
+        partners(in.coupling, in.T, s, lo, hi);
+        for (int32_t r = std::max(lo, in.coupling == 0 ? s + 1 : lo); r < hi; ++r)  // ordinal: slot s is (s, s+1)
+          cw[in.cwoff + (in.coupling == 0 ? s : (int64_t)s * in.T + r)] = pair_num(jobs[i], in.coupling, in.T, s, r);
+      }
     }
     S.cw_d = c.ws->get<long long>("s_cw", G.ncw);
     check_cuda(cudaMemcpyAsync(S.cw_d, cw.data(), G.ncw * sizeof(long long), cudaMemcpyHostToDevice, c.stream),
@@ -423,7 +439,15 @@ void run_leiden(Ctx& c, const SupraGraph& G, const std::vector<InstParams>& jobs
       int rounds = p.max_rounds;
       if (stop_here && stop_rounds > 0) rounds = stop_rounds;
       if (stop_here && stop_rounds < 0) rounds = 0;
+      // MSLICE_TRACE: host wall time of each step of the level (synchronised)
+      auto wall = [&]() -> double {
+        if (!c.trace) return 0.0;
+        sync(c);
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+      };
+      double tw[6] = {wall(), 0, 0, 0, 0, 0};
       prepare_level(S, cur);
+      tw[1] = wall();
       cudaEvent_t t0 = clock.begin();
       const MoveOut mo = local_move(S, cur, lab, it, lvl, rounds);
       clock.end(1, t0);
@@ -442,7 +466,13 @@ void run_leiden(Ctx& c, const SupraGraph& G, const std::vector<InstParams>& jobs
         debug_done = true;
         break;
       }
-      if (B > 1 ? freeze_settled(S, cur, lab) == 0 : count_distinct(S, lab, cur.d.N) == cur.d.N) {
+      tw[2] = wall();
+      const bool settled = B > 1 ? freeze_settled(S, cur, lab) == 0 : count_distinct(S, lab, cur.d.N) == cur.d.N;
+      tw[3] = wall();
+      if (c.trace)
+        fprintf(stderr, "[mslice steps] it=%d lvl=%d prepare_ms=%.3f local_move_ms=%.3f count_ms=%.3f\n", it, lvl,
+                tw[1] - tw[0], tw[2] - tw[1], tw[3] - tw[2]);
+      if (settled) {
         ro.stop_reason = 1;
         break;
       }
@@ -450,9 +480,12 @@ void run_leiden(Ctx& c, const SupraGraph& G, const std::vector<InstParams>& jobs
         ro.stop_reason = 2;
         break;
       }
+      tw[4] = wall();
       cudaEvent_t t1 = clock.begin();
       refine(S, cur, lab, it, lvl);
       clock.end(2, t1);
+      tw[5] = wall();
+      if (c.trace) fprintf(stderr, "[mslice steps] it=%d lvl=%d refine_ms=%.3f\n", it, lvl, tw[5] - tw[4]);
       if (stop_here && stop_stage == 2) {
         check_cuda(cudaMemcpyAsync(out, S.R, cur.d.N * sizeof(int32_t), cudaMemcpyDeviceToDevice, c.stream), "copy");
         ro.out_n = cur.d.N;
@@ -470,6 +503,7 @@ void run_leiden(Ctx& c, const SupraGraph& G, const std::vector<InstParams>& jobs
       const bool shrunk = aggregate(S, cur, lab, nxt, (lvl % 2 == 0) ? "LA" : "LB", lab_next, node_of0,
                                     (stop_here && stop_stage == 3) ? &ck : nullptr);
       clock.end(3, t2);
+      if (c.trace) fprintf(stderr, "[mslice steps] it=%d lvl=%d aggregate_ms=%.3f\n", it, lvl, wall() - tw[5]);
       if (!shrunk) {
         ro.stop_reason = 3;
         break;
