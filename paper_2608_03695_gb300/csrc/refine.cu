@@ -42,18 +42,21 @@ __global__ void k_ref_init(LevelDev g, const int32_t* P, SigStore sig, const u12
       if (edge_at(g, e, u, W, om) && P[u] == C) w += W;
     }
     w = warp_sum(w);
-    // the lanes share the node's (snapshot, strength) list
+    // a long (snapshot, strength) list is shared by the lanes; a short one
+    // (every level-0 node's) is walked by lane 0 alone
     int64_t b, e;
     slice_range(g, (int32_t)v, b, e);
+    const bool wide = e - b > 32;
     u128 rhs = 0;
-    for (int64_t j = b + lane; j < e; j += 32) {
-      int32_t s;
-      long long k;
-      slice_entry(g, (int32_t)v, j, s, k);
-      rhs += lam_k_x(lam, s, k, ss_get(sig, C, s) - k);
-      ss_add(kr, (int32_t)v, s, k);
-    }
-    rhs = warp_sum_u128(rhs);
+    if (wide || lane == 0)
+      for (int64_t j = b + (wide ? lane : 0); j < e; j += (wide ? 32 : 1)) {
+        int32_t s;
+        long long k;
+        slice_entry(g, (int32_t)v, j, s, k);
+        rhs += lam_k_x(lam, s, k, ss_get(sig, C, s) - k);
+        ss_add(kr, (int32_t)v, s, k);
+      }
+    if (wide) rhs = warp_sum_u128(rhs);
     if (lane == 0) {
       R[v] = (int32_t)v;
       PR[v] = (long long)(((unsigned long long)(uint32_t)C << 32) | (uint32_t)v);

@@ -1,7 +1,8 @@
 """The bounds-checked build (-DMSLICE_CHECKED=1: indices and table
 capacities tested on the hot paths, a violation reported as an error instead
 of accessed) on randomised small cases against the oracle, on the hashed
-tables, batched and served, and twice over for identical bits.  It runs in a
+tables, batched and served, under the other null models and general coupling,
+on a long sequence and windowed, and twice over for identical bits.  It runs in a
 subprocess so that the checked library is the one loaded."""
 import os
 import subprocess
@@ -63,6 +64,38 @@ with pkg.Server(window=2, n_slots=2) as srv:
             init = np.concatenate([prev[j * 100:(j + 1) * 100] for j in src]).astype(np.int32)
         assert np.array_equal(lab, oracle.leiden(stream[max(0, t - 1):t + 1], init=init)[0]), t
         prev = lab
+# the other null models, general coupling (coupling-table lookups are bound-checked), long slice lists
+# (block tiers' slice-parallel scoring) and windowed optimisation
+for seed in range(8):
+    rng = np.random.default_rng(900 + seed)
+    T, n = int(rng.integers(2, 6)), int(rng.integers(8, 60))
+    snaps, _ = synth.planted_partition_temporal(n, T, 3, 0.3, 0.03, 0.1, None, 4, seed)
+    coupling = ["ordinal", "categorical"][seed % 2]
+    if coupling == "ordinal":
+        omegas = [int(x) for x in rng.integers(0, 4, size=T - 1)]
+    else:
+        M = np.zeros((T, T), np.int64)
+        for a in range(T):
+            for b in range(a + 1, T):
+                M[a, b] = M[b, a] = int(rng.integers(0, 4))
+        omegas = [int(x) for x in M.ravel()]
+    null = ["multislice", "global", "cpm", "multislice"][seed % 4]
+    gamma = (1, 4) if null == "cpm" else (1, 1)
+    gammas = [(int(rng.integers(1, 4)), 2) for _ in range(T)] if null != "global" and seed % 3 == 0 else None
+    with pkg.mslice_build(snaps, coupling=coupling) as h:
+        lab, Q, _ = h.mslice_leiden(gamma=gamma, omega=(1, 2), omegas=omegas, gammas=gammas, null=null, seed=seed)
+    ref, Qref, _ = oracle.leiden(snaps, gamma, (1, 2), coupling=coupling, omegas=omegas, gammas=gammas, null=null,
+                                 seed=seed)
+    assert np.array_equal(lab, ref), ("general", seed)
+    assert abs(Q - Qref) <= 1e-12 * max(1.0, abs(Qref)), ("general", seed)
+long = synth.recipe_graph("school_t7375_n327", T=600)
+with pkg.mslice_build(long) as h:
+    lab, Q, _ = h.mslice_leiden()
+ref, Qref, _ = oracle.leiden(long)
+assert np.array_equal(lab, ref) and abs(Q - Qref) <= 1e-12 * max(1.0, abs(Qref)), "long"
+wl, wq, _ = pkg.leiden_windowed(long[:200], 24, 10)
+owl, owq, _ = oracle.leiden_windowed(long[:200], 24, 10)
+assert np.array_equal(wl, owl), "windowed"
 print("checked ok")
 '''
 

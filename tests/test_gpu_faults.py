@@ -135,3 +135,22 @@ def test_served_request_failure_leaves_the_window(inject):
         prev = lab
     for got, exp in zip(first + rest, expect):
         assert np.array_equal(got, exp)
+
+
+def test_windowed_run_fails_cleanly_and_recovers(inject):
+    on, off = inject
+    snaps = synth.recipe_graph("school_t7375_n327", T=60)
+    ref, _, _ = oracle.leiden_windowed(snaps, 16, 8)
+    failures = 0
+    for k in [0, 2, 8, 40]:
+        on(k)
+        try:
+            lab, _, _ = pkg.leiden_windowed(snaps, 16, 8)
+            assert np.array_equal(lab, ref)
+        except pkg.MsliceError as e:
+            assert e.code == pkg.MSLICE_ENOMEM, (k, e)
+            failures += 1
+        off()
+    assert failures > 0
+    lab, _, _ = pkg.leiden_windowed(snaps, 16, 8)
+    assert np.array_equal(lab, ref)
