@@ -315,7 +315,9 @@ void check_opts(const mslice_opts& opt) {
   if (t[0] || t[1] || t[2] || t[3]) {
     int32_t lo = 0;
     for (int k = 0; k < 4; ++k) {
-      if (t[k] < lo || t[k] > TIER_MAX[k]) fail(MSLICE_EINVAL, "tier cuts must be ascending and within 16, 32, 256, 1024");
+      if (t[k] < lo || t[k] > TIER_MAX[k])
+        fail(MSLICE_EINVAL, "tier cuts must be ascending and within the tiers' capacities (16, 32, " +
+                                std::to_string(TIER_MAX[2]) + ", 1024)");
       lo = t[k];
     }
   }

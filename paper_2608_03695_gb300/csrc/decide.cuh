@@ -60,19 +60,25 @@ namespace mslice {
 #define MSLICE_DENSE_MIN_BLOCKS 3
 #endif
 // entries loaded per lane per round by the warp-per-node tier
-#ifndef MSLICE_T2_EPL
-#define MSLICE_T2_EPL 2
+// tier 2: lanes per node (32: a warp per node, 512-slot tables; 16: two
+// nodes per warp, 256-slot tables, so degrees up to 128)
+#ifndef MSLICE_T2_LANES
+#define MSLICE_T2_LANES 32
 #endif
+#ifndef MSLICE_T2_EPL
+#define MSLICE_T2_EPL (MSLICE_T2_LANES == 32 ? 2 : 4)
+#endif
+constexpr int T2_BITS = MSLICE_T2_LANES == 32 ? 9 : 8;
 
 constexpr int NTIERS = 5;
 // Largest degree each of tiers 0-3 can take (their table capacities); the
 // cuts in use may be lower (TierCuts), the rest go to the next tier.
-constexpr int TIER_MAX[NTIERS - 1] = {16, 32, 256, 1024};
+constexpr int TIER_MAX[NTIERS - 1] = {16, 32, (1 << T2_BITS) / 2, 1024};
 
 // Degree cuts between the tiers: tier t takes degrees in (t[t-1], t[t]].
 // Which tier decides a node never changes its decision, only the speed.
 struct TierCuts {
-  int32_t t[NTIERS - 1] = {16, 32, 256, 1024};
+  int32_t t[NTIERS - 1] = {16, 32, (1 << T2_BITS) / 2, 1024};
 };
 constexpr int TIER3_BITS = 11;  // 2 * 1024 slots
 constexpr int BLOCK_THREADS = 256;
@@ -540,7 +546,7 @@ void decide_all(Ctx& c, const Pol& pol, const TierSegs& sg, const int32_t* tier_
   if (tier_cnt[3] > 0)
     launch_on(c, st[3], k_decide_block<Pol>, dim3(152 * 4), dim3(BLOCK_THREADS), 0, pol, sg.list[3], sg.count[3]);
   if (tier_cnt[2] > 0)
-    launch_on(c, st[2], k_decide_groups<Pol, 32, 9, MSLICE_T2_EPL>, dim3(152 * 4), dim3(GROUP_THREADS), 0, pol,
+    launch_on(c, st[2], k_decide_groups<Pol, MSLICE_T2_LANES, T2_BITS, MSLICE_T2_EPL>, dim3(152 * 4), dim3(GROUP_THREADS), 0, pol,
               sg.list[2], sg.count[2]);
   if (tier_cnt[1] > 0)
     launch_on(c, st[1], k_decide_groups<Pol, 8, 6, 4>, dim3(152 * 4), dim3(GROUP_THREADS), 0, pol, sg.list[1],

@@ -688,8 +688,10 @@ void bucket(Solver& S, const Level& L, uint64_t tag, int it, int lvl, int r, con
 template <class Decide>
 static void autotune_cuts(Solver& S, const Level& L, int it, int r, const int32_t* active, Decide&& decide) {
   Ctx& c = *S.c;
-  static const TierCuts kCand[] = {{{16, 32, 256, 1024}}, {{12, 32, 256, 1024}}, {{16, 24, 256, 1024}},
-                                   {{16, 32, 256, 512}},  {{12, 24, 256, 512}},  {{16, 32, 192, 1024}}};
+  // (cut 2 in units of the tier-2 capacity: T2 = TIER_MAX[2])
+  constexpr int T2 = TIER_MAX[2];
+  static const TierCuts kCand[] = {{{16, 32, T2, 1024}}, {{12, 32, T2, 1024}}, {{16, 24, T2, 1024}},
+                                   {{16, 32, T2, 512}},  {{12, 24, T2, 512}},  {{16, 32, T2 * 3 / 4, 1024}}};
   cudaEvent_t e0, e1;
   check_cuda(cudaEventCreate(&e0), "event");
   check_cuda(cudaEventCreate(&e1), "event");
