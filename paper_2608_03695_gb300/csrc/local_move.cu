@@ -304,40 +304,60 @@ __global__ void k_round_freeze(int32_t* lm_active, int32_t* inst_moved, int32_t 
   }
 }
 
+// A mover's (snapshot, strength) list moves between the two communities'
+// rows; a long list (more than 32 entries, late levels of long sequences) is
+// walked by the whole warp, a short one by its own thread.  The warp stays
+// converged: every lane runs every iteration of the grid-stride loop.
+__device__ __forceinline__ void move_slices(const LevelDev& g, SigStore& sig, int32_t v, int32_t a, int32_t t,
+                                            int64_t b, int64_t e, int64_t from, int64_t step) {
+  for (int64_t j = b + from; j < e; j += step) {
+    int32_t s;
+    long long k;
+    slice_entry(g, v, j, s, k);
+    ss_add(sig, a, s, -k);
+    if (t >= 0) ss_add(sig, t, s, k);
+  }
+}
+
 __global__ void k_lm_apply(LevelDev g, Segs sg, int32_t* labels, int32_t* size, SigStore sig, int32_t* target,
                            int32_t* counters, int32_t* inst_moved) {
   const int total = seg_total(sg);
+  const int lane = threadIdx.x & 31;
   int local = 0, local_empty = 0;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    int32_t v;
-    if (!seg_item(sg, idx, v)) break;
-    const int32_t t = target[v];
-    if (t == NO_MOVE) continue;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t idx = base + lane;
+    int32_t v = 0, t = NO_MOVE, a = 0;
+    int64_t b = 0, e = 0;
+    if (idx < total && seg_item(sg, idx, v)) t = target[v];
 #if MSLICE_CHECKED
-    if (t >= g.N || (t < 0 && t != TO_EMPTY)) {
+    if (t != NO_MOVE && (t >= g.N || (t < 0 && t != TO_EMPTY))) {
       atomicOr(g.chk, ERR_BOUNDS);
-      continue;
+      t = NO_MOVE;
     }
 #endif
-    if (inst_moved) inst_moved[node_inst(g, v)] = 1;
-    const int32_t a = labels[v];
-    atomicSub(&size[a], 1);
-    int64_t b, e;
-    slice_range(g, v, b, e);
-    for (int64_t j = b; j < e; ++j) {
-      int32_t s;
-      long long k;
-      slice_entry(g, v, j, s, k);
-      ss_add(sig, a, s, -k);
-      if (t >= 0) ss_add(sig, t, s, k);
+    if (t != NO_MOVE) {
+      if (inst_moved) inst_moved[node_inst(g, v)] = 1;
+      a = labels[v];
+      atomicSub(&size[a], 1);
+      slice_range(g, v, b, e);
+      if (e - b <= 32) move_slices(g, sig, v, a, t, b, e, 0, 1);
+    }
+    unsigned wide = __ballot_sync(0xffffffffu, t != NO_MOVE && e - b > 32);
+    while (wide) {
+      const int src = __ffs(wide) - 1;
+      wide &= wide - 1;
+      const int32_t vs = __shfl_sync(0xffffffffu, v, src), as = __shfl_sync(0xffffffffu, a, src),
+                    ts = __shfl_sync(0xffffffffu, t, src);
+      const int64_t bs = __shfl_sync(0xffffffffu, b, src), es = __shfl_sync(0xffffffffu, e, src);
+      move_slices(g, sig, vs, as, ts, bs, es, lane, 32);
     }
     if (t >= 0) {
       atomicAdd(&size[t], 1);
       labels[v] = t;
       target[v] = NO_MOVE;
       local++;
-    } else {
+    } else if (t == TO_EMPTY) {
       local_empty++;
     }
   }

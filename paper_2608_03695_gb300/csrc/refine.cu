@@ -291,16 +291,19 @@ __global__ void k_ref_apply(LevelDev g, Segs3 sg, const int32_t* P, const int32_
       atomicAdd(&sizeR[t], 1);
       atomicAdd((ull*)&Wout[t], (ull)(Wc[v] - 2 * Wsel[v] - wp));
       Wout[v] = 0;
-      int64_t b, e;
-      slice_range(g, v, b, e);
-      for (int64_t j = b; j < e; ++j) {
+    }
+    // the sub-community rows take the node's list: by the warp when long
+    int64_t b, e;
+    slice_range(g, v, b, e);
+    const bool wide = e - b > 32;
+    if (wide || lane == 0)
+      for (int64_t j = b + (wide ? lane : 0); j < e; j += (wide ? 32 : 1)) {
         int32_t s;
         long long k;
         slice_entry(g, v, j, s, k);
         ss_add(kr, v, s, -k);
         ss_add(kr, t, s, k);
       }
-    }
   }
 }
 
