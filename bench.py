@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving", "large", "school"])
     ap.add_argument("--null", default="multislice", choices=["multislice", "global", "cpm"],
                     help="plain workload: Q_MS (default), the supra-graph's plain modularity, or temporal CPM")
+    ap.add_argument("--coupling", default="ordinal", choices=["ordinal", "categorical", "tables"],
+                    help="plain workload: ordinal omega (default), categorical coupling of every snapshot pair, "
+                         "or the general form's tables (per-pair omega, per-snapshot gamma)")
     ap.add_argument("--requests", type=int, default=4, help="serving workload: timed snapshots per graph")
     ap.add_argument("--slots", type=int, default=2, help="serving workload: server workers")
     ap.add_argument("--scale", type=float, default=1.0, help="batched workload: node-count scale of every graph")
@@ -147,21 +150,55 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# General-form tables of the plain workload (--coupling tables): omega^(s,s+1)
+# alternating 1/2 and 3/2, gamma^(s) cycling 3/4, 1, 5/4.
+TABLE_OMEGAS = [1 if s % 2 == 0 else 3 for s in range(15)]  # over omega_den 2
+TABLE_GAMMAS = [[(3, 4), (1, 1), (5, 4)][s % 3] for s in range(16)]
+
+
+def gen_kwargs(args):
+    """(build kwargs, solve kwargs shared by the library and the oracle) of the
+    plain workload's model."""
+    build, solve = {}, {"null": args.null}
+    if args.coupling == "categorical":
+        build["coupling"] = "categorical"
+    elif args.coupling == "tables":
+        solve.update(omega=(1, 2), omegas=TABLE_OMEGAS)
+        if args.null != "global":
+            solve["gammas"] = TABLE_GAMMAS
+    return build, solve
+
+
+def oracle_kwargs(args):
+    build, solve = gen_kwargs(args)
+    return {**solve, **build}
+
+
 def workload(args):
-    """The plain workload's config; the null model is named when it is not Q_MS."""
-    if args.null == "multislice":
+    """The plain workload's config; the null model and coupling are named when
+    they are not Q_MS with ordinal omega."""
+    if args.null == "multislice" and args.coupling == "ordinal":
         return dict(WORKLOAD)
-    what = {"global": "global null model (plain modularity of the supra-graph)",
-            "cpm": "temporal Constant Potts Model"}[args.null]
-    return {**WORKLOAD, "workload": WORKLOAD["workload"] + ", " + what, "null_model": args.null}
+    c = dict(WORKLOAD)
+    if args.null != "multislice":
+        what = {"global": "global null model (plain modularity of the supra-graph)",
+                "cpm": "temporal Constant Potts Model"}[args.null]
+        c.update(workload=c["workload"] + ", " + what, null_model=args.null)
+    if args.coupling == "categorical":
+        c.update(workload=c["workload"] + ", categorical coupling", coupling="categorical")
+    elif args.coupling == "tables":
+        c.update(workload=c["workload"] + ", per-pair omega and per-snapshot gamma",
+                 omega="per pair: 1/2, 3/2 alternating",
+                 gamma="per snapshot: 3/4, 1, 5/4 cycling" if args.null != "global" else c["gamma"])
+    return c
 
 
-def cpu_baseline(null="multislice"):
+def cpu_baseline(args):
     import oracle
     from paper_2608_03695_gb300 import synth
     snaps = synth.recipe_graph("powerlaw_t16_n100k", scale_n=ORACLE_SAMPLE_N)
     t = time.perf_counter()
-    _, _, st = oracle.leiden(snaps, null=null)
+    _, _, st = oracle.leiden(snaps, **oracle_kwargs(args))
     el = time.perf_counter() - t
     return {"value": st["lm_edges"] / el, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"one oracle solve of the same recipe at n={ORACLE_SAMPLE_N}, T=16 "
@@ -177,11 +214,11 @@ def run_reference(args):
     oracle.build()
     snaps = synth.recipe_graph("powerlaw_t16_n100k", scale_n=ORACLE_SAMPLE_N)
     for _ in range(args.warmup):
-        oracle.leiden(snaps, n_iterations=1, max_rounds=2, null=args.null)  # short warm-up (page-in, caches)
+        oracle.leiden(snaps, n_iterations=1, max_rounds=2, **oracle_kwargs(args))  # short warm-up (page-in)
     edges, secs = 0, 0.0
     for _ in range(args.steps):
         t = time.perf_counter()
-        _, _, st = oracle.leiden(snaps, null=args.null)
+        _, _, st = oracle.leiden(snaps, **oracle_kwargs(args))
         secs += time.perf_counter() - t
         edges += st["lm_edges"]
     v = edges / secs
@@ -643,8 +680,9 @@ def main():
     snaps = synth.recipe_graph("powerlaw_t16_n100k")
     stream = torch.cuda.Stream()
     if args.profile_run:
-        with pkg.mslice_build(snaps) as h:
-            _, Q, st = h.mslice_leiden(null=args.null)
+        bkw, skw = gen_kwargs(args)
+        with pkg.mslice_build(snaps, **bkw) as h:
+            _, Q, st = h.mslice_leiden(**skw)
         print(json.dumps({"profile_run": True, "Q": Q, "kernel_launches": st["kernel_launches"],
                           "ms_total": st["ms_total"]}), flush=True)
         return
@@ -660,8 +698,8 @@ def main():
     torch.cuda.synchronize()
 
     def step_device(profile=False):
-        h = pkg.mslice_build(dsnaps, device_ptrs=True, stream=stream.cuda_stream)
-        _, Q, st = h.mslice_leiden(out=dlabels, profile=profile, null=args.null)
+        h = pkg.mslice_build(dsnaps, device_ptrs=True, stream=stream.cuda_stream, **gen_kwargs(args)[0])
+        _, Q, st = h.mslice_leiden(out=dlabels, profile=profile, **gen_kwargs(args)[1])
         launches = h.kernel_launches
         h.close()
         return st, launches, Q
@@ -695,7 +733,8 @@ def main():
     stp, _, _ = step_device(profile=True)
     peak, peak_kind = measured_peak()
     achieved = stp["decide_bytes"] / (stp["ms_decide"] / 1e3) / 1e9 if stp["ms_decide"] > 0 else 0.0
-    traffic = decide_traffic() if args.null == "multislice" else None  # counters taken under Q_MS only
+    # counters taken under Q_MS with ordinal omega only
+    traffic = decide_traffic() if args.null == "multislice" and args.coupling == "ordinal" else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (traffic if traffic is None else traffic), "peak_source": peak_kind,
                 "kernel": "local-moving decision, level-0 sub-round (all degree tiers)",
@@ -711,8 +750,8 @@ def main():
         d2h = 4 * N + 8
 
         def step_e2e():
-            h = pkg.mslice_build(hsnaps, host_tensors=True, stream=stream.cuda_stream)
-            _, Q, st = h.mslice_leiden(out=hlabels, null=args.null)
+            h = pkg.mslice_build(hsnaps, host_tensors=True, stream=stream.cuda_stream, **gen_kwargs(args)[0])
+            _, Q, st = h.mslice_leiden(out=hlabels, **gen_kwargs(args)[1])
             h.close()
             return st
 
@@ -739,7 +778,7 @@ def main():
                                 "note": "same edges over local-moving device time only (profiled step)"},
             "roofline": roofline, "clocks": clk, "e2e": e2e}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.null)
+        line["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
