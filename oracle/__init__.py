@@ -36,7 +36,8 @@ class _Csr(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("n_iterations", C.c_int32), ("K", C.c_int32), ("max_rounds", C.c_int32),
                 ("max_levels", C.c_int32), ("seed", C.c_uint64), ("stop_level", C.c_int32),
-                ("stop_stage", C.c_int32), ("stop_rounds", C.c_int32), ("null_model", C.c_int32)]
+                ("stop_stage", C.c_int32), ("stop_rounds", C.c_int32), ("null_model", C.c_int32),
+                ("pad_", C.c_int32), ("theta_num", C.c_int64), ("theta_den", C.c_int64)]
 
 
 class _General(C.Structure):
@@ -107,6 +108,8 @@ def lib():
         L.orc_lambda.argtypes = [P, C.c_int32, C.c_int64, C.c_int64, P, P]
         L.orc_count_improving.argtypes = [P, C.c_int32, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
                                           P, P]
+        L.orc_exp_weight.argtypes = [C.c_uint64] * 5
+        L.orc_exp_weight.restype = C.c_uint64
         L.orc_mix64.argtypes = [C.c_uint64]
         L.orc_mix64.restype = C.c_uint64
         L.orc_default_opts.argtypes = [P]
@@ -151,12 +154,15 @@ def _null(null) -> int:
 
 def leiden(snaps, gamma=(1, 1), omega=(1, 1), n_iterations=2, K=4, max_rounds=100, max_levels=32, seed=0,
            init=None, stop_level=-1, stop_stage=0, stop_rounds=0, null="multislice", coupling="ordinal",
-           omegas=None, gammas=None):
+           omegas=None, gammas=None, theta=None):
     """Returns (labels int32[...], Q, stats dict).  coupling / omegas /
     gammas: the general form (omega^(sr) numerators over omega[1], per-slice
-    gamma pairs)."""
+    gamma pairs).  theta: (num, den) of the randomised refinement (None:
+    the greedy limit)."""
     S = _Slices(snaps)
-    o = _Opts(n_iterations, K, max_rounds, max_levels, seed, stop_level, stop_stage, stop_rounds, _null(null))
+    tn, td = theta if theta is not None else (0, 1)
+    o = _Opts(n_iterations, K, max_rounds, max_levels, seed, stop_level, stop_stage, stop_rounds, _null(null), 0,
+              tn, td)
     cap = max(S.N, 1)
     out = np.zeros(cap, dtype=np.int32)
     Q = C.c_double(0.0)
@@ -210,6 +216,13 @@ def count_improving(snaps, labels, gamma=(1, 1), omega=(1, 1), null="multislice"
     _check(lib().orc_count_improving(S.ptr, S.T, _ptr(lab), gamma[0], gamma[1], omega[0], omega[1], _null(null),
                                      gen.ptr, C.byref(cnt)), "orc_count_improving")
     return cnt.value
+
+
+def exp_weight(d: int, div: int, theta_den: int) -> int:
+    """The randomised refinement's fixed-point weight for key difference d and
+    divisor div = 2M * theta_num (Python ints, each below 2^128)."""
+    m = (1 << 64) - 1
+    return int(lib().orc_exp_weight(d & m, d >> 64, div & m, div >> 64, theta_den))
 
 
 def mix64(x: int) -> int:

@@ -89,6 +89,7 @@ struct Problem {
   bool gamma_table = false;
   std::vector<int64_t> gsn, gsd;
   std::vector<int64_t> cstr;
+  int64_t twoM_all = 0;  // od * 2mu: od*sum(2m_s) + n*sum_s cstr[s]
   int32_t null_model = ORC_NULL_MULTISLICE;
   int64_t ns = 1;              // null scale of the key: od (multislice) or 1 (global)
   std::vector<int64_t> two_m;  // 2m_s of every snapshot
@@ -201,6 +202,12 @@ void slice_masses(const orc_csr* slices, Problem& p) {
     int64_t t = 0;
     for (int64_t e = 0; e < (p.n > 0 ? slices[s].indptr[p.n] : 0); ++e) t += slices[s].weights[e];
     p.two_m[s] = t;
+  }
+  {
+    int64_t sum2m = 0, csum = 0;
+    for (int64_t t : p.two_m) sum2m += t;
+    for (int64_t c : p.cstr) csum += c;
+    p.twoM_all = p.od * sum2m + p.n * csum;
   }
   if (p.null_model == ORC_NULL_GLOBAL) {
     int64_t sum2m = 0;
@@ -429,8 +436,55 @@ MoveResult local_move(const Level& G, const Problem& p, const orc_opts& o, std::
 }
 
 // ---------------------------------------------------------------------------
+// Randomised refinement (Traag et al. 2019: a node joins a target X with
+// probability proportional to exp(dH_X / theta) among the targets with
+// dH_X >= 0, staying alone included).  Reading: with the exact keys G (the
+// gain dQ = 2G / (2^P od 2mu)), the weight of a candidate c is
+//   E(Gmax - G_c) ~= 2^40 exp(-(Gmax - G_c) / (2^(P-1) od 2mu theta)),
+// evaluated by one fixed-point integer recipe (so every implementation gets
+// the same bits):
+//   Y  = floor(d / (2M * theta_num))            (2M = od*2mu, an integer)
+//   yF = floor(Y * theta_den / 2^31)            (y = d/(2^63 2M theta), Q32)
+//   u  = yF * LOG2E                             (y log2 e, Q64; LOG2E = round(log2(e) 2^32))
+//   I  = floor(u / 2^64), f = u mod 2^64        (2^-y log2e = 2^-I 2^-(f/2^64))
+//   g  = floor(f * LN2 / 2^64)                  (f ln 2, Q62; LN2 = round(ln 2 * 2^62))
+//   e^-g by its Taylor series in Q62 (term_k = floor(term_{k-1} g / 2^62) / k,
+//   alternating signs, stopping when a term is 0)
+//   E  = floor(e^-g / 2^(22 + I))               (Q40); 0 when Y >= 2^96, yF >= 64*2^32 or I >= 40.
+// The draw: R = the class hash's 64-bit value for (seed, tag 2, it, level,
+// round 0, node) shifted right by 32; the threshold floor(R * total / 2^32)
+// picks the first candidate, in the order stay, then ascending label, whose
+// cumulative weight exceeds it.
+const uint64_t LOG2E_Q32 = 6196328019ull;
+const uint64_t LN2_Q62 = 3196577161300663915ull;
+
+uint64_t exp_weight(u128 d, u128 div, uint64_t td) {
+  const u128 Y = d / div;
+  if (Y >> 96) return 0;
+  const u128 yF = (Y * (u128)td) >> 31;
+  if (yF >= ((u128)64 << 32)) return 0;
+  const u128 u = yF * (u128)LOG2E_Q32;
+  const uint64_t I = (uint64_t)(u >> 64);
+  if (I >= 40) return 0;
+  const uint64_t f = (uint64_t)u;
+  const u128 g = ((u128)f * (u128)LN2_Q62) >> 64;
+  u128 term = (u128)1 << 62;
+  i128 sum = (i128)term;
+  for (int k = 1; k <= 40; ++k) {
+    term = ((term * g) >> 62) / (u128)k;
+    if (term == 0) break;
+    sum += (k & 1) ? -(i128)term : (i128)term;
+  }
+  return (uint64_t)((u128)sum >> (22 + I));
+}
+
+uint64_t class_hash(uint64_t seed, uint64_t tag, uint64_t it, uint64_t lvl, uint64_t r, uint64_t v) {
+  return mix64(seed ^ mix64(tag ^ mix64(it ^ mix64(lvl ^ mix64(r ^ mix64(v))))));
+}
+
+// ---------------------------------------------------------------------------
 // Refinement (Leiden, Sec. 3.2; Traag et al. 2019, refinement phase) in the
-// greedy limit.  Inside each local-moving community C every node starts as
+// greedy limit (theta = 0; theta > 0: randomised, above).  Inside each local-moving community C every node starts as
 // its own sub-community; one pass of K sub-rounds (class tag 1, round 0).
 // A node still alone in its sub-community and well connected to C joins the
 // well-connected sub-community R of C with the largest positive key
@@ -495,16 +549,36 @@ std::vector<int32_t> refine(const Level& G, const Problem& p, const orc_opts& o,
         if (P[uw.first] == C) Wmap[R[uw.first]] += uw.second;
       int32_t best = NO_MOVE;
       i128 Gbest = 0;  // key of staying alone
+      std::vector<std::pair<int32_t, i128>> cands;  // randomised: targets with G >= 0, ascending X
       for (const auto& xw : Wmap) {
         const int32_t X = xw.first;
         if (X == R[v]) continue;
         if (sizeR[X] == 1 && vertex_class(o.seed, 1, it, lvl, 0, member[X], o.K) == q) continue;
         if (!wc[X]) continue;
         const i128 Gx = key(p, xw.second, null_sum(p, G.kvec[v], [&](int32_t s) { return kr(X, s); }));
+        if (Gx >= 0) cands.push_back({X, Gx});
         if (Gx > Gbest) {  // ascending X: the first maximum is the smallest label
           best = X;
           Gbest = Gx;
         }
+      }
+      if (o.theta_num > 0) {
+        const u128 div = (u128)(uint64_t)p.twoM_all * (u128)(uint64_t)o.theta_num;
+        const uint64_t td = (uint64_t)o.theta_den;
+        u128 total = exp_weight((u128)Gbest, div, td);  // staying: key 0
+        for (const auto& xc : cands) total += exp_weight((u128)(Gbest - xc.second), div, td);
+        const uint64_t Rd = class_hash(o.seed, 2, it, lvl, 0, v) >> 32;
+        const u128 thr = ((u128)Rd * total) >> 32;
+        u128 cum = exp_weight((u128)Gbest, div, td);
+        best = NO_MOVE;
+        if (!(thr < cum))
+          for (const auto& xc : cands) {
+            cum += exp_weight((u128)(Gbest - xc.second), div, td);
+            if (thr < cum) {
+              best = xc.first;
+              break;
+            }
+          }
       }
       target[v] = best;
     }
@@ -714,6 +788,12 @@ extern "C" {
 
 uint64_t orc_mix64(uint64_t x) { return mix64(x); }
 
+uint64_t orc_exp_weight(uint64_t d_lo, uint64_t d_hi, uint64_t div_lo, uint64_t div_hi, uint64_t theta_den) {
+  const u128 d = ((u128)d_hi << 64) | d_lo, div = ((u128)div_hi << 64) | div_lo;
+  if (div == 0) return 0;
+  return exp_weight(d, div, theta_den);
+}
+
 void orc_default_opts(orc_opts* o) {
   o->n_iterations = 2;  // two optimisation passes (paper Sec. 4)
   o->K = 4;
@@ -724,6 +804,8 @@ void orc_default_opts(orc_opts* o) {
   o->stop_stage = 0;
   o->stop_rounds = 0;
   o->null_model = ORC_NULL_MULTISLICE;
+  o->theta_num = 0;
+  o->theta_den = 1;
 }
 
 int orc_lambda(const orc_csr* slices, int32_t T, int64_t gn, int64_t gd, uint64_t* lam, int64_t* two_m) {
@@ -818,6 +900,8 @@ int orc_leiden(const orc_csr* slices, int32_t T, int64_t gn, int64_t gd, int64_t
   orc_opts opt;
   orc_default_opts(&opt);
   if (o) opt = *o;
+  if (opt.theta_num < 0 || opt.theta_den < 1 || opt.theta_num > ((int64_t)1 << 31) || opt.theta_den > ((int64_t)1 << 31))
+    return ORC_EINVAL;
   Problem p;
   int rc = setup(slices, T, gn, gd, on, od, p, opt.null_model, gen);
   if (rc) return rc;

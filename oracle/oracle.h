@@ -103,8 +103,18 @@ typedef struct {
   int32_t stop_level;
   int32_t stop_stage;
   int32_t stop_rounds;
-  int32_t null_model;  /* ORC_NULL_MULTISLICE (default) or ORC_NULL_GLOBAL */
+  int32_t null_model;  /* ORC_NULL_MULTISLICE (default), ORC_NULL_GLOBAL or ORC_NULL_CPM */
+  int32_t pad_;
+  /* refinement randomness theta = theta_num/theta_den (Traag et al.'s
+   * randomised refinement); theta_num = 0 (default): the greedy limit */
+  int64_t theta_num;
+  int64_t theta_den;
 } orc_opts;
+
+/* The randomised refinement's fixed-point weight 2^40 exp(-d / (2^63 div /
+ * theta_den)) for d (lo, hi) and div = 2M * theta_num (lo, hi): test access
+ * to the integer recipe the refinement uses. */
+uint64_t orc_exp_weight(uint64_t d_lo, uint64_t d_hi, uint64_t div_lo, uint64_t div_hi, uint64_t theta_den);
 
 typedef struct {
   int32_t iterations;      /* outer iterations run */

@@ -13,6 +13,7 @@ quantity another way:
     persistence and omega=0 decoupling.
 """
 import itertools
+import math
 import os
 from fractions import Fraction
 
@@ -1200,3 +1201,103 @@ def test_windowed_regions_are_the_window_partitions(seed):
         got, want = lab[a * n:end * n], part[region]
         assert len(set(zip(got.tolist(), want.tolist()))) == len(set(want.tolist())) == len(set(got.tolist()))
         prev = part
+
+
+# ----------------------------------------------------------------- randomised refinement
+# Traag et al.'s randomised refinement: a node joins a target X (or stays)
+# with probability proportional to exp(dQ_X / theta), staying weighing
+# exp(0).  Pinned by: the fixed-point weight against math.exp; the
+# frequencies of one node's choices over many seeds against those
+# probabilities (chi-square), computed from the definition; determinism
+# per seed; the usual convergence invariants.
+MASK64 = (1 << 64) - 1
+
+
+def py_mix64(x):
+    """The SplitMix64 finaliser (pinned to published outputs above)."""
+    x = ((x ^ (x >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+    x = ((x ^ (x >> 27)) * 0x94D049BB133111EB) & MASK64
+    return x ^ (x >> 31)
+
+
+def py_class(seed, tag, it, lvl, r, v, K):
+    h = py_mix64(seed ^ py_mix64(tag ^ py_mix64(it ^ py_mix64(lvl ^ py_mix64(r ^ py_mix64(v))))))
+    return h % K
+
+
+def test_splitmix_restatement_matches_oracle():
+    for x in [0, 1, 12345, MASK64, 0xDEADBEEF]:
+        assert py_mix64(x) == oracle.mix64(x)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_exp_weight_against_math(seed):
+    rng = np.random.default_rng(2500 + seed)
+    for _ in range(300):
+        div = int(rng.integers(1, 1 << 61)) * int(rng.integers(1, 1 << 20))
+        td = int(rng.integers(1, 1 << 31))
+        y = float(rng.uniform(0, 30)) if rng.random() < 0.9 else float(rng.uniform(0, 1e-6))
+        d = int(y * (1 << 63) * div / td)  # y = d td / (2^63 div)
+        if d >= 1 << 127:
+            continue
+        got = oracle.exp_weight(d, div, td)
+        want = (1 << 40) * math.exp(-d * td / ((1 << 63) * div))
+        assert abs(got - want) <= 1e-8 * want + 2, (d, div, td, got, want)
+    assert oracle.exp_weight(0, 12345, 7) == 1 << 40
+    assert oracle.exp_weight(1 << 126, 1, 1 << 31) == 0
+
+
+def test_randomised_choice_frequencies():
+    """Star: centre 0 with leaves of weights 3, 1, 4, 1, 5, all in one
+    community, no local moving, K = 2.  Over the seeds where the centre is
+    in class 0, its target is a class-1 leaf with probability proportional
+    to exp(dQ_i / theta) (staying: exp(0)); leaves of class 0 are active and
+    not targets."""
+    stats = pytest.importorskip("scipy.stats")
+    w = [3, 1, 4, 1, 5]
+    u = np.zeros(5, np.int64)
+    v = np.arange(1, 6, dtype=np.int64)
+    snaps = [synth.csr_from_edges(6, u, v, np.array(w, np.int32))]
+    gamma, theta = (1, 4), (1, 10)
+    two_m = 2 * sum(w)
+    k0 = sum(w)
+    obs = np.zeros(6)
+    exp_ = np.zeros(6)
+    for seed in range(6000):
+        if py_class(seed, 1, 0, 0, 0, 0, 2) != 0:
+            continue
+        lab, _, _ = oracle.leiden(snaps, gamma, (1, 1), K=2, seed=seed, init=np.zeros(6, np.int32), stop_level=0,
+                                  stop_stage=2, stop_rounds=-1, theta=theta)
+        obs[lab[0]] += 1
+        wts = np.zeros(6)
+        wts[0] = 1.0
+        for i in range(1, 6):
+            if py_class(seed, 1, 0, 0, 0, i, 2) == 1:
+                dq = 2 * (w[i - 1] - gamma[0] / gamma[1] * k0 * w[i - 1] / two_m) / two_m
+                wts[i] = math.exp(dq * theta[1] / theta[0])
+        exp_ += wts / wts.sum()
+    assert obs.sum() > 2500 and abs(obs.sum() - exp_.sum()) < 1e-6
+    chi = stats.chisquare(obs, exp_)
+    assert chi.pvalue > 1e-4, (obs, exp_, chi)
+    assert obs[5] > obs[3] > obs[1] > obs[0]  # heavier leaves are chosen more often
+
+
+def test_randomised_refinement_determinism_and_invariants():
+    snaps, _ = synth.planted_partition_temporal(60, 3, n_blocks=3, p_in=0.3, p_out=0.04, switch_frac=0.1, w_max=5,
+                                                seed=4)
+    a = oracle.leiden(snaps, theta=(1, 100), seed=3)
+    b = oracle.leiden(snaps, theta=(1, 100), seed=3)
+    assert np.array_equal(a[0], b[0]) and a[1] == b[1]
+    differ = 0
+    for s in range(6):
+        lab, Q, st = oracle.leiden(snaps, theta=(1, 100), seed=s, n_iterations=20)
+        g, Qg, _ = oracle.leiden(snaps, seed=s, n_iterations=20)
+        differ += not np.array_equal(lab, g)
+        if st["last_level0_moves"] == 0:
+            assert oracle.count_improving(snaps, lab) == 0
+        if st["stop_reason"] == 1:
+            assert components_ok(snaps, lab, (1, 1))
+        assert Q == pytest.approx(oracle.modularity(snaps, lab), rel=1e-15)
+    assert differ > 0  # the randomness is not vacuous
+    with pytest.raises(oracle.OracleError):
+        oracle.leiden(snaps, theta=(-1, 1))
