@@ -142,6 +142,15 @@ typedef struct {
    * 32, 256, 1024.  Otherwise 0 <= c0 <= 16, c0 <= c1 <= 32, c1 <= c2 <= 256,
    * c2 <= c3 <= 1024.  They change the speed only, never the result. */
   int32_t tier_cuts[4];
+  /* Randomised refinement (Traag et al.): theta = theta_num/theta_den > 0
+   * makes an eligible singleton join a target X with probability
+   * proportional to exp(dQ_X / theta) among the targets with dQ_X >= 0,
+   * staying weighing exp(0); theta_num = 0 (the default) is the greedy
+   * limit (largest positive gain).  The weights are 2^40 exp(-(Gmax - G) /
+   * (2^63 2M theta)) by a fixed integer recipe (2M = omega_den * 2mu) and the
+   * draw comes from the schedule's hash, so results stay reproducible bit for
+   * bit.  0 <= theta_num <= 2^31, 1 <= theta_den <= 2^31. */
+  int64_t theta_num, theta_den;
 } mslice_opts;
 
 typedef struct {

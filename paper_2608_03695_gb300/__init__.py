@@ -71,7 +71,8 @@ class Opts(C.Structure):
                 ("max_levels", C.c_int32), ("seed", C.c_uint64), ("gamma_num", C.c_int64),
                 ("gamma_den", C.c_int64), ("omega_num", C.c_int64), ("omega_den", C.c_int64),
                 ("flags", C.c_int32), ("stop_level", C.c_int32), ("stop_stage", C.c_int32),
-                ("stop_rounds", C.c_int32), ("tier_cuts", C.c_int32 * 4)]
+                ("stop_rounds", C.c_int32), ("tier_cuts", C.c_int32 * 4), ("theta_num", C.c_int64),
+                ("theta_den", C.c_int64)]
 
 
 class Stats(C.Structure):
@@ -249,17 +250,21 @@ class Handle:
 
     def mslice_leiden(self, gamma=(1, 1), omega=(1, 1), max_levels=32, seed=0, n_iterations=2, K=4,
                       max_rounds=100, init=None, stop_level=-1, stop_stage=0, stop_rounds=0, out=None,
-                      profile=False, tier_cuts=None, autotune=False, null="multislice", omegas=None, gammas=None):
+                      profile=False, tier_cuts=None, autotune=False, null="multislice", omegas=None, gammas=None,
+                      theta=None):
         """Returns (labels, Q, stats).  With ``out`` a device tensor (int32[N])
         the labels stay on the device (MSLICE_DEVICE_PTRS); ``init`` may then
         be a device tensor as well.  ``null="global"`` optimises the plain
         modularity of the supra-graph instead of Q_MS (MSLICE_NULL_GLOBAL).
-        ``omegas`` / ``gammas``: the general form (mslice_leiden_general)."""
+        ``omegas`` / ``gammas``: the general form (mslice_leiden_general).
+        ``theta``: (num, den) of the randomised refinement (None: greedy)."""
         o = default_opts()
         o.gamma_num, o.gamma_den = gamma
         o.omega_num, o.omega_den = omega
         o.max_levels, o.seed, o.n_iterations, o.K, o.max_rounds = max_levels, seed, n_iterations, K, max_rounds
         o.stop_level, o.stop_stage, o.stop_rounds = stop_level, stop_stage, stop_rounds
+        if theta is not None:
+            o.theta_num, o.theta_den = theta
         dev = out is not None and hasattr(out, "is_cuda") and out.is_cuda
         if profile:
             o.flags |= MSLICE_PROFILE
@@ -355,9 +360,11 @@ class Batch:
         return idx.value
 
     def mslice_batch_run(self, n_iterations=2, K=4, max_rounds=100, max_levels=32, seed=0, profile=False,
-                         tier_cuts=None, autotune=False, null="multislice") -> dict:
+                         tier_cuts=None, autotune=False, null="multislice", theta=None) -> dict:
         o = default_opts()
         o.n_iterations, o.K, o.max_rounds, o.max_levels, o.seed = n_iterations, K, max_rounds, max_levels, seed
+        if theta is not None:
+            o.theta_num, o.theta_den = theta
         if profile:
             o.flags |= MSLICE_PROFILE
         if autotune:
@@ -413,7 +420,7 @@ class Server:
 
     def __init__(self, window=8, n_slots=2, max_batch=64, hbm_budget=0, gamma=(1, 1), omega=(1, 1),
                  n_iterations=2, K=4, max_rounds=100, max_levels=32, seed=0, max_batch_nodes=None,
-                 null="multislice"):
+                 null="multislice", theta=None):
         o = ServerOpts()
         lib().mslice_server_default_opts(C.byref(o))
         o.window, o.n_slots, o.max_batch, o.hbm_budget = window, n_slots, max_batch, hbm_budget
@@ -424,6 +431,8 @@ class Server:
         o.solve.n_iterations, o.solve.K, o.solve.max_rounds = n_iterations, K, max_rounds
         o.solve.max_levels, o.solve.seed = max_levels, seed
         o.solve.flags = _NULLS[null]
+        if theta is not None:
+            o.solve.theta_num, o.solve.theta_den = theta
         s = C.c_void_p()
         _check(lib().mslice_server_create(C.byref(o), C.byref(s)), "mslice_server_create")
         self._s = s
@@ -570,7 +579,7 @@ def _csr_array(snaps, device_ptrs=False, host_tensors=False):
 
 
 def mslice_leiden_windowed(snaps, W, stride, gamma=(1, 1), omega=(1, 1), null="multislice", n_iterations=2, K=4,
-                           max_rounds=100, max_levels=32, seed=0, stream=None, device_ptrs=False):
+                           max_rounds=100, max_levels=32, seed=0, stream=None, device_ptrs=False, theta=None):
     """Windowed optimisation of a long snapshot sequence
     (``mslice_leiden_windowed``): windows of W snapshots at the given stride,
     warm-started and stitched through their overlaps.  Returns (labels
@@ -583,6 +592,8 @@ def mslice_leiden_windowed(snaps, W, stride, gamma=(1, 1), omega=(1, 1), null="m
     o.omega_num, o.omega_den = omega
     o.n_iterations, o.K, o.max_rounds, o.max_levels, o.seed = n_iterations, K, max_rounds, max_levels, seed
     o.flags = _NULLS[null] | (MSLICE_DEVICE_PTRS if device_ptrs else 0)
+    if theta is not None:
+        o.theta_num, o.theta_den = theta
     labels = np.zeros(max(n * T, 1), dtype=np.int32)
     cap = T + 1
     Qw = np.zeros(cap, dtype=np.float64)

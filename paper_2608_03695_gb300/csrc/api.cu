@@ -311,6 +311,7 @@ void check_opts(const mslice_opts& opt) {
   if (opt.n_iterations < 1 || opt.K < 1 || opt.max_rounds < 1 || opt.max_levels < 1)
     fail(MSLICE_EINVAL, "n_iterations, K, max_rounds and max_levels must be >= 1");
   if (opt.K > 64) fail(MSLICE_EINVAL, "K must be at most 64");
+  if (!rational_ok(opt.theta_num, opt.theta_den, true)) fail(MSLICE_EINVAL, "theta must be a rational >= 0");
   const int32_t* t = opt.tier_cuts;
   if (t[0] || t[1] || t[2] || t[3]) {
     int32_t lo = 0;
@@ -389,6 +390,8 @@ void run_solve(Ctx& c, const SupraGraph& G, const std::vector<InstParams>& jobs,
   p.cuts = cuts_of(opt);
   p.autotune = (opt.flags & MSLICE_AUTOTUNE) != 0;
   p.global_null = null_model_of(opt.flags) == NULL_SUPRA_GLOBAL;
+  p.theta_num = opt.theta_num;
+  p.theta_den = opt.theta_den;
   p.cpm = null_model_of(opt.flags) == NULL_CPM;
   run_leiden(c, G, jobs, p, opt.stop_level, opt.stop_stage, opt.stop_rounds, init, out, S, ro);
   std::memset(&stats, 0, sizeof(stats));
@@ -446,6 +449,8 @@ void mslice_default_opts(mslice_opts* o) {
   o->stop_level = -1;
   o->stop_stage = 0;
   o->stop_rounds = 0;
+  o->theta_num = 0;
+  o->theta_den = 1;
 }
 
 const char* mslice_last_error(void) { return g_last_error.c_str(); }
@@ -1022,6 +1027,8 @@ extern "C" int mslice_leiden_windowed(const mslice_csr* slices, int32_t T, int32
     sp.cuts = cuts_of(opt);
     sp.global_null = nm == NULL_SUPRA_GLOBAL;
     sp.cpm = nm == NULL_CPM;
+    sp.theta_num = opt.theta_num;
+    sp.theta_den = opt.theta_den;
     const int64_t Nw = n * Wn;
     int32_t* prev = ws.get<int32_t>("w_prev", Nw);
     int32_t* init = ws.get<int32_t>("w_init", Nw);

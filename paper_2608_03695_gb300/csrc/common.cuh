@@ -37,10 +37,17 @@ __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 
 // Class of node v in round r of level lvl, iteration it; tag 0 = local
 // moving, 1 = refinement.  The chain folds one counter per step.
+// The schedule's counter-based hash of (seed, tag, iteration, level, round,
+// node); its value mod K is the node's class, and tag 2 gives the draw of
+// the randomised refinement.
+__host__ __device__ __forceinline__ uint64_t class_hash(uint64_t seed, uint64_t tag, uint64_t it, uint64_t lvl,
+                                                        uint64_t r, uint64_t v) {
+  return mix64(seed ^ mix64(tag ^ mix64(it ^ mix64(lvl ^ mix64(r ^ mix64(v))))));
+}
+
 __host__ __device__ __forceinline__ int vertex_class(uint64_t seed, uint64_t tag, uint64_t it, uint64_t lvl,
                                                      uint64_t r, uint64_t v, int K) {
-  uint64_t h = mix64(seed ^ mix64(tag ^ mix64(it ^ mix64(lvl ^ mix64(r ^ mix64(v))))));
-  return (int)(h % (uint64_t)K);
+  return (int)(class_hash(seed, tag, it, lvl, r, v) % (uint64_t)K);
 }
 
 // -------------------------------------------------------------------------

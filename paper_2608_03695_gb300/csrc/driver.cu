@@ -377,7 +377,21 @@ void set_instances(Ctx& c, Solver& S, const std::vector<InstParams>& jobs) {
     check_cuda(cudaMemcpyAsync(S.gs_d, gs.data(), gs.size() * sizeof(long long), cudaMemcpyHostToDevice, c.stream),
                "copy");
   }
-  sync(c);  // hp, cw and gs are pageable host memory
+  // randomised refinement: 2M theta_num of every instance
+  S.rdiv = nullptr;
+  if (S.p.theta_num > 0) {
+    std::vector<u128> rd(B);
+    for (int32_t i = 0; i < B; ++i) {
+      const InstInfo& in = G.inst[i];
+      long long sum2m = 0;
+      for (int32_t s = in.soff; s < in.soff + in.T; ++s) sum2m += G.two_m_host[s];
+      rd[i] = (u128)(ull)(S.od_h[i] * sum2m + S.csum_h[i]) * (u128)(ull)S.p.theta_num;
+      if (rd[i] == 0) rd[i] = 1;  // an edgeless instance: every key is 0
+    }
+    S.rdiv = c.ws->get<u128>("s_rdiv", B);
+    check_cuda(cudaMemcpyAsync(S.rdiv, rd.data(), B * sizeof(u128), cudaMemcpyHostToDevice, c.stream), "copy");
+  }
+  sync(c);  // hp, cw, gs and rd are pageable host memory
 }
 
 void run_leiden(Ctx& c, const SupraGraph& G, const std::vector<InstParams>& jobs, const SolveParams& p,

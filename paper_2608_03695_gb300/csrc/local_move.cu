@@ -615,6 +615,7 @@ void prepare_level(Solver& S, const Level& L) {
     S.gcap = hb.gt;
     S.gkeys = c.ws->get<int32_t>("s_gkeys", S.gcap);
     S.gvals = c.ws->get<long long>("s_gvals", S.gcap);
+    if (S.p.theta_num > 0) S.gwts = c.ws->get<ull>("s_gwts", S.gcap);
   }
 }
 

@@ -238,7 +238,335 @@ struct RefPolicy {
       target[v] = NO_MOVE;
     }
   }
+  // randomised refinement: the key of target X when X is allowed and the
+  // key is >= 0 (cand() without its strict-gain filter)
+  __device__ bool rand_key(int32_t v, const VCtx& vc, int32_t X, long long W, i128& G) const {
+    const Probe p = probe(v, vc, X);
+    if (p.size == 1 && p.cls == q) return false;
+    if (!p.wc) return false;
+    if (vc.single) {
+      const long long x = vc.k > 0 ? sst_resolve<DENSE>(kr, X, vc.s, p.first) : 0;
+      G = (((i128)W) << P_BITS) - (i128)(vc.A * (u128)(ull)x);
+    } else {
+      int64_t b, e;
+      slice_range(g, v, b, e);
+      u128 ns = 0;
+      for (int64_t j = b; j < e; ++j) {
+        int32_t s;
+        long long k;
+        slice_entry(g, v, j, s, k);
+        ns += lam_k_x(lam, s, k, sst_get<DENSE>(kr, X, s));
+      }
+      G = (((i128)W) << P_BITS) - (i128)((u128)(ull)null_scale(g, vc.om) * ns);
+    }
+    return G >= 0;
+  }
 };
+
+// ---------------------------------------------------------------------------
+// Randomised refinement (Traag et al.: an eligible singleton joins a target X
+// with probability proportional to exp(dQ_X / theta) among the targets with
+// dQ_X >= 0, staying weighing exp(0)).  With dQ = G / (2^63 2M) (G the exact
+// key, 2M = od*2mu) the weight of a candidate is 2^40 exp(-(Gmax - G) /
+// (2^63 2M theta)), evaluated by an integer recipe that every implementation
+// follows bit for bit:
+//   Y  = floor(d / (2M theta_num))   (0 weight when Y >= 2^96)
+//   yF = floor(Y theta_den / 2^31)   (y in Q32; 0 weight when y >= 64)
+//   u  = yF * LOG2E                  (y log2 e in Q64; LOG2E = round(log2(e) 2^32))
+//   I  = floor(u / 2^64)             (0 weight when I >= 40), f = u mod 2^64
+//   g  = floor(f LN2 / 2^64)         (f ln 2 in Q62; LN2 = round(ln(2) 2^62))
+//   e^-g = its Taylor series in Q62 (term_k = floor(floor(term_{k-1} g / 2^62) / k),
+//          alternating signs, ending at the first zero term)
+//   weight = floor(e^-g / 2^(22 + I))   (Q40).
+// The draw R = class_hash(seed, 2, it, level, 0, node) / 2^32 sets the
+// threshold floor(R * total / 2^32); the first candidate, in the order
+// staying, then ascending label, whose cumulative weight exceeds it wins.
+constexpr ull LOG2E_Q32 = 6196328019ull;
+constexpr ull LN2_Q62 = 3196577161300663915ull;
+
+__device__ __forceinline__ ull rand_weight(u128 d, u128 div, ull td) {
+  const u128 Y = d / div;
+  if (Y >> 96) return 0;
+  const u128 yF = (Y * (u128)td) >> 31;
+  if (yF >= ((u128)64 << 32)) return 0;
+  const u128 u = yF * (u128)LOG2E_Q32;
+  const ull I = (ull)(u >> 64);
+  if (I >= 40) return 0;
+  const u128 g = ((u128)(ull)u * (u128)LN2_Q62) >> 64;
+  u128 term = (u128)1 << 62;
+  i128 sum = (i128)term;
+  for (int k = 1; k <= 40; ++k) {
+    term = ((term * g) >> 62) / (u128)k;
+    if (term == 0) break;
+    sum += (k & 1) ? -(i128)term : (i128)term;
+  }
+  return (ull)((u128)sum >> (22 + I));
+}
+
+struct RandParams {
+  uint64_t seed, it, lvl;
+  const u128* div;  // 2M theta_num of every instance
+  ull td;           // theta_den
+};
+
+__device__ __forceinline__ i128 shfl_xor_i128(i128 x, int m) {
+  ull lo = (ull)(u128)x, hi = (ull)((u128)x >> 64);
+  lo = __shfl_xor_sync(0xffffffffu, lo, m);
+  hi = __shfl_xor_sync(0xffffffffu, hi, m);
+  return (i128)(((u128)hi << 64) | lo);
+}
+
+__device__ __forceinline__ i128 warp_max_i128(i128 x) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    const i128 o = shfl_xor_i128(x, m);
+    if (o > x) x = o;
+  }
+  return x;
+}
+
+// One node's randomised choice over the candidate keys listed in its table
+// (slots cand[0..n), or every slot when cand is null), by a team of `nt`
+// threads (a warp, or a block with sm scratch); returns the chosen label
+// (INT32_MAX: stay) and its weight W through Wb, valid on thread t == 0.
+template <class Pol, bool BLOCK>
+__device__ int32_t rand_choose(const Pol& pol, int32_t v, const typename Pol::VCtx& vc, const RandParams& rp,
+                               const int32_t* K, const long long* V, ull* WT, const uint16_t* cand, int64_t n,
+                               int t, int nt, u128* sm128, long long& Wb) {
+  const u128 div = rp.div[node_inst(pol.g, v)];
+  // pass 1: largest allowed key (staying: 0)
+  i128 gmax = 0;
+  for (int64_t j = t; j < n; j += nt) {
+    const int slot = cand ? cand[j] : (int)j;
+    const int32_t X = K[slot];
+    i128 G;
+    if (X >= 0 && pol.rand_key(v, vc, X, V[slot], G) && G > gmax) gmax = G;
+  }
+  gmax = warp_max_i128(gmax);
+  if (BLOCK) {
+    if ((threadIdx.x & 31) == 0) sm128[threadIdx.x >> 5] = (u128)gmax;
+    __syncthreads();
+    gmax = 0;
+    for (int w = 0; w < (nt >> 5); ++w)
+      if ((i128)sm128[w] > gmax) gmax = (i128)sm128[w];
+    __syncthreads();
+  }
+  // pass 2: weights (0 for a slot that is not a candidate) and their total
+  u128 part = 0;
+  for (int64_t j = t; j < n; j += nt) {
+    const int slot = cand ? cand[j] : (int)j;
+    const int32_t X = K[slot];
+    i128 G;
+    ull w = 0;
+    if (X >= 0 && pol.rand_key(v, vc, X, V[slot], G)) w = rand_weight((u128)(gmax - G), div, rp.td);
+    WT[slot] = w;
+    part += w;
+  }
+  part = warp_sum_u128(part);
+  if (BLOCK) {
+    if ((threadIdx.x & 31) == 0) sm128[threadIdx.x >> 5] = part;
+    __syncthreads();
+    part = 0;
+    for (int w = 0; w < (nt >> 5); ++w) part += sm128[w];
+    __syncthreads();
+  } else {
+    __syncwarp();
+  }
+  const ull wstay = rand_weight((u128)gmax, div, rp.td);
+  const u128 total = part + wstay;
+  const ull R = class_hash(rp.seed, 2, rp.it, rp.lvl, 0, local_id(pol.g, v)) >> 32;
+  const u128 thr = ((u128)R * total) >> 32;
+  if (BLOCK) {
+    if (threadIdx.x == 0) sm128[0] = ~(u128)0;  // "no candidate chosen"
+    __syncthreads();
+  }
+  // pass 3: the candidate whose interval [cum, cum + w) holds thr, in
+  // ascending label order after staying
+  int32_t chosen = INT32_MAX;
+  long long wchosen = 0;
+  if (!(thr < wstay)) {
+    for (int64_t j = t; j < n; j += nt) {
+      const int slot = cand ? cand[j] : (int)j;
+      const ull wj = WT[slot];
+      if (wj == 0) continue;
+      const int32_t X = K[slot];
+      u128 cb = wstay;
+      for (int64_t i = 0; i < n; ++i) {
+        const int s2 = cand ? cand[i] : (int)i;
+        const ull wi = WT[s2];
+        if (wi && K[s2] < X) cb += wi;
+      }
+      if (cb <= thr && thr < cb + wj) {
+        chosen = X;
+        wchosen = V[slot];
+      }
+    }
+  }
+  // at most one thread holds the choice: hand it to every thread
+  if (BLOCK) {
+    if (chosen != INT32_MAX) sm128[0] = ((u128)(uint32_t)chosen << 64) | (u128)(ull)wchosen;
+    __syncthreads();
+    const u128 r = sm128[0];
+    __syncthreads();
+    if (r == ~(u128)0) {
+      chosen = INT32_MAX;
+      wchosen = 0;
+    } else {
+      chosen = (int32_t)(uint32_t)(r >> 64);
+      wchosen = (long long)(ull)r;
+    }
+  } else {
+    const unsigned hit = __ballot_sync(0xffffffffu, chosen != INT32_MAX);
+    if (hit) {
+      const int src = __ffs(hit) - 1;
+      chosen = __shfl_sync(0xffffffffu, chosen, src);
+      wchosen = __shfl_sync(0xffffffffu, wchosen, src);
+    }
+  }
+  Wb = wchosen;
+  return chosen;
+}
+
+// Randomised decisions, degree tiers 0-2 (degree <= 256): one warp per node,
+// a 512-slot table per warp in shared memory.
+template <bool DENSE>
+__global__ void __launch_bounds__(128) k_ref_random_warp(RefPolicy<DENSE> pol, const int32_t* list,
+                                                         const int32_t* count_ptr, RandParams rp) {
+  constexpr int WARPS = 4, BITS = 9, SLOTS = 1 << BITS, MAXC = SLOTS / 2;
+  __shared__ int32_t hk[WARPS][SLOTS];
+  __shared__ long long hv[WARPS][SLOTS];
+  __shared__ ull hw[WARPS][SLOTS];
+  __shared__ uint16_t cl[WARPS][MAXC];
+  __shared__ int32_t ncand[WARPS];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t* K = hk[w];
+  long long* V = hv[w];
+  ull* WT = hw[w];
+  uint16_t* CL = cl[w];
+  for (int i = lane; i < SLOTS; i += 32) {
+    K[i] = -1;
+    V[i] = 0;
+  }
+  if (lane == 0) ncand[w] = 0;
+  __syncwarp();
+  const int count = *count_ptr;
+  for (int idx = blockIdx.x * WARPS + w; idx < count; idx += gridDim.x * WARPS) {
+    const int32_t v = list[idx];
+    if (!pol.begin(v)) {
+      if (lane == 0) pol.skip(v);
+      continue;
+    }
+    const typename RefPolicy<DENSE>::VCtx vc = pol.vctx(v);
+    for (int64_t e = pol.g.rowptr[v] + lane; e < pol.g.rowptr[v + 1]; e += 32) {
+      int32_t key;
+      long long wgt;
+      if (pol.edge(v, vc, e, key, wgt)) {
+        bool fresh;
+        const int slot = table_add_slot(K, V, BITS, key, wgt, fresh);
+#if MSLICE_CHECKED
+        if (slot < 0) atomicOr(pol.g.chk, ERR_BOUNDS);
+#endif
+        if (fresh) CL[atomicAdd(&ncand[w], 1)] = (uint16_t)slot;
+      }
+    }
+    __syncwarp();
+    const int n = ncand[w];
+    long long Wb;
+    const int32_t X = rand_choose<RefPolicy<DENSE>, false>(pol, v, vc, rp, K, V, WT, CL, n, lane, 32, nullptr, Wb);
+    if (lane == 0) pol.finish(v, Cand{0, X}, Wb, 0, vc);
+    __syncwarp();
+    for (int j = lane; j < n; j += 32) {
+      const int slot = CL[j];
+      K[slot] = -1;
+      V[slot] = 0;
+    }
+    if (lane == 0) ncand[w] = 0;
+    __syncwarp();
+  }
+}
+
+// Randomised decisions, tiers 3 and 4: one block per node, the table in
+// shared memory (degree <= 1024) or in global scratch at goff[v].
+template <bool DENSE>
+__global__ void __launch_bounds__(256) k_ref_random_block(RefPolicy<DENSE> pol, const int32_t* list,
+                                                          const int32_t* count_ptr, RandParams rp, int32_t* gkeys,
+                                                          long long* gvals, ull* gwts, const int64_t* goff,
+                                                          unsigned* status, int in_global) {
+  constexpr int BITS = 11, SLOTS = 1 << BITS;
+  __shared__ int32_t hk[SLOTS];
+  __shared__ long long hv[SLOTS];
+  __shared__ ull hw[SLOTS];
+  __shared__ uint16_t cl[SLOTS / 2];
+  __shared__ int32_t ncand;
+  __shared__ u128 sm128[8];
+  if (!in_global) {
+    for (int i = threadIdx.x; i < SLOTS; i += 256) {
+      hk[i] = -1;
+      hv[i] = 0;
+    }
+    if (threadIdx.x == 0) ncand = 0;
+    __syncthreads();
+  }
+  const int count = *count_ptr;
+  for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
+    const int32_t v = list[idx];
+    if (!pol.begin(v)) {
+      if (threadIdx.x == 0) pol.skip(v);
+      continue;
+    }
+    const typename RefPolicy<DENSE>::VCtx vc = pol.vctx(v);
+    const int64_t beg = pol.g.rowptr[v], end = pol.g.rowptr[v + 1];
+    long long Wb;
+    int32_t X;
+    if (!in_global) {
+      const int bits = table_bits_for_degree(end - beg);
+      for (int64_t e = beg + threadIdx.x; e < end; e += 256) {
+        int32_t key;
+        long long wgt;
+        if (pol.edge(v, vc, e, key, wgt)) {
+          bool fresh;
+          const int slot = table_add_slot(hk, hv, bits, key, wgt, fresh);
+#if MSLICE_CHECKED
+          if (slot < 0) atomicOr(pol.g.chk, ERR_BOUNDS);
+#endif
+          if (fresh) cl[atomicAdd(&ncand, 1)] = (uint16_t)slot;
+        }
+      }
+      __syncthreads();
+      const int n = ncand;
+      X = rand_choose<RefPolicy<DENSE>, true>(pol, v, vc, rp, hk, hv, hw, cl, n, threadIdx.x, 256, sm128, Wb);
+      if (threadIdx.x == 0) pol.finish(v, Cand{0, X}, Wb, 0, vc);
+      __syncthreads();
+      for (int j = threadIdx.x; j < n; j += 256) {
+        const int slot = cl[j];
+        hk[slot] = -1;
+        hv[slot] = 0;
+      }
+      if (threadIdx.x == 0) ncand = 0;
+      __syncthreads();
+    } else {
+      const int bits = table_bits_for_degree(end - beg);
+      const int64_t S = 1ll << bits;
+      int32_t* K = gkeys + goff[v];
+      long long* V = gvals + goff[v];
+      ull* WT = gwts + goff[v];
+      for (int64_t i = threadIdx.x; i < S; i += 256) {
+        K[i] = -1;
+        V[i] = 0;
+      }
+      __syncthreads();
+      for (int64_t e = beg + threadIdx.x; e < end; e += 256) {
+        int32_t key;
+        long long wgt;
+        if (pol.edge(v, vc, e, key, wgt)) gtable_add(K, V, bits, key, wgt, status);
+      }
+      __syncthreads();
+      X = rand_choose<RefPolicy<DENSE>, true>(pol, v, vc, rp, K, V, WT, nullptr, S, threadIdx.x, 256, sm128, Wb);
+      if (threadIdx.x == 0) pol.finish(v, Cand{0, X}, Wb, 0, vc);
+      __syncthreads();
+    }
+  }
+}
 
 typedef TierSegs Segs3;
 
@@ -361,7 +689,18 @@ static void refine_impl(Solver& S, const Level& L, const int32_t* P, int it, int
            (const ull*)S.rhs, (const uint8_t*)S.elig, (const uint8_t*)S.cls, S.wc, desc);
     pol.q = q;
     const Segs3 sg = bucket_segments(S, q);
-    decide_all(c, pol, sg, S.tier_cnt, S.gkeys, S.gvals, S.goff);
+    if (S.p.theta_num > 0) {
+      const RandParams rp{S.p.seed, (uint64_t)it, (uint64_t)lvl, S.rdiv, (ull)S.p.theta_den};
+      for (int t = 0; t < 3; ++t)
+        if (S.tier_cnt[t] > 0)
+          launch(c, k_ref_random_warp<DENSE>, dim3(152 * 8), dim3(128), 0, pol, sg.list[t], sg.count[t], rp);
+      for (int t = 3; t < NTIERS; ++t)
+        if (S.tier_cnt[t] > 0)
+          launch(c, k_ref_random_block<DENSE>, dim3(152 * 4), dim3(256), 0, pol, sg.list[t], sg.count[t], rp,
+                 S.gkeys, S.gvals, S.gwts, (const int64_t*)S.goff, c.d_status, (int)(t == NTIERS - 1));
+    } else {
+      decide_all(c, pol, sg, S.tier_cnt, S.gkeys, S.gvals, S.goff);
+    }
     launch(c, k_ref_apply, dim3(fixed_grid(8)), dim3(256), 0, L.d, sg, P, (const int32_t*)S.target,
            (const long long*)S.Wc, (const long long*)S.Wsel, S.R, S.sizeR, S.Wout, S.kr, PR);
     launch(c, k_ref_reset, dim3(fixed_grid(4)), dim3(256), 0, sg, S.target);

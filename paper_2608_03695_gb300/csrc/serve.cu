@@ -276,6 +276,8 @@ void run_batch(mslice_server_s* s, Worker& slot, std::vector<SrvRequest*>& batch
     sp.n_iterations = s->opt.solve.n_iterations;
     sp.seed = s->opt.solve.seed;
     sp.global_null = s->null_model() == NULL_SUPRA_GLOBAL;
+    sp.theta_num = s->opt.solve.theta_num;
+    sp.theta_den = s->opt.solve.theta_den;
     sp.cpm = s->null_model() == NULL_CPM;
     for (int k = 0; k < 4; ++k)
       if (s->opt.solve.tier_cuts[0] || s->opt.solve.tier_cuts[1] || s->opt.solve.tier_cuts[2] ||
@@ -419,6 +421,8 @@ int mslice_server_create(const mslice_server_opts* o, mslice_server* out) {
     const mslice_opts& so = opt.solve;
     if (so.n_iterations < 1 || so.K < 1 || so.K > 64 || so.max_rounds < 1 || so.max_levels < 1)
       fail(MSLICE_EINVAL, "bad schedule options");
+    if (so.theta_num < 0 || so.theta_num > ((int64_t)1 << 31) || so.theta_den < 1 || so.theta_den > ((int64_t)1 << 31))
+      fail(MSLICE_EINVAL, "theta must be a rational >= 0");
     if ((so.flags & MSLICE_NULL_GLOBAL) && (so.flags & MSLICE_NULL_CPM))
       fail(MSLICE_EINVAL, "MSLICE_NULL_GLOBAL and MSLICE_NULL_CPM exclude each other");
     if (so.tier_cuts[0] || so.tier_cuts[1] || so.tier_cuts[2] || so.tier_cuts[3]) {

@@ -16,6 +16,7 @@ struct SolveParams {
   bool autotune = false;  // choose the cuts by timing round 0 of level 0
   bool global_null = false;  // plain modularity of the supra-graph instead of Q_MS
   bool cpm = false;          // the temporal Constant Potts Model instead of Q_MS
+  long long theta_num = 0, theta_den = 1;  // randomised refinement (theta_num = 0: greedy)
 };
 
 // Null models of a solve (the check_bounds argument).
@@ -47,6 +48,8 @@ struct Solver {
   // level-0 coupling entries that are edges
   long long* cw_d = nullptr;
   long long* gs_d = nullptr;
+  u128* rdiv = nullptr;     // randomised refinement: 2M * theta_num of every instance (2M = od * 2mu)
+  ull* gwts = nullptr;      // randomised refinement: weights beside gkeys/gvals
   std::vector<long long> cstr_h, csum_h, gs_h;
   std::vector<uint8_t> has_cw_h, has_gs_h;
   int64_t cpl_edges = 0;
