@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving", "large", "school"])
     ap.add_argument("--null", default="multislice", choices=["multislice", "global", "cpm"],
                     help="plain workload: Q_MS (default), the supra-graph's plain modularity, or temporal CPM")
+    ap.add_argument("--theta", default=None,
+                    help="plain workload: randomised refinement theta as num/den (default: the greedy limit)")
     ap.add_argument("--coupling", default="ordinal", choices=["ordinal", "categorical", "tables"],
                     help="plain workload: ordinal omega (default), categorical coupling of every snapshot pair, "
                          "or the general form's tables (per-pair omega, per-snapshot gamma)")
@@ -160,6 +162,9 @@ def gen_kwargs(args):
     """(build kwargs, solve kwargs shared by the library and the oracle) of the
     plain workload's model."""
     build, solve = {}, {"null": args.null}
+    if args.theta:
+        num, den = (args.theta.split("/") + ["1"])[:2]
+        solve["theta"] = (int(num), int(den))
     if args.coupling == "categorical":
         build["coupling"] = "categorical"
     elif args.coupling == "tables":
@@ -177,9 +182,11 @@ def oracle_kwargs(args):
 def workload(args):
     """The plain workload's config; the null model and coupling are named when
     they are not Q_MS with ordinal omega."""
-    if args.null == "multislice" and args.coupling == "ordinal":
+    if args.null == "multislice" and args.coupling == "ordinal" and not args.theta:
         return dict(WORKLOAD)
     c = dict(WORKLOAD)
+    if args.theta:
+        c.update(workload=c["workload"] + ", randomised refinement", theta=args.theta)
     if args.null != "multislice":
         what = {"global": "global null model (plain modularity of the supra-graph)",
                 "cpm": "temporal Constant Potts Model"}[args.null]
@@ -734,7 +741,7 @@ def main():
     peak, peak_kind = measured_peak()
     achieved = stp["decide_bytes"] / (stp["ms_decide"] / 1e3) / 1e9 if stp["ms_decide"] > 0 else 0.0
     # counters taken under Q_MS with ordinal omega only
-    traffic = decide_traffic() if args.null == "multislice" and args.coupling == "ordinal" else None
+    traffic = decide_traffic() if args.null == "multislice" and args.coupling == "ordinal" and not args.theta else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (traffic if traffic is None else traffic), "peak_source": peak_kind,
                 "kernel": "local-moving decision, level-0 sub-round (all degree tiers)",
