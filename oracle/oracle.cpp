@@ -563,7 +563,8 @@ std::vector<int32_t> refine(const Level& G, const Problem& p, const orc_opts& o,
         }
       }
       if (o.theta_num > 0) {
-        const u128 div = (u128)(uint64_t)p.twoM_all * (u128)(uint64_t)o.theta_num;
+        u128 div = (u128)(uint64_t)p.twoM_all * (u128)(uint64_t)o.theta_num;
+        if (div == 0) div = 1;  // no edges and no coupling: every key is 0
         const uint64_t td = (uint64_t)o.theta_den;
         u128 total = exp_weight((u128)Gbest, div, td);  // staying: key 0
         for (const auto& xc : cands) total += exp_weight((u128)(Gbest - xc.second), div, td);
