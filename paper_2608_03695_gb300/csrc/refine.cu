@@ -284,23 +284,58 @@ struct RefPolicy {
 constexpr ull LOG2E_Q32 = 6196328019ull;
 constexpr ull LN2_Q62 = 3196577161300663915ull;
 
+// (Every intermediate of the series fits 64 bits: g < 2^62 and each term is
+// at most 2^62, so the products are 64x64 -> 128 and the divisions 64-bit;
+// the values are those of the 128-bit statement above.)
+// floor(d / div) exactly: a double estimate corrected by exact products when
+// the quotient is below 2^50 (the estimate is then off by at most one), the
+// 128-bit division otherwise.
+__device__ __forceinline__ u128 udiv_exact(u128 d, u128 div) {
+  if (d < div) return 0;
+  const double qd = (double)d / (double)div;
+  if (qd < 1125899906842624.0) {  // 2^50
+    u128 q = (u128)(ull)qd;
+    while (q > 0 && q * div > d) --q;
+    while ((q + 1) * div <= d) ++q;
+    return q;
+  }
+  return d / div;
+}
+
+// floor(2^64 / k) for k = 2..40, computed by the compiler: floor(x / k) is
+// then the high product with it, corrected upward (by at most 2).
+struct SmallRecips {
+  ull r[41];
+  constexpr SmallRecips() : r() {
+    for (int k = 2; k <= 40; ++k) r[k] = ~0ull / (ull)k;
+  }
+};
+__device__ constexpr SmallRecips SMALL_RECIPS{};
+
+__device__ __forceinline__ ull div_small(ull x, int k) {
+  if (k == 1) return x;
+  ull q = __umul64hi(x, SMALL_RECIPS.r[k]);
+  while ((q + 1) * (ull)k <= x) ++q;
+  return q;
+}
+
 __device__ __forceinline__ ull rand_weight(u128 d, u128 div, ull td) {
-  const u128 Y = d / div;
+  const u128 Y = udiv_exact(d, div);
   if (Y >> 96) return 0;
   const u128 yF = (Y * (u128)td) >> 31;
   if (yF >= ((u128)64 << 32)) return 0;
   const u128 u = yF * (u128)LOG2E_Q32;
   const ull I = (ull)(u >> 64);
   if (I >= 40) return 0;
-  const u128 g = ((u128)(ull)u * (u128)LN2_Q62) >> 64;
-  u128 term = (u128)1 << 62;
-  i128 sum = (i128)term;
+  const ull g = (ull)(((u128)(ull)u * (u128)LN2_Q62) >> 64);
+  ull term = 1ull << 62;
+  long long sum = (long long)term;
   for (int k = 1; k <= 40; ++k) {
-    term = ((term * g) >> 62) / (u128)k;
+    term = div_small((ull)(((u128)term * (u128)g) >> 62), k);
     if (term == 0) break;
-    sum += (k & 1) ? -(i128)term : (i128)term;
+    sum += (k & 1) ? -(long long)term : (long long)term;
   }
-  return (ull)((u128)sum >> (22 + I));
+  return (ull)sum >> (22 + I);
 }
 
 struct RandParams {
@@ -332,15 +367,22 @@ __device__ __forceinline__ i128 warp_max_i128(i128 x) {
 template <class Pol, bool BLOCK>
 __device__ int32_t rand_choose(const Pol& pol, int32_t v, const typename Pol::VCtx& vc, const RandParams& rp,
                                const int32_t* K, const long long* V, ull* WT, const uint16_t* cand, int64_t n,
-                               int t, int nt, u128* sm128, long long& Wb) {
+                               int bits, int t, int nt, u128* sm128, long long& Wb) {
   const u128 div = rp.div[node_inst(pol.g, v)];
-  // pass 1: largest allowed key (staying: 0)
+  // pass 1: largest allowed key (staying: 0); with at most one candidate per
+  // thread its key is kept for pass 2
+  const bool one_each = n <= nt;
+  i128 G1 = 0;
+  bool ok1 = false;
   i128 gmax = 0;
   for (int64_t j = t; j < n; j += nt) {
     const int slot = cand ? cand[j] : (int)j;
     const int32_t X = K[slot];
-    i128 G;
-    if (X >= 0 && pol.rand_key(v, vc, X, V[slot], G) && G > gmax) gmax = G;
+    i128 G = 0;
+    const bool ok = X >= 0 && pol.rand_key(v, vc, X, V[slot], G);
+    if (ok && G > gmax) gmax = G;
+    G1 = G;
+    ok1 = ok;
   }
   gmax = warp_max_i128(gmax);
   if (BLOCK) {
@@ -356,9 +398,10 @@ __device__ int32_t rand_choose(const Pol& pol, int32_t v, const typename Pol::VC
   for (int64_t j = t; j < n; j += nt) {
     const int slot = cand ? cand[j] : (int)j;
     const int32_t X = K[slot];
-    i128 G;
+    i128 G = G1;
     ull w = 0;
-    if (X >= 0 && pol.rand_key(v, vc, X, V[slot], G)) w = rand_weight((u128)(gmax - G), div, rp.td);
+    if (one_each ? ok1 : (X >= 0 && pol.rand_key(v, vc, X, V[slot], G)))
+      w = rand_weight((u128)(gmax - G), div, rp.td);
     WT[slot] = w;
     part += w;
   }
@@ -381,10 +424,13 @@ __device__ int32_t rand_choose(const Pol& pol, int32_t v, const typename Pol::VC
     __syncthreads();
   }
   // pass 3: the candidate whose interval [cum, cum + w) holds thr, in
-  // ascending label order after staying
+  // ascending label order after staying.  Few candidates: each thread sums
+  // the weights of the smaller labels for its own candidates.  Many: a
+  // binary search for the smallest label L with wstay + sum_{label <= L} w
+  // > thr (about 31 team sums instead of n^2 work).
   int32_t chosen = INT32_MAX;
   long long wchosen = 0;
-  if (!(thr < wstay)) {
+  if (!(thr < wstay) && n <= 64) {
     for (int64_t j = t; j < n; j += nt) {
       const int slot = cand ? cand[j] : (int)j;
       const ull wj = WT[slot];
@@ -400,6 +446,34 @@ __device__ int32_t rand_choose(const Pol& pol, int32_t v, const typename Pol::VC
         chosen = X;
         wchosen = V[slot];
       }
+    }
+  } else if (!(thr < wstay)) {
+    int64_t lo = -1, hi = INT32_MAX;  // wstay + C(lo) <= thr < wstay + C(hi)
+    while (hi - lo > 1) {
+      const int64_t mid = lo + (hi - lo) / 2;
+      u128 c = 0;
+      for (int64_t j = t; j < n; j += nt) {
+        const int slot = cand ? cand[j] : (int)j;
+        const ull wj = WT[slot];
+        if (wj && K[slot] <= mid) c += wj;
+      }
+      c = warp_sum_u128(c);
+      if (BLOCK) {
+        if ((threadIdx.x & 31) == 0) sm128[threadIdx.x >> 5] = c;
+        __syncthreads();
+        c = 0;
+        for (int w = 0; w < (nt >> 5); ++w) c += sm128[w];
+        __syncthreads();
+      }
+      if (wstay + c > thr)
+        hi = mid;
+      else
+        lo = mid;
+    }
+    // hi is a candidate's label; thread 0 of the team reports it
+    if (t == 0) {
+      chosen = (int32_t)hi;
+      wchosen = table_get(K, V, bits, (int32_t)hi);
     }
   }
   // at most one thread holds the choice: hand it to every thread
@@ -472,7 +546,7 @@ __global__ void __launch_bounds__(128) k_ref_random_warp(RefPolicy<DENSE> pol, c
     __syncwarp();
     const int n = ncand[w];
     long long Wb;
-    const int32_t X = rand_choose<RefPolicy<DENSE>, false>(pol, v, vc, rp, K, V, WT, CL, n, lane, 32, nullptr, Wb);
+    const int32_t X = rand_choose<RefPolicy<DENSE>, false>(pol, v, vc, rp, K, V, WT, CL, n, BITS, lane, 32, nullptr, Wb);
     if (lane == 0) pol.finish(v, Cand{0, X}, Wb, 0, vc);
     __syncwarp();
     for (int j = lane; j < n; j += 32) {
@@ -534,7 +608,7 @@ __global__ void __launch_bounds__(256) k_ref_random_block(RefPolicy<DENSE> pol, 
       }
       __syncthreads();
       const int n = ncand;
-      X = rand_choose<RefPolicy<DENSE>, true>(pol, v, vc, rp, hk, hv, hw, cl, n, threadIdx.x, 256, sm128, Wb);
+      X = rand_choose<RefPolicy<DENSE>, true>(pol, v, vc, rp, hk, hv, hw, cl, n, bits, threadIdx.x, 256, sm128, Wb);
       if (threadIdx.x == 0) pol.finish(v, Cand{0, X}, Wb, 0, vc);
       __syncthreads();
       for (int j = threadIdx.x; j < n; j += 256) {
@@ -561,7 +635,8 @@ __global__ void __launch_bounds__(256) k_ref_random_block(RefPolicy<DENSE> pol, 
         if (pol.edge(v, vc, e, key, wgt)) gtable_add(K, V, bits, key, wgt, status);
       }
       __syncthreads();
-      X = rand_choose<RefPolicy<DENSE>, true>(pol, v, vc, rp, K, V, WT, nullptr, S, threadIdx.x, 256, sm128, Wb);
+      X = rand_choose<RefPolicy<DENSE>, true>(pol, v, vc, rp, K, V, WT, nullptr, S, bits, threadIdx.x, 256, sm128,
+                                              Wb);
       if (threadIdx.x == 0) pol.finish(v, Cand{0, X}, Wb, 0, vc);
       __syncthreads();
     }
