@@ -79,16 +79,26 @@ def test_refined_labels_at_a_stage(level):
         assert np.array_equal(g[0], o[0]), theta
 
 
-def test_star_choices_match_for_every_seed():
-    w = [3, 1, 4, 1, 5]
-    snaps = [synth.csr_from_edges(6, np.zeros(5, np.int64), np.arange(1, 6, dtype=np.int64),
-                                  np.array(w, np.int32))]
+# A star (leaves 3, 1, 4, 1, 5), a graph where node 0's target 1 has a key of
+# exactly 0 (2m = 32, gamma 1/2) and two disjoint stars: node 0's (and node
+# 6's) draw for every seed.
+CHOICE_GRAPHS = [
+    (6, [0, 0, 0, 0, 0], [1, 2, 3, 4, 5], [3, 1, 4, 1, 5], (1, 4)),
+    (6, [0, 0, 0, 1, 4], [1, 2, 3, 4, 5], [1, 3, 4, 7, 1], (1, 2)),
+    (12, [0] * 5 + [6] * 5, [1, 2, 3, 4, 5, 7, 8, 9, 10, 11], [3, 1, 4, 1, 5, 2, 6, 1, 3, 2], (1, 4)),
+]
+
+
+@pytest.mark.parametrize("graph", range(len(CHOICE_GRAPHS)))
+def test_small_choices_match_for_every_seed(graph):
+    n, u, v, w, gamma = CHOICE_GRAPHS[graph]
+    snaps = [synth.csr_from_edges(n, np.array(u, np.int64), np.array(v, np.int64), np.array(w, np.int32))]
     with pkg.mslice_build(snaps) as h:
         for seed in range(200):
-            kw = dict(K=2, seed=seed, init=np.zeros(6, np.int32), stop_level=0, stop_stage=2, stop_rounds=-1,
+            kw = dict(K=2, seed=seed, init=np.zeros(n, np.int32), stop_level=0, stop_stage=2, stop_rounds=-1,
                       theta=(1, 10))
-            lab, _, _ = h.mslice_leiden(gamma=(1, 4), **kw)
-            ref, _, _ = oracle.leiden(snaps, (1, 4), **kw)
+            lab, _, _ = h.mslice_leiden(gamma=gamma, **kw)
+            ref, _, _ = oracle.leiden(snaps, gamma, **kw)
             assert np.array_equal(lab, ref), seed
 
 

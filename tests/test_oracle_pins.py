@@ -1247,20 +1247,33 @@ def test_exp_weight_against_math(seed):
     assert oracle.exp_weight(1 << 126, 1, 1 << 31) == 0
 
 
-def test_randomised_choice_frequencies():
-    """Star: centre 0 with leaves of weights 3, 1, 4, 1, 5, all in one
-    community, no local moving, K = 2.  Over the seeds where the centre is
-    in class 0, its target is a class-1 leaf with probability proportional
-    to exp(dQ_i / theta) (staying: exp(0)); leaves of class 0 are active and
-    not targets."""
+# Two graphs for the choice frequencies, all nodes in one community, node 0
+# the centre.  STAR: leaves of weights 3, 1, 4, 1, 5, gamma 1/4.  ZERO_KEY:
+# 0-1 (1), 0-2 (3), 0-3 (4), 1-4 (7), 4-5 (1), gamma 1/2: 2m = 32 makes the
+# null coefficient exact and node 1's key exactly 0 (1 = 1/2 * 8 * 8 / 32),
+# so it must be drawn as often as staying (candidates have dQ >= 0).
+CHOICE_GRAPHS = {
+    "star": ([0, 0, 0, 0, 0], [1, 2, 3, 4, 5], [3, 1, 4, 1, 5], (1, 4)),
+    "zero_key": ([0, 0, 0, 1, 4], [1, 2, 3, 4, 5], [1, 3, 4, 7, 1], (1, 2)),
+}
+
+
+@pytest.mark.parametrize("graph", sorted(CHOICE_GRAPHS))
+def test_randomised_choice_frequencies(graph):
+    """No local moving, K = 2.  Over the seeds where the centre is in class
+    0, its target is a class-1 neighbour with probability proportional to
+    exp(dQ_i / theta) (staying: exp(0)); class-0 nodes are active in the
+    same sub-round and not targets.  Every singleton is well connected
+    (one community, gamma <= 1)."""
     stats = pytest.importorskip("scipy.stats")
-    w = [3, 1, 4, 1, 5]
-    u = np.zeros(5, np.int64)
-    v = np.arange(1, 6, dtype=np.int64)
-    snaps = [synth.csr_from_edges(6, u, v, np.array(w, np.int32))]
-    gamma, theta = (1, 4), (1, 10)
-    two_m = 2 * sum(w)
-    k0 = sum(w)
+    u, v, w, gamma = CHOICE_GRAPHS[graph]
+    snaps = [synth.csr_from_edges(6, np.array(u, np.int64), np.array(v, np.int64), np.array(w, np.int32))]
+    theta = (1, 10)
+    deg = np.zeros(6)
+    np.add.at(deg, u, w)
+    np.add.at(deg, v, w)
+    two_m = deg.sum()
+    w0 = {b: x for a, b, x in zip(u, v, w) if a == 0}
     obs = np.zeros(6)
     exp_ = np.zeros(6)
     for seed in range(6000):
@@ -1271,15 +1284,58 @@ def test_randomised_choice_frequencies():
         obs[lab[0]] += 1
         wts = np.zeros(6)
         wts[0] = 1.0
-        for i in range(1, 6):
+        for i, wi in w0.items():
             if py_class(seed, 1, 0, 0, 0, i, 2) == 1:
-                dq = 2 * (w[i - 1] - gamma[0] / gamma[1] * k0 * w[i - 1] / two_m) / two_m
+                dq = 2 * (wi - gamma[0] / gamma[1] * deg[0] * deg[i] / two_m) / two_m
+                assert dq >= 0
                 wts[i] = math.exp(dq * theta[1] / theta[0])
         exp_ += wts / wts.sum()
     assert obs.sum() > 2500 and abs(obs.sum() - exp_.sum()) < 1e-6
-    chi = stats.chisquare(obs, exp_)
+    pos = exp_ > 0
+    assert not obs[~pos].any()  # never a node that is not a neighbour of the centre
+    chi = stats.chisquare(obs[pos], exp_[pos])
     assert chi.pvalue > 1e-4, (obs, exp_, chi)
-    assert obs[5] > obs[3] > obs[1] > obs[0]  # heavier leaves are chosen more often
+    if graph == "star":
+        assert obs[5] > obs[3] > obs[1] > obs[0]  # heavier leaves are chosen more often
+    else:
+        assert obs[1] > 0.5 * exp_[1] > 50  # the key-0 target is a candidate
+
+
+def test_randomised_draws_independent_across_nodes():
+    """Two disjoint stars in one community (centres 0 and 6).  Over the seeds
+    where both centres are in class 0, the joint frequencies of their two
+    choices match the product of their per-seed probabilities: each node
+    draws its own random number."""
+    stats = pytest.importorskip("scipy.stats")
+    wa, wb = [3, 1, 4, 1, 5], [2, 6, 1, 3, 2]
+    u = np.array([0] * 5 + [6] * 5, np.int64)
+    v = np.array(list(range(1, 6)) + list(range(7, 12)), np.int64)
+    snaps = [synth.csr_from_edges(12, u, v, np.array(wa + wb, np.int32))]
+    gamma, theta = (1, 4), (1, 10)
+    two_m = 2 * (sum(wa) + sum(wb))
+
+    def probs(seed, centre, w):
+        k0 = sum(w)
+        p = np.zeros(6)
+        p[0] = 1.0
+        for i in range(1, 6):
+            if py_class(seed, 1, 0, 0, 0, centre + i, 2) == 1:
+                dq = 2 * (w[i - 1] - gamma[0] / gamma[1] * k0 * w[i - 1] / two_m) / two_m
+                p[i] = math.exp(dq * theta[1] / theta[0])
+        return p / p.sum()
+
+    obs = np.zeros((6, 6))
+    exp_ = np.zeros((6, 6))
+    for seed in range(16000):
+        if py_class(seed, 1, 0, 0, 0, 0, 2) != 0 or py_class(seed, 1, 0, 0, 0, 6, 2) != 0:
+            continue
+        lab, _, _ = oracle.leiden(snaps, gamma, (1, 1), K=2, seed=seed, init=np.zeros(12, np.int32), stop_level=0,
+                                  stop_stage=2, stop_rounds=-1, theta=theta)
+        obs[lab[0], lab[6] - 6] += 1
+        exp_ += np.outer(probs(seed, 0, wa), probs(seed, 6, wb))
+    assert obs.sum() > 3000
+    chi = stats.chisquare(obs.ravel(), exp_.ravel())
+    assert chi.pvalue > 1e-4, (obs, exp_, chi)
 
 
 def test_randomised_refinement_determinism_and_invariants():
