@@ -380,16 +380,35 @@ void set_instances(Ctx& c, Solver& S, const std::vector<InstParams>& jobs) {
   // randomised refinement: 2M theta_num of every instance
   S.rdiv = nullptr;
   if (S.p.theta_num > 0) {
-    std::vector<u128> rd(B);
+    std::vector<RandDiv> rd(B);
     for (int32_t i = 0; i < B; ++i) {
       const InstInfo& in = G.inst[i];
       long long sum2m = 0;
       for (int32_t s = in.soff; s < in.soff + in.T; ++s) sum2m += G.two_m_host[s];
-      rd[i] = (u128)(ull)(S.od_h[i] * sum2m + S.csum_h[i]) * (u128)(ull)S.p.theta_num;
-      if (rd[i] == 0) rd[i] = 1;  // an edgeless instance: every key is 0
+      u128 d = (u128)(ull)(S.od_h[i] * sum2m + S.csum_h[i]) * (u128)(ull)S.p.theta_num;
+      if (d == 0) d = 1;  // an edgeless instance: every key is 0
+      int L = 0;
+      while (L < 128 && (d >> L) != 0) ++L;
+      // R = floor(2^k / div) by binary long division (the remainder stays
+      // below 2 div < 2^93; the quotient below 2^64)
+      const int k = 62 + L;
+      u128 r = 0;
+      ull R = 0;
+      for (int b = k; b >= 0; --b) {
+        r = (r << 1) | (u128)(b == k ? 1 : 0);
+        R <<= 1;
+        if (r >= d) {
+          r -= d;
+          R |= 1;
+        }
+      }
+      rd[i].div = d;
+      rd[i].R = R;
+      rd[i].k = k;
+      rd[i].pad_ = 0;
     }
-    S.rdiv = c.ws->get<u128>("s_rdiv", B);
-    check_cuda(cudaMemcpyAsync(S.rdiv, rd.data(), B * sizeof(u128), cudaMemcpyHostToDevice, c.stream), "copy");
+    S.rdiv = c.ws->get<RandDiv>("s_rdiv", B);
+    check_cuda(cudaMemcpyAsync(S.rdiv, rd.data(), B * sizeof(RandDiv), cudaMemcpyHostToDevice, c.stream), "copy");
   }
   sync(c);  // hp, cw, gs and rd are pageable host memory
 }

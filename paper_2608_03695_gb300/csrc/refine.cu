@@ -287,19 +287,29 @@ constexpr ull LN2_Q62 = 3196577161300663915ull;
 // (Every intermediate of the series fits 64 bits: g < 2^62 and each term is
 // at most 2^62, so the products are 64x64 -> 128 and the divisions 64-bit;
 // the values are those of the 128-bit statement above.)
-// floor(d / div) exactly: a double estimate corrected by exact products when
-// the quotient is below 2^50 (the estimate is then off by at most one), the
-// 128-bit division otherwise.
-__device__ __forceinline__ u128 udiv_exact(u128 d, u128 div) {
-  if (d < div) return 0;
-  const double qd = (double)d / (double)div;
-  if (qd < 1125899906842624.0) {  // 2^50
-    u128 q = (u128)(ull)qd;
-    while (q > 0 && q * div > d) --q;
-    while ((q + 1) * div <= d) ++q;
-    return q;
+__device__ __forceinline__ int bitlen128(u128 x) {
+  const ull hi = (ull)(x >> 64);
+  return hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)(ull)x);
+}
+
+// floor(d / div) for d >= div, in integers: the top 64 bits of d times the
+// reciprocal R give an estimate q_est <= the quotient (both factors are
+// truncated) and, below 2^59, within 2 of it (relative errors 2^-63 and
+// 2^-62), corrected by subtracting div from the remainder.  A larger
+// estimate returns false with q_est in q (the caller then needs only to know
+// whether the quotient reaches 2^69, or divides exactly).
+__device__ __forceinline__ bool udiv_recip(u128 d, const RandDiv& rd, u128& q) {
+  const int ld = bitlen128(d);
+  const int sd = ld > 64 ? ld - 64 : 0;
+  const ull dt = (ull)(d >> sd);
+  q = ((u128)dt * (u128)rd.R) >> (rd.k - sd);  // k - sd <= 126 since d >= div
+  if (q >> 59) return false;
+  u128 r = d - q * rd.div;
+  while (r >= rd.div) {
+    r -= rd.div;
+    ++q;
   }
-  return d / div;
+  return true;
 }
 
 // floor(2^64 / k) for k = 2..40, computed by the compiler: floor(x / k) is
@@ -319,8 +329,13 @@ __device__ __forceinline__ ull div_small(ull x, int k) {
   return q;
 }
 
-__device__ __forceinline__ ull rand_weight(u128 d, u128 div, ull td) {
-  const u128 Y = udiv_exact(d, div);
+__device__ __forceinline__ ull rand_weight(u128 d, const RandDiv& rd, ull td) {
+  u128 Y = 0;
+  if (d >= rd.div && !udiv_recip(d, rd, Y)) {
+    // Y >= q_est >= 2^69 makes Y * theta_den / 2^31 >= 64 * 2^32: weight 0
+    if (Y >> 69) return 0;
+    Y = d / rd.div;
+  }
   if (Y >> 96) return 0;
   const u128 yF = (Y * (u128)td) >> 31;
   if (yF >= ((u128)64 << 32)) return 0;
@@ -340,42 +355,78 @@ __device__ __forceinline__ ull rand_weight(u128 d, u128 div, ull td) {
 
 struct RandParams {
   uint64_t seed, it, lvl;
-  const u128* div;  // 2M theta_num of every instance
-  ull td;           // theta_den
+  const RandDiv* div;  // 2M theta_num of every instance
+  ull td;              // theta_den
 };
 
-__device__ __forceinline__ i128 shfl_xor_i128(i128 x, int m) {
+__device__ __forceinline__ i128 shfl_xor_i128(i128 x, int m, unsigned mask) {
   ull lo = (ull)(u128)x, hi = (ull)((u128)x >> 64);
-  lo = __shfl_xor_sync(0xffffffffu, lo, m);
-  hi = __shfl_xor_sync(0xffffffffu, hi, m);
+  lo = __shfl_xor_sync(mask, lo, m);
+  hi = __shfl_xor_sync(mask, hi, m);
   return (i128)(((u128)hi << 64) | lo);
 }
 
-__device__ __forceinline__ i128 warp_max_i128(i128 x) {
+// Maximum / sum over a team of NT threads: a group of NT <= 32 aligned lanes
+// (mask: its lanes), or a block of NT threads through sm (one word per warp;
+// every thread gets the result; two barriers).
+template <int NT>
+__device__ __forceinline__ i128 team_max_i128(i128 x, unsigned mask, u128* sm) {
 #pragma unroll
-  for (int m = 16; m >= 1; m >>= 1) {
-    const i128 o = shfl_xor_i128(x, m);
+  for (int m = (NT < 32 ? NT : 32) / 2; m >= 1; m >>= 1) {
+    const i128 o = shfl_xor_i128(x, m, mask);
     if (o > x) x = o;
+  }
+  if constexpr (NT > 32) {
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = (u128)x;
+    __syncthreads();
+    x = 0;
+    for (int w = 0; w < NT / 32; ++w)
+      if ((i128)sm[w] > x) x = (i128)sm[w];
+    __syncthreads();
+  }
+  return x;
+}
+
+template <int NT>
+__device__ __forceinline__ u128 team_sum_u128(u128 x, unsigned mask, u128* sm) {
+  ull lo = (ull)x, hi = (ull)(x >> 64);
+#pragma unroll
+  for (int m = (NT < 32 ? NT : 32) / 2; m >= 1; m >>= 1) {
+    const ull l2 = __shfl_xor_sync(mask, lo, m), h2 = __shfl_xor_sync(mask, hi, m);
+    const ull nl = lo + l2;
+    hi += h2 + (nl < lo ? 1ull : 0ull);
+    lo = nl;
+  }
+  x = ((u128)hi << 64) | lo;
+  if constexpr (NT > 32) {
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = x;
+    __syncthreads();
+    x = 0;
+    for (int w = 0; w < NT / 32; ++w) x += sm[w];
+    __syncthreads();
   }
   return x;
 }
 
 // One node's randomised choice over the candidate keys listed in its table
-// (slots cand[0..n), or every slot when cand is null), by a team of `nt`
-// threads (a warp, or a block with sm scratch); returns the chosen label
-// (INT32_MAX: stay) and its weight W through Wb, valid on thread t == 0.
-template <class Pol, bool BLOCK>
+// (slots cand[0..n), or every slot when cand is null), by a team of NT
+// threads: t is the thread's rank in the team, base the team's first lane
+// (groups), mask its lanes; a block (NT > 32) uses sm (NT/32 + 1 words).
+// Returns the chosen label (INT32_MAX: stay) and its weight W through Wb,
+// on every thread of the team.
+template <class Pol, int NT>
 __device__ int32_t rand_choose(const Pol& pol, int32_t v, const typename Pol::VCtx& vc, const RandParams& rp,
                                const int32_t* K, const long long* V, ull* WT, const uint16_t* cand, int64_t n,
-                               int bits, int t, int nt, u128* sm128, long long& Wb) {
-  const u128 div = rp.div[node_inst(pol.g, v)];
+                               int bits, int t, int base, unsigned mask, u128* sm128, long long& Wb) {
+  constexpr bool BLOCK = NT > 32;
+  const RandDiv rd = rp.div[node_inst(pol.g, v)];
   // pass 1: largest allowed key (staying: 0); with at most one candidate per
   // thread its key is kept for pass 2
-  const bool one_each = n <= nt;
+  const bool one_each = n <= NT;
   i128 G1 = 0;
   bool ok1 = false;
   i128 gmax = 0;
-  for (int64_t j = t; j < n; j += nt) {
+  for (int64_t j = t; j < n; j += NT) {
     const int slot = cand ? cand[j] : (int)j;
     const int32_t X = K[slot];
     i128 G = 0;
@@ -384,38 +435,49 @@ __device__ int32_t rand_choose(const Pol& pol, int32_t v, const typename Pol::VC
     G1 = G;
     ok1 = ok;
   }
-  gmax = warp_max_i128(gmax);
-  if (BLOCK) {
-    if ((threadIdx.x & 31) == 0) sm128[threadIdx.x >> 5] = (u128)gmax;
-    __syncthreads();
-    gmax = 0;
-    for (int w = 0; w < (nt >> 5); ++w)
-      if ((i128)sm128[w] > gmax) gmax = (i128)sm128[w];
-    __syncthreads();
-  }
-  // pass 2: weights (0 for a slot that is not a candidate) and their total
+  gmax = team_max_i128<NT>(gmax, mask, sm128);
+  // pass 2: weights (0 for a slot that is not a candidate) and their total.
+  // With fewer candidates than threads, thread n weighs staying in the same
+  // pass (one weight evaluation per thread instead of two in a row).
   u128 part = 0;
-  for (int64_t j = t; j < n; j += nt) {
-    const int slot = cand ? cand[j] : (int)j;
-    const int32_t X = K[slot];
-    i128 G = G1;
-    ull w = 0;
-    if (one_each ? ok1 : (X >= 0 && pol.rand_key(v, vc, X, V[slot], G)))
-      w = rand_weight((u128)(gmax - G), div, rp.td);
-    WT[slot] = w;
-    part += w;
-  }
-  part = warp_sum_u128(part);
-  if (BLOCK) {
-    if ((threadIdx.x & 31) == 0) sm128[threadIdx.x >> 5] = part;
-    __syncthreads();
-    part = 0;
-    for (int w = 0; w < (nt >> 5); ++w) part += sm128[w];
-    __syncthreads();
+  ull wstay = 0;
+  const bool stay_lane = n < NT;
+  if (stay_lane) {
+    const int slot = t < n ? (cand ? cand[t] : t) : 0;
+    const bool has = t < n ? ok1 : t == n;
+    const u128 d = t < n ? (u128)(gmax - G1) : (u128)gmax;
+    const ull w = has ? rand_weight(d, rd, rp.td) : 0;
+    if (t < n) {
+      WT[slot] = w;
+      part = w;
+    }
+    if (BLOCK) {
+      if (t == n) sm128[NT / 32] = w;  // read after the first barrier of the sum below
+    } else {
+      wstay = __shfl_sync(mask, w, base + (int)n);
+    }
   } else {
-    __syncwarp();
+    for (int64_t j = t; j < n; j += NT) {
+      const int slot = cand ? cand[j] : (int)j;
+      const int32_t X = K[slot];
+      i128 G = G1;
+      ull w = 0;
+      if (one_each ? ok1 : (X >= 0 && pol.rand_key(v, vc, X, V[slot], G)))
+        w = rand_weight((u128)(gmax - G), rd, rp.td);
+      WT[slot] = w;
+      part += w;
+    }
   }
-  const ull wstay = rand_weight((u128)gmax, div, rp.td);
+  if (BLOCK && stay_lane) {
+    // team_sum_u128's barriers order the write above before this read
+    part = team_sum_u128<NT>(part, mask, sm128);
+    wstay = (ull)sm128[NT / 32];
+    __syncthreads();  // before a later node's write of the word
+  } else {
+    part = team_sum_u128<NT>(part, mask, sm128);
+    if (!BLOCK) __syncwarp(mask);  // WT written by the team
+  }
+  if (!stay_lane) wstay = rand_weight((u128)gmax, rd, rp.td);
   const u128 total = part + wstay;
   const ull R = class_hash(rp.seed, 2, rp.it, rp.lvl, 0, local_id(pol.g, v)) >> 32;
   const u128 thr = ((u128)R * total) >> 32;
@@ -431,7 +493,7 @@ __device__ int32_t rand_choose(const Pol& pol, int32_t v, const typename Pol::VC
   int32_t chosen = INT32_MAX;
   long long wchosen = 0;
   if (!(thr < wstay) && n <= 64) {
-    for (int64_t j = t; j < n; j += nt) {
+    for (int64_t j = t; j < n; j += NT) {
       const int slot = cand ? cand[j] : (int)j;
       const ull wj = WT[slot];
       if (wj == 0) continue;
@@ -452,25 +514,18 @@ __device__ int32_t rand_choose(const Pol& pol, int32_t v, const typename Pol::VC
     while (hi - lo > 1) {
       const int64_t mid = lo + (hi - lo) / 2;
       u128 c = 0;
-      for (int64_t j = t; j < n; j += nt) {
+      for (int64_t j = t; j < n; j += NT) {
         const int slot = cand ? cand[j] : (int)j;
         const ull wj = WT[slot];
         if (wj && K[slot] <= mid) c += wj;
       }
-      c = warp_sum_u128(c);
-      if (BLOCK) {
-        if ((threadIdx.x & 31) == 0) sm128[threadIdx.x >> 5] = c;
-        __syncthreads();
-        c = 0;
-        for (int w = 0; w < (nt >> 5); ++w) c += sm128[w];
-        __syncthreads();
-      }
+      c = team_sum_u128<NT>(c, mask, sm128);
       if (wstay + c > thr)
         hi = mid;
       else
         lo = mid;
     }
-    // hi is a candidate's label; thread 0 of the team reports it
+    // hi is a candidate's label; the team's first thread reports it
     if (t == 0) {
       chosen = (int32_t)hi;
       wchosen = table_get(K, V, bits, (int32_t)hi);
@@ -490,48 +545,56 @@ __device__ int32_t rand_choose(const Pol& pol, int32_t v, const typename Pol::VC
       wchosen = (long long)(ull)r;
     }
   } else {
-    const unsigned hit = __ballot_sync(0xffffffffu, chosen != INT32_MAX);
+    const unsigned hit = __ballot_sync(mask, chosen != INT32_MAX) & mask;
     if (hit) {
       const int src = __ffs(hit) - 1;
-      chosen = __shfl_sync(0xffffffffu, chosen, src);
-      wchosen = __shfl_sync(0xffffffffu, wchosen, src);
+      chosen = __shfl_sync(mask, chosen, src);
+      wchosen = __shfl_sync(mask, wchosen, src);
     }
   }
   Wb = wchosen;
   return chosen;
 }
 
-// Randomised decisions, degree tiers 0-2 (degree <= 256): one warp per node,
-// a 512-slot table per warp in shared memory.
-template <bool DENSE>
-__global__ void __launch_bounds__(128) k_ref_random_warp(RefPolicy<DENSE> pol, const int32_t* list,
-                                                         const int32_t* count_ptr, RandParams rp) {
-  constexpr int WARPS = 4, BITS = 9, SLOTS = 1 << BITS, MAXC = SLOTS / 2;
-  __shared__ int32_t hk[WARPS][SLOTS];
-  __shared__ long long hv[WARPS][SLOTS];
-  __shared__ ull hw[WARPS][SLOTS];
-  __shared__ uint16_t cl[WARPS][MAXC];
-  __shared__ int32_t ncand[WARPS];
+// Randomised decisions, degree tiers 0-2: G lanes per node, 2^BITS-slot
+// tables per group in shared memory, with the weights beside them; the
+// distinct target labels are listed as their slots are claimed, and only
+// those slots are reset.  THREADS keeps the static tables within 48 KB per
+// block.  All three tiers use a warp per node: most of a node's work is per
+// candidate (a probe and an integer exponential), which a warp spreads over
+// its lanes, and 4- or 8-lane groups were measured slower (refinement 74
+// against 57 ms per solve of the power-law workload at theta = 1/100).
+template <bool DENSE, int G, int BITS, int THREADS>
+__global__ void __launch_bounds__(THREADS, 512 / THREADS)
+    k_ref_random_groups(RefPolicy<DENSE> pol, const int32_t* list, const int32_t* count_ptr, RandParams rp) {
+  constexpr int GPW = 32 / G, NG = (THREADS / 32) * GPW, SLOTS = 1 << BITS, MAXC = SLOTS / 2;
+  __shared__ int32_t hk[NG][SLOTS];
+  __shared__ long long hv[NG][SLOTS];
+  __shared__ ull hw[NG][SLOTS];
+  __shared__ uint16_t cl[NG][MAXC];
+  __shared__ int32_t ncand[NG];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int32_t* K = hk[w];
-  long long* V = hv[w];
-  ull* WT = hw[w];
-  uint16_t* CL = cl[w];
-  for (int i = lane; i < SLOTS; i += 32) {
+  const int gl = lane % G, gi = lane / G, gx = w * GPW + gi;
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (gi * G));
+  int32_t* K = hk[gx];
+  long long* V = hv[gx];
+  ull* WT = hw[gx];
+  uint16_t* CL = cl[gx];
+  for (int i = gl; i < SLOTS; i += G) {
     K[i] = -1;
     V[i] = 0;
   }
-  if (lane == 0) ncand[w] = 0;
-  __syncwarp();
+  if (gl == 0) ncand[gx] = 0;
+  __syncwarp(gmask);
   const int count = *count_ptr;
-  for (int idx = blockIdx.x * WARPS + w; idx < count; idx += gridDim.x * WARPS) {
+  for (int idx = blockIdx.x * NG + gx; idx < count; idx += gridDim.x * NG) {
     const int32_t v = list[idx];
     if (!pol.begin(v)) {
-      if (lane == 0) pol.skip(v);
+      if (gl == 0) pol.skip(v);
       continue;
     }
     const typename RefPolicy<DENSE>::VCtx vc = pol.vctx(v);
-    for (int64_t e = pol.g.rowptr[v] + lane; e < pol.g.rowptr[v + 1]; e += 32) {
+    for (int64_t e = pol.g.rowptr[v] + gl; e < pol.g.rowptr[v + 1]; e += G) {
       int32_t key;
       long long wgt;
       if (pol.edge(v, vc, e, key, wgt)) {
@@ -540,22 +603,23 @@ __global__ void __launch_bounds__(128) k_ref_random_warp(RefPolicy<DENSE> pol, c
 #if MSLICE_CHECKED
         if (slot < 0) atomicOr(pol.g.chk, ERR_BOUNDS);
 #endif
-        if (fresh) CL[atomicAdd(&ncand[w], 1)] = (uint16_t)slot;
+        if (fresh) CL[atomicAdd(&ncand[gx], 1)] = (uint16_t)slot;
       }
     }
-    __syncwarp();
-    const int n = ncand[w];
+    __syncwarp(gmask);
+    const int n = ncand[gx];
     long long Wb;
-    const int32_t X = rand_choose<RefPolicy<DENSE>, false>(pol, v, vc, rp, K, V, WT, CL, n, BITS, lane, 32, nullptr, Wb);
-    if (lane == 0) pol.finish(v, Cand{0, X}, Wb, 0, vc);
-    __syncwarp();
-    for (int j = lane; j < n; j += 32) {
+    const int32_t X =
+        rand_choose<RefPolicy<DENSE>, G>(pol, v, vc, rp, K, V, WT, CL, n, BITS, gl, gi * G, gmask, nullptr, Wb);
+    if (gl == 0) pol.finish(v, Cand{0, X}, Wb, 0, vc);
+    __syncwarp(gmask);
+    for (int j = gl; j < n; j += G) {
       const int slot = CL[j];
       K[slot] = -1;
       V[slot] = 0;
     }
-    if (lane == 0) ncand[w] = 0;
-    __syncwarp();
+    if (gl == 0) ncand[gx] = 0;
+    __syncwarp(gmask);
   }
 }
 
@@ -572,7 +636,7 @@ __global__ void __launch_bounds__(256) k_ref_random_block(RefPolicy<DENSE> pol, 
   __shared__ ull hw[SLOTS];
   __shared__ uint16_t cl[SLOTS / 2];
   __shared__ int32_t ncand;
-  __shared__ u128 sm128[8];
+  __shared__ u128 sm128[9];  // 8 warp partials, then staying's weight
   if (!in_global) {
     for (int i = threadIdx.x; i < SLOTS; i += 256) {
       hk[i] = -1;
@@ -608,7 +672,8 @@ __global__ void __launch_bounds__(256) k_ref_random_block(RefPolicy<DENSE> pol, 
       }
       __syncthreads();
       const int n = ncand;
-      X = rand_choose<RefPolicy<DENSE>, true>(pol, v, vc, rp, hk, hv, hw, cl, n, bits, threadIdx.x, 256, sm128, Wb);
+      X = rand_choose<RefPolicy<DENSE>, 256>(pol, v, vc, rp, hk, hv, hw, cl, n, bits, threadIdx.x, 0, 0xffffffffu,
+                                             sm128, Wb);
       if (threadIdx.x == 0) pol.finish(v, Cand{0, X}, Wb, 0, vc);
       __syncthreads();
       for (int j = threadIdx.x; j < n; j += 256) {
@@ -635,8 +700,8 @@ __global__ void __launch_bounds__(256) k_ref_random_block(RefPolicy<DENSE> pol, 
         if (pol.edge(v, vc, e, key, wgt)) gtable_add(K, V, bits, key, wgt, status);
       }
       __syncthreads();
-      X = rand_choose<RefPolicy<DENSE>, true>(pol, v, vc, rp, K, V, WT, nullptr, S, bits, threadIdx.x, 256, sm128,
-                                              Wb);
+      X = rand_choose<RefPolicy<DENSE>, 256>(pol, v, vc, rp, K, V, WT, nullptr, S, bits, threadIdx.x, 0, 0xffffffffu,
+                                             sm128, Wb);
       if (threadIdx.x == 0) pol.finish(v, Cand{0, X}, Wb, 0, vc);
       __syncthreads();
     }
@@ -727,6 +792,50 @@ void bucket(Solver& S, const Level& L, uint64_t tag, int it, int lvl, int r, con
             const int32_t* r_dev = nullptr);
 TierSegs bucket_segments(Solver& S, int q);
 
+// Launches the randomised decisions of one sub-round: the tiers decide
+// disjoint nodes with separate scratch, so they run concurrently, heaviest
+// first, each on its own side stream (as the greedy tiers do).
+template <bool DENSE>
+static void random_all(Solver& S, const RefPolicy<DENSE>& pol, const TierSegs& sg, const RandParams& rp) {
+  Ctx& c = *S.c;
+  const int32_t* cnt = S.tier_cnt;
+  StreamFan* f = c.fan;
+  cudaStream_t st[NTIERS] = {c.stream, c.stream, c.stream, c.stream, c.stream};
+  bool used[StreamFan::kSide] = {false, false, false, false};
+  if (f) {
+    int busy = 0;
+    for (int t = 0; t < NTIERS; ++t) busy += cnt[t] > 0;
+    if (busy > 1) {
+      check_cuda(cudaEventRecord(f->fork, c.stream), "event");
+      for (int t = NTIERS - 1; t >= 1; --t)
+        if (cnt[t] > 0) {
+          const int k = NTIERS - 1 - t;
+          check_cuda(cudaStreamWaitEvent(f->side[k], f->fork, 0), "event");
+          st[t] = f->side[k];
+          used[k] = true;
+        }
+    }
+  }
+  for (int t = NTIERS - 1; t >= 3; --t)
+    if (cnt[t] > 0)
+      launch_on(c, st[t], k_ref_random_block<DENSE>, dim3(152 * 4), dim3(256), 0, pol, sg.list[t], sg.count[t], rp,
+                S.gkeys, S.gvals, S.gwts, (const int64_t*)S.goff, c.d_status, (int)(t == NTIERS - 1));
+  if (cnt[2] > 0)
+    launch_on(c, st[2], k_ref_random_groups<DENSE, 32, 9, 128>, dim3(152 * 8), dim3(128), 0, pol, sg.list[2],
+              sg.count[2], rp);
+  if (cnt[1] > 0)
+    launch_on(c, st[1], k_ref_random_groups<DENSE, 32, 9, 128>, dim3(152 * 8), dim3(128), 0, pol, sg.list[1],
+              sg.count[1], rp);
+  if (cnt[0] > 0)
+    launch_on(c, st[0], k_ref_random_groups<DENSE, 32, 9, 128>, dim3(152 * 8), dim3(128), 0, pol, sg.list[0],
+              sg.count[0], rp);
+  for (int k = 0; k < StreamFan::kSide; ++k)
+    if (used[k]) {
+      check_cuda(cudaEventRecord(f->join[k], f->side[k]), "event");
+      check_cuda(cudaStreamWaitEvent(c.stream, f->join[k], 0), "event");
+    }
+}
+
 template <bool DENSE>
 static void refine_impl(Solver& S, const Level& L, const int32_t* P, int it, int lvl) {
   Ctx& c = *S.c;
@@ -765,14 +874,7 @@ static void refine_impl(Solver& S, const Level& L, const int32_t* P, int it, int
     pol.q = q;
     const Segs3 sg = bucket_segments(S, q);
     if (S.p.theta_num > 0) {
-      const RandParams rp{S.p.seed, (uint64_t)it, (uint64_t)lvl, S.rdiv, (ull)S.p.theta_den};
-      for (int t = 0; t < 3; ++t)
-        if (S.tier_cnt[t] > 0)
-          launch(c, k_ref_random_warp<DENSE>, dim3(152 * 8), dim3(128), 0, pol, sg.list[t], sg.count[t], rp);
-      for (int t = 3; t < NTIERS; ++t)
-        if (S.tier_cnt[t] > 0)
-          launch(c, k_ref_random_block<DENSE>, dim3(152 * 4), dim3(256), 0, pol, sg.list[t], sg.count[t], rp,
-                 S.gkeys, S.gvals, S.gwts, (const int64_t*)S.goff, c.d_status, (int)(t == NTIERS - 1));
+      random_all<DENSE>(S, pol, sg, RandParams{S.p.seed, (uint64_t)it, (uint64_t)lvl, S.rdiv, (ull)S.p.theta_den});
     } else {
       decide_all(c, pol, sg, S.tier_cnt, S.gkeys, S.gvals, S.goff);
     }

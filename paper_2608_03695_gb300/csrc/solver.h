@@ -33,6 +33,17 @@ struct PhaseClock {
   void totals(double out[5]);  // total ms per phase
 };
 
+// Randomised refinement's divisor of one instance, div = 2M * theta_num
+// (1 <= div < 2^92), with a fixed-point reciprocal R = floor(2^k / div),
+// k = 62 + bitlen(div), so 2^62 < R <= 2^63 (an estimate only: every
+// quotient is corrected to the exact floor).
+struct RandDiv {
+  u128 div;
+  unsigned long long R;
+  int k;
+  int pad_;
+};
+
 struct Solver {
   Ctx* c = nullptr;
   const SupraGraph* G0 = nullptr;
@@ -48,7 +59,7 @@ struct Solver {
   // level-0 coupling entries that are edges
   long long* cw_d = nullptr;
   long long* gs_d = nullptr;
-  u128* rdiv = nullptr;     // randomised refinement: 2M * theta_num of every instance (2M = od * 2mu)
+  RandDiv* rdiv = nullptr;  // randomised refinement: 2M * theta_num of every instance (2M = od * 2mu)
   ull* gwts = nullptr;      // randomised refinement: weights beside gkeys/gvals
   std::vector<long long> cstr_h, csum_h, gs_h;
   std::vector<uint8_t> has_cw_h, has_gs_h;
