@@ -79,6 +79,45 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+class Ranks:
+    """The replicas' process group: one rank per GPU, each solving its own
+    copy of the workload, with no collective on the data path -- only the
+    barriers around the timed region and the reductions of the reported
+    numbers.  dist is torch.distributed (None for one rank); device is where
+    the reduction tensors live ("cuda" under NCCL, "cpu" under gloo)."""
+
+    def __init__(self, dist=None, device="cuda"):
+        self.dist = dist
+        self.device = device
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def _reduce(self, x, op):
+        if self.dist is None:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, x):
+        return self._reduce(x, None if self.dist is None else self.dist.ReduceOp.MAX)
+
+    def sum(self, x):
+        return self._reduce(x, None if self.dist is None else self.dist.ReduceOp.SUM)
+
+
+def replica_throughput(ranks, ms, units):
+    """Whole-job throughput of weak-scaled replicas: the units every rank
+    processed divided by the slowest rank's time (ms).  Returns (units per
+    second, slowest ms, total units)."""
+    ms_max = ranks.max(ms)
+    total = ranks.sum(units)
+    return total / (ms_max / 1e3), ms_max, total
+
+
 def measured_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -665,24 +704,8 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    ranks = Ranks(dist, "cuda")
+    barrier, max_over_ranks, sum_over_ranks = ranks.barrier, ranks.max, ranks.sum
 
     snaps = synth.recipe_graph("powerlaw_t16_n100k")
     stream = torch.cuda.Stream()
@@ -732,9 +755,7 @@ def main():
     barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    ms_max = max_over_ranks(ms)
-    total_edges = sum_over_ranks(edges)
-    value = total_edges / (ms_max / 1e3)
+    value, ms_max, total_edges = replica_throughput(ranks, ms, edges)
 
     # decision-kernel roofline from one profiled step (not part of the timed region)
     stp, _, _ = step_device(profile=True)
