@@ -2,7 +2,8 @@
 capacities tested on the hot paths, a violation reported as an error instead
 of accessed) on randomised small cases against the oracle, on the hashed
 tables, batched and served, under the other null models and general coupling,
-on a long sequence and windowed, and twice over for identical bits.  It runs in a
+on a long sequence and windowed, with randomised refinement, and twice over for
+identical bits.  It runs in a
 subprocess so that the checked library is the one loaded."""
 import os
 import subprocess
@@ -96,6 +97,33 @@ assert np.array_equal(lab, ref) and abs(Q - Qref) <= 1e-12 * max(1.0, abs(Qref))
 wl, wq, _ = pkg.leiden_windowed(long[:200], 24, 10)
 owl, owq, _ = oracle.leiden_windowed(long[:200], 24, 10)
 assert np.array_equal(wl, owl), "windowed"
+# randomised refinement (theta > 0): its group and block kernels, on random cases, hashed tables and a
+# graph with hubs of the block and global-table tiers
+for seed in range(6):
+    rng = np.random.default_rng(1300 + seed)
+    T, n = int(rng.integers(1, 5)), int(rng.integers(4, 60))
+    snaps, _ = synth.planted_partition_temporal(max(n, 8), T, 3, 0.3, 0.03, 0.1, None, 4, seed)
+    theta = [(1, 10), (1, 1000), (2, 1)][seed % 3]
+    if seed % 2:
+        os.environ["MSLICE_DENSE_LIMIT"] = "0"
+    with pkg.mslice_build(snaps) as h:
+        lab, Q, _ = h.mslice_leiden(theta=theta, seed=seed)
+    os.environ.pop("MSLICE_DENSE_LIMIT", None)
+    ref, Qref, _ = oracle.leiden(snaps, theta=theta, seed=seed)
+    assert np.array_equal(lab, ref) and abs(Q - Qref) <= 1e-12 * max(1.0, abs(Qref)), ("theta", seed)
+rng = np.random.default_rng(31)
+nh = 2500
+u = np.concatenate([np.zeros(1200, np.int64), np.ones(300, np.int64), rng.integers(2, nh, 6000)])
+v = np.concatenate([rng.choice(np.arange(2, nh), 1200, replace=False), rng.choice(np.arange(2, nh), 300, replace=False),
+                    rng.integers(2, nh, 6000)])
+key = np.unique(np.minimum(u, v) * nh + np.maximum(u, v))
+u, v = key // nh, key % nh
+u, v = u[u != v], v[u != v]
+hubs = [synth.csr_from_edges(nh, u, v, rng.integers(1, 5, size=len(u))) for _ in range(2)]
+with pkg.mslice_build(hubs) as h:
+    lab, Q, _ = h.mslice_leiden(theta=(1, 100), omega=(1, 2))
+ref, Qref, _ = oracle.leiden(hubs, (1, 1), (1, 2), theta=(1, 100))
+assert np.array_equal(lab, ref), "theta hubs"
 print("checked ok")
 '''
 
