@@ -284,9 +284,6 @@ struct RefPolicy {
 constexpr ull LOG2E_Q32 = 6196328019ull;
 constexpr ull LN2_Q62 = 3196577161300663915ull;
 
-// (Every intermediate of the series fits 64 bits: g < 2^62 and each term is
-// at most 2^62, so the products are 64x64 -> 128 and the divisions 64-bit;
-// the values are those of the 128-bit statement above.)
 __device__ __forceinline__ int bitlen128(u128 x) {
   const ull hi = (ull)(x >> 64);
   return hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)(ull)x);
@@ -312,8 +309,8 @@ __device__ __forceinline__ bool udiv_recip(u128 d, const RandDiv& rd, u128& q) {
   return true;
 }
 
-// floor(2^64 / k) for k = 2..40, computed by the compiler: floor(x / k) is
-// then the high product with it, corrected upward (by at most 2).
+// floor((2^64 - 1) / k) for k = 2..40, computed by the compiler: floor(x / k)
+// is then the high product with it, corrected upward (by at most 2).
 struct SmallRecips {
   ull r[41];
   constexpr SmallRecips() : r() {
@@ -329,6 +326,10 @@ __device__ __forceinline__ ull div_small(ull x, int k) {
   return q;
 }
 
+// The weight of a key difference d.  (Every intermediate of the series fits
+// 64 bits: g < 2^62 and each term is at most 2^62, so the products are
+// 64x64 -> 128 and the divisions 64-bit; the values are those of the 128-bit
+// statement above.)
 __device__ __forceinline__ ull rand_weight(u128 d, const RandDiv& rd, ull td) {
   u128 Y = 0;
   if (d >= rd.div && !udiv_recip(d, rd, Y)) {
