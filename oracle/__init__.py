@@ -72,6 +72,13 @@ class _Gen:
         return C.byref(self.struct) if self.struct is not None else None
 
 
+class _LevelOut(C.Structure):
+    _fields_ = [("N", C.c_int64), ("nnz", C.c_int64), ("ns", C.c_int64), ("cap_N", C.c_int64),
+                ("cap_nnz", C.c_int64), ("cap_ns", C.c_int64), ("rowptr", C.c_void_p), ("col", C.c_void_p),
+                ("W", C.c_void_p), ("sptr", C.c_void_p), ("sidx", C.c_void_p), ("sval", C.c_void_p),
+                ("init_labels", C.c_void_p), ("node_map", C.c_void_p)]
+
+
 class _Stats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("levels", C.c_int32), ("lm_rounds", C.c_int64),
                 ("lm_edges", C.c_int64), ("lm_moves", C.c_int64), ("last_level0_moves", C.c_int64),
@@ -108,6 +115,9 @@ def lib():
         L.orc_lambda.argtypes = [P, C.c_int32, C.c_int64, C.c_int64, P, P]
         L.orc_count_improving.argtypes = [P, C.c_int32, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
                                           P, P]
+        L.orc_aggregate.argtypes = [P, C.c_int32, C.c_int64, C.c_int64, C.c_int32, P, P, P, P]
+        L.orc_level_key.argtypes = [P, C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int32, P, P, P,
+                                    P, C.c_int64, C.c_int64, P]
         L.orc_exp_weight.argtypes = [C.c_uint64] * 5
         L.orc_exp_weight.restype = C.c_uint64
         L.orc_mix64.argtypes = [C.c_uint64]
@@ -216,6 +226,88 @@ def count_improving(snaps, labels, gamma=(1, 1), omega=(1, 1), null="multislice"
     _check(lib().orc_count_improving(S.ptr, S.T, _ptr(lab), gamma[0], gamma[1], omega[0], omega[1], _null(null),
                                      gen.ptr, C.byref(cnt)), "orc_count_improving")
     return cnt.value
+
+
+def aggregate(snaps, P, R, omega=(1, 1), null="multislice", coupling="ordinal", omegas=None):
+    """One aggregation step of the level-0 supra-graph for the local-moving
+    partition P and its refinement R.  Returns a dict: N, rows (per new node a
+    list of (column, W) pairs, W in units of 1/omega[1]), slices (per new node
+    a list of (snapshot, strength) pairs), init (initial labels of the new
+    level) and map (new id of every level-0 node)."""
+    S = _Slices(snaps)
+    Pa = np.ascontiguousarray(P, dtype=np.int32)
+    Ra = np.ascontiguousarray(R, dtype=np.int32)
+    gen = _Gen(coupling, omegas, None)
+    out = _LevelOut()
+    _check(lib().orc_aggregate(S.ptr, S.T, omega[0], omega[1], _null(null), gen.ptr, _ptr(Pa), _ptr(Ra),
+                               C.byref(out)), "orc_aggregate")
+    N, nnz, ns = out.N, out.nnz, out.ns
+    rowptr = np.zeros(N + 1, np.int64)
+    col = np.zeros(max(nnz, 1), np.int32)
+    W = np.zeros(max(nnz, 1), np.int64)
+    sptr = np.zeros(N + 1, np.int64)
+    sidx = np.zeros(max(ns, 1), np.int32)
+    sval = np.zeros(max(ns, 1), np.int64)
+    init = np.zeros(max(N, 1), np.int32)
+    mp = np.zeros(max(S.N, 1), np.int32)
+    out.cap_N, out.cap_nnz, out.cap_ns = N, nnz, ns
+    for f, a in [("rowptr", rowptr), ("col", col), ("W", W), ("sptr", sptr), ("sidx", sidx), ("sval", sval),
+                 ("init_labels", init), ("node_map", mp)]:
+        setattr(out, f, _ptr(a))
+    _check(lib().orc_aggregate(S.ptr, S.T, omega[0], omega[1], _null(null), gen.ptr, _ptr(Pa), _ptr(Ra),
+                               C.byref(out)), "orc_aggregate")
+    rows = [[(int(col[e]), int(W[e])) for e in range(rowptr[x], rowptr[x + 1])] for x in range(N)]
+    slices = [[(int(sidx[j]), int(sval[j])) for j in range(sptr[x], sptr[x + 1])] for x in range(N)]
+    return {"N": N, "rows": rows, "slices": slices, "init": init[:N].tolist(), "map": mp[:S.N].tolist()}
+
+
+def level_key(snaps, P, R, labels1, x, c, gamma=(1, 1), omega=(1, 1), null="multislice", coupling="ordinal",
+              omegas=None, gammas=None) -> int:
+    """Key G(x, c) at the level aggregated from (P, R), under that level's
+    labels labels1 (c = -1: an empty community)."""
+    S = _Slices(snaps)
+    Pa = np.ascontiguousarray(P, dtype=np.int32)
+    Ra = np.ascontiguousarray(R, dtype=np.int32)
+    La = np.ascontiguousarray(labels1, dtype=np.int32)
+    out = (C.c_uint64 * 2)()
+    gen = _Gen(coupling, omegas, gammas)
+    _check(lib().orc_level_key(S.ptr, S.T, gamma[0], gamma[1], omega[0], omega[1], _null(null), gen.ptr, _ptr(Pa),
+                               _ptr(Ra), _ptr(La), x, c, out), "orc_level_key")
+    v = out[0] | (out[1] << 64)
+    return v - (1 << 128) if v >> 127 else v
+
+
+def serve_warm_start(prev, n, W):
+    """Initial labels of the next served window (the serving rule; the paper
+    names windowed optimisation, Sec. 4, without a procedure): with w_prev
+    slices in the previous result and e = 1 when the window already held W
+    slices (the oldest is evicted), supra-node (j, i) of the new window of
+    min(w_prev + 1, W) slices starts with the previous label of
+    (min(j + e, w_prev - 1), i): surviving slices keep their labels and the
+    new slice copies the previous newest one.  None (the first snapshot):
+    singletons."""
+    if prev is None:
+        return None
+    prev = np.asarray(prev)
+    w_prev = len(prev) // n
+    e = 1 if w_prev == W else 0
+    w_new = min(w_prev + 1, W)
+    src = np.minimum(np.arange(w_new) + e, w_prev - 1)
+    return np.concatenate([prev[s * n:(s + 1) * n] for s in src]).astype(np.int32)
+
+
+def serve_chain(stream, W, gamma=(1, 1), omega=(1, 1), **kw):
+    """What a server computes for one live graph: request t solves the window
+    of the last min(t + 1, W) snapshots, warm-started by serve_warm_start from
+    the previous request's labels.  Returns [(labels, Q), ...] per request."""
+    n = stream[0].n
+    prev, out = None, []
+    for t in range(len(stream)):
+        window = stream[max(0, t + 1 - W):t + 1]
+        lab, Q, _ = leiden(window, gamma, omega, init=serve_warm_start(prev, n, W), **kw)
+        out.append((lab, Q))
+        prev = lab
+    return out
 
 
 def exp_weight(d: int, div: int, theta_den: int) -> int:

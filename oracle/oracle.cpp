@@ -763,6 +763,34 @@ double modularity_of(const orc_csr* slices, const Problem& p, const std::vector<
   return num / twomu;
 }
 
+// Key G(v, c) of node v of a level for community c under `labels` (c = -1:
+// an empty community, key 0): the key of Eq. multislice-modularity's gain
+// as stated above `key`, with W(v, c\v) summed over v's entries (a level has
+// no self-loops) and Sigma_{c\v,s} over the other members of c.
+i128 level_key(const Level& G, const Problem& p, const int32_t* labels, int64_t v, int64_t c) {
+  if (c < 0) return 0;
+  int64_t W = 0;
+  for (const auto& uw : G.adj[v])
+    if (labels[uw.first] == c) W += uw.second;
+  SliceMap sig;
+  for (int64_t u = 0; u < G.N; ++u)
+    if (labels[u] == c && u != v)
+      for (const auto& sk : G.kvec[u]) sig[sk.first] += sk.second;
+  return key(p, W, null_sum(p, G.kvec[v], [&](int32_t s) { return sig.count(s) ? sig[s] : 0; }));
+}
+
+// A local-moving partition P and a refinement R of it (labels in [0, N),
+// every R-community inside one P-community), as aggregation takes them.
+int check_partitions(int64_t N, const int32_t* P, const int32_t* R) {
+  std::vector<int32_t> parent(N, -1);
+  for (int64_t v = 0; v < N; ++v) {
+    if (P[v] < 0 || P[v] >= N || R[v] < 0 || R[v] >= N) return ORC_EINVAL;
+    if (parent[R[v]] >= 0 && parent[R[v]] != P[v]) return ORC_EINVAL;
+    parent[R[v]] = P[v];
+  }
+  return ORC_OK;
+}
+
 int setup(const orc_csr* slices, int32_t T, int64_t gn, int64_t gd, int64_t on, int64_t od, Problem& p,
           int32_t null_model, const orc_general* gen) {
   int rc = validate(slices, T);
@@ -841,17 +869,64 @@ int orc_move_key(const orc_csr* slices, int32_t T, const int32_t* labels, int64_
   if (rc) return rc;
   Level G = build_level0(slices, p);
   if (v < 0 || v >= G.N) return ORC_EINVAL;
-  i128 Gk = 0;
-  if (c >= 0) {
-    int64_t W = 0;
-    for (const auto& uw : G.adj[v])
-      if (labels[uw.first] == c) W += uw.second;
-    SliceMap sig;
-    for (int64_t u = 0; u < G.N; ++u)
-      if (labels[u] == c && u != v)
-        for (const auto& sk : G.kvec[u]) sig[sk.first] += sk.second;
-    Gk = key(p, W, null_sum(p, G.kvec[v], [&](int32_t s) { return sig.count(s) ? sig[s] : 0; }));
+  const i128 Gk = level_key(G, p, labels, v, c);
+  out[0] = (uint64_t)(u128)Gk;
+  out[1] = (uint64_t)((u128)Gk >> 64);
+  return ORC_OK;
+}
+
+int orc_aggregate(const orc_csr* slices, int32_t T, int64_t on, int64_t od, int32_t null_model,
+                  const orc_general* gen, const int32_t* P, const int32_t* R, orc_level_out* out) {
+  Problem p;
+  int rc = setup(slices, T, 1, 1, on, od, p, null_model, gen);
+  if (rc) return rc;
+  const Level G = build_level0(slices, p);
+  rc = check_partitions(G.N, P, R);
+  if (rc) return rc;
+  std::vector<int32_t> Pv(P, P + G.N), Rv(R, R + G.N), nl, mp;
+  const Level H = aggregate(G, Pv, Rv, nl, mp);
+  int64_t ns = 0;
+  for (const auto& kv : H.kvec) ns += (int64_t)kv.size();
+  out->N = H.N;
+  out->nnz = H.nnz();
+  out->ns = ns;
+  if (!out->rowptr) return ORC_OK;  // sizes only
+  if (out->cap_N < H.N || out->cap_nnz < out->nnz || out->cap_ns < ns) return ORC_EINVAL;
+  int64_t e = 0, j = 0;
+  for (int64_t x = 0; x < H.N; ++x) {
+    out->rowptr[x] = e;
+    out->sptr[x] = j;
+    for (const auto& yw : H.adj[x]) {
+      out->col[e] = yw.first;
+      out->W[e++] = yw.second;
+    }
+    for (const auto& sk : H.kvec[x]) {
+      out->sidx[j] = sk.first;
+      out->sval[j++] = sk.second;
+    }
+    out->init_labels[x] = nl[x];
   }
+  out->rowptr[H.N] = e;
+  out->sptr[H.N] = j;
+  std::copy(mp.begin(), mp.end(), out->node_map);
+  return ORC_OK;
+}
+
+int orc_level_key(const orc_csr* slices, int32_t T, int64_t gn, int64_t gd, int64_t on, int64_t od,
+                  int32_t null_model, const orc_general* gen, const int32_t* P, const int32_t* R,
+                  const int32_t* labels1, int64_t x, int64_t c, uint64_t out[2]) {
+  Problem p;
+  int rc = setup(slices, T, gn, gd, on, od, p, null_model, gen);
+  if (rc) return rc;
+  const Level G = build_level0(slices, p);
+  rc = check_partitions(G.N, P, R);
+  if (rc) return rc;
+  std::vector<int32_t> Pv(P, P + G.N), Rv(R, R + G.N), nl, mp;
+  const Level H = aggregate(G, Pv, Rv, nl, mp);
+  if (x < 0 || x >= H.N || c >= H.N) return ORC_EINVAL;
+  for (int64_t y = 0; y < H.N; ++y)
+    if (labels1[y] < 0 || labels1[y] >= H.N) return ORC_EINVAL;
+  const i128 Gk = level_key(H, p, labels1, x, c);
   out[0] = (uint64_t)(u128)Gk;
   out[1] = (uint64_t)((u128)Gk >> 64);
   return ORC_OK;

@@ -166,6 +166,39 @@ int orc_count_improving(const orc_csr* slices, int32_t T, const int32_t* labels,
                         int64_t gamma_den, int64_t omega_num, int64_t omega_den, int32_t null_model,
                         const orc_general* gen, int64_t* count);
 
+/* One aggregation step (Leiden, Sec. 3.2; the aggregation reading: new ids
+ * rank the refined labels ascending, self-loops are dropped, slice strengths
+ * are summed, and a new node starts in the smallest new id of its
+ * local-moving community), exposed for the tests.  The caller gives the
+ * level-0 local-moving partition P and a refinement R of it (labels in
+ * [0, N), every R-community inside one P-community; EINVAL otherwise).
+ * Written: N, nnz (directed entries) and ns (slice entries) always; the
+ * arrays only when rowptr is non-null and the capacities suffice (EINVAL
+ * when they do not).  Rows list columns ascending with W in units of 1/od;
+ * slice lists are ascending (snapshot, strength) pairs. */
+typedef struct {
+  int64_t N, nnz, ns;              /* sizes of the aggregated level (out) */
+  int64_t cap_N, cap_nnz, cap_ns;  /* capacities of the arrays below (in) */
+  int64_t* rowptr;                 /* N + 1 */
+  int32_t* col;                    /* nnz */
+  int64_t* W;                      /* nnz */
+  int64_t* sptr;                   /* N + 1 */
+  int32_t* sidx;                   /* ns */
+  int64_t* sval;                   /* ns */
+  int32_t* init_labels;            /* N: initial labels of the new level */
+  int32_t* node_map;               /* level-0 node count: new id of every level-0 node */
+} orc_level_out;
+
+int orc_aggregate(const orc_csr* slices, int32_t T, int64_t omega_num, int64_t omega_den, int32_t null_model,
+                  const orc_general* gen, const int32_t* P, const int32_t* R, orc_level_out* out);
+
+/* Key G(x, c) at the level that aggregating (P, R) produces, under the
+ * labels labels1 of that level (c = -1: an empty community), as a signed
+ * 128-bit integer in out[0] (low) / out[1] (high). */
+int orc_level_key(const orc_csr* slices, int32_t T, int64_t gamma_num, int64_t gamma_den, int64_t omega_num,
+                  int64_t omega_den, int32_t null_model, const orc_general* gen, const int32_t* P,
+                  const int32_t* R, const int32_t* labels1, int64_t x, int64_t c, uint64_t out[2]);
+
 /* The counter-based hash used to draw vertex classes (SplitMix64 finaliser). */
 uint64_t orc_mix64(uint64_t x);
 

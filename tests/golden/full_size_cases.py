@@ -48,19 +48,6 @@ def digest_labels(labels) -> str:
     return digest_arrays([np.asarray(labels, dtype=np.int32)])
 
 
-def warm_start(prev, n, W):
-    """Initial labels of the next window (the serving rule): (j, i) takes the
-    previous label of (min(j + e, w_prev - 1), i), e = 1 when a slice is
-    evicted."""
-    if prev is None:
-        return None
-    w_prev = len(prev) // n
-    e = 1 if w_prev == W else 0
-    w_new = min(w_prev + 1, W)
-    src = np.minimum(np.arange(w_new) + e, w_prev - 1)
-    return np.concatenate([prev[s * n:(s + 1) * n] for s in src]).astype(np.int32)
-
-
 def cases():
     """name -> (builder returning a list of solves).  A solve is a dict with
     snaps, gamma, omega and optional init."""
@@ -121,13 +108,7 @@ def cases():
 def run_solve(oracle, s):
     if "stream" in s:  # a serving chain: one result per request
         stream, W = s["stream"], s["W"]
-        n = stream[0].n
-        prev, res = None, []
-        for t in range(len(stream)):
-            window = stream[max(0, t + 1 - W):t + 1]
-            lab, Q, _ = oracle.leiden(window, init=warm_start(prev, n, W))
-            res.append({"labels": digest_labels(lab), "Q": repr(Q)})
-            prev = lab
+        res = [{"labels": digest_labels(lab), "Q": repr(Q)} for lab, Q in oracle.serve_chain(stream, W)]
         return {"input": digest_snaps(stream), "chain": res}
     if "W" in s:  # windowed optimisation: stitched labels and every window's Q
         lab, Qs, nw = oracle.leiden_windowed(s["snaps"], s["W"], s["stride"])

@@ -21,9 +21,11 @@ CASES = r'''
 import os, sys
 import numpy as np
 sys.path.insert(0, ROOT)
+sys.path.insert(0, os.path.join(ROOT, "tests"))
 import oracle
 import paper_2608_03695_gb300 as pkg
 from paper_2608_03695_gb300 import synth
+from qtol import q_close
 assert pkg.LIB_PATH.endswith("libmslice_checked.so")
 oracle.build()
 for seed in range(16):
@@ -43,7 +45,7 @@ for seed in range(16):
     os.environ.pop("MSLICE_DENSE_LIMIT", None)
     ref, Qref, _ = oracle.leiden(snaps, gamma, omega, K=1 + seed % 4, seed=seed)
     assert np.array_equal(lab, ref) and np.array_equal(lab2, lab) and Q2 == Q, seed
-    assert abs(Q - Qref) <= 1e-12 * max(1.0, abs(Qref)), seed
+    assert q_close(Q, Qref), seed
 snaps = synth.recipe_graph({**synth.RECIPES["powerlaw_t16_n100k"], "n": 3000, "T": 4})
 with pkg.mslice_build(snaps) as h, pkg.Batch() as b:
     for gm in [(1, 1), (3, 2), (1, 2)]:
@@ -88,12 +90,12 @@ for seed in range(8):
     ref, Qref, _ = oracle.leiden(snaps, gamma, (1, 2), coupling=coupling, omegas=omegas, gammas=gammas, null=null,
                                  seed=seed)
     assert np.array_equal(lab, ref), ("general", seed)
-    assert abs(Q - Qref) <= 1e-12 * max(1.0, abs(Qref)), ("general", seed)
+    assert q_close(Q, Qref), ("general", seed)
 long = synth.recipe_graph("school_t7375_n327", T=600)
 with pkg.mslice_build(long) as h:
     lab, Q, _ = h.mslice_leiden()
 ref, Qref, _ = oracle.leiden(long)
-assert np.array_equal(lab, ref) and abs(Q - Qref) <= 1e-12 * max(1.0, abs(Qref)), "long"
+assert np.array_equal(lab, ref) and q_close(Q, Qref), "long"
 wl, wq, _ = pkg.leiden_windowed(long[:200], 24, 10)
 owl, owq, _ = oracle.leiden_windowed(long[:200], 24, 10)
 assert np.array_equal(wl, owl), "windowed"
@@ -110,7 +112,7 @@ for seed in range(6):
         lab, Q, _ = h.mslice_leiden(theta=theta, seed=seed)
     os.environ.pop("MSLICE_DENSE_LIMIT", None)
     ref, Qref, _ = oracle.leiden(snaps, theta=theta, seed=seed)
-    assert np.array_equal(lab, ref) and abs(Q - Qref) <= 1e-12 * max(1.0, abs(Qref)), ("theta", seed)
+    assert np.array_equal(lab, ref) and q_close(Q, Qref), ("theta", seed)
 rng = np.random.default_rng(31)
 nh = 2500
 u = np.concatenate([np.zeros(1200, np.int64), np.ones(300, np.int64), rng.integers(2, nh, 6000)])

@@ -29,10 +29,9 @@ import paper_2608_03695_gb300 as pkg
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.join(HERE, "golden"))
 import full_size_cases as fsc  # noqa: E402
+from qtol import q_close
 
 pytestmark = pytest.mark.gpu
-
-QTOL = 1e-12
 
 
 def _cuda():
@@ -63,7 +62,7 @@ def expected(name, solves):
 
 def q_ok(q, ref):
     ref = float(ref)
-    return abs(q - ref) <= QTOL * max(1.0, abs(ref))
+    return q_close(q, ref)
 
 
 def test_power_law_full_size():

@@ -15,10 +15,9 @@ import pytest
 import oracle
 import paper_2608_03695_gb300 as pkg
 from paper_2608_03695_gb300 import synth
+from qtol import q_close
 
 pytestmark = pytest.mark.gpu
-
-QTOL = 1e-12
 
 
 def _cuda():
@@ -33,10 +32,6 @@ def built():
     _cuda()
     pkg.build()
     oracle.build()
-
-
-def q_close(a, b):
-    return abs(a - b) <= QTOL * max(1.0, abs(b))
 
 
 def rand_table(rng, T, coupling, hi=5):

@@ -11,10 +11,10 @@ import pytest
 import oracle
 import paper_2608_03695_gb300 as pkg
 from paper_2608_03695_gb300 import synth
+from qtol import q_close
 
 pytestmark = pytest.mark.gpu
 
-QTOL = 1e-12
 THETAS = [(1, 10), (1, 100), (1, 1000), (2, 1), (1, 10000)]
 
 
@@ -30,10 +30,6 @@ def built():
     _cuda()
     pkg.build()
     oracle.build()
-
-
-def q_close(a, b):
-    return abs(a - b) <= QTOL * max(1.0, abs(b))
 
 
 def solve_both(snaps, gamma=(1, 1), omega=(1, 1), **kw):

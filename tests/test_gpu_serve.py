@@ -9,10 +9,9 @@ import pytest
 import oracle
 import paper_2608_03695_gb300 as pkg
 from paper_2608_03695_gb300 import synth
+from qtol import q_close
 
 pytestmark = pytest.mark.gpu
-
-QTOL = 1e-12
 
 
 def _cuda():
@@ -29,20 +28,6 @@ def built():
     oracle.build()
 
 
-def warm_start(prev, n, W):
-    """Initial labels of the window after one more snapshot: (j, i) takes the
-    previous label of (min(j + e, w_prev - 1), i), e = 1 when the oldest slice
-    is evicted."""
-    if prev is None:
-        return None
-    w_prev = len(prev) // n
-    e = 1 if w_prev == W else 0
-    w_new = min(w_prev + 1, W)
-    j = np.arange(w_new)
-    src = np.minimum(j + e, w_prev - 1)
-    return np.concatenate([prev[s * n:(s + 1) * n] for s in src]).astype(np.int32)
-
-
 def stream(n, steps, seed, churn=0.05):
     snaps, _ = synth.planted_partition_temporal(n, steps, n_blocks=3, p_in=min(1.0, 12.0 / n), p_out=1.2 / n,
                                                 switch_frac=0.1, churn=churn, w_max=8, seed=seed)
@@ -50,16 +35,10 @@ def stream(n, steps, seed, churn=0.05):
 
 
 def oracle_chain(snaps, W, gamma=(1, 1), omega=(1, 1)):
-    """Expected (labels, Q) of every request of one graph's stream."""
-    out, prev = [], None
-    n = snaps[0].n
-    for t in range(len(snaps)):
-        window = snaps[max(0, t + 1 - W):t + 1]
-        init = warm_start(prev, n, W)
-        lab, Q, _ = oracle.leiden(window, gamma, omega, init=init)
-        out.append((lab, Q))
-        prev = lab
-    return out
+    """Expected (labels, Q) of every request of one graph's stream: the
+    oracle's serving chain (window of the last W snapshots, warm-started from
+    the previous request's labels)."""
+    return oracle.serve_chain(snaps, W, gamma, omega)
 
 
 def test_window_chain_matches_oracle():
@@ -72,7 +51,7 @@ def test_window_chain_matches_oracle():
             lab, info = srv.wait(srv.submit(g, sn))
             assert info["slices"] == min(t + 1, W) and info["N"] == 120 * min(t + 1, W)
             assert np.array_equal(lab, expect[t][0]), t
-            assert abs(info["Q"] - expect[t][1]) <= QTOL * max(1.0, abs(expect[t][1]))
+            assert q_close(info["Q"], expect[t][1])
 
 
 def test_alone_and_in_the_mix_agree():

@@ -15,10 +15,9 @@ import pytest
 
 import paper_2608_03695_gb300 as pkg
 from paper_2608_03695_gb300 import synth
+from qtol import q_close
 
 pytestmark = pytest.mark.gpu
-
-QTOL = 1e-12
 
 
 def _torch():
@@ -49,7 +48,7 @@ def _noalloc_q(torch, snaps, labels, gamma, omega):
 
 
 def _close(a, b):
-    return abs(a - b) <= QTOL * max(1.0, abs(b))
+    return q_close(a, b)
 
 
 @pytest.mark.parametrize("case", range(3))
