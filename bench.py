@@ -2,8 +2,9 @@
 """Throughput benchmark of the multislice-Leiden hot path on GB300.
 
 A step is one complete solve of the synthetic power-law temporal workload
-(T=16 snapshots of n=100,000 nodes, degree-corrected SBM with power-law
-degrees and community sizes, 5% edge churn per snapshot, weights 1..8,
+with T=64 snapshots of n=1,000,000 nodes (64M supra-nodes, ~1.15G stored
+entries; degree-corrected SBM with power-law degrees (exponent 2.3, mean 16)
+and community sizes, mixing 0.4, 5% edge churn per snapshot, weights 1..16,
 ordinal coupling omega=1, gamma=1): supra-graph build from device-resident
 snapshots, Leiden (two passes: local moving, refinement, aggregation) and
 Q_MS.  The metric is local-moving supra-edges per second: the sum over all
@@ -11,9 +12,10 @@ local-moving rounds of the level's directed entries, divided by the whole
 step's device time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mslice|reference]
+  python bench.py --workload plain-t16        (T=16, n=100,000: the smaller power-law recipe)
   python bench.py --workload batched [--scale S]
   python bench.py --workload serving [--scale S] [--requests R] [--slots K]
-  python bench.py --workload large [--scale S]
+  python bench.py --workload large-sweep [--scale S]   (T=64 at omega 1/10, 1, 10, plain and batched)
 
 The batched workload (64 temporal planted-partition graphs of uneven n and
 T, each solved at 6 gammas x 3 omegas = 1,152 solves) is timed twice on the
@@ -41,13 +43,23 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = {"workload": "multislice Leiden, power-law temporal DC-SBM", "T": 16, "n": 100000,
-            "deg_exp": 2.5, "mean_deg": 20, "size_exp": 1.5, "sizes": "20-5000", "mixing": 0.3, "churn": 0.05,
-            "weights": "1-8", "gamma": "1/1", "omega": "1/1", "n_iterations": 2, "K": 4, "seed": 0,
-            "supra_nodes": 1600000}
+# The plain workloads: the recipe, its config and the oracle's bounded sample
+# (n scaled so that one single-thread oracle solve takes ~10-30 s).
+PLAIN = {
+    "plain": dict(
+        recipe="powerlaw_t64_n1m", oracle_n=3000,
+        config={"workload": "multislice Leiden, power-law temporal DC-SBM, T=64, n=1,000,000", "T": 64,
+                "n": 1000000, "deg_exp": 2.3, "mean_deg": 16, "size_exp": 1.5, "sizes": "20-5000", "mixing": 0.4,
+                "churn": 0.05, "weights": "1-16", "gamma": "1/1", "omega": "1/1", "n_iterations": 2, "K": 4,
+                "seed": 0, "supra_nodes": 64000000}),
+    "plain-t16": dict(
+        recipe="powerlaw_t16_n100k", oracle_n=20000,
+        config={"workload": "multislice Leiden, power-law temporal DC-SBM", "T": 16, "n": 100000, "deg_exp": 2.5,
+                "mean_deg": 20, "size_exp": 1.5, "sizes": "20-5000", "mixing": 0.3, "churn": 0.05, "weights": "1-8",
+                "gamma": "1/1", "omega": "1/1", "n_iterations": 2, "K": 4, "seed": 0, "supra_nodes": 1600000}),
+}
 METRIC = "supra-edges/s in Leiden local-move"
 UNIT = "supra-edges/s"
-ORACLE_SAMPLE_N = 20000  # same recipe, n scaled so one oracle solve takes ~10-30 s
 
 
 def parse():
@@ -58,7 +70,8 @@ def parse():
     ap.add_argument("--impl", default="mslice", choices=["mslice", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving", "large", "school"])
+    ap.add_argument("--workload", default="plain",
+                    choices=["plain", "plain-t16", "batched", "serving", "large-sweep", "school"])
     ap.add_argument("--null", default="multislice", choices=["multislice", "global", "cpm"],
                     help="plain workload: Q_MS (default), the supra-graph's plain modularity, or temporal CPM")
     ap.add_argument("--theta", default=None,
@@ -126,10 +139,17 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def decide_traffic():
+# Committed ncu summaries of one decision round per plain workload; each
+# holds a "traffic_bytes_per_launch:" line (DRAM bytes of one sub-round's
+# decision launches, null once the kernels changed after the capture).
+TRAFFIC_PROFILES = {"plain": "local_move_decide_powerlaw_t64_n1m.md",
+                    "plain-t16": "local_move_decide_powerlaw_t16_n100k.md"}
+
+
+def decide_traffic(args):
     """DRAM bytes per launch of the decision kernel from the committed ncu
-    summary (None when absent)."""
-    p = os.path.join(ROOT, "profiles", "local_move_decide_powerlaw_t16_n100k.md")
+    summary of this workload (None when absent)."""
+    p = os.path.join(ROOT, "profiles", TRAFFIC_PROFILES.get(args.workload, ""))
     try:
         for line in open(p):
             if line.startswith("traffic_bytes_per_launch:"):
@@ -191,25 +211,34 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# General-form tables of the plain workload (--coupling tables): omega^(s,s+1)
+# General-form tables of the plain workloads (--coupling tables): omega^(s,s+1)
 # alternating 1/2 and 3/2, gamma^(s) cycling 3/4, 1, 5/4.
-TABLE_OMEGAS = [1 if s % 2 == 0 else 3 for s in range(15)]  # over omega_den 2
-TABLE_GAMMAS = [[(3, 4), (1, 1), (5, 4)][s % 3] for s in range(16)]
+def table_omegas(T):
+    return [1 if s % 2 == 0 else 3 for s in range(T - 1)]  # over omega_den 2
+
+
+def table_gammas(T):
+    return [[(3, 4), (1, 1), (5, 4)][s % 3] for s in range(T)]
+
+
+def plain_spec(args):
+    return PLAIN[args.workload]
 
 
 def gen_kwargs(args):
     """(build kwargs, solve kwargs shared by the library and the oracle) of the
     plain workload's model."""
     build, solve = {}, {"null": args.null}
+    T = plain_spec(args)["config"]["T"]
     if args.theta:
         num, den = (args.theta.split("/") + ["1"])[:2]
         solve["theta"] = (int(num), int(den))
     if args.coupling == "categorical":
         build["coupling"] = "categorical"
     elif args.coupling == "tables":
-        solve.update(omega=(1, 2), omegas=TABLE_OMEGAS)
+        solve.update(omega=(1, 2), omegas=table_omegas(T))
         if args.null != "global":
-            solve["gammas"] = TABLE_GAMMAS
+            solve["gammas"] = table_gammas(T)
     return build, solve
 
 
@@ -221,9 +250,9 @@ def oracle_kwargs(args):
 def workload(args):
     """The plain workload's config; the null model and coupling are named when
     they are not Q_MS with ordinal omega."""
+    c = dict(plain_spec(args)["config"])
     if args.null == "multislice" and args.coupling == "ordinal" and not args.theta:
-        return dict(WORKLOAD)
-    c = dict(WORKLOAD)
+        return c
     if args.theta:
         c.update(workload=c["workload"] + ", randomised refinement", theta=args.theta)
     if args.null != "multislice":
@@ -239,15 +268,22 @@ def workload(args):
     return c
 
 
+def oracle_sample(args):
+    """The oracle's bounded sample of the plain workload: the same recipe with
+    n scaled down (every snapshot kept)."""
+    from paper_2608_03695_gb300 import synth
+    spec = plain_spec(args)
+    return synth.recipe_graph(spec["recipe"], scale_n=spec["oracle_n"]), spec["oracle_n"], spec["config"]["T"]
+
+
 def cpu_baseline(args):
     import oracle
-    from paper_2608_03695_gb300 import synth
-    snaps = synth.recipe_graph("powerlaw_t16_n100k", scale_n=ORACLE_SAMPLE_N)
+    snaps, n, T = oracle_sample(args)
     t = time.perf_counter()
     _, _, st = oracle.leiden(snaps, **oracle_kwargs(args))
     el = time.perf_counter() - t
     return {"value": st["lm_edges"] / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one oracle solve of the same recipe at n={ORACLE_SAMPLE_N}, T=16 "
+            "sample": f"one oracle solve of the same recipe at n={n}, T={T} "
                       f"({st['lm_edges']} local-move supra-edges in {el:.1f} s, single thread)"}
 
 
@@ -256,9 +292,8 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    from paper_2608_03695_gb300 import synth
     oracle.build()
-    snaps = synth.recipe_graph("powerlaw_t16_n100k", scale_n=ORACLE_SAMPLE_N)
+    snaps, n, T = oracle_sample(args)
     for _ in range(args.warmup):
         oracle.leiden(snaps, n_iterations=1, max_rounds=2, **oracle_kwargs(args))  # short warm-up (page-in)
     edges, secs = 0, 0.0
@@ -272,10 +307,10 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic",
-            "config": {**workload(args), "n": ORACLE_SAMPLE_N, "supra_nodes": ORACLE_SAMPLE_N * 16,
+            "config": {**workload(args), "n": n, "supra_nodes": n * T,
                        "note": "bounded sample of the same recipe (n scaled) for the single-thread CPU oracle"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} oracle solves at n={ORACLE_SAMPLE_N}, T=16"},
+                             "sample": f"{args.steps} oracle solves at n={n}, T={T}"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -690,7 +725,7 @@ def main():
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
-    if args.workload == "large":
+    if args.workload == "large-sweep":
         return run_large(args)
     if args.workload == "school":
         return run_school(args)
@@ -707,7 +742,9 @@ def main():
     ranks = Ranks(dist, "cuda")
     barrier, max_over_ranks, sum_over_ranks = ranks.barrier, ranks.max, ranks.sum
 
-    snaps = synth.recipe_graph("powerlaw_t16_n100k")
+    t_gen = time.perf_counter()
+    snaps = synth.recipe_graph(plain_spec(args)["recipe"])
+    t_gen = time.perf_counter() - t_gen
     stream = torch.cuda.Stream()
     if args.profile_run:
         bkw, skw = gen_kwargs(args)
@@ -724,6 +761,9 @@ def main():
 
     dsnaps = [DevSnap(s, device="cuda") for s in snaps]
     N = snaps[0].n * len(snaps)
+    # level-0 supra-CSR: int64 row pointers and 8-byte {column, weight} entries
+    # (intra-snapshot entries plus two per ordinal coupling pair)
+    csr_bytes = 8 * (N + 1) + 8 * (sum(s.nnz for s in snaps) + 2 * snaps[0].n * (len(snaps) - 1))
     dlabels = torch.empty(N, dtype=torch.int32, device="cuda")
     torch.cuda.synchronize()
 
@@ -762,7 +802,8 @@ def main():
     peak, peak_kind = measured_peak()
     achieved = stp["decide_bytes"] / (stp["ms_decide"] / 1e3) / 1e9 if stp["ms_decide"] > 0 else 0.0
     # counters taken under Q_MS with ordinal omega only
-    traffic = decide_traffic() if args.null == "multislice" and args.coupling == "ordinal" and not args.theta else None
+    traffic = (decide_traffic(args) if args.null == "multislice" and args.coupling == "ordinal" and not args.theta
+               else None)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (traffic if traffic is None else traffic), "peak_source": peak_kind,
                 "kernel": "local-moving decision, level-0 sub-round (all degree tiers)",
@@ -788,7 +829,7 @@ def main():
         torch.cuda.synchronize()
         t = time.perf_counter()
         e_edges = 0
-        k_e2e = max(1, args.steps // 2)
+        k_e2e = max(2, args.steps // 4)
         for _ in range(k_e2e):
             e_edges += step_e2e()["lm_edges"]
         torch.cuda.synchronize()
@@ -800,7 +841,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {**workload(args), "parallelism": f"replicas{world}" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (level-0 supra-CSR 280 MB vs 129 MB L2)"},
+                       "l2": f"inputs larger than L2 (level-0 supra-CSR {csr_bytes / 1e9:.2f} GB vs 129 MB L2)"},
+            "generate_s": t_gen,
             "Q": Qs[-1] if Qs else None, "gpu_launches": int(sum_over_ranks(launches)),
             "local_move_only": {"value": stp["lm_edges"] / (stp["ms_local_move"] / 1e3), "unit": UNIT,
                                 "note": "same edges over local-moving device time only (profiled step)"},

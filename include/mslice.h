@@ -238,26 +238,32 @@ int mslice_modularity_general(mslice_handle h, const int32_t* labels, const msli
                               const mslice_general* gen, double* Q_out);
 
 /* Q_MS of int32[N] labels in [0, N), read straight from device snapshot
- * arrays, for callers that cannot allocate device memory: code that runs
- * while a CUDA graph is being captured, plug-ins held to a memory budget by
- * their host application, services that reserve all device memory up front.
- * The paper has no counterpart; it is the evaluation of mslice_modularity
- * (same integer sums and FP64 order) without a handle.
- *   slices: T snapshots whose indptr/indices/weights are DEVICE pointers
- *           (the mslice_csr conventions; row pointers, column indices and
- *           weights are checked, symmetry is not);
+ * arrays, for callers that cannot allocate device memory: plug-ins held to a
+ * memory budget by their host application, and services that reserve all
+ * device memory up front and hand out slices of it.  The paper has no
+ * counterpart; it is the evaluation of mslice_modularity (same integer sums
+ * and FP64 order) without a handle.
+ *   slices: T snapshots whose indptr/indices/weights are DEVICE pointers, with
+ *           the mslice_csr conventions checked on the device (row pointers,
+ *           index and weight arrays present when a snapshot has entries,
+ *           columns in range, strictly ascending, no self-loops, weights
+ *           >= 1), except symmetry, which is not checked;
  *   labels: device int32[N], N = n*T;  stream: cudaStream_t (NULL: default);
  *   Q_out:  host double.
  * No device memory is allocated: all scratch lives in one 32 MiB array inside
  * the library (4 + 6*T + N*T 8-byte words must fit in 4,194,304 words, else
  * MSLICE_EINVAL), which every GPU that loads the library keeps until the
  * process exits.  The first call on each device looks up that array's device
- * address (with the device current) and caches it; make that first call
- * before any stream capture.  Every call clears the scratch it uses, but all
- * calls share the one array, so calls that overlap on a GPU (other streams,
- * other host threads) race and must be serialised by the caller.  The call
- * returns after the stream is synchronised.  Errors: EINVAL, EOVERFLOW,
- * ECUDA. */
+ * address (with the device current) and caches it for the process; after a
+ * cudaDeviceReset of that device the cached address is stale and the call
+ * must not be used there again.  Every call clears the scratch it uses, but
+ * all calls share the one array, so calls that overlap on a GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * The call copies a pointer table from host memory and synchronises the
+ * stream before it returns, so it must not be issued on a stream that is
+ * being captured into a CUDA graph.  A CUDA error already pending from the
+ * caller's earlier work makes it fail with MSLICE_ECUDA and is left pending.
+ * Errors: EINVAL, EOVERFLOW, ECUDA. */
 int mslice_modularity_noalloc(const mslice_csr* slices, int32_t T, const int32_t* labels, int64_t gamma_num,
                               int64_t gamma_den, int64_t omega_num, int64_t omega_den, void* stream,
                               double* Q_out);

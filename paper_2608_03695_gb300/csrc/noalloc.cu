@@ -2,12 +2,14 @@
 // any device memory.
 //
 // Some callers cannot call cudaMalloc (or any routine that allocates device
-// memory): code running while a CUDA graph is being captured, plug-ins that
-// must stay inside a memory budget fixed by their host application, and
-// services that pre-reserve all device memory at start-up.  For them this
-// entry point keeps all of its scratch in one fixed array that is part of the
-// library image (below).  Every GPU that loads the library holds that array
-// until the process exits.
+// memory): plug-ins that must stay inside a memory budget fixed by their host
+// application, and services that pre-reserve all device memory at start-up
+// and hand out slices of it.  For them this entry point keeps all of its
+// scratch in one fixed array that is part of the library image (below).
+// Every GPU that loads the library holds that array until the process exits.
+// The call copies a small pointer table from host memory and synchronises its
+// stream before it returns, so it must not be issued on a stream that is
+// being captured into a CUDA graph.
 //
 // The computation is the same as mslice_modularity (same integer sums, same
 // FP64 evaluation order), read straight from the caller's snapshot arrays.
@@ -61,19 +63,28 @@ __global__ void k_na_clear(ull* p, size_t words) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (size_t)gridDim.x * blockDim.x) p[i] = 0;
 }
 
-// Row pointers monotone within [0, nnz_s], column indices and labels in range
-// (a violation sets a status bit; nothing is read out of bounds).
+// The snapshot conventions of mslice_build, except symmetry: row pointers
+// monotone within [0, nnz_s]; index and weight arrays present when a
+// snapshot has entries; columns in [0, n), strictly ascending within a row
+// (no duplicates) and never the row itself (no self-loops); weights >= 1;
+// labels in [0, N).  A violation sets a status bit, and nothing is read out
+// of bounds (a row is walked only after its bounds and arrays checked out).
 __global__ void k_na_check(Layout L, const int32_t* labels) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < L.N; v += (int64_t)gridDim.x * blockDim.x) {
     const int32_t s = (int32_t)(v / L.n);
     const int64_t i = v - (int64_t)s * L.n;
     const int64_t* ip = L.ip[s];
+    const int32_t* ix = L.ix[s];
+    const int32_t* wt = L.wt[s];
     const int64_t a = ip[i], b = ip[i + 1], nnz = ip[L.n];
-    bool bad = a < 0 || b < a || b > nnz || (i == 0 && a != 0);
+    bool bad = a < 0 || b < a || b > nnz || (i == 0 && a != 0) || (nnz > 0 && (!ix || !wt));
     if (!bad)
       for (int64_t e = a; e < b; ++e) {
-        const int32_t j = L.ix[s][e];
-        if (j < 0 || j >= L.n || L.wt[s][e] < 1) bad = true;
+        const int32_t j = ix[e];
+        if (j < 0 || j >= L.n || j == i || wt[e] < 1 || (e > a && ix[e - 1] >= j)) {
+          bad = true;
+          break;
+        }
       }
     if (labels[v] < 0 || labels[v] >= L.N) bad = true;
     if (bad) atomicOr((unsigned*)&L.base[W_STATUS], 1u);
@@ -153,7 +164,9 @@ __global__ void k_na_q(Layout L, long long gn, long long gd, long long on, long 
 }
 
 // Device address of the scratch array, looked up once per device (with that
-// device current) and cached.
+// device current) and cached.  The cached address belongs to the device's
+// primary context; after cudaDeviceReset on that device it is stale, and
+// this entry point must not be called there again in the same process.
 ull* scratch_address(int dev, std::string& err) {
   static std::mutex mu;
   static std::vector<ull*> cache;
@@ -202,8 +215,14 @@ extern "C" int mslice_modularity_noalloc(const mslice_csr* slices, int32_t T, co
                                    " exceeds the allocation-free scratch (at most about 4.1M (node, snapshot) x T "
                                    "words, 32 MiB)");
   if (N > 0 && !labels) return fail(MSLICE_EINVAL, "null labels");
+  // A CUDA error left pending by the caller's earlier work is reported, not
+  // consumed: the launch checks below would otherwise clear it and blame this
+  // call for it.
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess)
+    return fail(MSLICE_ECUDA, std::string("a CUDA error from earlier work is pending: ") + cudaGetErrorString(e));
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(MSLICE_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   std::string err;
   ull* base = scratch_address(dev, err);
@@ -242,7 +261,10 @@ extern "C" int mslice_modularity_noalloc(const mslice_csr* slices, int32_t T, co
   e = cudaMemcpyAsync(out, base, 2 * sizeof(ull), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(MSLICE_ECUDA, std::string("readback: ") + cudaGetErrorString(e));
-  if (out[0] & 1u) return fail(MSLICE_EINVAL, "malformed snapshot or label out of [0, N)");
+  if (out[0] & 1u)
+    return fail(MSLICE_EINVAL,
+                "malformed snapshot (row pointers, missing arrays, unsorted or repeated columns, self-loop, weight "
+                "< 1) or label out of [0, N)");
   if (out[0] & 2u) return fail(MSLICE_EOVERFLOW, "the 2^61 bounds of the library conventions do not hold");
   double Q;
   std::memcpy(&Q, &out[1], sizeof(double));

@@ -8,8 +8,12 @@ digest matches the stored one they compare with the stored result, otherwise
 (a platform whose floating-point library changes the generated graph) they
 run the oracle live.
 
-    python tests/golden/full_size_cases.py            # all cases (~20 min, one core)
+    python tests/golden/full_size_cases.py            # all cases (hours, one core)
     python tests/golden/full_size_cases.py powerlaw   # cases whose name starts so
+    python tests/golden/full_size_cases.py --jobs 4 batched_full   # cases in parallel processes
+
+Each case is written to the JSON file as soon as it finishes (under a file
+lock, so parallel runs may share it).
 """
 from __future__ import annotations
 
@@ -28,6 +32,11 @@ sys.path.insert(0, ROOT)
 from paper_2608_03695_gb300 import synth  # noqa: E402
 
 EXPECTED = os.path.join(HERE, "full_size_expected.json")
+
+# Graphs of the batched workload solved over the whole (gamma, omega) grid:
+# the largest by n whose single-thread oracle solves fit the time this
+# script is given (see the design notes for the limit).
+BATCHED_SWEEP_GRAPHS = []
 
 
 def digest_arrays(arrays) -> str:
@@ -83,6 +92,22 @@ def cases():
 
     out["batched_sample"] = batched_sample
 
+    # every graph of the batched workload at full size, at gamma = omega = 1
+    for k in range(synth.BATCHED["n_graphs"]):
+        def batched_full(k=k):
+            return [dict(snaps=synth.batched_graph(synth.batched_specs()[k]), gamma=(1, 1), omega=(1, 1), graph=k)]
+
+        out[f"batched_full_g{k:02d}"] = batched_full
+
+    # the whole gamma x omega grid on the batched workload's largest graphs
+    for k in BATCHED_SWEEP_GRAPHS:
+        for gm in synth.BATCHED_GAMMAS:
+            for om in synth.BATCHED_OMEGAS:
+                def batched_sweep(k=k, gm=gm, om=om):
+                    return [dict(snaps=synth.batched_graph(synth.batched_specs()[k]), gamma=gm, omega=om, graph=k)]
+
+                out[f"batched_sweep_g{k:02d}_{gm[0]}_{gm[1]}_{om[0]}_{om[1]}"] = batched_sweep
+
     def serving_chain():
         W = synth.SERVING["window"]
         spec = sorted(synth.serving_specs(), key=lambda s: s[0])[0]  # the smallest live graph (n ~ 10k)
@@ -121,20 +146,44 @@ def run_solve(oracle, s):
             "stats": {k: int(st[k]) for k in ("iterations", "levels", "lm_rounds", "lm_edges", "lm_moves")}}
 
 
-def main(prefixes):
+def _store(name, result):
+    """Writes one case's result into the JSON file (read-modify-write under
+    an exclusive lock, replaced atomically)."""
+    import fcntl
+    with open(EXPECTED + ".lock", "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        data = json.load(open(EXPECTED)) if os.path.exists(EXPECTED) else {}
+        data[name] = result
+        tmp = EXPECTED + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+        os.replace(tmp, EXPECTED)
+
+
+def _run_case(name):
     import oracle
     oracle.build()
-    data = {}
-    if os.path.exists(EXPECTED):
-        data = json.load(open(EXPECTED))
-    for name, make in cases().items():
-        if prefixes and not any(name.startswith(p) for p in prefixes):
-            continue
-        t = time.time()
-        data[name] = [run_solve(oracle, s) for s in make()]
-        print(f"{name}: {time.time() - t:.1f} s", flush=True)
-        with open(EXPECTED, "w") as f:
-            json.dump(data, f, indent=1, sort_keys=True)
+    t = time.time()
+    result = [run_solve(oracle, s) for s in cases()[name]()]
+    _store(name, result)
+    return name, time.time() - t
+
+
+def main(argv):
+    jobs = 1
+    if argv[:1] == ["--jobs"]:
+        jobs, argv = int(argv[1]), argv[2:]
+    import oracle
+    oracle.build()
+    names = list(cases()) if not argv else list(dict.fromkeys(n for p in argv for n in cases() if n.startswith(p)))
+    if jobs <= 1:
+        for name in names:
+            print("%s: %.1f s" % _run_case(name), flush=True)
+        return
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(jobs, maxtasksperchild=1) as pool:
+        for name, el in pool.imap_unordered(_run_case, names):
+            print(f"{name}: {el:.1f} s", flush=True)
 
 
 if __name__ == "__main__":
