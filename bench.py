@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--impl", default="mslice", choices=["mslice", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="plain workload: skip the three-omega plain-vs-batched comparison")
     ap.add_argument("--workload", default="plain",
                     choices=["plain", "plain-t16", "batched", "serving", "large-sweep", "school"])
     ap.add_argument("--null", default="multislice", choices=["multislice", "global", "cpm"],
@@ -81,8 +83,14 @@ def parse():
                          "or the general form's tables (per-pair omega, per-snapshot gamma)")
     ap.add_argument("--requests", type=int, default=4, help="serving workload: timed snapshots per graph")
     ap.add_argument("--slots", type=int, default=2, help="serving workload: server workers")
-    ap.add_argument("--scale", type=float, default=1.0, help="batched workload: node-count scale of every graph")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="node-count scale of every graph (batched and serving workloads; plain workloads: "
+                         "--profile-run only, for small profiler captures)")
     ap.add_argument("--graphs", type=int, default=None, help="batched workload: first G graphs only")
+    ap.add_argument("--batch-nodes", type=int, default=BATCH_MAX_NODES,
+                    help="batched workload: supra-nodes packed into one batch at most")
+    ap.add_argument("--batch-entries", type=int, default=BATCH_MAX_ENTRIES,
+                    help="batched workload: stored entries packed into one batch at most")
     ap.add_argument("--profile-run", action="store_true",
                     help="one solve of the workload and exit (a short target for ncu captures)")
     return ap.parse_args()
@@ -358,18 +366,19 @@ def run_batched(args):
     clocks.start()
     # plain path: one call per solve
     t = time.perf_counter()
-    plain, work, launches_plain = [], 0, 0
+    plain, work, launches_plain, host_plain = [], 0, 0, 0
     for gi, gm, om in solves:
         lab, Q, st = handles[gi].mslice_leiden(gamma=gm, omega=om)
         plain.append(digest(lab, Q))
         work += st["lm_edges"]
         launches_plain += st["kernel_launches"]
+        host_plain += st["host_launches"]
     t_plain = time.perf_counter() - t
     # batched path: solves packed in add order under the per-batch budget
     chunks, cur, cn, ce = [], [], 0, 0
     for k, (gi, gm, om) in enumerate(solves):
         h = handles[gi]
-        if cur and (cn + h.N > BATCH_MAX_NODES or ce + h.nnz > BATCH_MAX_ENTRIES):
+        if cur and (cn + h.N > args.batch_nodes or ce + h.nnz > args.batch_entries):
             chunks.append(cur)
             cur, cn, ce = [], 0, 0
         cur.append(k)
@@ -378,7 +387,7 @@ def run_batched(args):
     if cur:
         chunks.append(cur)
     t = time.perf_counter()
-    batched, launches_b = [None] * len(solves), 0
+    batched, launches_b, host_b = [None] * len(solves), 0, 0
     ms_dev = 0.0
     for ch in chunks:
         with pkg.Batch() as b:
@@ -387,6 +396,7 @@ def run_batched(args):
                 b.add(handles[gi], gm, om)
             st = b.run()
             launches_b += st["kernel_launches"]
+            host_b += st["host_launches"]
             ms_dev += st["ms_total"]
             labs, Qs = b.results()
             _, _, off = b.info()
@@ -408,9 +418,11 @@ def run_batched(args):
     line = {"metric": "supra-edges/s in Leiden local-move, batched vs plain", "value": v_batch, "unit": UNIT,
             "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * t_batch, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic", "config": cfg,
-            "plain": {"value": v_plain, "unit": UNIT, "seconds": t_plain, "gpu_launches": launches_plain},
+            "plain": {"value": v_plain, "unit": UNIT, "seconds": t_plain, "gpu_launches": launches_plain,
+                      "host_launches": host_plain},
             "batched": {"value": v_batch, "unit": UNIT, "seconds": t_batch, "gpu_launches": launches_b,
-                        "device_ms": ms_dev},
+                        "host_launches": host_b, "device_ms": ms_dev,
+                        "packing": {"max_nodes": args.batch_nodes, "max_entries": args.batch_entries}},
             "batched_over_plain": v_batch / v_plain, "identical_results": same,
             "work_supra_edges": work, "generate_s": t_gen, "clocks": clk}
     print(json.dumps(line), flush=True)
@@ -717,6 +729,61 @@ def run_school(args):
     print(json.dumps(line), flush=True)
 
 
+# Config 4's own comparison: the same graph at omega = 1/10, 1 and 10, solved
+# plain (one call per omega) and as one batch of the three instances.
+PLAIN_VS_BATCHED_OMEGAS = [(1, 10), (1, 1), (10, 1)]
+
+
+def plain_vs_batched(pkg, dsnaps, stream, skw):
+    """Times the three omegas as three plain solves and as one batch on a
+    handle built from the device-resident snapshots (CUDA events on the
+    library's stream), and checks that the batch gives the plain labels and Q
+    bit for bit.  Not part of the timed region of the headline metric."""
+    import hashlib
+    import torch
+
+    def digest(lab):
+        return hashlib.sha1(np.ascontiguousarray(lab.cpu().numpy() if hasattr(lab, "cpu") else lab,
+                                                 dtype=np.int32).tobytes()).hexdigest()
+
+    h = pkg.mslice_build(dsnaps, device_ptrs=True, stream=stream.cuda_stream)
+    try:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        plain, edges, st_plain = [], 0, []
+        e0.record(stream)
+        for om in PLAIN_VS_BATCHED_OMEGAS:
+            lab, Q, st = h.mslice_leiden(omega=om, **skw)
+            plain.append((digest(lab), Q))
+            edges += st["lm_edges"]
+            st_plain.append(st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_plain = e0.elapsed_time(e1)
+        try:
+            with pkg.Batch(stream=stream.cuda_stream) as b:
+                for om in PLAIN_VS_BATCHED_OMEGAS:
+                    b.mslice_batch_add(h, (1, 1), om)
+                e0.record(stream)
+                bst = b.mslice_batch_run(**skw)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms_batch = e0.elapsed_time(e1)
+                batched = [(digest(b.results(i)[0]), b.results(i)[1]) for i in range(len(PLAIN_VS_BATCHED_OMEGAS))]
+        except pkg.MsliceError as ex:  # a batch that does not fit the device
+            return {"omegas": ["1/10", "1/1", "10/1"], "plain_ms": ms_plain, "batched": None,
+                    "batched_note": f"not run: {ex}"}
+        return {"omegas": ["1/10", "1/1", "10/1"], "plain_ms": ms_plain, "batched_ms": ms_batch,
+                "speedup": ms_plain / ms_batch, "plain_value": edges / (ms_plain / 1e3),
+                "batched_value": edges / (ms_batch / 1e3), "unit": UNIT, "identical_results": batched == plain,
+                "Q": [q for _, q in plain],
+                "kernel_launches": {"plain": sum(x["kernel_launches"] for x in st_plain),
+                                    "batched": bst["kernel_launches"]},
+                "host_launches": {"plain": sum(x["host_launches"] for x in st_plain),
+                                  "batched": bst["host_launches"]}}
+    finally:
+        h.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -743,9 +810,13 @@ def main():
     barrier, max_over_ranks, sum_over_ranks = ranks.barrier, ranks.max, ranks.sum
 
     t_gen = time.perf_counter()
-    snaps = synth.recipe_graph(plain_spec(args)["recipe"])
+    n_full = plain_spec(args)["config"]["n"]
+    snaps = synth.recipe_graph(plain_spec(args)["recipe"],
+                               scale_n=None if args.scale == 1.0 else max(8, int(round(n_full * args.scale))))
     t_gen = time.perf_counter() - t_gen
     stream = torch.cuda.Stream()
+    if args.scale != 1.0 and not args.profile_run:
+        raise SystemExit("--scale applies to a plain workload's --profile-run only")
     if args.profile_run:
         bkw, skw = gen_kwargs(args)
         with pkg.mslice_build(snaps, **bkw) as h:
@@ -837,6 +908,12 @@ def main():
         e2e = {"value": sum_over_ranks(e_edges) / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": k_e2e, "ms_per_step": 1e3 * el / k_e2e}
 
+    pvb = None
+    if args.workload == "plain" and rank == 0 and not args.no_batched and args.null == "multislice" \
+            and args.coupling == "ordinal" and not args.theta:
+        torch.cuda.empty_cache()
+        pvb = plain_vs_batched(pkg, dsnaps, stream, {})
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
@@ -846,7 +923,15 @@ def main():
             "Q": Qs[-1] if Qs else None, "gpu_launches": int(sum_over_ranks(launches)),
             "local_move_only": {"value": stp["lm_edges"] / (stp["ms_local_move"] / 1e3), "unit": UNIT,
                                 "note": "same edges over local-moving device time only (profiled step)"},
+            "phases_ms": {k: round(stp["ms_" + k], 2) for k in
+                          ("total", "local_move", "refine", "aggregate", "modularity", "decide")},
+            "capped_levels": {"levels": stp["capped_levels"], "rounds": stp["capped_rounds"],
+                              "ms": round(stp["ms_capped"], 2),
+                              "share_of_solve": stp["ms_capped"] / max(stp["ms_total"], 1e-9),
+                              "note": "local-moving levels that stopped at max_rounds with nodes still moving"},
             "roofline": roofline, "clocks": clk, "e2e": e2e}
+    if pvb is not None:
+        line["plain_vs_batched"] = pvb
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:

@@ -179,6 +179,12 @@ typedef struct {
                                 community's 16-byte table slot); probes of other candidate
                                 communities are not counted, so this is a lower bound */
   int32_t tier_cuts[4];      /* degree cuts the decision tiers used (chosen by MSLICE_AUTOTUNE) */
+  double ms_capped;          /* local-moving device time of the levels that stopped at max_rounds with
+                                nodes still moving (the synchronous schedule cycling), part of ms_local_move */
+  int64_t capped_levels;     /* number of those levels */
+  int64_t capped_rounds;     /* their local-moving rounds */
+  int64_t host_launches;     /* launch calls the host made for this call (kernels launched one by one, and
+                                graph launches, each counting once however many kernels the graph runs) */
 } mslice_stats;
 
 /* Defaults above; stop_level = -1. */

@@ -83,7 +83,8 @@ class Stats(C.Structure):
                 ("kernel_launches", C.c_int64), ("ms_total", C.c_double), ("ms_local_move", C.c_double),
                 ("ms_refine", C.c_double), ("ms_aggregate", C.c_double), ("ms_modularity", C.c_double),
                 ("ms_decide", C.c_double), ("decide_launches", C.c_int64), ("decide_bytes", C.c_int64),
-                ("tier_cuts", C.c_int32 * 4)]
+                ("tier_cuts", C.c_int32 * 4), ("ms_capped", C.c_double), ("capped_levels", C.c_int64),
+                ("capped_rounds", C.c_int64), ("host_launches", C.c_int64)]
 
 
 class ServerOpts(C.Structure):

@@ -62,7 +62,8 @@ def build(force: bool = False, verbose: bool = False, extra=(), checked: bool = 
     if force:
         for f in glob.glob(os.path.join(obj_dir, "*.o")):
             os.remove(f)
-    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+    jobs = int(os.environ.get("MSLICE_BUILD_JOBS", "0")) or min(8, os.cpu_count() or 1)
+    with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra, obj_dir), srcs))
     if _stale(lib, objs):
         tmp = lib + f".tmp{os.getpid()}"

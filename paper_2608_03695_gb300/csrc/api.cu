@@ -80,6 +80,17 @@ void* Workspace::get_bytes(const std::string& name, size_t bytes) {
     fail(MSLICE_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes for " + name + " failed (injected)");
   void* p = nullptr;
   cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+  if (e == cudaErrorMemoryAllocation) {
+    // The device pool keeps freed memory for reuse (keep_pool_memory); when
+    // that leaves too little for this request, wait for pending frees,
+    // return the pool's unused memory and try once more.
+    cudaGetLastError();
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaDeviceSynchronize() == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess && cudaMemPoolTrimTo(pool, 0) == cudaSuccess)
+      e = cudaMallocAsync(&p, bytes, stream);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     fail(MSLICE_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes for " + name + " failed");
@@ -408,10 +419,14 @@ void run_solve(Ctx& c, const SupraGraph& G, const std::vector<InstParams>& jobs,
   stats.ms_refine = ro.ms[2];
   stats.ms_aggregate = ro.ms[3];
   stats.ms_modularity = ro.ms[4];
+  stats.ms_capped = ro.ms_capped;
+  stats.capped_levels = ro.capped_levels;
+  stats.capped_rounds = ro.capped_rounds;
   stats.lm_rounds = S.lm_rounds;
   stats.lm_edges = S.lm_edges;
   stats.lm_moves = S.lm_moves;
   stats.kernel_launches = c.launches;
+  stats.host_launches = c.host_launches;
   for (int k = 0; k < 4; ++k) stats.tier_cuts[k] = S.p.cuts.t[k];
   if (c.trace) trace_report(c);
   if (c.profile) {
@@ -1068,6 +1083,9 @@ extern "C" int mslice_leiden_windowed(const mslice_csr* slices, int32_t T, int32
       acc.ms_refine += ro.ms[2];
       acc.ms_aggregate += ro.ms[3];
       acc.ms_modularity += ro.ms[4];
+      acc.ms_capped += ro.ms_capped;
+      acc.capped_levels += ro.capped_levels;
+      acc.capped_rounds += ro.capped_rounds;
       acc.iterations = std::max<int32_t>(acc.iterations, (int32_t)ro.iterations);
       acc.levels = std::max<int32_t>(acc.levels, (int32_t)ro.levels);
       // stitching (canonical labels: first occurrence order is label order)
@@ -1100,6 +1118,7 @@ extern "C" int mslice_leiden_windowed(const mslice_csr* slices, int32_t T, int32
     }
     acc.out_n = (int64_t)stitched.size();
     acc.kernel_launches = c.launches;
+    acc.host_launches = c.host_launches;
     for (int kk = 0; kk < 4; ++kk) acc.tier_cuts[kk] = sp.cuts.t[kk];
     if (st) *st = acc;
   });

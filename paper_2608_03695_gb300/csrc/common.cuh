@@ -61,26 +61,48 @@ struct alignas(16) Slot {
   long long val;
 };
 
+// The table is cut into one region per null slice s (the low 32 bits of a
+// key): keys (c, s) live in slots [region[s], region[s+1]), and probing wraps
+// inside the region.  A region is sized for the level-0 nodes of its slice,
+// so the keys a sub-round touches, which belong to the few snapshots its
+// nodes are drawn from at any moment, stay in a small part of the table
+// (L2-resident) instead of spreading over all of it.
 struct HashView {
   Slot* slots;
-  uint64_t cap;
+  uint64_t cap;                      // all regions
   unsigned* status;
-  ull* used = nullptr;  // optional: counts slots taken since the last clear
+  ull* used = nullptr;               // optional: regions past half their capacity since the last clear
+  const uint64_t* region = nullptr;  // R + 1 slot offsets
+  ull* region_used = nullptr;        // optional with `used`: slots taken per region since the last clear
 };
-
-// Home slot: one multiplicative mixing step (Fibonacci hashing) and a
-// multiply-high range reduction; slot positions never affect results.
-__device__ __forceinline__ uint64_t hash_home(ull key, uint64_t cap) {
-  return __umul64hi((key ^ (key >> 29)) * 0x9E3779B97F4A7C15ULL, cap);
-}
 
 __device__ __forceinline__ ull pack_cs(int32_t c, int32_t s) {
   return ((ull)(uint32_t)c << 32) | (uint32_t)s;
 }
 
+// Region of a key: its first slot and its size.
+__device__ __forceinline__ void hash_region(const HashView& h, ull key, uint64_t& base, uint64_t& size) {
+  const uint32_t s = (uint32_t)key;
+  base = __ldg(&h.region[s]);
+  size = __ldg(&h.region[s + 1]) - base;
+}
+
+// Home slot inside the region: one multiplicative mixing step (Fibonacci
+// hashing) and a multiply-high range reduction; slot positions never affect
+// results.
+__device__ __forceinline__ uint64_t hash_home(ull key, uint64_t base, uint64_t size) {
+  return base + __umul64hi((key ^ (key >> 29)) * 0x9E3779B97F4A7C15ULL, size);
+}
+
+__device__ __forceinline__ uint64_t hash_next(uint64_t i, uint64_t base, uint64_t size) {
+  return (i + 1 == base + size) ? base : i + 1;
+}
+
 __device__ __forceinline__ void hash_add(const HashView& h, ull key, long long delta) {
-  uint64_t i = hash_home(key, h.cap);
-  for (uint64_t probe = 0; probe < h.cap; ++probe) {
+  uint64_t base, size;
+  hash_region(h, key, base, size);
+  uint64_t i = hash_home(key, base, size);
+  for (uint64_t probe = 0; probe < size; ++probe) {
     ull k = h.slots[i].key;
     if (k == key) {
       atomicAdd((ull*)&h.slots[i].val, (ull)delta);
@@ -90,23 +112,29 @@ __device__ __forceinline__ void hash_add(const HashView& h, ull key, long long d
       ull prev = atomicCAS(&h.slots[i].key, EMPTY_KEY, key);
       if (prev == EMPTY_KEY || prev == key) {
         atomicAdd((ull*)&h.slots[i].val, (ull)delta);
-        if (prev == EMPTY_KEY && h.used) atomicAdd(h.used, 1ull);
+        if (prev == EMPTY_KEY && h.used) {
+          // count the region once, when its taken slots pass half of it
+          const ull taken = atomicAdd(&h.region_used[(uint32_t)key], 1ull) + 1;
+          if (2 * taken > size && 2 * (taken - 1) <= size) atomicAdd(h.used, 1ull);
+        }
         return;
       }
     }
-    i = (i + 1 == h.cap) ? 0 : i + 1;
+    i = hash_next(i, base, size);
   }
   atomicOr(h.status, ERR_HASH_FULL);
 }
 
 // Read-only lookup (0 when absent).  Only valid while no thread inserts.
 __device__ __forceinline__ long long hash_get(const HashView& h, ull key) {
-  uint64_t i = hash_home(key, h.cap);
-  for (uint64_t probe = 0; probe < h.cap; ++probe) {
+  uint64_t base, size;
+  hash_region(h, key, base, size);
+  uint64_t i = hash_home(key, base, size);
+  for (uint64_t probe = 0; probe < size; ++probe) {
     const Slot s = h.slots[i];
     if (s.key == key) return s.val;
     if (s.key == EMPTY_KEY) return 0;
-    i = (i + 1 == h.cap) ? 0 : i + 1;
+    i = hash_next(i, base, size);
   }
   return 0;
 }
@@ -115,9 +143,11 @@ __device__ __forceinline__ long long hash_get(const HashView& h, ull key) {
 __device__ __forceinline__ long long hash_get_from(const HashView& h, ull key, const Slot& first) {
   if (first.key == key) return first.val;
   if (first.key == EMPTY_KEY) return 0;
-  uint64_t i = hash_home(key, h.cap);
-  for (uint64_t probe = 1; probe < h.cap; ++probe) {
-    i = (i + 1 == h.cap) ? 0 : i + 1;
+  uint64_t base, size;
+  hash_region(h, key, base, size);
+  uint64_t i = hash_home(key, base, size);
+  for (uint64_t probe = 1; probe < size; ++probe) {
+    i = hash_next(i, base, size);
     const Slot s = h.slots[i];
     if (s.key == key) return s.val;
     if (s.key == EMPTY_KEY) return 0;
@@ -125,7 +155,11 @@ __device__ __forceinline__ long long hash_get_from(const HashView& h, ull key, c
   return 0;
 }
 
-__device__ __forceinline__ Slot hash_first(const HashView& h, ull key) { return h.slots[hash_home(key, h.cap)]; }
+__device__ __forceinline__ Slot hash_first(const HashView& h, ull key) {
+  uint64_t base, size;
+  hash_region(h, key, base, size);
+  return h.slots[hash_home(key, base, size)];
+}
 
 // -------------------------------------------------------------------------
 // Table of per-(label, snapshot) sums (Sigma_{c,s}, K_{R,s}).  Dense rows of

@@ -19,7 +19,9 @@
 //   tier 2  deg <= 256   one warp per node, 512-slot table
 //   tier 3  deg <= 1024  one 256-thread block per node, shared table of
 //                        2*deg slots rounded up to a power of two
-//   tier 4  larger       one block per node, table in global scratch
+//   tier 4  larger       one block per node, table of up to 8192 slots in
+//                        dynamic shared memory (degree <= 4096), global
+//                        scratch above
 //
 // Policy interface (all __device__):
 //   bool begin(v)                      node takes part (uniform per node)
@@ -40,6 +42,8 @@
 //   bool own_walks_slices()            own() walks the list (else it is cheap)
 //   i128 own_ns(v, vc, W_own, ns)      own() from a complete null sum
 #pragma once
+#include <cstdlib>
+
 #include "internal.h"
 #include "level.h"
 
@@ -81,6 +85,12 @@ struct TierCuts {
   int32_t t[NTIERS - 1] = {16, 32, (1 << T2_BITS) / 2, 1024};
 };
 constexpr int TIER3_BITS = 11;  // 2 * 1024 slots
+// Tier 4's shared-memory table: 2^13 slots (degrees up to 4096) in 104 KB of
+// dynamic shared memory, with room for 2^12 listed candidates.
+constexpr int TIER4_SMEM_BITS = 13;
+constexpr int TIER4_SMEM_SLOTS = 1 << TIER4_SMEM_BITS;
+constexpr size_t TIER4_SMEM_BYTES =
+    (size_t)TIER4_SMEM_SLOTS * (sizeof(long long) + sizeof(int32_t)) + (size_t)(TIER4_SMEM_SLOTS / 2) * sizeof(uint16_t);
 constexpr int BLOCK_THREADS = 256;
 constexpr int GROUP_THREADS = 256;
 
@@ -324,8 +334,86 @@ __device__ __forceinline__ Cand score_range(const Pol& pol, int32_t v, const typ
   return c;
 }
 
-// Tier 3: one block per node, shared table of 2*deg (rounded up) slots; the
-// node's distinct keys are listed as their slots are claimed.
+// One node decided by the whole block with its table in shared memory
+// (hk/hv of at least 2^bits slots, all free on entry and left free; cl: room
+// for 2^bits / 2 slot numbers; ncand: a shared counter, 0 on entry and left
+// 0).  The node's distinct keys are listed as their slots are claimed.
+template <class Pol>
+__device__ __forceinline__ void block_decide_node(const Pol& pol, int32_t v, int32_t* hk, long long* hv, uint16_t* cl,
+                                                  int32_t* ncand, Cand* red, ull* usm, i128* own_sm) {
+  const typename Pol::VCtx vc = pol.vctx(v);
+  const int64_t beg = pol.g.rowptr[v], end = pol.g.rowptr[v + 1];
+  const int bits = table_bits_for_degree(end - beg);
+  for (int64_t e = beg + threadIdx.x; e < end; e += BLOCK_THREADS) {
+    int32_t key;
+    long long w;
+    if (pol.edge(v, vc, e, key, w)) {
+      bool fresh;
+      const int slot = table_add_slot(hk, hv, bits, key, w, fresh);
+#if MSLICE_CHECKED
+      if (slot < 0) atomicOr(pol.g.chk, ERR_BOUNDS);
+#endif
+      if (fresh) cl[atomicAdd(ncand, 1)] = (uint16_t)slot;
+    }
+  }
+  __syncthreads();
+  const int n = *ncand;
+  const int32_t own = pol.own_key(v);
+  if (slice_parallel(n, pol.slice_count(v), BLOCK_THREADS)) {
+    // every thread walks a share of the slice list for each candidate in
+    // turn; thread 0 keeps the best
+    Cand c{0, INT32_MAX};
+    for (int j = 0; j < n; ++j) {
+      const int slot = cl[j];
+      const int32_t k = hk[slot];
+      if (k == own) continue;
+      const u128 ns =
+          block_sum_u128<BLOCK_THREADS / 32>(pol.null_part(v, vc, k, false, threadIdx.x, BLOCK_THREADS), usm);
+      if (threadIdx.x == 0) {
+        const Cand x = pol.cand_ns(v, vc, k, hv[slot], ns);
+        if (better(x, c)) c = x;
+      }
+    }
+    i128 Go = 0;
+    if (pol.own_walks_slices()) {
+      const u128 ns =
+          block_sum_u128<BLOCK_THREADS / 32>(pol.null_part(v, vc, own, true, threadIdx.x, BLOCK_THREADS), usm);
+      if (threadIdx.x == 0) Go = pol.own_ns(v, vc, table_get(hk, hv, bits, own), ns);
+    } else if (threadIdx.x == 0) {
+      Go = pol.own(v, vc, table_get(hk, hv, bits, own));
+    }
+    if (threadIdx.x == 0) {
+      const long long Wb = c.label != INT32_MAX ? table_get(hk, hv, bits, c.label) : 0;
+      pol.finish(v, c, Wb, Go, vc);
+    }
+  } else {
+    Cand c{0, INT32_MAX};
+    for (int j = threadIdx.x; j < n; j += BLOCK_THREADS) {
+      const int slot = cl[j];
+      const int32_t k = hk[slot];
+      if (k != own) {
+        const Cand x = pol.cand(v, vc, k, hv[slot], pol.probe(v, vc, k));
+        if (better(x, c)) c = x;
+      }
+    }
+    if (threadIdx.x == 0) *own_sm = pol.own(v, vc, table_get(hk, hv, bits, own));
+    const Cand best = block_best<BLOCK_THREADS / 32>(c, red);
+    if (threadIdx.x == 0) {
+      const long long Wb = best.label != INT32_MAX ? table_get(hk, hv, bits, best.label) : 0;
+      pol.finish(v, best, Wb, *own_sm, vc);
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += BLOCK_THREADS) {
+    const int slot = cl[j];
+    hk[slot] = -1;
+    hv[slot] = 0;
+  }
+  if (threadIdx.x == 0) *ncand = 0;
+  __syncthreads();
+}
+
+// Tier 3: one block per node, shared table of 2*deg (rounded up) slots.
 template <class Pol>
 __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_block(Pol pol, const int32_t* list, const int32_t* count_ptr) {
   constexpr int SLOTS = 1 << TIER3_BITS;
@@ -349,76 +437,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_block(Pol pol, const i
       if (threadIdx.x == 0) pol.skip(v);
       continue;
     }
-    const typename Pol::VCtx vc = pol.vctx(v);
-    const int64_t beg = pol.g.rowptr[v], end = pol.g.rowptr[v + 1];
-    const int bits = table_bits_for_degree(end - beg);
-    for (int64_t e = beg + threadIdx.x; e < end; e += BLOCK_THREADS) {
-      int32_t key;
-      long long w;
-      if (pol.edge(v, vc, e, key, w)) {
-        bool fresh;
-        const int slot = table_add_slot(hk, hv, bits, key, w, fresh);
-#if MSLICE_CHECKED
-        if (slot < 0) atomicOr(pol.g.chk, ERR_BOUNDS);
-#endif
-        if (fresh) cl[atomicAdd(&ncand, 1)] = (uint16_t)slot;
-      }
-    }
-    __syncthreads();
-    const int n = ncand;
-    const int32_t own = pol.own_key(v);
-    if (slice_parallel(n, pol.slice_count(v), BLOCK_THREADS)) {
-      // every thread walks a share of the slice list for each candidate in
-      // turn; thread 0 keeps the best
-      Cand c{0, INT32_MAX};
-      for (int j = 0; j < n; ++j) {
-        const int slot = cl[j];
-        const int32_t k = hk[slot];
-        if (k == own) continue;
-        const u128 ns =
-            block_sum_u128<BLOCK_THREADS / 32>(pol.null_part(v, vc, k, false, threadIdx.x, BLOCK_THREADS), usm);
-        if (threadIdx.x == 0) {
-          const Cand x = pol.cand_ns(v, vc, k, hv[slot], ns);
-          if (better(x, c)) c = x;
-        }
-      }
-      i128 Go = 0;
-      if (pol.own_walks_slices()) {
-        const u128 ns =
-            block_sum_u128<BLOCK_THREADS / 32>(pol.null_part(v, vc, own, true, threadIdx.x, BLOCK_THREADS), usm);
-        if (threadIdx.x == 0) Go = pol.own_ns(v, vc, table_get(hk, hv, bits, own), ns);
-      } else if (threadIdx.x == 0) {
-        Go = pol.own(v, vc, table_get(hk, hv, bits, own));
-      }
-      if (threadIdx.x == 0) {
-        const long long Wb = c.label != INT32_MAX ? table_get(hk, hv, bits, c.label) : 0;
-        pol.finish(v, c, Wb, Go, vc);
-      }
-    } else {
-      Cand c{0, INT32_MAX};
-      for (int j = threadIdx.x; j < n; j += BLOCK_THREADS) {
-        const int slot = cl[j];
-        const int32_t k = hk[slot];
-        if (k != own) {
-          const Cand x = pol.cand(v, vc, k, hv[slot], pol.probe(v, vc, k));
-          if (better(x, c)) c = x;
-        }
-      }
-      if (threadIdx.x == 0) own_sm = pol.own(v, vc, table_get(hk, hv, bits, own));
-      const Cand best = block_best<BLOCK_THREADS / 32>(c, red);
-      if (threadIdx.x == 0) {
-        const long long Wb = best.label != INT32_MAX ? table_get(hk, hv, bits, best.label) : 0;
-        pol.finish(v, best, Wb, own_sm, vc);
-      }
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < n; j += BLOCK_THREADS) {
-      const int slot = cl[j];
-      hk[slot] = -1;
-      hv[slot] = 0;
-    }
-    if (threadIdx.x == 0) ncand = 0;
-    __syncthreads();
+    block_decide_node(pol, v, hk, hv, cl, &ncand, red, usm, &own_sm);
   }
 }
 
@@ -437,19 +456,37 @@ __device__ __forceinline__ void gtable_add(int32_t* hk, long long* hv, int bits,
   atomicOr(status, ERR_HASH_FULL);
 }
 
-// Tier 4: one block per node, table in global scratch at goff[v].
+// Tier 4: one block per node.  A node whose table fits 2^TIER4_SMEM_BITS
+// slots (degree up to 4096) keeps it in dynamic shared memory (two blocks
+// per SM), as tier 3 does; a larger one uses global scratch at goff[v].
 template <class Pol>
 __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_global(Pol pol, const int32_t* list, const int32_t* count_ptr,
                                                                  int32_t* gkeys, long long* gvals, const int64_t* goff,
-                                                                 unsigned* status) {
+                                                                 unsigned* status, bool use_smem) {
+  extern __shared__ __align__(16) unsigned char t4_smem[];
+  long long* shv = reinterpret_cast<long long*>(t4_smem);
+  int32_t* shk = reinterpret_cast<int32_t*>(t4_smem + TIER4_SMEM_SLOTS * sizeof(long long));
+  uint16_t* scl = reinterpret_cast<uint16_t*>(t4_smem + TIER4_SMEM_SLOTS * (sizeof(long long) + sizeof(int32_t)));
+  __shared__ int32_t ncand;
   __shared__ Cand red[BLOCK_THREADS / 32];
   __shared__ ull usm[2 * (BLOCK_THREADS / 32)];
   __shared__ i128 own_sm;
   const int count = *count_ptr;
+  if (use_smem)
+    for (int i = threadIdx.x; i < TIER4_SMEM_SLOTS; i += BLOCK_THREADS) {
+      shk[i] = -1;
+      shv[i] = 0;
+    }
+  if (threadIdx.x == 0) ncand = 0;
+  __syncthreads();
   for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
     const int32_t v = list[idx];
     if (!pol.begin(v)) {
       if (threadIdx.x == 0) pol.skip(v);
+      continue;
+    }
+    if (use_smem && table_bits_for_degree(pol.g.rowptr[v + 1] - pol.g.rowptr[v]) <= TIER4_SMEM_BITS) {
+      block_decide_node(pol, v, shk, shv, scl, &ncand, red, usm, &own_sm);
       continue;
     }
     const typename Pol::VCtx vc = pol.vctx(v);
@@ -540,9 +577,23 @@ void decide_all(Ctx& c, const Pol& pol, const TierSegs& sg, const int32_t* tier_
         }
     }
   }
-  if (tier_cnt[4] > 0)
-    launch_on(c, st[4], k_decide_global<Pol>, dim3(152 * 2), dim3(BLOCK_THREADS), 0, pol, sg.list[4], sg.count[4],
-              gkeys, gvals, goff, c.d_status);
+  if (tier_cnt[4] > 0) {
+    // MSLICE_TIER4_SHARED=0: every tier-4 node uses global scratch
+    static const bool smem = [] {
+      const char* e = std::getenv("MSLICE_TIER4_SHARED");
+      return !(e && e[0] == '0');
+    }();
+    static bool smem_set = false;  // per policy type: the dynamic shared memory limit, set once
+    if (smem && !smem_set) {
+      check_cuda(cudaFuncSetAttribute(k_decide_global<Pol>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)TIER4_SMEM_BYTES), "tier-4 shared memory");
+      smem_set = true;
+    }
+    // with the shared table, one block per SM: its 104 KB leave room for the
+    // other tiers' blocks, which run concurrently
+    launch_on(c, st[4], k_decide_global<Pol>, dim3(smem ? 152 : 152 * 2), dim3(BLOCK_THREADS),
+              smem ? TIER4_SMEM_BYTES : 0, pol, sg.list[4], sg.count[4], gkeys, gvals, goff, c.d_status, smem);
+  }
   if (tier_cnt[3] > 0)
     launch_on(c, st[3], k_decide_block<Pol>, dim3(152 * 4), dim3(BLOCK_THREADS), 0, pol, sg.list[3], sg.count[3]);
   if (tier_cnt[2] > 0)

@@ -484,6 +484,15 @@ void run_leiden(Ctx& c, const SupraGraph& G, const std::vector<InstParams>& jobs
       cudaEvent_t t0 = clock.begin();
       const MoveOut mo = local_move(S, cur, lab, it, lvl, rounds);
       clock.end(1, t0);
+      if (mo.capped) {
+        // a level that ran out of rounds still moving: the cost of cycling
+        sync(c);
+        float ms = 0;
+        check_cuda(cudaEventElapsedTime(&ms, t0, clock.spans.back().second.second), "event time");
+        ro.ms_capped += ms;
+        ro.capped_levels++;
+        ro.capped_rounds += mo.rounds;
+      }
       if (c.trace) {
         sync(c);
         float ms = 0;

@@ -65,6 +65,7 @@ struct Ctx {
   Workspace* ws = nullptr;
   unsigned* d_status = nullptr;  // device error bits
   int64_t launches = 0;
+  int64_t host_launches = 0;     // launch calls the host made (a graph launch counts once)
   bool profile = false;          // event-time the decision kernels
   // MSLICE_TRACE: every launch is bracketed by CUDA events (per-kernel table
   // printed at the end of a solve)
@@ -84,6 +85,7 @@ inline void launch(Ctx& c, void (*k)(KArgs...), dim3 grid, dim3 block, size_t sm
   if (c.trace) trace_begin(c, (const void*)k, &e0);
   k<<<grid, block, smem, c.stream>>>(std::forward<Args>(args)...);
   c.launches++;
+  if (!c.capturing) c.host_launches++;
   check_cuda(cudaGetLastError(), "kernel launch");
   if (c.trace) trace_end(c, (const void*)k, e0);
 }
@@ -118,6 +120,7 @@ inline void launch_coop(Ctx& c, void (*k)(KArgs...), dim3 grid, dim3 block, size
   } else {
     CoopOrder order(c.stream);
     check_cuda(cudaLaunchCooperativeKernel((const void*)k, grid, block, argv, smem, c.stream), "cooperative launch");
+    c.host_launches++;
   }
   c.launches++;
   if (c.trace) trace_end(c, (const void*)k, e0);

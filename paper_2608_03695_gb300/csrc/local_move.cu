@@ -30,6 +30,7 @@
 #include <cstdlib>
 #include <cstring>
 
+#include "../../include/mslice.h"
 #include "decide.cuh"
 #include "solver.h"
 
@@ -79,27 +80,110 @@ struct TierOff {
   int32_t off[NTIERS];
 };
 
-__global__ void k_bucket(LevelDev g, const uint8_t* tier, uint64_t seed, uint64_t tag, uint64_t it, uint64_t lvl,
-                         uint64_t r, int K, int32_t* lists, int64_t row_stride, TierOff tier_off, int32_t* cursors,
-                         const int32_t* active, const int32_t* r_dev) {
-  const int lane = threadIdx.x & 31;
-  const int32_t N = g.N;
+// Bucketing in node order, in three steps over chunks of BUCKET_CHUNK
+// consecutive nodes: count every chunk's nodes per (class, tier) segment,
+// scan the counts of each segment over the chunks, then write every chunk's
+// nodes at its offsets.  The lists come out in ascending node order, so the
+// nodes a decision kernel holds in flight at any moment (a window of the
+// list) are close in node order and their gathers (neighbour labels in the
+// same snapshots, the snapshots' community-table regions) stay in L2.  A
+// chunk is one block; ranks inside a chunk come from shared-memory atomics
+// (order inside a chunk does not matter).
+constexpr int BUCKET_THREADS = 256;
+constexpr int BUCKET_ITEMS = 16;
+constexpr int64_t BUCKET_CHUNK = (int64_t)BUCKET_THREADS * BUCKET_ITEMS;
+constexpr int BUCKET_MAX_SEGS = 64 * NTIERS;  // segments (K * NTIERS) for K <= 64
+constexpr uint16_t BUCKET_FROZEN = 0xffff;    // segment of a node of a converged instance
+
+__device__ __forceinline__ int bucket_seg(const LevelDev& g, const uint8_t* tier, uint64_t seed, uint64_t tag,
+                                          uint64_t it, uint64_t lvl, uint64_t r, int K, const int32_t* active,
+                                          int64_t v) {
+  if (active && !active[node_inst(g, (int32_t)v)]) return BUCKET_FROZEN;  // converged instance: frozen
+  return vertex_class(seed, tag, it, lvl, r, local_id(g, (int32_t)v), K) * NTIERS + tier[v];
+}
+
+// Step 1: segment of every node (seg, one byte) and counts[s * nchunks + chunk].
+__global__ void __launch_bounds__(BUCKET_THREADS)
+    k_bucket_count(LevelDev g, const uint8_t* tier, uint64_t seed, uint64_t tag, uint64_t it, uint64_t lvl, uint64_t r,
+                   int K, const int32_t* active, const int32_t* r_dev, uint16_t* seg, int32_t* counts,
+                   int64_t nchunks) {
+  __shared__ int32_t cnt[BUCKET_MAX_SEGS];
   if (r_dev) r = (uint64_t)*r_dev;  // a graph replay reads its round here
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < N; base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t v = base + threadIdx.x;
-    bool ok = v < N;
-    if (ok && active && !active[node_inst(g, (int32_t)v)]) ok = false;  // converged instance: frozen
-    int seg = -1;
-    if (ok) seg = vertex_class(seed, tag, it, lvl, r, local_id(g, (int32_t)v), K) * NTIERS + tier[v];
-    const unsigned peers = __match_any_sync(0xffffffffu, seg);
-    const int leader = __ffs(peers) - 1;
-    int pos = 0;
-    if (ok && lane == leader) pos = atomicAdd(&cursors[seg], __popc(peers));
-    pos = __shfl_sync(peers, pos, leader);
-    if (ok) {
-      const int q = seg / NTIERS, t = seg % NTIERS;
-      lists[(int64_t)q * row_stride + tier_off.off[t] + pos + __popc(peers & ((1u << lane) - 1u))] = (int32_t)v;
+  const int nseg = K * NTIERS;
+  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    for (int i = threadIdx.x; i < nseg; i += BUCKET_THREADS) cnt[i] = 0;
+    __syncthreads();
+    for (int k = 0; k < BUCKET_ITEMS; ++k) {
+      const int64_t v = ch * BUCKET_CHUNK + (int64_t)k * BUCKET_THREADS + threadIdx.x;
+      if (v >= g.N) break;
+      const int sg = bucket_seg(g, tier, seed, tag, it, lvl, r, K, active, v);
+      seg[v] = (uint16_t)sg;
+      if (sg < nseg) atomicAdd(&cnt[sg], 1);
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nseg; i += BUCKET_THREADS) counts[(int64_t)i * nchunks + ch] = cnt[i];
+    __syncthreads();
+  }
+}
+
+// Step 2: one block per segment turns its counts into exclusive offsets over
+// the chunks and stores the segment's size in cursors[s].
+__global__ void __launch_bounds__(1024) k_bucket_scan(int32_t* counts, int64_t nchunks, int32_t* cursors) {
+  __shared__ int32_t part[32];
+  __shared__ int32_t carry;
+  const int s = blockIdx.x;
+  int32_t* c = counts + (int64_t)s * nchunks;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < nchunks; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const int32_t x = i < nchunks ? c[i] : 0;
+    int32_t incl = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    if (lane == 31) part[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      const int32_t p = lane < (int)(blockDim.x >> 5) ? part[lane] : 0;
+      int32_t pi = p;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, pi, d);
+        if (lane >= d) pi += y;
+      }
+      part[lane] = pi - p;
+    }
+    __syncthreads();
+    if (i < nchunks) c[i] = carry + part[w] + incl - x;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += part[w] + incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) cursors[s] = carry;
+}
+
+// Step 3: every chunk writes its nodes at its offsets.
+__global__ void __launch_bounds__(BUCKET_THREADS)
+    k_bucket_write(int32_t N, const uint16_t* seg, const int32_t* counts, int64_t nchunks, int K, int32_t* lists,
+                   int64_t row_stride, TierOff tier_off) {
+  __shared__ int32_t pos[BUCKET_MAX_SEGS];
+  const int nseg = K * NTIERS;
+  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    for (int i = threadIdx.x; i < nseg; i += BUCKET_THREADS) pos[i] = counts[(int64_t)i * nchunks + ch];
+    __syncthreads();
+    for (int k = 0; k < BUCKET_ITEMS; ++k) {
+      const int64_t v = ch * BUCKET_CHUNK + (int64_t)k * BUCKET_THREADS + threadIdx.x;
+      if (v >= N) break;
+      const int sg = seg[v];
+      if (sg >= nseg) continue;
+      const int q = sg / NTIERS, t = sg % NTIERS;
+      lists[(int64_t)q * row_stride + tier_off.off[t] + atomicAdd(&pos[sg], 1)] = (int32_t)v;
+    }
+    __syncthreads();
   }
 }
 
@@ -292,7 +376,21 @@ __device__ __forceinline__ int seg_total(const Segs& sg) {
 // Applies the sub-round's decisions: labels, community sizes and Sigma, and
 // resets each applied decision.  Moves to an empty community only leave here
 // (their label is assigned by k_empty_pass).
-__global__ void k_round_next(int32_t* r_dev) { *r_dev += 1; }
+// End of a round of the device-side loop: accounts the round (acc: rounds
+// run, moves, moves of this round), advances the round index and lets the
+// loop go on while nodes moved, rounds remain, no hash region has passed half
+// its slots (the host then rebuilds the table) and no error was raised.
+__global__ void k_round_control(cudaGraphConditionalHandle h, int32_t* r_dev, int32_t r_end, const int32_t* counters,
+                                const ull* sig_used, const unsigned* status, long long* acc) {
+  const long long moved = (long long)(((unsigned long long)(uint32_t)counters[1] << 32) | (uint32_t)counters[0]);
+  acc[0] += 1;
+  acc[1] += moved;
+  acc[2] = moved;
+  const int32_t r = *r_dev + 1;
+  *r_dev = r;
+  const bool go = moved > 0 && r < r_end && (sig_used == nullptr || *sig_used == 0) && *status == 0;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
 
 // lm_active[i] stays 1 only for instances that moved in the round; clears
 // the flags for the next round.
@@ -553,6 +651,8 @@ void solver_alloc(Solver& S) {
   S.freelist = c.ws->get<int32_t>("s_free", N + 1);
   S.tier = c.ws->get<uint8_t>("s_tier", N);
   S.cls = c.ws->get<uint8_t>("s_cls", N);
+  S.bseg = c.ws->get<uint16_t>("s_bseg", N);
+  S.bcounts = c.ws->get<int32_t>("s_bcounts", (size_t)S.p.K * NTIERS * ((N + BUCKET_CHUNK - 1) / BUCKET_CHUNK));
   S.lists = c.ws->get<int32_t>("s_lists", (size_t)N * S.p.K);
   S.cursors = c.ws->get<int32_t>("s_cursors", NTIERS * S.p.K + NTIERS);
   S.counters = c.ws->get<int32_t>("s_counters", 8);
@@ -566,7 +666,6 @@ void solver_alloc(Solver& S) {
   S.rhs = c.ws->get<ull>("s_rhs", 2 * N);
   S.elig = c.ws->get<uint8_t>("s_elig", N);
   S.wc = c.ws->get<uint8_t>("s_wc", N);
-  configure_stores(S, S.N0);
   int max_blocks = 0;
   check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_blocks, k_empty_pass, EMPTY_THREADS, 0), "occupancy");
   int dev = 0, sms = 0;
@@ -575,6 +674,7 @@ void solver_alloc(Solver& S) {
   S.empty_grid = std::max(1, std::min(max_blocks, 2) * sms);
   S.empty_blk = c.ws->get<int32_t>("s_empty_blk", 2 * S.empty_grid);
   S.round_dev = c.ws->get<int32_t>("s_round", 1);
+  S.loop_acc = c.ws->get<long long>("s_loop_acc", 3);
   S.lm_active = c.ws->get<int32_t>("s_lm_active", S.B);
   S.inst_moved = c.ws->get<int32_t>("s_inst_moved", S.B);
   check_cuda(cudaMemsetAsync(S.inst_moved, 0, S.B * sizeof(int32_t), c.stream), "memset");
@@ -619,18 +719,26 @@ void prepare_level(Solver& S, const Level& L) {
   }
 }
 
+// Level-0 nodes of every null slice: the snapshot's n (Q_MS and CPM, whose
+// null slices are the snapshots) or the instance's n*T (the global model,
+// one null slice per instance).
+static std::vector<int64_t> null_slice_nodes(const Solver& S) {
+  const SupraGraph& G = *S.G0;
+  std::vector<int64_t> out(S.Tn > 0 ? S.Tn : 1, 0);
+  for (int32_t i = 0; i < G.B; ++i) {
+    const InstInfo& in = G.inst[i];
+    if (S.p.global_null) {
+      if (i < (int32_t)out.size()) out[i] = in.n * in.T;
+    } else {
+      for (int32_t s = in.soff; s < in.soff + in.T && s < (int32_t)out.size(); ++s) out[s] = in.n;
+    }
+  }
+  return out;
+}
+
 void configure_stores(Solver& S, int64_t N) {
   Ctx& c = *S.c;
   const int64_t T = S.Tn;
-  if (!S.sig_h.slots) {
-    // hash tables keyed by (label, snapshot), sized for level 0: at most one
-    // live key per (node, snapshot) entry plus the keys created by one round
-    // of moves; a rebuild is triggered when taken slots pass half
-    const int64_t N0 = S.N0 > 0 ? S.N0 : 1;
-    const uint64_t cap = (uint64_t)(2 * N0 + 2 * ((N0 + S.p.K - 1) / S.p.K) + 64);
-    S.sig_h = HashView{nullptr, cap, c.d_status, S.sig_used};
-    S.kr_h = HashView{nullptr, cap, c.d_status, nullptr};
-  }
   S.sig = SigStore{};
   S.kr = SigStore{};
   S.sig.T = S.kr.T = (int32_t)T;
@@ -646,14 +754,29 @@ void configure_stores(Solver& S, int64_t N) {
     S.sig.d = S.sig_d;
     S.kr.d = S.kr_d;
     S.sig.rows = S.kr.rows = (N > 0 ? N : 1);
-  } else {
-    if (!S.sig_h.slots) {
-      S.sig_h.slots = c.ws->get<Slot>("s_sig", S.sig_h.cap);
-      S.kr_h.slots = c.ws->get<Slot>("s_kr", S.kr_h.cap);
-    }
-    S.sig.h = S.sig_h;
-    S.kr.h = S.kr_h;
+    return;
   }
+  if (S.region_T != T) {
+    // hash tables keyed by (label, null slice), one region per null slice
+    // sized for its level-0 nodes: at most one live key per (node, slice)
+    // entry of that slice plus the keys one round of moves creates; a
+    // rebuild is triggered once a region has taken half of its slots
+    const std::vector<int64_t> ns = null_slice_nodes(S);
+    S.region_h.assign(ns.size() + 1, 0);
+    for (size_t s = 0; s < ns.size(); ++s)
+      S.region_h[s + 1] = S.region_h[s] + (uint64_t)(2 * ns[s] + 2 * ((ns[s] + S.p.K - 1) / S.p.K) + 64);
+    const uint64_t cap = S.region_h.back();
+    uint64_t* region = c.ws->get<uint64_t>("s_region", S.region_h.size());
+    check_cuda(cudaMemcpyAsync(region, S.region_h.data(), S.region_h.size() * sizeof(uint64_t),
+                               cudaMemcpyHostToDevice, c.stream), "copy");
+    ull* rused = S.sig_used ? c.ws->get<ull>("s_region_used", ns.size()) : nullptr;
+    if (rused) check_cuda(cudaMemsetAsync(rused, 0, ns.size() * sizeof(ull), c.stream), "memset");
+    S.sig_h = HashView{c.ws->get<Slot>("s_sig", cap), cap, c.d_status, S.sig_used, region, rused};
+    S.kr_h = HashView{c.ws->get<Slot>("s_kr", cap), cap, c.d_status, nullptr, region, nullptr};
+    S.region_T = T;
+  }
+  S.sig.h = S.sig_h;
+  S.kr.h = S.kr_h;
 }
 
 // Empties a store (dense rows zeroed, hash slots freed).
@@ -671,6 +794,8 @@ static void rebuild_sigma(Solver& S, const Level& L, const int32_t* labels, bool
   const int32_t N = L.d.N;
   if (sizes) check_cuda(cudaMemsetAsync(S.size, 0, (N > 0 ? N : 1) * sizeof(int32_t), c.stream), "memset");
   if (S.sig_used) check_cuda(cudaMemsetAsync(S.sig_used, 0, sizeof(ull), c.stream), "memset");
+  if (!S.sig.d && S.sig.h.region_used)
+    check_cuda(cudaMemsetAsync(S.sig.h.region_used, 0, (S.region_h.size() - 1) * sizeof(ull), c.stream), "memset");
   clear_store(S, S.sig);
   if (N > 0)
     if (L.d.is0)
@@ -693,12 +818,20 @@ TierSegs bucket_segments(Solver& S, int q) {
 void bucket(Solver& S, const Level& L, uint64_t tag, int it, int lvl, int r, const int32_t* active,
             const int32_t* r_dev) {
   Ctx& c = *S.c;
-  check_cuda(cudaMemsetAsync(S.cursors, 0, NTIERS * S.p.K * sizeof(int32_t), c.stream), "memset");
   TierOff to;
   for (int t = 0; t < NTIERS; ++t) to.off[t] = S.tier_off[t];
-  if (L.d.N > 0)
-    launch(c, k_bucket, dim3(grid_for(L.d.N, 256)), dim3(256), 0, L.d, (const uint8_t*)S.tier, S.p.seed, tag,
-           (uint64_t)it, (uint64_t)lvl, (uint64_t)r, S.p.K, S.lists, (int64_t)S.N0, to, S.cursors, active, r_dev);
+  const int64_t N = L.d.N;
+  if (N == 0) {
+    check_cuda(cudaMemsetAsync(S.cursors, 0, NTIERS * S.p.K * sizeof(int32_t), c.stream), "memset");
+    return;
+  }
+  const int64_t nchunks = (N + BUCKET_CHUNK - 1) / BUCKET_CHUNK;
+  const unsigned grid = (unsigned)std::min<int64_t>(nchunks, fixed_grid(16));
+  launch(c, k_bucket_count, dim3(grid), dim3(BUCKET_THREADS), 0, L.d, (const uint8_t*)S.tier, S.p.seed, tag,
+         (uint64_t)it, (uint64_t)lvl, (uint64_t)r, S.p.K, active, r_dev, S.bseg, S.bcounts, nchunks);
+  launch(c, k_bucket_scan, dim3(S.p.K * NTIERS), dim3(1024), 0, S.bcounts, nchunks, S.cursors);
+  launch(c, k_bucket_write, dim3(grid), dim3(BUCKET_THREADS), 0, L.d.N, (const uint16_t*)S.bseg,
+         (const int32_t*)S.bcounts, nchunks, S.p.K, S.lists, (int64_t)S.N0, to);
 }
 
 // Chooses the degree cuts of the decision tiers for this solve: every
@@ -746,32 +879,50 @@ static void autotune_cuts(Solver& S, const Level& L, int it, int r, const int32_
   fill_i32(c, S.target, NO_MOVE, L.d.N);
 }
 
-// Captures body() on the context's stream into an executable graph; returns
-// nullptr (and leaves the stream usable) when capture is not possible.
-// kernels: how many kernel launches one replay makes.
+// Builds a graph holding one conditional WHILE node and captures body(h) on
+// the context's stream into its body graph (h: the loop's condition, set by
+// the body's last kernel).  Returns the executable graph, or nullptr (and
+// leaves the stream usable) when the loop cannot be built.  kernels: the
+// kernels one pass of the body runs.
 template <class Body>
-static cudaGraphExec_t capture_round(Ctx& c, Body&& body, int64_t& kernels) {
-  const int64_t before = c.launches;
+static cudaGraphExec_t capture_loop(Ctx& c, Body&& body, int64_t& kernels) {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  if (cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+  kernels = 0;
+  if (cudaGraphCreate(&graph, 0) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
-  c.capturing = true;
-  bool ok = true;
-  try {
-    body();
-  } catch (const Error&) {
-    ok = false;
+  cudaGraphConditionalHandle h{};
+  bool ok = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  ok = ok && cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np) == cudaSuccess;
+  ok = ok && cudaStreamBeginCaptureToGraph(c.stream, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    const int64_t before = c.launches, before_host = c.host_launches;
+    c.capturing = true;
+    try {
+      body(h);
+    } catch (const Error&) {
+      ok = false;
+    }
+    c.capturing = false;
+    cudaGraph_t captured = nullptr;
+    if (cudaStreamEndCapture(c.stream, &captured) != cudaSuccess) ok = false;
+    kernels = c.launches - before;
+    c.launches = before;
+    c.host_launches = before_host;
   }
-  c.capturing = false;
-  const cudaError_t e = cudaStreamEndCapture(c.stream, &graph);
-  if (!ok || e != cudaSuccess || !graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
-  if (graph) cudaGraphDestroy(graph);
+  if (ok && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
+  if (!ok) exec = nullptr;
+  cudaGraphDestroy(graph);
   cudaGetLastError();
-  kernels = c.launches - before;
-  c.launches = before;
   return exec;
 }
 
@@ -820,10 +971,13 @@ MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, 
                "copy");
   const int32_t* active = batch ? S.lm_active : S.inst_active;
   // One round: buckets, K sub-rounds of decisions, applies and moves to
-  // empty communities, then the moved count, the hash fill and the status
-  // word copied to the pinned buffer.  r_dev (graph replays): the round is
-  // read from and advanced on the device.
-  auto round_body = [&](int r, const int32_t* r_dev, bool prof) {
+  // empty communities, then its end:
+  //   HOST  the moved count, the table fill and the status word copied to
+  //         the pinned buffer (the host decides whether another round runs);
+  //   LOOP  k_round_control decides on the device and sets the condition of
+  //         the enclosing graph loop (r_dev holds the round).
+  enum class RoundEnd { HOST, LOOP };
+  auto round_body = [&](int r, const int32_t* r_dev, bool prof, RoundEnd end, cudaGraphConditionalHandle h) {
     check_cuda(cudaMemsetAsync(S.counters, 0, 3 * sizeof(int32_t), c.stream), "memset");
     bucket(S, L, 0, it, lvl, r, active, r_dev);
     for (int q = 0; q < S.p.K; ++q) {
@@ -846,57 +1000,104 @@ MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, 
     }
     if (batch)
       launch(c, k_round_freeze, dim3(grid_for(S.B, 256)), dim3(256), 0, S.lm_active, S.inst_moved, S.B);
+    if (end == RoundEnd::LOOP) {
+      launch(c, k_round_control, dim3(1), dim3(1), 0, h, S.round_dev, (int32_t)max_rounds,
+             (const int32_t*)S.counters, (const ull*)(S.sig.d ? nullptr : S.sig_used), (const unsigned*)c.d_status,
+             S.loop_acc);
+      return;
+    }
     check_cuda(cudaMemcpyAsync(c.pinned, S.counters, sizeof(int64_t), cudaMemcpyDeviceToHost, c.stream), "copy");
     check_cuda(cudaMemcpyAsync(static_cast<char*>(c.pinned) + 8, S.sig_used, sizeof(ull), cudaMemcpyDeviceToHost,
                                c.stream), "copy");
     check_cuda(cudaMemcpyAsync(static_cast<char*>(c.pinned) + 16, c.d_status, sizeof(unsigned),
                                cudaMemcpyDeviceToHost, c.stream), "copy");
-    if (r_dev) launch(c, k_round_next, dim3(1), dim3(1), 0, S.round_dev);
   };
-  // A level still moving after GRAPH_FROM_ROUND rounds replays one captured
-  // graph per round (one launch instead of ~7K+3 kernels and copies); capture
-  // and instantiation cost more than they save on levels that settle sooner.
-  // Not while profiling or tracing, nor on a level whose tier cuts are still
-  // being tuned.
-  // Measured: ~1% faster for batches of small instances, ~1.7% slower for a
-  // single 1.6M-node solve (its large levels keep the GPU busy between
-  // launches), so batches use graphs and single solves only on request
-  // (MSLICE_GRAPHS=1; MSLICE_NO_GRAPHS=1 turns them off).
+  // A level still moving after GRAPH_FROM_ROUND rounds runs its remaining
+  // rounds as one graph launch: a device-side loop (a conditional WHILE node)
+  // around one captured round, whose last kernel decides whether another
+  // round runs, so the host syncs once per level (or per table rebuild)
+  // instead of once per round.  Capture and instantiation cost more than
+  // they save on levels that settle sooner.  Not while profiling or tracing,
+  // nor on a level whose tier cuts are still being tuned.  Batches use it;
+  // single solves on request (MSLICE_GRAPHS=1; MSLICE_NO_GRAPHS=1 turns it
+  // off everywhere), see the design notes for the measurements.
   int64_t graph_max_nodes = GRAPH_MAX_NODES;
   if (const char* e = std::getenv("MSLICE_GRAPH_MAX_NODES")) graph_max_nodes = std::atoll(e);
   const bool want =
       (batch || N <= graph_max_nodes || std::getenv("MSLICE_GRAPHS")) && !std::getenv("MSLICE_NO_GRAPHS");
   const bool graphs = want && c.stream != nullptr && !c.profile && !c.trace && !(S.p.autotune && lvl == 0);
   cudaGraphExec_t exec = nullptr;
-  int64_t graph_kernels = 0;
+  int64_t loop_kernels = 0;
   bool graph_failed = false;
   bool rebuild = false;
-  for (int r = 0; r < max_rounds; ++r) {
+  int r = 0;
+  while (r < max_rounds) {
     if (rebuild) rebuild_sigma(S, L, labels, false);
     // tuning waits for round 2, when the partition looks like the later rounds'
     if (S.p.autotune && lvl == 0 && r == 2) autotune_cuts(S, L, it, r, active, decide);
+    if (graphs && r >= GRAPH_FROM_ROUND && !graph_failed) {
+      if (!exec) {
+        exec = capture_loop(c, [&](cudaGraphConditionalHandle h) { round_body(0, S.round_dev, false, RoundEnd::LOOP, h); },
+                            loop_kernels);
+        if (!exec) graph_failed = true;
+      }
+      if (exec) {
+        struct LoopIn {
+          int32_t r;
+          int32_t pad;
+          long long acc[3];
+        };
+        LoopIn* in = static_cast<LoopIn*>(c.pinned);
+        in->r = r;
+        in->acc[0] = in->acc[1] = in->acc[2] = 0;
+        check_cuda(cudaMemcpyAsync(S.round_dev, &in->r, sizeof(int32_t), cudaMemcpyHostToDevice, c.stream), "copy");
+        check_cuda(cudaMemcpyAsync(S.loop_acc, in->acc, 3 * sizeof(long long), cudaMemcpyHostToDevice, c.stream),
+                   "copy");
+        {
+          CoopOrder order(c.stream);
+          check_cuda(cudaGraphLaunch(exec, c.stream), "graph launch");
+        }
+        c.host_launches++;
+        struct {
+          long long acc[3];  // rounds run, moves, moves of the last round
+          ull used;
+          unsigned status;
+        } lb;
+        check_cuda(cudaMemcpyAsync(c.pinned, S.loop_acc, 3 * sizeof(long long), cudaMemcpyDeviceToHost, c.stream),
+                   "copy");
+        check_cuda(cudaMemcpyAsync(static_cast<char*>(c.pinned) + 24, S.sig_used, sizeof(ull),
+                                   cudaMemcpyDeviceToHost, c.stream), "copy");
+        check_cuda(cudaMemcpyAsync(static_cast<char*>(c.pinned) + 32, c.d_status, sizeof(unsigned),
+                                   cudaMemcpyDeviceToHost, c.stream), "copy");
+        sync(c);
+        std::memcpy(&lb, c.pinned, sizeof(lb));
+        const int64_t ran = lb.acc[0];
+        c.launches += ran * loop_kernels;
+        S.lm_rounds += ran;
+        S.lm_edges += ran * L.nnz_eff;
+        out.rounds += ran;
+        out.moves += lb.acc[1];
+        r += (int)ran;
+        if (lb.status) {
+          cudaGraphExecDestroy(exec);
+          exec = nullptr;
+          check_status(c, "local moving");
+        }
+        if (ran < 1) fail(MSLICE_ECUDA, "device round loop ran no round");
+        if (lb.acc[2] == 0) break;
+        if (r >= max_rounds) {
+          out.capped = true;
+          break;
+        }
+        rebuild = !S.sig.d && lb.used > 0;  // a region has taken half of its slots
+        continue;
+      }
+    }
     S.lm_rounds++;
     S.lm_edges += L.nnz_eff;
     const bool prof = c.profile && lvl == 0;
     if (prof) c.prof_bytes += 12 * L.nnz_eff + 40 * (int64_t)N;
-    if (graphs && r >= GRAPH_FROM_ROUND && !graph_failed) {
-      if (!exec) {
-        const int32_t r32 = r;
-        check_cuda(cudaMemcpyAsync(S.round_dev, &r32, sizeof(int32_t), cudaMemcpyHostToDevice, c.stream), "copy");
-        sync(c);  // r32 is pageable
-        exec = capture_round(c, [&] { round_body(r, S.round_dev, false); }, graph_kernels);
-        if (!exec) graph_failed = true;
-      }
-      if (exec) {
-        CoopOrder order(c.stream);
-        check_cuda(cudaGraphLaunch(exec, c.stream), "graph launch");
-        c.launches += graph_kernels;
-      } else {
-        round_body(r, nullptr, prof);
-      }
-    } else {
-      round_body(r, nullptr, prof);
-    }
+    round_body(r, nullptr, prof, RoundEnd::HOST, cudaGraphConditionalHandle{});
     sync(c);
     struct {
       int64_t moved;
@@ -909,10 +1110,12 @@ MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, 
       exec = nullptr;
       check_status(c, "local moving");
     }
-    rebuild = !S.sig.d && rb.used * 2 > S.sig.h.cap;
+    rebuild = !S.sig.d && rb.used > 0;  // a region has taken half of its slots
     out.rounds++;
     out.moves += rb.moved;
+    ++r;
     if (rb.moved == 0) break;
+    if (r == max_rounds) out.capped = true;
   }
   if (exec) cudaGraphExecDestroy(exec);
   S.lm_moves += out.moves;

@@ -27,37 +27,49 @@ __device__ __forceinline__ u128 lam_k_x(const u128* lam, int32_t s, long long k,
   return lam[s] * (u128)(ull)k * (u128)(ull)x;
 }
 
-// Per node: W(v,C\v), eligibility, initial sub-community state.
+// Per node: W(v,C\v), eligibility, initial sub-community state.  G lanes per
+// node (G = 32 at aggregated levels, whose long (snapshot, strength) lists
+// the lanes share; fewer at level 0, whose rows are short and whose nodes
+// hold one snapshot each, so a warp takes several nodes at once).
+template <int G>
 __global__ void k_ref_init(LevelDev g, const int32_t* P, SigStore sig, const u128* lam, int32_t* R, int32_t* sizeR,
                            long long* Wc, long long* Wout, uint8_t* elig, SigStore kr, long long* PR) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t v = (((int64_t)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); v < g.N; v += warps) {
-    const int32_t C = P[v];
-    const Omega om = node_omega(g, (int32_t)v);
+  const int lane = threadIdx.x & 31, gl = lane % G;
+  const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane - gl));
+  const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
+  // every lane of a warp runs the same number of iterations (shuffles below)
+  const int64_t first = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int64_t warp_first = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / G;
+  for (int64_t v0 = warp_first; v0 < g.N; v0 += groups) {
+    const int64_t v = v0 + (first - warp_first);
+    const bool ok = v < g.N;
+    const int32_t C = ok ? P[v] : 0;
+    const Omega om = ok ? node_omega(g, (int32_t)v) : Omega{1, 1};
     long long w = 0;
-    for (int64_t e = g.rowptr[v] + lane; e < g.rowptr[v + 1]; e += 32) {
-      int32_t u;
-      long long W;
-      if (edge_at(g, e, u, W, om) && P[u] == C) w += W;
-    }
-    w = warp_sum(w);
-    // a long (snapshot, strength) list is shared by the lanes; a short one
-    // (every level-0 node's) is walked by lane 0 alone
-    int64_t b, e;
-    slice_range(g, (int32_t)v, b, e);
-    const bool wide = e - b > 32;
+    if (ok)
+      for (int64_t e = g.rowptr[v] + gl; e < g.rowptr[v + 1]; e += G) {
+        int32_t u;
+        long long W;
+        if (edge_at(g, e, u, W, om) && P[u] == C) w += W;
+      }
+#pragma unroll
+    for (int m = G / 2; m >= 1; m >>= 1) w += __shfl_xor_sync(gmask, w, m);
+    // a long (snapshot, strength) list is shared by the lanes of the group;
+    // a short one (every level-0 node's) is walked by its first lane
+    int64_t b = 0, e = 0;
+    if (ok) slice_range(g, (int32_t)v, b, e);
+    const bool wide = G == 32 && e - b > 32;
     u128 rhs = 0;
-    if (wide || lane == 0)
-      for (int64_t j = b + (wide ? lane : 0); j < e; j += (wide ? 32 : 1)) {
+    if (ok && (wide || gl == 0))
+      for (int64_t j = b + (wide ? gl : 0); j < e; j += (wide ? G : 1)) {
         int32_t s;
         long long k;
         slice_entry(g, (int32_t)v, j, s, k);
         rhs += lam_k_x(lam, s, k, ss_get(sig, C, s) - k);
         ss_add(kr, (int32_t)v, s, k);
       }
-    if (wide) rhs = warp_sum_u128(rhs);
-    if (lane == 0) {
+    if (G == 32 && __any_sync(0xffffffffu, wide)) rhs = warp_sum_u128(rhs);
+    if (ok && gl == 0) {
       R[v] = (int32_t)v;
       PR[v] = (long long)(((unsigned long long)(uint32_t)C << 32) | (uint32_t)v);
       sizeR[v] = 1;
@@ -846,8 +858,12 @@ static void refine_impl(Solver& S, const Level& L, const int32_t* P, int it, int
   if (N == 0) return;
   clear_store(S, S.kr);
   long long* PR = c.ws->get<long long>("ref_PR", N);
-  launch(c, k_ref_init, dim3(fixed_grid(8)), dim3(256), 0, L.d, P, S.sig, (const u128*)S.lam, S.R, S.sizeR, S.Wc,
-         S.Wout, S.elig, S.kr, PR);
+  if (L.d.is0)
+    launch(c, k_ref_init<8>, dim3(fixed_grid(8)), dim3(256), 0, L.d, P, S.sig, (const u128*)S.lam, S.R, S.sizeR,
+           S.Wc, S.Wout, S.elig, S.kr, PR);
+  else
+    launch(c, k_ref_init<32>, dim3(fixed_grid(8)), dim3(256), 0, L.d, P, S.sig, (const u128*)S.lam, S.R, S.sizeR,
+           S.Wc, S.Wout, S.elig, S.kr, PR);
   bucket(S, L, 1, it, lvl, 0, S.inst_active);
   RefPolicy<DENSE> pol;
   pol.g = L.d;

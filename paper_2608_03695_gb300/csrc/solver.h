@@ -75,7 +75,9 @@ struct Solver {
   uint8_t* tier = nullptr;
   uint8_t* cls = nullptr;       // refinement class of every node of the level
   int32_t* lists = nullptr;     // K rows of N0 entries: nodes bucketed by class and tier
-  int32_t* cursors = nullptr;   // 3K bucket fill counts (device)
+  int32_t* cursors = nullptr;   // bucket sizes per (class, tier) segment (device)
+  uint16_t* bseg = nullptr;     // segment of every node in the round being bucketed
+  int32_t* bcounts = nullptr;   // per segment and chunk of nodes: counts, then offsets
   int32_t* counters = nullptr;  // [0] moves in round (low), [1] moves (high), [2] moves to empty in sub-round
   ull* sig_used = nullptr;      // Sigma slots taken since its last rebuild
   int32_t empty_grid = 0;       // co-resident grid of the empty-community pass
@@ -90,7 +92,8 @@ struct Solver {
   int32_t* inst_active = nullptr;  // per instance: 1 while not converged (nullptr: all active)
   int32_t* lm_active = nullptr;    // per instance: still moving in this level's local moving
   int32_t* inst_moved = nullptr;   // per instance: moved in the current round
-  int32_t* round_dev = nullptr;    // the round a captured round graph is replaying
+  int32_t* round_dev = nullptr;    // the round the device-side round loop is at
+  long long* loop_acc = nullptr;   // device-side round loop: rounds run, moves, moves of the last round
   int64_t* goff = nullptr;      // global-tier table offsets
   int32_t* gkeys = nullptr;
   long long* gvals = nullptr;
@@ -101,6 +104,8 @@ struct Solver {
   SigStore sig{};
   SigStore kr{};
   HashView sig_h{}, kr_h{};
+  std::vector<uint64_t> region_h;  // slot offsets of the hash regions (one per null slice, + 1)
+  int64_t region_T = -1;           // null slices the regions were laid out for (-1: none yet)
   long long* sig_d = nullptr;
   long long* kr_d = nullptr;
   int64_t dense_cap = 0;
@@ -131,7 +136,7 @@ void solver_alloc(Solver& S);
 constexpr int64_t DENSE_LIMIT = (int64_t)1 << 22;
 
 // Points sig/kr at dense rows (allocated on demand) or the hash tables for a
-// level of N nodes.
+// level of N nodes.  Needs the null slices (setup_null_model) first.
 void configure_stores(Solver& S, int64_t N);
 void clear_store(Solver& S, const SigStore& st);
 
@@ -140,6 +145,7 @@ void prepare_level(Solver& S, const Level& L);
 
 struct MoveOut {
   int64_t rounds = 0, moves = 0;
+  bool capped = false;  // stopped at max_rounds while nodes were still moving
 };
 // Local moving of `labels` (N entries, values in [0, N)) at level lvl.
 MoveOut local_move(Solver& S, const Level& L, int32_t* labels, int it, int lvl, int max_rounds);
@@ -213,6 +219,8 @@ struct RunOut {
   int64_t next_n = 0, next_nnz = 0;
   uint64_t next_checksum = 0;
   double ms[5] = {0, 0, 0, 0, 0};  // total, local moving, refinement, aggregation, Q
+  double ms_capped = 0;            // local moving of the levels that stopped at max_rounds still moving
+  int64_t capped_levels = 0, capped_rounds = 0;
 };
 
 // Per-instance rationals of a solve into S (host and device copies); B =

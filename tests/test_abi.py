@@ -92,7 +92,7 @@ def test_struct_layouts_match_header():
     assert C.sizeof(pkg.ServerOpts) == 16 + 8 + 8 + 32 + C.sizeof(pkg.Opts)
     assert C.sizeof(pkg.RequestInfo) == 8 + 8 + 8 + 24 + 8 + 8 + 16
     assert C.sizeof(pkg.Opts) == 4 * 4 + 8 + 4 * 8 + 4 * 4 + 4 * 4 + 2 * 8
-    assert C.sizeof(pkg.Stats) == 4 + 4 + 8 * 7 + 8 + 4 + 4 + 8 + 8 * 5 + 8 * 3 + 4 * 4
+    assert C.sizeof(pkg.Stats) == 4 + 4 + 8 * 7 + 8 + 4 + 4 + 8 + 8 * 5 + 8 * 3 + 4 * 4 + 8 * 4
 
 
 def test_struct_layouts_match_the_c_compiler(tmp_path):
