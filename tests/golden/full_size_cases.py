@@ -11,6 +11,7 @@ run the oracle live.
     python tests/golden/full_size_cases.py            # all cases (hours, one core)
     python tests/golden/full_size_cases.py powerlaw   # cases whose name starts so
     python tests/golden/full_size_cases.py --jobs 4 batched_full   # cases in parallel processes
+    python tests/golden/full_size_cases.py 'powerlaw_t64_n200k_w1_1$'   # exactly one case
 
 Each case is written to the JSON file as soon as it finishes (under a file
 lock, so parallel runs may share it).
@@ -34,9 +35,14 @@ from paper_2608_03695_gb300 import synth  # noqa: E402
 EXPECTED = os.path.join(HERE, "full_size_expected.json")
 
 # Graphs of the batched workload solved over the whole (gamma, omega) grid:
-# the largest by n whose single-thread oracle solves fit the time this
-# script is given (see the design notes for the limit).
-BATCHED_SWEEP_GRAPHS = []
+# the largest by n whose single-thread oracle solves take minutes (n = 151k,
+# 139k and 124k with T = 3-4); the two largest (n = 166k and 159k, T = 28
+# and 26) take the oracle 48 and 38 minutes per solve, too long for 17 more.
+BATCHED_SWEEP_GRAPHS = [48, 13, 44]
+
+# n of the largest stored T=64 case (the recipe's n = 1,000,000 needs ~120 GB
+# in the single-thread oracle; 200,000 needs ~25 GB)
+T64_ORACLE_N = 200_000
 
 
 def digest_arrays(arrays) -> str:
@@ -79,6 +85,15 @@ def cases():
 
     out["powerlaw_t64_n20k"] = powerlaw_t64_n20k
 
+    # the T=64 recipe at the largest n whose oracle solve fits this
+    # container's memory next to the other cases (~12 GB per 100k nodes)
+    for om in [(1, 1), (1, 10), (10, 1)]:
+        def powerlaw_t64_large(om=om):
+            snaps = synth.recipe_graph("powerlaw_t64_n1m", scale_n=T64_ORACLE_N)
+            return [dict(snaps=snaps, gamma=(1, 1), omega=om)]
+
+        out[f"powerlaw_t64_n{T64_ORACLE_N // 1000}k_w{om[0]}_{om[1]}"] = powerlaw_t64_large
+
     def batched_sample():
         specs = synth.batched_specs()
         picks = [0, 1, 2, 5]  # full-size graphs of the batched workload (n 1.6k-22k, T 7-21)
@@ -115,6 +130,15 @@ def cases():
         return [dict(stream=stream, W=W)]
 
     out["serving_chain"] = serving_chain
+
+    def serving_chain_largest():
+        # the largest live graph of the serving workload (n ~ 2M): 11 requests,
+        # the window growing to W = 8 snapshots and then sliding three times
+        W = synth.SERVING["window"]
+        spec = max(synth.serving_specs(), key=lambda s: s[0])
+        return [dict(stream=synth.serving_stream(spec, W + 3), W=W)]
+
+    out["serving_chain_largest"] = serving_chain_largest
 
     def school_full():
         # the school-shaped contact sequence (n = 327, T = 7,375) solved whole
@@ -175,7 +199,9 @@ def main(argv):
         jobs, argv = int(argv[1]), argv[2:]
     import oracle
     oracle.build()
-    names = list(cases()) if not argv else list(dict.fromkeys(n for p in argv for n in cases() if n.startswith(p)))
+    # a name ending in "$" selects that case only; others select by prefix
+    names = list(cases()) if not argv else list(dict.fromkeys(
+        n for p in argv for n in cases() if (n == p[:-1] if p.endswith("$") else n.startswith(p))))
     if jobs <= 1:
         for name in names:
             print("%s: %.1f s" % _run_case(name), flush=True)

@@ -1,0 +1,165 @@
+"""Full-size parity on the batched, large and serving workloads: labels bit
+for bit and Q within 1e-12 relative against oracle results stored by
+tests/golden/full_size_cases.py (a script that calls only the oracle).
+
+* every graph of the batched workload (64 temporal planted-partition graphs,
+  n 1k-166k, T 2-32) at gamma = omega = 1, solved one by one and packed into
+  batches as the benchmark packs them;
+* the whole 6 x 3 (gamma, omega) grid on the batched workload's largest graphs
+  whose oracle solves fit the script's time (n = 151k, 139k, 124k), each grid
+  as one batch and as plain solves;
+* the T = 64 power-law recipe at n = 200,000 (12.8M supra-nodes, the largest n
+  the single-thread oracle holds in this build's memory) at omega = 1/10, 1
+  and 10, plain and as one batch;
+* the serving workload's largest live graph (n = 1,991,289) over 11 requests,
+  the window growing to 8 snapshots and sliding three times.
+
+The inputs are regenerated here and must match the stored input digests; the
+oracle is never run live at these sizes.
+"""
+import json
+import multiprocessing as mp
+import os
+import sys
+
+import numpy as np
+import pytest
+
+import paper_2608_03695_gb300 as pkg
+from paper_2608_03695_gb300 import synth
+from qtol import q_close
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.join(HERE, "golden"))
+import full_size_cases as fsc  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+# the benchmark's packing of the batched workload
+BATCH_MAX_NODES = 1 << 21
+BATCH_MAX_ENTRIES = 1 << 26
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pkg.build()
+
+
+def stored(name):
+    data = json.load(open(fsc.EXPECTED))
+    if name not in data:
+        pytest.fail(f"no stored oracle result for {name}; run tests/golden/full_size_cases.py {name}")
+    return data[name]
+
+
+def check_input(snaps_or_stream, exp, what):
+    assert fsc.digest_snaps(snaps_or_stream) == exp["input"], f"{what}: generated input differs from the stored one"
+
+
+def _graph(k):
+    return synth.batched_graph(synth.batched_specs()[k])
+
+
+def test_batched_workload_every_graph_full_size():
+    specs = synth.batched_specs()
+    exp = [stored(f"batched_full_g{k:02d}")[0] for k in range(len(specs))]
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        graphs = pool.map(_graph, range(len(specs)), chunksize=1)
+    handles = []
+    try:
+        for k, g in enumerate(graphs):
+            check_input(g, exp[k], f"graph {k}")
+            handles.append(pkg.mslice_build(g))
+        for k, h in enumerate(handles):
+            lab, Q, _ = h.mslice_leiden()
+            assert fsc.digest_labels(lab) == exp[k]["labels"], k
+            assert q_close(Q, float(exp[k]["Q"])), k
+        # packed as the benchmark packs them
+        chunks, cur, cn, ce = [], [], 0, 0
+        for k, h in enumerate(handles):
+            if cur and (cn + h.N > BATCH_MAX_NODES or ce + h.nnz > BATCH_MAX_ENTRIES):
+                chunks.append(cur)
+                cur, cn, ce = [], 0, 0
+            cur.append(k)
+            cn += h.N
+            ce += h.nnz
+        chunks.append(cur)
+        for ch in chunks:
+            with pkg.Batch() as b:
+                for k in ch:
+                    b.add(handles[k])
+                b.run()
+                for j, k in enumerate(ch):
+                    lab, Q = b.results(j)
+                    assert fsc.digest_labels(lab) == exp[k]["labels"], ("batch", k)
+                    assert q_close(Q, float(exp[k]["Q"])), ("batch", k)
+    finally:
+        for h in handles:
+            h.close()
+
+
+@pytest.mark.parametrize("k", fsc.BATCHED_SWEEP_GRAPHS)
+def test_batched_workload_gamma_omega_grid_full_size(k):
+    grid = [(gm, om) for gm in synth.BATCHED_GAMMAS for om in synth.BATCHED_OMEGAS]
+    exp = [stored(f"batched_sweep_g{k:02d}_{gm[0]}_{gm[1]}_{om[0]}_{om[1]}")[0] for gm, om in grid]
+    snaps = _graph(k)
+    for e in exp:
+        check_input(snaps, e, f"graph {k}")
+    with pkg.mslice_build(snaps) as h:
+        for (gm, om), e in zip(grid, exp):
+            lab, Q, _ = h.mslice_leiden(gamma=gm, omega=om)
+            assert fsc.digest_labels(lab) == e["labels"], (gm, om)
+            assert q_close(Q, float(e["Q"])), (gm, om)
+        with pkg.Batch() as b:
+            for gm, om in grid:
+                b.add(h, gm, om)
+            b.run()
+            for i, e in enumerate(exp):
+                lab, Q = b.results(i)
+                assert fsc.digest_labels(lab) == e["labels"], ("batch",) + grid[i]
+                assert q_close(Q, float(e["Q"])), ("batch",) + grid[i]
+
+
+def test_T64_recipe_largest_oracle_size():
+    n = fsc.T64_ORACLE_N
+    omegas = [(1, 10), (1, 1), (10, 1)]
+    names = [f"powerlaw_t64_n{n // 1000}k_w{om[0]}_{om[1]}" for om in omegas]
+    data = json.load(open(fsc.EXPECTED))
+    have = [(om, data[nm][0]) for om, nm in zip(omegas, names) if nm in data]
+    assert have, f"no stored oracle result for {names}"
+    snaps = synth.recipe_graph("powerlaw_t64_n1m", scale_n=n)
+    for _, e in have:
+        check_input(snaps, e, "T=64 recipe")
+    with pkg.mslice_build(snaps) as h:
+        for om, e in have:
+            lab, Q, st = h.mslice_leiden(omega=om)
+            assert fsc.digest_labels(lab) == e["labels"], om
+            assert q_close(Q, float(e["Q"])), om
+            for key in ("iterations", "levels", "lm_rounds", "lm_edges", "lm_moves"):
+                assert st[key] == e["stats"][key], (om, key)
+        with pkg.Batch() as b:
+            for om, _ in have:
+                b.add(h, (1, 1), om)
+            b.run()
+            for i, (om, e) in enumerate(have):
+                lab, Q = b.results(i)
+                assert fsc.digest_labels(lab) == e["labels"], ("batch", om)
+                assert q_close(Q, float(e["Q"])), ("batch", om)
+
+
+def test_serving_largest_live_graph():
+    exp = stored("serving_chain_largest")[0]
+    s = fsc.cases()["serving_chain_largest"]()[0]
+    stream, W = s["stream"], s["W"]
+    check_input(stream, exp, "serving stream")
+    assert len(stream) >= 10
+    with pkg.Server(window=W, n_slots=2) as srv:
+        g = srv.add_graph(stream[0].n)
+        rids = [srv.submit(g, sn) for sn in stream]
+        for t, rid in enumerate(rids):
+            lab, info = srv.wait(rid)
+            assert fsc.digest_labels(lab) == exp["chain"][t]["labels"], t
+            assert q_close(info["Q"], float(exp["chain"][t]["Q"])), t
