@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="plain workload: skip the three-omega plain-vs-batched comparison")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="plain workload: skip the serving measurement at n/20")
     ap.add_argument("--workload", default="plain",
                     choices=["plain", "plain-t16", "batched", "serving", "large-sweep", "school"])
     ap.add_argument("--null", default="multislice", choices=["multislice", "global", "cpm"],
@@ -437,6 +439,13 @@ def _gen_serving(job):
 
 
 def run_serving(args):
+    line = serving_measurement(args)
+    print(json.dumps(line), flush=True)
+    if not line["identical_results"]:
+        raise SystemExit("served results differ between open loop, burst and plain paths")
+
+
+def serving_measurement(args):
     """Serving workload: 32 live graphs with windows of 8 slices.  The first
     8 snapshots of every graph fill the windows (untimed); then R snapshots per
     graph arrive as a Poisson process at the recipe's rate (open loop) and
@@ -534,11 +543,14 @@ def run_serving(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     plain = []
+    cyc = {"ms_total": 0.0, "ms_capped": 0.0, "capped_levels": 0, "capped_rounds": 0, "lm_rounds": 0}
     for g, t in seq:
         n = streams[g][0].n
-        lab, _ = _plain_window_solve(pkg, streams[g], t, W, prevs[g], n)
+        lab, _, st = _plain_window_solve(pkg, streams[g], t, W, prevs[g], n)
         prevs[g] = lab
         plain.append(digest(lab))
+        for key in cyc:
+            cyc[key] += st[key]
     t_plain = time.perf_counter() - t0
     same = same and plain == open_digest
     clk = clocks.stop()
@@ -564,13 +576,16 @@ def run_serving(args):
             "plain": {"value": nreq / t_plain, "unit": "snapshots/s",
                       "note": "one mslice_build + mslice_leiden_ex per request, same warm starts"},
             "served_over_plain": (nreq / t_burst) / (nreq / t_plain),
+            "capped_levels": {"levels": cyc["capped_levels"], "rounds": cyc["capped_rounds"],
+                              "of_rounds": cyc["lm_rounds"], "ms": cyc["ms_capped"],
+                              "share_of_solve": cyc["ms_capped"] / max(cyc["ms_total"], 1e-9),
+                              "note": "plain window solves: local-moving levels that stopped at max_rounds with "
+                                      "nodes still moving"},
             "batching": {"mean_batch": float(np.mean(batch_sizes)), "max_batch": int(max(batch_sizes)),
                          "slots_used": slots_used, "device_busy_s": busy, "busy_union_s": union,
                          "overlap": busy / union if union > 0 else 1.0},
             "identical_results": same, "generate_s": t_gen, "clocks": clk}
-    print(json.dumps(line), flush=True)
-    if not same:
-        raise SystemExit("served results differ between open loop, burst and plain paths")
+    return line
 
 
 def _plain_window_solve(pkg, snaps, t, W, prev, n):
@@ -584,8 +599,8 @@ def _plain_window_solve(pkg, snaps, t, W, prev, n):
         src = np.minimum(np.arange(len(window)) + e, w_prev - 1)
         init = np.concatenate([prev[s * n:(s + 1) * n] for s in src]).astype(np.int32)
     with pkg.mslice_build(window) as h:
-        lab, Q, _ = h.mslice_leiden(init=init)
-    return lab, Q
+        lab, Q, st = h.mslice_leiden(init=init)
+    return lab, Q, st
 
 
 def run_large(args):
@@ -729,6 +744,9 @@ def run_school(args):
     print(json.dumps(line), flush=True)
 
 
+# n scale of the serving measurement that the default run adds
+SERVING_SUB_SCALE = 0.05
+
 # Config 4's own comparison: the same graph at omega = 1/10, 1 and 10, solved
 # plain (one call per omega) and as one batch of the three instances.
 PLAIN_VS_BATCHED_OMEGAS = [(1, 10), (1, 1), (10, 1)]
@@ -746,19 +764,22 @@ def plain_vs_batched(pkg, dsnaps, stream, skw):
         return hashlib.sha1(np.ascontiguousarray(lab.cpu().numpy() if hasattr(lab, "cpu") else lab,
                                                  dtype=np.int32).tobytes()).hexdigest()
 
-    h = pkg.mslice_build(dsnaps, device_ptrs=True, stream=stream.cuda_stream)
-    try:
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        plain, edges, st_plain = [], 0, []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plain, edges, st_plain = [], 0, []
+    # the plain solves on a handle of their own, closed (with its solver
+    # scratch) before the batch is built
+    with pkg.mslice_build(dsnaps, device_ptrs=True, stream=stream.cuda_stream) as hp:
         e0.record(stream)
         for om in PLAIN_VS_BATCHED_OMEGAS:
-            lab, Q, st = h.mslice_leiden(omega=om, **skw)
+            lab, Q, st = hp.mslice_leiden(omega=om, **skw)
             plain.append((digest(lab), Q))
             edges += st["lm_edges"]
             st_plain.append(st)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms_plain = e0.elapsed_time(e1)
+    ms_plain = e0.elapsed_time(e1)
+    h = pkg.mslice_build(dsnaps, device_ptrs=True, stream=stream.cuda_stream)
+    try:
         try:
             with pkg.Batch(stream=stream.cuda_stream) as b:
                 for om in PLAIN_VS_BATCHED_OMEGAS:
@@ -908,11 +929,24 @@ def main():
         e2e = {"value": sum_over_ranks(e_edges) / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": k_e2e, "ms_per_step": 1e3 * el / k_e2e}
 
-    pvb = None
-    if args.workload == "plain" and rank == 0 and not args.no_batched and args.null == "multislice" \
-            and args.coupling == "ordinal" and not args.theta:
+    pvb = serving = None
+    default_model = args.null == "multislice" and args.coupling == "ordinal" and not args.theta
+    if args.workload == "plain" and rank == 0 and not args.no_batched and default_model:
         torch.cuda.empty_cache()
         pvb = plain_vs_batched(pkg, dsnaps, stream, {})
+    if args.workload == "plain" and rank == 0 and not args.no_serving and default_model:
+        # the serving workload with every live graph's n scaled by 1/20 (the
+        # full-size run takes --workload serving)
+        sargs = argparse.Namespace(**vars(args))
+        sargs.scale, sargs.requests, sargs.slots, sargs.graphs = SERVING_SUB_SCALE, 4, 2, None
+        sv = serving_measurement(sargs)
+        serving = {"scale_n": SERVING_SUB_SCALE, "note": "serving workload with every live graph's n scaled by "
+                   "1/20; full size: bench.py --workload serving", "achieved_per_s": sv["achieved_per_s"],
+                   "offered_per_s": sv["offered_per_s"], "latency_s": sv["latency_s"], "service_s": sv["service_s"],
+                   "capacity_per_s": sv["capacity"]["value"], "plain_per_s": sv["plain"]["value"],
+                   "served_over_plain": sv["served_over_plain"], "overlap": sv["batching"]["overlap"],
+                   "capped_levels": sv["capped_levels"],
+                   "timed_requests": sv["config"]["timed_requests"], "identical_results": sv["identical_results"]}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -932,6 +966,8 @@ def main():
             "roofline": roofline, "clocks": clk, "e2e": e2e}
     if pvb is not None:
         line["plain_vs_batched"] = pvb
+    if serving is not None:
+        line["serving"] = serving
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:

@@ -54,14 +54,13 @@ __global__ void k_contract_members(int32_t N, const int32_t* xmap, const int64_t
   }
 }
 
-__device__ __forceinline__ int64_t pow2_at_least(int64_t x) {
-  int64_t p = 2;
-  while (p < x) p <<= 1;
-  return p;
-}
+// Slots of a big row's global table for n entries: every entry could be a
+// distinct key, so twice n keeps the load at most one half (short probe
+// sequences; the power of two above 2n used before took up to twice this).
+__device__ __forceinline__ int64_t big_table_slots(int64_t n) { return 2 * n + 16; }
 
-// Rows by size: tier 0 (<= CW_MAX), 1 (<= CB_MAX), 2 (larger; its table of
-// pow2(2 * size) slots in global scratch).
+// Rows by size: tier 0 (<= CW_MAX), 1 (<= CB_MAX), 2 (larger; its tables of
+// big_table_slots(size) slots in global scratch).
 __global__ void k_contract_tier(int32_t Np, const long long* dsum, const int32_t* scnt, int32_t* lists,
                                 int32_t* tcnt, int64_t* gsize, int64_t* ssize) {
   const int lane = threadIdx.x & 31;
@@ -71,8 +70,8 @@ __global__ void k_contract_tier(int32_t Np, const long long* dsum, const int32_t
     if (x < Np) {
       const long long need = max(dsum[x], (long long)scnt[x]);
       t = need <= CW_MAX ? 0 : (need <= CB_MAX ? 1 : 2);
-      gsize[x] = t == 2 ? pow2_at_least(2 * dsum[x]) : 0;
-      ssize[x] = t == 2 ? pow2_at_least(2 * (int64_t)scnt[x]) : 0;
+      gsize[x] = t == 2 ? big_table_slots(dsum[x]) : 0;
+      ssize[x] = t == 2 ? big_table_slots(scnt[x]) : 0;
     }
     const unsigned peers = __match_any_sync(0xffffffffu, t);
     const int leader = __ffs(peers) - 1;
@@ -97,6 +96,24 @@ __device__ __forceinline__ int64_t ctab_add(int32_t* hk, long long* hv, int64_t 
       return (int64_t)i;
     }
     i = (i + 1) & mask;
+  }
+  fresh = false;
+  return -1;
+}
+
+// Insert-or-add into a global table of `cap` slots (any size): home by a
+// multiplicative hash and a multiply-high range reduction, linear probing.
+__device__ __forceinline__ int64_t gtab_add(int32_t* hk, long long* hv, int64_t cap, int32_t key, long long w,
+                                            bool& fresh) {
+  uint64_t i = __umul64hi((uint64_t)(uint32_t)key * 0x9E3779B97F4A7C15ull, (uint64_t)cap);
+  for (int64_t p = 0; p < cap; ++p) {
+    const int32_t prev = atomicCAS(&hk[i], -1, key);
+    if (prev == -1 || prev == key) {
+      atomicAdd((ull*)&hv[i], (ull)w);
+      fresh = prev == -1;
+      return (int64_t)i;
+    }
+    i = (i + 1 == (uint64_t)cap) ? 0 : i + 1;
   }
   fresh = false;
   return -1;
@@ -212,11 +229,13 @@ __global__ void __launch_bounds__(CW_WARPS * 32)
 }
 
 // One block per new node x of tier 1: a table of 2^CB_BITS slots in shared
-// memory.  Warps take members in turn; lanes stride over entries.
+// memory.  Warps take members in turn; lanes stride over entries.  Blocks
+// claim their rows one at a time from a counter (queue), which keeps them
+// busy until the list is done whatever the spread of row sizes.
 __global__ void __launch_bounds__(CB_THREADS)
     k_contract_block(LevelDev g, const int32_t* xmap, const int64_t* moff, const int32_t* mem, const int32_t* list,
                      const int32_t* count_ptr, const int64_t* eoff, const int64_t* soff, int32_t* tcol, long long* tw,
-                     int32_t* ecnt, int32_t* tsidx, long long* tsval, int32_t* scnt_out) {
+                     int32_t* ecnt, int32_t* tsidx, long long* tsval, int32_t* scnt_out, int32_t* queue) {
   extern __shared__ __align__(16) unsigned char csm[];
   __shared__ int32_t ncnt;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -230,7 +249,9 @@ __global__ void __launch_bounds__(CB_THREADS)
     K[i] = -1;
     V[i] = 0;
   }
-  for (int64_t idx = blockIdx.x; idx < count; idx += gridDim.x) {
+  __shared__ int32_t claim;
+  if (threadIdx.x == 0) claim = -1;
+  for (int idx; (idx = block_claim(queue, count, &claim)) >= 0;) {
     const int32_t x = list[idx];
     if (threadIdx.x == 0) ncnt = 0;
     __syncthreads();
@@ -340,7 +361,7 @@ __global__ void k_big_insert(LevelDev g, const int32_t* xmap, const int64_t* mof
         const int32_t y = xmap[u];
         if (y != x) {
           bool fresh;
-          const int64_t slot = ctab_add(gk + o, gv + o, cap, y, W, fresh);
+          const int64_t slot = gtab_add(gk + o, gv + o, cap, y, W, fresh);
 #if MSLICE_CHECKED
           if (slot < 0) atomicOr(g.chk, ERR_BOUNDS);
 #endif
@@ -356,7 +377,7 @@ __global__ void k_big_insert(LevelDev g, const int32_t* xmap, const int64_t* mof
       long long k;
       slice_entry(g, v, q, s, k);
       bool fresh;
-      const int64_t slot = ctab_add(sk + so, sv + so, scap, s, k, fresh);
+      const int64_t slot = gtab_add(sk + so, sv + so, scap, s, k, fresh);
 #if MSLICE_CHECKED
       if (slot < 0) atomicOr(g.chk, ERR_BOUNDS);
 #endif
@@ -533,9 +554,11 @@ bool aggregate(Solver& S, const Level& L, const int32_t* P, Level& next, const s
   if (hd.t[1] > 0) {
     check_cuda(cudaFuncSetAttribute(k_contract_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cb_smem),
                "attribute");
+    int32_t* queue = c.ws->get<int32_t>("ag_queue", 1);
+    check_cuda(cudaMemsetAsync(queue, 0, sizeof(int32_t), c.stream), "memset");
     launch(c, k_contract_block, dim3(152 * 2), dim3(CB_THREADS), cb_smem, L.d, (const int32_t*)xmap,
            (const int64_t*)moff, (const int32_t*)mem, (const int32_t*)(lists + Np), (const int32_t*)(tcnt + 1),
-           (const int64_t*)eoff, (const int64_t*)soff, tcol, tw, ecnt, tsidx, tsval, scnt_out);
+           (const int64_t*)eoff, (const int64_t*)soff, tcol, tw, ecnt, tsidx, tsval, scnt_out, queue);
   }
   if (hd.t[2] > 0) {
     if (hd.gtot > ((int64_t)1 << 31) * 8) fail(MSLICE_ENOMEM, "aggregation scratch too large");

@@ -204,9 +204,21 @@ __device__ __forceinline__ int table_add_slot(int32_t* hk, long long* hv, int bi
 // listed as their slots are claimed, so scoring touches only real
 // candidates and only those slots are reset afterwards (the table is cleared
 // once per block, not once per node).
+// Work is claimed in runs of consecutive list entries from a per-tier
+// counter (queue), a warp at a time, so the nodes in flight form a narrow
+// window of the node-ordered list and their gathers (neighbour labels, the
+// snapshots' community-table regions) stay in L2.  A static grid-stride walk
+// let the blocks drift apart over a launch (per-node cost varies widely),
+// spreading the nodes in flight over many snapshots.
+template <int G>
+struct GroupClaim {
+  static constexpr int NPG = G == 32 ? 4 : (G == 8 ? 8 : 4);  // nodes per group per claim
+  static constexpr int SIZE = (32 / G) * NPG;                 // list entries per warp claim
+};
+
 template <class Pol, int G, int BITS, int EPL>
 __global__ void __launch_bounds__(GROUP_THREADS, Pol::MIN_BLOCKS)
-    k_decide_groups(Pol pol, const int32_t* list, const int32_t* count_ptr) {
+    k_decide_groups(Pol pol, const int32_t* list, const int32_t* count_ptr, int32_t* queue) {
   constexpr int WARPS = GROUP_THREADS / 32, GPW = 32 / G, SLOTS = 1 << BITS, MAXC = SLOTS / 2;
   constexpr bool ONE_CHUNK = MAXC <= G * EPL;  // every row fits one load round
   constexpr int NG = WARPS * GPW;
@@ -228,17 +240,47 @@ __global__ void __launch_bounds__(GROUP_THREADS, Pol::MIN_BLOCKS)
   }
   if (gl == 0) ncand[gx] = 0;
   __syncwarp(gmask);
-  const int ngroups = gridDim.x * NG;
-  int idx = blockIdx.x * NG + gx;
-  if (idx >= count) return;  // uniform per group
-  int32_t v = list[idx];
-  int64_t beg = pol.g.rowptr[v], end = pol.g.rowptr[v + 1];
+  // claims of claim_size entries: group gi takes entries base + k * GPW +
+  // gi, k < npg; the next claim is taken one claim ahead (its first node's
+  // row bounds are prefetched like any next node's).  queue == nullptr: the
+  // claims are dealt to the warps round-robin instead (short lists, where
+  // the atomics would cost more than they save)
+  // (round-robin runs are one node per group, the finest dealing: a short
+  // list gives each warp few runs, and coarse runs would leave the warps
+  // that drew one run more working alone at the end)
+  const int npg = queue ? GroupClaim<G>::NPG : 1;
+  const int claim_size = GPW * npg;
+  const int warp_id = blockIdx.x * WARPS + w, warps = gridDim.x * WARPS;
+  int ticket = warp_id;
+  auto claim = [&]() -> int {
+    int b = 0;
+    if (queue) {
+      if (lane == 0) b = atomicAdd(queue, claim_size);
+      b = __shfl_sync(0xffffffffu, b, 0);
+    } else {
+      b = ticket * claim_size;
+      ticket += warps;
+    }
+    return b;
+  };
+  int base = claim();
+  if (base >= count) return;  // uniform per warp
+  int nbase = claim();
+  int k = 0;
+  int idx = base + gi;
+  bool have = idx < count;
+  int32_t v = have ? list[idx] : 0;
+  int64_t beg = have ? pol.g.rowptr[v] : 0, end = have ? pol.g.rowptr[v + 1] : 0;
   for (;;) {
-    const int nidx = idx + ngroups;
+    const bool next_claim = k + 1 == npg;  // uniform per warp
+    const int nb = next_claim ? nbase : base;
+    const int nidx = nb + (next_claim ? 0 : k + 1) * GPW + gi;
     const bool more = nidx < count;
     const int32_t nv = more ? list[nidx] : 0;
     int64_t nbeg = 0, nend = 0;
-    if (pol.begin(v)) {
+    if (!have) {
+      // past the end of the list inside the last claim
+    } else if (pol.begin(v)) {
       const typename Pol::VCtx vc = pol.vctx(v);
       // one load round: all of a lane's entries (and gathers) in flight
       // before any insert
@@ -306,8 +348,20 @@ __global__ void __launch_bounds__(GROUP_THREADS, Pol::MIN_BLOCKS)
         nend = pol.g.rowptr[nv + 1];
       }
     }
-    if (!more) break;
+    if (!have && more) {
+      nbeg = pol.g.rowptr[nv];
+      nend = pol.g.rowptr[nv + 1];
+    }
+    if (next_claim) {
+      if (nbase >= count) break;  // uniform per warp
+      base = nbase;
+      nbase = claim();
+      k = 0;
+    } else {
+      ++k;
+    }
     idx = nidx;
+    have = more;
     v = nv;
     beg = nbeg;
     end = nend;
@@ -414,8 +468,22 @@ __device__ __forceinline__ void block_decide_node(const Pol& pol, int32_t v, int
 }
 
 // Tier 3: one block per node, shared table of 2*deg (rounded up) slots.
+// Claims one node at a time from the tier's counter (thread 0), broadcast
+// through shared memory; -1 once the list is exhausted.  queue == nullptr:
+// nodes dealt to the blocks round-robin (*slot starts at -1).
+__device__ __forceinline__ int block_claim(int32_t* queue, int count, int32_t* slot) {
+  __syncthreads();  // every thread has read the previous claim
+  if (threadIdx.x == 0) {
+    const int i = queue ? atomicAdd(queue, 1) : (*slot < 0 ? (int)blockIdx.x : *slot + (int)gridDim.x);
+    *slot = i < count ? i : -(1 << 30);
+  }
+  __syncthreads();
+  return *slot < 0 ? -1 : *slot;
+}
+
 template <class Pol>
-__global__ void __launch_bounds__(BLOCK_THREADS) k_decide_block(Pol pol, const int32_t* list, const int32_t* count_ptr) {
+__global__ void __launch_bounds__(BLOCK_THREADS)
+    k_decide_block(Pol pol, const int32_t* list, const int32_t* count_ptr, int32_t* queue) {
   constexpr int SLOTS = 1 << TIER3_BITS;
   __shared__ int32_t hk[SLOTS];
   __shared__ long long hv[SLOTS];
@@ -429,9 +497,12 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_block(Pol pol, const i
     hk[i] = -1;
     hv[i] = 0;
   }
-  if (threadIdx.x == 0) ncand = 0;
-  __syncthreads();
-  for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
+  __shared__ int32_t claim;
+  if (threadIdx.x == 0) {
+    ncand = 0;
+    claim = -1;
+  }
+  for (int idx; (idx = block_claim(queue, count, &claim)) >= 0;) {
     const int32_t v = list[idx];
     if (!pol.begin(v)) {
       if (threadIdx.x == 0) pol.skip(v);
@@ -462,7 +533,7 @@ __device__ __forceinline__ void gtable_add(int32_t* hk, long long* hv, int bits,
 template <class Pol>
 __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_global(Pol pol, const int32_t* list, const int32_t* count_ptr,
                                                                  int32_t* gkeys, long long* gvals, const int64_t* goff,
-                                                                 unsigned* status, bool use_smem) {
+                                                                 unsigned* status, bool use_smem, int32_t* queue) {
   extern __shared__ __align__(16) unsigned char t4_smem[];
   long long* shv = reinterpret_cast<long long*>(t4_smem);
   int32_t* shk = reinterpret_cast<int32_t*>(t4_smem + TIER4_SMEM_SLOTS * sizeof(long long));
@@ -477,9 +548,12 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_global(Pol pol, const 
       shk[i] = -1;
       shv[i] = 0;
     }
-  if (threadIdx.x == 0) ncand = 0;
-  __syncthreads();
-  for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
+  __shared__ int32_t claim;
+  if (threadIdx.x == 0) {
+    ncand = 0;
+    claim = -1;
+  }
+  for (int idx; (idx = block_claim(queue, count, &claim)) >= 0;) {
     const int32_t v = list[idx];
     if (!pol.begin(v)) {
       if (threadIdx.x == 0) pol.skip(v);
@@ -545,10 +619,17 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_global(Pol pol, const 
   }
 }
 
+// Nodes a tier must hold at a level before its kernels claim work from a
+// counter (at the T=64, n=10^6 workload's level 0 every tier but the top one
+// does; the T=16, n=10^5 workload's lists are dealt round-robin, where the
+// counter's atomics cost more than they saved).
+constexpr int32_t DYN_CLAIM_MIN[NTIERS] = {1 << 22, 1 << 22, 1 << 21, 1 << 16, 1 << 16};
+
 // The tier lists of one sub-round (device pointers; counts on device).
 struct TierSegs {
   const int32_t* list[NTIERS];
   const int32_t* count[NTIERS];
+  int32_t* queue = nullptr;  // NTIERS work counters of the decision kernels (zeroed by decide_all)
 };
 
 // Launches the tiers of one sub-round; tier_cnt (host) skips tiers that are
@@ -559,6 +640,16 @@ void decide_all(Ctx& c, const Pol& pol, const TierSegs& sg, const int32_t* tier_
   // The tiers decide disjoint node sets with separate scratch, so they may
   // run concurrently: heaviest first, each on its own side stream (their few
   // long rows then overlap the group tiers instead of trailing them).
+  // dynamic claims only for tiers with many nodes at this level (each warp
+  // or block then takes many claims, and balancing the concurrent tiers pays
+  // for the atomics); short lists are dealt round-robin
+  int32_t* q[NTIERS];
+  bool any_dyn = false;
+  for (int t = 0; t < NTIERS; ++t) {
+    q[t] = tier_cnt[t] >= DYN_CLAIM_MIN[t] ? sg.queue + t : nullptr;
+    any_dyn = any_dyn || q[t];
+  }
+  if (any_dyn) check_cuda(cudaMemsetAsync(sg.queue, 0, NTIERS * sizeof(int32_t), c.stream), "memset");
   StreamFan* f = c.fan;
   cudaStream_t st[NTIERS] = {c.stream, c.stream, c.stream, c.stream, c.stream};
   bool used[StreamFan::kSide] = {false, false, false, false};
@@ -592,19 +683,21 @@ void decide_all(Ctx& c, const Pol& pol, const TierSegs& sg, const int32_t* tier_
     // with the shared table, one block per SM: its 104 KB leave room for the
     // other tiers' blocks, which run concurrently
     launch_on(c, st[4], k_decide_global<Pol>, dim3(smem ? 152 : 152 * 2), dim3(BLOCK_THREADS),
-              smem ? TIER4_SMEM_BYTES : 0, pol, sg.list[4], sg.count[4], gkeys, gvals, goff, c.d_status, smem);
+              smem ? TIER4_SMEM_BYTES : 0, pol, sg.list[4], sg.count[4], gkeys, gvals, goff, c.d_status, smem,
+              q[4]);
   }
   if (tier_cnt[3] > 0)
-    launch_on(c, st[3], k_decide_block<Pol>, dim3(152 * 4), dim3(BLOCK_THREADS), 0, pol, sg.list[3], sg.count[3]);
+    launch_on(c, st[3], k_decide_block<Pol>, dim3(152 * 4), dim3(BLOCK_THREADS), 0, pol, sg.list[3], sg.count[3],
+              q[3]);
   if (tier_cnt[2] > 0)
     launch_on(c, st[2], k_decide_groups<Pol, MSLICE_T2_LANES, T2_BITS, MSLICE_T2_EPL>, dim3(152 * 4), dim3(GROUP_THREADS), 0, pol,
-              sg.list[2], sg.count[2]);
+              sg.list[2], sg.count[2], q[2]);
   if (tier_cnt[1] > 0)
     launch_on(c, st[1], k_decide_groups<Pol, 8, 6, 4>, dim3(152 * 4), dim3(GROUP_THREADS), 0, pol, sg.list[1],
-              sg.count[1]);
+              sg.count[1], q[1]);
   if (tier_cnt[0] > 0)
     launch_on(c, st[0], k_decide_groups<Pol, 4, 5, 4>, dim3(152 * 4), dim3(GROUP_THREADS), 0, pol, sg.list[0],
-              sg.count[0]);
+              sg.count[0], q[0]);
   for (int k = 0; k < StreamFan::kSide; ++k)
     if (used[k]) {
       check_cuda(cudaEventRecord(f->join[k], f->side[k]), "event");

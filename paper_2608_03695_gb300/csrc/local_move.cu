@@ -675,6 +675,7 @@ void solver_alloc(Solver& S) {
   S.empty_blk = c.ws->get<int32_t>("s_empty_blk", 2 * S.empty_grid);
   S.round_dev = c.ws->get<int32_t>("s_round", 1);
   S.loop_acc = c.ws->get<long long>("s_loop_acc", 3);
+  S.wqueue = c.ws->get<int32_t>("s_wqueue", NTIERS);
   S.lm_active = c.ws->get<int32_t>("s_lm_active", S.B);
   S.inst_moved = c.ws->get<int32_t>("s_inst_moved", S.B);
   check_cuda(cudaMemsetAsync(S.inst_moved, 0, S.B * sizeof(int32_t), c.stream), "memset");
@@ -812,6 +813,7 @@ TierSegs bucket_segments(Solver& S, int q) {
     sg.list[t] = S.lists + (int64_t)q * S.N0 + S.tier_off[t];
     sg.count[t] = S.cursors + NTIERS * q + t;
   }
+  sg.queue = S.wqueue;
   return sg;
 }
 

@@ -94,6 +94,7 @@ struct Solver {
   int32_t* inst_moved = nullptr;   // per instance: moved in the current round
   int32_t* round_dev = nullptr;    // the round the device-side round loop is at
   long long* loop_acc = nullptr;   // device-side round loop: rounds run, moves, moves of the last round
+  int32_t* wqueue = nullptr;       // work counters of the decision kernels, one per degree tier
   int64_t* goff = nullptr;      // global-tier table offsets
   int32_t* gkeys = nullptr;
   long long* gvals = nullptr;
