@@ -67,18 +67,33 @@ struct alignas(16) Slot {
 // so the keys a sub-round touches, which belong to the few snapshots its
 // nodes are drawn from at any moment, stay in a small part of the table
 // (L2-resident) instead of spreading over all of it.
+//
+// Narrow tables hold 8-byte slots {community, sum}: inside a region the
+// snapshot is implied, and a sum fits 32 bits when every null slice's mass
+// (the largest sum it can reach) is below 2^32.  They take half the bytes of
+// the 16-byte {key, sum} slots and put four slots in a sector.
+struct alignas(8) Slot8 {
+  uint32_t key;  // community, EMPTY_KEY8 when free
+  uint32_t val;
+};
+constexpr uint32_t EMPTY_KEY8 = 0xffffffffu;
+
 struct HashView {
-  Slot* slots;
-  uint64_t cap;                      // all regions
+  Slot* slots;                       // 16-byte slots, or (narrow) Slot8 storage
+  uint64_t cap;                      // slots over all regions
   unsigned* status;
   ull* used = nullptr;               // optional: regions past half their capacity since the last clear
   const uint64_t* region = nullptr;  // R + 1 slot offsets
   ull* region_used = nullptr;        // optional with `used`: slots taken per region since the last clear
+  int32_t nregions = 0;
+  int32_t narrow = 0;
 };
 
 __device__ __forceinline__ ull pack_cs(int32_t c, int32_t s) {
   return ((ull)(uint32_t)c << 32) | (uint32_t)s;
 }
+
+__device__ __forceinline__ Slot8* slots8(const HashView& h) { return reinterpret_cast<Slot8*>(h.slots); }
 
 // Region of a key: its first slot and its size.
 __device__ __forceinline__ void hash_region(const HashView& h, ull key, uint64_t& base, uint64_t& size) {
@@ -89,18 +104,54 @@ __device__ __forceinline__ void hash_region(const HashView& h, ull key, uint64_t
 
 // Home slot inside the region: one multiplicative mixing step (Fibonacci
 // hashing) and a multiply-high range reduction; slot positions never affect
-// results.
+// results.  Narrow tables hash the community alone (the region fixes the
+// snapshot).
 __device__ __forceinline__ uint64_t hash_home(ull key, uint64_t base, uint64_t size) {
   return base + __umul64hi((key ^ (key >> 29)) * 0x9E3779B97F4A7C15ULL, size);
+}
+
+__device__ __forceinline__ uint64_t hash_home8(uint32_t c, uint64_t base, uint64_t size) {
+  return base + __umul64hi((ull)c * 0x9E3779B97F4A7C15ULL, size);
 }
 
 __device__ __forceinline__ uint64_t hash_next(uint64_t i, uint64_t base, uint64_t size) {
   return (i + 1 == base + size) ? base : i + 1;
 }
 
+// Counts a freshly taken slot against its region (rebuild trigger).
+__device__ __forceinline__ void hash_took_slot(const HashView& h, ull key, uint64_t size) {
+  if (!h.used) return;
+  // count the region once, when its taken slots pass half of it
+  const ull taken = atomicAdd(&h.region_used[(uint32_t)key], 1ull) + 1;
+  if (2 * taken > size && 2 * (taken - 1) <= size) atomicAdd(h.used, 1ull);
+}
+
 __device__ __forceinline__ void hash_add(const HashView& h, ull key, long long delta) {
   uint64_t base, size;
   hash_region(h, key, base, size);
+  if (h.narrow) {
+    Slot8* sl = slots8(h);
+    const uint32_t c = (uint32_t)(key >> 32);
+    uint64_t i = hash_home8(c, base, size);
+    for (uint64_t probe = 0; probe < size; ++probe) {
+      const uint32_t k = sl[i].key;
+      if (k == c) {
+        atomicAdd(&sl[i].val, (uint32_t)delta);
+        return;
+      }
+      if (k == EMPTY_KEY8) {
+        const uint32_t prev = atomicCAS(&sl[i].key, EMPTY_KEY8, c);
+        if (prev == EMPTY_KEY8 || prev == c) {
+          atomicAdd(&sl[i].val, (uint32_t)delta);
+          if (prev == EMPTY_KEY8) hash_took_slot(h, key, size);
+          return;
+        }
+      }
+      i = hash_next(i, base, size);
+    }
+    atomicOr(h.status, ERR_HASH_FULL);
+    return;
+  }
   uint64_t i = hash_home(key, base, size);
   for (uint64_t probe = 0; probe < size; ++probe) {
     ull k = h.slots[i].key;
@@ -112,11 +163,7 @@ __device__ __forceinline__ void hash_add(const HashView& h, ull key, long long d
       ull prev = atomicCAS(&h.slots[i].key, EMPTY_KEY, key);
       if (prev == EMPTY_KEY || prev == key) {
         atomicAdd((ull*)&h.slots[i].val, (ull)delta);
-        if (prev == EMPTY_KEY && h.used) {
-          // count the region once, when its taken slots pass half of it
-          const ull taken = atomicAdd(&h.region_used[(uint32_t)key], 1ull) + 1;
-          if (2 * taken > size && 2 * (taken - 1) <= size) atomicAdd(h.used, 1ull);
-        }
+        if (prev == EMPTY_KEY) hash_took_slot(h, key, size);
         return;
       }
     }
@@ -125,10 +172,27 @@ __device__ __forceinline__ void hash_add(const HashView& h, ull key, long long d
   atomicOr(h.status, ERR_HASH_FULL);
 }
 
+// A narrow slot as a 16-byte one: key = the community (EMPTY_KEY when free).
+__device__ __forceinline__ Slot widen(const Slot8& x) {
+  return Slot{x.key == EMPTY_KEY8 ? EMPTY_KEY : (ull)x.key, (long long)x.val};
+}
+
 // Read-only lookup (0 when absent).  Only valid while no thread inserts.
 __device__ __forceinline__ long long hash_get(const HashView& h, ull key) {
   uint64_t base, size;
   hash_region(h, key, base, size);
+  if (h.narrow) {
+    const Slot8* sl = slots8(h);
+    const uint32_t c = (uint32_t)(key >> 32);
+    uint64_t i = hash_home8(c, base, size);
+    for (uint64_t probe = 0; probe < size; ++probe) {
+      const Slot8 x = sl[i];
+      if (x.key == c) return (long long)x.val;
+      if (x.key == EMPTY_KEY8) return 0;
+      i = hash_next(i, base, size);
+    }
+    return 0;
+  }
   uint64_t i = hash_home(key, base, size);
   for (uint64_t probe = 0; probe < size; ++probe) {
     const Slot s = h.slots[i];
@@ -139,8 +203,25 @@ __device__ __forceinline__ long long hash_get(const HashView& h, ull key) {
   return 0;
 }
 
-// Lookup continuing from an already loaded home slot `first`.
+// Lookup continuing from an already loaded home slot `first` (narrow: as
+// widen() gives it).
 __device__ __forceinline__ long long hash_get_from(const HashView& h, ull key, const Slot& first) {
+  if (h.narrow) {
+    const uint32_t c = (uint32_t)(key >> 32);
+    if (first.key == (ull)c) return first.val;
+    if (first.key == EMPTY_KEY) return 0;
+    uint64_t base, size;
+    hash_region(h, key, base, size);
+    const Slot8* sl = slots8(h);
+    uint64_t i = hash_home8(c, base, size);
+    for (uint64_t probe = 1; probe < size; ++probe) {
+      i = hash_next(i, base, size);
+      const Slot8 x = sl[i];
+      if (x.key == c) return (long long)x.val;
+      if (x.key == EMPTY_KEY8) return 0;
+    }
+    return 0;
+  }
   if (first.key == key) return first.val;
   if (first.key == EMPTY_KEY) return 0;
   uint64_t base, size;
@@ -158,7 +239,18 @@ __device__ __forceinline__ long long hash_get_from(const HashView& h, ull key, c
 __device__ __forceinline__ Slot hash_first(const HashView& h, ull key) {
   uint64_t base, size;
   hash_region(h, key, base, size);
+  if (h.narrow) return widen(slots8(h)[hash_home8((uint32_t)(key >> 32), base, size)]);
   return h.slots[hash_home(key, base, size)];
+}
+
+// Region holding slot i (binary search over the offsets).
+__device__ __forceinline__ int32_t hash_region_of(const HashView& h, uint64_t i) {
+  int32_t lo = 0, hi = h.nregions - 1;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi + 1) >> 1;
+    if (__ldg(&h.region[mid]) <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
 }
 
 // -------------------------------------------------------------------------
@@ -232,6 +324,14 @@ __device__ __forceinline__ bool ss_entry(const SigStore& st, uint64_t i, int32_t
     if (v == 0) return false;
     c = (int32_t)(i / (uint64_t)st.T);
     s = (int32_t)(i % (uint64_t)st.T);
+    return true;
+  }
+  if (st.h.narrow) {
+    const Slot8 x = slots8(st.h)[i];
+    if (x.key == EMPTY_KEY8 || x.val == 0) return false;
+    c = (int32_t)x.key;
+    s = hash_region_of(st.h, i);
+    v = (long long)x.val;
     return true;
   }
   const Slot sl = st.h.slots[i];

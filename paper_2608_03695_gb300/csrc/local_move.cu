@@ -187,9 +187,16 @@ __global__ void __launch_bounds__(BUCKET_THREADS)
   }
 }
 
-__global__ void k_hash_clear(Slot* slots, uint64_t cap) {
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += (uint64_t)gridDim.x * blockDim.x)
-    slots[i] = Slot{EMPTY_KEY, 0};
+__global__ void k_hash_clear(HashView h) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  if (h.narrow) {
+    Slot8* sl = slots8(h);
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < h.cap; i += stride)
+      sl[i] = Slot8{EMPTY_KEY8, 0};
+  } else {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < h.cap; i += stride)
+      h.slots[i] = Slot{EMPTY_KEY, 0};
+  }
 }
 
 // Aggregated levels: one warp per node, the lanes sharing its list.
@@ -737,6 +744,29 @@ static std::vector<int64_t> null_slice_nodes(const Solver& S) {
   return out;
 }
 
+// Largest mass of a null slice, the bound on every sum its table keys hold:
+// 2m_s (Q_MS), the node count n (CPM, whose strengths are 1) or the
+// instance's 2M' in units of 1/omega_den (the global model).
+static int64_t null_slice_mass_max(const Solver& S) {
+  const SupraGraph& G = *S.G0;
+  int64_t mx = 0;
+  for (int32_t i = 0; i < G.B; ++i) {
+    const InstInfo& in = G.inst[i];
+    if (S.p.cpm) {
+      mx = std::max<int64_t>(mx, in.n);
+    } else if (S.p.global_null) {
+      u128 sum2m = 0;
+      for (int32_t s = in.soff; s < in.soff + in.T; ++s) sum2m += (u128)(ull)G.two_m_host[s];
+      const u128 m = (u128)(ull)S.od_h[i] * sum2m + (u128)(ull)S.csum_h[i];
+      mx = m >= ((u128)1 << 62) ? INT64_MAX : std::max<int64_t>(mx, (int64_t)m);
+      if (mx == INT64_MAX) break;
+    } else {
+      for (int32_t s = in.soff; s < in.soff + in.T; ++s) mx = std::max<int64_t>(mx, G.two_m_host[s]);
+    }
+  }
+  return mx;
+}
+
 void configure_stores(Solver& S, int64_t N) {
   Ctx& c = *S.c;
   const int64_t T = S.Tn;
@@ -776,6 +806,11 @@ void configure_stores(Solver& S, int64_t N) {
     S.kr_h = HashView{c.ws->get<Slot>("s_kr", cap), cap, c.d_status, nullptr, region, nullptr};
     S.region_T = T;
   }
+  // 8-byte slots when no null slice's mass reaches 2^32 (no sum can)
+  bool narrow = null_slice_mass_max(S) < ((int64_t)1 << 32);
+  if (const char* e = std::getenv("MSLICE_WIDE_SLOTS")) narrow = narrow && std::atoi(e) == 0;
+  S.sig_h.narrow = S.kr_h.narrow = narrow ? 1 : 0;
+  S.sig_h.nregions = S.kr_h.nregions = (int32_t)(S.region_h.size() - 1);
   S.sig.h = S.sig_h;
   S.kr.h = S.kr_h;
 }
@@ -786,7 +821,7 @@ void clear_store(Solver& S, const SigStore& st) {
   if (st.d)
     check_cuda(cudaMemsetAsync(st.d, 0, (size_t)st.rows * st.T * sizeof(long long), c.stream), "memset");
   else
-    launch(c, k_hash_clear, dim3(fixed_grid(8)), dim3(256), 0, st.h.slots, st.h.cap);
+    launch(c, k_hash_clear, dim3(fixed_grid(8)), dim3(256), 0, st.h);
 }
 
 // Sigma (and, optionally, the community sizes) from the labels.

@@ -230,11 +230,14 @@ def test_invalid_inputs_rejected():
         assert e.value.code == pkg.MSLICE_EOVERFLOW
 
 
+@pytest.mark.parametrize("wide", [0, 1])
 @pytest.mark.parametrize("seed", range(6))
-def test_hashed_tables_path(seed, monkeypatch):
+def test_hashed_tables_path(seed, wide, monkeypatch):
     """The hashed (label, snapshot) tables used when labels x T exceeds the
-    dense budget give the same bits as the dense rows."""
+    dense budget give the same bits as the dense rows, with 8-byte slots (the
+    default while every snapshot's mass is below 2^32) and 16-byte ones."""
     monkeypatch.setenv("MSLICE_DENSE_LIMIT", "0")
+    monkeypatch.setenv("MSLICE_WIDE_SLOTS", str(wide))
     rng = np.random.default_rng(40 + seed)
     T = int(rng.integers(1, 6))
     snaps, _ = synth.planted_partition_temporal(int(rng.integers(30, 200)), T, n_blocks=3, p_in=0.2, p_out=0.02,
@@ -253,6 +256,27 @@ def test_hashed_tables_medium(monkeypatch):
     snaps = synth.recipe_graph({**synth.RECIPES["powerlaw_t16_n100k"], "n": 6000, "T": 5})
     g, o = solve_both(snaps)
     assert_same(g, o)
+
+
+def test_hashed_tables_masses_past_32_bits(monkeypatch):
+    """Snapshots whose mass 2m_s passes 2^32 (sums that 8-byte slots cannot
+    hold) run on 16-byte slots and still match the oracle; a light snapshot
+    beside them does not change that."""
+    monkeypatch.setenv("MSLICE_DENSE_LIMIT", "0")
+    snaps, _ = synth.planted_partition_temporal(150, 3, n_blocks=4, p_in=0.3, p_out=0.03, switch_frac=0.1,
+                                                w_max=5, seed=3)
+    rng = np.random.default_rng(3)
+    heavy = []
+    for s, sn in enumerate(snaps):
+        w = sn.weights.astype(np.int64)
+        if s < 2:  # symmetric scaling keeps the snapshot symmetric
+            w = w * (1 << 25) + 7
+        heavy.append(synth.Snapshot(sn.indptr, sn.indices, w.astype(np.int32)))
+    assert int(heavy[0].weights.astype(np.int64).sum()) >= 1 << 32
+    assert int(heavy[2].weights.astype(np.int64).sum()) < 1 << 32
+    for gamma, omega in [((1, 1), (1, 1)), ((2, 1), (1 << 20, 1))]:
+        g, o = solve_both(heavy, gamma, omega)
+        assert_same(g, o)
 
 
 def test_tier_cuts_and_autotune_do_not_change_results():
