@@ -335,53 +335,126 @@ __global__ void k_big_members(const int32_t* big, const int32_t* nbig_ptr, const
     cnt[i] = moff[big[i] + 1] - moff[big[i]];
 }
 
-__global__ void k_big_insert(LevelDev g, const int32_t* xmap, const int64_t* moff, const int32_t* mem,
-                             const int32_t* big, const int32_t* nbig_ptr, const int64_t* mpre, const int64_t* gofs,
-                             const int64_t* gsize, int32_t* gk, long long* gv, uint32_t* gl, int32_t* gcnt,
-                             const int64_t* sofs, const int64_t* ssize, int32_t* sk, long long* sv, uint32_t* sl,
-                             int32_t* scnt) {
-  const int lane = threadIdx.x & 31;
+// Members of tier-2 rows are taken BI_CHUNK at a time by a block, which sums
+// their entries per target in shared memory first (the members of one coarse
+// community mostly reach the same few others, so adding every entry straight
+// into the global table serialised on a few slots) and then adds each
+// distinct target once to the row's global table.  An entry whose probe in
+// the shared table runs past BI_PROBES slots goes to the global table
+// directly; sums are integers, so the split changes nothing.
+constexpr int BI_BITS = 11, BI_SBITS = 8, BI_CHUNK = 64, BI_PROBES = 16;
+constexpr size_t BI_SMEM = ((size_t)1 << BI_BITS) * (sizeof(int32_t) + sizeof(long long) + sizeof(uint16_t)) +
+                           ((size_t)1 << BI_SBITS) * (sizeof(int32_t) + sizeof(long long) + sizeof(uint16_t));
+
+// Insert-or-add into a shared table of 2^bits slots, listing a newly taken
+// slot in L (n: its length); false when the probe limit is reached (nothing
+// added).
+__device__ __forceinline__ bool stab_add(int32_t* K, long long* V, uint16_t* L, int* n, int bits, int32_t key,
+                                         long long w) {
+  const unsigned mask = (1u << bits) - 1u;
+  unsigned i = ((uint32_t)key * 0x9E3779B1u) >> (32 - bits);
+  for (int p = 0; p < BI_PROBES; ++p) {
+    const int32_t prev = atomicCAS(&K[i], -1, key);
+    if (prev == -1 || prev == key) {
+      atomicAdd((ull*)&V[i], (ull)w);
+      if (prev == -1) L[atomicAdd(n, 1)] = (uint16_t)i;
+      return true;
+    }
+    i = (i + 1) & mask;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void big_add(int32_t* hk, long long* hv, uint32_t* hl, int64_t o, int64_t cap,
+                                        int32_t* cnt, int32_t key, long long w, const LevelDev& g) {
+  bool fresh;
+  const int64_t slot = gtab_add(hk + o, hv + o, cap, key, w, fresh);
+#if MSLICE_CHECKED
+  if (slot < 0) atomicOr(g.chk, ERR_BOUNDS);
+#endif
+  if (fresh) hl[o + atomicAdd(cnt, 1)] = (uint32_t)slot;
+}
+
+__global__ void __launch_bounds__(256)
+    k_big_insert(LevelDev g, const int32_t* xmap, const int64_t* moff, const int32_t* mem, const int32_t* big,
+                 const int32_t* nbig_ptr, const int64_t* mpre, const int64_t* gofs, const int64_t* gsize, int32_t* gk,
+                 long long* gv, uint32_t* gl, int32_t* gcnt, const int64_t* sofs, const int64_t* ssize, int32_t* sk,
+                 long long* sv, uint32_t* sl, int32_t* scnt) {
+  extern __shared__ __align__(16) unsigned char bi_smem[];
+  constexpr int EB = 1 << BI_BITS, SB = 1 << BI_SBITS;
+  long long* EV = reinterpret_cast<long long*>(bi_smem);
+  long long* SV = EV + EB;
+  int32_t* EK = reinterpret_cast<int32_t*>(SV + SB);
+  int32_t* SK = EK + EB;
+  uint16_t* EL = reinterpret_cast<uint16_t*>(SK + SB);
+  uint16_t* SL = EL + EB;
+  __shared__ int row_sh, ne, ns;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < EB; i += blockDim.x) {
+    EK[i] = -1;
+    EV[i] = 0;
+  }
+  for (int i = threadIdx.x; i < SB; i += blockDim.x) {
+    SK[i] = -1;
+    SV[i] = 0;
+  }
+  if (threadIdx.x == 0) ne = ns = 0;
   const int nbig = *nbig_ptr;
   const int64_t total = mpre[nbig];
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t f = (((int64_t)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); f < total; f += warps) {
-    int lo = 0, hi = nbig - 1;  // the big row holding member f
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (mpre[mid] <= f) lo = mid; else hi = mid - 1;
+  const int64_t chunks = (total + BI_CHUNK - 1) / BI_CHUNK;
+  for (int64_t ch = blockIdx.x; ch < chunks; ch += gridDim.x) {
+    const int64_t f0 = ch * BI_CHUNK, f1 = f0 + BI_CHUNK < total ? f0 + BI_CHUNK : total;
+    if (threadIdx.x == 0) {
+      int lo = 0, hi = nbig - 1;  // the big row holding member f0
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (mpre[mid] <= f0) lo = mid; else hi = mid - 1;
+      }
+      row_sh = lo;
     }
-    const int32_t x = big[lo];
-    const int32_t v = mem[moff[x] + (f - mpre[lo])];
-    const int64_t o = gofs[x], cap = gsize[x];
-    const Omega om = node_omega(g, v);
-    for (int64_t i = g.rowptr[v] + lane; i < g.rowptr[v + 1]; i += 32) {
-      int32_t u;
-      long long W;
-      if (edge_at(g, i, u, W, om)) {
-        const int32_t y = xmap[u];
-        if (y != x) {
-          bool fresh;
-          const int64_t slot = gtab_add(gk + o, gv + o, cap, y, W, fresh);
-#if MSLICE_CHECKED
-          if (slot < 0) atomicOr(g.chk, ERR_BOUNDS);
-#endif
-          if (fresh) gl[o + atomicAdd(&gcnt[lo], 1)] = (uint32_t)slot;
+    __syncthreads();
+    // the rows overlapping [f0, f1), one at a time (block-uniform)
+    for (int lo = row_sh; lo < nbig && mpre[lo] < f1; ++lo) {
+      const int64_t a = mpre[lo] > f0 ? mpre[lo] : f0, b = mpre[lo + 1] < f1 ? mpre[lo + 1] : f1;
+      const int32_t x = big[lo];
+      const int64_t o = gofs[x], cap = gsize[x], so = sofs[x], scap = ssize[x];
+      for (int64_t f = a + warp; f < b; f += nwarps) {
+        const int32_t v = mem[moff[x] + (f - mpre[lo])];
+        const Omega om = node_omega(g, v);
+        for (int64_t i = g.rowptr[v] + lane; i < g.rowptr[v + 1]; i += 32) {
+          int32_t u;
+          long long W;
+          if (edge_at(g, i, u, W, om)) {
+            const int32_t y = xmap[u];
+            if (y != x && !stab_add(EK, EV, EL, &ne, BI_BITS, y, W)) big_add(gk, gv, gl, o, cap, &gcnt[lo], y, W, g);
+          }
+        }
+        int64_t sb, se;
+        slice_range(g, v, sb, se);
+        for (int64_t q = sb + lane; q < se; q += 32) {
+          int32_t s;
+          long long k;
+          slice_entry(g, v, q, s, k);
+          if (!stab_add(SK, SV, SL, &ns, BI_SBITS, s, k)) big_add(sk, sv, sl, so, scap, &scnt[lo], s, k, g);
         }
       }
-    }
-    int64_t b, e;
-    slice_range(g, v, b, e);
-    const int64_t so = sofs[x], scap = ssize[x];
-    for (int64_t q = b + lane; q < e; q += 32) {
-      int32_t s;
-      long long k;
-      slice_entry(g, v, q, s, k);
-      bool fresh;
-      const int64_t slot = gtab_add(sk + so, sv + so, scap, s, k, fresh);
-#if MSLICE_CHECKED
-      if (slot < 0) atomicOr(g.chk, ERR_BOUNDS);
-#endif
-      if (fresh) sl[so + atomicAdd(&scnt[lo], 1)] = (uint32_t)slot;
+      __syncthreads();
+      const int me = ne, ms = ns;
+      __syncthreads();  // every thread has the counts before they are reset
+      if (threadIdx.x == 0) ne = ns = 0;
+      for (int j = threadIdx.x; j < me; j += blockDim.x) {
+        const int i = EL[j];
+        big_add(gk, gv, gl, o, cap, &gcnt[lo], EK[i], EV[i], g);
+        EK[i] = -1;
+        EV[i] = 0;
+      }
+      for (int j = threadIdx.x; j < ms; j += blockDim.x) {
+        const int i = SL[j];
+        big_add(sk, sv, sl, so, scap, &scnt[lo], SK[i], SV[i], g);
+        SK[i] = -1;
+        SV[i] = 0;
+      }
+      __syncthreads();
     }
   }
 }
@@ -582,7 +655,9 @@ bool aggregate(Solver& S, const Level& L, const int32_t* P, Level& next, const s
     check_cuda(cudaMemsetAsync(mcnt_big + nbig, 0, sizeof(int64_t), c.stream), "memset");
     launch(c, k_big_members, dim3(gsz(nbig)), dim3(256), 0, big, nbig_d, (const int64_t*)moff, mcnt_big);
     scan_excl(c, (const int64_t*)mcnt_big, mpre, (int64_t)nbig + 1, (int64_t*)nullptr);
-    launch(c, k_big_insert, dim3(152 * 8), dim3(256), 0, L.d, (const int32_t*)xmap, (const int64_t*)moff,
+    check_cuda(cudaFuncSetAttribute(k_big_insert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BI_SMEM),
+               "attribute");
+    launch(c, k_big_insert, dim3(152 * 4), dim3(256), BI_SMEM, L.d, (const int32_t*)xmap, (const int64_t*)moff,
            (const int32_t*)mem, big, nbig_d, (const int64_t*)mpre, (const int64_t*)gofs, (const int64_t*)gsize, gk,
            gv, gl, cnts, (const int64_t*)sofs, (const int64_t*)ssize, sk, sv, sl, cnts + nbig);
     launch(c, k_big_output, dim3(std::min<int32_t>(nbig, 152 * 4)), dim3(256), 0, big, nbig_d,

@@ -746,28 +746,60 @@ __device__ __forceinline__ bool seg3_item(const Segs3& sg, int64_t idx, int32_t&
 
 // One warp per active node: movers compute W(v, M_t \ v) over their edges to
 // other movers with the same target, then update sizes, K_{R,s} and W(R,C\R).
+// Nodes of tiers [T0, T1) of a sub-round's segments.
+template <int T0, int T1>
+__device__ __forceinline__ int seg3_total_in(const Segs3& sg) {
+  int t = 0;
+#pragma unroll
+  for (int i = T0; i < T1; ++i) t += *sg.count[i];
+  return t;
+}
+template <int T0, int T1>
+__device__ __forceinline__ bool seg3_item_in(const Segs3& sg, int64_t idx, int32_t& v) {
+#pragma unroll
+  for (int t = T0; t < T1; ++t) {
+    const int cnt = *sg.count[t];
+    if (idx < cnt) {
+      v = sg.list[t][idx];
+      return true;
+    }
+    idx -= cnt;
+  }
+  return false;
+}
+
+// Applies the sub-round's refinement moves of tiers [T0, T1): G lanes per
+// node (8 for the short rows of the low tiers, a warp otherwise).
+template <int G, int T0, int T1>
 __global__ void k_ref_apply(LevelDev g, Segs3 sg, const int32_t* P, const int32_t* target, const long long* Wc,
                             const long long* Wsel, int32_t* R, int32_t* sizeR, long long* Wout, SigStore kr,
                             long long* PR) {
-  const int lane = threadIdx.x & 31;
-  const int total = seg3_total(sg);
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t idx = (((int64_t)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); idx < total; idx += warps) {
-    int32_t v;
-    if (!seg3_item(sg, idx, v)) break;
-    const int32_t t = target[v];
-    if (t < 0) continue;
+  const int lane = threadIdx.x & 31, gl = lane % G;
+  const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane - gl));
+  const int total = seg3_total_in<T0, T1>(sg);
+  const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
+  // every lane of a warp runs the same number of iterations (shuffles below)
+  const int64_t first = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int64_t warp_first = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / G;
+  for (int64_t i0 = warp_first; i0 < total; i0 += groups) {
+    const int64_t idx = i0 + (first - warp_first);
+    int32_t v = 0, t = NO_MOVE;
+    if (idx < total && seg3_item_in<T0, T1>(sg, idx, v)) t = target[v];
     long long wp = 0;
-    const Omega om = node_omega(g, v);
-    for (int64_t e = g.rowptr[v] + lane; e < g.rowptr[v + 1]; e += 32) {
-      int32_t u;
-      long long W;
-      // a target lies in the mover's own community, so target[u] == t
-      // implies P[u] == P[v]
-      if (edge_at(g, e, u, W, om) && target[u] == t) wp += W;
+    if (t >= 0) {
+      const Omega om = node_omega(g, v);
+      for (int64_t e = g.rowptr[v] + gl; e < g.rowptr[v + 1]; e += G) {
+        int32_t u;
+        long long W;
+        // a target lies in the mover's own community, so target[u] == t
+        // implies P[u] == P[v]
+        if (edge_at(g, e, u, W, om) && target[u] == t) wp += W;
+      }
     }
-    wp = warp_sum(wp);
-    if (lane == 0) {
+#pragma unroll
+    for (int m = G / 2; m >= 1; m >>= 1) wp += __shfl_xor_sync(gmask, wp, m);
+    if (t < 0) continue;
+    if (gl == 0) {
       R[v] = t;
       PR[v] = (long long)(((unsigned long long)(uint32_t)P[v] << 32) | (uint32_t)t);
       atomicSub(&sizeR[v], 1);
@@ -775,12 +807,12 @@ __global__ void k_ref_apply(LevelDev g, Segs3 sg, const int32_t* P, const int32_
       atomicAdd((ull*)&Wout[t], (ull)(Wc[v] - 2 * Wsel[v] - wp));
       Wout[v] = 0;
     }
-    // the sub-community rows take the node's list: by the warp when long
+    // the sub-community rows take the node's list: by the group when long
     int64_t b, e;
     slice_range(g, v, b, e);
-    const bool wide = e - b > 32;
-    if (wide || lane == 0)
-      for (int64_t j = b + (wide ? lane : 0); j < e; j += (wide ? 32 : 1)) {
+    const bool wide = e - b > G;
+    if (wide || gl == 0)
+      for (int64_t j = b + (wide ? gl : 0); j < e; j += (wide ? G : 1)) {
         int32_t s;
         long long k;
         slice_entry(g, v, j, s, k);
@@ -897,7 +929,9 @@ static void refine_impl(Solver& S, const Level& L, const int32_t* P, int it, int
     } else {
       decide_all(c, pol, sg, S.tier_cnt, S.gkeys, S.gvals, S.goff);
     }
-    launch(c, k_ref_apply, dim3(fixed_grid(8)), dim3(256), 0, L.d, sg, P, (const int32_t*)S.target,
+    launch(c, k_ref_apply<8, 0, 2>, dim3(fixed_grid(8)), dim3(256), 0, L.d, sg, P, (const int32_t*)S.target,
+           (const long long*)S.Wc, (const long long*)S.Wsel, S.R, S.sizeR, S.Wout, S.kr, PR);
+    launch(c, k_ref_apply<32, 2, NTIERS>, dim3(fixed_grid(8)), dim3(256), 0, L.d, sg, P, (const int32_t*)S.target,
            (const long long*)S.Wc, (const long long*)S.Wsel, S.R, S.sizeR, S.Wout, S.kr, PR);
     launch(c, k_ref_reset, dim3(fixed_grid(4)), dim3(256), 0, sg, S.target);
   }
