@@ -392,13 +392,13 @@ __device__ __forceinline__ Cand score_range(const Pol& pol, int32_t v, const typ
 // (hk/hv of at least 2^bits slots, all free on entry and left free; cl: room
 // for 2^bits / 2 slot numbers; ncand: a shared counter, 0 on entry and left
 // 0).  The node's distinct keys are listed as their slots are claimed.
-template <class Pol>
+template <class Pol, int NT = BLOCK_THREADS>
 __device__ __forceinline__ void block_decide_node(const Pol& pol, int32_t v, int32_t* hk, long long* hv, uint16_t* cl,
                                                   int32_t* ncand, Cand* red, ull* usm, i128* own_sm) {
   const typename Pol::VCtx vc = pol.vctx(v);
   const int64_t beg = pol.g.rowptr[v], end = pol.g.rowptr[v + 1];
   const int bits = table_bits_for_degree(end - beg);
-  for (int64_t e = beg + threadIdx.x; e < end; e += BLOCK_THREADS) {
+  for (int64_t e = beg + threadIdx.x; e < end; e += NT) {
     int32_t key;
     long long w;
     if (pol.edge(v, vc, e, key, w)) {
@@ -413,7 +413,7 @@ __device__ __forceinline__ void block_decide_node(const Pol& pol, int32_t v, int
   __syncthreads();
   const int n = *ncand;
   const int32_t own = pol.own_key(v);
-  if (slice_parallel(n, pol.slice_count(v), BLOCK_THREADS)) {
+  if (slice_parallel(n, pol.slice_count(v), NT)) {
     // every thread walks a share of the slice list for each candidate in
     // turn; thread 0 keeps the best
     Cand c{0, INT32_MAX};
@@ -422,7 +422,7 @@ __device__ __forceinline__ void block_decide_node(const Pol& pol, int32_t v, int
       const int32_t k = hk[slot];
       if (k == own) continue;
       const u128 ns =
-          block_sum_u128<BLOCK_THREADS / 32>(pol.null_part(v, vc, k, false, threadIdx.x, BLOCK_THREADS), usm);
+          block_sum_u128<NT / 32>(pol.null_part(v, vc, k, false, threadIdx.x, NT), usm);
       if (threadIdx.x == 0) {
         const Cand x = pol.cand_ns(v, vc, k, hv[slot], ns);
         if (better(x, c)) c = x;
@@ -431,7 +431,7 @@ __device__ __forceinline__ void block_decide_node(const Pol& pol, int32_t v, int
     i128 Go = 0;
     if (pol.own_walks_slices()) {
       const u128 ns =
-          block_sum_u128<BLOCK_THREADS / 32>(pol.null_part(v, vc, own, true, threadIdx.x, BLOCK_THREADS), usm);
+          block_sum_u128<NT / 32>(pol.null_part(v, vc, own, true, threadIdx.x, NT), usm);
       if (threadIdx.x == 0) Go = pol.own_ns(v, vc, table_get(hk, hv, bits, own), ns);
     } else if (threadIdx.x == 0) {
       Go = pol.own(v, vc, table_get(hk, hv, bits, own));
@@ -442,7 +442,7 @@ __device__ __forceinline__ void block_decide_node(const Pol& pol, int32_t v, int
     }
   } else {
     Cand c{0, INT32_MAX};
-    for (int j = threadIdx.x; j < n; j += BLOCK_THREADS) {
+    for (int j = threadIdx.x; j < n; j += NT) {
       const int slot = cl[j];
       const int32_t k = hk[slot];
       if (k != own) {
@@ -451,14 +451,14 @@ __device__ __forceinline__ void block_decide_node(const Pol& pol, int32_t v, int
       }
     }
     if (threadIdx.x == 0) *own_sm = pol.own(v, vc, table_get(hk, hv, bits, own));
-    const Cand best = block_best<BLOCK_THREADS / 32>(c, red);
+    const Cand best = block_best<NT / 32>(c, red);
     if (threadIdx.x == 0) {
       const long long Wb = best.label != INT32_MAX ? table_get(hk, hv, bits, best.label) : 0;
       pol.finish(v, best, Wb, *own_sm, vc);
     }
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < n; j += BLOCK_THREADS) {
+  for (int j = threadIdx.x; j < n; j += NT) {
     const int slot = cl[j];
     hk[slot] = -1;
     hv[slot] = 0;
@@ -527,11 +527,12 @@ __device__ __forceinline__ void gtable_add(int32_t* hk, long long* hv, int bits,
   atomicOr(status, ERR_HASH_FULL);
 }
 
-// Tier 4: one block per node.  A node whose table fits 2^TIER4_SMEM_BITS
-// slots (degree up to 4096) keeps it in dynamic shared memory (two blocks
-// per SM), as tier 3 does; a larger one uses global scratch at goff[v].
-template <class Pol>
-__global__ void __launch_bounds__(BLOCK_THREADS) k_decide_global(Pol pol, const int32_t* list, const int32_t* count_ptr,
+// Tier 4: one block of NT threads per node.  A node whose table fits
+// 2^TIER4_SMEM_BITS slots (degree up to 4096) keeps it in dynamic shared
+// memory (one block per SM), as tier 3 does; a larger one uses global
+// scratch at goff[v].
+template <class Pol, int NT>
+__global__ void __launch_bounds__(NT) k_decide_global(Pol pol, const int32_t* list, const int32_t* count_ptr,
                                                                  int32_t* gkeys, long long* gvals, const int64_t* goff,
                                                                  unsigned* status, bool use_smem, int32_t* queue) {
   extern __shared__ __align__(16) unsigned char t4_smem[];
@@ -539,12 +540,12 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_global(Pol pol, const 
   int32_t* shk = reinterpret_cast<int32_t*>(t4_smem + TIER4_SMEM_SLOTS * sizeof(long long));
   uint16_t* scl = reinterpret_cast<uint16_t*>(t4_smem + TIER4_SMEM_SLOTS * (sizeof(long long) + sizeof(int32_t)));
   __shared__ int32_t ncand;
-  __shared__ Cand red[BLOCK_THREADS / 32];
-  __shared__ ull usm[2 * (BLOCK_THREADS / 32)];
+  __shared__ Cand red[NT / 32];
+  __shared__ ull usm[2 * (NT / 32)];
   __shared__ i128 own_sm;
   const int count = *count_ptr;
   if (use_smem)
-    for (int i = threadIdx.x; i < TIER4_SMEM_SLOTS; i += BLOCK_THREADS) {
+    for (int i = threadIdx.x; i < TIER4_SMEM_SLOTS; i += NT) {
       shk[i] = -1;
       shv[i] = 0;
     }
@@ -560,7 +561,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_global(Pol pol, const 
       continue;
     }
     if (use_smem && table_bits_for_degree(pol.g.rowptr[v + 1] - pol.g.rowptr[v]) <= TIER4_SMEM_BITS) {
-      block_decide_node(pol, v, shk, shv, scl, &ncand, red, usm, &own_sm);
+      block_decide_node<Pol, NT>(pol, v, shk, shv, scl, &ncand, red, usm, &own_sm);
       continue;
     }
     const typename Pol::VCtx vc = pol.vctx(v);
@@ -569,19 +570,19 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_global(Pol pol, const 
     const int64_t S = 1ll << bits;
     int32_t* hk = gkeys + goff[v];
     long long* hv = gvals + goff[v];
-    for (int64_t i = threadIdx.x; i < S; i += BLOCK_THREADS) {
+    for (int64_t i = threadIdx.x; i < S; i += NT) {
       hk[i] = -1;
       hv[i] = 0;
     }
     __syncthreads();
-    for (int64_t e = beg + threadIdx.x; e < end; e += BLOCK_THREADS) {
+    for (int64_t e = beg + threadIdx.x; e < end; e += NT) {
       int32_t key;
       long long w;
       if (pol.edge(v, vc, e, key, w)) gtable_add(hk, hv, bits, key, w, status);
     }
     __syncthreads();
     const int32_t own = pol.own_key(v);
-    if (slice_parallel(end - beg, pol.slice_count(v), BLOCK_THREADS)) {
+    if (slice_parallel(end - beg, pol.slice_count(v), NT)) {
       // (the degree bounds the candidates) the block splits each
       // candidate's slice walk; thread 0 keeps the best
       Cand c{0, INT32_MAX};
@@ -589,7 +590,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_global(Pol pol, const 
         const int32_t k = hk[i];
         if (k < 0 || k == own) continue;
         const u128 ns =
-            block_sum_u128<BLOCK_THREADS / 32>(pol.null_part(v, vc, k, false, threadIdx.x, BLOCK_THREADS), usm);
+            block_sum_u128<NT / 32>(pol.null_part(v, vc, k, false, threadIdx.x, NT), usm);
         if (threadIdx.x == 0) {
           const Cand x = pol.cand_ns(v, vc, k, hv[i], ns);
           if (better(x, c)) c = x;
@@ -598,7 +599,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_global(Pol pol, const 
       i128 Go = 0;
       if (pol.own_walks_slices()) {
         const u128 ns =
-            block_sum_u128<BLOCK_THREADS / 32>(pol.null_part(v, vc, own, true, threadIdx.x, BLOCK_THREADS), usm);
+            block_sum_u128<NT / 32>(pol.null_part(v, vc, own, true, threadIdx.x, NT), usm);
         if (threadIdx.x == 0) Go = pol.own_ns(v, vc, table_get(hk, hv, bits, own), ns);
       } else if (threadIdx.x == 0) {
         Go = pol.own(v, vc, table_get(hk, hv, bits, own));
@@ -609,7 +610,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_global(Pol pol, const 
       }
     } else {
       if (threadIdx.x == 0) own_sm = pol.own(v, vc, table_get(hk, hv, bits, own));
-      const Cand best = block_best<BLOCK_THREADS / 32>(score_range(pol, v, vc, own, hk, hv, S), red);
+      const Cand best = block_best<NT / 32>(score_range(pol, v, vc, own, hk, hv, S), red);
       if (threadIdx.x == 0) {
         const long long Wb = best.label != INT32_MAX ? table_get(hk, hv, bits, best.label) : 0;
         pol.finish(v, best, Wb, own_sm, vc);
@@ -631,6 +632,23 @@ struct TierSegs {
   const int32_t* count[NTIERS];
   int32_t* queue = nullptr;  // NTIERS work counters of the decision kernels (zeroed by decide_all)
 };
+
+constexpr int64_t T4_WIDE_BELOW = 1 << 22;
+
+template <class Pol, int NT>
+void launch_tier4(Ctx& c, cudaStream_t st, const Pol& pol, const TierSegs& sg, int32_t* gkeys, long long* gvals,
+                  const int64_t* goff, bool smem, int32_t* queue) {
+  static bool smem_set = false;  // per instantiation: the dynamic shared memory limit, set once
+  if (smem && !smem_set) {
+    check_cuda(cudaFuncSetAttribute(k_decide_global<Pol, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)TIER4_SMEM_BYTES), "tier-4 shared memory");
+    smem_set = true;
+  }
+  // with the shared table, one block per SM: its 104 KB leave room for the
+  // other tiers' blocks, which run concurrently
+  launch_on(c, st, k_decide_global<Pol, NT>, dim3(smem ? 152 : 152 * 2048 / NT), dim3(NT),
+            smem ? TIER4_SMEM_BYTES : 0, pol, sg.list[4], sg.count[4], gkeys, gvals, goff, c.d_status, smem, queue);
+}
 
 // Launches the tiers of one sub-round; tier_cnt (host) skips tiers that are
 // empty at this level.  Grids are fixed multiples of the 152 SMs.
@@ -674,17 +692,14 @@ void decide_all(Ctx& c, const Pol& pol, const TierSegs& sg, const int32_t* tier_
       const char* e = std::getenv("MSLICE_TIER4_SHARED");
       return !(e && e[0] == '0');
     }();
-    static bool smem_set = false;  // per policy type: the dynamic shared memory limit, set once
-    if (smem && !smem_set) {
-      check_cuda(cudaFuncSetAttribute(k_decide_global<Pol>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)TIER4_SMEM_BYTES), "tier-4 shared memory");
-      smem_set = true;
-    }
-    // with the shared table, one block per SM: its 104 KB leave room for the
-    // other tiers' blocks, which run concurrently
-    launch_on(c, st[4], k_decide_global<Pol>, dim3(smem ? 152 : 152 * 2), dim3(BLOCK_THREADS),
-              smem ? TIER4_SMEM_BYTES : 0, pol, sg.list[4], sg.count[4], gkeys, gvals, goff, c.d_status, smem,
-              q[4]);
+    // 32 warps per tier-4 block where the group tiers hold few nodes (coarse
+    // levels, where the hubs are the whole sub-round), 16 beside long group
+    // tiers, whose blocks share the SMs
+    const int64_t group_nodes = (int64_t)tier_cnt[0] + tier_cnt[1] + tier_cnt[2];
+    if (group_nodes < T4_WIDE_BELOW)
+      launch_tier4<Pol, 1024>(c, st[4], pol, sg, gkeys, gvals, goff, smem, q[4]);
+    else
+      launch_tier4<Pol, 512>(c, st[4], pol, sg, gkeys, gvals, goff, smem, q[4]);
   }
   if (tier_cnt[3] > 0)
     launch_on(c, st[3], k_decide_block<Pol>, dim3(152 * 4), dim3(BLOCK_THREADS), 0, pol, sg.list[3], sg.count[3],

@@ -497,8 +497,8 @@ void run_leiden(Ctx& c, const SupraGraph& G, const std::vector<InstParams>& jobs
         sync(c);
         float ms = 0;
         cudaEventElapsedTime(&ms, t0, clock.spans.back().second.second);
-        fprintf(stderr, "[mslice level] it=%d lvl=%d N=%d nnz=%lld rounds=%lld moves=%lld lm_ms=%.3f\n", it, lvl,
-                cur.d.N, (long long)cur.nnz, (long long)mo.rounds, (long long)mo.moves, ms);
+        fprintf(stderr, "[mslice level] it=%d lvl=%d N=%d nnz=%lld ns=%lld rounds=%lld moves=%lld lm_ms=%.3f\n", it,
+                lvl, cur.d.N, (long long)cur.nnz, (long long)cur.ns, (long long)mo.rounds, (long long)mo.moves, ms);
       }
       if (lvl == 0) ro.last_level0_moves = mo.moves;
       if (stop_here && stop_stage == 1) {
