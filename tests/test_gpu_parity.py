@@ -122,6 +122,32 @@ def test_degree_tiers():
     assert np.array_equal(g[0], o[0]) and g[2]["next_checksum"] == o[2]["next_checksum"]
 
 
+@pytest.mark.parametrize("shared", ["1", "0"])
+def test_hubs_past_the_shared_table(shared, monkeypatch):
+    """Hubs of degree 5,000 and 9,000, past the 8,192-slot shared tables of
+    the top tier (their tables live in global scratch), beside one that fits
+    (1,500); shared = 0 puts every top-tier node in global scratch."""
+    monkeypatch.setenv("MSLICE_TIER4_SHARED", shared)
+    rng = np.random.default_rng(11)
+    n = 12000
+    us, vs = [], []
+    for hub, deg in [(0, 9000), (1, 5000), (2, 1500)]:
+        us.append(np.full(deg, hub))
+        vs.append(rng.choice(np.arange(10, n), size=deg, replace=False))
+    us.append(rng.integers(10, n, 30000))
+    vs.append(rng.integers(10, n, 30000))
+    u = np.concatenate(us)
+    v = np.concatenate(vs)
+    key = np.unique(np.minimum(u, v) * n + np.maximum(u, v))
+    u, v = key // n, key % n
+    ok = u != v
+    u, v = u[ok], v[ok]
+    snaps = [synth.csr_from_edges(n, u, v, rng.integers(1, 5, size=len(u))) for _ in range(2)]
+    for gamma, omega in [((1, 1), (1, 2)), ((1, 4), (1, 1))]:
+        g, o = solve_both(snaps, gamma, omega)
+        assert_same(g, o)
+
+
 def test_modularity_parity():
     snaps = synth.recipe_graph("planted_t4_n1000")
     rng = np.random.default_rng(0)
