@@ -140,6 +140,15 @@ def cases():
 
     out["serving_chain_largest"] = serving_chain_largest
 
+    def serving_chain_largest_fifth():
+        # the same live graph with the serving workload's n scaled by 1/5
+        # (n ~ 400k, windows up to 3.2M supra-nodes), 11 requests
+        W = synth.SERVING["window"]
+        spec = max(synth.serving_specs(0.2), key=lambda s: s[0])
+        return [dict(stream=synth.serving_stream(spec, W + 3), W=W)]
+
+    out["serving_chain_largest_fifth"] = serving_chain_largest_fifth
+
     def school_full():
         # the school-shaped contact sequence (n = 327, T = 7,375) solved whole
         return [dict(snaps=synth.recipe_graph("school_t7375_n327"), gamma=(1, 1), omega=(1, 1))]

@@ -12,7 +12,8 @@ tests/golden/full_size_cases.py (a script that calls only the oracle).
   the single-thread oracle holds in this build's memory) at omega = 1/10, 1
   and 10, plain and as one batch;
 * the serving workload's largest live graph (n = 1,991,289) over 11 requests,
-  the window growing to 8 snapshots and sliding three times.
+  the window growing to 8 snapshots and sliding three times, and the same
+  graph with the workload's n scaled by 1/5.
 
 The inputs are regenerated here and must match the stored input digests; the
 oracle is never run live at these sizes.
@@ -151,9 +152,10 @@ def test_T64_recipe_largest_oracle_size():
                 assert q_close(Q, float(e["Q"])), ("batch", om)
 
 
-def test_serving_largest_live_graph():
-    exp = stored("serving_chain_largest")[0]
-    s = fsc.cases()["serving_chain_largest"]()[0]
+@pytest.mark.parametrize("case", ["serving_chain_largest", "serving_chain_largest_fifth"])
+def test_serving_largest_live_graph(case):
+    exp = stored(case)[0]
+    s = fsc.cases()[case]()[0]
     stream, W = s["stream"], s["W"]
     check_input(stream, exp, "serving stream")
     assert len(stream) >= 10
